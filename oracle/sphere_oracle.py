@@ -1,0 +1,465 @@
+"""Plain, slow CPU FP64 oracle for the double-Fourier-sphere (DFS) spectral
+Poisson solver on the unit sphere (Townsend, Wilber & Wright, "Computing with
+functions in spherical and polar geometries I. The sphere", Section 5).
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and bench.py's
+CPU-baseline / reference legs may import this module.  The product path (the
+CUDA library and its Python binding) never calls it, and the two share no code.
+
+What it computes, step by step in the paper's order and notation:
+
+  1. DFS doubling (Section 2.2, eq. BMCsphere): the samples f(lambda, theta) on
+     theta in (0, pi) are extended to ftilde on [-pi, pi]^2 by the glide
+     reflection ftilde(lambda, -theta) = f(lambda + pi, theta).  The grid is the
+     pole-free DFS grid theta_p = -pi + (p + 1/2) 2pi/m, lambda_q = -pi + 2pi q/n
+     with m = 2 n_theta, n = n_lambda (the paper is silent on the grid; this is
+     the pole-avoiding alternative it mentions at the end of Section 4).
+  2. F = matrix of 2D Fourier coefficients of sin^2(theta) ftilde in the
+     expansion of eq. 2DFourierExpansion, j in [-m/2, m/2-1], k in [-n/2, n/2-1],
+     computed by a naive 2D DFT (two dense DFT-matrix products) of the sampled
+     product, normalised by 1/(mn).
+  3. For each k the column system of eq. linearSystems,
+        (M_sin^2 D_m^2 + M_cos M_sin D_m - k^2 I) X_k = F_k,
+     with D_m, M_cos (Section 5) and M_sin (eq. Msin).  The sign of the k^2
+     term follows the Sylvester form (eq. SylvesterSphericalPoisson): the
+     column k of X D_n^2 is -k^2 X_k.  For k = 0 the zeroth row is replaced by
+     w^T X_0 = 0 (eq. pentdiagonalPlusRankOne) with the weights w of
+     eq. integrationCoeffs.
+     Two readings of the truncated operator:
+       "A" (literal): the products of the truncated m x m matrices.
+       "B" (default): the exact banded entries of the infinite operator,
+           a_j = (j-1)(j-2)/4 at column j-2, b_j = -j^2/2 - k^2, c_j =
+           (j+1)(j+2)/4 at column j+2, on the symmetric window
+           j in [-(m/2-1), m/2-1]; the theta-Nyquist mode j = -m/2 is zero.
+  4. u = real part of the inverse 2D expansion (eq. tildeuFourierExpansion)
+     evaluated on the theta > 0 half of the DFS grid.
+
+The per-k systems are solved by dense LU (numpy.linalg.solve) at small m and
+by LAPACK's banded LU (scipy.linalg.solve_banded) otherwise; neither uses the
+parity split or the BMC fold, which are properties the tests check.
+
+Also here: the surface integral sum2 (Section 4, Integration, eq.
+integrationCoeffs) and the transpose (adjoint) of the whole linear map f -> u,
+both matrix-free and as a dense matrix for tiny grids.
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+try:  # scipy's banded LU is used for grids too large for dense LU
+    import scipy.linalg as _sla
+except Exception:  # pragma: no cover - scipy is present wherever the oracle runs
+    _sla = None
+
+DENSE_MAX_M = 256  # dense LU per k up to this DFS size
+
+
+# ----------------------------------------------------------------------------
+# Grid and DFS doubling (Section 2)
+# ----------------------------------------------------------------------------
+
+def dfs_theta(m: int) -> np.ndarray:
+    """DFS colatitudes theta_p = -pi + (p + 1/2) 2 pi / m, p = 0..m-1."""
+    p = np.arange(m, dtype=np.float64)
+    return -math.pi + (p + 0.5) * 2.0 * math.pi / m
+
+
+def dfs_lambda(n: int) -> np.ndarray:
+    """DFS longitudes lambda_q = -pi + 2 pi q / n, q = 0..n-1."""
+    q = np.arange(n, dtype=np.float64)
+    return -math.pi + 2.0 * math.pi * q / n
+
+
+def dfs_double(f: np.ndarray) -> np.ndarray:
+    """eq. BMCsphere: ftilde on the m x n DFS grid from f on n_theta x n_lambda.
+
+    Rows p >= n_theta hold theta_p = theta_{p - n_theta} > 0, where ftilde = f.
+    Rows p < n_theta hold theta_p = -theta_{n_theta-1-p} < 0, where
+    ftilde(lambda, theta) = f(lambda + pi, -theta) (lambda + pi taken mod 2 pi,
+    which is the grid shift q -> q + n/2).
+    """
+    f = np.asarray(f, dtype=np.float64)
+    nt, n = f.shape
+    if n % 2:
+        raise ValueError("n_lambda must be even for the DFS glide reflection")
+    ft = np.empty((2 * nt, n), dtype=np.float64)
+    ft[nt:] = f
+    shifted = np.roll(f, -(n // 2), axis=1)          # shifted[:, q] = f[:, q + n/2]
+    ft[:nt] = shifted[::-1]                            # row p <- f row n_theta-1-p
+    return ft
+
+
+# ----------------------------------------------------------------------------
+# 2D Fourier coefficients and samples (Section 4, eq. 2DFourierExpansion)
+# ----------------------------------------------------------------------------
+
+def _phase_theta(m: int) -> np.ndarray:
+    """E[j + m/2, p] = exp(-i j theta_p), the exponent reduced exactly:
+    j theta_p = pi * j (2p + 1 - m) / m."""
+    j = np.arange(-m // 2, m // 2, dtype=np.int64)[:, None]
+    p = np.arange(m, dtype=np.int64)[None, :]
+    r = np.mod(j * (2 * p + 1 - m), 2 * m).astype(np.float64)
+    ang = math.pi * r / m
+    return np.cos(ang) - 1j * np.sin(ang)
+
+
+def _phase_lambda(n: int) -> np.ndarray:
+    """E[k + n/2, q] = exp(-i k lambda_q), k lambda_q = pi * k (2q - n) / n."""
+    k = np.arange(-n // 2, n // 2, dtype=np.int64)[:, None]
+    q = np.arange(n, dtype=np.int64)[None, :]
+    r = np.mod(k * (2 * q - n), 2 * n).astype(np.float64)
+    ang = math.pi * r / n
+    return np.cos(ang) - 1j * np.sin(ang)
+
+
+def coeffs2(values: np.ndarray) -> np.ndarray:
+    """Naive 2D DFT: X[j + m/2, k + n/2] = (1/mn) sum_pq v(lambda_q, theta_p)
+    exp(-i j theta_p) exp(-i k lambda_q)  (the interpolant's coefficients)."""
+    m, n = values.shape
+    return (_phase_theta(m) @ values @ _phase_lambda(n).T) / (m * n)
+
+
+def sample(X: np.ndarray) -> np.ndarray:
+    """Inverse of coeffs2: values sum_jk X_jk exp(i j theta_p) exp(i k lambda_q)
+    on the m x n DFS grid (complex)."""
+    m, n = X.shape
+    return _phase_theta(m).conj().T @ X @ _phase_lambda(n).conj()
+
+
+# ----------------------------------------------------------------------------
+# Operators (Section 4 eq. Msin, Section 5)
+# ----------------------------------------------------------------------------
+
+def op_Dm(m: int) -> np.ndarray:
+    """D_m = diag(i j), j = -m/2..m/2-1  (d/dtheta)."""
+    return np.diag(1j * np.arange(-m // 2, m // 2, dtype=np.float64))
+
+
+def op_Mcos(m: int) -> np.ndarray:
+    """M_cos = (1/2) [ones on the sub- and super-diagonal]  (multiply by cos theta)."""
+    return 0.5 * (np.eye(m, k=1) + np.eye(m, k=-1))
+
+
+def op_Msin(m: int) -> np.ndarray:
+    """M_sin = (i/2) [+1 on the super-diagonal, -1 on the sub-diagonal] (eq. Msin)."""
+    return 0.5j * (np.eye(m, k=1) - np.eye(m, k=-1))
+
+
+def theta_operator_A(m: int) -> np.ndarray:
+    """Reading A: M_sin^2 D_m^2 + M_cos M_sin D_m from the truncated matrices
+    (eq. SylvesterSphericalPoisson, left factor).  Real-valued."""
+    D = op_Dm(m)
+    Ms = op_Msin(m)
+    Mc = op_Mcos(m)
+    L = Ms @ Ms @ D @ D + Mc @ Ms @ D
+    assert np.abs(L.imag).max() < 1e-12 * max(1.0, np.abs(L.real).max())
+    return L.real.copy()
+
+
+def theta_bands_B(m: int) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Reading B: entries of sin^2 d2/dtheta2 + sin cos d/dtheta on e^{ij theta}
+    for j = -m/2..m/2-1: row j has a_j at column j-2, b_j (without -k^2) at j,
+    c_j at column j+2.  Derived from sin^2 = 1/2 - (e^{2i t} + e^{-2i t})/4 and
+    sin cos = (e^{2i t} - e^{-2i t})/(4i)."""
+    j = np.arange(-m // 2, m // 2, dtype=np.float64)
+    a = (j - 1.0) * (j - 2.0) / 4.0
+    b = -(j * j) / 2.0
+    c = (j + 1.0) * (j + 2.0) / 4.0
+    return a, b, c
+
+
+def theta_operator_B(m: int) -> np.ndarray:
+    """Reading B as a dense m x m matrix; the Nyquist row/column j = -m/2 is
+    removed from the system (its row is the identity, forcing X_{-m/2} = 0)."""
+    a, b, c = theta_bands_B(m)
+    L = np.diag(b) + np.diag(a[2:], k=-2) + np.diag(c[:-2], k=2)
+    L[0, :] = 0.0
+    L[:, 0] = 0.0
+    return L
+
+
+def integration_weights(m: int) -> np.ndarray:
+    """eq. integrationCoeffs: w_j = (1 + e^{i pi j}) / (1 - j^2), w_{+-1} = 0,
+    j = -m/2..m/2-1, so that int_0^pi c(theta) sin(theta) dtheta = sum_j w_j a_j
+    for a theta-even c."""
+    j = np.arange(-m // 2, m // 2, dtype=np.int64)
+    w = np.zeros(m, dtype=np.float64)
+    even = (j % 2) == 0
+    w[even] = 2.0 / (1.0 - j[even].astype(np.float64) ** 2)
+    return w
+
+
+def system_matrix(m: int, k: int, reading: str = "B") -> np.ndarray:
+    """Dense matrix of the k-th column system (eq. linearSystems); for k = 0
+    the zeroth row is replaced by w^T (eq. pentdiagonalPlusRankOne)."""
+    if reading == "A":
+        L = theta_operator_A(m) - float(k * k) * np.eye(m)
+    elif reading == "B":
+        L = theta_operator_B(m) - float(k * k) * np.eye(m)
+        L[0, 0] = 1.0  # X_{-m/2} = 0
+    else:
+        raise ValueError(reading)
+    if k == 0:
+        w = integration_weights(m)
+        if reading == "B":
+            w = w.copy()
+            w[0] = 0.0
+        L[m // 2, :] = w
+    return L
+
+
+def _bands_of(m: int, k: int, reading: str):
+    """Diagonals (offsets -2, 0, +2) of the k-th system before the k = 0 row
+    replacement.  Reading A's bands are read off the literal matrix product."""
+    if reading == "A":
+        L = theta_operator_A(m)
+        sub = np.zeros(m)
+        sup = np.zeros(m)
+        sub[2:] = np.diag(L, k=-2)
+        sup[:-2] = np.diag(L, k=2)
+        d = np.diag(L).copy() - float(k * k)
+        # the literal product has no entries off the 0, +-2 diagonals
+        return sub, d, sup
+    a, b, c = theta_bands_B(m)
+    sub = a.copy()
+    sub[:2] = 0.0
+    sup = c.copy()
+    sup[-2:] = 0.0
+    d = b - float(k * k)
+    # Nyquist row/column j = -m/2 (index 0) removed: identity row
+    d[0] = 1.0
+    sup[0] = 0.0
+    sub[2] = 0.0
+    return sub, d, sup
+
+
+def _banded_solve(sub, d, sup, rhs):
+    """Solve the pentadiagonal-band (offsets -2, 0, +2) system with LAPACK."""
+    mm = d.shape[0]
+    ab = np.zeros((5, mm), dtype=np.float64)
+    ab[0, 2:] = sup[:-2]   # upper diagonal +2: ab[u + i - j, j] with u = 2
+    ab[2, :] = d
+    ab[4, :-2] = sub[2:]   # lower diagonal -2
+    return _sla.solve_banded((2, 2), ab, rhs)
+
+
+def solve_columns(F: np.ndarray, reading: str = "B", method: str = "auto") -> np.ndarray:
+    """X with X_k solving the k-th system of eq. linearSystems for every k."""
+    m, n = F.shape
+    if method == "auto":
+        method = "dense" if m <= DENSE_MAX_M else "banded"
+    X = np.zeros_like(F, dtype=np.complex128)
+    for kk in range(n):
+        k = kk - n // 2
+        if method == "dense":
+            rhs = F[:, kk].astype(np.complex128).copy()
+            if k == 0:
+                rhs[m // 2] = 0.0
+            if reading == "B":
+                rhs[0] = 0.0
+            X[:, kk] = np.linalg.solve(system_matrix(m, k, reading), rhs)
+        else:
+            X[:, kk] = _solve_one(F[:, kk], m, k, reading, banded=True)
+    return X
+
+
+def apply_columns(X: np.ndarray, reading: str = "B") -> np.ndarray:
+    """L_k X_k for every k (the operator of eq. linearSystems, no row replaced)."""
+    m, n = X.shape
+    out = np.zeros_like(X, dtype=np.complex128)
+    for kk in range(n):
+        k = kk - n // 2
+        if reading == "A":
+            L = theta_operator_A(m) - float(k * k) * np.eye(m)
+        else:
+            L = theta_operator_B(m) - float(k * k) * np.eye(m)
+        out[:, kk] = L @ X[:, kk]
+    return out
+
+
+# ----------------------------------------------------------------------------
+# The solver (Section 5) and sum2 (Section 4)
+# ----------------------------------------------------------------------------
+
+def rhs_coefficients(f: np.ndarray) -> np.ndarray:
+    """F = 2D Fourier coefficients of sin^2(theta) ftilde (eq. SylvesterSphericalPoisson)."""
+    ft = dfs_double(f)
+    m, _ = ft.shape
+    s2 = np.sin(dfs_theta(m)) ** 2
+    return coeffs2(s2[:, None] * ft)
+
+
+def poisson(f: np.ndarray, reading: str = "B", method: str = "auto", return_all: bool = False):
+    """u on the n_theta x n_lambda grid with Delta u = f and zero sphere mean.
+
+    f must have zero sphere mean (the paper's assumption).  Returns u, or
+    (u, F, X, imag_max) with return_all."""
+    f = np.asarray(f, dtype=np.float64)
+    nt, n = f.shape
+    F = rhs_coefficients(f)
+    X = solve_columns(F, reading, method)
+    U = sample(X)[nt:]
+    u = U.real.copy()
+    if return_all:
+        return u, F, X, float(np.abs(U.imag).max())
+    return u
+
+
+def sum2(values_on_grid: np.ndarray) -> float:
+    """Surface integral over the unit sphere (Section 4, Integration):
+    2 pi sum_j w_j A_{j,0} with A = coeffs2(ftilde)."""
+    ft = dfs_double(values_on_grid)
+    m, n = ft.shape
+    A = coeffs2(ft)
+    col0 = A[:, n // 2]
+    val = 2.0 * math.pi * (integration_weights(m) @ col0)
+    return float(val.real)
+
+
+# ----------------------------------------------------------------------------
+# Transpose of the linear map f -> u (for gradients)
+# ----------------------------------------------------------------------------
+
+def _solve_columns_T(B: np.ndarray, reading: str = "B") -> np.ndarray:
+    """Y with M_k^T Y_k = B_k, M_k the (row-replaced) system matrix of column k."""
+    m, n = B.shape
+    Y = np.zeros_like(B, dtype=np.complex128)
+    for kk in range(n):
+        k = kk - n // 2
+        M = system_matrix(m, k, reading)
+        Y[:, kk] = np.linalg.solve(M.T, B[:, kk])
+    return Y
+
+
+def poisson_adjoint(g: np.ndarray, reading: str = "B") -> np.ndarray:
+    """S^T g for the real-linear map S: f -> u of poisson(), by transposing each
+    step: restriction -> zero-extension, Re -> real embedding, complex-linear
+    maps -> conjugate transposes, row replacement and Nyquist removal ->
+    transposed system matrices, DFS doubling -> folding of mirrored rows.
+    Dense per-k solves, so for small grids only."""
+    g = np.asarray(g, dtype=np.float64)
+    nt, n = g.shape
+    m = 2 * nt
+    # u = Re(sample(X))[nt:]  ->  transpose: zero-extend, then sample^H
+    Gfull = np.zeros((m, n), dtype=np.complex128)
+    Gfull[nt:] = g
+    Et = _phase_theta(m)
+    El = _phase_lambda(n)
+    Xbar = Et @ Gfull @ El.T                       # (E^H)^H G (conj E)^H
+    # X = M^{-1} R F (R zeroes the replaced rows of the right-hand side)
+    Fbar = _solve_columns_T(Xbar, reading)
+    Fbar[m // 2, n // 2] = 0.0
+    if reading == "B":
+        Fbar[0, :] = 0.0
+    # F = coeffs2(s2 * ftilde)  ->  real part of the conjugate-transposed DFT
+    Vbar = (Et.conj().T @ Fbar @ El.conj()) / (m * n)
+    vbar = Vbar.real
+    s2 = np.sin(dfs_theta(m)) ** 2
+    vbar = s2[:, None] * vbar
+    # ftilde = E f  ->  fold mirrored rows back
+    out = vbar[nt:].copy()
+    back = vbar[:nt][::-1]                         # row n_theta-1-p -> f row i
+    out += np.roll(back, n // 2, axis=1)           # undo the q + n/2 shift
+    return out
+
+
+def dense_solution_operator(n_theta: int, n_lambda: int, reading: str = "B") -> np.ndarray:
+    """The matrix S of f -> u (columns = responses to unit inputs); tiny grids."""
+    N = n_theta * n_lambda
+    S = np.zeros((N, N))
+    for idx in range(N):
+        e = np.zeros(N)
+        e[idx] = 1.0
+        S[:, idx] = poisson(e.reshape(n_theta, n_lambda), reading, "dense").ravel()
+    return S
+
+
+# ----------------------------------------------------------------------------
+# Sampled columns, for grids too large for the full 2D DFT
+# ----------------------------------------------------------------------------
+
+def sampled_columns(f: np.ndarray, ks, reading: str = "B", chunk: int = 1024):
+    """For each wavenumber k in ks, the column U_k(theta_i) = sum_j X_jk e^{i j theta_i}
+    of the solution on the theta > 0 rows, where X_k solves the k-th system of
+    eq. linearSystems with F_k from the same naive DFT as coeffs2 restricted to
+    column k.  Then u(lambda_q, theta_i) = sum_k U_k(theta_i) e^{i k lambda_q},
+    so (1/n) sum_q u[i, q] e^{-i k lambda_q} = U_k(theta_i) for |k| < n/2.
+
+    Returns (U, F, X) with shapes (n_theta, K), (m, K), (m, K)."""
+    f = np.asarray(f, dtype=np.float64)
+    nt, n = f.shape
+    m = 2 * nt
+    ks = [int(k) for k in ks]
+    ft = dfs_double(f)
+    s2 = np.sin(dfs_theta(m)) ** 2
+    v = s2[:, None] * ft
+    q = np.arange(n, dtype=np.int64)
+    El = np.empty((n, len(ks)), dtype=np.complex128)
+    for c, k in enumerate(ks):
+        r = np.mod(k * (2 * q - n), 2 * n).astype(np.float64)
+        El[:, c] = np.cos(math.pi * r / n) - 1j * np.sin(math.pi * r / n)
+    G = v @ El / n                                     # lambda-DFT, (m, K)
+    F = np.zeros((m, len(ks)), dtype=np.complex128)
+    jj = np.arange(-m // 2, m // 2, dtype=np.int64)
+    for p0 in range(0, m, chunk):
+        p = np.arange(p0, min(m, p0 + chunk), dtype=np.int64)
+        r = np.mod(jj[:, None] * (2 * p[None, :] + 1 - m), 2 * m).astype(np.float64)
+        E = np.cos(math.pi * r / m) - 1j * np.sin(math.pi * r / m)
+        F += E @ G[p0:p0 + len(p)]
+    F /= m
+    X = np.zeros_like(F)
+    for c, k in enumerate(ks):
+        X[:, c] = _solve_one(F[:, c], m, k, reading)
+    U = np.zeros((nt, len(ks)), dtype=np.complex128)
+    for i0 in range(0, nt, chunk):
+        i = np.arange(i0, min(nt, i0 + chunk), dtype=np.int64)
+        p = i + nt
+        r = np.mod(jj[None, :] * (2 * p[:, None] + 1 - m), 2 * m).astype(np.float64)
+        Einv = np.cos(math.pi * r / m) + 1j * np.sin(math.pi * r / m)
+        U[i0:i0 + len(i)] = Einv @ X
+    return U, F, X
+
+
+def _solve_one(Fk: np.ndarray, m: int, k: int, reading: str, banded: bool = False) -> np.ndarray:
+    """X_k for one column (same systems as solve_columns)."""
+    rhs = Fk.astype(np.complex128).copy()
+    if k == 0:
+        rhs[m // 2] = 0.0
+    if reading == "B":
+        rhs[0] = 0.0
+    if m <= DENSE_MAX_M and not banded:
+        return np.linalg.solve(system_matrix(m, k, reading), rhs)
+    sub, d, sup = _bands_of(m, k, reading)
+    if k != 0:
+        return _banded_solve(sub, d, sup, rhs)
+    keep = np.arange(m) != m // 2
+    sub_r = sub[keep].copy()
+    sup_r = sup[keep].copy()
+    i0 = m // 2
+    sub_r[i0] = 0.0
+    sub_r[i0 + 1] = 0.0
+    sup_r[i0 - 2] = 0.0
+    sup_r[i0 - 1] = 0.0
+    xr = _banded_solve(sub_r, d[keep], sup_r, rhs[keep])
+    x = np.zeros(m, dtype=np.complex128)
+    x[keep] = xr
+    w = integration_weights(m)
+    if reading == "B":
+        w[0] = 0.0
+    x[m // 2] = -(w[keep] @ xr) / w[m // 2]
+    return x
+
+
+def lambda_spectrum(u: np.ndarray, ks) -> np.ndarray:
+    """(1/n) sum_q u[i, q] exp(-i k lambda_q) for each k in ks: (n_theta, K)."""
+    u = np.asarray(u, dtype=np.float64)
+    n = u.shape[1]
+    q = np.arange(n, dtype=np.int64)
+    El = np.empty((n, len(ks)), dtype=np.complex128)
+    for c, k in enumerate(ks):
+        r = np.mod(int(k) * (2 * q - n), 2 * n).astype(np.float64)
+        El[:, c] = np.cos(math.pi * r / n) - 1j * np.sin(math.pi * r / n)
+    return u @ El / n
