@@ -1,0 +1,137 @@
+/*
+ * sphere_poisson.h -- C ABI of the GB300 (sm_103a) spherical Poisson solver.
+ *
+ * Solves Poisson's equation on the unit sphere,  Delta u = f  with
+ * int_S u = 0, by the double-Fourier-sphere (DFS) Fourier spectral method of
+ * Townsend, Wilber & Wright, "Computing with functions in spherical and polar
+ * geometries I. The sphere", Section 5:
+ *   - sin^2(theta)-multiplied Laplacian, eq. SphericalLaplacian, doubled up
+ *     to [-pi, pi]^2 by the glide reflection of eq. BMCsphere (eq. BMCPoisson);
+ *   - 2D Fourier coefficients F of sin^2(theta) f~ (eq. 2DFourierExpansion);
+ *   - one banded system per longitudinal wavenumber k, eq. linearSystems,
+ *     with the k = 0 zeroth row replaced by the zero-mean constraint w^T X_0 = 0
+ *     (eq. pentdiagonalPlusRankOne, weights w of eq. integrationCoeffs);
+ *   - inverse 2D expansion back to grid values (eq. tildeuFourierExpansion).
+ *
+ * Grid.  f and u are row-major arrays [n_theta][n_lambda] of doubles,
+ *   row i    = colatitude theta_i  = (i + 1/2) pi / n_theta   (no pole samples),
+ *   column q = longitude  lambda_q = -pi + 2 pi q / n_lambda.
+ * The DFS grid then has m = 2 n_theta colatitudes and n = n_lambda longitudes.
+ * Truncation: coefficients X_{j,k} with |j| <= m/2 - 1 and -n/2 <= k <= n/2 - 1;
+ * the theta-Nyquist mode j = -m/2 is set to zero (the symmetric window keeps
+ * the BMC symmetry X_{-j,k} = (-1)^k X_{j,k} exact).
+ *
+ * Memory.  All array arguments of the solve calls are DEVICE pointers unless a
+ * name says _host.  The caller owns f, u and the workspace; the library owns
+ * the plan and the device tables inside it (twiddle factors and the factorised
+ * per-k systems).  f, u and workspace must be 16-byte aligned and must not
+ * overlap.  Calls are asynchronous on the given stream (a cudaStream_t passed
+ * as void*, or NULL for the legacy default stream) except where stated.
+ *
+ * Errors.  Every call returns an int status: 0 = success, > 0 = success with a
+ * warning, < 0 = error (nothing was launched).  sphere_poisson_status_string()
+ * gives a message.  No call aborts the process.
+ */
+#ifndef SPHERE_POISSON_H
+#define SPHERE_POISSON_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SP_OK                0
+#define SP_ERR_BAD_SIZE     -1   /* n_theta < 1, n_lambda < 2 or odd, too large, or a prime factor > 31 */
+#define SP_ERR_NULL         -2   /* a required pointer is NULL */
+#define SP_ERR_MISALIGNED   -3   /* a device pointer is not 16-byte aligned */
+#define SP_ERR_WORKSPACE    -4   /* workspace smaller than the plan requires */
+#define SP_ERR_CUDA         -5   /* a CUDA runtime call failed (message via status_string) */
+#define SP_ERR_UNSUPPORTED  -6   /* precision / flag combination not built */
+#define SP_ERR_BAD_PLAN     -7   /* NULL or destroyed plan handle */
+#define SP_ERR_BAD_ARG      -8   /* other invalid argument */
+
+/* precision of the arithmetic inside the solve (inputs and outputs are always double) */
+#define SP_FP64         0   /* IEEE double throughout */
+#define SP_FP32         1   /* single precision transforms and eliminations */
+#define SP_FP32_REFINE  2   /* FP32 eliminations + FP64 residual refinement, FP64-accurate transforms */
+
+typedef struct sp_plan_s* sp_plan_t;
+
+/*
+ * Create a plan for grids of n_theta colatitudes x n_lambda longitudes.
+ *   n_theta >= 1, n_lambda >= 2 and even (the glide reflection lambda -> lambda+pi
+ *   of eq. BMCsphere must map the grid to itself); n_theta and n_lambda/2 must
+ *   factor into primes <= 31 and be at most 12288.
+ *   precision     SP_FP64 (others return SP_ERR_UNSUPPORTED until built).
+ *   refine_sweeps number of FP64 residual sweeps for SP_FP32_REFINE (else ignored).
+ *   flags         reserved, pass 0.
+ *   workspace_bytes (out, optional) device workspace the solve calls need.
+ * Synchronous: allocates the plan's device tables and fills them on the
+ * current device; the plan may only be used with that device.
+ */
+int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precision,
+                        int refine_sweeps, unsigned flags, size_t* workspace_bytes);
+
+/* Device workspace size of a plan (bytes). */
+int sphere_poisson_workspace_size(sp_plan_t plan, size_t* workspace_bytes);
+
+/*
+ * u = S f: the zero-mean solution of Delta u = f on the plan's grid.
+ *   f          device, [n_theta][n_lambda] doubles, read only.  The paper assumes
+ *              int_S f = 0; for other f the k = 0, j = 0 equation is dropped as in
+ *              eq. pentdiagonalPlusRankOne and u solves the remaining equations.
+ *   u          device, [n_theta][n_lambda] doubles, written.
+ *   workspace  device, >= workspace_bytes; contents are scratch.
+ *   stream     cudaStream_t (as void*) or NULL.
+ */
+int sphere_poisson_solve(sp_plan_t plan, const double* f, double* u, void* workspace,
+                         size_t workspace_bytes, void* stream);
+
+/*
+ * fbar = S^T ubar: the transpose of the linear map f -> u of sphere_poisson_solve
+ * with respect to the plain Euclidean inner product on [n_theta][n_lambda]
+ * arrays (the vector-Jacobian product of the solve).  Same layouts and rules.
+ */
+int sphere_poisson_solve_adjoint(sp_plan_t plan, const double* ubar, double* fbar,
+                                 void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Host-buffer convenience form of sphere_poisson_solve: copies f_host to the
+ * device, solves, copies u back to u_host and synchronises the stream before
+ * returning.  device_buffer must hold host_buffer_bytes (from
+ * sphere_poisson_host_buffer_size): room for f, u and the workspace.
+ * Pinned host memory gives the fastest copies; pageable memory also works.
+ */
+int sphere_poisson_host_buffer_size(sp_plan_t plan, size_t* device_buffer_bytes);
+int sphere_poisson_solve_host(sp_plan_t plan, const double* f_host, double* u_host,
+                              void* device_buffer, size_t device_buffer_bytes, void* stream);
+
+/* Number of kernel launches one solve (adjoint = 1) issues for this plan. */
+int sphere_poisson_launch_count(sp_plan_t plan, int adjoint, int* launches);
+
+/*
+ * Stage timing.  After profile_begin, each solve / adjoint call on the plan (up
+ * to max_solves of them) records a CUDA event before each of its kernel
+ * launches and one after the last, on the call's stream.  profile_end waits for
+ * those events, writes the summed milliseconds of stage s over the recorded
+ * calls to stage_ms[s] (s < max_stages), the number of recorded calls to
+ * *solves and the number of stages per call to *stages, and releases the events.
+ * Stage names: sphere_poisson_stage_name.  Host-side bookkeeping only.
+ */
+int sphere_poisson_profile_begin(sp_plan_t plan, int max_solves);
+int sphere_poisson_profile_end(sp_plan_t plan, double* stage_ms, int max_stages, int* solves, int* stages);
+const char* sphere_poisson_stage_name(sp_plan_t plan, int stage);
+
+/* Release the plan and its device tables.  Synchronous; NULL is accepted. */
+int sphere_poisson_destroy(sp_plan_t plan);
+
+/* Static message for a status code (the last CUDA error text for SP_ERR_CUDA). */
+const char* sphere_poisson_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPHERE_POISSON_H */

@@ -381,7 +381,20 @@ def dense_solution_operator(n_theta: int, n_lambda: int, reading: str = "B") -> 
 # Sampled columns, for grids too large for the full 2D DFT
 # ----------------------------------------------------------------------------
 
-def sampled_columns(f: np.ndarray, ks, reading: str = "B", chunk: int = 1024):
+_theta_cache: dict = {}
+
+
+def _theta_phase_cached(m: int) -> np.ndarray:
+    """_phase_theta(m), kept for the last size used (1.6 GB at m = 10^4)."""
+    E = _theta_cache.get(m)
+    if E is None:
+        _theta_cache.clear()
+        E = _phase_theta(m)
+        _theta_cache[m] = E
+    return E
+
+
+def sampled_columns(f: np.ndarray, ks, reading: str = "B"):
     """For each wavenumber k in ks, the column U_k(theta_i) = sum_j X_jk e^{i j theta_i}
     of the solution on the theta > 0 rows, where X_k solves the k-th system of
     eq. linearSystems with F_k from the same naive DFT as coeffs2 restricted to
@@ -402,24 +415,13 @@ def sampled_columns(f: np.ndarray, ks, reading: str = "B", chunk: int = 1024):
         r = np.mod(k * (2 * q - n), 2 * n).astype(np.float64)
         El[:, c] = np.cos(math.pi * r / n) - 1j * np.sin(math.pi * r / n)
     G = v @ El / n                                     # lambda-DFT, (m, K)
-    F = np.zeros((m, len(ks)), dtype=np.complex128)
-    jj = np.arange(-m // 2, m // 2, dtype=np.int64)
-    for p0 in range(0, m, chunk):
-        p = np.arange(p0, min(m, p0 + chunk), dtype=np.int64)
-        r = np.mod(jj[:, None] * (2 * p[None, :] + 1 - m), 2 * m).astype(np.float64)
-        E = np.cos(math.pi * r / m) - 1j * np.sin(math.pi * r / m)
-        F += E @ G[p0:p0 + len(p)]
-    F /= m
+    E = _theta_phase_cached(m)                         # E[j + m/2, p] = exp(-i j theta_p)
+    F = (E @ G) / m
     X = np.zeros_like(F)
     for c, k in enumerate(ks):
         X[:, c] = _solve_one(F[:, c], m, k, reading)
-    U = np.zeros((nt, len(ks)), dtype=np.complex128)
-    for i0 in range(0, nt, chunk):
-        i = np.arange(i0, min(nt, i0 + chunk), dtype=np.int64)
-        p = i + nt
-        r = np.mod(jj[None, :] * (2 * p[:, None] + 1 - m), 2 * m).astype(np.float64)
-        Einv = np.cos(math.pi * r / m) + 1j * np.sin(math.pi * r / m)
-        U[i0:i0 + len(i)] = Einv @ X
+    # U[i] = sum_j X_j exp(i j theta_{nt+i}) = conj(X^H E[:, nt + i])
+    U = np.conj(X.conj().T @ E[:, nt:]).T
     return U, F, X
 
 

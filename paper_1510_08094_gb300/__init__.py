@@ -1,0 +1,208 @@
+"""GB300 (sm_103a) spherical Poisson solver: Python binding of the C ABI.
+
+Every step of the solve runs in the library's CUDA kernels; this module only
+marshals torch tensors (device memory, the current stream) into the C calls.
+
+    import paper_1510_08094_gb300 as sp
+    u = sp.solve(f)                 # f: float64 CUDA tensor [n_theta, n_lambda]
+    plan = sp.Plan(n_theta, n_lambda)
+    u = plan.solve(f); fbar = plan.solve_adjoint(ubar)
+    u = sp.poisson(f)               # differentiable (torch.autograd.Function)
+"""
+
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import torch
+
+from . import _lib
+from ._lib import (  # noqa: F401
+    SP_FP32,
+    SP_FP32_REFINE,
+    SP_FP64,
+    SpherePoissonError,
+    library_path,
+)
+
+__all__ = ["Plan", "solve", "solve_adjoint", "poisson", "SpherePoisson", "SpherePoissonError", "get_plan"]
+
+_PRECISIONS = {"fp64": SP_FP64, "fp32": SP_FP32, "fp32_refine": SP_FP32_REFINE}
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _check_grid(t: torch.Tensor, shape, name: str):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64, got {t.dtype}")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Plan:
+    """A solver plan for one grid size (n_theta colatitudes x n_lambda longitudes)."""
+
+    def __init__(self, n_theta: int, n_lambda: int, precision: str = "fp64", refine_sweeps: int = 0,
+                 device=None):
+        lib = _lib.load()
+        if precision not in _PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(_PRECISIONS)}")
+        self.n_theta, self.n_lambda = int(n_theta), int(n_lambda)
+        self.precision = precision
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        h = ctypes.c_void_p()
+        ws = ctypes.c_size_t()
+        with torch.cuda.device(self.device):
+            _lib.check(lib.sphere_poisson_plan(ctypes.byref(h), self.n_theta, self.n_lambda,
+                                               _PRECISIONS[precision], int(refine_sweeps), 0,
+                                               ctypes.byref(ws)), "sphere_poisson_plan")
+        self._h = h
+        self.workspace_bytes = int(ws.value)
+        self._lib = lib
+        self._ws = None
+
+    @property
+    def shape(self):
+        return (self.n_theta, self.n_lambda)
+
+    def _workspace(self, workspace):
+        if workspace is not None:
+            if workspace.device != self.device or workspace.numel() * workspace.element_size() < self.workspace_bytes:
+                raise ValueError("workspace too small or on another device")
+            return workspace
+        if self._ws is None:
+            self._ws = torch.empty(max(1, self.workspace_bytes), dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def launches(self, adjoint: bool = False) -> int:
+        n = ctypes.c_int()
+        _lib.check(self._lib.sphere_poisson_launch_count(self._h, int(adjoint), ctypes.byref(n)),
+                   "sphere_poisson_launch_count")
+        return int(n.value)
+
+    def solve(self, f: torch.Tensor, out: torch.Tensor | None = None, workspace=None, stream=None):
+        """u with Delta u = f and zero sphere mean (f: float64 CUDA [n_theta, n_lambda])."""
+        _check_grid(f, self.shape, "f")
+        if out is None:
+            out = torch.empty_like(f)
+        _check_grid(out, self.shape, "out")
+        ws = self._workspace(workspace)
+        _lib.check(self._lib.sphere_poisson_solve(self._h, f.data_ptr(), out.data_ptr(), ws.data_ptr(),
+                                                  ws.numel() * ws.element_size(), _stream_ptr(stream)),
+                   "sphere_poisson_solve")
+        return out
+
+    def solve_adjoint(self, ubar: torch.Tensor, out: torch.Tensor | None = None, workspace=None, stream=None):
+        """S^T ubar, the transpose of f -> u (the vector-Jacobian product)."""
+        _check_grid(ubar, self.shape, "ubar")
+        if out is None:
+            out = torch.empty_like(ubar)
+        _check_grid(out, self.shape, "out")
+        ws = self._workspace(workspace)
+        _lib.check(self._lib.sphere_poisson_solve_adjoint(self._h, ubar.data_ptr(), out.data_ptr(),
+                                                          ws.data_ptr(), ws.numel() * ws.element_size(),
+                                                          _stream_ptr(stream)),
+                   "sphere_poisson_solve_adjoint")
+        return out
+
+    def host_buffer_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        _lib.check(self._lib.sphere_poisson_host_buffer_size(self._h, ctypes.byref(n)),
+                   "sphere_poisson_host_buffer_size")
+        return int(n.value)
+
+    def solve_host(self, f_host: torch.Tensor, out: torch.Tensor | None = None, device_buffer=None,
+                   stream=None):
+        """Host-memory form: copies f in, solves, copies u out, then synchronises."""
+        if f_host.dtype != torch.float64 or f_host.is_cuda or tuple(f_host.shape) != self.shape:
+            raise ValueError("f_host must be a float64 CPU tensor of the plan's shape")
+        f_host = f_host.contiguous()
+        if out is None:
+            out = torch.empty_like(f_host)
+        need = self.host_buffer_bytes()
+        if device_buffer is None:
+            device_buffer = torch.empty(need, dtype=torch.uint8, device=self.device)
+        _lib.check(self._lib.sphere_poisson_solve_host(self._h, f_host.data_ptr(), out.data_ptr(),
+                                                       device_buffer.data_ptr(),
+                                                       device_buffer.numel(), _stream_ptr(stream)),
+                   "sphere_poisson_solve_host")
+        return out
+
+    def profile_begin(self, max_solves: int):
+        """Start recording per-stage CUDA events for the next max_solves calls."""
+        _lib.check(self._lib.sphere_poisson_profile_begin(self._h, int(max_solves)), "profile_begin")
+
+    def profile_end(self) -> tuple[dict, int]:
+        """({stage name: summed ms}, calls recorded) since profile_begin."""
+        ms = (ctypes.c_double * 16)()
+        n, ns = ctypes.c_int(), ctypes.c_int()
+        _lib.check(self._lib.sphere_poisson_profile_end(self._h, ms, 16, ctypes.byref(n), ctypes.byref(ns)),
+                   "profile_end")
+        names = [self._lib.sphere_poisson_stage_name(self._h, s).decode() for s in range(ns.value)]
+        return {names[s]: float(ms[s]) for s in range(ns.value)}, int(n.value)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.sphere_poisson_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_plans: dict = {}
+_plans_lock = threading.Lock()
+
+
+def get_plan(n_theta: int, n_lambda: int, precision: str = "fp64", refine_sweeps: int = 0, device=None) -> Plan:
+    dev = torch.cuda.current_device() if device is None else torch.device(device).index or 0
+    key = (int(n_theta), int(n_lambda), precision, int(refine_sweeps), dev)
+    with _plans_lock:
+        p = _plans.get(key)
+        if p is None:
+            p = Plan(n_theta, n_lambda, precision, refine_sweeps, device=torch.device("cuda", dev))
+            _plans[key] = p
+        return p
+
+
+def solve(f: torch.Tensor, precision: str = "fp64", refine_sweeps: int = 0) -> torch.Tensor:
+    """u = S f on f's device (cached plan per shape)."""
+    return get_plan(f.shape[0], f.shape[1], precision, refine_sweeps, f.device).solve(f)
+
+
+def solve_adjoint(ubar: torch.Tensor, precision: str = "fp64", refine_sweeps: int = 0) -> torch.Tensor:
+    return get_plan(ubar.shape[0], ubar.shape[1], precision, refine_sweeps, ubar.device).solve_adjoint(ubar)
+
+
+class SpherePoisson(torch.autograd.Function):
+    """Differentiable solve: forward u = S f, backward grad_f = S^T grad_u."""
+
+    @staticmethod
+    def forward(ctx, f, precision="fp64", refine_sweeps=0):
+        ctx.precision = precision
+        ctx.refine_sweeps = refine_sweeps
+        return solve(f.contiguous(), precision, refine_sweeps)
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        g = solve_adjoint(grad_u.contiguous(), ctx.precision, ctx.refine_sweeps)
+        return g, None, None
+
+
+def poisson(f: torch.Tensor, precision: str = "fp64", refine_sweeps: int = 0) -> torch.Tensor:
+    return SpherePoisson.apply(f, precision, refine_sweeps)

@@ -1,0 +1,262 @@
+// Shared-memory mixed-radix FFT used by every transform stage.
+//
+// One CTA transforms `nbatch` sequences of length L = R_1 R_2 ... R_s that sit
+// back to back in shared memory, in place, by decimation in time: the input is
+// loaded in mixed-radix digit-reversed order, pass t combines R_t sub-DFTs of
+// length Ns = R_1 ... R_{t-1}, and the output comes out in natural order.
+// Twiddles come from a table tw[t] = exp(-2 pi i t / L).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace sp {
+
+template <typename T>
+struct alignas(2 * sizeof(T)) cpx {
+  T re, im;
+};
+
+template <typename T> __device__ __forceinline__ cpx<T> mk(T a, T b) { return cpx<T>{a, b}; }
+template <typename T> __device__ __forceinline__ cpx<T> operator+(cpx<T> a, cpx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T> __device__ __forceinline__ cpx<T> operator-(cpx<T> a, cpx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T> __device__ __forceinline__ cpx<T> operator*(T s, cpx<T> a) { return {s * a.re, s * a.im}; }
+template <typename T> __device__ __forceinline__ cpx<T> conj(cpx<T> a) { return {a.re, -a.im}; }
+// a * b
+template <typename T> __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
+  return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+}
+// a * conj(b)
+template <typename T> __device__ __forceinline__ cpx<T> cmulc(cpx<T> a, cpx<T> b) {
+  return {fma(a.re, b.re, a.im * b.im), fma(a.im, b.re, -a.re * b.im)};
+}
+// a * (-i) for DIR = -1, a * (+i) for DIR = +1
+template <int DIR, typename T> __device__ __forceinline__ cpx<T> rot(cpx<T> a) {
+  return DIR < 0 ? cpx<T>{a.im, -a.re} : cpx<T>{-a.im, a.re};
+}
+// a * w^DIR-sense: w from the forward table; inverse uses conj(w)
+template <int DIR, typename T> __device__ __forceinline__ cpx<T> twmul(cpx<T> a, cpx<T> w) {
+  return DIR < 0 ? cmul(a, w) : cmulc(a, w);
+}
+
+// read-only cached load of a table entry
+__device__ __forceinline__ cpx<double> ldg_c(const cpx<double>* p) {
+  double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  return {v.x, v.y};
+}
+__device__ __forceinline__ cpx<float> ldg_c(const cpx<float>* p) {
+  float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return {v.x, v.y};
+}
+
+constexpr int kMaxStages = 16;
+
+struct FftDesc {
+  int L;
+  int nstages;
+  int radix[kMaxStages];
+};
+
+// ---------------------------------------------------------------------------
+// R-point DFTs on registers: y_a = sum_b x_b exp(DIR 2 pi i a b / R)
+// ---------------------------------------------------------------------------
+
+template <int DIR, typename T>
+__device__ __forceinline__ void dft2(cpx<T>* v) {
+  cpx<T> a = v[0], b = v[1];
+  v[0] = a + b;
+  v[1] = a - b;
+}
+
+template <int DIR, typename T>
+__device__ __forceinline__ void dft4(cpx<T>* v) {
+  cpx<T> s0 = v[0] + v[2], d0 = v[0] - v[2];
+  cpx<T> s1 = v[1] + v[3], d1 = rot<DIR>(v[1] - v[3]);
+  v[0] = s0 + s1;
+  v[2] = s0 - s1;
+  v[1] = d0 + d1;
+  v[3] = d0 - d1;
+}
+
+template <int DIR, typename T>
+__device__ __forceinline__ void dft8(cpx<T>* v) {
+  const T h = (T)0.70710678118654752440084436210484903928;
+  cpx<T> e[4] = {v[0], v[2], v[4], v[6]};
+  cpx<T> o[4] = {v[1], v[3], v[5], v[7]};
+  // 4-point DFTs of the even and odd samples (inputs in natural order 0,1,2,3)
+  {
+    cpx<T> s0 = e[0] + e[2], d0 = e[0] - e[2], s1 = e[1] + e[3], d1 = rot<DIR>(e[1] - e[3]);
+    e[0] = s0 + s1; e[2] = s0 - s1; e[1] = d0 + d1; e[3] = d0 - d1;
+  }
+  {
+    cpx<T> s0 = o[0] + o[2], d0 = o[0] - o[2], s1 = o[1] + o[3], d1 = rot<DIR>(o[1] - o[3]);
+    o[0] = s0 + s1; o[2] = s0 - s1; o[1] = d0 + d1; o[3] = d0 - d1;
+  }
+  // twiddles W8^k (DIR sense): W8^1 = (1 + DIR i)/sqrt2, W8^2 = DIR i, W8^3 = (-1 + DIR i)/sqrt2
+  cpx<T> t1, t3;
+  if (DIR < 0) {
+    t1 = {h * (o[1].re + o[1].im), h * (o[1].im - o[1].re)};
+    t3 = {h * (o[3].im - o[3].re), -h * (o[3].re + o[3].im)};
+  } else {
+    t1 = {h * (o[1].re - o[1].im), h * (o[1].im + o[1].re)};
+    t3 = {-h * (o[3].re + o[3].im), h * (o[3].re - o[3].im)};
+  }
+  cpx<T> t2 = rot<DIR>(o[2]);
+  v[0] = e[0] + o[0]; v[4] = e[0] - o[0];
+  v[1] = e[1] + t1;   v[5] = e[1] - t1;
+  v[2] = e[2] + t2;   v[6] = e[2] - t2;
+  v[3] = e[3] + t3;   v[7] = e[3] - t3;
+}
+
+template <int DIR, typename T>
+__device__ __forceinline__ void dft3(cpx<T>* v) {
+  const T c = (T)-0.5;
+  const T s = (T)0.86602540378443864676372317075293618347;  // sin(2 pi / 3)
+  cpx<T> a = v[1] + v[2], b = v[1] - v[2];
+  cpx<T> t = {fma(c, a.re, v[0].re), fma(c, a.im, v[0].im)};
+  cpx<T> sb = s * b;
+  v[0] = v[0] + a;
+  // y1 = t + DIR i s b, y2 = t - DIR i s b
+  cpx<T> isb = DIR < 0 ? cpx<T>{sb.im, -sb.re} : cpx<T>{-sb.im, sb.re};
+  v[1] = t + isb;
+  v[2] = t - isb;
+}
+
+template <int DIR, typename T>
+__device__ __forceinline__ void dft5(cpx<T>* v) {
+  const T c1 = (T)0.30901699437494742410229341718281905886;   // cos(2 pi/5)
+  const T c2 = (T)-0.80901699437494742410229341718281905886;  // cos(4 pi/5)
+  const T s1 = (T)0.95105651629515357211643933337938214340;   // sin(2 pi/5)
+  const T s2 = (T)0.58778525229247312916870595463907276860;   // sin(4 pi/5)
+  cpx<T> a1 = v[1] + v[4], b1 = v[1] - v[4];
+  cpx<T> a2 = v[2] + v[3], b2 = v[2] - v[3];
+  cpx<T> x0 = v[0];
+  cpx<T> t1 = {fma(c2, a2.re, fma(c1, a1.re, x0.re)), fma(c2, a2.im, fma(c1, a1.im, x0.im))};
+  cpx<T> t2 = {fma(c1, a2.re, fma(c2, a1.re, x0.re)), fma(c1, a2.im, fma(c2, a1.im, x0.im))};
+  cpx<T> u1 = {fma(s2, b2.re, s1 * b1.re), fma(s2, b2.im, s1 * b1.im)};
+  cpx<T> u2 = {fma(-s1, b2.re, s2 * b1.re), fma(-s1, b2.im, s2 * b1.im)};
+  v[0] = x0 + a1 + a2;
+  // y1 = t1 + DIR i u1, y4 = t1 - DIR i u1, y2 = t2 + DIR i u2, y3 = t2 - DIR i u2
+  cpx<T> iu1 = DIR < 0 ? cpx<T>{u1.im, -u1.re} : cpx<T>{-u1.im, u1.re};
+  cpx<T> iu2 = DIR < 0 ? cpx<T>{u2.im, -u2.re} : cpx<T>{-u2.im, u2.re};
+  v[1] = t1 + iu1;
+  v[4] = t1 - iu1;
+  v[2] = t2 + iu2;
+  v[3] = t2 - iu2;
+}
+
+// Generic odd R: pair outputs a and R-a, using p_b = x_b + x_{R-b}, q_b = x_b - x_{R-b}.
+// Cos/sin of 2 pi a b / R are read from the length-L table at (a b mod R) L/R.
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void dft_odd(cpx<T>* v, const cpx<T>* __restrict__ tw, int tstride) {
+  constexpr int H = (R - 1) / 2;
+  cpx<T> p[H], q[H];
+#pragma unroll
+  for (int b = 1; b <= H; ++b) {
+    p[b - 1] = v[b] + v[R - b];
+    q[b - 1] = v[b] - v[R - b];
+  }
+  cpx<T> x0 = v[0];
+  cpx<T> y0 = x0;
+#pragma unroll
+  for (int b = 0; b < H; ++b) y0 = y0 + p[b];
+#pragma unroll
+  for (int a = 1; a <= H; ++a) {
+    cpx<T> A = x0, B = {(T)0, (T)0};
+#pragma unroll
+    for (int b = 1; b <= H; ++b) {
+      cpx<T> w = ldg_c(tw + ((a * b) % R) * tstride);
+      T c = w.re, s = -w.im;  // w = exp(-2 pi i ab/R) = c - i s
+      A.re = fma(c, p[b - 1].re, A.re);
+      A.im = fma(c, p[b - 1].im, A.im);
+      B.re = fma(s, q[b - 1].re, B.re);
+      B.im = fma(s, q[b - 1].im, B.im);
+    }
+    // y_a = A + DIR i B, y_{R-a} = A - DIR i B
+    cpx<T> iB = DIR < 0 ? cpx<T>{B.im, -B.re} : cpx<T>{-B.im, B.re};
+    v[a] = A + iB;
+    v[R - a] = A - iB;
+  }
+  v[0] = y0;
+}
+
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void dft_any(cpx<T>* v, const cpx<T>* __restrict__ tw, int tstride) {
+  if constexpr (R == 2) dft2<DIR>(v);
+  else if constexpr (R == 3) dft3<DIR>(v);
+  else if constexpr (R == 4) dft4<DIR>(v);
+  else if constexpr (R == 5) dft5<DIR>(v);
+  else if constexpr (R == 8) dft8<DIR>(v);
+  else dft_odd<R, DIR>(v, tw, tstride);
+}
+
+// ---------------------------------------------------------------------------
+// One in-place decimation-in-time pass over all batches; ends with a barrier.
+// Butterfly (g, k), k < Ns, owns the R elements g Ns R + k + r Ns, multiplies
+// element r by w^(r k), w = exp(-+2 pi i/(Ns R)), and applies the R-point DFT.
+// Butterflies of a pass touch disjoint elements, so threads stream through
+// them holding only R values.
+// ---------------------------------------------------------------------------
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void fft_pass(cpx<T>* buf, int L, int nbatch, int Ns,
+                                         const cpx<T>* __restrict__ tw) {
+  const int nb = L / R;
+  const int total = nb * nbatch;
+  const int tstride_stage = L / (Ns * R);  // table step for w = exp(-2 pi i/(Ns R))
+  const int tstride_R = L / R;
+  for (int b = threadIdx.x; b < total; b += blockDim.x) {
+    const int batch = b / nb;
+    const int j = b - batch * nb;
+    const int g = j / Ns;
+    const int k = j - g * Ns;
+    cpx<T>* base = buf + batch * L + g * Ns * R + k;
+    cpx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = base[r * Ns];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = twmul<DIR>(v[r], ldg_c(tw + r * k * tstride_stage));
+    }
+    dft_any<R, DIR>(v, tw, tstride_R);
+#pragma unroll
+    for (int r = 0; r < R; ++r) base[r * Ns] = v[r];
+  }
+  __syncthreads();
+}
+
+// Full transform of sequences stored in digit-reversed order (position
+// perm[q] holds input q; see the host's digit_reversal): DIR = -1 computes
+// sum_q a_q exp(-2 pi i q k / L) (unnormalised), DIR = +1 the same with exp(+...),
+// leaving the result in natural order.  Expects a barrier before entry.
+// BIG = false: radices 2, 3, 4, 5, 7, 8 only (keeps register allocation tight);
+// BIG = true adds the odd primes 11 .. 31 for lengths that need them.
+template <int DIR, bool BIG, typename T>
+__device__ __forceinline__ void fft_run(cpx<T>* buf, int nbatch, const FftDesc& d, const cpx<T>* __restrict__ tw) {
+  int Ns = 1;
+  for (int s = 0; s < d.nstages; ++s) {
+    const int R = d.radix[s];
+    switch (R) {
+      case 2: fft_pass<2, DIR>(buf, d.L, nbatch, Ns, tw); break;
+      case 3: fft_pass<3, DIR>(buf, d.L, nbatch, Ns, tw); break;
+      case 4: fft_pass<4, DIR>(buf, d.L, nbatch, Ns, tw); break;
+      case 5: fft_pass<5, DIR>(buf, d.L, nbatch, Ns, tw); break;
+      case 7: fft_pass<7, DIR>(buf, d.L, nbatch, Ns, tw); break;
+      case 8: fft_pass<8, DIR>(buf, d.L, nbatch, Ns, tw); break;
+      default: break;
+    }
+    if constexpr (BIG) {
+      switch (R) {
+      case 11: fft_pass<11, DIR>(buf, d.L, nbatch, Ns, tw); break;
+      case 13: fft_pass<13, DIR>(buf, d.L, nbatch, Ns, tw); break;
+      case 17: fft_pass<17, DIR>(buf, d.L, nbatch, Ns, tw); break;
+      case 19: fft_pass<19, DIR>(buf, d.L, nbatch, Ns, tw); break;
+      case 23: fft_pass<23, DIR>(buf, d.L, nbatch, Ns, tw); break;
+      case 29: fft_pass<29, DIR>(buf, d.L, nbatch, Ns, tw); break;
+      case 31: fft_pass<31, DIR>(buf, d.L, nbatch, Ns, tw); break;
+      default: break;  // the host never builds other radices
+      }
+    }
+    Ns *= R;
+  }
+}
+
+}  // namespace sp

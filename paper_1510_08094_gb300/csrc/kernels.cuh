@@ -1,0 +1,408 @@
+// Device kernels of the spherical Poisson solve (Section 5), one per stage.
+//
+// Data flow of one solve (n = n_lambda, L = n/2, N = n_theta, K = L + 1
+// half-spectrum wavenumbers, Kp = K rounded up to even, workspace W[N][Kp]):
+//   rows_forward   f[N][n]  -> W: G_i(k) = sin^2(theta_i)/n * sum_q f_iq e^{-2 pi i k q/n}
+//                  (real FFT of each colatitude row through a length-L complex FFT)
+//   theta_forward  W -> W:  per k, the length-2N DFS transform of the column,
+//                  folded by the BMC symmetry X_{-j,k} = (-1)^k X_{j,k}: a DCT-II
+//                  (k even) or DST-II (k odd) of length N, each through one
+//                  length-N complex FFT (Makhoul's reordering), scaled 1/N
+//   solve          W -> W:  per k, rows j >= 1 split by parity into two
+//                  tridiagonal systems (offsets 0, +-2 of eq. linearSystems),
+//                  eliminated with factors precomputed at plan time; then the
+//                  j = 0 closure (row 0 for k != 0, w^T X_0 = 0 for k = 0)
+//   theta_inverse  W -> W:  DCT-III / DST-III back to colatitude samples
+//   rows_inverse   W -> u[N][n]: inverse real FFT of each row
+// The adjoint runs the transposed stages in reverse order (ADJ = true); each
+// transposed stage is the other transform family with different weights.
+#pragma once
+
+#include "fft.cuh"
+
+namespace sp {
+
+// position of colatitude sample i in Makhoul's reordering: even samples first,
+// odd samples reversed at the end (v_p = x_{2p}, v_{N-1-p} = x_{2p+1})
+__device__ __forceinline__ int makhoul_pos(int i, int N) {
+  return (i & 1) ? N - 1 - (i >> 1) : (i >> 1);
+}
+
+// ---------------------------------------------------------------------------
+// rows_forward: real FFT along longitude.
+//   forward (ADJ = false): W[i][k] = row_scale[i] * G_i(k)
+//   adjoint (ADJ = true):  W[i][k] = c_k * sum_q ubar_iq e^{-2 pi i k q/n},
+//                          c_0 = c_L = 1, else 2  (transpose of rows_inverse)
+// One CTA per `rows` consecutive rows; shared memory rows * L complex.
+// ---------------------------------------------------------------------------
+template <typename T, bool ADJ, bool BIG>
+__global__ void __launch_bounds__(512) k_rows_forward(
+    const double* __restrict__ f, cpx<T>* __restrict__ W, int nt, int n, int Kp, int rows,
+    FftDesc d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
+    const cpx<T>* __restrict__ post, const double* __restrict__ row_scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  const int L = n >> 1;
+  const int row0 = blockIdx.x * rows;
+  for (int idx = threadIdx.x; idx < rows * L; idx += blockDim.x) {
+    int r = idx / L, q = idx - r * L;
+    int row = row0 + r;
+    cpx<T> z = {(T)0, (T)0};
+    if (row < nt) {
+      double2 v = __ldg(reinterpret_cast<const double2*>(f + (size_t)row * n) + q);
+      z = {(T)v.x, (T)v.y};
+    }
+    sm[r * L + __ldg(perm + q)] = z;
+  }
+  __syncthreads();
+  fft_run<-1, BIG>(sm, rows, d, tw);
+  const int K = L + 1;
+  for (int idx = threadIdx.x; idx < rows * Kp; idx += blockDim.x) {
+    int r = idx / Kp, k = idx - r * Kp;
+    int row = row0 + r;
+    if (row >= nt) continue;
+    cpx<T> out = {(T)0, (T)0};
+    if (k < K) {
+      const cpx<T>* Z = sm + r * L;
+      cpx<T> zk = Z[k == L ? 0 : k];
+      cpx<T> zc = conj(Z[k == 0 ? 0 : L - k]);
+      cpx<T> e = ldg_c(post + k);                 // exp(-2 pi i k / n)
+      cpx<T> s = (T)0.5 * (zk + zc);
+      cpx<T> t = cmul(e, zk - zc);                // G = s - (i/2) t
+      out = {fma((T)0.5, t.im, s.re), fma((T)-0.5, t.re, s.im)};
+      T scale;
+      if (ADJ) scale = (k == 0 || k == L) ? (T)1 : (T)2;
+      else scale = (T)__ldg(row_scale + row);
+      out = scale * out;
+    }
+    W[(size_t)row * Kp + k] = out;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// rows_inverse: inverse real FFT along longitude,
+//   u_iq = Re U_0 + 2 Re sum_{k=1}^{L-1} U_k e^{2 pi i k q/n} + Re U_L (-1)^q.
+//   forward: U = W, u written unscaled.
+//   adjoint: U_k = W_k * (k == 0 || k == L ? 1 : 1/2), u scaled by row_scale
+//            (transpose of rows_forward).
+// ---------------------------------------------------------------------------
+template <typename T, bool ADJ, bool BIG>
+__global__ void __launch_bounds__(512) k_rows_inverse(
+    const cpx<T>* __restrict__ W, double* __restrict__ u, int nt, int n, int Kp, int rows,
+    FftDesc d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
+    const cpx<T>* __restrict__ post, const double* __restrict__ row_scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  const int L = n >> 1;
+  const int row0 = blockIdx.x * rows;
+  for (int idx = threadIdx.x; idx < rows * L; idx += blockDim.x) {
+    int r = idx / L, k = idx - r * L;
+    int row = row0 + r;
+    cpx<T> z = {(T)0, (T)0};
+    if (row < nt) {
+      const cpx<T>* U = W + (size_t)row * Kp;
+      cpx<T> uk = U[k];
+      cpx<T> up = U[L - k];                      // k = 0 pairs with the Nyquist bin
+      if (k == 0) {
+        uk.im = (T)0;
+        up.im = (T)0;
+      } else if (ADJ) {
+        uk = (T)0.5 * uk;
+        up = (T)0.5 * up;
+      }
+      cpx<T> uc = conj(up);
+      cpx<T> e = conj(ldg_c(post + k));          // exp(+2 pi i k / n)
+      cpx<T> t = cmul(e, uk - uc);               // Z = (uk + uc) + i t
+      cpx<T> s = uk + uc;
+      z = {s.re - t.im, s.im + t.re};
+    }
+    sm[r * L + __ldg(perm + k)] = z;
+  }
+  __syncthreads();
+  fft_run<+1, BIG>(sm, rows, d, tw);
+  for (int idx = threadIdx.x; idx < rows * L; idx += blockDim.x) {
+    int r = idx / L, q = idx - r * L;
+    int row = row0 + r;
+    if (row >= nt) continue;
+    cpx<T> z = sm[idx];
+    double scale = ADJ ? __ldg(row_scale + row) : 1.0;
+    double2 v = {scale * (double)z.re, scale * (double)z.im};
+    reinterpret_cast<double2*>(u + (size_t)row * n)[q] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// theta_forward: per column k, P_j = (1/2)(w_j V_j + conj(w_j) V_{N-j}), with
+// V = FFT_N of the Makhoul-reordered column (odd k: samples times (-1)^i) and
+// w_j = exp(-i pi j / (2N)); P is DCT-II of the column (odd k: P_{N-j} is its
+// DST-II at j).
+//   forward: F_j = P_j / N (k even), F_j = -i P_{N-j} / N (k odd, F_0 = 0)
+//   adjoint: Xbar_j = c_j P_j (k even, c_0 = 1, c_j = 2), Xbar_j = -2i P_{N-j}
+//            (k odd, Xbar_0 = 0)  (transpose of theta_inverse)
+// One CTA per `cols` consecutive columns.
+// ---------------------------------------------------------------------------
+template <typename T, bool ADJ, bool BIG>
+__global__ void __launch_bounds__(512) k_theta_forward(
+    cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d,
+    const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  const int k0 = blockIdx.x * cols;
+  for (int idx = threadIdx.x; idx < N * cols; idx += blockDim.x) {
+    int i = idx / cols, c = idx - i * cols;
+    int k = k0 + c;
+    cpx<T> v = {(T)0, (T)0};
+    if (k < K) {
+      v = W[(size_t)i * Kp + k];
+      if ((k & 1) && (i & 1)) v = {-v.re, -v.im};
+    }
+    sm[c * N + __ldg(perm + makhoul_pos(i, N))] = v;
+  }
+  __syncthreads();
+  fft_run<-1, BIG>(sm, cols, d, tw);
+  const T invN = (T)1 / (T)N;
+  for (int idx = threadIdx.x; idx < N * cols; idx += blockDim.x) {
+    int j = idx / cols, c = idx - j * cols;
+    int k = k0 + c;
+    if (k >= K) continue;
+    const cpx<T>* V = sm + c * N;
+    cpx<T> out;
+    if ((k & 1) == 0) {
+      cpx<T> w = ldg_c(post + j);
+      cpx<T> a = V[j], b = V[j == 0 ? 0 : N - j];
+      cpx<T> p = (T)0.5 * (cmul(w, a) + cmulc(b, w));
+      if (ADJ) out = (j == 0 ? (T)1 : (T)2) * p;
+      else out = invN * p;
+    } else if (j == 0) {
+      out = {(T)0, (T)0};
+    } else {
+      int jj = N - j;
+      cpx<T> w = ldg_c(post + jj);
+      cpx<T> a = V[jj], b = V[j];
+      cpx<T> p = (T)0.5 * (cmul(w, a) + cmulc(b, w));
+      // forward: -i p / N ; adjoint: -2 i p
+      T s = ADJ ? (T)2 : invN;
+      out = {s * p.im, -s * p.re};
+    }
+    W[(size_t)j * Kp + k] = out;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// theta_inverse: per column k, DCT-III (k even) U_i = Y_0 + 2 sum_j Y_j cos(j theta_i)
+// with Y = X, or for k odd i (-1)^i times the DCT-III of Y_j = X_{N-j} (Y_0 = 0),
+// through one inverse FFT of V_j = exp(i pi j/(2N)) (Y_j - i Y_{N-j}) (Y_N = 0)
+// and the inverse Makhoul reordering.
+//   forward: U = DCT-III(X) (k even), i DST-III(X) (k odd)
+//   adjoint: inputs with j >= 1 halved and outputs scaled 1/N: the transpose
+//            of theta_forward
+// ---------------------------------------------------------------------------
+template <typename T, bool ADJ, bool BIG>
+__global__ void __launch_bounds__(512) k_theta_inverse(
+    cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d,
+    const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  const int k0 = blockIdx.x * cols;
+  // pre-twiddle straight from global memory, one thread per pair (j, N - j),
+  // j = 0 .. N/2, writing V_j and V_{N-j} to their digit-reversed slots
+  const int H = N / 2 + 1;
+  for (int idx = threadIdx.x; idx < H * cols; idx += blockDim.x) {
+    int j = idx / cols, c = idx - j * cols;
+    int k = k0 + c;
+    cpx<T>* V = sm + c * N;
+    const bool odd = (k & 1);
+    if (k >= K) {
+      V[__ldg(perm + j)] = {(T)0, (T)0};
+      if (j > 0 && N - j != j) V[__ldg(perm + N - j)] = {(T)0, (T)0};
+      continue;
+    }
+    if (j == 0) {
+      // V_0 = Y_0 - i Y_N = X_0 (k even) or 0 (k odd)
+      V[__ldg(perm + 0)] = odd ? cpx<T>{(T)0, (T)0} : W[k];
+      continue;
+    }
+    int jj = N - j;
+    cpx<T> xa = W[(size_t)j * Kp + k], xb = W[(size_t)jj * Kp + k];
+    if (ADJ) {
+      xa = (T)0.5 * xa;
+      xb = (T)0.5 * xb;
+    }
+    // Y_j, Y_{N-j}
+    cpx<T> ya = odd ? xb : xa;
+    cpx<T> yb = odd ? xa : xb;
+    cpx<T> wa = conj(ldg_c(post + j));     // exp(+i pi j/(2N))
+    V[__ldg(perm + j)] = cmul(wa, cpx<T>{ya.re + yb.im, ya.im - yb.re});   // w (Y_j - i Y_{N-j})
+    if (jj != j) {
+      cpx<T> wb = conj(ldg_c(post + jj));
+      V[__ldg(perm + jj)] = cmul(wb, cpx<T>{yb.re + ya.im, yb.im - ya.re});
+    }
+  }
+  __syncthreads();
+  fft_run<+1, BIG>(sm, cols, d, tw);
+  const T scale = ADJ ? (T)1 / (T)N : (T)1;
+  for (int idx = threadIdx.x; idx < N * cols; idx += blockDim.x) {
+    int i = idx / cols, c = idx - i * cols;
+    int k = k0 + c;
+    if (k >= K) continue;
+    cpx<T> v = sm[c * N + makhoul_pos(i, N)];
+    if (k & 1) {
+      // times i (-1)^i
+      T sg = (i & 1) ? -scale : scale;
+      v = {-sg * v.im, sg * v.re};
+    } else {
+      v = scale * v;
+    }
+    W[(size_t)i * Kp + k] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Plan-time factorisation of the parity tridiagonals of every column.
+// Chain rows j = j0, j0+2, ... < N (j0 = 1 odd chain, 2 even chain):
+//   a_j = (j-1)(j-2)/4 (couples j-2), b_j = -(j^2/2 + k^2), c_j = (j+1)(j+2)/4.
+// Thomas without pivoting in increasing j: u_0 = b_j0, l_t = a_t / u_{t-1},
+// u_t = b_t - l_t c_{t-1}.  Stored per (j, k): l, 1/u, c/u.
+// Thread layout: idx < K -> odd chain of k = idx; else even chain of k = idx - K.
+// ---------------------------------------------------------------------------
+__global__ void k_factor(double* __restrict__ fl, double* __restrict__ fiu, double* __restrict__ fcu,
+                         int N, int K, int Kp) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 2 * K) return;
+  const bool even = idx >= K;
+  const int k = even ? idx - K : idx;
+  const double k2 = (double)k * (double)k;
+  const int j0 = even ? 2 : 1;
+  double u_prev = 0.0, c_prev = 0.0;
+  for (int j = j0; j < N; j += 2) {
+    const double jd = (double)j;
+    const double a = (jd - 1.0) * (jd - 2.0) * 0.25;
+    const double b = -(jd * jd * 0.5 + k2);
+    const double c = (jd + 1.0) * (jd + 2.0) * 0.25;
+    double l = 0.0, uu = b;
+    if (j > j0) {
+      l = a / u_prev;
+      uu = b - l * c_prev;
+    }
+    const double iu = 1.0 / uu;
+    const size_t o = (size_t)j * Kp + k;
+    fl[o] = l;
+    fiu[o] = iu;
+    fcu[o] = c * iu;
+    u_prev = uu;
+    c_prev = c;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// solve (ADJ = false): X = M_k^{-1} F per column, in place.
+//   chains: y_t = d_t - l_t y_{t-1}; x_t = y_t/u_t - (c_t/u_t) x_{t+1}
+//   closure (even-chain thread): k = 0: X_0 = sum_{j even >= 2} 2 X_j/(j^2-1)
+//   (w^T X_0 = 0 with X_{-j,0} = X_{j,0}); k even != 0: X_0 = (X_2 - F_0)/k^2
+//   (row 0 with X_{-2,k} = X_{2,k}); k odd: X_0 = 0.
+// solve (ADJ = true): the transpose, F = M_k^{-T} X:
+//   k even != 0: Fbar_0 = -Xbar_0/k^2 and Xbar_2 += Xbar_0/k^2; k = 0:
+//   Xbar_j += 2 Xbar_0/(j^2-1) for even j, Fbar_0 = 0; k odd: Fbar_0 = 0;
+//   then T^T = U^T L^T: z_t = (b_t - c_{t-1} z_{t-1})/u_t, y_t = z_t - l_{t+1} y_{t+1}.
+// ---------------------------------------------------------------------------
+template <bool ADJ>
+__global__ void k_solve(cpx<double>* __restrict__ W, const double* __restrict__ fl,
+                        const double* __restrict__ fiu, const double* __restrict__ fcu,
+                        int N, int K, int Kp) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 2 * K) return;
+  const bool even = idx >= K;
+  const int k = even ? idx - K : idx;
+  const int j0 = even ? 2 : 1;
+  if (j0 >= N) {
+    // no chain rows; only the closure of row 0 remains
+    if (even) {
+      cpx<double>& x0 = W[k];
+      if (!ADJ) {
+        x0 = (k == 0 || (k & 1)) ? cpx<double>{0.0, 0.0}
+                                 : (-1.0 / ((double)k * (double)k)) * x0;
+      } else {
+        x0 = (k == 0 || (k & 1)) ? cpx<double>{0.0, 0.0}
+                                 : (-1.0 / ((double)k * (double)k)) * x0;
+      }
+    }
+    return;
+  }
+  const int jlast = j0 + 2 * ((N - 1 - j0) / 2);
+  if (!ADJ) {
+    cpx<double> y = {0.0, 0.0};
+    for (int j = j0; j <= jlast; j += 2) {
+      const size_t o = (size_t)j * Kp + k;
+      cpx<double> dv = W[o];
+      double l = __ldg(fl + o);
+      y = {fma(-l, y.re, dv.re), fma(-l, y.im, dv.im)};
+      W[o] = y;
+    }
+    cpx<double> x = {0.0, 0.0};
+    cpx<double> acc = {0.0, 0.0};
+    for (int j = jlast; j >= j0; j -= 2) {
+      const size_t o = (size_t)j * Kp + k;
+      cpx<double> yv = W[o];
+      double iu = __ldg(fiu + o), cu = __ldg(fcu + o);
+      x = {fma(yv.re, iu, -cu * x.re), fma(yv.im, iu, -cu * x.im)};
+      W[o] = x;
+      if (even && k == 0) {
+        double jd = (double)j;
+        double wj = 2.0 / (jd * jd - 1.0);
+        acc = {fma(wj, x.re, acc.re), fma(wj, x.im, acc.im)};
+      }
+    }
+    if (even) {
+      // x now holds X_2
+      cpx<double>& x0 = W[k];
+      if (k == 0) {
+        x0 = acc;
+      } else if (k & 1) {
+        x0 = {0.0, 0.0};
+      } else {
+        double ik2 = 1.0 / ((double)k * (double)k);
+        x0 = {(x.re - x0.re) * ik2, (x.im - x0.im) * ik2};
+      }
+    }
+  } else {
+    cpx<double> xb0 = {0.0, 0.0};
+    if (even) {
+      xb0 = W[k];
+      W[k] = (k == 0 || (k & 1)) ? cpx<double>{0.0, 0.0}
+                                 : (-1.0 / ((double)k * (double)k)) * xb0;
+    }
+    // forward sweep with U^T: z_t = (b_t - c_{t-1} z_{t-1}) / u_t
+    cpx<double> z = {0.0, 0.0};
+    for (int j = j0; j <= jlast; j += 2) {
+      const size_t o = (size_t)j * Kp + k;
+      cpx<double> bv = W[o];
+      if (even) {
+        if (k == 0) {
+          double jd = (double)j;
+          double wj = 2.0 / (jd * jd - 1.0);
+          bv = {fma(wj, xb0.re, bv.re), fma(wj, xb0.im, bv.im)};
+        } else if (j == 2 && !(k & 1)) {
+          double ik2 = 1.0 / ((double)k * (double)k);
+          bv = {fma(ik2, xb0.re, bv.re), fma(ik2, xb0.im, bv.im)};
+        }
+      }
+      double iu = __ldg(fiu + o);
+      double cprev = (double)((j - 1) * j) * 0.25;    // c_{j-2} = (j-1) j / 4
+      if (j == j0) cprev = 0.0;
+      z = {(bv.re - cprev * z.re) * iu, (bv.im - cprev * z.im) * iu};
+      W[o] = z;
+    }
+    // backward sweep with L^T: y_t = z_t - l_{t+1} y_{t+1}
+    cpx<double> y = {0.0, 0.0};
+    double lnext = 0.0;
+    for (int j = jlast; j >= j0; j -= 2) {
+      const size_t o = (size_t)j * Kp + k;
+      cpx<double> zv = W[o];
+      y = {fma(-lnext, y.re, zv.re), fma(-lnext, y.im, zv.im)};
+      W[o] = y;
+      lnext = __ldg(fl + o);
+    }
+  }
+}
+
+}  // namespace sp

@@ -1,0 +1,503 @@
+// C ABI of the spherical Poisson solver (declarations and argument rules in
+// include/sphere_poisson.h).  Host side: plan construction (FFT radix plans,
+// twiddle tables, launch shapes, the factorised per-k tridiagonals) and the
+// launch sequences of the solve and of its transpose.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sphere_poisson.h"
+#include "kernels.cuh"
+
+using sp::cpx;
+using sp::FftDesc;
+
+namespace {
+
+constexpr int kMaxLen = 12288;             // longest transform (n_theta, n_lambda/2)
+constexpr size_t kSmemBudget = 200 * 1024;  // shared memory per CTA for a transform tile
+constexpr uint32_t kMagic = 0x53504f31u;    // "SPO1"
+constexpr double kHalfPi = 1.57079632679489661923132169163975144;
+
+thread_local char g_cuda_msg[256] = "";
+
+int cuda_fail(cudaError_t e, const char* what) {
+  snprintf(g_cuda_msg, sizeof g_cuda_msg, "CUDA error in %s: %s", what, cudaGetErrorString(e));
+  return SP_ERR_CUDA;
+}
+
+#define SP_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+// Radix plan of a transform length: 8s, then 4 or 2 for the leftover power of
+// two, then 5, 3 and the odd primes up to 31.  Returns false if L has a prime
+// factor above 31 or needs too many passes.
+bool make_fft_desc(int L, FftDesc* d) {
+  std::memset(d, 0, sizeof *d);
+  d->L = L;
+  int rest = L, s = 0;
+  auto push = [&](int r) {
+    if (s >= sp::kMaxStages) return false;
+    d->radix[s++] = r;
+    rest /= r;
+    return true;
+  };
+  while (rest % 8 == 0) if (!push(8)) return false;
+  if (rest % 4 == 0 && !push(4)) return false;
+  if (rest % 2 == 0 && !push(2)) return false;
+  const int primes[] = {5, 3, 7, 11, 13, 17, 19, 23, 29, 31};
+  for (int p : primes)
+    while (rest % p == 0) if (!push(p)) return false;
+  d->nstages = s;
+  return rest == 1;
+}
+
+// threads for a CTA that transforms nbatch sequences of the plan's length:
+// about one butterfly of the smallest radix per thread, 64 .. 512
+int fft_threads(const FftDesc& d, int nbatch) {
+  int rmin = 32;
+  for (int s = 0; s < d.nstages; ++s) rmin = d.radix[s] < rmin ? d.radix[s] : rmin;
+  long want = (long)nbatch * d.L / rmin;
+  int t = (int)(want < 64 ? 64 : (want > 512 ? 512 : want));
+  return (t + 31) / 32 * 32;
+}
+
+// mixed-radix digit reversal for the in-place decimation-in-time passes:
+// q = r_1 + R_s (r_2 + R_{s-1} (r_3 + ...)) goes to p = r_1 L/R_s + r_2 L/(R_s R_{s-1}) + ...
+void digit_reversal(const FftDesc& d, std::vector<int>& perm) {
+  perm.resize(d.L);
+  for (int q0 = 0; q0 < d.L; ++q0) {
+    int q = q0, p = 0, w = d.L;
+    for (int s = d.nstages - 1; s >= 0; --s) {
+      int R = d.radix[s];
+      w /= R;
+      p += (q % R) * w;
+      q /= R;
+    }
+    perm[q0] = p;
+  }
+}
+
+// exp(-2 pi i t / M), with the angle reduced exactly: 4t = q M + r, |r| <= M/2,
+// so 2 pi t/M = q pi/2 + (pi/2) r/M and the residual angle is within +-pi/4.
+void unit_root(long t, long M, double* re, double* im) {
+  t %= M;
+  if (t < 0) t += M;
+  long q = (4 * t + M / 2) / M;  // nearest quarter turn
+  long r = 4 * t - q * M;
+  double phi = kHalfPi * (double)r / (double)M;
+  double c = std::cos(phi), s = std::sin(phi);
+  // angle = q pi/2 + phi; value exp(-i angle)
+  double cr, sr;
+  switch (q & 3) {
+    case 0: cr = c; sr = s; break;
+    case 1: cr = -s; sr = c; break;
+    case 2: cr = -c; sr = -s; break;
+    default: cr = s; sr = -c; break;
+  }
+  *re = cr;
+  *im = -sr;
+}
+
+}  // namespace
+
+struct sp_plan_s {
+  uint32_t magic;
+  int nt, nl, L, N, K, Kp;
+  int precision, sweeps;
+  int device;
+  FftDesc row_fft, col_fft;
+  int rows_per_cta, cols_per_cta;
+  int row_threads, col_threads;
+  size_t row_smem, col_smem;
+  size_t ws_bytes;
+  void* dev;           // one allocation holding every table
+  cpx<double>* tw_row;   // exp(-2 pi i t/L), t < L
+  cpx<double>* tw_col;   // exp(-2 pi i t/N), t < N
+  int* perm_row;         // digit reversal of the length-L passes
+  int* perm_col;         // digit reversal of the length-N passes
+  cpx<double>* post_row; // exp(-2 pi i k/n), k <= L
+  cpx<double>* post_col; // exp(-i pi j/(2N)), j <= N
+  double* row_scale;     // sin^2(theta_i)/n
+  double* fac_l;         // [N][Kp] Thomas multipliers
+  double* fac_iu;        // [N][Kp] 1/pivot
+  double* fac_cu;        // [N][Kp] super-diagonal / pivot
+  // stage timing (profile_begin / profile_end)
+  std::vector<cudaEvent_t> prof_events;
+  int prof_max, prof_count;
+};
+
+namespace {
+
+bool plan_ok(sp_plan_t p) { return p != nullptr && p->magic == kMagic; }
+
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+int check_arrays(sp_plan_t p, const void* a, const void* b, const void* ws, size_t ws_bytes) {
+  if (!plan_ok(p)) return SP_ERR_BAD_PLAN;
+  if (!a || !b || !ws) return SP_ERR_NULL;
+  if (((uintptr_t)a | (uintptr_t)b | (uintptr_t)ws) & 15) return SP_ERR_MISALIGNED;
+  if (ws_bytes < p->ws_bytes) return SP_ERR_WORKSPACE;
+  return SP_OK;
+}
+
+// true if the radix plan needs the general (large odd prime) pass set
+bool needs_big(const FftDesc& d) {
+  for (int s = 0; s < d.nstages; ++s)
+    if (d.radix[s] > 8) return true;
+  return false;
+}
+
+constexpr int kStages = 5;
+const char* const kStageNames[kStages] = {"rows_forward", "theta_forward", "solve", "theta_inverse",
+                                          "rows_inverse"};
+
+// records the boundary event s of the current profiled call, if any
+struct StageMarks {
+  sp_plan_t p;
+  cudaStream_t st;
+  bool on;
+  void mark(int s) {
+    if (on) cudaEventRecord(p->prof_events[(size_t)p->prof_count * (kStages + 1) + s], st);
+  }
+};
+
+template <bool ADJ, bool BR, bool BC>
+void enqueue_solve(sp_plan_t p, const double* in, double* out, cpx<double>* W, cudaStream_t st) {
+  StageMarks m{p, st, !p->prof_events.empty() && p->prof_count < p->prof_max};
+  const int row_blocks = (p->nt + p->rows_per_cta - 1) / p->rows_per_cta;
+  const int col_blocks = (p->K + p->cols_per_cta - 1) / p->cols_per_cta;
+  const int solve_threads = 128;
+  const int solve_blocks = (2 * p->K + solve_threads - 1) / solve_threads;
+  m.mark(0);
+  sp::k_rows_forward<double, ADJ, BR><<<row_blocks, p->row_threads, p->row_smem, st>>>(
+      in, W, p->nt, p->nl, p->Kp, p->rows_per_cta, p->row_fft, p->tw_row, p->perm_row, p->post_row,
+      p->row_scale);
+  m.mark(1);
+  sp::k_theta_forward<double, ADJ, BC><<<col_blocks, p->col_threads, p->col_smem, st>>>(
+      W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft, p->tw_col, p->perm_col, p->post_col);
+  m.mark(2);
+  sp::k_solve<ADJ><<<solve_blocks, solve_threads, 0, st>>>(W, p->fac_l, p->fac_iu, p->fac_cu, p->N, p->K,
+                                                            p->Kp);
+  m.mark(3);
+  sp::k_theta_inverse<double, ADJ, BC><<<col_blocks, p->col_threads, p->col_smem, st>>>(
+      W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft, p->tw_col, p->perm_col, p->post_col);
+  m.mark(4);
+  sp::k_rows_inverse<double, ADJ, BR><<<row_blocks, p->row_threads, p->row_smem, st>>>(
+      W, out, p->nt, p->nl, p->Kp, p->rows_per_cta, p->row_fft, p->tw_row, p->perm_row, p->post_row,
+      p->row_scale);
+  m.mark(5);
+  if (m.on) p->prof_count++;
+}
+
+template <bool ADJ>
+int launch_solve(sp_plan_t p, const double* in, double* out, void* workspace, cudaStream_t st) {
+  cpx<double>* W = static_cast<cpx<double>*>(workspace);
+  const bool br = needs_big(p->row_fft), bc = needs_big(p->col_fft);
+  if (!br && !bc) enqueue_solve<ADJ, false, false>(p, in, out, W, st);
+  else if (!br && bc) enqueue_solve<ADJ, false, true>(p, in, out, W, st);
+  else if (br && !bc) enqueue_solve<ADJ, true, false>(p, in, out, W, st);
+  else enqueue_solve<ADJ, true, true>(p, in, out, W, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "solve launch");
+  return SP_OK;
+}
+
+template <bool B>
+cudaError_t allow_all_smem(size_t row_smem, size_t col_smem) {
+  cudaError_t e = cudaSuccess;
+  auto upd = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  upd(allow_smem(sp::k_rows_forward<double, false, B>, row_smem));
+  upd(allow_smem(sp::k_rows_forward<double, true, B>, row_smem));
+  upd(allow_smem(sp::k_rows_inverse<double, false, B>, row_smem));
+  upd(allow_smem(sp::k_rows_inverse<double, true, B>, row_smem));
+  upd(allow_smem(sp::k_theta_forward<double, false, B>, col_smem));
+  upd(allow_smem(sp::k_theta_forward<double, true, B>, col_smem));
+  upd(allow_smem(sp::k_theta_inverse<double, false, B>, col_smem));
+  upd(allow_smem(sp::k_theta_inverse<double, true, B>, col_smem));
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precision,
+                        int refine_sweeps, unsigned flags, size_t* workspace_bytes) {
+  if (!plan) return SP_ERR_NULL;
+  *plan = nullptr;
+  if (n_theta < 1 || n_lambda < 2 || (n_lambda & 1)) return SP_ERR_BAD_SIZE;
+  if (n_theta > kMaxLen || n_lambda / 2 > kMaxLen) return SP_ERR_BAD_SIZE;
+  if (precision != SP_FP64) return SP_ERR_UNSUPPORTED;
+  if (flags != 0 || refine_sweeps < 0) return SP_ERR_BAD_ARG;
+
+  FftDesc rd, cd;
+  if (!make_fft_desc(n_lambda / 2, &rd) || !make_fft_desc(n_theta, &cd)) return SP_ERR_BAD_SIZE;
+
+  sp_plan_s* p = new (std::nothrow) sp_plan_s();
+  if (!p) return SP_ERR_CUDA;
+  p->nt = n_theta;
+  p->nl = n_lambda;
+  p->L = n_lambda / 2;
+  p->N = n_theta;
+  p->K = p->L + 1;
+  p->Kp = (p->K + 1) & ~1;
+  p->precision = precision;
+  p->sweeps = refine_sweeps;
+  p->row_fft = rd;
+  p->col_fft = cd;
+  const size_t csz = sizeof(cpx<double>);
+  // tiles: rows per CTA and columns per CTA, powers of two up to 8 within the budget
+  p->rows_per_cta = 1;
+  while (p->rows_per_cta < 8 && (size_t)(2 * p->rows_per_cta) * p->L * csz <= 96 * 1024 &&
+         2 * p->rows_per_cta <= p->nt)
+    p->rows_per_cta *= 2;
+  p->cols_per_cta = 1;
+  while (p->cols_per_cta < 8 && (size_t)(2 * p->cols_per_cta) * p->N * csz <= kSmemBudget &&
+         2 * p->cols_per_cta <= p->Kp)
+    p->cols_per_cta *= 2;
+  p->row_smem = (size_t)p->rows_per_cta * p->L * csz;
+  p->col_smem = (size_t)p->cols_per_cta * p->N * csz;
+  p->row_threads = fft_threads(rd, p->rows_per_cta);
+  p->col_threads = fft_threads(cd, p->cols_per_cta);
+  if (p->row_threads < 0 || p->col_threads < 0 || p->row_smem > 227 * 1024 || p->col_smem > 227 * 1024) {
+    delete p;
+    return SP_ERR_BAD_SIZE;
+  }
+  p->ws_bytes = (size_t)p->N * p->Kp * csz;
+
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return cuda_fail(cudaGetLastError(), "cudaGetDevice");
+  }
+
+  // host tables
+  std::vector<cpx<double>> tw_row(p->L), tw_col(p->N), post_row(p->L + 1), post_col(p->N + 1);
+  for (int t = 0; t < p->L; ++t) unit_root(t, p->L, &tw_row[t].re, &tw_row[t].im);
+  for (int t = 0; t < p->N; ++t) unit_root(t, p->N, &tw_col[t].re, &tw_col[t].im);
+  for (int k = 0; k <= p->L; ++k) unit_root(k, n_lambda, &post_row[k].re, &post_row[k].im);
+  for (int j = 0; j <= p->N; ++j) unit_root(j, 4L * p->N, &post_col[j].re, &post_col[j].im);
+  std::vector<int> perm_row, perm_col;
+  digit_reversal(rd, perm_row);
+  digit_reversal(cd, perm_col);
+  std::vector<double> row_scale(p->nt);
+  for (int i = 0; i < p->nt; ++i) {
+    double re, im;
+    unit_root(2 * i + 1, 4L * p->N, &re, &im);  // sin(theta_i) = -im
+    row_scale[i] = (im * im) / (double)n_lambda;
+  }
+
+  auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  size_t off = 0;
+  size_t o_tw_row = off; off = align(off + p->L * csz);
+  size_t o_tw_col = off; off = align(off + p->N * csz);
+  size_t o_post_row = off; off = align(off + (p->L + 1) * csz);
+  size_t o_post_col = off; off = align(off + (p->N + 1) * csz);
+  size_t o_scale = off; off = align(off + p->nt * sizeof(double));
+  size_t o_perm_row = off; off = align(off + p->L * sizeof(int));
+  size_t o_perm_col = off; off = align(off + p->N * sizeof(int));
+  const size_t fac = (size_t)p->N * p->Kp * sizeof(double);
+  size_t o_l = off; off = align(off + fac);
+  size_t o_iu = off; off = align(off + fac);
+  size_t o_cu = off; off = align(off + fac);
+
+  cudaError_t e = cudaMalloc(&p->dev, off);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "cudaMalloc(plan tables)");
+  }
+  char* base = static_cast<char*>(p->dev);
+  p->tw_row = reinterpret_cast<cpx<double>*>(base + o_tw_row);
+  p->tw_col = reinterpret_cast<cpx<double>*>(base + o_tw_col);
+  p->post_row = reinterpret_cast<cpx<double>*>(base + o_post_row);
+  p->post_col = reinterpret_cast<cpx<double>*>(base + o_post_col);
+  p->row_scale = reinterpret_cast<double*>(base + o_scale);
+  p->perm_row = reinterpret_cast<int*>(base + o_perm_row);
+  p->perm_col = reinterpret_cast<int*>(base + o_perm_col);
+  p->fac_l = reinterpret_cast<double*>(base + o_l);
+  p->fac_iu = reinterpret_cast<double*>(base + o_iu);
+  p->fac_cu = reinterpret_cast<double*>(base + o_cu);
+  p->magic = kMagic;
+
+  int rc = SP_OK;
+  auto step = [&](cudaError_t err, const char* what) {
+    if (rc == SP_OK && err != cudaSuccess) rc = cuda_fail(err, what);
+  };
+  step(cudaMemcpy(p->tw_row, tw_row.data(), p->L * csz, cudaMemcpyHostToDevice), "copy tw_row");
+  step(cudaMemcpy(p->tw_col, tw_col.data(), p->N * csz, cudaMemcpyHostToDevice), "copy tw_col");
+  step(cudaMemcpy(p->post_row, post_row.data(), (p->L + 1) * csz, cudaMemcpyHostToDevice), "copy post_row");
+  step(cudaMemcpy(p->post_col, post_col.data(), (p->N + 1) * csz, cudaMemcpyHostToDevice), "copy post_col");
+  step(cudaMemcpy(p->row_scale, row_scale.data(), p->nt * sizeof(double), cudaMemcpyHostToDevice), "copy row_scale");
+  step(cudaMemcpy(p->perm_row, perm_row.data(), p->L * sizeof(int), cudaMemcpyHostToDevice), "copy perm_row");
+  step(cudaMemcpy(p->perm_col, perm_col.data(), p->N * sizeof(int), cudaMemcpyHostToDevice), "copy perm_col");
+  step(cudaMemset(p->fac_l, 0, off - o_l), "clear factors");
+  if (rc == SP_OK) {
+    int threads = 128, blocks = (2 * p->K + threads - 1) / threads;
+    sp::k_factor<<<blocks, threads>>>(p->fac_l, p->fac_iu, p->fac_cu, p->N, p->K, p->Kp);
+    step(cudaGetLastError(), "k_factor launch");
+    step(cudaDeviceSynchronize(), "k_factor");
+  }
+  step(allow_all_smem<false>(p->row_smem, p->col_smem), "shared memory attribute");
+  step(allow_all_smem<true>(p->row_smem, p->col_smem), "shared memory attribute");
+  if (rc != SP_OK) {
+    cudaFree(p->dev);
+    p->magic = 0;
+    delete p;
+    return rc;
+  }
+  if (workspace_bytes) *workspace_bytes = p->ws_bytes;
+  *plan = p;
+  return SP_OK;
+}
+
+int sphere_poisson_workspace_size(sp_plan_t plan, size_t* workspace_bytes) {
+  if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
+  if (!workspace_bytes) return SP_ERR_NULL;
+  *workspace_bytes = plan->ws_bytes;
+  return SP_OK;
+}
+
+int sphere_poisson_solve(sp_plan_t plan, const double* f, double* u, void* workspace,
+                         size_t workspace_bytes, void* stream) {
+  int rc = check_arrays(plan, f, u, workspace, workspace_bytes);
+  if (rc != SP_OK) return rc;
+  return launch_solve<false>(plan, f, u, workspace, static_cast<cudaStream_t>(stream));
+}
+
+int sphere_poisson_solve_adjoint(sp_plan_t plan, const double* ubar, double* fbar, void* workspace,
+                                 size_t workspace_bytes, void* stream) {
+  int rc = check_arrays(plan, ubar, fbar, workspace, workspace_bytes);
+  if (rc != SP_OK) return rc;
+  return launch_solve<true>(plan, ubar, fbar, workspace, static_cast<cudaStream_t>(stream));
+}
+
+int sphere_poisson_host_buffer_size(sp_plan_t plan, size_t* device_buffer_bytes) {
+  if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
+  if (!device_buffer_bytes) return SP_ERR_NULL;
+  size_t grid = ((size_t)plan->nt * plan->nl * sizeof(double) + 255) & ~(size_t)255;
+  *device_buffer_bytes = 2 * grid + plan->ws_bytes;
+  return SP_OK;
+}
+
+int sphere_poisson_solve_host(sp_plan_t plan, const double* f_host, double* u_host, void* device_buffer,
+                              size_t device_buffer_bytes, void* stream) {
+  if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
+  if (!f_host || !u_host || !device_buffer) return SP_ERR_NULL;
+  if ((uintptr_t)device_buffer & 15) return SP_ERR_MISALIGNED;
+  size_t need = 0;
+  sphere_poisson_host_buffer_size(plan, &need);
+  if (device_buffer_bytes < need) return SP_ERR_WORKSPACE;
+  const size_t bytes = (size_t)plan->nt * plan->nl * sizeof(double);
+  const size_t grid = (bytes + 255) & ~(size_t)255;
+  char* base = static_cast<char*>(device_buffer);
+  double* d_f = reinterpret_cast<double*>(base);
+  double* d_u = reinterpret_cast<double*>(base + grid);
+  void* ws = base + 2 * grid;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SP_CUDA(cudaMemcpyAsync(d_f, f_host, bytes, cudaMemcpyHostToDevice, st));
+  int rc = launch_solve<false>(plan, d_f, d_u, ws, st);
+  if (rc != SP_OK) return rc;
+  SP_CUDA(cudaMemcpyAsync(u_host, d_u, bytes, cudaMemcpyDeviceToHost, st));
+  SP_CUDA(cudaStreamSynchronize(st));
+  return SP_OK;
+}
+
+int sphere_poisson_launch_count(sp_plan_t plan, int adjoint, int* launches) {
+  if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
+  if (!launches) return SP_ERR_NULL;
+  (void)adjoint;
+  *launches = kStages;
+  return SP_OK;
+}
+
+static void release_events(sp_plan_t plan) {
+  for (cudaEvent_t e : plan->prof_events) cudaEventDestroy(e);
+  plan->prof_events.clear();
+  plan->prof_max = plan->prof_count = 0;
+}
+
+int sphere_poisson_profile_begin(sp_plan_t plan, int max_solves) {
+  if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
+  if (max_solves < 1 || max_solves > 100000) return SP_ERR_BAD_ARG;
+  release_events(plan);
+  plan->prof_events.resize((size_t)max_solves * (kStages + 1));
+  for (auto& e : plan->prof_events) {
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) {
+      e = nullptr;
+      release_events(plan);
+      return cuda_fail(err, "cudaEventCreate");
+    }
+  }
+  plan->prof_max = max_solves;
+  plan->prof_count = 0;
+  return SP_OK;
+}
+
+int sphere_poisson_profile_end(sp_plan_t plan, double* stage_ms, int max_stages, int* solves, int* stages) {
+  if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
+  if (!stage_ms || !solves || !stages) return SP_ERR_NULL;
+  for (int s = 0; s < max_stages; ++s) stage_ms[s] = 0.0;
+  int rc = SP_OK;
+  for (int c = 0; c < plan->prof_count && rc == SP_OK; ++c) {
+    cudaEvent_t* ev = &plan->prof_events[(size_t)c * (kStages + 1)];
+    cudaError_t err = cudaEventSynchronize(ev[kStages]);
+    if (err != cudaSuccess) { rc = cuda_fail(err, "cudaEventSynchronize"); break; }
+    for (int s = 0; s < kStages && s < max_stages; ++s) {
+      float ms = 0.f;
+      err = cudaEventElapsedTime(&ms, ev[s], ev[s + 1]);
+      if (err != cudaSuccess) { rc = cuda_fail(err, "cudaEventElapsedTime"); break; }
+      stage_ms[s] += ms;
+    }
+  }
+  *solves = plan->prof_count;
+  *stages = kStages;
+  release_events(plan);
+  return rc;
+}
+
+const char* sphere_poisson_stage_name(sp_plan_t plan, int stage) {
+  if (!plan_ok(plan) || stage < 0 || stage >= kStages) return "";
+  return kStageNames[stage];
+}
+
+int sphere_poisson_destroy(sp_plan_t plan) {
+  if (!plan) return SP_OK;
+  if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
+  release_events(plan);
+  cudaError_t e = cudaFree(plan->dev);
+  plan->magic = 0;
+  delete plan;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFree(plan tables)");
+  return SP_OK;
+}
+
+const char* sphere_poisson_status_string(int status) {
+  switch (status) {
+    case SP_OK: return "success";
+    case SP_ERR_BAD_SIZE: return "bad grid size: need n_theta >= 1, even n_lambda >= 2, lengths <= 12288 "
+                                 "with prime factors <= 31";
+    case SP_ERR_NULL: return "a required pointer is NULL";
+    case SP_ERR_MISALIGNED: return "a device pointer is not 16-byte aligned";
+    case SP_ERR_WORKSPACE: return "workspace smaller than the plan requires";
+    case SP_ERR_CUDA: return g_cuda_msg[0] ? g_cuda_msg : "CUDA runtime error";
+    case SP_ERR_UNSUPPORTED: return "precision or flag combination not supported";
+    case SP_ERR_BAD_PLAN: return "NULL or destroyed plan handle";
+    case SP_ERR_BAD_ARG: return "invalid argument";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -290,7 +290,7 @@ def test_sampled_columns_match_full_solve():
     f, _ = _series(40, 80, 15, seed=3)
     u = O.poisson(f)
     ks = [0, 1, 2, 7, -5, 39, -39]
-    U, F, X = O.sampled_columns(f, ks, chunk=16)
+    U, F, X = O.sampled_columns(f, ks)
     assert np.abs(U - O.lambda_spectrum(u, ks)).max() < 1e-14
 
 
