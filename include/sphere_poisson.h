@@ -124,6 +124,15 @@ int sphere_poisson_profile_begin(sp_plan_t plan, int max_solves);
 int sphere_poisson_profile_end(sp_plan_t plan, double* stage_ms, int max_stages, int* solves, int* stages);
 const char* sphere_poisson_stage_name(sp_plan_t plan, int stage);
 
+/*
+ * Diagnostic, not part of the solve: measured FMA issue rates of the current
+ * GPU in G instructions/s (FP64 and FP32 pipes, register-only loops filling
+ * every SM, about 50 ms).  Used as the denominator of the ALU roofline of the
+ * transform kernels, which this GPU's FP64 rate bounds.  The paper has no
+ * counterpart.  Synchronous.
+ */
+int sphere_poisson_pipe_rates(double* fp64_fma_gops, double* fp32_fma_gops);
+
 /* Release the plan and its device tables.  Synchronous; NULL is accepted. */
 int sphere_poisson_destroy(sp_plan_t plan);
 

@@ -204,5 +204,13 @@ class SpherePoisson(torch.autograd.Function):
         return g, None, None
 
 
+def pipe_rates() -> dict:
+    """Measured FMA issue rates of the current GPU (G instructions/s)."""
+    lib = _lib.load()
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _lib.check(lib.sphere_poisson_pipe_rates(ctypes.byref(a), ctypes.byref(b)), "sphere_poisson_pipe_rates")
+    return {"fp64_fma_gops": a.value, "fp32_fma_gops": b.value}
+
+
 def poisson(f: torch.Tensor, precision: str = "fp64", refine_sweeps: int = 0) -> torch.Tensor:
     return SpherePoisson.apply(f, precision, refine_sweeps)

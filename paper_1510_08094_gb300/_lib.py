@@ -38,6 +38,7 @@ EXPORTED = (
     "sphere_poisson_profile_begin",
     "sphere_poisson_profile_end",
     "sphere_poisson_stage_name",
+    "sphere_poisson_pipe_rates",
     "sphere_poisson_destroy",
     "sphere_poisson_status_string",
 )
@@ -78,6 +79,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.sphere_poisson_stage_name.argtypes = [vp, i32]
     lib.sphere_poisson_stage_name.restype = ctypes.c_char_p
+    lib.sphere_poisson_pipe_rates.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.sphere_poisson_destroy.argtypes = [vp]
     lib.sphere_poisson_status_string.argtypes = [i32]
     lib.sphere_poisson_status_string.restype = ctypes.c_char_p

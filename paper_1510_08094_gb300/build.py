@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB_NAME = "libsphere_poisson.so"
 LIB_PATH = os.path.join(BUILD, LIB_NAME)
-SOURCES = ["sphere_poisson.cu"]
+SOURCES = ["sphere_poisson.cu", "pipe_probe.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

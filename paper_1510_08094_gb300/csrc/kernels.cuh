@@ -305,102 +305,192 @@ __global__ void k_factor(double* __restrict__ fl, double* __restrict__ fiu, doub
 //   Xbar_j += 2 Xbar_0/(j^2-1) for even j, Fbar_0 = 0; k odd: Fbar_0 = 0;
 //   then T^T = U^T L^T: z_t = (b_t - c_{t-1} z_{t-1})/u_t, y_t = z_t - l_{t+1} y_{t+1}.
 // ---------------------------------------------------------------------------
+constexpr int kSolveBatch = 8;  // rows per register batch; two batches in flight
+
 template <bool ADJ>
-__global__ void k_solve(cpx<double>* __restrict__ W, const double* __restrict__ fl,
-                        const double* __restrict__ fiu, const double* __restrict__ fcu,
-                        int N, int K, int Kp) {
+__global__ void __launch_bounds__(64) k_solve(cpx<double>* __restrict__ W, const double* __restrict__ fl,
+                                              const double* __restrict__ fiu, const double* __restrict__ fcu,
+                                              int N, int K, int Kp) {
+  constexpr int U = kSolveBatch;
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= 2 * K) return;
   const bool even = idx >= K;
   const int k = even ? idx - K : idx;
   const int j0 = even ? 2 : 1;
+  const double ik2 = k ? 1.0 / ((double)k * (double)k) : 0.0;
   if (j0 >= N) {
-    // no chain rows; only the closure of row 0 remains
+    // no chain rows; only the closure of row 0 remains (forward: X_0 = -F_0/k^2,
+    // adjoint: Fbar_0 = -Xbar_0/k^2, both zero for k = 0 and odd k)
     if (even) {
-      cpx<double>& x0 = W[k];
-      if (!ADJ) {
-        x0 = (k == 0 || (k & 1)) ? cpx<double>{0.0, 0.0}
-                                 : (-1.0 / ((double)k * (double)k)) * x0;
-      } else {
-        x0 = (k == 0 || (k & 1)) ? cpx<double>{0.0, 0.0}
-                                 : (-1.0 / ((double)k * (double)k)) * x0;
-      }
+      cpx<double> x0 = W[k];
+      W[k] = (k == 0 || (k & 1)) ? cpx<double>{0.0, 0.0} : (-ik2) * x0;
     }
     return;
   }
-  const int jlast = j0 + 2 * ((N - 1 - j0) / 2);
+  const int M = (N - 1 - j0) / 2 + 1;            // chain length
+  const size_t stride = (size_t)2 * Kp;          // one chain step
+  cpx<double>* Wc = W + (size_t)j0 * Kp + k;
+  const double* Lc = fl + (size_t)j0 * Kp + k;
+  const double* IUc = fiu + (size_t)j0 * Kp + k;
+  const double* CUc = fcu + (size_t)j0 * Kp + k;
+  const bool zonal = even && k == 0;
+
   if (!ADJ) {
+    // forward sweep y_t = d_t - l_t y_{t-1}, rows in batches of U with the next
+    // batch's loads issued before the current batch is consumed
     cpx<double> y = {0.0, 0.0};
-    for (int j = j0; j <= jlast; j += 2) {
-      const size_t o = (size_t)j * Kp + k;
-      cpx<double> dv = W[o];
-      double l = __ldg(fl + o);
-      y = {fma(-l, y.re, dv.re), fma(-l, y.im, dv.im)};
-      W[o] = y;
+    cpx<double> dA[U], dB[U];
+    double lA[U], lB[U];
+    auto load_fwd = [&](int t0, cpx<double>* d, double* l) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        int t = t0 + u;
+        if (t < M) {
+          d[u] = Wc[t * stride];
+          l[u] = __ldg(Lc + t * stride);
+        }
+      }
+    };
+    auto run_fwd = [&](int t0, const cpx<double>* d, const double* l) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        int t = t0 + u;
+        if (t < M) {
+          y = {fma(-l[u], y.re, d[u].re), fma(-l[u], y.im, d[u].im)};
+          Wc[t * stride] = y;
+        }
+      }
+    };
+    load_fwd(0, dA, lA);
+    for (int t0 = 0; t0 < M; t0 += 2 * U) {
+      load_fwd(t0 + U, dB, lB);
+      run_fwd(t0, dA, lA);
+      load_fwd(t0 + 2 * U, dA, lA);
+      run_fwd(t0 + U, dB, lB);
     }
+    // backward sweep x_t = y_t / u_t - (c_t / u_t) x_{t+1}
     cpx<double> x = {0.0, 0.0};
     cpx<double> acc = {0.0, 0.0};
-    for (int j = jlast; j >= j0; j -= 2) {
-      const size_t o = (size_t)j * Kp + k;
-      cpx<double> yv = W[o];
-      double iu = __ldg(fiu + o), cu = __ldg(fcu + o);
-      x = {fma(yv.re, iu, -cu * x.re), fma(yv.im, iu, -cu * x.im)};
-      W[o] = x;
-      if (even && k == 0) {
-        double jd = (double)j;
-        double wj = 2.0 / (jd * jd - 1.0);
-        acc = {fma(wj, x.re, acc.re), fma(wj, x.im, acc.im)};
+    double iA[U], iB[U], cA[U], cB[U];
+    auto load_bwd = [&](int t0, cpx<double>* yv, double* iu, double* cu) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        int t = t0 - u;
+        if (t >= 0) {
+          yv[u] = Wc[t * stride];
+          iu[u] = __ldg(IUc + t * stride);
+          cu[u] = __ldg(CUc + t * stride);
+        }
       }
+    };
+    auto run_bwd = [&](int t0, const cpx<double>* yv, const double* iu, const double* cu) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        int t = t0 - u;
+        if (t >= 0) {
+          x = {fma(yv[u].re, iu[u], -cu[u] * x.re), fma(yv[u].im, iu[u], -cu[u] * x.im)};
+          Wc[t * stride] = x;
+          if (zonal) {
+            double jd = (double)(j0 + 2 * t);
+            double wj = 2.0 / (jd * jd - 1.0);
+            acc = {fma(wj, x.re, acc.re), fma(wj, x.im, acc.im)};
+          }
+        }
+      }
+    };
+    load_bwd(M - 1, dA, iA, cA);
+    for (int t0 = M - 1; t0 >= 0; t0 -= 2 * U) {
+      load_bwd(t0 - U, dB, iB, cB);
+      run_bwd(t0, dA, iA, cA);
+      load_bwd(t0 - 2 * U, dA, iA, cA);
+      run_bwd(t0 - U, dB, iB, cB);
     }
     if (even) {
-      // x now holds X_2
-      cpx<double>& x0 = W[k];
-      if (k == 0) {
-        x0 = acc;
-      } else if (k & 1) {
-        x0 = {0.0, 0.0};
-      } else {
-        double ik2 = 1.0 / ((double)k * (double)k);
-        x0 = {(x.re - x0.re) * ik2, (x.im - x0.im) * ik2};
-      }
+      // x holds X_2: row 0 closure (k even != 0), w^T X_0 = 0 (k = 0), X_0 = 0 (k odd)
+      cpx<double> f0 = W[k];
+      if (k == 0) W[k] = acc;
+      else if (k & 1) W[k] = {0.0, 0.0};
+      else W[k] = {(x.re - f0.re) * ik2, (x.im - f0.im) * ik2};
     }
   } else {
     cpx<double> xb0 = {0.0, 0.0};
     if (even) {
       xb0 = W[k];
-      W[k] = (k == 0 || (k & 1)) ? cpx<double>{0.0, 0.0}
-                                 : (-1.0 / ((double)k * (double)k)) * xb0;
+      W[k] = (k == 0 || (k & 1)) ? cpx<double>{0.0, 0.0} : (-ik2) * xb0;
     }
+    const bool bump2 = even && k != 0 && !(k & 1);   // Xbar_2 += Xbar_0 / k^2
     // forward sweep with U^T: z_t = (b_t - c_{t-1} z_{t-1}) / u_t
     cpx<double> z = {0.0, 0.0};
-    for (int j = j0; j <= jlast; j += 2) {
-      const size_t o = (size_t)j * Kp + k;
-      cpx<double> bv = W[o];
-      if (even) {
-        if (k == 0) {
-          double jd = (double)j;
-          double wj = 2.0 / (jd * jd - 1.0);
-          bv = {fma(wj, xb0.re, bv.re), fma(wj, xb0.im, bv.im)};
-        } else if (j == 2 && !(k & 1)) {
-          double ik2 = 1.0 / ((double)k * (double)k);
-          bv = {fma(ik2, xb0.re, bv.re), fma(ik2, xb0.im, bv.im)};
+    cpx<double> bA[U], bB[U];
+    double iA[U], iB[U];
+    auto load_f = [&](int t0, cpx<double>* b, double* iu) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        int t = t0 + u;
+        if (t < M) {
+          b[u] = Wc[t * stride];
+          iu[u] = __ldg(IUc + t * stride);
         }
       }
-      double iu = __ldg(fiu + o);
-      double cprev = (double)((j - 1) * j) * 0.25;    // c_{j-2} = (j-1) j / 4
-      if (j == j0) cprev = 0.0;
-      z = {(bv.re - cprev * z.re) * iu, (bv.im - cprev * z.im) * iu};
-      W[o] = z;
+    };
+    auto run_f = [&](int t0, const cpx<double>* b, const double* iu) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        int t = t0 + u;
+        if (t < M) {
+          cpx<double> bv = b[u];
+          int j = j0 + 2 * t;
+          if (zonal) {
+            double jd = (double)j;
+            double wj = 2.0 / (jd * jd - 1.0);
+            bv = {fma(wj, xb0.re, bv.re), fma(wj, xb0.im, bv.im)};
+          } else if (bump2 && t == 0) {
+            bv = {fma(ik2, xb0.re, bv.re), fma(ik2, xb0.im, bv.im)};
+          }
+          double cprev = t ? (double)((j - 1) * j) * 0.25 : 0.0;   // c_{j-2} = (j-1) j / 4
+          z = {(bv.re - cprev * z.re) * iu[u], (bv.im - cprev * z.im) * iu[u]};
+          Wc[t * stride] = z;
+        }
+      }
+    };
+    load_f(0, bA, iA);
+    for (int t0 = 0; t0 < M; t0 += 2 * U) {
+      load_f(t0 + U, bB, iB);
+      run_f(t0, bA, iA);
+      load_f(t0 + 2 * U, bA, iA);
+      run_f(t0 + U, bB, iB);
     }
     // backward sweep with L^T: y_t = z_t - l_{t+1} y_{t+1}
     cpx<double> y = {0.0, 0.0};
     double lnext = 0.0;
-    for (int j = jlast; j >= j0; j -= 2) {
-      const size_t o = (size_t)j * Kp + k;
-      cpx<double> zv = W[o];
-      y = {fma(-lnext, y.re, zv.re), fma(-lnext, y.im, zv.im)};
-      W[o] = y;
-      lnext = __ldg(fl + o);
+    double lA2[U], lB2[U];
+    auto load_b = [&](int t0, cpx<double>* zv, double* l) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        int t = t0 - u;
+        if (t >= 0) {
+          zv[u] = Wc[t * stride];
+          l[u] = __ldg(Lc + t * stride);
+        }
+      }
+    };
+    auto run_b = [&](int t0, const cpx<double>* zv, const double* l) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        int t = t0 - u;
+        if (t >= 0) {
+          y = {fma(-lnext, y.re, zv[u].re), fma(-lnext, y.im, zv[u].im)};
+          Wc[t * stride] = y;
+          lnext = l[u];
+        }
+      }
+    };
+    load_b(M - 1, bA, lA2);
+    for (int t0 = M - 1; t0 >= 0; t0 -= 2 * U) {
+      load_b(t0 - U, bB, lB2);
+      run_b(t0, bA, lA2);
+      load_b(t0 - 2 * U, bA, lA2);
+      run_b(t0 - U, bB, lB2);
     }
   }
 }

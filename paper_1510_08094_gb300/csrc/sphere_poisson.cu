@@ -179,7 +179,7 @@ void enqueue_solve(sp_plan_t p, const double* in, double* out, cpx<double>* W, c
   StageMarks m{p, st, !p->prof_events.empty() && p->prof_count < p->prof_max};
   const int row_blocks = (p->nt + p->rows_per_cta - 1) / p->rows_per_cta;
   const int col_blocks = (p->K + p->cols_per_cta - 1) / p->cols_per_cta;
-  const int solve_threads = 128;
+  const int solve_threads = 32;
   const int solve_blocks = (2 * p->K + solve_threads - 1) / solve_threads;
   m.mark(0);
   sp::k_rows_forward<double, ADJ, BR><<<row_blocks, p->row_threads, p->row_smem, st>>>(
