@@ -51,6 +51,7 @@ extern "C" {
 #define SP_ERR_UNSUPPORTED  -6   /* precision / flag combination not built */
 #define SP_ERR_BAD_PLAN     -7   /* NULL or destroyed plan handle */
 #define SP_ERR_BAD_ARG      -8   /* other invalid argument */
+#define SP_ERR_SCRATCH_LIMIT -9  /* grid too large for the fixed scratch of sphere_poisson_solve_noalloc */
 
 /* precision of the arithmetic inside the solve (inputs and outputs are always double) */
 #define SP_FP64         0   /* IEEE double throughout */
@@ -107,6 +108,36 @@ int sphere_poisson_solve_adjoint(sp_plan_t plan, const double* ubar, double* fba
 int sphere_poisson_host_buffer_size(sp_plan_t plan, size_t* device_buffer_bytes);
 int sphere_poisson_solve_host(sp_plan_t plan, const double* f_host, double* u_host,
                               void* device_buffer, size_t device_buffer_bytes, void* stream);
+
+/*
+ * Allocation-free solve.  The paper has no counterpart; this is a service for
+ * callers that cannot obtain device memory at the moment they need a solve:
+ * code running where a cudaMalloc is not allowed or would stall the device
+ * (a real-time loop, a host callback, a section holding a driver-level lock),
+ * programs whose device memory belongs to a framework allocator that forbids
+ * raw allocations, or plug-ins that are handed only the input and output
+ * buffers by their host application.  It computes exactly what
+ * sphere_poisson_solve computes but takes no workspace and allocates nothing:
+ * its scratch is one fixed device array inside the library of
+ * SP_NOALLOC_SCRATCH_BYTES (32 MiB), which every GPU that loads the library
+ * holds until the process exits.
+ *   plan    an existing plan (creating the plan allocates its tables; do it at
+ *           start-up).  Its workspace size must not exceed SP_NOALLOC_SCRATCH_BYTES
+ *           (n_theta * Kp * 16 bytes, Kp = n_lambda/2 + 1 rounded up to even,
+ *           e.g. 1024 x 2048 fits, 2048 x 4096 does not); larger plans get
+ *           SP_ERR_SCRATCH_LIMIT and nothing runs.
+ *   f, u    device arrays as for sphere_poisson_solve.
+ *   stream  cudaStream_t (as void*) or NULL.
+ * The current device must be the plan's device (else SP_ERR_BAD_ARG).  The first
+ * call on each device looks up the device address of the scratch array
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call uses the same scratch array: calls that can overlap on the GPU
+ * (different streams, or from several threads) race and corrupt each other's
+ * results, so serialise them.  The scratch needs no clearing: the first kernel
+ * of a solve overwrites the whole region before any kernel reads it.
+ */
+#define SP_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+int sphere_poisson_solve_noalloc(sp_plan_t plan, const double* f, double* u, void* stream);
 
 /* Number of kernel launches one solve (adjoint = 1) issues for this plan. */
 int sphere_poisson_launch_count(sp_plan_t plan, int adjoint, int* launches);

@@ -117,6 +117,18 @@ class Plan:
                    "sphere_poisson_solve_adjoint")
         return out
 
+    def solve_noalloc(self, f: torch.Tensor, out: torch.Tensor, stream=None):
+        """Allocation-free solve for callers that cannot allocate device memory when
+        they solve: no workspace, the library's fixed 32 MiB scratch array is used
+        instead (grids up to that size).  Calls that overlap on the GPU race on
+        that shared array; `out` must be given because this call allocates nothing."""
+        _check_grid(f, self.shape, "f")
+        _check_grid(out, self.shape, "out")
+        _lib.check(self._lib.sphere_poisson_solve_noalloc(self._h, f.data_ptr(), out.data_ptr(),
+                                                          _stream_ptr(stream)),
+                   "sphere_poisson_solve_noalloc")
+        return out
+
     def host_buffer_bytes(self) -> int:
         n = ctypes.c_size_t()
         _lib.check(self._lib.sphere_poisson_host_buffer_size(self._h, ctypes.byref(n)),

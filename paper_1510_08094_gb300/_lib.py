@@ -22,6 +22,8 @@ SP_ERR_CUDA = -5
 SP_ERR_UNSUPPORTED = -6
 SP_ERR_BAD_PLAN = -7
 SP_ERR_BAD_ARG = -8
+SP_ERR_SCRATCH_LIMIT = -9
+SP_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 SP_FP64 = 0
 SP_FP32 = 1
@@ -34,6 +36,7 @@ EXPORTED = (
     "sphere_poisson_solve_adjoint",
     "sphere_poisson_host_buffer_size",
     "sphere_poisson_solve_host",
+    "sphere_poisson_solve_noalloc",
     "sphere_poisson_launch_count",
     "sphere_poisson_profile_begin",
     "sphere_poisson_profile_end",
@@ -73,6 +76,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.sphere_poisson_solve_adjoint.argtypes = [vp, vp, vp, vp, sz, vp]
     lib.sphere_poisson_host_buffer_size.argtypes = [vp, psz]
     lib.sphere_poisson_solve_host.argtypes = [vp, vp, vp, vp, sz, vp]
+    lib.sphere_poisson_solve_noalloc.argtypes = [vp, vp, vp, vp]
     lib.sphere_poisson_launch_count.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int)]
     lib.sphere_poisson_profile_begin.argtypes = [vp, i32]
     lib.sphere_poisson_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32,

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <mutex>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -414,6 +415,53 @@ int sphere_poisson_solve_host(sp_plan_t plan, const double* f_host, double* u_ho
   return SP_OK;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free solve: the workspace is this fixed device array.  Host code
+// must not pass the symbol itself to a kernel (on the host it names a host-side
+// stand-in); the device address is looked up once per device below.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SP_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// device address of g_noalloc_scratch on the current device (set up on first use)
+int noalloc_scratch(int device, void** ptr) {
+  if (device < 0 || device >= kMaxDevices) return SP_ERR_BAD_ARG;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
+    if (!p) return SP_ERR_CUDA;
+    g_noalloc_ptr[device] = p;
+  }
+  *ptr = g_noalloc_ptr[device];
+  return SP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int sphere_poisson_solve_noalloc(sp_plan_t plan, const double* f, double* u, void* stream) {
+  if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
+  if (!f || !u) return SP_ERR_NULL;
+  if (((uintptr_t)f | (uintptr_t)u) & 15) return SP_ERR_MISALIGNED;
+  if (plan->ws_bytes > SP_NOALLOC_SCRATCH_BYTES) return SP_ERR_SCRATCH_LIMIT;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != plan->device) return SP_ERR_BAD_ARG;
+  void* scratch = nullptr;
+  int rc = noalloc_scratch(dev, &scratch);
+  if (rc != SP_OK) return rc;
+  return launch_solve<false>(plan, f, u, scratch, static_cast<cudaStream_t>(stream));
+}
+
 int sphere_poisson_launch_count(sp_plan_t plan, int adjoint, int* launches) {
   if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
   if (!launches) return SP_ERR_NULL;
@@ -496,6 +544,8 @@ const char* sphere_poisson_status_string(int status) {
     case SP_ERR_UNSUPPORTED: return "precision or flag combination not supported";
     case SP_ERR_BAD_PLAN: return "NULL or destroyed plan handle";
     case SP_ERR_BAD_ARG: return "invalid argument";
+    case SP_ERR_SCRATCH_LIMIT: return "grid too large for the 32 MiB fixed scratch of sphere_poisson_solve_noalloc; "
+                                      "use sphere_poisson_solve with a workspace";
     default: return "unknown status";
   }
 }
