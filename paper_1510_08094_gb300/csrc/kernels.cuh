@@ -171,8 +171,17 @@ __global__ void __launch_bounds__(512) k_theta_forward(
       cpx<T> w = ldg_c(post + j);
       cpx<T> a = V[j], b = V[j == 0 ? 0 : N - j];
       cpx<T> p = (T)0.5 * (cmul(w, a) + cmulc(b, w));
-      if (ADJ) out = (j == 0 ? (T)1 : (T)2) * p;
-      else out = invN * p;
+      if (ADJ) {
+        out = (j == 0 ? (T)1 : (T)2) * p;
+        // transpose of the k = 0 closure X_0 = sum_{j even >= 2} 2 X_j/(j^2-1):
+        // Xbar_j += 2 Xbar_0/(j^2-1), with Xbar_0 = P_0 = V_0
+        if (k == 0 && j >= 2 && !(j & 1)) {
+          T wj = (T)2 / ((T)j * (T)j - (T)1);
+          out = out + wj * V[0];
+        }
+      } else {
+        out = invN * p;
+      }
     } else if (j == 0) {
       out = {(T)0, (T)0};
     } else {
@@ -204,6 +213,27 @@ __global__ void __launch_bounds__(512) k_theta_inverse(
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
   const int k0 = blockIdx.x * cols;
+  if (!ADJ && k0 == 0) {
+    // k = 0 closure of the solve: w^T X_0 = 0 gives X_00 = sum_{j even >= 2} 2 X_j0/(j^2-1)
+    cpx<T> acc = {(T)0, (T)0};
+    for (int j = 2 + 2 * threadIdx.x; j < N; j += 2 * blockDim.x) {
+      T wj = (T)2 / ((T)j * (T)j - (T)1);
+      acc = acc + wj * W[(size_t)j * Kp];
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      acc.re = acc.re + __shfl_down_sync(0xffffffffu, acc.re, off);
+      acc.im = acc.im + __shfl_down_sync(0xffffffffu, acc.im, off);
+    }
+    __shared__ cpx<T> red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      cpx<T> tot = {(T)0, (T)0};
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot = tot + red[w];
+      W[0] = tot;
+    }
+    __syncthreads();
+  }
   // pre-twiddle straight from global memory, one thread per pair (j, N - j),
   // j = 0 .. N/2, writing V_j and V_{N-j} to their digit-reversed slots
   const int H = N / 2 + 1;
@@ -297,25 +327,50 @@ __global__ void k_factor(double* __restrict__ fl, double* __restrict__ fiu, doub
 // ---------------------------------------------------------------------------
 // solve (ADJ = false): X = M_k^{-1} F per column, in place.
 //   chains: y_t = d_t - l_t y_{t-1}; x_t = y_t/u_t - (c_t/u_t) x_{t+1}
-//   closure (even-chain thread): k = 0: X_0 = sum_{j even >= 2} 2 X_j/(j^2-1)
-//   (w^T X_0 = 0 with X_{-j,0} = X_{j,0}); k even != 0: X_0 = (X_2 - F_0)/k^2
-//   (row 0 with X_{-2,k} = X_{2,k}); k odd: X_0 = 0.
+//   closure (even-chain thread): k even != 0: X_0 = (X_2 - F_0)/k^2 (row 0 with
+//   X_{-2,k} = X_{2,k}); k odd: X_0 = 0.  For k = 0, w^T X_0 = 0 with
+//   X_{-j,0} = X_{j,0} gives X_0 = sum_{j even >= 2} 2 X_j/(j^2-1), summed by
+//   the first CTA of theta_inverse.
 // solve (ADJ = true): the transpose, F = M_k^{-T} X:
 //   k even != 0: Fbar_0 = -Xbar_0/k^2 and Xbar_2 += Xbar_0/k^2; k = 0:
-//   Xbar_j += 2 Xbar_0/(j^2-1) for even j, Fbar_0 = 0; k odd: Fbar_0 = 0;
+//   Xbar_j += 2 Xbar_0/(j^2-1) for even j (added by theta_forward's adjoint),
+//   Fbar_0 = 0; k odd: Fbar_0 = 0;
 //   then T^T = U^T L^T: z_t = (b_t - c_{t-1} z_{t-1})/u_t, y_t = z_t - l_{t+1} y_{t+1}.
 // ---------------------------------------------------------------------------
-constexpr int kSolveBatch = 8;  // rows per register batch; two batches in flight
+// cp.async helpers (per-thread asynchronous global -> shared copies)
+__device__ __forceinline__ void cp_async16(void* smem, const void* g) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* g) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// One warp = 32 chains (consecutive k, one parity).  Each lane streams its own
+// chain's rows through a ring of kRing shared-memory slots filled by its own
+// cp.async copies, kRing rows ahead of the elimination, so every lane keeps
+// kRing rows of loads in flight without any cross-lane synchronisation.
+constexpr int kRing = 32;
+struct RingSlot {
+  cpx<double> d[32];
+  double a[32];
+  double b[32];
+};
 
 template <bool ADJ>
-__global__ void __launch_bounds__(64) k_solve(cpx<double>* __restrict__ W, const double* __restrict__ fl,
+__global__ void __launch_bounds__(32) k_solve(cpx<double>* __restrict__ W, const double* __restrict__ fl,
                                               const double* __restrict__ fiu, const double* __restrict__ fcu,
                                               int N, int K, int Kp) {
-  constexpr int U = kSolveBatch;
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= 2 * K) return;
-  const bool even = idx >= K;
-  const int k = even ? idx - K : idx;
+  __shared__ RingSlot ring[kRing];
+  const int lane = threadIdx.x;
+  const bool even = blockIdx.y == 1;
+  const int k = blockIdx.x * 32 + lane;
+  if (k >= K) return;
   const int j0 = even ? 2 : 1;
   const double ik2 = k ? 1.0 / ((double)k * (double)k) : 0.0;
   if (j0 >= N) {
@@ -333,83 +388,62 @@ __global__ void __launch_bounds__(64) k_solve(cpx<double>* __restrict__ W, const
   const double* Lc = fl + (size_t)j0 * Kp + k;
   const double* IUc = fiu + (size_t)j0 * Kp + k;
   const double* CUc = fcu + (size_t)j0 * Kp + k;
-  const bool zonal = even && k == 0;
+
+  // ascending sweep issue: row t -> slot t % kRing (data + one table)
+  auto issue_up = [&](int t, const double* tab) {
+    if (t < M) {
+      RingSlot& sl = ring[t & (kRing - 1)];
+      cp_async16(&sl.d[lane], Wc + t * stride);
+      cp_async8(&sl.a[lane], tab + t * stride);
+    }
+    cp_commit();
+  };
+  // descending sweep issue: r-th row from the end -> slot r % kRing (data + two tables)
+  auto issue_down = [&](int r, const double* ta, const double* tb) {
+    int t = M - 1 - r;
+    if (t >= 0) {
+      RingSlot& sl = ring[r & (kRing - 1)];
+      cp_async16(&sl.d[lane], Wc + t * stride);
+      cp_async8(&sl.a[lane], ta + t * stride);
+      if (tb) cp_async8(&sl.b[lane], tb + t * stride);
+    }
+    cp_commit();
+  };
 
   if (!ADJ) {
-    // forward sweep y_t = d_t - l_t y_{t-1}, rows in batches of U with the next
-    // batch's loads issued before the current batch is consumed
+    // forward sweep y_t = d_t - l_t y_{t-1}
+    for (int t = 0; t < kRing; ++t) issue_up(t, Lc);
     cpx<double> y = {0.0, 0.0};
-    cpx<double> dA[U], dB[U];
-    double lA[U], lB[U];
-    auto load_fwd = [&](int t0, cpx<double>* d, double* l) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        int t = t0 + u;
-        if (t < M) {
-          d[u] = Wc[t * stride];
-          l[u] = __ldg(Lc + t * stride);
-        }
-      }
-    };
-    auto run_fwd = [&](int t0, const cpx<double>* d, const double* l) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        int t = t0 + u;
-        if (t < M) {
-          y = {fma(-l[u], y.re, d[u].re), fma(-l[u], y.im, d[u].im)};
-          Wc[t * stride] = y;
-        }
-      }
-    };
-    load_fwd(0, dA, lA);
-    for (int t0 = 0; t0 < M; t0 += 2 * U) {
-      load_fwd(t0 + U, dB, lB);
-      run_fwd(t0, dA, lA);
-      load_fwd(t0 + 2 * U, dA, lA);
-      run_fwd(t0 + U, dB, lB);
+    for (int t = 0; t < M; ++t) {
+      cp_wait<kRing - 1>();
+      const RingSlot& sl = ring[t & (kRing - 1)];
+      cpx<double> d = sl.d[lane];
+      double l = sl.a[lane];
+      y = {fma(-l, y.re, d.re), fma(-l, y.im, d.im)};
+      Wc[t * stride] = y;
+      issue_up(t + kRing, Lc);
     }
+    cp_wait_all();
+    __threadfence();  // the descending copies read rows this thread just stored
     // backward sweep x_t = y_t / u_t - (c_t / u_t) x_{t+1}
+    for (int r = 0; r < kRing; ++r) issue_down(r, IUc, CUc);
     cpx<double> x = {0.0, 0.0};
-    cpx<double> acc = {0.0, 0.0};
-    double iA[U], iB[U], cA[U], cB[U];
-    auto load_bwd = [&](int t0, cpx<double>* yv, double* iu, double* cu) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        int t = t0 - u;
-        if (t >= 0) {
-          yv[u] = Wc[t * stride];
-          iu[u] = __ldg(IUc + t * stride);
-          cu[u] = __ldg(CUc + t * stride);
-        }
-      }
-    };
-    auto run_bwd = [&](int t0, const cpx<double>* yv, const double* iu, const double* cu) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        int t = t0 - u;
-        if (t >= 0) {
-          x = {fma(yv[u].re, iu[u], -cu[u] * x.re), fma(yv[u].im, iu[u], -cu[u] * x.im)};
-          Wc[t * stride] = x;
-          if (zonal) {
-            double jd = (double)(j0 + 2 * t);
-            double wj = 2.0 / (jd * jd - 1.0);
-            acc = {fma(wj, x.re, acc.re), fma(wj, x.im, acc.im)};
-          }
-        }
-      }
-    };
-    load_bwd(M - 1, dA, iA, cA);
-    for (int t0 = M - 1; t0 >= 0; t0 -= 2 * U) {
-      load_bwd(t0 - U, dB, iB, cB);
-      run_bwd(t0, dA, iA, cA);
-      load_bwd(t0 - 2 * U, dA, iA, cA);
-      run_bwd(t0 - U, dB, iB, cB);
+    for (int r = 0; r < M; ++r) {
+      cp_wait<kRing - 1>();
+      const RingSlot& sl = ring[r & (kRing - 1)];
+      cpx<double> yv = sl.d[lane];
+      double iu = sl.a[lane], cu = sl.b[lane];
+      const int t = M - 1 - r;
+      x = {fma(yv.re, iu, -cu * x.re), fma(yv.im, iu, -cu * x.im)};
+      Wc[t * stride] = x;
+      issue_down(r + kRing, IUc, CUc);
     }
-    if (even) {
-      // x holds X_2: row 0 closure (k even != 0), w^T X_0 = 0 (k = 0), X_0 = 0 (k odd)
+    cp_wait_all();
+    if (even && k != 0) {
+      // x holds X_2: row 0 closure X_0 = (X_2 - F_0)/k^2 (k even), X_0 = 0 (k odd).
+      // The k = 0 closure (w^T X_0 = 0) is summed by theta_inverse's first CTA.
       cpx<double> f0 = W[k];
-      if (k == 0) W[k] = acc;
-      else if (k & 1) W[k] = {0.0, 0.0};
+      if (k & 1) W[k] = {0.0, 0.0};
       else W[k] = {(x.re - f0.re) * ik2, (x.im - f0.im) * ik2};
     }
   } else {
@@ -420,78 +454,41 @@ __global__ void __launch_bounds__(64) k_solve(cpx<double>* __restrict__ W, const
     }
     const bool bump2 = even && k != 0 && !(k & 1);   // Xbar_2 += Xbar_0 / k^2
     // forward sweep with U^T: z_t = (b_t - c_{t-1} z_{t-1}) / u_t
+    for (int t = 0; t < kRing; ++t) issue_up(t, IUc);
     cpx<double> z = {0.0, 0.0};
-    cpx<double> bA[U], bB[U];
-    double iA[U], iB[U];
-    auto load_f = [&](int t0, cpx<double>* b, double* iu) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        int t = t0 + u;
-        if (t < M) {
-          b[u] = Wc[t * stride];
-          iu[u] = __ldg(IUc + t * stride);
-        }
+    for (int t = 0; t < M; ++t) {
+      cp_wait<kRing - 1>();
+      const RingSlot& sl = ring[t & (kRing - 1)];
+      cpx<double> bv = sl.d[lane];
+      double iu = sl.a[lane];
+      const int j = j0 + 2 * t;
+      // (k = 0: the terms 2 Xbar_0/(j^2-1) were added by theta_forward's adjoint)
+      if (bump2 && t == 0) {
+        bv = {fma(ik2, xb0.re, bv.re), fma(ik2, xb0.im, bv.im)};
       }
-    };
-    auto run_f = [&](int t0, const cpx<double>* b, const double* iu) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        int t = t0 + u;
-        if (t < M) {
-          cpx<double> bv = b[u];
-          int j = j0 + 2 * t;
-          if (zonal) {
-            double jd = (double)j;
-            double wj = 2.0 / (jd * jd - 1.0);
-            bv = {fma(wj, xb0.re, bv.re), fma(wj, xb0.im, bv.im)};
-          } else if (bump2 && t == 0) {
-            bv = {fma(ik2, xb0.re, bv.re), fma(ik2, xb0.im, bv.im)};
-          }
-          double cprev = t ? (double)((j - 1) * j) * 0.25 : 0.0;   // c_{j-2} = (j-1) j / 4
-          z = {(bv.re - cprev * z.re) * iu[u], (bv.im - cprev * z.im) * iu[u]};
-          Wc[t * stride] = z;
-        }
-      }
-    };
-    load_f(0, bA, iA);
-    for (int t0 = 0; t0 < M; t0 += 2 * U) {
-      load_f(t0 + U, bB, iB);
-      run_f(t0, bA, iA);
-      load_f(t0 + 2 * U, bA, iA);
-      run_f(t0 + U, bB, iB);
+      double cprev = t ? (double)((j - 1) * j) * 0.25 : 0.0;   // c_{j-2} = (j-1) j / 4
+      z = {(bv.re - cprev * z.re) * iu, (bv.im - cprev * z.im) * iu};
+      Wc[t * stride] = z;
+      issue_up(t + kRing, IUc);
     }
+    cp_wait_all();
+    __threadfence();
     // backward sweep with L^T: y_t = z_t - l_{t+1} y_{t+1}
+    for (int r = 0; r < kRing; ++r) issue_down(r, Lc, nullptr);
     cpx<double> y = {0.0, 0.0};
     double lnext = 0.0;
-    double lA2[U], lB2[U];
-    auto load_b = [&](int t0, cpx<double>* zv, double* l) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        int t = t0 - u;
-        if (t >= 0) {
-          zv[u] = Wc[t * stride];
-          l[u] = __ldg(Lc + t * stride);
-        }
-      }
-    };
-    auto run_b = [&](int t0, const cpx<double>* zv, const double* l) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        int t = t0 - u;
-        if (t >= 0) {
-          y = {fma(-lnext, y.re, zv[u].re), fma(-lnext, y.im, zv[u].im)};
-          Wc[t * stride] = y;
-          lnext = l[u];
-        }
-      }
-    };
-    load_b(M - 1, bA, lA2);
-    for (int t0 = M - 1; t0 >= 0; t0 -= 2 * U) {
-      load_b(t0 - U, bB, lB2);
-      run_b(t0, bA, lA2);
-      load_b(t0 - 2 * U, bA, lA2);
-      run_b(t0 - U, bB, lB2);
+    for (int r = 0; r < M; ++r) {
+      cp_wait<kRing - 1>();
+      const RingSlot& sl = ring[r & (kRing - 1)];
+      cpx<double> zv = sl.d[lane];
+      double l = sl.a[lane];
+      const int t = M - 1 - r;
+      y = {fma(-lnext, y.re, zv.re), fma(-lnext, y.im, zv.im)};
+      Wc[t * stride] = y;
+      lnext = l;
+      issue_down(r + kRing, Lc, nullptr);
     }
+    cp_wait_all();
   }
 }
 

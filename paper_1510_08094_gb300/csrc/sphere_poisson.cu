@@ -180,8 +180,7 @@ void enqueue_solve(sp_plan_t p, const double* in, double* out, cpx<double>* W, c
   StageMarks m{p, st, !p->prof_events.empty() && p->prof_count < p->prof_max};
   const int row_blocks = (p->nt + p->rows_per_cta - 1) / p->rows_per_cta;
   const int col_blocks = (p->K + p->cols_per_cta - 1) / p->cols_per_cta;
-  const int solve_threads = 32;
-  const int solve_blocks = (2 * p->K + solve_threads - 1) / solve_threads;
+  const dim3 solve_grid((p->K + 31) / 32, 2);
   m.mark(0);
   sp::k_rows_forward<double, ADJ, BR><<<row_blocks, p->row_threads, p->row_smem, st>>>(
       in, W, p->nt, p->nl, p->Kp, p->rows_per_cta, p->row_fft, p->tw_row, p->perm_row, p->post_row,
@@ -190,7 +189,7 @@ void enqueue_solve(sp_plan_t p, const double* in, double* out, cpx<double>* W, c
   sp::k_theta_forward<double, ADJ, BC><<<col_blocks, p->col_threads, p->col_smem, st>>>(
       W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft, p->tw_col, p->perm_col, p->post_col);
   m.mark(2);
-  sp::k_solve<ADJ><<<solve_blocks, solve_threads, 0, st>>>(W, p->fac_l, p->fac_iu, p->fac_cu, p->N, p->K,
+  sp::k_solve<ADJ><<<solve_grid, 32, 0, st>>>(W, p->fac_l, p->fac_iu, p->fac_cu, p->N, p->K,
                                                             p->Kp);
   m.mark(3);
   sp::k_theta_inverse<double, ADJ, BC><<<col_blocks, p->col_threads, p->col_smem, st>>>(
