@@ -6,6 +6,7 @@ The library is rebuilt when any source under csrc/ or include/ is newer than it.
 
 from __future__ import annotations
 
+import concurrent.futures
 import os
 import shutil
 import subprocess
@@ -18,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB_NAME = "libsphere_poisson.so"
 LIB_PATH = os.path.join(BUILD, LIB_NAME)
-SOURCES = ["sphere_poisson.cu", "pipe_probe.cu"]
+SOURCES = ["sphere_poisson.cu", "pipe_probe.cu", "k_f64.cu", "k_f32.cu", "k_dd.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -42,22 +43,36 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile the library if needed and return its path."""
-    if not force and up_to_date():
-        return LIB_PATH
-    os.makedirs(BUILD, exist_ok=True)
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = [_nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-I", INCLUDE, "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
+def _run(cmd, verbose):
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
         print(" ".join(cmd), file=sys.stderr)
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
-        raise RuntimeError(f"nvcc failed ({res.returncode}):\n{res.stdout}\n{res.stderr}")
-    if verbose:
+        raise RuntimeError(f"nvcc failed ({res.returncode}): {' '.join(cmd)}\n{res.stdout}\n{res.stderr}")
+    if verbose and res.stderr:
         print(res.stderr, file=sys.stderr)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the library if needed and return its path.  The translation
+    units compile in parallel, then link into one shared library."""
+    if not force and up_to_date():
+        return LIB_PATH
+    os.makedirs(BUILD, exist_ok=True)
+    nvcc = _nvcc()
+    flags = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+    if verbose:
+        flags.append("-Xptxas=-v")
+    tag = f"{os.getpid()}"
+    objs = [os.path.join(BUILD, os.path.splitext(s)[0] + f".{tag}.o") for s in SOURCES]
+    jobs = [[nvcc] + flags + ["-c", os.path.join(CSRC, s), "-o", o] for s, o in zip(SOURCES, objs)]
+    with concurrent.futures.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        for fut in [ex.submit(_run, j, verbose) for j in jobs]:
+            fut.result()
+    tmp = LIB_PATH + f".tmp{tag}"
+    _run([nvcc, ARCH, "-shared", "-o", tmp] + objs, verbose)
+    for o in objs:
+        os.remove(o)
     os.replace(tmp, LIB_PATH)
     return LIB_PATH
 

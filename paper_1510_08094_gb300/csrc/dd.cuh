@@ -17,14 +17,16 @@
 
 namespace sp {
 
+using ::fma;  // keep the float / double overloads visible next to the double-float one
+
 struct alignas(8) dd {
   float hi, lo;
   dd() = default;
   __host__ __device__ constexpr dd(float h, float l) : hi(h), lo(l) {}
   // split of a double constant (exact to ~2^-48 relative)
-  __host__ __device__ constexpr dd(double x)
+  __host__ __device__ constexpr explicit dd(double x)
       : hi(static_cast<float>(x)), lo(static_cast<float>(x - static_cast<double>(static_cast<float>(x)))) {}
-  __host__ __device__ constexpr dd(int x) : dd(static_cast<double>(x)) {}
+  __host__ __device__ constexpr explicit dd(int x) : dd(static_cast<double>(x)) {}
 };
 
 __device__ __forceinline__ dd dd_add(dd a, dd b) {

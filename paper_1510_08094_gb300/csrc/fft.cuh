@@ -9,6 +9,8 @@
 
 #include <cuda_runtime.h>
 
+#include "dd.cuh"
+
 namespace sp {
 
 template <typename T>
@@ -47,6 +49,25 @@ __device__ __forceinline__ cpx<float> ldg_c(const cpx<float>* p) {
   float2 v = __ldg(reinterpret_cast<const float2*>(p));
   return {v.x, v.y};
 }
+__device__ __forceinline__ cpx<dd> ldg_c(const cpx<dd>* p) {
+  float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return {dd(v.x, v.y), dd(v.z, v.w)};
+}
+
+// conversions between the arithmetic type of a transform and double
+template <typename T> struct num;
+template <> struct num<double> {
+  static __device__ __forceinline__ double from_double(double x) { return x; }
+  static __device__ __forceinline__ double to_double(double x) { return x; }
+};
+template <> struct num<float> {
+  static __device__ __forceinline__ float from_double(double x) { return __double2float_rn(x); }
+  static __device__ __forceinline__ double to_double(float x) { return (double)x; }
+};
+template <> struct num<dd> {
+  static __device__ __forceinline__ dd from_double(double x) { return dd_from_double(x); }
+  static __device__ __forceinline__ double to_double(dd x) { return dd_to_double(x); }
+};
 
 constexpr int kMaxStages = 16;
 
@@ -186,7 +207,7 @@ __device__ __forceinline__ void dft_any(cpx<T>* v, const cpx<T>* __restrict__ tw
   else if constexpr (R == 4) dft4<DIR>(v);
   else if constexpr (R == 5) dft5<DIR>(v);
   else if constexpr (R == 8) dft8<DIR>(v);
-  else dft_odd<R, DIR>(v, tw, tstride);
+  else dft_odd<R, DIR>(v, tw, tstride);  // 7
 }
 
 // ---------------------------------------------------------------------------
@@ -216,9 +237,46 @@ __device__ __forceinline__ void fft_pass(cpx<T>* buf, int L, int nbatch, int Ns,
 #pragma unroll
       for (int r = 1; r < R; ++r) v[r] = twmul<DIR>(v[r], ldg_c(tw + r * k * tstride_stage));
     }
-    dft_any<R, DIR>(v, tw, tstride_R);
+    if constexpr (R <= 8) {
+      dft_any<R, DIR>(v, tw, tstride_R);
 #pragma unroll
-    for (int r = 0; r < R; ++r) base[r * Ns] = v[r];
+      for (int r = 0; r < R; ++r) base[r * Ns] = v[r];
+    } else {
+      // large odd prime: p_b = x_b + x_{R-b}, q_b = x_b - x_{R-b} in registers; each
+      // output pair (a, R-a) is formed in a rolled loop over a and stored at once
+      // (the butterfly's inputs are all in registers, so in-place is safe)
+      constexpr int H = (R - 1) / 2;
+      cpx<T> p[H], q[H];
+      cpx<T> y0 = v[0];
+#pragma unroll
+      for (int bb = 1; bb <= H; ++bb) {
+        p[bb - 1] = v[bb] + v[R - bb];
+        q[bb - 1] = v[bb] - v[R - bb];
+        y0 = y0 + p[bb - 1];
+      }
+      const cpx<T> x0 = v[0];
+      base[0] = y0;
+#pragma unroll 1
+      for (int a = 1; a <= H; ++a) {
+        cpx<T> A = x0, B = {(T)0, (T)0};
+        int ab = 0;
+#pragma unroll
+        for (int bb = 1; bb <= H; ++bb) {
+          ab += a;
+          if (ab >= R) ab -= R;                  // ab = a * bb mod R
+          cpx<T> w = ldg_c(tw + ab * tstride_R);
+          T c = w.re, sn = -w.im;                // w = exp(-2 pi i ab/R) = c - i sn
+          A.re = fma(c, p[bb - 1].re, A.re);
+          A.im = fma(c, p[bb - 1].im, A.im);
+          B.re = fma(sn, q[bb - 1].re, B.re);
+          B.im = fma(sn, q[bb - 1].im, B.im);
+        }
+        // y_a = A + DIR i B, y_{R-a} = A - DIR i B
+        cpx<T> iB = DIR < 0 ? cpx<T>{B.im, -B.re} : cpx<T>{-B.im, B.re};
+        base[a * Ns] = A + iB;
+        base[(R - a) * Ns] = A - iB;
+      }
+    }
   }
   __syncthreads();
 }

@@ -1,0 +1,63 @@
+// Double-float transform kernels and the refinement kernels (the SP_FP32_REFINE form).
+// That form has no adjoint, so only the forward instantiations exist.
+#define SP_REFINE_KERNELS
+#include "launchers.inl"
+
+namespace sp {
+
+template <>
+void launch_rows_forward<dd>(bool adj, bool big, const Launch& l, const double* f, cpx<dd>* W, int nt, int n,
+                             int Kp, int rows, const FftDesc& d, const cpx<dd>* tw, const int* perm,
+                             const cpx<dd>* post, const double* row_scale, cpx<double>* zonal) {
+  (void)adj;
+  SP_PICK_FWD(k_rows_forward, dd, big, f, W, nt, n, Kp, rows, d, tw, perm, post, row_scale, zonal);
+}
+template <>
+void launch_rows_inverse<dd>(bool adj, bool big, const Launch& l, const cpx<dd>* W, double* u, int nt, int n,
+                             int Kp, int rows, const FftDesc& d, const cpx<dd>* tw, const int* perm,
+                             const cpx<dd>* post, const double* row_scale, const cpx<double>* zonal) {
+  (void)adj;
+  SP_PICK_FWD(k_rows_inverse, dd, big, W, u, nt, n, Kp, rows, d, tw, perm, post, row_scale, zonal);
+}
+template <>
+void launch_theta_forward<dd>(bool adj, bool big, const Launch& l, cpx<dd>* W, int N, int K, int Kp, int cols,
+                              const FftDesc& d, const cpx<dd>* tw, const int* perm, const cpx<dd>* post,
+                              dd inv_n, int zonal) {
+  (void)adj;
+  SP_PICK_FWD(k_theta_forward, dd, big, W, N, K, Kp, cols, d, tw, perm, post, inv_n, zonal);
+}
+template <>
+void launch_theta_inverse<dd>(bool adj, bool big, const Launch& l, cpx<dd>* W, int N, int K, int Kp, int cols,
+                              const FftDesc& d, const cpx<dd>* tw, const int* perm, const cpx<dd>* post,
+                              dd inv_n, int zonal) {
+  (void)adj;
+  SP_PICK_FWD(k_theta_inverse, dd, big, W, N, K, Kp, cols, d, tw, perm, post, inv_n, zonal);
+}
+template <>
+cudaError_t allow_transform_smem<dd>(int bytes) {
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaSuccess;
+  auto upd = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  upd(cudaFuncSetAttribute(k_rows_forward<dd, false, false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_rows_forward<dd, false, true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_rows_inverse<dd, false, false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_rows_inverse<dd, false, true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_forward<dd, false, false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_forward<dd, false, true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_inverse<dd, false, false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_inverse<dd, false, true>, a, bytes));
+  return e;
+}
+
+void launch_refine(const Launch& l, const cpx<dd>* F, cpx<dd>* X, cpx<float>* Y, const float* fl,
+                   const float* fiu, const float* fcu, int N, int K, int Kp, int first) {
+  k_refine<<<l.grid, l.threads, l.smem, l.stream>>>(F, X, Y, fl, fiu, fcu, N, K, Kp, first);
+}
+void launch_zonal_extract(const Launch& l, const cpx<dd>* Wdd, cpx<double>* Z, int N, int Kp) {
+  k_zonal_extract<<<l.grid, l.threads, l.smem, l.stream>>>(Wdd, Z, N, Kp);
+}
+void launch_zonal_insert(const Launch& l, const cpx<double>* Z, cpx<dd>* X, int N, int Kp) {
+  k_zonal_insert<<<l.grid, l.threads, l.smem, l.stream>>>(Z, X, N, Kp);
+}
+
+}  // namespace sp

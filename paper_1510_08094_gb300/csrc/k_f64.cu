@@ -1,0 +1,66 @@
+// FP64 transform and elimination kernels (and the FP64 zonal side path of the FP32 forms).
+#include "launchers.inl"
+
+namespace sp {
+
+template <>
+void launch_rows_forward<double>(bool adj, bool big, const Launch& l, const double* f, cpx<double>* W, int nt,
+                                 int n, int Kp, int rows, const FftDesc& d, const cpx<double>* tw,
+                                 const int* perm, const cpx<double>* post, const double* row_scale,
+                                 cpx<double>* zonal) {
+  SP_PICK(k_rows_forward, double, adj, big, f, W, nt, n, Kp, rows, d, tw, perm, post, row_scale, zonal);
+}
+template <>
+void launch_rows_inverse<double>(bool adj, bool big, const Launch& l, const cpx<double>* W, double* u, int nt,
+                                 int n, int Kp, int rows, const FftDesc& d, const cpx<double>* tw,
+                                 const int* perm, const cpx<double>* post, const double* row_scale,
+                                 const cpx<double>* zonal) {
+  SP_PICK(k_rows_inverse, double, adj, big, W, u, nt, n, Kp, rows, d, tw, perm, post, row_scale, zonal);
+}
+template <>
+void launch_theta_forward<double>(bool adj, bool big, const Launch& l, cpx<double>* W, int N, int K, int Kp,
+                                  int cols, const FftDesc& d, const cpx<double>* tw, const int* perm,
+                                  const cpx<double>* post, double inv_n, int zonal) {
+  SP_PICK(k_theta_forward, double, adj, big, W, N, K, Kp, cols, d, tw, perm, post, inv_n, zonal);
+}
+template <>
+void launch_theta_inverse<double>(bool adj, bool big, const Launch& l, cpx<double>* W, int N, int K, int Kp,
+                                  int cols, const FftDesc& d, const cpx<double>* tw, const int* perm,
+                                  const cpx<double>* post, double inv_n, int zonal) {
+  SP_PICK(k_theta_inverse, double, adj, big, W, N, K, Kp, cols, d, tw, perm, post, inv_n, zonal);
+}
+template <>
+cudaError_t allow_transform_smem<double>(int bytes) {
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaSuccess;
+  auto upd = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  upd(cudaFuncSetAttribute(k_rows_forward<double, false, false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_rows_forward<double, false, true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_rows_forward<double, true, false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_rows_forward<double, true, true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_rows_inverse<double, false, false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_rows_inverse<double, false, true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_rows_inverse<double, true, false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_rows_inverse<double, true, true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_forward<double, false, false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_forward<double, false, true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_forward<double, true, false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_forward<double, true, true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_inverse<double, false, false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_inverse<double, false, true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_inverse<double, true, false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_inverse<double, true, true>, a, bytes));
+  return e;
+}
+template <>
+void launch_solve<double>(bool adj, const Launch& l, cpx<double>* W, const double* fl, const double* fiu,
+                          const double* fcu, int N, int K, int Kp) {
+  if (adj) k_solve<true, double><<<l.grid, l.threads, l.smem, l.stream>>>(W, fl, fiu, fcu, N, K, Kp);
+  else k_solve<false, double><<<l.grid, l.threads, l.smem, l.stream>>>(W, fl, fiu, fcu, N, K, Kp);
+}
+template <>
+void launch_factor<double>(const Launch& l, double* fl, double* fiu, double* fcu, int N, int K, int Kp) {
+  k_factor<double><<<l.grid, l.threads, l.smem, l.stream>>>(fl, fiu, fcu, N, K, Kp);
+}
+
+}  // namespace sp

@@ -18,6 +18,8 @@
 // transposed stage is the other transform family with different weights.
 #pragma once
 
+#include <type_traits>
+
 #include "fft.cuh"
 
 namespace sp {
@@ -28,31 +30,90 @@ __device__ __forceinline__ int makhoul_pos(int i, int N) {
   return (i & 1) ? N - 1 - (i >> 1) : (i >> 1);
 }
 
+// Split of a double into two floats hi + lo (|x - hi - lo| <= 2^-48 |x|) with
+// integer operations only: hi keeps the top 24 significand bits (truncated),
+// lo the next 29 bits rounded to 24.  Used where FP64-accurate sums of double
+// inputs are needed without spending the scarce FP64 pipe.  Values outside the
+// float range (and subnormals) give 0 / infinity.
+__device__ __forceinline__ dd split_double(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+  const unsigned sign = h32 & 0x80000000u;
+  const int e = (int)((h32 >> 20) & 0x7ffu);
+  const int fe = e - 1023 + 127;
+  if (e == 0 || fe <= 0) return dd(0.f, 0.f);
+  if (e == 0x7ff || fe >= 255) return dd(__uint_as_float(sign | 0x7f800000u | ((e == 0x7ff && ((h32 & 0xfffffu) | l32)) ? 0x400000u : 0u)), 0.f);
+  const unsigned m23 = ((h32 & 0xfffffu) << 3) | (l32 >> 29);
+  const float hi = __uint_as_float(sign | ((unsigned)fe << 23) | m23);
+  const int se = e - 1075 + 127;                 // exponent of the unit of the low 29 bits
+  float lo = 0.f;
+  if (se > 0) lo = __fmul_rn(__uint2float_rn(l32 & 0x1fffffffu), __uint_as_float((unsigned)se << 23));
+  return dd(hi, sign ? -lo : lo);
+}
+
+__device__ __forceinline__ dd warp_sum_dd(dd v) {
+  for (int off = 16; off > 0; off >>= 1) {
+    dd o(__shfl_down_sync(0xffffffffu, v.hi, off), __shfl_down_sync(0xffffffffu, v.lo, off));
+    v = dd_add(v, o);
+  }
+  return v;
+}
+
+// block-wide double-float sum (result valid in thread 0); all threads must call
+__device__ __forceinline__ dd block_sum_dd(dd v) {
+  __shared__ dd red_dd[32];
+  v = warp_sum_dd(v);
+  if ((threadIdx.x & 31) == 0) red_dd[threadIdx.x >> 5] = v;
+  __syncthreads();
+  dd t(0.f, 0.f);
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = dd_add(t, red_dd[w]);
+  __syncthreads();
+  return t;
+}
+
 // ---------------------------------------------------------------------------
-// rows_forward: real FFT along longitude.
+// rows_forward: real FFT along longitude in arithmetic T.
 //   forward (ADJ = false): W[i][k] = row_scale[i] * G_i(k)
 //   adjoint (ADJ = true):  W[i][k] = c_k * sum_q ubar_iq e^{-2 pi i k q/n},
 //                          c_0 = c_L = 1, else 2  (transpose of rows_inverse)
+//   zonal (optional, FP32 arithmetic): Z[i][0] = the k = 0 value of row i
+//   (row_scale[i] * sum_q f_iq, or sum_q ubar_iq), summed in double-float from
+//   the double inputs, Z[i][1] = 0; the FP64 side path takes the zonal column
+//   from there.
 // One CTA per `rows` consecutive rows; shared memory rows * L complex.
 // ---------------------------------------------------------------------------
 template <typename T, bool ADJ, bool BIG>
 __global__ void __launch_bounds__(512) k_rows_forward(
     const double* __restrict__ f, cpx<T>* __restrict__ W, int nt, int n, int Kp, int rows,
     FftDesc d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
-    const cpx<T>* __restrict__ post, const double* __restrict__ row_scale) {
+    const cpx<T>* __restrict__ post, const double* __restrict__ row_scale,
+    cpx<double>* __restrict__ zonal) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
   const int L = n >> 1;
   const int row0 = blockIdx.x * rows;
-  for (int idx = threadIdx.x; idx < rows * L; idx += blockDim.x) {
-    int r = idx / L, q = idx - r * L;
-    int row = row0 + r;
-    cpx<T> z = {(T)0, (T)0};
-    if (row < nt) {
-      double2 v = __ldg(reinterpret_cast<const double2*>(f + (size_t)row * n) + q);
-      z = {(T)v.x, (T)v.y};
+  for (int r = 0; r < rows; ++r) {
+    const int row = row0 + r;
+    dd acc(0.f, 0.f);
+    for (int q = threadIdx.x; q < L; q += blockDim.x) {
+      cpx<T> z = {(T)0, (T)0};
+      if (row < nt) {
+        double2 v = __ldg(reinterpret_cast<const double2*>(f + (size_t)row * n) + q);
+        z = {num<T>::from_double(v.x), num<T>::from_double(v.y)};
+        if (zonal) acc = dd_add(acc, dd_add(split_double(v.x), split_double(v.y)));
+      }
+      sm[r * L + __ldg(perm + q)] = z;
     }
-    sm[r * L + __ldg(perm + q)] = z;
+    if (zonal) {  // uniform over the block
+      dd tot = block_sum_dd(acc);
+      if (threadIdx.x == 0 && row < nt) {
+        double g0 = dd_to_double(tot);
+        if (!ADJ) g0 *= __ldg(row_scale + row);
+        zonal[(size_t)row * 2] = {g0, 0.0};
+        zonal[(size_t)row * 2 + 1] = {0.0, 0.0};
+      }
+    }
   }
   __syncthreads();
   fft_run<-1, BIG>(sm, rows, d, tw);
@@ -72,7 +133,7 @@ __global__ void __launch_bounds__(512) k_rows_forward(
       out = {fma((T)0.5, t.im, s.re), fma((T)-0.5, t.re, s.im)};
       T scale;
       if (ADJ) scale = (k == 0 || k == L) ? (T)1 : (T)2;
-      else scale = (T)__ldg(row_scale + row);
+      else scale = num<T>::from_double(__ldg(row_scale + row));
       out = scale * out;
     }
     W[(size_t)row * Kp + k] = out;
@@ -85,12 +146,15 @@ __global__ void __launch_bounds__(512) k_rows_forward(
 //   forward: U = W, u written unscaled.
 //   adjoint: U_k = W_k * (k == 0 || k == L ? 1 : 1/2), u scaled by row_scale
 //            (transpose of rows_forward).
+//   zonal (optional): U_0 of row i is taken as Z[i][0].re, added in double
+//            after the transform (the FP64 side path's zonal column).
 // ---------------------------------------------------------------------------
 template <typename T, bool ADJ, bool BIG>
 __global__ void __launch_bounds__(512) k_rows_inverse(
     const cpx<T>* __restrict__ W, double* __restrict__ u, int nt, int n, int Kp, int rows,
     FftDesc d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
-    const cpx<T>* __restrict__ post, const double* __restrict__ row_scale) {
+    const cpx<T>* __restrict__ post, const double* __restrict__ row_scale,
+    const cpx<double>* __restrict__ zonal) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
   const int L = n >> 1;
@@ -106,6 +170,7 @@ __global__ void __launch_bounds__(512) k_rows_inverse(
       if (k == 0) {
         uk.im = (T)0;
         up.im = (T)0;
+        if (zonal) uk.re = (T)0;
       } else if (ADJ) {
         uk = (T)0.5 * uk;
         up = (T)0.5 * up;
@@ -126,7 +191,13 @@ __global__ void __launch_bounds__(512) k_rows_inverse(
     if (row >= nt) continue;
     cpx<T> z = sm[idx];
     double scale = ADJ ? __ldg(row_scale + row) : 1.0;
-    double2 v = {scale * (double)z.re, scale * (double)z.im};
+    double2 v;
+    if (zonal) {
+      double u0 = zonal[(size_t)row * 2].re;
+      v = {scale * (num<T>::to_double(z.re) + u0), scale * (num<T>::to_double(z.im) + u0)};
+    } else {
+      v = {scale * num<T>::to_double(z.re), scale * num<T>::to_double(z.im)};
+    }
     reinterpret_cast<double2*>(u + (size_t)row * n)[q] = v;
   }
 }
@@ -138,13 +209,16 @@ __global__ void __launch_bounds__(512) k_rows_inverse(
 // DST-II at j).
 //   forward: F_j = P_j / N (k even), F_j = -i P_{N-j} / N (k odd, F_0 = 0)
 //   adjoint: Xbar_j = c_j P_j (k even, c_0 = 1, c_j = 2), Xbar_j = -2i P_{N-j}
-//            (k odd, Xbar_0 = 0)  (transpose of theta_inverse)
-// One CTA per `cols` consecutive columns.
+//            (k odd, Xbar_0 = 0)  (transpose of theta_inverse); with zonal
+//            set (FP64 arithmetic), column 0 also gets the transposed k = 0
+//            closure.
+// One CTA per `cols` consecutive columns.  inv_n = 1/N in arithmetic T.
 // ---------------------------------------------------------------------------
 template <typename T, bool ADJ, bool BIG>
 __global__ void __launch_bounds__(512) k_theta_forward(
     cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d,
-    const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post) {
+    const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
+    T inv_n, int zonal) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
   const int k0 = blockIdx.x * cols;
@@ -160,7 +234,6 @@ __global__ void __launch_bounds__(512) k_theta_forward(
   }
   __syncthreads();
   fft_run<-1, BIG>(sm, cols, d, tw);
-  const T invN = (T)1 / (T)N;
   for (int idx = threadIdx.x; idx < N * cols; idx += blockDim.x) {
     int j = idx / cols, c = idx - j * cols;
     int k = k0 + c;
@@ -173,14 +246,16 @@ __global__ void __launch_bounds__(512) k_theta_forward(
       cpx<T> p = (T)0.5 * (cmul(w, a) + cmulc(b, w));
       if (ADJ) {
         out = (j == 0 ? (T)1 : (T)2) * p;
-        // transpose of the k = 0 closure X_0 = sum_{j even >= 2} 2 X_j/(j^2-1):
-        // Xbar_j += 2 Xbar_0/(j^2-1), with Xbar_0 = P_0 = V_0
-        if (k == 0 && j >= 2 && !(j & 1)) {
-          T wj = (T)2 / ((T)j * (T)j - (T)1);
-          out = out + wj * V[0];
+        if constexpr (std::is_same<T, double>::value) {
+          // transpose of the k = 0 closure X_0 = sum_{j even >= 2} 2 X_j/(j^2-1):
+          // Xbar_j += 2 Xbar_0/(j^2-1), with Xbar_0 = P_0 = V_0
+          if (zonal && k == 0 && j >= 2 && !(j & 1)) {
+            double wj = 2.0 / ((double)j * (double)j - 1.0);
+            out = out + wj * V[0];
+          }
         }
       } else {
-        out = invN * p;
+        out = inv_n * p;
       }
     } else if (j == 0) {
       out = {(T)0, (T)0};
@@ -190,8 +265,8 @@ __global__ void __launch_bounds__(512) k_theta_forward(
       cpx<T> a = V[jj], b = V[j];
       cpx<T> p = (T)0.5 * (cmul(w, a) + cmulc(b, w));
       // forward: -i p / N ; adjoint: -2 i p
-      T s = ADJ ? (T)2 : invN;
-      out = {s * p.im, -s * p.re};
+      T s = ADJ ? (T)2 : inv_n;
+      out = {s * p.im, -(s * p.re)};
     }
     W[(size_t)j * Kp + k] = out;
   }
@@ -202,37 +277,41 @@ __global__ void __launch_bounds__(512) k_theta_forward(
 // with Y = X, or for k odd i (-1)^i times the DCT-III of Y_j = X_{N-j} (Y_0 = 0),
 // through one inverse FFT of V_j = exp(i pi j/(2N)) (Y_j - i Y_{N-j}) (Y_N = 0)
 // and the inverse Makhoul reordering.
-//   forward: U = DCT-III(X) (k even), i DST-III(X) (k odd)
-//   adjoint: inputs with j >= 1 halved and outputs scaled 1/N: the transpose
-//            of theta_forward
+//   forward: U = DCT-III(X) (k even), i DST-III(X) (k odd); with zonal set
+//            (FP64 arithmetic) the first CTA first closes the k = 0 column:
+//            X_00 = sum_{j even >= 2} 2 X_j0/(j^2-1) (w^T X_0 = 0).
+//   adjoint: inputs with j >= 1 halved and outputs scaled by inv_n = 1/N: the
+//            transpose of theta_forward
 // ---------------------------------------------------------------------------
 template <typename T, bool ADJ, bool BIG>
 __global__ void __launch_bounds__(512) k_theta_inverse(
     cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d,
-    const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post) {
+    const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
+    T inv_n, int zonal) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
   const int k0 = blockIdx.x * cols;
-  if (!ADJ && k0 == 0) {
-    // k = 0 closure of the solve: w^T X_0 = 0 gives X_00 = sum_{j even >= 2} 2 X_j0/(j^2-1)
-    cpx<T> acc = {(T)0, (T)0};
-    for (int j = 2 + 2 * threadIdx.x; j < N; j += 2 * blockDim.x) {
-      T wj = (T)2 / ((T)j * (T)j - (T)1);
-      acc = acc + wj * W[(size_t)j * Kp];
+  if constexpr (std::is_same<T, double>::value) {
+    if (!ADJ && zonal && k0 == 0) {
+      cpx<double> acc = {0.0, 0.0};
+      for (int j = 2 + 2 * threadIdx.x; j < N; j += 2 * blockDim.x) {
+        double wj = 2.0 / ((double)j * (double)j - 1.0);
+        acc = acc + wj * W[(size_t)j * Kp];
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        acc.re = acc.re + __shfl_down_sync(0xffffffffu, acc.re, off);
+        acc.im = acc.im + __shfl_down_sync(0xffffffffu, acc.im, off);
+      }
+      __shared__ cpx<double> red[32];
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        cpx<double> tot = {0.0, 0.0};
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot = tot + red[w];
+        W[0] = tot;
+      }
+      __syncthreads();
     }
-    for (int off = 16; off > 0; off >>= 1) {
-      acc.re = acc.re + __shfl_down_sync(0xffffffffu, acc.re, off);
-      acc.im = acc.im + __shfl_down_sync(0xffffffffu, acc.im, off);
-    }
-    __shared__ cpx<T> red[32];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      cpx<T> tot = {(T)0, (T)0};
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot = tot + red[w];
-      W[0] = tot;
-    }
-    __syncthreads();
   }
   // pre-twiddle straight from global memory, one thread per pair (j, N - j),
   // j = 0 .. N/2, writing V_j and V_{N-j} to their digit-reversed slots
@@ -270,18 +349,15 @@ __global__ void __launch_bounds__(512) k_theta_inverse(
   }
   __syncthreads();
   fft_run<+1, BIG>(sm, cols, d, tw);
-  const T scale = ADJ ? (T)1 / (T)N : (T)1;
   for (int idx = threadIdx.x; idx < N * cols; idx += blockDim.x) {
     int i = idx / cols, c = idx - i * cols;
     int k = k0 + c;
     if (k >= K) continue;
     cpx<T> v = sm[c * N + makhoul_pos(i, N)];
+    if (ADJ) v = inv_n * v;
     if (k & 1) {
       // times i (-1)^i
-      T sg = (i & 1) ? -scale : scale;
-      v = {-sg * v.im, sg * v.re};
-    } else {
-      v = scale * v;
+      v = (i & 1) ? cpx<T>{v.im, -v.re} : cpx<T>{-v.im, v.re};
     }
     W[(size_t)i * Kp + k] = v;
   }
@@ -295,7 +371,8 @@ __global__ void __launch_bounds__(512) k_theta_inverse(
 // u_t = b_t - l_t c_{t-1}.  Stored per (j, k): l, 1/u, c/u.
 // Thread layout: idx < K -> odd chain of k = idx; else even chain of k = idx - K.
 // ---------------------------------------------------------------------------
-__global__ void k_factor(double* __restrict__ fl, double* __restrict__ fiu, double* __restrict__ fcu,
+template <typename S>
+__global__ void k_factor(S* __restrict__ fl, S* __restrict__ fiu, S* __restrict__ fcu,
                          int N, int K, int Kp) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= 2 * K) return;
@@ -316,9 +393,9 @@ __global__ void k_factor(double* __restrict__ fl, double* __restrict__ fiu, doub
     }
     const double iu = 1.0 / uu;
     const size_t o = (size_t)j * Kp + k;
-    fl[o] = l;
-    fiu[o] = iu;
-    fcu[o] = c * iu;
+    fl[o] = (S)l;
+    fiu[o] = (S)iu;
+    fcu[o] = (S)(c * iu);
     u_prev = uu;
     c_prev = c;
   }
@@ -355,57 +432,74 @@ __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;
 // chain's rows through a ring of kRing shared-memory slots filled by its own
 // cp.async copies, kRing rows ahead of the elimination, so every lane keeps
 // kRing rows of loads in flight without any cross-lane synchronisation.
+// S is the storage and arithmetic type (double, or float for the FP32 form).
 constexpr int kRing = 32;
+template <typename S>
 struct RingSlot {
-  cpx<double> d[32];
-  double a[32];
-  double b[32];
+  cpx<S> d[32];
+  S a[32];
+  S b[32];
 };
 
-template <bool ADJ>
-__global__ void __launch_bounds__(32) k_solve(cpx<double>* __restrict__ W, const double* __restrict__ fl,
-                                              const double* __restrict__ fiu, const double* __restrict__ fcu,
+template <typename S>
+__device__ __forceinline__ void cp_async_c(cpx<S>* smem, const cpx<S>* g) {
+  if constexpr (sizeof(cpx<S>) == 16) cp_async16(smem, g);
+  else cp_async8(smem, g);
+}
+template <typename S>
+__device__ __forceinline__ void cp_async_s(S* smem, const S* g) {
+  if constexpr (sizeof(S) == 8) {
+    cp_async8(smem, g);
+  } else {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(g) : "memory");
+  }
+}
+
+template <bool ADJ, typename S>
+__global__ void __launch_bounds__(32) k_solve(cpx<S>* __restrict__ W, const S* __restrict__ fl,
+                                              const S* __restrict__ fiu, const S* __restrict__ fcu,
                                               int N, int K, int Kp) {
-  __shared__ RingSlot ring[kRing];
+  __shared__ RingSlot<S> ring[kRing];
   const int lane = threadIdx.x;
   const bool even = blockIdx.y == 1;
   const int k = blockIdx.x * 32 + lane;
   if (k >= K) return;
   const int j0 = even ? 2 : 1;
-  const double ik2 = k ? 1.0 / ((double)k * (double)k) : 0.0;
+  const S ik2 = k ? (S)(1.0 / ((double)k * (double)k)) : (S)0;
   if (j0 >= N) {
     // no chain rows; only the closure of row 0 remains (forward: X_0 = -F_0/k^2,
     // adjoint: Fbar_0 = -Xbar_0/k^2, both zero for k = 0 and odd k)
     if (even) {
-      cpx<double> x0 = W[k];
-      W[k] = (k == 0 || (k & 1)) ? cpx<double>{0.0, 0.0} : (-ik2) * x0;
+      cpx<S> x0 = W[k];
+      W[k] = (k == 0 || (k & 1)) ? cpx<S>{(S)0, (S)0} : (-ik2) * x0;
     }
     return;
   }
   const int M = (N - 1 - j0) / 2 + 1;            // chain length
   const size_t stride = (size_t)2 * Kp;          // one chain step
-  cpx<double>* Wc = W + (size_t)j0 * Kp + k;
-  const double* Lc = fl + (size_t)j0 * Kp + k;
-  const double* IUc = fiu + (size_t)j0 * Kp + k;
-  const double* CUc = fcu + (size_t)j0 * Kp + k;
+  cpx<S>* Wc = W + (size_t)j0 * Kp + k;
+  const S* Lc = fl + (size_t)j0 * Kp + k;
+  const S* IUc = fiu + (size_t)j0 * Kp + k;
+  const S* CUc = fcu + (size_t)j0 * Kp + k;
 
   // ascending sweep issue: row t -> slot t % kRing (data + one table)
-  auto issue_up = [&](int t, const double* tab) {
+  auto issue_up = [&](int t, const S* tab) {
     if (t < M) {
-      RingSlot& sl = ring[t & (kRing - 1)];
-      cp_async16(&sl.d[lane], Wc + t * stride);
-      cp_async8(&sl.a[lane], tab + t * stride);
+      RingSlot<S>& sl = ring[t & (kRing - 1)];
+      cp_async_c(&sl.d[lane], Wc + t * stride);
+      cp_async_s(&sl.a[lane], tab + t * stride);
     }
     cp_commit();
   };
   // descending sweep issue: r-th row from the end -> slot r % kRing (data + two tables)
-  auto issue_down = [&](int r, const double* ta, const double* tb) {
+  auto issue_down = [&](int r, const S* ta, const S* tb) {
     int t = M - 1 - r;
     if (t >= 0) {
-      RingSlot& sl = ring[r & (kRing - 1)];
-      cp_async16(&sl.d[lane], Wc + t * stride);
-      cp_async8(&sl.a[lane], ta + t * stride);
-      if (tb) cp_async8(&sl.b[lane], tb + t * stride);
+      RingSlot<S>& sl = ring[r & (kRing - 1)];
+      cp_async_c(&sl.d[lane], Wc + t * stride);
+      cp_async_s(&sl.a[lane], ta + t * stride);
+      if (tb) cp_async_s(&sl.b[lane], tb + t * stride);
     }
     cp_commit();
   };
@@ -413,12 +507,12 @@ __global__ void __launch_bounds__(32) k_solve(cpx<double>* __restrict__ W, const
   if (!ADJ) {
     // forward sweep y_t = d_t - l_t y_{t-1}
     for (int t = 0; t < kRing; ++t) issue_up(t, Lc);
-    cpx<double> y = {0.0, 0.0};
+    cpx<S> y = {(S)0, (S)0};
     for (int t = 0; t < M; ++t) {
       cp_wait<kRing - 1>();
-      const RingSlot& sl = ring[t & (kRing - 1)];
-      cpx<double> d = sl.d[lane];
-      double l = sl.a[lane];
+      const RingSlot<S>& sl = ring[t & (kRing - 1)];
+      cpx<S> d = sl.d[lane];
+      S l = sl.a[lane];
       y = {fma(-l, y.re, d.re), fma(-l, y.im, d.im)};
       Wc[t * stride] = y;
       issue_up(t + kRing, Lc);
@@ -427,12 +521,12 @@ __global__ void __launch_bounds__(32) k_solve(cpx<double>* __restrict__ W, const
     __threadfence();  // the descending copies read rows this thread just stored
     // backward sweep x_t = y_t / u_t - (c_t / u_t) x_{t+1}
     for (int r = 0; r < kRing; ++r) issue_down(r, IUc, CUc);
-    cpx<double> x = {0.0, 0.0};
+    cpx<S> x = {(S)0, (S)0};
     for (int r = 0; r < M; ++r) {
       cp_wait<kRing - 1>();
-      const RingSlot& sl = ring[r & (kRing - 1)];
-      cpx<double> yv = sl.d[lane];
-      double iu = sl.a[lane], cu = sl.b[lane];
+      const RingSlot<S>& sl = ring[r & (kRing - 1)];
+      cpx<S> yv = sl.d[lane];
+      S iu = sl.a[lane], cu = sl.b[lane];
       const int t = M - 1 - r;
       x = {fma(yv.re, iu, -cu * x.re), fma(yv.im, iu, -cu * x.im)};
       Wc[t * stride] = x;
@@ -442,31 +536,31 @@ __global__ void __launch_bounds__(32) k_solve(cpx<double>* __restrict__ W, const
     if (even && k != 0) {
       // x holds X_2: row 0 closure X_0 = (X_2 - F_0)/k^2 (k even), X_0 = 0 (k odd).
       // The k = 0 closure (w^T X_0 = 0) is summed by theta_inverse's first CTA.
-      cpx<double> f0 = W[k];
-      if (k & 1) W[k] = {0.0, 0.0};
+      cpx<S> f0 = W[k];
+      if (k & 1) W[k] = {(S)0, (S)0};
       else W[k] = {(x.re - f0.re) * ik2, (x.im - f0.im) * ik2};
     }
   } else {
-    cpx<double> xb0 = {0.0, 0.0};
+    cpx<S> xb0 = {(S)0, (S)0};
     if (even) {
       xb0 = W[k];
-      W[k] = (k == 0 || (k & 1)) ? cpx<double>{0.0, 0.0} : (-ik2) * xb0;
+      W[k] = (k == 0 || (k & 1)) ? cpx<S>{(S)0, (S)0} : (-ik2) * xb0;
     }
     const bool bump2 = even && k != 0 && !(k & 1);   // Xbar_2 += Xbar_0 / k^2
     // forward sweep with U^T: z_t = (b_t - c_{t-1} z_{t-1}) / u_t
     for (int t = 0; t < kRing; ++t) issue_up(t, IUc);
-    cpx<double> z = {0.0, 0.0};
+    cpx<S> z = {(S)0, (S)0};
     for (int t = 0; t < M; ++t) {
       cp_wait<kRing - 1>();
-      const RingSlot& sl = ring[t & (kRing - 1)];
-      cpx<double> bv = sl.d[lane];
-      double iu = sl.a[lane];
+      const RingSlot<S>& sl = ring[t & (kRing - 1)];
+      cpx<S> bv = sl.d[lane];
+      S iu = sl.a[lane];
       const int j = j0 + 2 * t;
       // (k = 0: the terms 2 Xbar_0/(j^2-1) were added by theta_forward's adjoint)
       if (bump2 && t == 0) {
         bv = {fma(ik2, xb0.re, bv.re), fma(ik2, xb0.im, bv.im)};
       }
-      double cprev = t ? (double)((j - 1) * j) * 0.25 : 0.0;   // c_{j-2} = (j-1) j / 4
+      S cprev = t ? (S)((double)((j - 1) * j) * 0.25) : (S)0;   // c_{j-2} = (j-1) j / 4
       z = {(bv.re - cprev * z.re) * iu, (bv.im - cprev * z.im) * iu};
       Wc[t * stride] = z;
       issue_up(t + kRing, IUc);
@@ -475,13 +569,13 @@ __global__ void __launch_bounds__(32) k_solve(cpx<double>* __restrict__ W, const
     __threadfence();
     // backward sweep with L^T: y_t = z_t - l_{t+1} y_{t+1}
     for (int r = 0; r < kRing; ++r) issue_down(r, Lc, nullptr);
-    cpx<double> y = {0.0, 0.0};
-    double lnext = 0.0;
+    cpx<S> y = {(S)0, (S)0};
+    S lnext = (S)0;
     for (int r = 0; r < M; ++r) {
       cp_wait<kRing - 1>();
-      const RingSlot& sl = ring[r & (kRing - 1)];
-      cpx<double> zv = sl.d[lane];
-      double l = sl.a[lane];
+      const RingSlot<S>& sl = ring[r & (kRing - 1)];
+      cpx<S> zv = sl.d[lane];
+      S l = sl.a[lane];
       const int t = M - 1 - r;
       y = {fma(-lnext, y.re, zv.re), fma(-lnext, y.im, zv.im)};
       Wc[t * stride] = y;
@@ -491,5 +585,184 @@ __global__ void __launch_bounds__(32) k_solve(cpx<double>* __restrict__ W, const
     cp_wait_all();
   }
 }
+
+#ifdef SP_REFINE_KERNELS  // defined only in the double-float translation unit
+// ---------------------------------------------------------------------------
+// Iterative refinement of the per-k eliminations (FP32 + refinement form).
+// F (double-float) holds the right-hand sides, X (double-float) the current
+// solution, Y a float scratch.  One sweep of chain (k >= 1, parity):
+//   R_t = F_t - (a_t X_{t-1} + b_t X_t + c_t X_{t+1})   in double-float (FP64-accurate)
+//   FP32 Thomas on R with the FP32 factors: y = R - l y_prev; d = y/u - (c/u) d_next
+//   X_t += d_t                                            in double-float
+// With first = 1, X is taken as zero (R = F): the unrefined FP32 solve.
+// The even chain also sets the row 0 closure X_0 = (X_2 - F_0)/k^2 (k even),
+// X_0 = 0 (k odd).  Column k = 0 is left to the FP64 zonal path.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ dd dd_of_int(long long v) {
+  float h = (float)v;
+  float l = (float)(v - (long long)h);
+  return dd(h, l);
+}
+__device__ __forceinline__ cpx<dd> cdd_scale(dd s, cpx<dd> x) { return {dd_mul(s, x.re), dd_mul(s, x.im)}; }
+
+struct RefSlot {
+  cpx<dd> f[32];
+  cpx<dd> x[32];
+  float a[32];
+};
+struct RefSlotDown {
+  cpx<float> y[32];
+  cpx<dd> x[32];
+  float a[32];
+  float b[32];
+};
+union RefRing {
+  RefSlot up[16];
+  RefSlotDown down[16];
+};
+constexpr int kRefRing = 16;
+
+__global__ void __launch_bounds__(32) k_refine(const cpx<dd>* __restrict__ F, cpx<dd>* __restrict__ X,
+                                               cpx<float>* __restrict__ Y, const float* __restrict__ fl,
+                                               const float* __restrict__ fiu, const float* __restrict__ fcu,
+                                               int N, int K, int Kp, int first) {
+  __shared__ RefRing ring;
+  const int lane = threadIdx.x;
+  const bool even = blockIdx.y == 1;
+  const int k = blockIdx.x * 32 + lane;
+  if (k >= K || k == 0) return;
+  const int j0 = even ? 2 : 1;
+  const long long k2 = (long long)k * k;
+  if (j0 < N) {
+    const int M = (N - 1 - j0) / 2 + 1;
+    const size_t stride = (size_t)2 * Kp;
+    const size_t base = (size_t)j0 * Kp + k;
+    // ascending: residual and FP32 forward elimination.  X_{t+1} is prefetched
+    // with row t's F; X_t and X_{t-1} stay in registers.
+    auto issue_up = [&](int t) {
+      if (t < M) {
+        RefSlot& sl = ring.up[t & (kRefRing - 1)];
+        cp_async16(&sl.f[lane], F + base + t * stride);
+        if (!first) {
+          if (t + 1 < M) cp_async16(&sl.x[lane], X + base + (t + 1) * stride);
+        }
+        unsigned sa = (unsigned)__cvta_generic_to_shared(&sl.a[lane]);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(fl + base + t * stride) : "memory");
+      }
+      cp_commit();
+    };
+    for (int t = 0; t < kRefRing; ++t) issue_up(t);
+    cpx<dd> xm1 = {dd(0.f, 0.f), dd(0.f, 0.f)};
+    cpx<dd> x0 = {dd(0.f, 0.f), dd(0.f, 0.f)};
+    if (!first) x0 = X[base];
+    cpx<float> y = {0.f, 0.f};
+    for (int t = 0; t < M; ++t) {
+      cp_wait<kRefRing - 1>();
+      const RefSlot& sl = ring.up[t & (kRefRing - 1)];
+      cpx<dd> r = sl.f[lane];
+      float l = sl.a[lane];
+      cpx<dd> xp1 = {dd(0.f, 0.f), dd(0.f, 0.f)};
+      if (!first) {
+        if (t + 1 < M) xp1 = sl.x[lane];
+        const long long j = j0 + 2 * t;
+        dd a = dd_mul(dd_of_int((j - 1) * (j - 2)), dd(0.25f, 0.f));
+        dd b = dd_mul(dd_of_int(j * j + 2 * k2), dd(-0.5f, 0.f));
+        dd c = dd_mul(dd_of_int((j + 1) * (j + 2)), dd(0.25f, 0.f));
+        cpx<dd> lx = cdd_scale(b, x0);
+        lx = {dd_fma(a, xm1.re, lx.re), dd_fma(a, xm1.im, lx.im)};
+        lx = {dd_fma(c, xp1.re, lx.re), dd_fma(c, xp1.im, lx.im)};
+        r = {dd_sub(r.re, lx.re), dd_sub(r.im, lx.im)};
+      }
+      cpx<float> rf = {r.re.hi + r.re.lo, r.im.hi + r.im.lo};
+      y = {fmaf(-l, y.re, rf.re), fmaf(-l, y.im, rf.im)};
+      Y[base + t * stride] = y;
+      xm1 = x0;
+      x0 = xp1;
+      issue_up(t + kRefRing);
+    }
+    cp_wait_all();
+    __threadfence();
+    // descending: FP32 back substitution and the double-float update of X
+    auto issue_down = [&](int r) {
+      int t = M - 1 - r;
+      if (t >= 0) {
+        RefSlotDown& sl = ring.down[r & (kRefRing - 1)];
+        cp_async8(&sl.y[lane], Y + base + t * stride);
+        if (!first) cp_async16(&sl.x[lane], X + base + t * stride);
+        unsigned sa = (unsigned)__cvta_generic_to_shared(&sl.a[lane]);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(fiu + base + t * stride) : "memory");
+        sa = (unsigned)__cvta_generic_to_shared(&sl.b[lane]);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(fcu + base + t * stride) : "memory");
+      }
+      cp_commit();
+    };
+    for (int r = 0; r < kRefRing; ++r) issue_down(r);
+    cpx<float> dlt = {0.f, 0.f};
+    for (int r = 0; r < M; ++r) {
+      cp_wait<kRefRing - 1>();
+      const RefSlotDown& sl = ring.down[r & (kRefRing - 1)];
+      cpx<float> yv = sl.y[lane];
+      float iu = sl.a[lane], cu = sl.b[lane];
+      const int t = M - 1 - r;
+      dlt = {fmaf(yv.re, iu, -cu * dlt.re), fmaf(yv.im, iu, -cu * dlt.im)};
+      cpx<dd> xv = {dd(0.f, 0.f), dd(0.f, 0.f)};
+      if (!first) xv = sl.x[lane];
+      xv = {dd_add(xv.re, dd(dlt.re, 0.f)), dd_add(xv.im, dd(dlt.im, 0.f))};
+      X[base + t * stride] = xv;
+      issue_down(r + kRefRing);
+    }
+    cp_wait_all();
+  }
+  if (even) {
+    // row 0 closure in double-float: X_0 = (X_2 - F_0)/k^2 (k even), 0 (k odd)
+    cpx<dd> x0v = {dd(0.f, 0.f), dd(0.f, 0.f)};
+    if (!(k & 1)) {
+      __threadfence();
+      cpx<dd> x2 = (2 < N) ? X[(size_t)2 * Kp + k] : cpx<dd>{dd(0.f, 0.f), dd(0.f, 0.f)};
+      cpx<dd> f0 = F[k];
+      dd ik2 = dd_from_double(1.0 / (double)k2);
+      x0v = {dd_mul(dd_sub(x2.re, f0.re), ik2), dd_mul(dd_sub(x2.im, f0.im), ik2)};
+    }
+    X[k] = x0v;
+  }
+}
+
+// zonal column of a double-float array -> Z[i][0] (double), Z[i][1] = 0
+__global__ void k_zonal_extract(const cpx<dd>* __restrict__ Wdd, cpx<double>* __restrict__ Z, int N, int Kp) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  cpx<dd> v = Wdd[(size_t)i * Kp];
+  Z[(size_t)i * 2] = {dd_to_double(v.re), dd_to_double(v.im)};
+  Z[(size_t)i * 2 + 1] = {0.0, 0.0};
+}
+
+// after the FP64 zonal eliminations on Z: close with w^T X_0 = 0
+// (X_00 = sum_{j even >= 2} 2 X_j0/(j^2-1)) and write the column, as
+// double-float, into column 0 of X.  One CTA.
+__global__ void k_zonal_insert(const cpx<double>* __restrict__ Z, cpx<dd>* __restrict__ X, int N, int Kp) {
+  cpx<double> acc = {0.0, 0.0};
+  for (int j = 2 + 2 * threadIdx.x; j < N; j += 2 * blockDim.x) {
+    double wj = 2.0 / ((double)j * (double)j - 1.0);
+    acc = acc + wj * Z[(size_t)j * 2];
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    acc.re = acc.re + __shfl_down_sync(0xffffffffu, acc.re, off);
+    acc.im = acc.im + __shfl_down_sync(0xffffffffu, acc.im, off);
+  }
+  __shared__ cpx<double> red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cpx<double> tot = {0.0, 0.0};
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot = tot + red[w];
+    X[0] = {dd_from_double(tot.re), dd_from_double(tot.im)};
+  }
+  for (int i = 1 + threadIdx.x; i < N; i += blockDim.x) {
+    cpx<double> v = Z[(size_t)i * 2];
+    X[(size_t)i * Kp] = {dd_from_double(v.re), dd_from_double(v.im)};
+  }
+}
+
+#endif  // SP_REFINE_KERNELS
 
 }  // namespace sp

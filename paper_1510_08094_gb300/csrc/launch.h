@@ -1,0 +1,51 @@
+// Host-side launchers of the transform and elimination kernels.  Each
+// arithmetic type's kernels are compiled in their own translation unit
+// (k_f64.cu, k_f32.cu, k_dd.cu); the plan code in sphere_poisson.cu only sees
+// these declarations.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fft.cuh"
+
+namespace sp {
+
+struct Launch {
+  dim3 grid;
+  int threads;
+  size_t smem;
+  cudaStream_t stream;
+};
+
+template <typename T>
+void launch_rows_forward(bool adj, bool big, const Launch& l, const double* f, cpx<T>* W, int nt, int n,
+                         int Kp, int rows, const FftDesc& d, const cpx<T>* tw, const int* perm,
+                         const cpx<T>* post, const double* row_scale, cpx<double>* zonal);
+template <typename T>
+void launch_rows_inverse(bool adj, bool big, const Launch& l, const cpx<T>* W, double* u, int nt, int n,
+                         int Kp, int rows, const FftDesc& d, const cpx<T>* tw, const int* perm,
+                         const cpx<T>* post, const double* row_scale, const cpx<double>* zonal);
+template <typename T>
+void launch_theta_forward(bool adj, bool big, const Launch& l, cpx<T>* W, int N, int K, int Kp, int cols,
+                          const FftDesc& d, const cpx<T>* tw, const int* perm, const cpx<T>* post, T inv_n,
+                          int zonal);
+template <typename T>
+void launch_theta_inverse(bool adj, bool big, const Launch& l, cpx<T>* W, int N, int K, int Kp, int cols,
+                          const FftDesc& d, const cpx<T>* tw, const int* perm, const cpx<T>* post, T inv_n,
+                          int zonal);
+// raise the dynamic shared-memory cap of T's transform kernels
+template <typename T>
+cudaError_t allow_transform_smem(int bytes);
+
+template <typename S>
+void launch_solve(bool adj, const Launch& l, cpx<S>* W, const S* fl, const S* fiu, const S* fcu, int N, int K,
+                  int Kp);
+template <typename S>
+void launch_factor(const Launch& l, S* fl, S* fiu, S* fcu, int N, int K, int Kp);
+
+void launch_refine(const Launch& l, const cpx<dd>* F, cpx<dd>* X, cpx<float>* Y, const float* fl,
+                   const float* fiu, const float* fcu, int N, int K, int Kp, int first);
+void launch_zonal_extract(const Launch& l, const cpx<dd>* Wdd, cpx<double>* Z, int N, int Kp);
+void launch_zonal_insert(const Launch& l, const cpx<double>* Z, cpx<dd>* X, int N, int Kp);
+
+}  // namespace sp

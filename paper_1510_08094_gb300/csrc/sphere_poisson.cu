@@ -13,7 +13,7 @@
 #include <vector>
 
 #include "sphere_poisson.h"
-#include "kernels.cuh"
+#include "launch.h"
 
 using sp::cpx;
 using sp::FftDesc;
@@ -116,21 +116,42 @@ struct sp_plan_s {
   int precision, sweeps;
   int device;
   FftDesc row_fft, col_fft;
-  int rows_per_cta, cols_per_cta;
+  bool big_row, big_col;
+  int rows_per_cta, cols_per_cta;  // transform tiles in the plan's arithmetic
   int row_threads, col_threads;
   size_t row_smem, col_smem;
+  int zcol_threads;                // FP64 zonal side path: one column per CTA
+  size_t zcol_smem;
   size_t ws_bytes;
-  void* dev;           // one allocation holding every table
+  size_t off_x, off_y, off_z;      // workspace layout (bytes): main array at 0
+  void* dev;                       // one allocation holding every table
+  // double tables (FP64 path and the FP64 zonal side path)
   cpx<double>* tw_row;   // exp(-2 pi i t/L), t < L
   cpx<double>* tw_col;   // exp(-2 pi i t/N), t < N
-  int* perm_row;         // digit reversal of the length-L passes
-  int* perm_col;         // digit reversal of the length-N passes
   cpx<double>* post_row; // exp(-2 pi i k/n), k <= L
   cpx<double>* post_col; // exp(-i pi j/(2N)), j <= N
+  int* perm_row;         // digit reversal of the length-L passes
+  int* perm_col;         // digit reversal of the length-N passes
   double* row_scale;     // sin^2(theta_i)/n
-  double* fac_l;         // [N][Kp] Thomas multipliers
-  double* fac_iu;        // [N][Kp] 1/pivot
-  double* fac_cu;        // [N][Kp] super-diagonal / pivot
+  // the same tables in float (SP_FP32) or double-float (SP_FP32_REFINE)
+  void* tw_row_t;
+  void* tw_col_t;
+  void* post_row_t;
+  void* post_col_t;
+  // factorised parity tridiagonals l, 1/u, c/u: FP64 [N][Kp] (SP_FP64),
+  // float [N][Kp] (FP32 forms) and FP64 [N][2] for the zonal column (FP32 forms)
+  double* fac_l;
+  double* fac_iu;
+  double* fac_cu;
+  float* f32_l;
+  float* f32_iu;
+  float* f32_cu;
+  double* z_l;
+  double* z_iu;
+  double* z_cu;
+  // the FP32 forms run the zonal column on a second stream
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
   // stage timing (profile_begin / profile_end)
   std::vector<cudaEvent_t> prof_events;
   int prof_max, prof_count;
@@ -139,12 +160,6 @@ struct sp_plan_s {
 namespace {
 
 bool plan_ok(sp_plan_t p) { return p != nullptr && p->magic == kMagic; }
-
-template <typename K>
-cudaError_t allow_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
 
 int check_arrays(sp_plan_t p, const void* a, const void* b, const void* ws, size_t ws_bytes) {
   if (!plan_ok(p)) return SP_ERR_BAD_PLAN;
@@ -173,61 +188,195 @@ struct StageMarks {
   void mark(int s) {
     if (on) cudaEventRecord(p->prof_events[(size_t)p->prof_count * (kStages + 1) + s], st);
   }
+  void done() {
+    if (on) p->prof_count++;
+  }
 };
 
-template <bool ADJ, bool BR, bool BC>
-void enqueue_solve(sp_plan_t p, const double* in, double* out, cpx<double>* W, cudaStream_t st) {
+size_t esize(int precision) {
+  return precision == SP_FP32 ? sizeof(cpx<float>) : sizeof(cpx<double>);
+}
+
+void enqueue_fp64(sp_plan_t p, bool adj, const double* in, double* out, void* ws, cudaStream_t st) {
+  using sp::Launch;
+  cpx<double>* W = static_cast<cpx<double>*>(ws);
   StageMarks m{p, st, !p->prof_events.empty() && p->prof_count < p->prof_max};
-  const int row_blocks = (p->nt + p->rows_per_cta - 1) / p->rows_per_cta;
-  const int col_blocks = (p->K + p->cols_per_cta - 1) / p->cols_per_cta;
-  const dim3 solve_grid((p->K + 31) / 32, 2);
+  const Launch rows{dim3((p->nt + p->rows_per_cta - 1) / p->rows_per_cta), p->row_threads, p->row_smem, st};
+  const Launch cols{dim3((p->K + p->cols_per_cta - 1) / p->cols_per_cta), p->col_threads, p->col_smem, st};
+  const Launch solve{dim3((p->K + 31) / 32, 2), 32, 0, st};
+  const double inv_n = 1.0 / (double)p->N;
   m.mark(0);
-  sp::k_rows_forward<double, ADJ, BR><<<row_blocks, p->row_threads, p->row_smem, st>>>(
-      in, W, p->nt, p->nl, p->Kp, p->rows_per_cta, p->row_fft, p->tw_row, p->perm_row, p->post_row,
-      p->row_scale);
+  sp::launch_rows_forward<double>(adj, p->big_row, rows, in, W, p->nt, p->nl, p->Kp, p->rows_per_cta,
+                                  p->row_fft, p->tw_row, p->perm_row, p->post_row, p->row_scale, nullptr);
   m.mark(1);
-  sp::k_theta_forward<double, ADJ, BC><<<col_blocks, p->col_threads, p->col_smem, st>>>(
-      W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft, p->tw_col, p->perm_col, p->post_col);
+  sp::launch_theta_forward<double>(adj, p->big_col, cols, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
+                                   p->tw_col, p->perm_col, p->post_col, inv_n, 1);
   m.mark(2);
-  sp::k_solve<ADJ><<<solve_grid, 32, 0, st>>>(W, p->fac_l, p->fac_iu, p->fac_cu, p->N, p->K,
-                                                            p->Kp);
+  sp::launch_solve<double>(adj, solve, W, p->fac_l, p->fac_iu, p->fac_cu, p->N, p->K, p->Kp);
   m.mark(3);
-  sp::k_theta_inverse<double, ADJ, BC><<<col_blocks, p->col_threads, p->col_smem, st>>>(
-      W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft, p->tw_col, p->perm_col, p->post_col);
+  sp::launch_theta_inverse<double>(adj, p->big_col, cols, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
+                                   p->tw_col, p->perm_col, p->post_col, inv_n, 1);
   m.mark(4);
-  sp::k_rows_inverse<double, ADJ, BR><<<row_blocks, p->row_threads, p->row_smem, st>>>(
-      W, out, p->nt, p->nl, p->Kp, p->rows_per_cta, p->row_fft, p->tw_row, p->perm_row, p->post_row,
-      p->row_scale);
+  sp::launch_rows_inverse<double>(adj, p->big_row, rows, W, out, p->nt, p->nl, p->Kp, p->rows_per_cta,
+                                  p->row_fft, p->tw_row, p->perm_row, p->post_row, p->row_scale, nullptr);
   m.mark(5);
-  if (m.on) p->prof_count++;
+  m.done();
+}
+
+// FP64 transforms and eliminations of the zonal column Z [N][2] (one column)
+void enqueue_zonal_fp64(sp_plan_t p, bool adj, cpx<double>* Z, cudaStream_t st) {
+  const double inv_n = 1.0 / (double)p->N;
+  const sp::Launch one{dim3(1), p->zcol_threads, p->zcol_smem, st};
+  sp::launch_theta_forward<double>(adj, p->big_col, one, Z, p->N, 1, 2, 1, p->col_fft, p->tw_col, p->perm_col,
+                                   p->post_col, inv_n, 1);
+  sp::launch_solve<double>(adj, sp::Launch{dim3(1, 2), 32, 0, st}, Z, p->z_l, p->z_iu, p->z_cu, p->N, 1, 2);
+  sp::launch_theta_inverse<double>(adj, p->big_col, one, Z, p->N, 1, 2, 1, p->col_fft, p->tw_col, p->perm_col,
+                                   p->post_col, inv_n, 1);
+}
+
+void enqueue_fp32(sp_plan_t p, bool adj, const double* in, double* out, void* ws, cudaStream_t st) {
+  using sp::Launch;
+  cpx<float>* W = static_cast<cpx<float>*>(ws);
+  cpx<double>* Z = reinterpret_cast<cpx<double>*>(static_cast<char*>(ws) + p->off_z);
+  StageMarks m{p, st, !p->prof_events.empty() && p->prof_count < p->prof_max};
+  const Launch rows{dim3((p->nt + p->rows_per_cta - 1) / p->rows_per_cta), p->row_threads, p->row_smem, st};
+  const Launch cols{dim3((p->K + p->cols_per_cta - 1) / p->cols_per_cta), p->col_threads, p->col_smem, st};
+  const Launch solve{dim3((p->K + 31) / 32, 2), 32, 0, st};
+  const float inv_n = 1.0f / (float)p->N;
+  const cpx<float>* twr = static_cast<const cpx<float>*>(p->tw_row_t);
+  const cpx<float>* twc = static_cast<const cpx<float>*>(p->tw_col_t);
+  const cpx<float>* por = static_cast<const cpx<float>*>(p->post_row_t);
+  const cpx<float>* poc = static_cast<const cpx<float>*>(p->post_col_t);
+  m.mark(0);
+  sp::launch_rows_forward<float>(adj, p->big_row, rows, in, W, p->nt, p->nl, p->Kp, p->rows_per_cta,
+                                 p->row_fft, twr, p->perm_row, por, p->row_scale, Z);
+  cudaEventRecord(p->ev_fork, st);
+  cudaStreamWaitEvent(p->side, p->ev_fork, 0);
+  enqueue_zonal_fp64(p, adj, Z, p->side);
+  cudaEventRecord(p->ev_join, p->side);
+  m.mark(1);
+  sp::launch_theta_forward<float>(adj, p->big_col, cols, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
+                                  twc, p->perm_col, poc, inv_n, 0);
+  m.mark(2);
+  sp::launch_solve<float>(adj, solve, W, p->f32_l, p->f32_iu, p->f32_cu, p->N, p->K, p->Kp);
+  m.mark(3);
+  sp::launch_theta_inverse<float>(adj, p->big_col, cols, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
+                                  twc, p->perm_col, poc, inv_n, 0);
+  cudaStreamWaitEvent(st, p->ev_join, 0);
+  m.mark(4);
+  sp::launch_rows_inverse<float>(adj, p->big_row, rows, W, out, p->nt, p->nl, p->Kp, p->rows_per_cta,
+                                 p->row_fft, twr, p->perm_row, por, p->row_scale, Z);
+  m.mark(5);
+  m.done();
+}
+
+void enqueue_refine(sp_plan_t p, const double* in, double* out, void* ws, cudaStream_t st) {
+  using sp::Launch;
+  using sp::dd;
+  char* base = static_cast<char*>(ws);
+  cpx<dd>* Fd = reinterpret_cast<cpx<dd>*>(base);
+  cpx<dd>* Xd = reinterpret_cast<cpx<dd>*>(base + p->off_x);
+  cpx<float>* Y = reinterpret_cast<cpx<float>*>(base + p->off_y);
+  cpx<double>* Z = reinterpret_cast<cpx<double>*>(base + p->off_z);
+  StageMarks m{p, st, !p->prof_events.empty() && p->prof_count < p->prof_max};
+  const Launch rows{dim3((p->nt + p->rows_per_cta - 1) / p->rows_per_cta), p->row_threads, p->row_smem, st};
+  const Launch cols{dim3((p->K + p->cols_per_cta - 1) / p->cols_per_cta), p->col_threads, p->col_smem, st};
+  const Launch solve{dim3((p->K + 31) / 32, 2), 32, 0, st};
+  const dd inv_n(1.0 / (double)p->N);
+  const cpx<dd>* twr = static_cast<const cpx<dd>*>(p->tw_row_t);
+  const cpx<dd>* twc = static_cast<const cpx<dd>*>(p->tw_col_t);
+  const cpx<dd>* por = static_cast<const cpx<dd>*>(p->post_row_t);
+  const cpx<dd>* poc = static_cast<const cpx<dd>*>(p->post_col_t);
+  m.mark(0);
+  sp::launch_rows_forward<dd>(false, p->big_row, rows, in, Fd, p->nt, p->nl, p->Kp, p->rows_per_cta,
+                              p->row_fft, twr, p->perm_row, por, p->row_scale, nullptr);
+  m.mark(1);
+  sp::launch_theta_forward<dd>(false, p->big_col, cols, Fd, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
+                               twc, p->perm_col, poc, inv_n, 0);
+  cudaEventRecord(p->ev_fork, st);
+  cudaStreamWaitEvent(p->side, p->ev_fork, 0);
+  {
+    const int zt = 256;
+    sp::launch_zonal_extract(Launch{dim3((p->N + zt - 1) / zt), zt, 0, p->side}, Fd, Z, p->N, p->Kp);
+    sp::launch_solve<double>(false, Launch{dim3(1, 2), 32, 0, p->side}, Z, p->z_l, p->z_iu, p->z_cu, p->N, 1, 2);
+    sp::launch_zonal_insert(Launch{dim3(1), 512, 0, p->side}, Z, Xd, p->N, p->Kp);
+  }
+  cudaEventRecord(p->ev_join, p->side);
+  m.mark(2);
+  for (int s = 0; s <= p->sweeps; ++s)
+    sp::launch_refine(solve, Fd, Xd, Y, p->f32_l, p->f32_iu, p->f32_cu, p->N, p->K, p->Kp, s == 0 ? 1 : 0);
+  cudaStreamWaitEvent(st, p->ev_join, 0);
+  m.mark(3);
+  sp::launch_theta_inverse<dd>(false, p->big_col, cols, Xd, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
+                               twc, p->perm_col, poc, inv_n, 0);
+  m.mark(4);
+  sp::launch_rows_inverse<dd>(false, p->big_row, rows, Xd, out, p->nt, p->nl, p->Kp, p->rows_per_cta,
+                              p->row_fft, twr, p->perm_row, por, p->row_scale, nullptr);
+  m.mark(5);
+  m.done();
 }
 
 template <bool ADJ>
 int launch_solve(sp_plan_t p, const double* in, double* out, void* workspace, cudaStream_t st) {
-  cpx<double>* W = static_cast<cpx<double>*>(workspace);
-  const bool br = needs_big(p->row_fft), bc = needs_big(p->col_fft);
-  if (!br && !bc) enqueue_solve<ADJ, false, false>(p, in, out, W, st);
-  else if (!br && bc) enqueue_solve<ADJ, false, true>(p, in, out, W, st);
-  else if (br && !bc) enqueue_solve<ADJ, true, false>(p, in, out, W, st);
-  else enqueue_solve<ADJ, true, true>(p, in, out, W, st);
+  if (p->precision == SP_FP64) {
+    enqueue_fp64(p, ADJ, in, out, workspace, st);
+  } else if (p->precision == SP_FP32) {
+    enqueue_fp32(p, ADJ, in, out, workspace, st);
+  } else {
+    if (ADJ) return SP_ERR_UNSUPPORTED;
+    enqueue_refine(p, in, out, workspace, st);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "solve launch");
   return SP_OK;
 }
 
-template <bool B>
-cudaError_t allow_all_smem(size_t row_smem, size_t col_smem) {
-  cudaError_t e = cudaSuccess;
-  auto upd = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
-  upd(allow_smem(sp::k_rows_forward<double, false, B>, row_smem));
-  upd(allow_smem(sp::k_rows_forward<double, true, B>, row_smem));
-  upd(allow_smem(sp::k_rows_inverse<double, false, B>, row_smem));
-  upd(allow_smem(sp::k_rows_inverse<double, true, B>, row_smem));
-  upd(allow_smem(sp::k_theta_forward<double, false, B>, col_smem));
-  upd(allow_smem(sp::k_theta_forward<double, true, B>, col_smem));
-  upd(allow_smem(sp::k_theta_inverse<double, false, B>, col_smem));
-  upd(allow_smem(sp::k_theta_inverse<double, true, B>, col_smem));
-  return e;
+std::mutex g_attr_mutex;
+bool g_attr_done[64] = {};
+
+// raise the dynamic shared-memory cap of every transform kernel once per
+// device to the device maximum, so plans of any size can share the kernels
+cudaError_t allow_all_smem(int device) {
+  std::lock_guard<std::mutex> lock(g_attr_mutex);
+  if (device >= 0 && device < 64 && g_attr_done[device]) return cudaSuccess;
+  int optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  if (e != cudaSuccess) return e;
+  optin -= 1024;  // headroom for the kernels' static shared memory
+  cudaError_t r = cudaSuccess;
+  auto upd = [&](cudaError_t x) { if (r == cudaSuccess) r = x; };
+  upd(sp::allow_transform_smem<double>(optin));
+  upd(sp::allow_transform_smem<float>(optin));
+  upd(sp::allow_transform_smem<sp::dd>(optin));
+  if (r == cudaSuccess && device >= 0 && device < 64) g_attr_done[device] = true;
+  return r;
+}
+
+template <typename S>
+void upload_table(const std::vector<cpx<double>>& src, std::vector<char>& dst);
+
+template <>
+void upload_table<float>(const std::vector<cpx<double>>& src, std::vector<char>& dst) {
+  dst.resize(src.size() * sizeof(cpx<float>));
+  cpx<float>* o = reinterpret_cast<cpx<float>*>(dst.data());
+  for (size_t i = 0; i < src.size(); ++i) o[i] = {(float)src[i].re, (float)src[i].im};
+}
+
+template <>
+void upload_table<sp::dd>(const std::vector<cpx<double>>& src, std::vector<char>& dst) {
+  dst.resize(src.size() * sizeof(cpx<sp::dd>));
+  cpx<sp::dd>* o = reinterpret_cast<cpx<sp::dd>*>(dst.data());
+  for (size_t i = 0; i < src.size(); ++i) o[i] = {sp::dd(src[i].re), sp::dd(src[i].im)};
+}
+
+void destroy_plan(sp_plan_s* p) {
+  for (cudaEvent_t e : p->prof_events) cudaEventDestroy(e);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->side) cudaStreamDestroy(p->side);
+  if (p->dev) cudaFree(p->dev);
+  p->magic = 0;
+  delete p;
 }
 
 }  // namespace
@@ -240,8 +389,8 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   *plan = nullptr;
   if (n_theta < 1 || n_lambda < 2 || (n_lambda & 1)) return SP_ERR_BAD_SIZE;
   if (n_theta > kMaxLen || n_lambda / 2 > kMaxLen) return SP_ERR_BAD_SIZE;
-  if (precision != SP_FP64) return SP_ERR_UNSUPPORTED;
-  if (flags != 0 || refine_sweeps < 0) return SP_ERR_BAD_ARG;
+  if (precision != SP_FP64 && precision != SP_FP32 && precision != SP_FP32_REFINE) return SP_ERR_UNSUPPORTED;
+  if (flags != 0 || refine_sweeps < 0 || refine_sweeps > 16) return SP_ERR_BAD_ARG;
 
   FftDesc rd, cd;
   if (!make_fft_desc(n_lambda / 2, &rd) || !make_fft_desc(n_theta, &cd)) return SP_ERR_BAD_SIZE;
@@ -255,10 +404,12 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   p->K = p->L + 1;
   p->Kp = (p->K + 1) & ~1;
   p->precision = precision;
-  p->sweeps = refine_sweeps;
+  p->sweeps = precision == SP_FP32_REFINE ? refine_sweeps : 0;
   p->row_fft = rd;
   p->col_fft = cd;
-  const size_t csz = sizeof(cpx<double>);
+  p->big_row = needs_big(rd);
+  p->big_col = needs_big(cd);
+  const size_t csz = esize(precision);
   // tiles: rows per CTA and columns per CTA, powers of two up to 8 within the budget
   p->rows_per_cta = 1;
   while (p->rows_per_cta < 8 && (size_t)(2 * p->rows_per_cta) * p->L * csz <= 96 * 1024 &&
@@ -272,11 +423,27 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   p->col_smem = (size_t)p->cols_per_cta * p->N * csz;
   p->row_threads = fft_threads(rd, p->rows_per_cta);
   p->col_threads = fft_threads(cd, p->cols_per_cta);
-  if (p->row_threads < 0 || p->col_threads < 0 || p->row_smem > 227 * 1024 || p->col_smem > 227 * 1024) {
+  p->zcol_threads = fft_threads(cd, 1);
+  p->zcol_smem = (size_t)p->N * sizeof(cpx<double>);
+  if (p->row_threads < 0 || p->col_threads < 0 || p->row_smem > 220 * 1024 || p->col_smem > 220 * 1024 ||
+      p->zcol_smem > 220 * 1024) {
     delete p;
     return SP_ERR_BAD_SIZE;
   }
-  p->ws_bytes = (size_t)p->N * p->Kp * csz;
+  auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t grid = (size_t)p->N * p->Kp;
+  const size_t zbytes = (size_t)p->N * 2 * sizeof(cpx<double>);
+  if (precision == SP_FP64) {
+    p->ws_bytes = grid * sizeof(cpx<double>);
+  } else if (precision == SP_FP32) {
+    p->off_z = align(grid * sizeof(cpx<float>));
+    p->ws_bytes = p->off_z + zbytes;
+  } else {
+    p->off_x = align(grid * sizeof(cpx<sp::dd>));
+    p->off_y = p->off_x + align(grid * sizeof(cpx<sp::dd>));
+    p->off_z = p->off_y + align(grid * sizeof(cpx<float>));
+    p->ws_bytes = p->off_z + zbytes;
+  }
 
   if (cudaGetDevice(&p->device) != cudaSuccess) {
     delete p;
@@ -284,6 +451,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   }
 
   // host tables
+  const size_t cd_sz = sizeof(cpx<double>);
   std::vector<cpx<double>> tw_row(p->L), tw_col(p->N), post_row(p->L + 1), post_col(p->N + 1);
   for (int t = 0; t < p->L; ++t) unit_root(t, p->L, &tw_row[t].re, &tw_row[t].im);
   for (int t = 0; t < p->N; ++t) unit_root(t, p->N, &tw_col[t].re, &tw_col[t].im);
@@ -298,25 +466,49 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
     unit_root(2 * i + 1, 4L * p->N, &re, &im);  // sin(theta_i) = -im
     row_scale[i] = (im * im) / (double)n_lambda;
   }
+  std::vector<char> t_tw_row, t_tw_col, t_post_row, t_post_col;
+  if (precision == SP_FP32) {
+    upload_table<float>(tw_row, t_tw_row);
+    upload_table<float>(tw_col, t_tw_col);
+    upload_table<float>(post_row, t_post_row);
+    upload_table<float>(post_col, t_post_col);
+  } else if (precision == SP_FP32_REFINE) {
+    upload_table<sp::dd>(tw_row, t_tw_row);
+    upload_table<sp::dd>(tw_col, t_tw_col);
+    upload_table<sp::dd>(post_row, t_post_row);
+    upload_table<sp::dd>(post_col, t_post_col);
+  }
 
-  auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
   size_t off = 0;
-  size_t o_tw_row = off; off = align(off + p->L * csz);
-  size_t o_tw_col = off; off = align(off + p->N * csz);
-  size_t o_post_row = off; off = align(off + (p->L + 1) * csz);
-  size_t o_post_col = off; off = align(off + (p->N + 1) * csz);
-  size_t o_scale = off; off = align(off + p->nt * sizeof(double));
-  size_t o_perm_row = off; off = align(off + p->L * sizeof(int));
-  size_t o_perm_col = off; off = align(off + p->N * sizeof(int));
-  const size_t fac = (size_t)p->N * p->Kp * sizeof(double);
-  size_t o_l = off; off = align(off + fac);
-  size_t o_iu = off; off = align(off + fac);
-  size_t o_cu = off; off = align(off + fac);
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align(off + bytes);
+    return o;
+  };
+  size_t o_tw_row = take(p->L * cd_sz), o_tw_col = take(p->N * cd_sz);
+  size_t o_post_row = take((p->L + 1) * cd_sz), o_post_col = take((p->N + 1) * cd_sz);
+  size_t o_scale = take(p->nt * sizeof(double));
+  size_t o_perm_row = take(p->L * sizeof(int)), o_perm_col = take(p->N * sizeof(int));
+  size_t o_t_tw_row = take(t_tw_row.size()), o_t_tw_col = take(t_tw_col.size());
+  size_t o_t_post_row = take(t_post_row.size()), o_t_post_col = take(t_post_col.size());
+  const size_t fac64 = precision == SP_FP64 ? grid * sizeof(double) : 0;
+  const size_t fac32 = precision == SP_FP64 ? 0 : grid * sizeof(float);
+  const size_t facz = precision == SP_FP64 ? 0 : (size_t)p->N * 2 * sizeof(double);
+  const size_t o_fac_begin = off;
+  size_t o_l = take(fac64), o_iu = take(fac64), o_cu = take(fac64);
+  size_t o_l32 = take(fac32), o_iu32 = take(fac32), o_cu32 = take(fac32);
+  size_t o_zl = take(facz), o_ziu = take(facz), o_zcu = take(facz);
+  const size_t total = off;
 
-  cudaError_t e = cudaMalloc(&p->dev, off);
-  if (e != cudaSuccess) {
-    delete p;
-    return cuda_fail(e, "cudaMalloc(plan tables)");
+  int rc = SP_OK;
+  auto step = [&](cudaError_t err, const char* what) {
+    if (rc == SP_OK && err != cudaSuccess) rc = cuda_fail(err, what);
+  };
+  step(cudaMalloc(&p->dev, total), "cudaMalloc(plan tables)");
+  if (rc != SP_OK) {
+    p->dev = nullptr;
+    destroy_plan(p);
+    return rc;
   }
   char* base = static_cast<char*>(p->dev);
   p->tw_row = reinterpret_cast<cpx<double>*>(base + o_tw_row);
@@ -326,35 +518,57 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   p->row_scale = reinterpret_cast<double*>(base + o_scale);
   p->perm_row = reinterpret_cast<int*>(base + o_perm_row);
   p->perm_col = reinterpret_cast<int*>(base + o_perm_col);
+  p->tw_row_t = base + o_t_tw_row;
+  p->tw_col_t = base + o_t_tw_col;
+  p->post_row_t = base + o_t_post_row;
+  p->post_col_t = base + o_t_post_col;
   p->fac_l = reinterpret_cast<double*>(base + o_l);
   p->fac_iu = reinterpret_cast<double*>(base + o_iu);
   p->fac_cu = reinterpret_cast<double*>(base + o_cu);
+  p->f32_l = reinterpret_cast<float*>(base + o_l32);
+  p->f32_iu = reinterpret_cast<float*>(base + o_iu32);
+  p->f32_cu = reinterpret_cast<float*>(base + o_cu32);
+  p->z_l = reinterpret_cast<double*>(base + o_zl);
+  p->z_iu = reinterpret_cast<double*>(base + o_ziu);
+  p->z_cu = reinterpret_cast<double*>(base + o_zcu);
   p->magic = kMagic;
 
-  int rc = SP_OK;
-  auto step = [&](cudaError_t err, const char* what) {
-    if (rc == SP_OK && err != cudaSuccess) rc = cuda_fail(err, what);
+  auto up = [&](void* dst, const void* src, size_t bytes, const char* what) {
+    if (bytes) step(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice), what);
   };
-  step(cudaMemcpy(p->tw_row, tw_row.data(), p->L * csz, cudaMemcpyHostToDevice), "copy tw_row");
-  step(cudaMemcpy(p->tw_col, tw_col.data(), p->N * csz, cudaMemcpyHostToDevice), "copy tw_col");
-  step(cudaMemcpy(p->post_row, post_row.data(), (p->L + 1) * csz, cudaMemcpyHostToDevice), "copy post_row");
-  step(cudaMemcpy(p->post_col, post_col.data(), (p->N + 1) * csz, cudaMemcpyHostToDevice), "copy post_col");
-  step(cudaMemcpy(p->row_scale, row_scale.data(), p->nt * sizeof(double), cudaMemcpyHostToDevice), "copy row_scale");
-  step(cudaMemcpy(p->perm_row, perm_row.data(), p->L * sizeof(int), cudaMemcpyHostToDevice), "copy perm_row");
-  step(cudaMemcpy(p->perm_col, perm_col.data(), p->N * sizeof(int), cudaMemcpyHostToDevice), "copy perm_col");
-  step(cudaMemset(p->fac_l, 0, off - o_l), "clear factors");
+  up(p->tw_row, tw_row.data(), p->L * cd_sz, "copy tw_row");
+  up(p->tw_col, tw_col.data(), p->N * cd_sz, "copy tw_col");
+  up(p->post_row, post_row.data(), (p->L + 1) * cd_sz, "copy post_row");
+  up(p->post_col, post_col.data(), (p->N + 1) * cd_sz, "copy post_col");
+  up(p->row_scale, row_scale.data(), p->nt * sizeof(double), "copy row_scale");
+  up(p->perm_row, perm_row.data(), p->L * sizeof(int), "copy perm_row");
+  up(p->perm_col, perm_col.data(), p->N * sizeof(int), "copy perm_col");
+  up(p->tw_row_t, t_tw_row.data(), t_tw_row.size(), "copy tw_row_t");
+  up(p->tw_col_t, t_tw_col.data(), t_tw_col.size(), "copy tw_col_t");
+  up(p->post_row_t, t_post_row.data(), t_post_row.size(), "copy post_row_t");
+  up(p->post_col_t, t_post_col.data(), t_post_col.size(), "copy post_col_t");
+  step(cudaMemset(base + o_fac_begin, 0, total - o_fac_begin), "clear factors");
   if (rc == SP_OK) {
     int threads = 128, blocks = (2 * p->K + threads - 1) / threads;
-    sp::k_factor<<<blocks, threads>>>(p->fac_l, p->fac_iu, p->fac_cu, p->N, p->K, p->Kp);
+    if (precision == SP_FP64) {
+      sp::launch_factor<double>(sp::Launch{dim3(blocks), threads, 0, 0}, p->fac_l, p->fac_iu, p->fac_cu, p->N,
+                                p->K, p->Kp);
+    } else {
+      sp::launch_factor<float>(sp::Launch{dim3(blocks), threads, 0, 0}, p->f32_l, p->f32_iu, p->f32_cu, p->N,
+                               p->K, p->Kp);
+      sp::launch_factor<double>(sp::Launch{dim3(1), threads, 0, 0}, p->z_l, p->z_iu, p->z_cu, p->N, 1, 2);
+    }
     step(cudaGetLastError(), "k_factor launch");
     step(cudaDeviceSynchronize(), "k_factor");
   }
-  step(allow_all_smem<false>(p->row_smem, p->col_smem), "shared memory attribute");
-  step(allow_all_smem<true>(p->row_smem, p->col_smem), "shared memory attribute");
+  if (precision != SP_FP64 && rc == SP_OK) {
+    step(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking), "cudaStreamCreate(side)");
+    step(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
+    step(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming), "cudaEventCreate");
+  }
+  step(allow_all_smem(p->device), "shared memory attribute");
   if (rc != SP_OK) {
-    cudaFree(p->dev);
-    p->magic = 0;
-    delete p;
+    destroy_plan(p);
     return rc;
   }
   if (workspace_bytes) *workspace_bytes = p->ws_bytes;
@@ -464,8 +678,9 @@ int sphere_poisson_solve_noalloc(sp_plan_t plan, const double* f, double* u, voi
 int sphere_poisson_launch_count(sp_plan_t plan, int adjoint, int* launches) {
   if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
   if (!launches) return SP_ERR_NULL;
-  (void)adjoint;
-  *launches = kStages;
+  if (plan->precision == SP_FP64) *launches = kStages;
+  else if (plan->precision == SP_FP32) *launches = kStages + 3;
+  else *launches = adjoint ? 0 : kStages - 1 + 3 + (plan->sweeps + 1);
   return SP_OK;
 }
 
@@ -524,10 +739,9 @@ int sphere_poisson_destroy(sp_plan_t plan) {
   if (!plan) return SP_OK;
   if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
   release_events(plan);
-  cudaError_t e = cudaFree(plan->dev);
-  plan->magic = 0;
-  delete plan;
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFree(plan tables)");
+  destroy_plan(plan);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "sphere_poisson_destroy");
   return SP_OK;
 }
 
