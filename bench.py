@@ -114,14 +114,15 @@ def algorithmic_flops(n_theta: int, n_lambda: int) -> dict:
             "theta_inverse": cols, "rows_inverse": rows}
 
 
-def algorithmic_bytes(n_theta: int, n_lambda: int) -> dict:
+def algorithmic_bytes(n_theta: int, n_lambda: int, spec_elem: int = 16, table_elem: int = 8) -> dict:
     """Bytes each stage must move: its input and output arrays once (plus the
-    three factor tables of the eliminations)."""
+    three factor tables of the eliminations).  spec_elem = bytes of one complex
+    spectral value (16 in FP64 and double-float, 8 in FP32)."""
     N, n = n_theta, n_lambda
     Kp = (n // 2 + 2) // 2 * 2
     grid = 8.0 * N * n
-    spec = 16.0 * N * Kp
-    return {"rows_forward": grid + spec, "theta_forward": 2 * spec, "solve": 2 * spec + 24.0 * N * Kp,
+    spec = float(spec_elem) * N * Kp
+    return {"rows_forward": grid + spec, "theta_forward": 2 * spec, "solve": 2 * spec + 3.0 * table_elem * N * Kp,
             "theta_inverse": 2 * spec, "rows_inverse": spec + grid}
 
 
@@ -141,7 +142,7 @@ def run_ours(args):
     N, n = w.n_theta, w.n_lambda
     dev = torch.device("cuda", local)
     f, u_exact = w.make(device=dev)
-    plan = sp.Plan(N, n, device=dev)
+    plan = sp.Plan(N, n, args.precision, args.sweeps, device=dev)
     ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=dev)
     u = torch.empty_like(f)
     stream = torch.cuda.current_stream()
@@ -197,11 +198,15 @@ def run_ours(args):
 
     # roofline of the dominant stage
     flops = algorithmic_flops(N, n)
-    bytes_ = algorithmic_bytes(N, n)
+    if args.precision == "fp32":
+        bytes_ = algorithmic_bytes(N, n, 8, 4)
+    else:
+        bytes_ = algorithmic_bytes(N, n)
     dom = max(stage_ms, key=stage_ms.get)
     dom_ms = stage_ms[dom] / max(recorded, 1)
     achieved_gflops = flops[dom] / (dom_ms * 1e-3) / 1e9
     stage_share = {k: round(v / sum(stage_ms.values()), 4) for k, v in stage_ms.items()}
+    dtype_name = {"fp64": "f64", "fp32": "f32", "fp32_refine": "f32+df64"}[args.precision]
     peaks = {}
     if os.path.exists(PEAKS_FILE):
         peaks = json.load(open(PEAKS_FILE))
@@ -214,20 +219,26 @@ def run_ours(args):
     except Exception as exc:  # keep the bench line even if the probe fails
         fp64_peak = FP64_PEAK_GFLOPS_FALLBACK
         peak_src = f"earlier probe on this pool (live probe failed: {exc})"
-    roofline = {
-        "kernel": dom,
-        "bound": "alu",
-        "achieved": round(achieved_gflops / 1e3, 4),
-        "peak": round(fp64_peak / 1e3, 4),
-        "unit": "TFLOP/s",
-        "frac": round(achieved_gflops / fp64_peak, 4),
-        "peak_source": peak_src,
+    hbm_gbs = bytes_[dom] / (dom_ms * 1e-3) / 1e9
+    if args.precision == "fp32":
+        # FP32 transforms are bounded by HBM traffic, not arithmetic
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": round(hbm_gbs, 1), "peak": hbm_peak,
+                    "unit": "GB/s", "frac": round(hbm_gbs / hbm_peak, 4),
+                    "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)"}
+    else:
+        roofline = {"kernel": dom, "bound": "alu", "achieved": round(achieved_gflops / 1e3, 4),
+                    "peak": round(fp64_peak / 1e3, 4), "unit": "TFLOP/s",
+                    "frac": round(achieved_gflops / fp64_peak, 4), "peak_source": peak_src}
+        if args.precision == "fp32_refine":
+            roofline["note"] = ("double-float arithmetic on the FP32 pipes; achieved counts conventional "
+                                "FP64-equivalent flops against the FP64 pipe peak")
+    roofline.update({
         "traffic": None,
-        "hbm_achieved_gbs": round(bytes_[dom] / (dom_ms * 1e-3) / 1e9, 1),
+        "hbm_achieved_gbs": round(hbm_gbs, 1),
         "hbm_peak_gbs": hbm_peak,
         "stage_ms_per_solve": {k: round(v / max(recorded, 1), 4) for k, v in stage_ms.items()},
         "stage_share": stage_share,
-    }
+    })
 
     out = {
         "metric": METRIC,
@@ -240,10 +251,12 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": dtype_name,
         "data": "synthetic: seeded spherical-harmonic series (no dataset)",
         "config": {
-            "workload": f"{w.name}: FP64 solve, n_theta={N} x n_lambda={n} (DFS {2*N}x{n}), "
+            "precision": args.precision,
+            "refine_sweeps": args.sweeps if args.precision == "fp32_refine" else None,
+            "workload": f"{w.name}: {args.precision} solve, n_theta={N} x n_lambda={n} (DFS {2*N}x{n}), "
                         f"random SH series l<={w.lmax}, c~N(0,1)/(1+l)^2, seed {w.seed}",
             "dof_per_solve": dof,
             "dof_convention": "n_theta*n_lambda (= mn/2, the paper's); mn convention = 2x",
@@ -258,6 +271,8 @@ def run_ours(args):
                 "max_rel_err_vs_closed_form": e2e_err},
         "roofline": roofline,
     }
+    if not args.no_forms and args.precision == "fp64":
+        out["forms"] = measure_forms(sp, f, u_exact, u, N, n, dev, ms_step, args)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(f.cpu().numpy(), budget_s=args.cpu_budget)
     if world > 1:
@@ -265,6 +280,38 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def measure_forms(sp, f, u_exact, u64, N, n, dev, ms_fp64, args):
+    """The reduced-precision forms on the same input and device, timed the same
+    way, with their error against the FP64 solution and the closed form."""
+    import torch
+
+    ex = float(u_exact.abs().max())
+    res = {}
+    steps = max(5, min(args.steps, 50))
+    for prec, sweeps in [("fp32", 0), ("fp32_refine", 0), ("fp32_refine", 1), ("fp32_refine", 2)]:
+        plan = sp.Plan(N, n, prec, sweeps, device=dev)
+        ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=dev)
+        u = torch.empty_like(f)
+        for _ in range(3):
+            plan.solve(f, u, ws)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            plan.solve(f, u, ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        key = prec if prec == "fp32" else f"{prec}_sweeps{sweeps}"
+        res[key] = {"value": N * n / (ms * 1e-3), "unit": "DOF/s", "ms_per_step": ms,
+                    "speedup_vs_fp64": ms_fp64 / ms,
+                    "max_rel_err_vs_fp64": float((u - u64).abs().max()) / ex,
+                    "max_rel_err_vs_closed_form": float((u - u_exact).abs().max()) / ex,
+                    "gpu_launches_per_step": plan.launches()}
+        del plan, ws
+    return res
 
 
 def _oracle_sample(f_np, ks):
@@ -364,6 +411,9 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp32_refine"])
+    ap.add_argument("--sweeps", type=int, default=1)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

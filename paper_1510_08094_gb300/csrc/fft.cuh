@@ -71,10 +71,31 @@ template <> struct num<dd> {
 
 constexpr int kMaxStages = 16;
 
+// Unsigned division by an invariant divisor d (Granlund & Montgomery 1994,
+// "Division by invariant integers using multiplication", Fig. 4.1):
+// l = ceil(log2 d), m = floor(2^32 (2^l - d)/d) + 1, and then
+// n / d = (t + ((n - t) >> min(l,1))) >> max(l-1,0) with t = umulhi(m, n).
+struct FastDiv {
+  unsigned m, s1, s2;
+};
+__host__ inline FastDiv make_fastdiv(unsigned d) {
+  unsigned l = 0;
+  while ((1ull << l) < d) ++l;
+  unsigned long long m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+  return {(unsigned)m, l < 1 ? l : 1u, l > 1 ? l - 1 : 0u};
+}
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) {
+  unsigned t = __umulhi(f.m, n);
+  return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
 struct FftDesc {
   int L;
   int nstages;
   int radix[kMaxStages];
+  FastDiv div_L;               // n / L
+  FastDiv div_nb[kMaxStages];  // n / (L / R_s)
+  FastDiv div_ns[kMaxStages];  // n / (R_1 ... R_{s-1})
 };
 
 // ---------------------------------------------------------------------------
@@ -219,15 +240,16 @@ __device__ __forceinline__ void dft_any(cpx<T>* v, const cpx<T>* __restrict__ tw
 // ---------------------------------------------------------------------------
 template <int R, int DIR, typename T>
 __device__ __forceinline__ void fft_pass(cpx<T>* buf, int L, int nbatch, int Ns,
-                                         const cpx<T>* __restrict__ tw) {
+                                         const cpx<T>* __restrict__ tw, const FastDiv& dnb,
+                                         const FastDiv& dns) {
   const int nb = L / R;
   const int total = nb * nbatch;
   const int tstride_stage = L / (Ns * R);  // table step for w = exp(-2 pi i/(Ns R))
   const int tstride_R = L / R;
   for (int b = threadIdx.x; b < total; b += blockDim.x) {
-    const int batch = b / nb;
+    const int batch = (int)fdiv((unsigned)b, dnb);
     const int j = b - batch * nb;
-    const int g = j / Ns;
+    const int g = (int)fdiv((unsigned)j, dns);
     const int k = j - g * Ns;
     cpx<T>* base = buf + batch * L + g * Ns * R + k;
     cpx<T> v[R];
@@ -246,13 +268,15 @@ __device__ __forceinline__ void fft_pass(cpx<T>* buf, int L, int nbatch, int Ns,
       // output pair (a, R-a) is formed in a rolled loop over a and stored at once
       // (the butterfly's inputs are all in registers, so in-place is safe)
       constexpr int H = (R - 1) / 2;
-      cpx<T> p[H], q[H];
+      // p_b = x_b + x_{R-b} overwrites v[b], q_b = x_b - x_{R-b} overwrites v[R-b]
       cpx<T> y0 = v[0];
 #pragma unroll
       for (int bb = 1; bb <= H; ++bb) {
-        p[bb - 1] = v[bb] + v[R - bb];
-        q[bb - 1] = v[bb] - v[R - bb];
-        y0 = y0 + p[bb - 1];
+        cpx<T> pb = v[bb] + v[R - bb];
+        cpx<T> qb = v[bb] - v[R - bb];
+        v[bb] = pb;
+        v[R - bb] = qb;
+        y0 = y0 + pb;
       }
       const cpx<T> x0 = v[0];
       base[0] = y0;
@@ -266,10 +290,10 @@ __device__ __forceinline__ void fft_pass(cpx<T>* buf, int L, int nbatch, int Ns,
           if (ab >= R) ab -= R;                  // ab = a * bb mod R
           cpx<T> w = ldg_c(tw + ab * tstride_R);
           T c = w.re, sn = -w.im;                // w = exp(-2 pi i ab/R) = c - i sn
-          A.re = fma(c, p[bb - 1].re, A.re);
-          A.im = fma(c, p[bb - 1].im, A.im);
-          B.re = fma(sn, q[bb - 1].re, B.re);
-          B.im = fma(sn, q[bb - 1].im, B.im);
+          A.re = fma(c, v[bb].re, A.re);
+          A.im = fma(c, v[bb].im, A.im);
+          B.re = fma(sn, v[R - bb].re, B.re);
+          B.im = fma(sn, v[R - bb].im, B.im);
         }
         // y_a = A + DIR i B, y_{R-a} = A - DIR i B
         cpx<T> iB = DIR < 0 ? cpx<T>{B.im, -B.re} : cpx<T>{-B.im, B.re};
@@ -293,23 +317,23 @@ __device__ __forceinline__ void fft_run(cpx<T>* buf, int nbatch, const FftDesc& 
   for (int s = 0; s < d.nstages; ++s) {
     const int R = d.radix[s];
     switch (R) {
-      case 2: fft_pass<2, DIR>(buf, d.L, nbatch, Ns, tw); break;
-      case 3: fft_pass<3, DIR>(buf, d.L, nbatch, Ns, tw); break;
-      case 4: fft_pass<4, DIR>(buf, d.L, nbatch, Ns, tw); break;
-      case 5: fft_pass<5, DIR>(buf, d.L, nbatch, Ns, tw); break;
-      case 7: fft_pass<7, DIR>(buf, d.L, nbatch, Ns, tw); break;
-      case 8: fft_pass<8, DIR>(buf, d.L, nbatch, Ns, tw); break;
+      case 2: fft_pass<2, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
+      case 3: fft_pass<3, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
+      case 4: fft_pass<4, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
+      case 5: fft_pass<5, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
+      case 7: fft_pass<7, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
+      case 8: fft_pass<8, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
       default: break;
     }
     if constexpr (BIG) {
       switch (R) {
-      case 11: fft_pass<11, DIR>(buf, d.L, nbatch, Ns, tw); break;
-      case 13: fft_pass<13, DIR>(buf, d.L, nbatch, Ns, tw); break;
-      case 17: fft_pass<17, DIR>(buf, d.L, nbatch, Ns, tw); break;
-      case 19: fft_pass<19, DIR>(buf, d.L, nbatch, Ns, tw); break;
-      case 23: fft_pass<23, DIR>(buf, d.L, nbatch, Ns, tw); break;
-      case 29: fft_pass<29, DIR>(buf, d.L, nbatch, Ns, tw); break;
-      case 31: fft_pass<31, DIR>(buf, d.L, nbatch, Ns, tw); break;
+      case 11: fft_pass<11, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
+      case 13: fft_pass<13, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
+      case 17: fft_pass<17, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
+      case 19: fft_pass<19, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
+      case 23: fft_pass<23, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
+      case 29: fft_pass<29, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
+      case 31: fft_pass<31, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
       default: break;  // the host never builds other radices
       }
     }

@@ -8,16 +8,16 @@ namespace sp {
 template <>
 void launch_rows_forward<dd>(bool adj, bool big, const Launch& l, const double* f, cpx<dd>* W, int nt, int n,
                              int Kp, int rows, const FftDesc& d, const cpx<dd>* tw, const int* perm,
-                             const cpx<dd>* post, const double* row_scale, cpx<double>* zonal) {
+                             const cpx<dd>* post, const double* row_scale, const dd* row_scale_t, cpx<double>* zonal) {
   (void)adj;
-  SP_PICK_FWD(k_rows_forward, dd, big, f, W, nt, n, Kp, rows, d, tw, perm, post, row_scale, zonal);
+  SP_PICK_FWD(k_rows_forward, dd, big, f, W, nt, n, Kp, rows, d, tw, perm, post, row_scale, row_scale_t, zonal);
 }
 template <>
 void launch_rows_inverse<dd>(bool adj, bool big, const Launch& l, const cpx<dd>* W, double* u, int nt, int n,
                              int Kp, int rows, const FftDesc& d, const cpx<dd>* tw, const int* perm,
-                             const cpx<dd>* post, const double* row_scale, const cpx<double>* zonal) {
+                             const cpx<dd>* post, const double* row_scale, const dd* row_scale_t, const cpx<double>* zonal) {
   (void)adj;
-  SP_PICK_FWD(k_rows_inverse, dd, big, W, u, nt, n, Kp, rows, d, tw, perm, post, row_scale, zonal);
+  SP_PICK_FWD(k_rows_inverse, dd, big, W, u, nt, n, Kp, rows, d, tw, perm, post, row_scale, row_scale_t, zonal);
 }
 template <>
 void launch_theta_forward<dd>(bool adj, bool big, const Launch& l, cpx<dd>* W, int N, int K, int Kp, int cols,

@@ -7,15 +7,15 @@ template <>
 void launch_rows_forward<float>(bool adj, bool big, const Launch& l, const double* f, cpx<float>* W, int nt,
                                  int n, int Kp, int rows, const FftDesc& d, const cpx<float>* tw,
                                  const int* perm, const cpx<float>* post, const double* row_scale,
-                                 cpx<double>* zonal) {
-  SP_PICK(k_rows_forward, float, adj, big, f, W, nt, n, Kp, rows, d, tw, perm, post, row_scale, zonal);
+                                 const float* row_scale_t, cpx<double>* zonal) {
+  SP_PICK(k_rows_forward, float, adj, big, f, W, nt, n, Kp, rows, d, tw, perm, post, row_scale, row_scale_t, zonal);
 }
 template <>
 void launch_rows_inverse<float>(bool adj, bool big, const Launch& l, const cpx<float>* W, double* u, int nt,
                                  int n, int Kp, int rows, const FftDesc& d, const cpx<float>* tw,
                                  const int* perm, const cpx<float>* post, const double* row_scale,
-                                 const cpx<double>* zonal) {
-  SP_PICK(k_rows_inverse, float, adj, big, W, u, nt, n, Kp, rows, d, tw, perm, post, row_scale, zonal);
+                                 const float* row_scale_t, const cpx<double>* zonal) {
+  SP_PICK(k_rows_inverse, float, adj, big, W, u, nt, n, Kp, rows, d, tw, perm, post, row_scale, row_scale_t, zonal);
 }
 template <>
 void launch_theta_forward<float>(bool adj, bool big, const Launch& l, cpx<float>* W, int N, int K, int Kp,

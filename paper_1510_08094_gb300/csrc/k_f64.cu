@@ -7,15 +7,15 @@ template <>
 void launch_rows_forward<double>(bool adj, bool big, const Launch& l, const double* f, cpx<double>* W, int nt,
                                  int n, int Kp, int rows, const FftDesc& d, const cpx<double>* tw,
                                  const int* perm, const cpx<double>* post, const double* row_scale,
-                                 cpx<double>* zonal) {
-  SP_PICK(k_rows_forward, double, adj, big, f, W, nt, n, Kp, rows, d, tw, perm, post, row_scale, zonal);
+                                 const double* row_scale_t, cpx<double>* zonal) {
+  SP_PICK(k_rows_forward, double, adj, big, f, W, nt, n, Kp, rows, d, tw, perm, post, row_scale, row_scale_t, zonal);
 }
 template <>
 void launch_rows_inverse<double>(bool adj, bool big, const Launch& l, const cpx<double>* W, double* u, int nt,
                                  int n, int Kp, int rows, const FftDesc& d, const cpx<double>* tw,
                                  const int* perm, const cpx<double>* post, const double* row_scale,
-                                 const cpx<double>* zonal) {
-  SP_PICK(k_rows_inverse, double, adj, big, W, u, nt, n, Kp, rows, d, tw, perm, post, row_scale, zonal);
+                                 const double* row_scale_t, const cpx<double>* zonal) {
+  SP_PICK(k_rows_inverse, double, adj, big, W, u, nt, n, Kp, rows, d, tw, perm, post, row_scale, row_scale_t, zonal);
 }
 template <>
 void launch_theta_forward<double>(bool adj, bool big, const Launch& l, cpx<double>* W, int N, int K, int Kp,
@@ -61,6 +61,14 @@ void launch_solve<double>(bool adj, const Launch& l, cpx<double>* W, const doubl
 template <>
 void launch_factor<double>(const Launch& l, double* fl, double* fiu, double* fcu, int N, int K, int Kp) {
   k_factor<double><<<l.grid, l.threads, l.smem, l.stream>>>(fl, fiu, fcu, N, K, Kp);
+}
+
+void launch_zonal_scan(bool adj, cudaStream_t st, cpx<double>* Z, const double* zl, const double* ziu,
+                       const double* zcu, int N) {
+  const int threads = 512;
+  const size_t smem = threads * sizeof(AffineC);
+  if (adj) k_zonal_scan<true><<<1, threads, smem, st>>>(Z, zl, ziu, zcu, N);
+  else k_zonal_scan<false><<<1, threads, smem, st>>>(Z, zl, ziu, zcu, N);
 }
 
 }  // namespace sp

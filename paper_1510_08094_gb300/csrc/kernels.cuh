@@ -51,6 +51,25 @@ __device__ __forceinline__ dd split_double(double x) {
   return dd(hi, sign ? -lo : lo);
 }
 
+// Exact float -> double with integer operations only (a float is exactly a
+// double): rebias the exponent and widen the significand.  Subnormal floats
+// are taken as zero; infinities and NaNs are kept.
+__device__ __forceinline__ double float_to_double_int(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned sign = b & 0x80000000u;
+  const unsigned e = (b >> 23) & 0xffu;
+  const unsigned m = b & 0x7fffffu;
+  unsigned hi;
+  if (e == 0) hi = sign;                                       // zero (and subnormals)
+  else if (e == 0xffu) hi = sign | 0x7ff00000u | (m >> 3) | (m ? 0x80000u : 0u);
+  else hi = sign | ((e + 896u) << 20) | (m >> 3);
+  const unsigned lo = m << 29;
+  return __hiloint2double((int)hi, (int)(e == 0 ? 0u : lo));
+}
+
+// double -> float without the FP64 pipe: hi + lo of the integer split, rounded once
+__device__ __forceinline__ float double_to_float_int(double x);
+
 __device__ __forceinline__ dd warp_sum_dd(dd v) {
   for (int off = 16; off > 0; off >>= 1) {
     dd o(__shfl_down_sync(0xffffffffu, v.hi, off), __shfl_down_sync(0xffffffffu, v.lo, off));
@@ -60,6 +79,29 @@ __device__ __forceinline__ dd warp_sum_dd(dd v) {
 }
 
 // block-wide double-float sum (result valid in thread 0); all threads must call
+__device__ __forceinline__ float double_to_float_int(double x) {
+  dd s = split_double(x);
+  return __fadd_rn(s.hi, s.lo);
+}
+
+// input conversion of the transforms: double -> T without the FP64 pipe
+template <typename T> __device__ __forceinline__ T load_conv(double x);
+template <> __device__ __forceinline__ double load_conv<double>(double x) { return x; }
+template <> __device__ __forceinline__ float load_conv<float>(double x) { return double_to_float_int(x); }
+template <> __device__ __forceinline__ dd load_conv<dd>(double x) {
+  dd s = split_double(x);
+  float h = __fadd_rn(s.hi, s.lo);                 // renormalise the split
+  return dd(h, __fsub_rn(s.lo, __fsub_rn(h, s.hi)));
+}
+// output conversion T -> double (float: integer widening; double-float: two
+// widenings and one FP64 add)
+template <typename T> __device__ __forceinline__ double store_conv(T x);
+template <> __device__ __forceinline__ double store_conv<double>(double x) { return x; }
+template <> __device__ __forceinline__ double store_conv<float>(float x) { return float_to_double_int(x); }
+template <> __device__ __forceinline__ double store_conv<dd>(dd x) {
+  return float_to_double_int(x.hi) + float_to_double_int(x.lo);
+}
+
 __device__ __forceinline__ dd block_sum_dd(dd v) {
   __shared__ dd red_dd[32];
   v = warp_sum_dd(v);
@@ -84,11 +126,11 @@ __device__ __forceinline__ dd block_sum_dd(dd v) {
 // One CTA per `rows` consecutive rows; shared memory rows * L complex.
 // ---------------------------------------------------------------------------
 template <typename T, bool ADJ, bool BIG>
-__global__ void __launch_bounds__(512) k_rows_forward(
+__global__ void __launch_bounds__(BIG ? 256 : 512) k_rows_forward(
     const double* __restrict__ f, cpx<T>* __restrict__ W, int nt, int n, int Kp, int rows,
     FftDesc d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
     const cpx<T>* __restrict__ post, const double* __restrict__ row_scale,
-    cpx<double>* __restrict__ zonal) {
+    const T* __restrict__ row_scale_t, cpx<double>* __restrict__ zonal) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
   const int L = n >> 1;
@@ -96,11 +138,12 @@ __global__ void __launch_bounds__(512) k_rows_forward(
   for (int r = 0; r < rows; ++r) {
     const int row = row0 + r;
     dd acc(0.f, 0.f);
+#pragma unroll 4
     for (int q = threadIdx.x; q < L; q += blockDim.x) {
       cpx<T> z = {(T)0, (T)0};
       if (row < nt) {
         double2 v = __ldg(reinterpret_cast<const double2*>(f + (size_t)row * n) + q);
-        z = {num<T>::from_double(v.x), num<T>::from_double(v.y)};
+        z = {load_conv<T>(v.x), load_conv<T>(v.y)};
         if (zonal) acc = dd_add(acc, dd_add(split_double(v.x), split_double(v.y)));
       }
       sm[r * L + __ldg(perm + q)] = z;
@@ -118,10 +161,11 @@ __global__ void __launch_bounds__(512) k_rows_forward(
   __syncthreads();
   fft_run<-1, BIG>(sm, rows, d, tw);
   const int K = L + 1;
-  for (int idx = threadIdx.x; idx < rows * Kp; idx += blockDim.x) {
-    int r = idx / Kp, k = idx - r * Kp;
-    int row = row0 + r;
-    if (row >= nt) continue;
+  for (int r = 0; r < rows; ++r) {
+   const int row = row0 + r;
+   if (row >= nt) break;
+   const T rs = ADJ ? (T)1 : row_scale_t[row];
+   for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
     cpx<T> out = {(T)0, (T)0};
     if (k < K) {
       const cpx<T>* Z = sm + r * L;
@@ -133,10 +177,11 @@ __global__ void __launch_bounds__(512) k_rows_forward(
       out = {fma((T)0.5, t.im, s.re), fma((T)-0.5, t.re, s.im)};
       T scale;
       if (ADJ) scale = (k == 0 || k == L) ? (T)1 : (T)2;
-      else scale = num<T>::from_double(__ldg(row_scale + row));
+      else scale = rs;
       out = scale * out;
     }
     W[(size_t)row * Kp + k] = out;
+   }
   }
 }
 
@@ -150,18 +195,19 @@ __global__ void __launch_bounds__(512) k_rows_forward(
 //            after the transform (the FP64 side path's zonal column).
 // ---------------------------------------------------------------------------
 template <typename T, bool ADJ, bool BIG>
-__global__ void __launch_bounds__(512) k_rows_inverse(
+__global__ void __launch_bounds__(BIG ? 256 : 512) k_rows_inverse(
     const cpx<T>* __restrict__ W, double* __restrict__ u, int nt, int n, int Kp, int rows,
     FftDesc d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
     const cpx<T>* __restrict__ post, const double* __restrict__ row_scale,
-    const cpx<double>* __restrict__ zonal) {
+    const T* __restrict__ row_scale_t, const cpx<double>* __restrict__ zonal) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
   const int L = n >> 1;
   const int row0 = blockIdx.x * rows;
-  for (int idx = threadIdx.x; idx < rows * L; idx += blockDim.x) {
-    int r = idx / L, k = idx - r * L;
-    int row = row0 + r;
+  for (int r = 0; r < rows; ++r)
+#pragma unroll 2
+  for (int k = threadIdx.x; k < L; k += blockDim.x) {
+    const int row = row0 + r;
     cpx<T> z = {(T)0, (T)0};
     if (row < nt) {
       const cpx<T>* U = W + (size_t)row * Kp;
@@ -185,18 +231,24 @@ __global__ void __launch_bounds__(512) k_rows_inverse(
   }
   __syncthreads();
   fft_run<+1, BIG>(sm, rows, d, tw);
-  for (int idx = threadIdx.x; idx < rows * L; idx += blockDim.x) {
-    int r = idx / L, q = idx - r * L;
-    int row = row0 + r;
-    if (row >= nt) continue;
-    cpx<T> z = sm[idx];
-    double scale = ADJ ? __ldg(row_scale + row) : 1.0;
+  for (int r = 0; r < rows; ++r)
+  for (int q = threadIdx.x; q < L; q += blockDim.x) {
+    const int row = row0 + r;
+    if (row >= nt) break;
+    cpx<T> z = sm[r * L + q];
     double2 v;
-    if (zonal) {
-      double u0 = zonal[(size_t)row * 2].re;
-      v = {scale * (num<T>::to_double(z.re) + u0), scale * (num<T>::to_double(z.im) + u0)};
+    if constexpr (std::is_same<T, double>::value) {
+      double scale = ADJ ? __ldg(row_scale + row) : 1.0;
+      v = {scale * z.re, scale * z.im};
     } else {
-      v = {scale * num<T>::to_double(z.re), scale * num<T>::to_double(z.im)};
+      // reduced-precision forms: the zonal value is added, and the adjoint's row
+      // scale applied, in the transform's arithmetic before widening to double
+      if (zonal) {
+        T u0 = load_conv<T>(zonal[(size_t)row * 2].re);
+        z = {z.re + u0, z.im + u0};
+      }
+      if (ADJ) z = row_scale_t[row] * z;
+      v = {store_conv<T>(z.re), store_conv<T>(z.im)};
     }
     reinterpret_cast<double2*>(u + (size_t)row * n)[q] = v;
   }
@@ -215,15 +267,17 @@ __global__ void __launch_bounds__(512) k_rows_inverse(
 // One CTA per `cols` consecutive columns.  inv_n = 1/N in arithmetic T.
 // ---------------------------------------------------------------------------
 template <typename T, bool ADJ, bool BIG>
-__global__ void __launch_bounds__(512) k_theta_forward(
+__global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_forward(
     cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d,
     const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
     T inv_n, int zonal) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
   const int k0 = blockIdx.x * cols;
+  const int cs = __ffs(cols) - 1;            // cols is a power of two
+#pragma unroll 4
   for (int idx = threadIdx.x; idx < N * cols; idx += blockDim.x) {
-    int i = idx / cols, c = idx - i * cols;
+    int i = idx >> cs, c = idx & (cols - 1);
     int k = k0 + c;
     cpx<T> v = {(T)0, (T)0};
     if (k < K) {
@@ -235,7 +289,7 @@ __global__ void __launch_bounds__(512) k_theta_forward(
   __syncthreads();
   fft_run<-1, BIG>(sm, cols, d, tw);
   for (int idx = threadIdx.x; idx < N * cols; idx += blockDim.x) {
-    int j = idx / cols, c = idx - j * cols;
+    int j = idx >> cs, c = idx & (cols - 1);
     int k = k0 + c;
     if (k >= K) continue;
     const cpx<T>* V = sm + c * N;
@@ -284,7 +338,7 @@ __global__ void __launch_bounds__(512) k_theta_forward(
 //            transpose of theta_forward
 // ---------------------------------------------------------------------------
 template <typename T, bool ADJ, bool BIG>
-__global__ void __launch_bounds__(512) k_theta_inverse(
+__global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_inverse(
     cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d,
     const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
     T inv_n, int zonal) {
@@ -316,8 +370,10 @@ __global__ void __launch_bounds__(512) k_theta_inverse(
   // pre-twiddle straight from global memory, one thread per pair (j, N - j),
   // j = 0 .. N/2, writing V_j and V_{N-j} to their digit-reversed slots
   const int H = N / 2 + 1;
+  const int cs = __ffs(cols) - 1;            // cols is a power of two
+#pragma unroll 2
   for (int idx = threadIdx.x; idx < H * cols; idx += blockDim.x) {
-    int j = idx / cols, c = idx - j * cols;
+    int j = idx >> cs, c = idx & (cols - 1);
     int k = k0 + c;
     cpx<T>* V = sm + c * N;
     const bool odd = (k & 1);
@@ -350,7 +406,7 @@ __global__ void __launch_bounds__(512) k_theta_inverse(
   __syncthreads();
   fft_run<+1, BIG>(sm, cols, d, tw);
   for (int idx = threadIdx.x; idx < N * cols; idx += blockDim.x) {
-    int i = idx / cols, c = idx - i * cols;
+    int i = idx >> cs, c = idx & (cols - 1);
     int k = k0 + c;
     if (k >= K) continue;
     cpx<T> v = sm[c * N + makhoul_pos(i, N)];
@@ -586,6 +642,123 @@ __global__ void __launch_bounds__(32) k_solve(cpx<S>* __restrict__ W, const S* _
   }
 }
 
+// ---------------------------------------------------------------------------
+// Zonal column (k = 0) eliminations in FP64 with a parallel scan.  The two
+// parity chains (threads [0, T/2) odd, [T/2, T) even) are each a sequence of
+// first-order recurrences x_t = alpha_t x_{t-1} + beta_t (ascending) or
+// x_t = alpha_t x_{t+1} + beta_t (descending).  Each thread owns a contiguous
+// segment of the chain: it composes its segment's affine map (alpha product
+// and the image of 0), the maps are combined across the half-block by a
+// Hillis-Steele scan in shared memory, and each thread then re-runs its
+// segment from the correct incoming value.  Same arithmetic results as the
+// sequential sweeps up to rounding order; used where one sequential chain
+// would be the critical path (the FP32 forms' FP64 zonal column).
+// ---------------------------------------------------------------------------
+struct AffineC {
+  double a;          // multiplier
+  cpx<double> b;     // offset
+};
+
+// combine: first `lo` (earlier segment), then `hi`: x -> hi.a (lo.a x + lo.b) + hi.b
+__device__ __forceinline__ AffineC affine_then(AffineC lo, AffineC hi) {
+  return {hi.a * lo.a, {fma(hi.a, lo.b.re, hi.b.re), fma(hi.a, lo.b.im, hi.b.im)}};
+}
+
+// inclusive scan of one affine map per thread over each half of the block;
+// returns the composition of all earlier segments (exclusive prefix) of this half
+__device__ __forceinline__ AffineC half_block_exclusive_scan(AffineC mine, AffineC* sh) {
+  const int half = blockDim.x >> 1;
+  const int h = threadIdx.x >= half;
+  const int i = threadIdx.x - h * half;
+  AffineC* arr = sh + h * half;
+  arr[i] = mine;
+  __syncthreads();
+  for (int off = 1; off < half; off <<= 1) {
+    AffineC cur = arr[i];
+    AffineC prev = i >= off ? arr[i - off] : AffineC{1.0, {0.0, 0.0}};
+    __syncthreads();
+    arr[i] = affine_then(prev, cur);
+    __syncthreads();
+  }
+  AffineC ex = i > 0 ? arr[i - 1] : AffineC{1.0, {0.0, 0.0}};
+  __syncthreads();
+  return ex;
+}
+
+// Z [N][2] column 0: forward (ADJ = false) or transposed (ADJ = true) k = 0
+// eliminations with the FP64 factors zl, ziu, zcu ([N][2] layout).  Launch
+// one CTA with an even number of threads and (threads) AffineC of dynamic
+// shared memory.  Row 0 (the closure) is left to the caller's k = 0 closure.
+template <bool ADJ>
+__global__ void __launch_bounds__(512) k_zonal_scan(cpx<double>* __restrict__ Z, const double* __restrict__ zl,
+                                                    const double* __restrict__ ziu,
+                                                    const double* __restrict__ zcu, int N) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  AffineC* sh = reinterpret_cast<AffineC*>(smem_raw);
+  const int half = blockDim.x >> 1;
+  const bool even = threadIdx.x >= half;
+  const int i = threadIdx.x - (even ? half : 0);
+  const int j0 = even ? 2 : 1;
+  const int M = j0 < N ? (N - 1 - j0) / 2 + 1 : 0;
+  const int seg = (M + half - 1) / half;
+  const int t_begin = min(M, i * seg), t_end = min(M, t_begin + seg);
+  auto row = [&](int t) { return (size_t)(j0 + 2 * t) * 2; };
+  // transposed k = 0 closure: Fbar_0 = 0 (its Xbar_0 terms were added by theta_forward)
+  if (ADJ && threadIdx.x == 0) Z[0] = {0.0, 0.0};
+  // ---- ascending sweep ----
+  // forward:  y_t = -l_t y_{t-1} + d_t
+  // adjoint:  z_t = -(c_{t-1} u_t^{-1}) z_{t-1} + b_t u_t^{-1}
+  auto up_alpha = [&](int t) -> double {
+    if (!ADJ) return -zl[row(t)];
+    if (t == 0) return 0.0;
+    const int j = j0 + 2 * t;
+    return -((double)((j - 1) * j) * 0.25) * ziu[row(t)];
+  };
+  auto up_beta = [&](int t) -> cpx<double> {
+    cpx<double> v = Z[row(t)];
+    if (!ADJ) return v;
+    return ziu[row(t)] * v;
+  };
+  AffineC m = {1.0, {0.0, 0.0}};
+  for (int t = t_begin; t < t_end; ++t) m = affine_then(m, AffineC{up_alpha(t), up_beta(t)});
+  AffineC ex = half_block_exclusive_scan(m, sh);
+  cpx<double> x = ex.b;  // value entering this segment (chain starts from 0)
+  for (int t = t_begin; t < t_end; ++t) {
+    double a = up_alpha(t);
+    cpx<double> b = up_beta(t);
+    x = {fma(a, x.re, b.re), fma(a, x.im, b.im)};
+    Z[row(t)] = x;
+  }
+  __syncthreads();
+  // ---- descending sweep (segments mirrored: thread i takes rows from the end) ----
+  // forward:  x_t = -(c_t/u_t) x_{t+1} + y_t / u_t
+  // adjoint:  y_t = -l_{t+1} y_{t+1} + z_t
+  auto dn_alpha = [&](int t) -> double {
+    if (!ADJ) return -zcu[row(t)];
+    return t + 1 < M ? -zl[row(t + 1)] : 0.0;
+  };
+  auto dn_beta = [&](int t) -> cpx<double> {
+    cpx<double> v = Z[row(t)];
+    if (!ADJ) return ziu[row(t)] * v;
+    return v;
+  };
+  const int r_begin = min(M, i * seg), r_end = min(M, r_begin + seg);   // r = M-1-t
+  m = {1.0, {0.0, 0.0}};
+  for (int r = r_begin; r < r_end; ++r) {
+    const int t = M - 1 - r;
+    m = affine_then(m, AffineC{dn_alpha(t), dn_beta(t)});
+  }
+  ex = half_block_exclusive_scan(m, sh);
+  x = ex.b;
+  for (int r = r_begin; r < r_end; ++r) {
+    const int t = M - 1 - r;
+    double a = dn_alpha(t);
+    cpx<double> b = dn_beta(t);
+    x = {fma(a, x.re, b.re), fma(a, x.im, b.im)};
+    Z[row(t)] = x;
+  }
+}
+
 #ifdef SP_REFINE_KERNELS  // defined only in the double-float translation unit
 // ---------------------------------------------------------------------------
 // Iterative refinement of the per-k eliminations (FP32 + refinement form).
@@ -598,10 +771,10 @@ __global__ void __launch_bounds__(32) k_solve(cpx<S>* __restrict__ W, const S* _
 // The even chain also sets the row 0 closure X_0 = (X_2 - F_0)/k^2 (k even),
 // X_0 = 0 (k odd).  Column k = 0 is left to the FP64 zonal path.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ dd dd_of_int(long long v) {
-  float h = (float)v;
-  float l = (float)(v - (long long)h);
-  return dd(h, l);
+// exact product of two floats holding integers, as double-float (TwoProduct)
+__device__ __forceinline__ dd dd_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return dd(p, __fmaf_rn(a, b, -p));
 }
 __device__ __forceinline__ cpx<dd> cdd_scale(dd s, cpx<dd> x) { return {dd_mul(s, x.re), dd_mul(s, x.im)}; }
 
@@ -632,7 +805,8 @@ __global__ void __launch_bounds__(32) k_refine(const cpx<dd>* __restrict__ F, cp
   const int k = blockIdx.x * 32 + lane;
   if (k >= K || k == 0) return;
   const int j0 = even ? 2 : 1;
-  const long long k2 = (long long)k * k;
+  const float kf = (float)k;
+  const dd two_k2 = dd_mul(dd_prod(kf, kf), dd(2.f, 0.f));   // 2 k^2, exact
   if (j0 < N) {
     const int M = (N - 1 - j0) / 2 + 1;
     const size_t stride = (size_t)2 * Kp;
@@ -656,7 +830,8 @@ __global__ void __launch_bounds__(32) k_refine(const cpx<dd>* __restrict__ F, cp
     cpx<dd> x0 = {dd(0.f, 0.f), dd(0.f, 0.f)};
     if (!first) x0 = X[base];
     cpx<float> y = {0.f, 0.f};
-    for (int t = 0; t < M; ++t) {
+    float jf = (float)j0;                       // j of row t, exact in float
+    for (int t = 0; t < M; ++t, jf += 2.f) {
       cp_wait<kRefRing - 1>();
       const RefSlot& sl = ring.up[t & (kRefRing - 1)];
       cpx<dd> r = sl.f[lane];
@@ -664,10 +839,13 @@ __global__ void __launch_bounds__(32) k_refine(const cpx<dd>* __restrict__ F, cp
       cpx<dd> xp1 = {dd(0.f, 0.f), dd(0.f, 0.f)};
       if (!first) {
         if (t + 1 < M) xp1 = sl.x[lane];
-        const long long j = j0 + 2 * t;
-        dd a = dd_mul(dd_of_int((j - 1) * (j - 2)), dd(0.25f, 0.f));
-        dd b = dd_mul(dd_of_int(j * j + 2 * k2), dd(-0.5f, 0.f));
-        dd c = dd_mul(dd_of_int((j + 1) * (j + 2)), dd(0.25f, 0.f));
+        // exact coefficients: a = (j-1)(j-2)/4, b = -(j^2 + 2k^2)/2, c = (j+1)(j+2)/4
+        dd a = dd_prod(jf - 1.f, jf - 2.f);
+        a = dd(a.hi * 0.25f, a.lo * 0.25f);
+        dd b = dd_add(dd_prod(jf, jf), two_k2);
+        b = dd(b.hi * -0.5f, b.lo * -0.5f);
+        dd c = dd_prod(jf + 1.f, jf + 2.f);
+        c = dd(c.hi * 0.25f, c.lo * 0.25f);
         cpx<dd> lx = cdd_scale(b, x0);
         lx = {dd_fma(a, xm1.re, lx.re), dd_fma(a, xm1.im, lx.im)};
         lx = {dd_fma(c, xp1.re, lx.re), dd_fma(c, xp1.im, lx.im)};
@@ -720,7 +898,7 @@ __global__ void __launch_bounds__(32) k_refine(const cpx<dd>* __restrict__ F, cp
       __threadfence();
       cpx<dd> x2 = (2 < N) ? X[(size_t)2 * Kp + k] : cpx<dd>{dd(0.f, 0.f), dd(0.f, 0.f)};
       cpx<dd> f0 = F[k];
-      dd ik2 = dd_from_double(1.0 / (double)k2);
+      dd ik2 = dd_from_double(1.0 / ((double)k * (double)k));
       x0v = {dd_mul(dd_sub(x2.re, f0.re), ik2), dd_mul(dd_sub(x2.im, f0.im), ik2)};
     }
     X[k] = x0v;

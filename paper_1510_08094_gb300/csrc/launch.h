@@ -20,11 +20,13 @@ struct Launch {
 template <typename T>
 void launch_rows_forward(bool adj, bool big, const Launch& l, const double* f, cpx<T>* W, int nt, int n,
                          int Kp, int rows, const FftDesc& d, const cpx<T>* tw, const int* perm,
-                         const cpx<T>* post, const double* row_scale, cpx<double>* zonal);
+                         const cpx<T>* post, const double* row_scale, const T* row_scale_t,
+                         cpx<double>* zonal);
 template <typename T>
 void launch_rows_inverse(bool adj, bool big, const Launch& l, const cpx<T>* W, double* u, int nt, int n,
                          int Kp, int rows, const FftDesc& d, const cpx<T>* tw, const int* perm,
-                         const cpx<T>* post, const double* row_scale, const cpx<double>* zonal);
+                         const cpx<T>* post, const double* row_scale, const T* row_scale_t,
+                         const cpx<double>* zonal);
 template <typename T>
 void launch_theta_forward(bool adj, bool big, const Launch& l, cpx<T>* W, int N, int K, int Kp, int cols,
                           const FftDesc& d, const cpx<T>* tw, const int* perm, const cpx<T>* post, T inv_n,
@@ -42,6 +44,10 @@ void launch_solve(bool adj, const Launch& l, cpx<S>* W, const S* fl, const S* fi
                   int Kp);
 template <typename S>
 void launch_factor(const Launch& l, S* fl, S* fiu, S* fcu, int N, int K, int Kp);
+
+// FP64 zonal-column eliminations by parallel scan (one CTA)
+void launch_zonal_scan(bool adj, cudaStream_t st, cpx<double>* Z, const double* zl, const double* ziu,
+                       const double* zcu, int N);
 
 void launch_refine(const Launch& l, const cpx<dd>* F, cpx<dd>* X, cpx<float>* Y, const float* fl,
                    const float* fiu, const float* fcu, int N, int K, int Kp, int first);

@@ -58,16 +58,29 @@ bool make_fft_desc(int L, FftDesc* d) {
   for (int p : primes)
     while (rest % p == 0) if (!push(p)) return false;
   d->nstages = s;
+  d->div_L = sp::make_fastdiv((unsigned)L);
+  int ns = 1;
+  for (int t = 0; t < s; ++t) {
+    d->div_nb[t] = sp::make_fastdiv((unsigned)(L / d->radix[t]));
+    d->div_ns[t] = sp::make_fastdiv((unsigned)ns);
+    ns *= d->radix[t];
+  }
   return rest == 1;
 }
 
 // threads for a CTA that transforms nbatch sequences of the plan's length:
-// about one butterfly of the smallest radix per thread, 64 .. 512
+// about one butterfly of the smallest radix per thread, 64 .. 512 (64 .. 256
+// for the large-prime kernels, whose launch bound is 256 threads)
 int fft_threads(const FftDesc& d, int nbatch) {
   int rmin = 32;
-  for (int s = 0; s < d.nstages; ++s) rmin = d.radix[s] < rmin ? d.radix[s] : rmin;
+  bool big = false;
+  for (int s = 0; s < d.nstages; ++s) {
+    rmin = d.radix[s] < rmin ? d.radix[s] : rmin;
+    big = big || d.radix[s] > 8;
+  }
+  const long cap = big ? 256 : 512;
   long want = (long)nbatch * d.L / rmin;
-  int t = (int)(want < 64 ? 64 : (want > 512 ? 512 : want));
+  int t = (int)(want < 64 ? 64 : (want > cap ? cap : want));
   return (t + 31) / 32 * 32;
 }
 
@@ -133,6 +146,7 @@ struct sp_plan_s {
   int* perm_row;         // digit reversal of the length-L passes
   int* perm_col;         // digit reversal of the length-N passes
   double* row_scale;     // sin^2(theta_i)/n
+  void* row_scale_t;     // the same in float (SP_FP32) or double-float (SP_FP32_REFINE)
   // the same tables in float (SP_FP32) or double-float (SP_FP32_REFINE)
   void* tw_row_t;
   void* tw_col_t;
@@ -207,7 +221,8 @@ void enqueue_fp64(sp_plan_t p, bool adj, const double* in, double* out, void* ws
   const double inv_n = 1.0 / (double)p->N;
   m.mark(0);
   sp::launch_rows_forward<double>(adj, p->big_row, rows, in, W, p->nt, p->nl, p->Kp, p->rows_per_cta,
-                                  p->row_fft, p->tw_row, p->perm_row, p->post_row, p->row_scale, nullptr);
+                                  p->row_fft, p->tw_row, p->perm_row, p->post_row, p->row_scale, p->row_scale,
+                                  nullptr);
   m.mark(1);
   sp::launch_theta_forward<double>(adj, p->big_col, cols, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
                                    p->tw_col, p->perm_col, p->post_col, inv_n, 1);
@@ -218,7 +233,8 @@ void enqueue_fp64(sp_plan_t p, bool adj, const double* in, double* out, void* ws
                                    p->tw_col, p->perm_col, p->post_col, inv_n, 1);
   m.mark(4);
   sp::launch_rows_inverse<double>(adj, p->big_row, rows, W, out, p->nt, p->nl, p->Kp, p->rows_per_cta,
-                                  p->row_fft, p->tw_row, p->perm_row, p->post_row, p->row_scale, nullptr);
+                                  p->row_fft, p->tw_row, p->perm_row, p->post_row, p->row_scale, p->row_scale,
+                                  nullptr);
   m.mark(5);
   m.done();
 }
@@ -229,7 +245,7 @@ void enqueue_zonal_fp64(sp_plan_t p, bool adj, cpx<double>* Z, cudaStream_t st) 
   const sp::Launch one{dim3(1), p->zcol_threads, p->zcol_smem, st};
   sp::launch_theta_forward<double>(adj, p->big_col, one, Z, p->N, 1, 2, 1, p->col_fft, p->tw_col, p->perm_col,
                                    p->post_col, inv_n, 1);
-  sp::launch_solve<double>(adj, sp::Launch{dim3(1, 2), 32, 0, st}, Z, p->z_l, p->z_iu, p->z_cu, p->N, 1, 2);
+  sp::launch_zonal_scan(adj, st, Z, p->z_l, p->z_iu, p->z_cu, p->N);
   sp::launch_theta_inverse<double>(adj, p->big_col, one, Z, p->N, 1, 2, 1, p->col_fft, p->tw_col, p->perm_col,
                                    p->post_col, inv_n, 1);
 }
@@ -249,7 +265,8 @@ void enqueue_fp32(sp_plan_t p, bool adj, const double* in, double* out, void* ws
   const cpx<float>* poc = static_cast<const cpx<float>*>(p->post_col_t);
   m.mark(0);
   sp::launch_rows_forward<float>(adj, p->big_row, rows, in, W, p->nt, p->nl, p->Kp, p->rows_per_cta,
-                                 p->row_fft, twr, p->perm_row, por, p->row_scale, Z);
+                                 p->row_fft, twr, p->perm_row, por, p->row_scale,
+                                 static_cast<const float*>(p->row_scale_t), Z);
   cudaEventRecord(p->ev_fork, st);
   cudaStreamWaitEvent(p->side, p->ev_fork, 0);
   enqueue_zonal_fp64(p, adj, Z, p->side);
@@ -265,7 +282,8 @@ void enqueue_fp32(sp_plan_t p, bool adj, const double* in, double* out, void* ws
   cudaStreamWaitEvent(st, p->ev_join, 0);
   m.mark(4);
   sp::launch_rows_inverse<float>(adj, p->big_row, rows, W, out, p->nt, p->nl, p->Kp, p->rows_per_cta,
-                                 p->row_fft, twr, p->perm_row, por, p->row_scale, Z);
+                                 p->row_fft, twr, p->perm_row, por, p->row_scale,
+                                 static_cast<const float*>(p->row_scale_t), Z);
   m.mark(5);
   m.done();
 }
@@ -289,7 +307,8 @@ void enqueue_refine(sp_plan_t p, const double* in, double* out, void* ws, cudaSt
   const cpx<dd>* poc = static_cast<const cpx<dd>*>(p->post_col_t);
   m.mark(0);
   sp::launch_rows_forward<dd>(false, p->big_row, rows, in, Fd, p->nt, p->nl, p->Kp, p->rows_per_cta,
-                              p->row_fft, twr, p->perm_row, por, p->row_scale, nullptr);
+                              p->row_fft, twr, p->perm_row, por, p->row_scale,
+                              static_cast<const dd*>(p->row_scale_t), nullptr);
   m.mark(1);
   sp::launch_theta_forward<dd>(false, p->big_col, cols, Fd, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
                                twc, p->perm_col, poc, inv_n, 0);
@@ -298,7 +317,7 @@ void enqueue_refine(sp_plan_t p, const double* in, double* out, void* ws, cudaSt
   {
     const int zt = 256;
     sp::launch_zonal_extract(Launch{dim3((p->N + zt - 1) / zt), zt, 0, p->side}, Fd, Z, p->N, p->Kp);
-    sp::launch_solve<double>(false, Launch{dim3(1, 2), 32, 0, p->side}, Z, p->z_l, p->z_iu, p->z_cu, p->N, 1, 2);
+    sp::launch_zonal_scan(false, p->side, Z, p->z_l, p->z_iu, p->z_cu, p->N);
     sp::launch_zonal_insert(Launch{dim3(1), 512, 0, p->side}, Z, Xd, p->N, p->Kp);
   }
   cudaEventRecord(p->ev_join, p->side);
@@ -311,7 +330,8 @@ void enqueue_refine(sp_plan_t p, const double* in, double* out, void* ws, cudaSt
                                twc, p->perm_col, poc, inv_n, 0);
   m.mark(4);
   sp::launch_rows_inverse<dd>(false, p->big_row, rows, Xd, out, p->nt, p->nl, p->Kp, p->rows_per_cta,
-                              p->row_fft, twr, p->perm_row, por, p->row_scale, nullptr);
+                              p->row_fft, twr, p->perm_row, por, p->row_scale,
+                              static_cast<const dd*>(p->row_scale_t), nullptr);
   m.mark(5);
   m.done();
 }
@@ -466,13 +486,17 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
     unit_root(2 * i + 1, 4L * p->N, &re, &im);  // sin(theta_i) = -im
     row_scale[i] = (im * im) / (double)n_lambda;
   }
-  std::vector<char> t_tw_row, t_tw_col, t_post_row, t_post_col;
+  std::vector<char> t_tw_row, t_tw_col, t_post_row, t_post_col, t_scale;
   if (precision == SP_FP32) {
+    t_scale.resize(p->nt * sizeof(float));
+    for (int i = 0; i < p->nt; ++i) reinterpret_cast<float*>(t_scale.data())[i] = (float)row_scale[i];
     upload_table<float>(tw_row, t_tw_row);
     upload_table<float>(tw_col, t_tw_col);
     upload_table<float>(post_row, t_post_row);
     upload_table<float>(post_col, t_post_col);
   } else if (precision == SP_FP32_REFINE) {
+    t_scale.resize(p->nt * sizeof(sp::dd));
+    for (int i = 0; i < p->nt; ++i) reinterpret_cast<sp::dd*>(t_scale.data())[i] = sp::dd(row_scale[i]);
     upload_table<sp::dd>(tw_row, t_tw_row);
     upload_table<sp::dd>(tw_col, t_tw_col);
     upload_table<sp::dd>(post_row, t_post_row);
@@ -491,6 +515,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   size_t o_perm_row = take(p->L * sizeof(int)), o_perm_col = take(p->N * sizeof(int));
   size_t o_t_tw_row = take(t_tw_row.size()), o_t_tw_col = take(t_tw_col.size());
   size_t o_t_post_row = take(t_post_row.size()), o_t_post_col = take(t_post_col.size());
+  size_t o_t_scale = take(t_scale.size());
   const size_t fac64 = precision == SP_FP64 ? grid * sizeof(double) : 0;
   const size_t fac32 = precision == SP_FP64 ? 0 : grid * sizeof(float);
   const size_t facz = precision == SP_FP64 ? 0 : (size_t)p->N * 2 * sizeof(double);
@@ -522,6 +547,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   p->tw_col_t = base + o_t_tw_col;
   p->post_row_t = base + o_t_post_row;
   p->post_col_t = base + o_t_post_col;
+  p->row_scale_t = base + o_t_scale;
   p->fac_l = reinterpret_cast<double*>(base + o_l);
   p->fac_iu = reinterpret_cast<double*>(base + o_iu);
   p->fac_cu = reinterpret_cast<double*>(base + o_cu);
@@ -547,6 +573,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   up(p->tw_col_t, t_tw_col.data(), t_tw_col.size(), "copy tw_col_t");
   up(p->post_row_t, t_post_row.data(), t_post_row.size(), "copy post_row_t");
   up(p->post_col_t, t_post_col.data(), t_post_col.size(), "copy post_col_t");
+  up(p->row_scale_t, t_scale.data(), t_scale.size(), "copy row_scale_t");
   step(cudaMemset(base + o_fac_begin, 0, total - o_fac_begin), "clear factors");
   if (rc == SP_OK) {
     int threads = 128, blocks = (2 * p->K + threads - 1) / threads;
