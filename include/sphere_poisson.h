@@ -75,6 +75,31 @@ typedef struct sp_plan_s* sp_plan_t;
 int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precision,
                         int refine_sweeps, unsigned flags, size_t* workspace_bytes);
 
+/*
+ * Batched plan: `count` independent spheres of uneven resolution, problem b on
+ * an n_theta[b] x n_lambda[b] grid (each size obeying the rules above), solved
+ * together in ONE persistent kernel launch: every CTA repeatedly claims the
+ * next problem (largest first) from an atomic counter and runs all stages of
+ * that problem itself, with the spectrum in its own scratch slot.  Problem
+ * sizes share tables.  f and u of the solve calls are then the problems'
+ * [n_theta][n_lambda] arrays packed back to back in problem order, problem b
+ * starting at offsets[b] doubles (sphere_poisson_batch_offsets).
+ *   precision   SP_FP64.
+ *   flags       0, or SP_FLAG_AUTOTUNE: time the transform tiles (rows / columns
+ *               per CTA pass) of every problem size at plan time and keep the
+ *               fastest; results are cached in the file named by the
+ *               environment variable SPHERE_POISSON_TUNE_CACHE if it is set.
+ * count = 0 gives a plan whose solve does nothing.  The batched plan supports
+ * sphere_poisson_solve (and _solve_host); the adjoint returns SP_ERR_UNSUPPORTED.
+ * The solve issues one cudaMemsetAsync (the work counter) and one kernel.
+ */
+#define SP_FLAG_AUTOTUNE 1u
+int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, const int* n_lambda,
+                                int precision, int refine_sweeps, unsigned flags, size_t* workspace_bytes);
+
+/* offsets[0..count]: start of problem b in the packed arrays (doubles); offsets[count] = total. */
+int sphere_poisson_batch_offsets(sp_plan_t plan, size_t* offsets);
+
 /* Device workspace size of a plan (bytes). */
 int sphere_poisson_workspace_size(sp_plan_t plan, size_t* workspace_bytes);
 

@@ -26,7 +26,7 @@ from ._lib import (  # noqa: F401
     library_path,
 )
 
-__all__ = ["Plan", "solve", "solve_adjoint", "poisson", "SpherePoisson", "SpherePoissonError", "get_plan"]
+__all__ = ["Plan", "BatchedPlan", "solve", "solve_adjoint", "poisson", "SpherePoisson", "SpherePoissonError", "get_plan"]
 
 _PRECISIONS = {"fp64": SP_FP64, "fp32": SP_FP32, "fp32_refine": SP_FP32_REFINE}
 
@@ -175,6 +175,67 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class BatchedPlan(Plan):
+    """Many independent spheres of uneven resolution solved in one persistent launch.
+
+    sizes: sequence of (n_theta, n_lambda).  The solve takes and returns the
+    problems' grids packed back to back in one float64 CUDA tensor (see
+    `offsets`, `pack`, `unpack`).  autotune=True times the transform tiles of
+    every size at plan time (cached in $SPHERE_POISSON_TUNE_CACHE if set)."""
+
+    def __init__(self, sizes, precision: str = "fp64", refine_sweeps: int = 0, autotune: bool = False,
+                 device=None):
+        lib = _lib.load()
+        if precision not in _PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(_PRECISIONS)}")
+        sizes = [(int(a), int(b)) for a, b in sizes]
+        self.sizes = sizes
+        self.precision = precision
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        cnt = len(sizes)
+        nts = (ctypes.c_int * max(cnt, 1))(*[a for a, _ in sizes])
+        nls = (ctypes.c_int * max(cnt, 1))(*[b for _, b in sizes])
+        h = ctypes.c_void_p()
+        ws = ctypes.c_size_t()
+        flags = _lib.SP_FLAG_AUTOTUNE if autotune else 0
+        with torch.cuda.device(self.device):
+            _lib.check(lib.sphere_poisson_plan_batched(ctypes.byref(h), cnt, nts, nls, _PRECISIONS[precision],
+                                                       int(refine_sweeps), flags, ctypes.byref(ws)),
+                       "sphere_poisson_plan_batched")
+        self._h = h
+        self._lib = lib
+        self._ws = None
+        self.workspace_bytes = int(ws.value)
+        offs = (ctypes.c_size_t * (cnt + 1))()
+        _lib.check(lib.sphere_poisson_batch_offsets(h, offs), "sphere_poisson_batch_offsets")
+        self.offsets = [int(offs[i]) for i in range(cnt + 1)]
+        self.n_theta, self.n_lambda = 1, self.offsets[-1]
+
+    @property
+    def shape(self):
+        return (self.offsets[-1],)
+
+    def pack(self, grids):
+        """One packed float64 tensor from per-problem [n_theta, n_lambda] tensors."""
+        if len(grids) != len(self.sizes):
+            raise ValueError("one grid per problem")
+        out = torch.empty(self.offsets[-1], dtype=torch.float64, device=self.device)
+        for b, g in enumerate(grids):
+            if tuple(g.shape) != self.sizes[b]:
+                raise ValueError(f"grid {b} has shape {tuple(g.shape)}, expected {self.sizes[b]}")
+            out[self.offsets[b]:self.offsets[b + 1]] = g.reshape(-1)
+        return out
+
+    def unpack(self, packed):
+        return [packed[self.offsets[b]:self.offsets[b + 1]].view(*self.sizes[b]) for b in range(len(self.sizes))]
+
+    def solve(self, f, out=None, workspace=None, stream=None):
+        if f.dim() != 1:
+            raise ValueError("batched solve takes the packed 1-D array")
+        return super().solve(f, out, workspace, stream)
 
 
 _plans: dict = {}

@@ -28,9 +28,12 @@ SP_NOALLOC_SCRATCH_BYTES = 32 << 20
 SP_FP64 = 0
 SP_FP32 = 1
 SP_FP32_REFINE = 2
+SP_FLAG_AUTOTUNE = 1
 
 EXPORTED = (
     "sphere_poisson_plan",
+    "sphere_poisson_plan_batched",
+    "sphere_poisson_batch_offsets",
     "sphere_poisson_workspace_size",
     "sphere_poisson_solve",
     "sphere_poisson_solve_adjoint",
@@ -71,6 +74,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     vp, sz, i32, u32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint
     psz = ctypes.POINTER(ctypes.c_size_t)
     lib.sphere_poisson_plan.argtypes = [ctypes.POINTER(vp), i32, i32, i32, i32, u32, psz]
+    lib.sphere_poisson_plan_batched.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(ctypes.c_int),
+                                                ctypes.POINTER(ctypes.c_int), i32, i32, u32, psz]
+    lib.sphere_poisson_batch_offsets.argtypes = [vp, psz]
     lib.sphere_poisson_workspace_size.argtypes = [vp, psz]
     lib.sphere_poisson_solve.argtypes = [vp, vp, vp, vp, sz, vp]
     lib.sphere_poisson_solve_adjoint.argtypes = [vp, vp, vp, vp, sz, vp]

@@ -1,5 +1,6 @@
 // FP64 transform and elimination kernels (and the FP64 zonal side path of the FP32 forms).
 #include "launchers.inl"
+#include "batched.cuh"
 
 namespace sp {
 
@@ -69,6 +70,23 @@ void launch_zonal_scan(bool adj, cudaStream_t st, cpx<double>* Z, const double* 
   const size_t smem = threads * sizeof(AffineC);
   if (adj) k_zonal_scan<true><<<1, threads, smem, st>>>(Z, zl, ziu, zcu, N);
   else k_zonal_scan<false><<<1, threads, smem, st>>>(Z, zl, ziu, zcu, N);
+}
+
+cudaError_t batched_fp64_occupancy(bool big, int threads, size_t smem, int* blocks_per_sm) {
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e;
+  if (big) {
+    e = cudaFuncSetAttribute(k_batched_fp64<true>, a, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batched_fp64<true>, threads, smem);
+  } else {
+    e = cudaFuncSetAttribute(k_batched_fp64<false>, a, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batched_fp64<false>, threads, smem);
+  }
+  return e;
+}
+void launch_batched_fp64(bool big, dim3 grid, int threads, size_t smem, cudaStream_t st, const BatchArgs& a) {
+  if (big) k_batched_fp64<true><<<grid, threads, smem, st>>>(a);
+  else k_batched_fp64<false><<<grid, threads, smem, st>>>(a);
 }
 
 }  // namespace sp

@@ -126,15 +126,13 @@ __device__ __forceinline__ dd block_sum_dd(dd v) {
 // One CTA per `rows` consecutive rows; shared memory rows * L complex.
 // ---------------------------------------------------------------------------
 template <typename T, bool ADJ, bool BIG>
-__global__ void __launch_bounds__(BIG ? 256 : 512) k_rows_forward(
+__device__ __forceinline__ void rows_forward_tile(int tile, cpx<T>* __restrict__ sm,
     const double* __restrict__ f, cpx<T>* __restrict__ W, int nt, int n, int Kp, int rows,
-    FftDesc d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
+    const FftDesc& d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
     const cpx<T>* __restrict__ post, const double* __restrict__ row_scale,
     const T* __restrict__ row_scale_t, cpx<double>* __restrict__ zonal) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
   const int L = n >> 1;
-  const int row0 = blockIdx.x * rows;
+  const int row0 = tile * rows;
   for (int r = 0; r < rows; ++r) {
     const int row = row0 + r;
     dd acc(0.f, 0.f);
@@ -185,6 +183,17 @@ __global__ void __launch_bounds__(BIG ? 256 : 512) k_rows_forward(
   }
 }
 
+template <typename T, bool ADJ, bool BIG>
+__global__ void __launch_bounds__(BIG ? 256 : 512) k_rows_forward(
+    const double* __restrict__ f, cpx<T>* __restrict__ W, int nt, int n, int Kp, int rows,
+    FftDesc d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
+    const cpx<T>* __restrict__ post, const double* __restrict__ row_scale,
+    const T* __restrict__ row_scale_t, cpx<double>* __restrict__ zonal) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  rows_forward_tile<T, ADJ, BIG>(blockIdx.x, sm, f, W, nt, n, Kp, rows, d, tw, perm, post, row_scale, row_scale_t, zonal);
+}
+
 // ---------------------------------------------------------------------------
 // rows_inverse: inverse real FFT along longitude,
 //   u_iq = Re U_0 + 2 Re sum_{k=1}^{L-1} U_k e^{2 pi i k q/n} + Re U_L (-1)^q.
@@ -195,15 +204,13 @@ __global__ void __launch_bounds__(BIG ? 256 : 512) k_rows_forward(
 //            after the transform (the FP64 side path's zonal column).
 // ---------------------------------------------------------------------------
 template <typename T, bool ADJ, bool BIG>
-__global__ void __launch_bounds__(BIG ? 256 : 512) k_rows_inverse(
+__device__ __forceinline__ void rows_inverse_tile(int tile, cpx<T>* __restrict__ sm,
     const cpx<T>* __restrict__ W, double* __restrict__ u, int nt, int n, int Kp, int rows,
-    FftDesc d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
+    const FftDesc& d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
     const cpx<T>* __restrict__ post, const double* __restrict__ row_scale,
     const T* __restrict__ row_scale_t, const cpx<double>* __restrict__ zonal) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
   const int L = n >> 1;
-  const int row0 = blockIdx.x * rows;
+  const int row0 = tile * rows;
   for (int r = 0; r < rows; ++r)
 #pragma unroll 2
   for (int k = threadIdx.x; k < L; k += blockDim.x) {
@@ -254,6 +261,17 @@ __global__ void __launch_bounds__(BIG ? 256 : 512) k_rows_inverse(
   }
 }
 
+template <typename T, bool ADJ, bool BIG>
+__global__ void __launch_bounds__(BIG ? 256 : 512) k_rows_inverse(
+    const cpx<T>* __restrict__ W, double* __restrict__ u, int nt, int n, int Kp, int rows,
+    FftDesc d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
+    const cpx<T>* __restrict__ post, const double* __restrict__ row_scale,
+    const T* __restrict__ row_scale_t, const cpx<double>* __restrict__ zonal) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  rows_inverse_tile<T, ADJ, BIG>(blockIdx.x, sm, W, u, nt, n, Kp, rows, d, tw, perm, post, row_scale, row_scale_t, zonal);
+}
+
 // ---------------------------------------------------------------------------
 // theta_forward: per column k, P_j = (1/2)(w_j V_j + conj(w_j) V_{N-j}), with
 // V = FFT_N of the Makhoul-reordered column (odd k: samples times (-1)^i) and
@@ -267,13 +285,11 @@ __global__ void __launch_bounds__(BIG ? 256 : 512) k_rows_inverse(
 // One CTA per `cols` consecutive columns.  inv_n = 1/N in arithmetic T.
 // ---------------------------------------------------------------------------
 template <typename T, bool ADJ, bool BIG>
-__global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_forward(
-    cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d,
+__device__ __forceinline__ void theta_forward_tile(int tile, cpx<T>* __restrict__ sm,
+    cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, const FftDesc& d,
     const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
     T inv_n, int zonal) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
-  const int k0 = blockIdx.x * cols;
+  const int k0 = tile * cols;
   const int cs = __ffs(cols) - 1;            // cols is a power of two
 #pragma unroll 4
   for (int idx = threadIdx.x; idx < N * cols; idx += blockDim.x) {
@@ -326,6 +342,16 @@ __global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_forward(
   }
 }
 
+template <typename T, bool ADJ, bool BIG>
+__global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_forward(
+    cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d,
+    const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
+    T inv_n, int zonal) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  theta_forward_tile<T, ADJ, BIG>(blockIdx.x, sm, W, N, K, Kp, cols, d, tw, perm, post, inv_n, zonal);
+}
+
 // ---------------------------------------------------------------------------
 // theta_inverse: per column k, DCT-III (k even) U_i = Y_0 + 2 sum_j Y_j cos(j theta_i)
 // with Y = X, or for k odd i (-1)^i times the DCT-III of Y_j = X_{N-j} (Y_0 = 0),
@@ -338,13 +364,11 @@ __global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_forward(
 //            transpose of theta_forward
 // ---------------------------------------------------------------------------
 template <typename T, bool ADJ, bool BIG>
-__global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_inverse(
-    cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d,
+__device__ __forceinline__ void theta_inverse_tile(int tile, cpx<T>* __restrict__ sm,
+    cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, const FftDesc& d,
     const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
     T inv_n, int zonal) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
-  const int k0 = blockIdx.x * cols;
+  const int k0 = tile * cols;
   if constexpr (std::is_same<T, double>::value) {
     if (!ADJ && zonal && k0 == 0) {
       cpx<double> acc = {0.0, 0.0};
@@ -417,6 +441,16 @@ __global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_inverse(
     }
     W[(size_t)i * Kp + k] = v;
   }
+}
+
+template <typename T, bool ADJ, bool BIG>
+__global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_inverse(
+    cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d,
+    const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
+    T inv_n, int zonal) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  theta_inverse_tile<T, ADJ, BIG>(blockIdx.x, sm, W, N, K, Kp, cols, d, tw, perm, post, inv_n, zonal);
 }
 
 // ---------------------------------------------------------------------------

@@ -6,6 +6,7 @@
 
 #include <cuda_runtime.h>
 
+#include "batch_types.h"
 #include "fft.cuh"
 
 namespace sp {
@@ -48,6 +49,11 @@ void launch_factor(const Launch& l, S* fl, S* fiu, S* fcu, int N, int K, int Kp)
 // FP64 zonal-column eliminations by parallel scan (one CTA)
 void launch_zonal_scan(bool adj, cudaStream_t st, cpx<double>* Z, const double* zl, const double* ziu,
                        const double* zcu, int N);
+
+// persistent batched FP64 solve: set the kernel's shared-memory cap and report
+// how many CTAs of `threads` fit per SM with `smem` dynamic bytes
+cudaError_t batched_fp64_occupancy(bool big, int threads, size_t smem, int* blocks_per_sm);
+void launch_batched_fp64(bool big, dim3 grid, int threads, size_t smem, cudaStream_t st, const BatchArgs& a);
 
 void launch_refine(const Launch& l, const cpx<dd>* F, cpx<dd>* X, cpx<float>* Y, const float* fl,
                    const float* fiu, const float* fcu, int N, int K, int Kp, int first);

@@ -4,12 +4,18 @@
 // launch sequences of the solve and of its transpose.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
-#include <mutex>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
 #include <new>
+#include <sstream>
+#include <string>
 #include <vector>
 
 #include "sphere_poisson.h"
@@ -169,6 +175,16 @@ struct sp_plan_s {
   // stage timing (profile_begin / profile_end)
   std::vector<cudaEvent_t> prof_events;
   int prof_max, prof_count;
+  // batched plans
+  int batched;
+  int count;
+  size_t total;                      // doubles in the packed f / u arrays
+  std::vector<size_t> offsets;       // count + 1
+  sp::BatchArgs bargs;               // device pointers (f, u, scratch, counter filled per call)
+  bool bbig;
+  int bgrid, bthreads;
+  size_t bsmem;
+  size_t off_counter;                // counter position in the workspace
 };
 
 namespace {
@@ -336,8 +352,31 @@ void enqueue_refine(sp_plan_t p, const double* in, double* out, void* ws, cudaSt
   m.done();
 }
 
+int launch_batched(sp_plan_t p, const double* in, double* out, void* workspace, cudaStream_t st) {
+  if (p->count == 0) return SP_OK;
+  sp::BatchArgs a = p->bargs;
+  a.f = in;
+  a.u = out;
+  a.scratch = static_cast<cpx<double>*>(workspace);
+  a.counter = reinterpret_cast<int*>(static_cast<char*>(workspace) + p->off_counter);
+  cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(batch counter)");
+  StageMarks m{p, st, !p->prof_events.empty() && p->prof_count < p->prof_max};
+  m.mark(0);
+  sp::launch_batched_fp64(p->bbig, dim3(p->bgrid), p->bthreads, p->bsmem, st, a);
+  for (int s = 1; s <= kStages; ++s) m.mark(s);
+  m.done();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "batched launch");
+  return SP_OK;
+}
+
 template <bool ADJ>
 int launch_solve(sp_plan_t p, const double* in, double* out, void* workspace, cudaStream_t st) {
+  if (p->batched) {
+    if (ADJ) return SP_ERR_UNSUPPORTED;
+    return launch_batched(p, in, out, workspace, st);
+  }
   if (p->precision == SP_FP64) {
     enqueue_fp64(p, ADJ, in, out, workspace, st);
   } else if (p->precision == SP_FP32) {
@@ -603,6 +642,377 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   return SP_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+constexpr int kBatchThreads = 256;
+
+// host copy of the per-size tables of a batched plan
+struct HostClass {
+  int nt, nl;
+  FftDesc rd, cd;
+  std::vector<cpx<double>> tw_row, tw_col, post_row, post_col;
+  std::vector<int> perm_row, perm_col;
+  std::vector<double> row_scale;
+};
+
+void default_tiles(sp::BatchClass& c) {
+  const size_t cs = sizeof(cpx<double>), budget = 96 * 1024;
+  c.rows = 1;
+  while (c.rows < 8 && (size_t)(2 * c.rows) * c.L * cs <= budget && 2 * c.rows <= c.nt) c.rows *= 2;
+  c.cols = 1;
+  while (c.cols < 8 && (size_t)(2 * c.cols) * c.N * cs <= budget && 2 * c.cols <= c.Kp) c.cols *= 2;
+}
+
+size_t class_smem(const sp::BatchClass& c) {
+  const size_t cs = sizeof(cpx<double>);
+  return std::max((size_t)c.rows * c.L * cs, (size_t)c.cols * c.N * cs);
+}
+
+std::string tune_key(const char* gpu, int nt, int nl) {
+  std::ostringstream o;
+  o << gpu << "|" << nt << "x" << nl << "|fp64";
+  std::string k = o.str();
+  for (char& ch : k)
+    if (ch == ' ') ch = '_';
+  return k;
+}
+
+std::map<std::string, std::pair<int, int>> read_tune_cache(const char* path) {
+  std::map<std::string, std::pair<int, int>> m;
+  if (!path) return m;
+  std::ifstream in(path);
+  std::string key;
+  int r, c;
+  double t;
+  while (in >> key >> r >> c >> t) m[key] = {r, c};
+  return m;
+}
+
+// Time candidate tiles of one size class on a batch of `reps_problems` copies
+// of that size (zero input), through the same persistent kernel.  Returns the
+// best (rows, cols) and its time.
+int tune_class(sp_plan_t p, int ci, std::vector<sp::BatchClass>& cls, sp::BatchClass* d_cls,
+               double* d_f, cpx<double>* d_scratch, int* d_counter, sp::BatchProblem* d_prob, int* d_order,
+               int nprob, std::pair<int, int>* best, double* best_ms) {
+  sp::BatchClass& c = cls[ci];
+  const size_t cs = sizeof(cpx<double>), cap = 200 * 1024;
+  std::vector<sp::BatchProblem> prob(nprob);
+  std::vector<int> order(nprob);
+  const long long per = (long long)c.nt * c.nl;
+  for (int i = 0; i < nprob; ++i) {
+    prob[i] = {ci, 0, (long long)i * per};
+    order[i] = i;
+  }
+  cudaMemcpy(d_prob, prob.data(), nprob * sizeof(sp::BatchProblem), cudaMemcpyHostToDevice);
+  cudaMemcpy(d_order, order.data(), nprob * sizeof(int), cudaMemcpyHostToDevice);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  *best_ms = 1e30;
+  const sp::BatchClass saved = c;
+  for (int r = 1; r <= 8 && r <= c.nt; r *= 2) {
+    for (int q = 1; q <= 8 && q <= c.Kp; q *= 2) {
+      if ((size_t)r * c.L * cs > cap || (size_t)q * c.N * cs > cap) continue;
+      c.rows = r;
+      c.cols = q;
+      cudaMemcpy(d_cls + ci, &c, sizeof(sp::BatchClass), cudaMemcpyHostToDevice);
+      const size_t smem = class_smem(c);
+      int bps = 0;
+      if (sp::batched_fp64_occupancy(p->bbig, kBatchThreads, smem, &bps) != cudaSuccess || bps < 1) continue;
+      sp::BatchArgs a = p->bargs;
+      a.problems = d_prob;
+      a.order = d_order;
+      a.count = nprob;
+      a.f = d_f;
+      a.u = d_f + (size_t)nprob * per;
+      a.scratch = d_scratch;
+      a.counter = d_counter;
+      const int grid = std::min(p->bgrid, nprob);
+      double ms_min = 1e30;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaMemsetAsync(d_counter, 0, sizeof(int), 0);
+        cudaEventRecord(e0, 0);
+        sp::launch_batched_fp64(p->bbig, dim3(grid), kBatchThreads, smem, 0, a);
+        cudaEventRecord(e1, 0);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) ms_min = std::min(ms_min, (double)ms);
+      }
+      if (cudaGetLastError() != cudaSuccess) continue;
+      if (ms_min < *best_ms) {
+        *best_ms = ms_min;
+        *best = {r, q};
+      }
+    }
+  }
+  c = saved;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return *best_ms < 1e29 ? SP_OK : SP_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, const int* n_lambda,
+                                int precision, int refine_sweeps, unsigned flags, size_t* workspace_bytes) {
+  if (!plan) return SP_ERR_NULL;
+  *plan = nullptr;
+  if (count < 0) return SP_ERR_BAD_ARG;
+  if (count > 0 && (!n_theta || !n_lambda)) return SP_ERR_NULL;
+  if (precision != SP_FP64) return SP_ERR_UNSUPPORTED;
+  if ((flags & ~SP_FLAG_AUTOTUNE) != 0 || refine_sweeps < 0) return SP_ERR_BAD_ARG;
+  // validate sizes and form the size classes
+  std::map<std::pair<int, int>, int> cls_of;
+  std::vector<HostClass> hcls;
+  std::vector<int> prob_cls(count);
+  for (int b = 0; b < count; ++b) {
+    const int nt = n_theta[b], nl = n_lambda[b];
+    if (nt < 1 || nl < 2 || (nl & 1) || nt > kMaxLen || nl / 2 > kMaxLen) return SP_ERR_BAD_SIZE;
+    auto it = cls_of.find({nt, nl});
+    if (it == cls_of.end()) {
+      HostClass h;
+      h.nt = nt;
+      h.nl = nl;
+      if (!make_fft_desc(nl / 2, &h.rd) || !make_fft_desc(nt, &h.cd)) return SP_ERR_BAD_SIZE;
+      it = cls_of.emplace(std::make_pair(nt, nl), (int)hcls.size()).first;
+      hcls.push_back(std::move(h));
+    }
+    prob_cls[b] = it->second;
+  }
+  sp_plan_s* p = new (std::nothrow) sp_plan_s();
+  if (!p) return SP_ERR_CUDA;
+  p->batched = 1;
+  p->count = count;
+  p->precision = precision;
+  p->nt = p->nl = 0;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return cuda_fail(cudaGetLastError(), "cudaGetDevice");
+  }
+  p->offsets.resize(count + 1);
+  p->offsets[0] = 0;
+  for (int b = 0; b < count; ++b) p->offsets[b + 1] = p->offsets[b] + (size_t)n_theta[b] * n_lambda[b];
+  p->total = p->offsets[count];
+
+  // per-class tables
+  const int nc = (int)hcls.size();
+  std::vector<sp::BatchClass> cls(nc);
+  auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align(off + bytes);
+    return o;
+  };
+  struct Offs { size_t tw_row, tw_col, post_row, post_col, perm_row, perm_col, scale, fl, fiu, fcu; };
+  std::vector<Offs> co(nc);
+  bool big = false;
+  size_t max_slot = 0;
+  for (int c = 0; c < nc; ++c) {
+    HostClass& h = hcls[c];
+    sp::BatchClass& b = cls[c];
+    b.nt = h.nt;
+    b.nl = h.nl;
+    b.L = h.nl / 2;
+    b.N = h.nt;
+    b.K = b.L + 1;
+    b.Kp = (b.K + 1) & ~1;
+    b.row_fft = h.rd;
+    b.col_fft = h.cd;
+    big = big || needs_big(h.rd) || needs_big(h.cd);
+    default_tiles(b);
+    max_slot = std::max(max_slot, (size_t)b.N * b.Kp);
+    h.tw_row.resize(b.L);
+    h.tw_col.resize(b.N);
+    h.post_row.resize(b.L + 1);
+    h.post_col.resize(b.N + 1);
+    for (int t = 0; t < b.L; ++t) unit_root(t, b.L, &h.tw_row[t].re, &h.tw_row[t].im);
+    for (int t = 0; t < b.N; ++t) unit_root(t, b.N, &h.tw_col[t].re, &h.tw_col[t].im);
+    for (int k = 0; k <= b.L; ++k) unit_root(k, b.nl, &h.post_row[k].re, &h.post_row[k].im);
+    for (int j = 0; j <= b.N; ++j) unit_root(j, 4L * b.N, &h.post_col[j].re, &h.post_col[j].im);
+    digit_reversal(h.rd, h.perm_row);
+    digit_reversal(h.cd, h.perm_col);
+    h.row_scale.resize(b.nt);
+    for (int i = 0; i < b.nt; ++i) {
+      double re, im;
+      unit_root(2 * i + 1, 4L * b.N, &re, &im);
+      h.row_scale[i] = (im * im) / (double)b.nl;
+    }
+    const size_t csz = sizeof(cpx<double>), fac = (size_t)b.N * b.Kp * sizeof(double);
+    co[c] = {take(b.L * csz), take(b.N * csz), take((b.L + 1) * csz), take((b.N + 1) * csz),
+             take(b.L * sizeof(int)), take(b.N * sizeof(int)), take(b.nt * sizeof(double)),
+             take(fac), take(fac), take(fac)};
+  }
+  const size_t o_cls = take(nc * sizeof(sp::BatchClass) + 1);
+  const size_t o_prob = take(count * sizeof(sp::BatchProblem) + 1);
+  const size_t o_order = take(count * sizeof(int) + 1);
+  const size_t total_dev = off;
+  p->bbig = big;
+  p->bthreads = kBatchThreads;
+
+  int rc = SP_OK;
+  auto step = [&](cudaError_t err, const char* what) {
+    if (rc == SP_OK && err != cudaSuccess) rc = cuda_fail(err, what);
+  };
+  step(cudaMalloc(&p->dev, total_dev), "cudaMalloc(batched plan tables)");
+  if (rc != SP_OK) {
+    p->dev = nullptr;
+    destroy_plan(p);
+    return rc;
+  }
+  p->magic = kMagic;
+  char* base = static_cast<char*>(p->dev);
+  for (int c = 0; c < nc; ++c) {
+    HostClass& h = hcls[c];
+    sp::BatchClass& b = cls[c];
+    const size_t csz = sizeof(cpx<double>);
+    b.tw_row = reinterpret_cast<cpx<double>*>(base + co[c].tw_row);
+    b.tw_col = reinterpret_cast<cpx<double>*>(base + co[c].tw_col);
+    b.post_row = reinterpret_cast<cpx<double>*>(base + co[c].post_row);
+    b.post_col = reinterpret_cast<cpx<double>*>(base + co[c].post_col);
+    b.perm_row = reinterpret_cast<int*>(base + co[c].perm_row);
+    b.perm_col = reinterpret_cast<int*>(base + co[c].perm_col);
+    b.row_scale = reinterpret_cast<double*>(base + co[c].scale);
+    b.fl = reinterpret_cast<double*>(base + co[c].fl);
+    b.fiu = reinterpret_cast<double*>(base + co[c].fiu);
+    b.fcu = reinterpret_cast<double*>(base + co[c].fcu);
+    step(cudaMemcpy((void*)b.tw_row, h.tw_row.data(), b.L * csz, cudaMemcpyHostToDevice), "copy");
+    step(cudaMemcpy((void*)b.tw_col, h.tw_col.data(), b.N * csz, cudaMemcpyHostToDevice), "copy");
+    step(cudaMemcpy((void*)b.post_row, h.post_row.data(), (b.L + 1) * csz, cudaMemcpyHostToDevice), "copy");
+    step(cudaMemcpy((void*)b.post_col, h.post_col.data(), (b.N + 1) * csz, cudaMemcpyHostToDevice), "copy");
+    step(cudaMemcpy((void*)b.perm_row, h.perm_row.data(), b.L * sizeof(int), cudaMemcpyHostToDevice), "copy");
+    step(cudaMemcpy((void*)b.perm_col, h.perm_col.data(), b.N * sizeof(int), cudaMemcpyHostToDevice), "copy");
+    step(cudaMemcpy((void*)b.row_scale, h.row_scale.data(), b.nt * sizeof(double), cudaMemcpyHostToDevice), "copy");
+    const size_t fac = (size_t)b.N * b.Kp * sizeof(double);
+    step(cudaMemset((void*)b.fl, 0, (size_t)((const char*)b.fcu - (const char*)b.fl) + fac), "clear factors");
+    if (rc == SP_OK) {
+      int threads = 128, blocks = (2 * b.K + threads - 1) / threads;
+      sp::launch_factor<double>(sp::Launch{dim3(blocks), threads, 0, 0}, (double*)b.fl, (double*)b.fiu,
+                                (double*)b.fcu, b.N, b.K, b.Kp);
+      step(cudaGetLastError(), "k_factor launch");
+    }
+  }
+  step(cudaDeviceSynchronize(), "batched factors");
+  // problems, largest first
+  std::vector<sp::BatchProblem> prob(count);
+  std::vector<int> order(count);
+  for (int b = 0; b < count; ++b) {
+    prob[b] = {prob_cls[b], 0, (long long)p->offsets[b]};
+    order[b] = b;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return (size_t)n_theta[x] * n_lambda[x] > (size_t)n_theta[y] * n_lambda[y];
+  });
+  sp::BatchClass* d_cls = reinterpret_cast<sp::BatchClass*>(base + o_cls);
+  sp::BatchProblem* d_prob = reinterpret_cast<sp::BatchProblem*>(base + o_prob);
+  int* d_order = reinterpret_cast<int*>(base + o_order);
+  p->bargs.classes = d_cls;
+  p->bargs.problems = d_prob;
+  p->bargs.order = d_order;
+  p->bargs.count = count;
+  p->bargs.slot = (long long)max_slot;
+  // persistent grid: every SM filled to the kernel's occupancy
+  int sms = 1;
+  step(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device), "SM count");
+  size_t smem = 0;
+  for (auto& b : cls) smem = std::max(smem, class_smem(b));
+  int bps = 0;
+  step(sp::batched_fp64_occupancy(big, kBatchThreads, std::max(smem, (size_t)200 * 1024), &bps), "occupancy");
+  p->bgrid = std::max(1, std::min(count, sms * std::max(bps, 1)));
+
+  // autotuning of the transform tiles per size class
+  if (rc == SP_OK && count > 0 && (flags & SP_FLAG_AUTOTUNE)) {
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, p->device);
+    const char* cache_path = std::getenv("SPHERE_POISSON_TUNE_CACHE");
+    auto cache = read_tune_cache(cache_path);
+    std::vector<std::string> new_lines;
+    // scratch for the timing batches: nprob problems of the largest class
+    const int nprob = std::max(1, p->bgrid);
+    size_t max_vals = 0;
+    for (auto& b : cls) max_vals = std::max(max_vals, (size_t)b.nt * b.nl);
+    double* d_f = nullptr;
+    cpx<double>* d_scr = nullptr;
+    int* d_cnt = nullptr;
+    sp::BatchProblem* d_tp = nullptr;
+    int* d_to = nullptr;
+    step(cudaMalloc(&d_f, 2 * (size_t)nprob * max_vals * sizeof(double)), "tune buffers");
+    step(cudaMalloc(&d_scr, (size_t)p->bgrid * max_slot * sizeof(cpx<double>)), "tune buffers");
+    step(cudaMalloc(&d_cnt, 256), "tune buffers");
+    step(cudaMalloc(&d_tp, nprob * sizeof(sp::BatchProblem)), "tune buffers");
+    step(cudaMalloc(&d_to, nprob * sizeof(int)), "tune buffers");
+    if (rc == SP_OK) {
+      step(cudaMemset(d_f, 0, 2 * (size_t)nprob * max_vals * sizeof(double)), "tune buffers");
+      step(cudaMemcpy(d_cls, cls.data(), nc * sizeof(sp::BatchClass), cudaMemcpyHostToDevice), "copy classes");
+    }
+    for (int c = 0; c < nc && rc == SP_OK; ++c) {
+      const std::string key = tune_key(prop.name, cls[c].nt, cls[c].nl);
+      auto it = cache.find(key);
+      if (it != cache.end()) {
+        cls[c].rows = it->second.first;
+        cls[c].cols = it->second.second;
+        continue;
+      }
+      std::pair<int, int> best{cls[c].rows, cls[c].cols};
+      double ms = 0;
+      if (tune_class(p, c, cls, d_cls, d_f, d_scr, d_cnt, d_tp, d_to, nprob, &best, &ms) == SP_OK) {
+        cls[c].rows = best.first;
+        cls[c].cols = best.second;
+        std::ostringstream o;
+        o << key << " " << best.first << " " << best.second << " " << ms;
+        new_lines.push_back(o.str());
+      }
+      step(cudaMemcpy(d_cls + c, &cls[c], sizeof(sp::BatchClass), cudaMemcpyHostToDevice), "copy class");
+    }
+    cudaFree(d_f);
+    cudaFree(d_scr);
+    cudaFree(d_cnt);
+    cudaFree(d_tp);
+    cudaFree(d_to);
+    if (cache_path && !new_lines.empty()) {
+      std::ofstream out(cache_path, std::ios::app);
+      for (auto& l : new_lines) out << l << "\n";
+    }
+  }
+  smem = 0;
+  for (auto& b : cls) smem = std::max(smem, class_smem(b));
+  p->bsmem = smem;
+  step(cudaMemcpy(d_cls, cls.data(), nc * sizeof(sp::BatchClass), cudaMemcpyHostToDevice), "copy classes");
+  if (count > 0) {
+    step(cudaMemcpy(d_prob, prob.data(), count * sizeof(sp::BatchProblem), cudaMemcpyHostToDevice), "copy problems");
+    step(cudaMemcpy(d_order, order.data(), count * sizeof(int), cudaMemcpyHostToDevice), "copy order");
+    step(sp::batched_fp64_occupancy(big, kBatchThreads, smem, &bps), "occupancy");
+    p->bgrid = std::max(1, std::min(count, sms * std::max(bps, 1)));
+  }
+  p->off_counter = align((size_t)p->bgrid * max_slot * sizeof(cpx<double>));
+  p->ws_bytes = p->off_counter + 256;
+  step(allow_all_smem(p->device), "shared memory attribute");
+  if (rc != SP_OK) {
+    destroy_plan(p);
+    return rc;
+  }
+  if (workspace_bytes) *workspace_bytes = p->ws_bytes;
+  *plan = p;
+  return SP_OK;
+}
+
+int sphere_poisson_batch_offsets(sp_plan_t plan, size_t* offsets) {
+  if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
+  if (!offsets) return SP_ERR_NULL;
+  if (!plan->batched) {
+    offsets[0] = 0;
+    offsets[1] = (size_t)plan->nt * plan->nl;
+    return SP_OK;
+  }
+  for (size_t i = 0; i < plan->offsets.size(); ++i) offsets[i] = plan->offsets[i];
+  return SP_OK;
+}
+
 int sphere_poisson_workspace_size(sp_plan_t plan, size_t* workspace_bytes) {
   if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
   if (!workspace_bytes) return SP_ERR_NULL;
@@ -627,7 +1037,8 @@ int sphere_poisson_solve_adjoint(sp_plan_t plan, const double* ubar, double* fba
 int sphere_poisson_host_buffer_size(sp_plan_t plan, size_t* device_buffer_bytes) {
   if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
   if (!device_buffer_bytes) return SP_ERR_NULL;
-  size_t grid = ((size_t)plan->nt * plan->nl * sizeof(double) + 255) & ~(size_t)255;
+  const size_t values = plan->batched ? plan->total : (size_t)plan->nt * plan->nl;
+  size_t grid = (values * sizeof(double) + 255) & ~(size_t)255;
   *device_buffer_bytes = 2 * grid + plan->ws_bytes;
   return SP_OK;
 }
@@ -640,7 +1051,7 @@ int sphere_poisson_solve_host(sp_plan_t plan, const double* f_host, double* u_ho
   size_t need = 0;
   sphere_poisson_host_buffer_size(plan, &need);
   if (device_buffer_bytes < need) return SP_ERR_WORKSPACE;
-  const size_t bytes = (size_t)plan->nt * plan->nl * sizeof(double);
+  const size_t bytes = (plan->batched ? plan->total : (size_t)plan->nt * plan->nl) * sizeof(double);
   const size_t grid = (bytes + 255) & ~(size_t)255;
   char* base = static_cast<char*>(device_buffer);
   double* d_f = reinterpret_cast<double*>(base);
@@ -705,7 +1116,8 @@ int sphere_poisson_solve_noalloc(sp_plan_t plan, const double* f, double* u, voi
 int sphere_poisson_launch_count(sp_plan_t plan, int adjoint, int* launches) {
   if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
   if (!launches) return SP_ERR_NULL;
-  if (plan->precision == SP_FP64) *launches = kStages;
+  if (plan->batched) *launches = plan->count ? 1 : 0;
+  else if (plan->precision == SP_FP64) *launches = kStages;
   else if (plan->precision == SP_FP32) *launches = kStages + 3;
   else *launches = adjoint ? 0 : kStages - 1 + 3 + (plan->sweeps + 1);
   return SP_OK;

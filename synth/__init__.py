@@ -13,6 +13,8 @@ from .sh import (  # noqa: F401
     random_sh_coeffs,
     single_sh_coeffs,
     synthesize,
+    synthesize_many,
+    batched_workload,
     poisson_exact,
     workload,
     WORKLOADS,

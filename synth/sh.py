@@ -136,6 +136,75 @@ def synthesize(coeffs: np.ndarray, n_theta: int, n_lambda: int, device="cpu") ->
     return f.contiguous()
 
 
+def synthesize_many(coeff_list, n_theta: int, n_lambda: int, device="cpu") -> torch.Tensor:
+    """synthesize() for several coefficient arrays of the same degree L on the
+    same grid at once; returns float64 [P, n_theta, n_lambda]."""
+    P = len(coeff_list)
+    lmax = coeff_list[0].shape[0] - 1
+    dev = torch.device(device)
+    cc = torch.tensor(np.stack([np.asarray(c, dtype=np.float64) for c in coeff_list]), dtype=torch.float64,
+                      device=dev)                                    # [P, L+1, 2L+1]
+    theta = torch.tensor(colatitudes(n_theta), dtype=torch.float64, device=dev)
+    x = torch.cos(theta)
+    s = torch.sin(theta)
+    ccos = cc[:, :, lmax:]                                           # [P, L+1, L+1] (m = 0..L)
+    csin = torch.flip(cc[:, :, : lmax + 1], dims=[2]).clone()
+    csin[:, :, 0] = 0.0
+    pmm = torch.empty((lmax + 1, n_theta), dtype=torch.float64, device=dev)
+    pmm[0] = 1.0 / math.sqrt(4.0 * math.pi)
+    for m in range(1, lmax + 1):
+        pmm[m] = pmm[m - 1] * s * math.sqrt((2.0 * m + 1.0) / (2.0 * m))
+    acc_c = torch.zeros((P, lmax + 1, n_theta), dtype=torch.float64, device=dev)
+    acc_s = torch.zeros((P, lmax + 1, n_theta), dtype=torch.float64, device=dev)
+    p_prev2 = torch.zeros((lmax + 1, n_theta), dtype=torch.float64, device=dev)
+    p_prev = torch.zeros((lmax + 1, n_theta), dtype=torch.float64, device=dev)
+    mvec = torch.arange(lmax + 1, dtype=torch.float64, device=dev)
+    for l in range(0, lmax + 1):
+        p_l = torch.zeros((lmax + 1, n_theta), dtype=torch.float64, device=dev)
+        if l >= 2:
+            mm = mvec[: l - 1]
+            a_l = torch.sqrt((4.0 * l * l - 1.0) / (l * l - mm * mm))
+            a_lm1 = torch.sqrt((4.0 * (l - 1) ** 2 - 1.0) / ((l - 1) ** 2 - mm * mm))
+            p_l[: l - 1] = a_l[:, None] * (x[None, :] * p_prev[: l - 1] - p_prev2[: l - 1] / a_lm1[:, None])
+        if l >= 1:
+            p_l[l - 1] = math.sqrt(2.0 * l + 1.0) * x * pmm[l - 1]
+        p_l[l] = pmm[l]
+        acc_c[:, : l + 1] += ccos[:, l, : l + 1, None] * p_l[None, : l + 1]
+        acc_s[:, : l + 1] += csin[:, l, : l + 1, None] * p_l[None, : l + 1]
+        p_prev2, p_prev = p_prev, p_l
+    scale = torch.full((lmax + 1,), math.sqrt(2.0), dtype=torch.float64, device=dev)
+    scale[0] = 1.0
+    acc_c = acc_c * scale[None, :, None]
+    acc_s = acc_s * scale[None, :, None]
+    cos_t, sin_t = _angle_table(lmax, n_lambda, dev)
+    f = acc_c.transpose(1, 2) @ cos_t + acc_s.transpose(1, 2) @ sin_t
+    return f.contiguous()
+
+
+def batched_workload(count: int = 4096, seed: int = 1510080944, device="cpu"):
+    """The uneven-resolution batch: n_theta = 16 s with s uniform in 2..32,
+    n_lambda = 2 n_theta, a random series l <= n_theta/2 with N(0,1)/(1+l)^2
+    coefficients per problem (seeds drawn from one PCG64 stream).  Returns
+    (sizes, f list, exact-solution list)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    svals = rng.integers(2, 33, size=count)
+    seeds = rng.integers(0, 2**62, size=count)
+    sizes = [(16 * int(v), 32 * int(v)) for v in svals]
+    fs = [None] * count
+    us = [None] * count
+    by_size = {}
+    for b, sz in enumerate(sizes):
+        by_size.setdefault(sz, []).append(b)
+    for (nt, nl), idx in by_size.items():
+        cs = [random_sh_coeffs(nt // 2, int(seeds[b]), "inv_sq") for b in idx]
+        f = synthesize_many(cs, nt, nl, device)
+        u = synthesize_many([poisson_exact(c) for c in cs], nt, nl, device)
+        for q, b in enumerate(idx):
+            fs[b] = f[q]
+            us[b] = u[q]
+    return sizes, fs, us
+
+
 def poisson_exact(coeffs: np.ndarray) -> np.ndarray:
     """Coefficients of the zero-mean solution of Delta u = f for f = sum C Y:
     Delta Y_l^m = -l(l+1) Y_l^m, so u has C[l]/(-l(l+1)) and no l = 0 term."""
@@ -178,6 +247,7 @@ WORKLOADS = {
     "sh2048_4096x8192": Workload("sh2048_4096x8192", 4096, 8192, 2048, 1510080943, "inv_sq"),
     "sh200_512x1024_noisy": Workload("sh200_512x1024_noisy", 512, 1024, 200, 1510080945, "inv_sq", 1e-3),
 }
+# the batched workload (4096 uneven spheres) is built by batched_workload()
 
 
 def workload(name: str) -> Workload:
