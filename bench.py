@@ -314,7 +314,40 @@ def measure_forms(sp, f, u_exact, u64, N, n, dev, ms_fp64, args):
                     "max_rel_err_vs_closed_form": float((u - u_exact).abs().max()) / ex,
                     "gpu_launches_per_step": plan.launches()}
         del plan, ws
+    if not args.no_paper_scale:
+        res["paper_scale"] = measure_paper_scale(sp, dev)
     return res
+
+
+def measure_paper_scale(sp, dev):
+    """The paper's headline size: m = n with mn/2 = 1.03e8 unknowns (7168 x 14336),
+    FP64 and FP32+refinement (1 sweep), against the paper's ~1 minute on a laptop."""
+    import torch
+    from synth import sh
+
+    w = sh.workload("sh2000_7168x14336")
+    f, ue = w.make(device=dev)
+    ex = float(ue.abs().max())
+    out = {"workload": f"{w.name}: n_theta={w.n_theta} x n_lambda={w.n_lambda}, DOF (mn/2) = "
+                       f"{w.n_theta * w.n_lambda}", "paper_seconds_context": 60.0}
+    for prec, sweeps in [("fp64", 0), ("fp32_refine", 1)]:
+        plan = sp.Plan(w.n_theta, w.n_lambda, prec, sweeps, device=dev)
+        ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=dev)
+        u = torch.empty_like(f)
+        for _ in range(2):
+            plan.solve(f, u, ws)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(5):
+            plan.solve(f, u, ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        out[prec] = {"ms_per_solve": ms, "value": w.n_theta * w.n_lambda / (ms * 1e-3), "unit": "DOF/s",
+                     "max_rel_err_vs_closed_form": float((u - ue).abs().max()) / ex}
+        del plan, ws, u
+    return out
 
 
 def measure_batched(sp, dev, args):
@@ -476,6 +509,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-paper-scale", action="store_true")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp32_refine"])
     ap.add_argument("--sweeps", type=int, default=1)

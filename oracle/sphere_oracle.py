@@ -324,13 +324,44 @@ def sum2(values_on_grid: np.ndarray) -> float:
 # ----------------------------------------------------------------------------
 
 def _solve_columns_T(B: np.ndarray, reading: str = "B") -> np.ndarray:
-    """Y with M_k^T Y_k = B_k, M_k the (row-replaced) system matrix of column k."""
+    """Y with M_k^T Y_k = B_k, M_k the (row-replaced) system matrix of column k.
+    Dense LU at small m; otherwise LAPACK's banded LU on the transposed bands
+    (for k = 0 the transposed system has the dense column w: its row j = 0
+    gives Y_0 = B_0 / w_0 first, the rest is banded)."""
     m, n = B.shape
     Y = np.zeros_like(B, dtype=np.complex128)
     for kk in range(n):
         k = kk - n // 2
-        M = system_matrix(m, k, reading)
-        Y[:, kk] = np.linalg.solve(M.T, B[:, kk])
+        if m <= DENSE_MAX_M:
+            Y[:, kk] = np.linalg.solve(system_matrix(m, k, reading).T, B[:, kk])
+            continue
+        sub, d, sup = _bands_of(m, k, reading)
+        # (M^T)[i, i-2] = M[i-2, i] = sup[i-2],  (M^T)[i, i+2] = M[i+2, i] = sub[i+2]
+        subT = np.zeros(m)
+        supT = np.zeros(m)
+        subT[2:] = sup[:-2]
+        supT[:-2] = sub[2:]
+        rhs = B[:, kk].astype(np.complex128)
+        if k != 0:
+            Y[:, kk] = _banded_solve(subT, d, supT, rhs)
+            continue
+        i0 = m // 2
+        w = integration_weights(m)
+        if reading == "B":
+            w[0] = 0.0
+        y0 = rhs[i0] / w[i0]
+        keep = np.arange(m) != i0
+        sub_r = subT[keep].copy()
+        sup_r = supT[keep].copy()
+        sub_r[i0] = 0.0
+        sub_r[i0 + 1] = 0.0
+        sup_r[i0 - 2] = 0.0
+        sup_r[i0 - 1] = 0.0
+        yr = _banded_solve(sub_r, d[keep], sup_r, rhs[keep] - w[keep] * y0)
+        y = np.zeros(m, dtype=np.complex128)
+        y[keep] = yr
+        y[i0] = y0
+        Y[:, kk] = y
     return Y
 
 
@@ -338,8 +369,7 @@ def poisson_adjoint(g: np.ndarray, reading: str = "B") -> np.ndarray:
     """S^T g for the real-linear map S: f -> u of poisson(), by transposing each
     step: restriction -> zero-extension, Re -> real embedding, complex-linear
     maps -> conjugate transposes, row replacement and Nyquist removal ->
-    transposed system matrices, DFS doubling -> folding of mirrored rows.
-    Dense per-k solves, so for small grids only."""
+    transposed system matrices, DFS doubling -> folding of mirrored rows."""
     g = np.asarray(g, dtype=np.float64)
     nt, n = g.shape
     m = 2 * nt

@@ -238,6 +238,15 @@ class Workload:
         u = synthesize(poisson_exact(c), self.n_theta, self.n_lambda, device)
         return f, u
 
+    def observation(self, device="cpu"):
+        """u_obs for the inverse-source fit: the seeded series sampled on the grid
+        plus i.i.d. N(0, noise_sigma^2) noise (seed + 1), float64 [n_theta, n_lambda]."""
+        c = self.coeffs()
+        u = synthesize(c, self.n_theta, self.n_lambda, device)
+        rng = np.random.Generator(np.random.PCG64(self.seed + 1))
+        noise = rng.standard_normal((self.n_theta, self.n_lambda)) * self.noise_sigma
+        return u + torch.tensor(noise, dtype=torch.float64, device=u.device)
+
 
 # Seeds follow 1510080940 + workload number.
 WORKLOADS = {
@@ -246,6 +255,8 @@ WORKLOADS = {
     "sh1024_2048x4096": Workload("sh1024_2048x4096", 2048, 4096, 1024, 1510080943, "inv_sq"),
     "sh2048_4096x8192": Workload("sh2048_4096x8192", 4096, 8192, 2048, 1510080943, "inv_sq"),
     "sh200_512x1024_noisy": Workload("sh200_512x1024_noisy", 512, 1024, 200, 1510080945, "inv_sq", 1e-3),
+    # the paper-comparable size: mn/2 = 1.03e8 unknowns (its "100 million in a minute")
+    "sh2000_7168x14336": Workload("sh2000_7168x14336", 7168, 14336, 2000, 1510080946, "inv_sq"),
 }
 # the batched workload (4096 uneven spheres) is built by batched_workload()
 

@@ -338,3 +338,21 @@ def test_adjoint_gradient_central_difference():
         e[idx] = 1.0
         fd = (loss(f + h * e) - loss(f - h * e)) / (2 * h)
         assert abs(fd - grad[idx]) < 1e-7 * max(1.0, abs(fd))
+
+
+def test_banded_adjoint_matches_dense_adjoint():
+    # the banded transposed solves (used above m = 256) against dense LU
+    nt, nl = 140, 40
+    rng = np.random.default_rng(12)
+    g = rng.standard_normal((nt, nl))
+    b = O.poisson_adjoint(g)
+    old = O.DENSE_MAX_M
+    try:
+        O.DENSE_MAX_M = 10 ** 6
+        a = O.poisson_adjoint(g)
+    finally:
+        O.DENSE_MAX_M = old
+    assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()
+    f = rng.standard_normal((nt, nl))
+    x = np.sum(O.poisson(f) * g)
+    assert abs(x - np.sum(f * b)) < 1e-12 * max(1.0, abs(x))
