@@ -164,6 +164,33 @@ int sphere_poisson_solve_host(sp_plan_t plan, const double* f_host, double* u_ho
 #define SP_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 int sphere_poisson_solve_noalloc(sp_plan_t plan, const double* f, double* u, void* stream);
 
+/*
+ * The transforms on their own (Section 4, "Computation of Fourier coefficients",
+ * eq. 2DFourierExpansion, and "Integration", eq. integrationCoeffs), on an
+ * SP_FP64 single-grid plan.
+ *
+ * sphere_poisson_coeffs2: coefficients X_{j,k} of f~ (the DFS doubling of f) in
+ *   f~(lambda, theta) = sum_{j,k} X_{j,k} e^{i j theta} e^{i k lambda},
+ *   written to coeffs as [n_theta][Kp] complex doubles (re, im interleaved),
+ *   Kp = n_lambda/2 + 1 rounded up to even: row j = 0..n_theta-1, column
+ *   k = 0..n_lambda/2, the last one holding k = -n_lambda/2; the pad column is
+ *   unspecified.  The other coefficients follow from the BMC symmetry
+ *   X_{-j,k} = (-1)^k X_{j,k} and from f being real, X_{j,-k} = (-1)^k conj X_{j,k};
+ *   the theta-Nyquist mode j = -n_theta is not represented.  Uses the workspace.
+ * sphere_poisson_sample: the inverse, values of the expansion on the grid
+ *   from coefficients in that layout (which must have the BMC symmetry a
+ *   function on the sphere has: k odd columns with X_{0,k} = 0).
+ * sphere_poisson_sum2: the surface integral of f over the unit sphere,
+ *   2 pi sum_j w_j X_{j,0}, written as one double to device memory `result`.
+ * All three are asynchronous on `stream`; coeffs and result are device pointers.
+ */
+int sphere_poisson_coeffs2(sp_plan_t plan, const double* f, void* coeffs, void* workspace,
+                           size_t workspace_bytes, void* stream);
+int sphere_poisson_sample(sp_plan_t plan, const void* coeffs, double* f, void* workspace,
+                          size_t workspace_bytes, void* stream);
+int sphere_poisson_sum2(sp_plan_t plan, const double* f, double* result, void* workspace,
+                        size_t workspace_bytes, void* stream);
+
 /* Number of kernel launches one solve (adjoint = 1) issues for this plan. */
 int sphere_poisson_launch_count(sp_plan_t plan, int adjoint, int* launches);
 

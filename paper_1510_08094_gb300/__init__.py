@@ -129,6 +129,42 @@ class Plan:
                    "sphere_poisson_solve_noalloc")
         return out
 
+    @property
+    def spectrum_shape(self):
+        """(n_theta, Kp) of the coefficient layout of coeffs2 / sample."""
+        kp = (self.n_lambda // 2 + 2) // 2 * 2
+        return (self.n_theta, kp)
+
+    def coeffs2(self, f: torch.Tensor, stream=None) -> torch.Tensor:
+        """2D Fourier coefficients X[j, k] of f~, j = 0..n_theta-1, k = 0..n_lambda/2
+        (the last column is k = -n_lambda/2), as a complex128 tensor [n_theta, Kp]."""
+        _check_grid(f, self.shape, "f")
+        out = torch.empty(self.spectrum_shape, dtype=torch.complex128, device=self.device)
+        ws = self._workspace(None)
+        _lib.check(self._lib.sphere_poisson_coeffs2(self._h, f.data_ptr(), out.data_ptr(), ws.data_ptr(),
+                                                    ws.numel(), _stream_ptr(stream)), "sphere_poisson_coeffs2")
+        return out
+
+    def sample(self, coeffs: torch.Tensor, stream=None) -> torch.Tensor:
+        """Grid values of the expansion with coefficients in the coeffs2 layout."""
+        if coeffs.dtype != torch.complex128 or tuple(coeffs.shape) != self.spectrum_shape or not coeffs.is_cuda:
+            raise ValueError("coeffs must be a complex128 CUDA tensor of spectrum_shape")
+        coeffs = coeffs.contiguous()
+        out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        ws = self._workspace(None)
+        _lib.check(self._lib.sphere_poisson_sample(self._h, coeffs.data_ptr(), out.data_ptr(), ws.data_ptr(),
+                                                   ws.numel(), _stream_ptr(stream)), "sphere_poisson_sample")
+        return out
+
+    def sum2(self, f: torch.Tensor, stream=None) -> float:
+        """Surface integral of f over the unit sphere (synchronises)."""
+        _check_grid(f, self.shape, "f")
+        res = torch.empty(2, dtype=torch.float64, device=self.device)
+        ws = self._workspace(None)
+        _lib.check(self._lib.sphere_poisson_sum2(self._h, f.data_ptr(), res.data_ptr(), ws.data_ptr(),
+                                                 ws.numel(), _stream_ptr(stream)), "sphere_poisson_sum2")
+        return float(res[0])
+
     def host_buffer_bytes(self) -> int:
         n = ctypes.c_size_t()
         _lib.check(self._lib.sphere_poisson_host_buffer_size(self._h, ctypes.byref(n)),

@@ -40,6 +40,9 @@ EXPORTED = (
     "sphere_poisson_host_buffer_size",
     "sphere_poisson_solve_host",
     "sphere_poisson_solve_noalloc",
+    "sphere_poisson_coeffs2",
+    "sphere_poisson_sample",
+    "sphere_poisson_sum2",
     "sphere_poisson_launch_count",
     "sphere_poisson_profile_begin",
     "sphere_poisson_profile_end",
@@ -83,6 +86,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.sphere_poisson_host_buffer_size.argtypes = [vp, psz]
     lib.sphere_poisson_solve_host.argtypes = [vp, vp, vp, vp, sz, vp]
     lib.sphere_poisson_solve_noalloc.argtypes = [vp, vp, vp, vp]
+    lib.sphere_poisson_coeffs2.argtypes = [vp, vp, vp, vp, sz, vp]
+    lib.sphere_poisson_sample.argtypes = [vp, vp, vp, vp, sz, vp]
+    lib.sphere_poisson_sum2.argtypes = [vp, vp, vp, vp, sz, vp]
     lib.sphere_poisson_launch_count.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int)]
     lib.sphere_poisson_profile_begin.argtypes = [vp, i32]
     lib.sphere_poisson_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32,

@@ -13,6 +13,7 @@ struct BatchClass {
   const cpx<double>* tw_col;
   const cpx<double>* post_row;
   const cpx<double>* post_col;
+  const cpx<double>* post_col_s;       // post_col / (2N), for the forward colatitude transform
   const int* perm_row;
   const int* perm_col;
   const double* row_scale;

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256) k_batched_fp64(BatchArgs a) {
     }
     for (int t = 0; t < tc; ++t) {
       theta_forward_tile<double, false, BIG>(t, sm, W, C.N, C.K, C.Kp, C.cols, C.col_fft, C.tw_col, C.perm_col,
-                                             C.post_col, inv_n, 1);
+                                             C.post_col_s, inv_n, 1);
       __syncthreads();
     }
     solve_chains_cta(W, C.fl, C.fiu, C.fcu, C.N, C.K, C.Kp);

@@ -1,4 +1,5 @@
 // FP64 transform and elimination kernels (and the FP64 zonal side path of the FP32 forms).
+#define SP_FP64_KERNELS
 #include "launchers.inl"
 #include "batched.cuh"
 
@@ -87,6 +88,10 @@ cudaError_t batched_fp64_occupancy(bool big, int threads, size_t smem, int* bloc
 void launch_batched_fp64(bool big, dim3 grid, int threads, size_t smem, cudaStream_t st, const BatchArgs& a) {
   if (big) k_batched_fp64<true><<<grid, threads, smem, st>>>(a);
   else k_batched_fp64<false><<<grid, threads, smem, st>>>(a);
+}
+
+void launch_sum2_finish(cudaStream_t st, const cpx<double>* C, int N, int Kp, double* out) {
+  k_sum2_finish<<<1, 256, 0, st>>>(C, N, Kp, out);
 }
 
 }  // namespace sp

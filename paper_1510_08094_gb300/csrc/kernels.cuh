@@ -162,7 +162,7 @@ __device__ __forceinline__ void rows_forward_tile(int tile, cpx<T>* __restrict__
   for (int r = 0; r < rows; ++r) {
    const int row = row0 + r;
    if (row >= nt) break;
-   const T rs = ADJ ? (T)1 : row_scale_t[row];
+   const T hrs = ADJ ? (T)1 : (T)0.5 * row_scale_t[row];   // half the row scale
    for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
     cpx<T> out = {(T)0, (T)0};
     if (k < K) {
@@ -170,13 +170,10 @@ __device__ __forceinline__ void rows_forward_tile(int tile, cpx<T>* __restrict__
       cpx<T> zk = Z[k == L ? 0 : k];
       cpx<T> zc = conj(Z[k == 0 ? 0 : L - k]);
       cpx<T> e = ldg_c(post + k);                 // exp(-2 pi i k / n)
-      cpx<T> s = (T)0.5 * (zk + zc);
-      cpx<T> t = cmul(e, zk - zc);                // G = s - (i/2) t
-      out = {fma((T)0.5, t.im, s.re), fma((T)-0.5, t.re, s.im)};
-      T scale;
-      if (ADJ) scale = (k == 0 || k == L) ? (T)1 : (T)2;
-      else scale = rs;
-      out = scale * out;
+      cpx<T> A = zk + zc, D = zk - zc;
+      // G = scale/2 * (A - i e D)
+      const T hs = ADJ ? ((k == 0 || k == L) ? (T)0.5 : (T)1) : hrs;
+      out = {hs * fma(e.re, D.im, fma(e.im, D.re, A.re)), hs * fma(-e.re, D.re, fma(e.im, D.im, A.im))};
     }
     W[(size_t)row * Kp + k] = out;
    }
@@ -229,10 +226,9 @@ __device__ __forceinline__ void rows_inverse_tile(int tile, cpx<T>* __restrict__
         up = (T)0.5 * up;
       }
       cpx<T> uc = conj(up);
-      cpx<T> e = conj(ldg_c(post + k));          // exp(+2 pi i k / n)
-      cpx<T> t = cmul(e, uk - uc);               // Z = (uk + uc) + i t
-      cpx<T> s = uk + uc;
-      z = {s.re - t.im, s.im + t.re};
+      cpx<T> e = ldg_c(post + k);                // conj(e) = exp(+2 pi i k / n)
+      cpx<T> A = uk + uc, D = uk - uc;           // Z = A + i conj(e) D
+      z = {fma(-e.re, D.im, fma(e.im, D.re, A.re)), fma(e.re, D.re, fma(e.im, D.im, A.im))};
     }
     sm[r * L + __ldg(perm + k)] = z;
   }
@@ -279,9 +275,11 @@ __global__ void __launch_bounds__(BIG ? 256 : 512) k_rows_inverse(
 // DST-II at j).
 //   forward: F_j = P_j / N (k even), F_j = -i P_{N-j} / N (k odd, F_0 = 0)
 //   adjoint: Xbar_j = c_j P_j (k even, c_0 = 1, c_j = 2), Xbar_j = -2i P_{N-j}
-//            (k odd, Xbar_0 = 0)  (transpose of theta_inverse); with zonal
-//            set (FP64 arithmetic), column 0 also gets the transposed k = 0
-//            closure.
+//            (k odd, Xbar_0 = 0)  (transpose of theta_inverse); with bit 1 of
+//            `zonal` set (FP64 arithmetic), column 0 also gets the transposed
+//            k = 0 closure.
+//   bit 2 of `zonal` multiplies the result by (-1)^k: the coefficients of the
+//   paper's expansion in e^{i k lambda} with lambda_q = -pi + 2 pi q/n.
 // One CTA per `cols` consecutive columns.  inv_n = 1/N in arithmetic T.
 // ---------------------------------------------------------------------------
 template <typename T, bool ADJ, bool BIG>
@@ -309,23 +307,25 @@ __device__ __forceinline__ void theta_forward_tile(int tile, cpx<T>* __restrict_
     int k = k0 + c;
     if (k >= K) continue;
     const cpx<T>* V = sm + c * N;
+    // p = w a + conj(w) b, with a = V_j, b = V_{N-j} (k even) or a = V_{N-j}, b = V_j
+    // (k odd); the forward passes the table w/(2N), the adjoint w itself
     cpx<T> out;
     if ((k & 1) == 0) {
       cpx<T> w = ldg_c(post + j);
       cpx<T> a = V[j], b = V[j == 0 ? 0 : N - j];
-      cpx<T> p = (T)0.5 * (cmul(w, a) + cmulc(b, w));
+      cpx<T> p = {fma(w.re, a.re + b.re, w.im * (b.im - a.im)), fma(w.re, a.im + b.im, w.im * (a.re - b.re))};
       if (ADJ) {
-        out = (j == 0 ? (T)1 : (T)2) * p;
+        out = j == 0 ? (T)0.5 * p : p;
         if constexpr (std::is_same<T, double>::value) {
           // transpose of the k = 0 closure X_0 = sum_{j even >= 2} 2 X_j/(j^2-1):
           // Xbar_j += 2 Xbar_0/(j^2-1), with Xbar_0 = P_0 = V_0
-          if (zonal && k == 0 && j >= 2 && !(j & 1)) {
+          if ((zonal & 1) && k == 0 && j >= 2 && !(j & 1)) {
             double wj = 2.0 / ((double)j * (double)j - 1.0);
             out = out + wj * V[0];
           }
         }
       } else {
-        out = inv_n * p;
+        out = p;
       }
     } else if (j == 0) {
       out = {(T)0, (T)0};
@@ -333,10 +333,9 @@ __device__ __forceinline__ void theta_forward_tile(int tile, cpx<T>* __restrict_
       int jj = N - j;
       cpx<T> w = ldg_c(post + jj);
       cpx<T> a = V[jj], b = V[j];
-      cpx<T> p = (T)0.5 * (cmul(w, a) + cmulc(b, w));
-      // forward: -i p / N ; adjoint: -2 i p
-      T s = ADJ ? (T)2 : inv_n;
-      out = {s * p.im, -(s * p.re)};
+      cpx<T> p = {fma(w.re, a.re + b.re, w.im * (b.im - a.im)), fma(w.re, a.im + b.im, w.im * (a.re - b.re))};
+      out = {p.im, -p.re};                       // -i p
+      if (zonal & 2) out = {-out.re, -out.im};   // coefficient convention: times (-1)^k, k odd
     }
     W[(size_t)j * Kp + k] = out;
   }
@@ -357,9 +356,10 @@ __global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_forward(
 // with Y = X, or for k odd i (-1)^i times the DCT-III of Y_j = X_{N-j} (Y_0 = 0),
 // through one inverse FFT of V_j = exp(i pi j/(2N)) (Y_j - i Y_{N-j}) (Y_N = 0)
 // and the inverse Makhoul reordering.
-//   forward: U = DCT-III(X) (k even), i DST-III(X) (k odd); with zonal set
-//            (FP64 arithmetic) the first CTA first closes the k = 0 column:
-//            X_00 = sum_{j even >= 2} 2 X_j0/(j^2-1) (w^T X_0 = 0).
+//   forward: U = DCT-III(X) (k even), i DST-III(X) (k odd); with bit 1 of
+//            `zonal` set (FP64 arithmetic) the first CTA first closes the
+//            k = 0 column: X_00 = sum_{j even >= 2} 2 X_j0/(j^2-1) (w^T X_0 = 0);
+//            bit 2 takes the input in the coefficient convention (times (-1)^k).
 //   adjoint: inputs with j >= 1 halved and outputs scaled by inv_n = 1/N: the
 //            transpose of theta_forward
 // ---------------------------------------------------------------------------
@@ -370,7 +370,7 @@ __device__ __forceinline__ void theta_inverse_tile(int tile, cpx<T>* __restrict_
     T inv_n, int zonal) {
   const int k0 = tile * cols;
   if constexpr (std::is_same<T, double>::value) {
-    if (!ADJ && zonal && k0 == 0) {
+    if (!ADJ && (zonal & 1) && k0 == 0) {
       cpx<double> acc = {0.0, 0.0};
       for (int j = 2 + 2 * threadIdx.x; j < N; j += 2 * blockDim.x) {
         double wj = 2.0 / ((double)j * (double)j - 1.0);
@@ -416,6 +416,10 @@ __device__ __forceinline__ void theta_inverse_tile(int tile, cpx<T>* __restrict_
     if (ADJ) {
       xa = (T)0.5 * xa;
       xb = (T)0.5 * xb;
+    }
+    if ((zonal & 2) && odd) {                  // input in the coefficient convention
+      xa = {-xa.re, -xa.im};
+      xb = {-xb.re, -xb.im};
     }
     // Y_j, Y_{N-j}
     cpx<T> ya = odd ? xb : xa;
@@ -792,6 +796,30 @@ __global__ void __launch_bounds__(512) k_zonal_scan(cpx<double>* __restrict__ Z,
     Z[row(t)] = x;
   }
 }
+
+#ifdef SP_FP64_KERNELS  // defined only in the FP64 translation unit
+// Surface integral from the k = 0 coefficient column A_j (j >= 0) of f~
+// (Section 4, Integration, eq. integrationCoeffs): int_S f = 2 pi sum_j w_j A_j
+// over j = -(N-1)..N-1, w_j = 2/(1-j^2) for even j, 0 for odd j; the column is
+// theta-even (A_{-j} = A_j), so the sum is 2 A_0 + 4 sum_{j even >= 2} A_j/(1-j^2).
+__global__ void k_sum2_finish(const cpx<double>* __restrict__ C, int N, int Kp, double* __restrict__ out) {
+  double acc = 0.0;
+  for (int j = 2 + 2 * threadIdx.x; j < N; j += 2 * blockDim.x) {
+    double jd = (double)j;
+    acc += C[(size_t)j * Kp].re / (1.0 - jd * jd);
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    const double two_pi = 6.283185307179586476925286766559;
+    *out = two_pi * (2.0 * C[0].re + 4.0 * t);
+  }
+}
+#endif  // SP_FP64_KERNELS
 
 #ifdef SP_REFINE_KERNELS  // defined only in the double-float translation unit
 // ---------------------------------------------------------------------------

@@ -55,6 +55,9 @@ void launch_zonal_scan(bool adj, cudaStream_t st, cpx<double>* Z, const double* 
 cudaError_t batched_fp64_occupancy(bool big, int threads, size_t smem, int* blocks_per_sm);
 void launch_batched_fp64(bool big, dim3 grid, int threads, size_t smem, cudaStream_t st, const BatchArgs& a);
 
+// surface integral from the k = 0 coefficient column (one CTA, result to device memory)
+void launch_sum2_finish(cudaStream_t st, const cpx<double>* C, int N, int Kp, double* out);
+
 void launch_refine(const Launch& l, const cpx<dd>* F, cpx<dd>* X, cpx<float>* Y, const float* fl,
                    const float* fiu, const float* fcu, int N, int K, int Kp, int first);
 void launch_zonal_extract(const Launch& l, const cpx<dd>* Wdd, cpx<double>* Z, int N, int Kp);

@@ -149,15 +149,18 @@ struct sp_plan_s {
   cpx<double>* tw_col;   // exp(-2 pi i t/N), t < N
   cpx<double>* post_row; // exp(-2 pi i k/n), k <= L
   cpx<double>* post_col; // exp(-i pi j/(2N)), j <= N
+  cpx<double>* post_col_s; // the same times 1/(2N) (forward colatitude transform)
   int* perm_row;         // digit reversal of the length-L passes
   int* perm_col;         // digit reversal of the length-N passes
   double* row_scale;     // sin^2(theta_i)/n
+  double* row_plain;     // 1/n (transforms without the sin^2 weight)
   void* row_scale_t;     // the same in float (SP_FP32) or double-float (SP_FP32_REFINE)
   // the same tables in float (SP_FP32) or double-float (SP_FP32_REFINE)
   void* tw_row_t;
   void* tw_col_t;
   void* post_row_t;
   void* post_col_t;
+  void* post_col_s_t;    // post_col_s in the plan's arithmetic
   // factorised parity tridiagonals l, 1/u, c/u: FP64 [N][Kp] (SP_FP64),
   // float [N][Kp] (FP32 forms) and FP64 [N][2] for the zonal column (FP32 forms)
   double* fac_l;
@@ -241,7 +244,7 @@ void enqueue_fp64(sp_plan_t p, bool adj, const double* in, double* out, void* ws
                                   nullptr);
   m.mark(1);
   sp::launch_theta_forward<double>(adj, p->big_col, cols, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
-                                   p->tw_col, p->perm_col, p->post_col, inv_n, 1);
+                                   p->tw_col, p->perm_col, adj ? p->post_col : p->post_col_s, inv_n, 1);
   m.mark(2);
   sp::launch_solve<double>(adj, solve, W, p->fac_l, p->fac_iu, p->fac_cu, p->N, p->K, p->Kp);
   m.mark(3);
@@ -260,7 +263,7 @@ void enqueue_zonal_fp64(sp_plan_t p, bool adj, cpx<double>* Z, cudaStream_t st) 
   const double inv_n = 1.0 / (double)p->N;
   const sp::Launch one{dim3(1), p->zcol_threads, p->zcol_smem, st};
   sp::launch_theta_forward<double>(adj, p->big_col, one, Z, p->N, 1, 2, 1, p->col_fft, p->tw_col, p->perm_col,
-                                   p->post_col, inv_n, 1);
+                                   adj ? p->post_col : p->post_col_s, inv_n, 1);
   sp::launch_zonal_scan(adj, st, Z, p->z_l, p->z_iu, p->z_cu, p->N);
   sp::launch_theta_inverse<double>(adj, p->big_col, one, Z, p->N, 1, 2, 1, p->col_fft, p->tw_col, p->perm_col,
                                    p->post_col, inv_n, 1);
@@ -289,7 +292,8 @@ void enqueue_fp32(sp_plan_t p, bool adj, const double* in, double* out, void* ws
   cudaEventRecord(p->ev_join, p->side);
   m.mark(1);
   sp::launch_theta_forward<float>(adj, p->big_col, cols, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
-                                  twc, p->perm_col, poc, inv_n, 0);
+                                  twc, p->perm_col, adj ? poc : static_cast<const cpx<float>*>(p->post_col_s_t),
+                                  inv_n, 0);
   m.mark(2);
   sp::launch_solve<float>(adj, solve, W, p->f32_l, p->f32_iu, p->f32_cu, p->N, p->K, p->Kp);
   m.mark(3);
@@ -327,7 +331,7 @@ void enqueue_refine(sp_plan_t p, const double* in, double* out, void* ws, cudaSt
                               static_cast<const dd*>(p->row_scale_t), nullptr);
   m.mark(1);
   sp::launch_theta_forward<dd>(false, p->big_col, cols, Fd, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
-                               twc, p->perm_col, poc, inv_n, 0);
+                               twc, p->perm_col, static_cast<const cpx<dd>*>(p->post_col_s_t), inv_n, 0);
   cudaEventRecord(p->ev_fork, st);
   cudaStreamWaitEvent(p->side, p->ev_fork, 0);
   {
@@ -516,6 +520,8 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   for (int t = 0; t < p->N; ++t) unit_root(t, p->N, &tw_col[t].re, &tw_col[t].im);
   for (int k = 0; k <= p->L; ++k) unit_root(k, n_lambda, &post_row[k].re, &post_row[k].im);
   for (int j = 0; j <= p->N; ++j) unit_root(j, 4L * p->N, &post_col[j].re, &post_col[j].im);
+  std::vector<cpx<double>> post_col_s(p->N + 1);
+  for (int j = 0; j <= p->N; ++j) post_col_s[j] = {post_col[j].re * (0.5 / p->N), post_col[j].im * (0.5 / p->N)};
   std::vector<int> perm_row, perm_col;
   digit_reversal(rd, perm_row);
   digit_reversal(cd, perm_col);
@@ -525,7 +531,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
     unit_root(2 * i + 1, 4L * p->N, &re, &im);  // sin(theta_i) = -im
     row_scale[i] = (im * im) / (double)n_lambda;
   }
-  std::vector<char> t_tw_row, t_tw_col, t_post_row, t_post_col, t_scale;
+  std::vector<char> t_tw_row, t_tw_col, t_post_row, t_post_col, t_post_col_s, t_scale;
   if (precision == SP_FP32) {
     t_scale.resize(p->nt * sizeof(float));
     for (int i = 0; i < p->nt; ++i) reinterpret_cast<float*>(t_scale.data())[i] = (float)row_scale[i];
@@ -533,6 +539,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
     upload_table<float>(tw_col, t_tw_col);
     upload_table<float>(post_row, t_post_row);
     upload_table<float>(post_col, t_post_col);
+    upload_table<float>(post_col_s, t_post_col_s);
   } else if (precision == SP_FP32_REFINE) {
     t_scale.resize(p->nt * sizeof(sp::dd));
     for (int i = 0; i < p->nt; ++i) reinterpret_cast<sp::dd*>(t_scale.data())[i] = sp::dd(row_scale[i]);
@@ -540,6 +547,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
     upload_table<sp::dd>(tw_col, t_tw_col);
     upload_table<sp::dd>(post_row, t_post_row);
     upload_table<sp::dd>(post_col, t_post_col);
+    upload_table<sp::dd>(post_col_s, t_post_col_s);
   }
 
   size_t off = 0;
@@ -550,11 +558,14 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   };
   size_t o_tw_row = take(p->L * cd_sz), o_tw_col = take(p->N * cd_sz);
   size_t o_post_row = take((p->L + 1) * cd_sz), o_post_col = take((p->N + 1) * cd_sz);
+  size_t o_post_col_s = take((p->N + 1) * cd_sz);
   size_t o_scale = take(p->nt * sizeof(double));
+  size_t o_plain = take(p->nt * sizeof(double));
   size_t o_perm_row = take(p->L * sizeof(int)), o_perm_col = take(p->N * sizeof(int));
   size_t o_t_tw_row = take(t_tw_row.size()), o_t_tw_col = take(t_tw_col.size());
   size_t o_t_post_row = take(t_post_row.size()), o_t_post_col = take(t_post_col.size());
   size_t o_t_scale = take(t_scale.size());
+  size_t o_t_post_col_s = take(t_post_col_s.size());
   const size_t fac64 = precision == SP_FP64 ? grid * sizeof(double) : 0;
   const size_t fac32 = precision == SP_FP64 ? 0 : grid * sizeof(float);
   const size_t facz = precision == SP_FP64 ? 0 : (size_t)p->N * 2 * sizeof(double);
@@ -579,7 +590,9 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   p->tw_col = reinterpret_cast<cpx<double>*>(base + o_tw_col);
   p->post_row = reinterpret_cast<cpx<double>*>(base + o_post_row);
   p->post_col = reinterpret_cast<cpx<double>*>(base + o_post_col);
+  p->post_col_s = reinterpret_cast<cpx<double>*>(base + o_post_col_s);
   p->row_scale = reinterpret_cast<double*>(base + o_scale);
+  p->row_plain = reinterpret_cast<double*>(base + o_plain);
   p->perm_row = reinterpret_cast<int*>(base + o_perm_row);
   p->perm_col = reinterpret_cast<int*>(base + o_perm_col);
   p->tw_row_t = base + o_t_tw_row;
@@ -587,6 +600,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   p->post_row_t = base + o_t_post_row;
   p->post_col_t = base + o_t_post_col;
   p->row_scale_t = base + o_t_scale;
+  p->post_col_s_t = base + o_t_post_col_s;
   p->fac_l = reinterpret_cast<double*>(base + o_l);
   p->fac_iu = reinterpret_cast<double*>(base + o_iu);
   p->fac_cu = reinterpret_cast<double*>(base + o_cu);
@@ -605,7 +619,13 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   up(p->tw_col, tw_col.data(), p->N * cd_sz, "copy tw_col");
   up(p->post_row, post_row.data(), (p->L + 1) * cd_sz, "copy post_row");
   up(p->post_col, post_col.data(), (p->N + 1) * cd_sz, "copy post_col");
+  up(p->post_col_s, post_col_s.data(), (p->N + 1) * cd_sz, "copy post_col_s");
+  up(p->post_col_s_t, t_post_col_s.data(), t_post_col_s.size(), "copy post_col_s_t");
   up(p->row_scale, row_scale.data(), p->nt * sizeof(double), "copy row_scale");
+  {
+    std::vector<double> plain(p->nt, 1.0 / (double)n_lambda);
+    up(p->row_plain, plain.data(), p->nt * sizeof(double), "copy row_plain");
+  }
   up(p->perm_row, perm_row.data(), p->L * sizeof(int), "copy perm_row");
   up(p->perm_col, perm_col.data(), p->N * sizeof(int), "copy perm_col");
   up(p->tw_row_t, t_tw_row.data(), t_tw_row.size(), "copy tw_row_t");
@@ -652,7 +672,7 @@ constexpr int kBatchThreads = 256;
 struct HostClass {
   int nt, nl;
   FftDesc rd, cd;
-  std::vector<cpx<double>> tw_row, tw_col, post_row, post_col;
+  std::vector<cpx<double>> tw_row, tw_col, post_row, post_col, post_col_s;
   std::vector<int> perm_row, perm_col;
   std::vector<double> row_scale;
 };
@@ -809,7 +829,7 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
     off = align(off + bytes);
     return o;
   };
-  struct Offs { size_t tw_row, tw_col, post_row, post_col, perm_row, perm_col, scale, fl, fiu, fcu; };
+  struct Offs { size_t tw_row, tw_col, post_row, post_col, post_col_s, perm_row, perm_col, scale, fl, fiu, fcu; };
   std::vector<Offs> co(nc);
   bool big = false;
   size_t max_slot = 0;
@@ -835,6 +855,8 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
     for (int t = 0; t < b.N; ++t) unit_root(t, b.N, &h.tw_col[t].re, &h.tw_col[t].im);
     for (int k = 0; k <= b.L; ++k) unit_root(k, b.nl, &h.post_row[k].re, &h.post_row[k].im);
     for (int j = 0; j <= b.N; ++j) unit_root(j, 4L * b.N, &h.post_col[j].re, &h.post_col[j].im);
+    h.post_col_s.resize(b.N + 1);
+    for (int j = 0; j <= b.N; ++j) h.post_col_s[j] = {h.post_col[j].re * (0.5 / b.N), h.post_col[j].im * (0.5 / b.N)};
     digit_reversal(h.rd, h.perm_row);
     digit_reversal(h.cd, h.perm_col);
     h.row_scale.resize(b.nt);
@@ -845,7 +867,7 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
     }
     const size_t csz = sizeof(cpx<double>), fac = (size_t)b.N * b.Kp * sizeof(double);
     co[c] = {take(b.L * csz), take(b.N * csz), take((b.L + 1) * csz), take((b.N + 1) * csz),
-             take(b.L * sizeof(int)), take(b.N * sizeof(int)), take(b.nt * sizeof(double)),
+             take((b.N + 1) * csz), take(b.L * sizeof(int)), take(b.N * sizeof(int)), take(b.nt * sizeof(double)),
              take(fac), take(fac), take(fac)};
   }
   const size_t o_cls = take(nc * sizeof(sp::BatchClass) + 1);
@@ -875,6 +897,7 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
     b.tw_col = reinterpret_cast<cpx<double>*>(base + co[c].tw_col);
     b.post_row = reinterpret_cast<cpx<double>*>(base + co[c].post_row);
     b.post_col = reinterpret_cast<cpx<double>*>(base + co[c].post_col);
+    b.post_col_s = reinterpret_cast<cpx<double>*>(base + co[c].post_col_s);
     b.perm_row = reinterpret_cast<int*>(base + co[c].perm_row);
     b.perm_col = reinterpret_cast<int*>(base + co[c].perm_col);
     b.row_scale = reinterpret_cast<double*>(base + co[c].scale);
@@ -885,6 +908,7 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
     step(cudaMemcpy((void*)b.tw_col, h.tw_col.data(), b.N * csz, cudaMemcpyHostToDevice), "copy");
     step(cudaMemcpy((void*)b.post_row, h.post_row.data(), (b.L + 1) * csz, cudaMemcpyHostToDevice), "copy");
     step(cudaMemcpy((void*)b.post_col, h.post_col.data(), (b.N + 1) * csz, cudaMemcpyHostToDevice), "copy");
+    step(cudaMemcpy((void*)b.post_col_s, h.post_col_s.data(), (b.N + 1) * csz, cudaMemcpyHostToDevice), "copy");
     step(cudaMemcpy((void*)b.perm_row, h.perm_row.data(), b.L * sizeof(int), cudaMemcpyHostToDevice), "copy");
     step(cudaMemcpy((void*)b.perm_col, h.perm_col.data(), b.N * sizeof(int), cudaMemcpyHostToDevice), "copy");
     step(cudaMemcpy((void*)b.row_scale, h.row_scale.data(), b.nt * sizeof(double), cudaMemcpyHostToDevice), "copy");
@@ -1111,6 +1135,69 @@ int sphere_poisson_solve_noalloc(sp_plan_t plan, const double* f, double* u, voi
   int rc = noalloc_scratch(dev, &scratch);
   if (rc != SP_OK) return rc;
   return launch_solve<false>(plan, f, u, scratch, static_cast<cudaStream_t>(stream));
+}
+
+static int check_transform_plan(sp_plan_t plan, const void* a, const void* b, const void* ws, size_t ws_bytes) {
+  int rc = check_arrays(plan, a, b, ws, ws_bytes);
+  if (rc != SP_OK) return rc;
+  if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
+  return SP_OK;
+}
+
+// forward transforms of f (no sin^2 weight) into W, coefficient sign convention
+static void enqueue_coeffs2(sp_plan_t p, const double* f, cpx<double>* W, int kcols, cudaStream_t st) {
+  using sp::Launch;
+  const Launch rows{dim3((p->nt + p->rows_per_cta - 1) / p->rows_per_cta), p->row_threads, p->row_smem, st};
+  const int K = kcols;
+  const Launch cols{dim3((K + p->cols_per_cta - 1) / p->cols_per_cta), p->col_threads, p->col_smem, st};
+  sp::launch_rows_forward<double>(false, p->big_row, rows, f, W, p->nt, p->nl, p->Kp, p->rows_per_cta,
+                                  p->row_fft, p->tw_row, p->perm_row, p->post_row, p->row_plain, p->row_plain,
+                                  nullptr);
+  sp::launch_theta_forward<double>(false, p->big_col, cols, W, p->N, K, p->Kp, p->cols_per_cta, p->col_fft,
+                                   p->tw_col, p->perm_col, p->post_col_s, 1.0 / p->N, 2);
+}
+
+int sphere_poisson_coeffs2(sp_plan_t plan, const double* f, void* coeffs, void* workspace, size_t workspace_bytes,
+                           void* stream) {
+  int rc = check_transform_plan(plan, f, coeffs, workspace, workspace_bytes);
+  if (rc != SP_OK) return rc;
+  (void)workspace;
+  enqueue_coeffs2(plan, f, static_cast<cpx<double>*>(coeffs), plan->K, static_cast<cudaStream_t>(stream));
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SP_OK : cuda_fail(e, "coeffs2 launch");
+}
+
+int sphere_poisson_sample(sp_plan_t plan, const void* coeffs, double* f, void* workspace, size_t workspace_bytes,
+                          void* stream) {
+  int rc = check_transform_plan(plan, coeffs, f, workspace, workspace_bytes);
+  if (rc != SP_OK) return rc;
+  using sp::Launch;
+  sp_plan_t p = plan;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cpx<double>* W = static_cast<cpx<double>*>(workspace);
+  cudaError_t e = cudaMemcpyAsync(W, coeffs, (size_t)p->N * p->Kp * sizeof(cpx<double>), cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "sample copy");
+  const Launch rows{dim3((p->nt + p->rows_per_cta - 1) / p->rows_per_cta), p->row_threads, p->row_smem, st};
+  const Launch cols{dim3((p->K + p->cols_per_cta - 1) / p->cols_per_cta), p->col_threads, p->col_smem, st};
+  sp::launch_theta_inverse<double>(false, p->big_col, cols, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
+                                   p->tw_col, p->perm_col, p->post_col, 1.0 / p->N, 2);
+  sp::launch_rows_inverse<double>(false, p->big_row, rows, W, f, p->nt, p->nl, p->Kp, p->rows_per_cta,
+                                  p->row_fft, p->tw_row, p->perm_row, p->post_row, p->row_scale, p->row_scale,
+                                  nullptr);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? SP_OK : cuda_fail(e, "sample launch");
+}
+
+int sphere_poisson_sum2(sp_plan_t plan, const double* f, double* result, void* workspace, size_t workspace_bytes,
+                        void* stream) {
+  int rc = check_transform_plan(plan, f, result, workspace, workspace_bytes);
+  if (rc != SP_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cpx<double>* W = static_cast<cpx<double>*>(workspace);
+  enqueue_coeffs2(plan, f, W, 1, st);  // only the k = 0 column is transformed in colatitude
+  sp::launch_sum2_finish(st, W, plan->N, plan->Kp, result);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SP_OK : cuda_fail(e, "sum2 launch");
 }
 
 int sphere_poisson_launch_count(sp_plan_t plan, int adjoint, int* launches) {
