@@ -34,9 +34,53 @@ if ROOT not in sys.path:
 METRIC = "Poisson DOF/s on 1 GB300 at stated error vs FP64 oracle"
 WORKLOAD = "sh2000_5000x10000"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 pipe peak if the live probe fails: 504 G DFMA/s measured on this machine's
-# GB300 (profiles/fp64_fp32_peak_probe.md) = 1008 GFLOP/s counting an FMA as 2 flops.
+# FP64 pipe peak if the live probe fails: 504 G DFMA/s measured on a GB300
+# (profiles/fp64_fp32_peak_probe.md) = 1008 GFLOP/s counting an FMA as 2 flops.
 FP64_PEAK_GFLOPS_FALLBACK = 1008.0
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each FP64
+# stage kernel, from one ncu capture of the 4096 x 8192 workload (inputs 268 MB, larger
+# than L2) on the kernel sources whose hash is `csrc_sha256`; see
+# profiles/traffic_fp64_4096x8192.md.  bench.py scales them to its own grid by the
+# spectrum size n_theta * Kp (every stage streams the spectrum once or twice) and
+# reports null when the sources have changed since the capture.
+TRAFFIC_CAPTURE = {
+    "csrc_sha256": "ff69b87e3fdb7438",
+    "n_theta": 4096, "n_lambda": 8192,
+    "bytes": {"rows_forward": 268681472 + 223775488, "theta_forward": 269292032 + 210642688,
+              "solve": 901552384 + 457566720, "theta_inverse": 269249536 + 210393088,
+              "rows_inverse": 269476608 + 219835904},
+}
+
+
+def csrc_hash() -> str:
+    """First 16 hex digits of SHA-256 over the kernel sources (names and bytes, sorted)."""
+    import hashlib
+
+    d = os.path.join(ROOT, "paper_1510_08094_gb300", "csrc")
+    h = hashlib.sha256()
+    for n in sorted(os.listdir(d)):
+        q = os.path.join(d, n)
+        if os.path.isfile(q):
+            h.update(n.encode())
+            with open(q, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(stage: str, n_theta: int, n_lambda: int, precision: str):
+    """(bytes per launch, note) of an FP64 stage kernel scaled from the ncu capture,
+    or (None, why) when no capture of the current sources exists."""
+    cap = TRAFFIC_CAPTURE
+    if precision != "fp64":
+        return None, "no ncu traffic capture of the reduced-precision kernels on these sources"
+    if csrc_hash() != cap["csrc_sha256"]:
+        return None, "kernel sources changed since the ncu traffic capture"
+    kp = lambda nl: (nl // 2 + 2) // 2 * 2
+    ratio = (n_theta * kp(n_lambda)) / (cap["n_theta"] * kp(cap["n_lambda"]))
+    note = (f"ncu dram read+write of one {cap['n_theta']}x{cap['n_lambda']} launch x {ratio:.4f} "
+            f"(spectrum-size ratio); writes still dirty in L2 at kernel end are not counted")
+    return int(cap["bytes"][stage] * ratio), note
 
 
 def _env_int(name, default):
@@ -232,8 +276,11 @@ def run_ours(args):
         if args.precision == "fp32_refine":
             roofline["note"] = ("double-float arithmetic on the FP32 pipes; achieved counts conventional "
                                 "FP64-equivalent flops against the FP64 pipe peak")
+    traffic, traffic_note = traffic_for(dom, N, n, args.precision)
     roofline.update({
-        "traffic": None,
+        "traffic": traffic,
+        "traffic_note": traffic_note,
+        "algorithmic_bytes": int(bytes_[dom]),
         "hbm_achieved_gbs": round(hbm_gbs, 1),
         "hbm_peak_gbs": hbm_peak,
         "stage_ms_per_solve": {k: round(v / max(recorded, 1), 4) for k, v in stage_ms.items()},
@@ -354,7 +401,7 @@ def measure_batched(sp, dev, args):
     """4096 spheres of uneven resolution (n_theta = 16 s, s uniform in 2..32,
     n_lambda = 2 n_theta, SH series l <= n_theta/2) in one persistent launch
     with autotuned tiles, against the same problems solved one by one with
-    single-problem FP64 plans."""
+    single-problem FP64 plans; then the same batch in FP32 + refinement."""
     import tempfile
 
     import torch
@@ -403,11 +450,41 @@ def measure_batched(sp, dev, args):
     torch.cuda.synchronize()
     ms_plain = e0.elapsed_time(e1)
     dof = plan.offsets[-1]
-    return {"value": dof / (ms * 1e-3), "unit": "DOF/s", "ms_per_batch": ms, "problems": len(sizes),
-            "dof_per_batch": dof, "distinct_sizes": len(set(sizes)), "gpu_launches_per_batch": plan.launches(),
-            "plain_fp64_loop_ms": ms_plain, "speedup_vs_plain_fp64_loop": ms_plain / ms,
-            "max_rel_err_vs_closed_form": worst, "autotuned": True, "plan_seconds": t_plan,
-            "input_generation_seconds": t_gen}
+    del outs, views, singles
+    out = {"value": dof / (ms * 1e-3), "unit": "DOF/s", "ms_per_batch": ms, "problems": len(sizes),
+           "dof_per_batch": dof, "distinct_sizes": len(set(sizes)), "gpu_launches_per_batch": plan.launches(),
+           "plain_fp64_loop_ms": ms_plain, "speedup_vs_plain_fp64_loop": ms_plain / ms,
+           "max_rel_err_vs_closed_form": worst, "autotuned": True, "plan_seconds": t_plan,
+           "input_generation_seconds": t_gen}
+
+    # the same batch in FP32 + refinement (one sweep), one persistent launch
+    sweeps = 1
+    t0 = time.perf_counter()
+    rplan = sp.BatchedPlan(sizes, precision="fp32_refine", refine_sweeps=sweeps, autotune=True, device=dev)
+    t_rplan = time.perf_counter() - t0
+    del ws
+    rws = torch.empty(rplan.workspace_bytes, dtype=torch.uint8, device=dev)
+    ur = torch.empty_like(f)
+    for _ in range(2):
+        rplan.solve(f, ur, rws)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        rplan.solve(f, ur, rws)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_r = e0.elapsed_time(e1) / reps
+    worst_r = worst_r64 = 0.0
+    for b in range(len(sizes)):
+        a, c = plan.offsets[b], plan.offsets[b + 1]
+        worst_r = max(worst_r, float((ur[a:c] - ue[a:c]).abs().max() / ue[a:c].abs().max()))
+        worst_r64 = max(worst_r64, float((ur[a:c] - u[a:c]).abs().max() / u[a:c].abs().max()))
+    out["fp32_refine"] = {"value": dof / (ms_r * 1e-3), "unit": "DOF/s", "ms_per_batch": ms_r,
+                          "refine_sweeps": sweeps, "speedup_vs_batched_fp64": ms / ms_r,
+                          "max_rel_err_vs_batched_fp64": worst_r64, "max_rel_err_vs_closed_form": worst_r,
+                          "gpu_launches_per_batch": rplan.launches(), "autotuned": True,
+                          "plan_seconds": t_rplan}
+    return out
 
 
 def _oracle_sample(f_np, ks):

@@ -65,8 +65,13 @@ typedef struct sp_plan_s* sp_plan_t;
  *   n_theta >= 1, n_lambda >= 2 and even (the glide reflection lambda -> lambda+pi
  *   of eq. BMCsphere must map the grid to itself); n_theta and n_lambda/2 must
  *   factor into primes <= 31 and be at most 12288.
- *   precision     SP_FP64 (others return SP_ERR_UNSUPPORTED until built).
- *   refine_sweeps number of FP64 residual sweeps for SP_FP32_REFINE (else ignored).
+ *   precision     SP_FP64; SP_FP32 (FP32 transforms and eliminations, the ill-
+ *                 conditioned k = 0 column in FP64); or SP_FP32_REFINE (double-
+ *                 float transforms, FP32 eliminations refined by residual sweeps
+ *                 computed to FP64 accuracy, the k = 0 column in FP64).  Other
+ *                 values return SP_ERR_UNSUPPORTED.
+ *   refine_sweeps 0..16 residual sweeps for SP_FP32_REFINE (ignored otherwise;
+ *                 outside 0..16 SP_ERR_BAD_ARG).
  *   flags         reserved, pass 0.
  *   workspace_bytes (out, optional) device workspace the solve calls need.
  * Synchronous: allocates the plan's device tables and fills them on the
@@ -84,7 +89,9 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
  * sizes share tables.  f and u of the solve calls are then the problems'
  * [n_theta][n_lambda] arrays packed back to back in problem order, problem b
  * starting at offsets[b] doubles (sphere_poisson_batch_offsets).
- *   precision   SP_FP64.
+ *   precision   SP_FP64, or SP_FP32_REFINE (the arithmetic of the single-plan
+ *               form, refine_sweeps 0..16 as there; SP_FP32 returns
+ *               SP_ERR_UNSUPPORTED).
  *   flags       0, or SP_FLAG_AUTOTUNE: time the transform tiles (rows / columns
  *               per CTA pass) of every problem size at plan time and keep the
  *               fastest; results are cached in the file named by the

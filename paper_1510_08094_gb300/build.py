@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB_NAME = "libsphere_poisson.so"
 LIB_PATH = os.path.join(BUILD, LIB_NAME)
-SOURCES = ["sphere_poisson.cu", "pipe_probe.cu", "k_f64.cu", "k_f32.cu", "k_dd.cu"]
+SOURCES = ["sphere_poisson.cu", "pipe_probe.cu", "k_f64.cu", "k_f32.cu", "k_dd.cu", "k_batched_dd.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -66,14 +66,17 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tag = f"{os.getpid()}"
     objs = [os.path.join(BUILD, os.path.splitext(s)[0] + f".{tag}.o") for s in SOURCES]
     jobs = [[nvcc] + flags + ["-c", os.path.join(CSRC, s), "-o", o] for s, o in zip(SOURCES, objs)]
-    with concurrent.futures.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
-        for fut in [ex.submit(_run, j, verbose) for j in jobs]:
-            fut.result()
     tmp = LIB_PATH + f".tmp{tag}"
-    _run([nvcc, ARCH, "-shared", "-o", tmp] + objs, verbose)
-    for o in objs:
-        os.remove(o)
-    os.replace(tmp, LIB_PATH)
+    try:
+        with concurrent.futures.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+            for fut in [ex.submit(_run, j, verbose) for j in jobs]:
+                fut.result()
+        _run([nvcc, ARCH, "-shared", "-o", tmp] + objs, verbose)
+        os.replace(tmp, LIB_PATH)
+    finally:
+        for o in objs + [tmp]:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB_PATH
 
 

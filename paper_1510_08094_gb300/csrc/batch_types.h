@@ -1,6 +1,7 @@
 // Data of a batched plan shared by the host plan code and the persistent kernel.
 #pragma once
 
+#include "dd.cuh"
 #include "fft.cuh"
 
 namespace sp {
@@ -17,9 +18,23 @@ struct BatchClass {
   const int* perm_row;
   const int* perm_col;
   const double* row_scale;
-  const double* fl;                    // [N][Kp] factorised parity tridiagonals
+  const double* fl;                    // [N][Kp] factorised parity tridiagonals (FP64 plans)
   const double* fiu;
   const double* fcu;
+  // FP32 + refinement plans: double-float transform tables, FP32 factors of every
+  // column, FP64 factors of the k = 0 column ([N][2], column 0 used)
+  const cpx<dd>* tw_row_d;
+  const cpx<dd>* tw_col_d;
+  const cpx<dd>* post_row_d;
+  const cpx<dd>* post_col_d;
+  const cpx<dd>* post_col_s_d;
+  const dd* row_scale_d;
+  const float* fl32;                   // [N][Kp]
+  const float* fiu32;
+  const float* fcu32;
+  const double* zl;                    // [N][2]
+  const double* ziu;
+  const double* zcu;
 };
 
 struct BatchProblem {
@@ -36,8 +51,9 @@ struct BatchArgs {
   const double* f;
   double* u;
   cpx<double>* scratch;                // gridDim.x slots
-  long long slot;                      // complex elements per slot
+  long long slot;                      // 16-byte units per slot
   int* counter;                        // zeroed before the launch
+  int sweeps;                          // refinement sweeps (FP32 + refinement plans)
 };
 
 }  // namespace sp

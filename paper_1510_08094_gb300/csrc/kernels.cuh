@@ -821,6 +821,13 @@ __global__ void k_sum2_finish(const cpx<double>* __restrict__ C, int N, int Kp, 
 }
 #endif  // SP_FP64_KERNELS
 
+// exact product of two floats holding integers, as double-float (TwoProduct)
+__device__ __forceinline__ dd dd_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return dd(p, __fmaf_rn(a, b, -p));
+}
+__device__ __forceinline__ cpx<dd> cdd_scale(dd s, cpx<dd> x) { return {dd_mul(s, x.re), dd_mul(s, x.im)}; }
+
 #ifdef SP_REFINE_KERNELS  // defined only in the double-float translation unit
 // ---------------------------------------------------------------------------
 // Iterative refinement of the per-k eliminations (FP32 + refinement form).
@@ -833,13 +840,6 @@ __global__ void k_sum2_finish(const cpx<double>* __restrict__ C, int N, int Kp, 
 // The even chain also sets the row 0 closure X_0 = (X_2 - F_0)/k^2 (k even),
 // X_0 = 0 (k odd).  Column k = 0 is left to the FP64 zonal path.
 // ---------------------------------------------------------------------------
-// exact product of two floats holding integers, as double-float (TwoProduct)
-__device__ __forceinline__ dd dd_prod(float a, float b) {
-  float p = __fmul_rn(a, b);
-  return dd(p, __fmaf_rn(a, b, -p));
-}
-__device__ __forceinline__ cpx<dd> cdd_scale(dd s, cpx<dd> x) { return {dd_mul(s, x.re), dd_mul(s, x.im)}; }
-
 struct RefSlot {
   cpx<dd> f[32];
   cpx<dd> x[32];

@@ -54,6 +54,9 @@ void launch_zonal_scan(bool adj, cudaStream_t st, cpx<double>* Z, const double* 
 // how many CTAs of `threads` fit per SM with `smem` dynamic bytes
 cudaError_t batched_fp64_occupancy(bool big, int threads, size_t smem, int* blocks_per_sm);
 void launch_batched_fp64(bool big, dim3 grid, int threads, size_t smem, cudaStream_t st, const BatchArgs& a);
+// the same for the persistent batched FP32 + refinement solve
+cudaError_t batched_refine_occupancy(bool big, int threads, size_t smem, int* blocks_per_sm);
+void launch_batched_refine(bool big, dim3 grid, int threads, size_t smem, cudaStream_t st, const BatchArgs& a);
 
 // surface integral from the k = 0 coefficient column (one CTA, result to device memory)
 void launch_sum2_finish(cudaStream_t st, const cpx<double>* C, int N, int Kp, double* out);

@@ -28,6 +28,7 @@ namespace {
 
 constexpr int kMaxLen = 12288;             // longest transform (n_theta, n_lambda/2)
 constexpr size_t kSmemBudget = 200 * 1024;  // shared memory per CTA for a transform tile
+constexpr int kBatchThreadsPerCta = 256;     // threads of a persistent batched CTA
 constexpr uint32_t kMagic = 0x53504f31u;    // "SPO1"
 constexpr double kHalfPi = 1.57079632679489661923132169163975144;
 
@@ -356,6 +357,16 @@ void enqueue_refine(sp_plan_t p, const double* in, double* out, void* ws, cudaSt
   m.done();
 }
 
+// the persistent kernel of the plan's arithmetic
+cudaError_t batched_occupancy(const sp_plan_s* p, size_t smem, int* bps) {
+  if (p->precision == SP_FP64) return sp::batched_fp64_occupancy(p->bbig, kBatchThreadsPerCta, smem, bps);
+  return sp::batched_refine_occupancy(p->bbig, kBatchThreadsPerCta, smem, bps);
+}
+void launch_batched_kernel(const sp_plan_s* p, dim3 grid, size_t smem, cudaStream_t st, const sp::BatchArgs& a) {
+  if (p->precision == SP_FP64) sp::launch_batched_fp64(p->bbig, grid, kBatchThreadsPerCta, smem, st, a);
+  else sp::launch_batched_refine(p->bbig, grid, kBatchThreadsPerCta, smem, st, a);
+}
+
 int launch_batched(sp_plan_t p, const double* in, double* out, void* workspace, cudaStream_t st) {
   if (p->count == 0) return SP_OK;
   sp::BatchArgs a = p->bargs;
@@ -367,7 +378,7 @@ int launch_batched(sp_plan_t p, const double* in, double* out, void* workspace, 
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(batch counter)");
   StageMarks m{p, st, !p->prof_events.empty() && p->prof_count < p->prof_max};
   m.mark(0);
-  sp::launch_batched_fp64(p->bbig, dim3(p->bgrid), p->bthreads, p->bsmem, st, a);
+  launch_batched_kernel(p, dim3(p->bgrid), p->bsmem, st, a);
   for (int s = 1; s <= kStages; ++s) m.mark(s);
   m.done();
   e = cudaGetLastError();
@@ -666,7 +677,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
 
 namespace {
 
-constexpr int kBatchThreads = 256;
+constexpr int kBatchThreads = kBatchThreadsPerCta;
 
 // host copy of the per-size tables of a batched plan
 struct HostClass {
@@ -690,9 +701,9 @@ size_t class_smem(const sp::BatchClass& c) {
   return std::max((size_t)c.rows * c.L * cs, (size_t)c.cols * c.N * cs);
 }
 
-std::string tune_key(const char* gpu, int nt, int nl) {
+std::string tune_key(const char* gpu, int nt, int nl, int precision) {
   std::ostringstream o;
-  o << gpu << "|" << nt << "x" << nl << "|fp64";
+  o << gpu << "|" << nt << "x" << nl << (precision == SP_FP64 ? "|fp64" : "|fp32_refine");
   std::string k = o.str();
   for (char& ch : k)
     if (ch == ' ') ch = '_';
@@ -740,7 +751,7 @@ int tune_class(sp_plan_t p, int ci, std::vector<sp::BatchClass>& cls, sp::BatchC
       cudaMemcpy(d_cls + ci, &c, sizeof(sp::BatchClass), cudaMemcpyHostToDevice);
       const size_t smem = class_smem(c);
       int bps = 0;
-      if (sp::batched_fp64_occupancy(p->bbig, kBatchThreads, smem, &bps) != cudaSuccess || bps < 1) continue;
+      if (batched_occupancy(p, smem, &bps) != cudaSuccess || bps < 1) continue;
       sp::BatchArgs a = p->bargs;
       a.problems = d_prob;
       a.order = d_order;
@@ -754,7 +765,7 @@ int tune_class(sp_plan_t p, int ci, std::vector<sp::BatchClass>& cls, sp::BatchC
       for (int rep = 0; rep < 3; ++rep) {
         cudaMemsetAsync(d_counter, 0, sizeof(int), 0);
         cudaEventRecord(e0, 0);
-        sp::launch_batched_fp64(p->bbig, dim3(grid), kBatchThreads, smem, 0, a);
+        launch_batched_kernel(p, dim3(grid), smem, 0, a);
         cudaEventRecord(e1, 0);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -784,8 +795,9 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
   *plan = nullptr;
   if (count < 0) return SP_ERR_BAD_ARG;
   if (count > 0 && (!n_theta || !n_lambda)) return SP_ERR_NULL;
-  if (precision != SP_FP64) return SP_ERR_UNSUPPORTED;
-  if ((flags & ~SP_FLAG_AUTOTUNE) != 0 || refine_sweeps < 0) return SP_ERR_BAD_ARG;
+  if (precision != SP_FP64 && precision != SP_FP32_REFINE) return SP_ERR_UNSUPPORTED;
+  if ((flags & ~SP_FLAG_AUTOTUNE) != 0 || refine_sweeps < 0 || refine_sweeps > 16) return SP_ERR_BAD_ARG;
+  const bool refine = precision == SP_FP32_REFINE;
   // validate sizes and form the size classes
   std::map<std::pair<int, int>, int> cls_of;
   std::vector<HostClass> hcls;
@@ -809,6 +821,7 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
   p->batched = 1;
   p->count = count;
   p->precision = precision;
+  p->sweeps = refine ? refine_sweeps : 0;
   p->nt = p->nl = 0;
   if (cudaGetDevice(&p->device) != cudaSuccess) {
     delete p;
@@ -829,7 +842,10 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
     off = align(off + bytes);
     return o;
   };
-  struct Offs { size_t tw_row, tw_col, post_row, post_col, post_col_s, perm_row, perm_col, scale, fl, fiu, fcu; };
+  struct Offs {
+    size_t tw_row, tw_col, post_row, post_col, post_col_s, perm_row, perm_col, scale, fl, fiu, fcu;
+    size_t d_tw_row, d_tw_col, d_post_row, d_post_col, d_post_col_s, d_scale, l32, iu32, cu32, zl, ziu, zcu;
+  };
   std::vector<Offs> co(nc);
   bool big = false;
   size_t max_slot = 0;
@@ -846,7 +862,10 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
     b.col_fft = h.cd;
     big = big || needs_big(h.rd) || needs_big(h.cd);
     default_tiles(b);
-    max_slot = std::max(max_slot, (size_t)b.N * b.Kp);
+    // scratch slot in 16-byte units: the half spectrum (FP64), or F, X and the
+    // FP32 correction (FP32 + refinement: 16 + 16 + 8 bytes per element)
+    const size_t nkp = (size_t)b.N * b.Kp;
+    max_slot = std::max(max_slot, refine ? (5 * nkp + 1) / 2 : nkp);
     h.tw_row.resize(b.L);
     h.tw_col.resize(b.N);
     h.post_row.resize(b.L + 1);
@@ -865,10 +884,33 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
       unit_root(2 * i + 1, 4L * b.N, &re, &im);
       h.row_scale[i] = (im * im) / (double)b.nl;
     }
-    const size_t csz = sizeof(cpx<double>), fac = (size_t)b.N * b.Kp * sizeof(double);
-    co[c] = {take(b.L * csz), take(b.N * csz), take((b.L + 1) * csz), take((b.N + 1) * csz),
-             take((b.N + 1) * csz), take(b.L * sizeof(int)), take(b.N * sizeof(int)), take(b.nt * sizeof(double)),
-             take(fac), take(fac), take(fac)};
+    const size_t csz = sizeof(cpx<double>), fac = refine ? 0 : (size_t)b.N * b.Kp * sizeof(double);
+    const size_t dsz = refine ? sizeof(cpx<sp::dd>) : 0, f32 = refine ? (size_t)b.N * b.Kp * sizeof(float) : 0;
+    const size_t fz = refine ? (size_t)b.N * 2 * sizeof(double) : 0;
+    Offs& o = co[c];
+    o.tw_row = take(b.L * csz);
+    o.tw_col = take(b.N * csz);
+    o.post_row = take((b.L + 1) * csz);
+    o.post_col = take((b.N + 1) * csz);
+    o.post_col_s = take((b.N + 1) * csz);
+    o.perm_row = take(b.L * sizeof(int));
+    o.perm_col = take(b.N * sizeof(int));
+    o.scale = take(b.nt * sizeof(double));
+    o.fl = take(fac);
+    o.fiu = take(fac);
+    o.fcu = take(fac);
+    o.d_tw_row = take(b.L * dsz);
+    o.d_tw_col = take(b.N * dsz);
+    o.d_post_row = take((b.L + 1) * dsz);
+    o.d_post_col = take((b.N + 1) * dsz);
+    o.d_post_col_s = take((b.N + 1) * dsz);
+    o.d_scale = take(refine ? b.nt * sizeof(sp::dd) : 0);
+    o.l32 = take(f32);
+    o.iu32 = take(f32);
+    o.cu32 = take(f32);
+    o.zl = take(fz);
+    o.ziu = take(fz);
+    o.zcu = take(fz);
   }
   const size_t o_cls = take(nc * sizeof(sp::BatchClass) + 1);
   const size_t o_prob = take(count * sizeof(sp::BatchProblem) + 1);
@@ -912,12 +954,57 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
     step(cudaMemcpy((void*)b.perm_row, h.perm_row.data(), b.L * sizeof(int), cudaMemcpyHostToDevice), "copy");
     step(cudaMemcpy((void*)b.perm_col, h.perm_col.data(), b.N * sizeof(int), cudaMemcpyHostToDevice), "copy");
     step(cudaMemcpy((void*)b.row_scale, h.row_scale.data(), b.nt * sizeof(double), cudaMemcpyHostToDevice), "copy");
-    const size_t fac = (size_t)b.N * b.Kp * sizeof(double);
-    step(cudaMemset((void*)b.fl, 0, (size_t)((const char*)b.fcu - (const char*)b.fl) + fac), "clear factors");
+    const int threads = 128, blocks = (2 * b.K + threads - 1) / threads;
+    if (!refine) {
+      const size_t fac = (size_t)b.N * b.Kp * sizeof(double);
+      for (const double* t : {b.fl, b.fiu, b.fcu}) step(cudaMemset((void*)t, 0, fac), "clear factors");
+      if (rc == SP_OK) {
+        sp::launch_factor<double>(sp::Launch{dim3(blocks), threads, 0, 0}, (double*)b.fl, (double*)b.fiu,
+                                  (double*)b.fcu, b.N, b.K, b.Kp);
+        step(cudaGetLastError(), "k_factor launch");
+      }
+      b.tw_row_d = b.tw_col_d = b.post_row_d = b.post_col_d = b.post_col_s_d = nullptr;
+      b.row_scale_d = nullptr;
+      b.fl32 = b.fiu32 = b.fcu32 = nullptr;
+      b.zl = b.ziu = b.zcu = nullptr;
+      continue;
+    }
+    b.fl = b.fiu = b.fcu = nullptr;
+    b.tw_row_d = reinterpret_cast<cpx<sp::dd>*>(base + co[c].d_tw_row);
+    b.tw_col_d = reinterpret_cast<cpx<sp::dd>*>(base + co[c].d_tw_col);
+    b.post_row_d = reinterpret_cast<cpx<sp::dd>*>(base + co[c].d_post_row);
+    b.post_col_d = reinterpret_cast<cpx<sp::dd>*>(base + co[c].d_post_col);
+    b.post_col_s_d = reinterpret_cast<cpx<sp::dd>*>(base + co[c].d_post_col_s);
+    b.row_scale_d = reinterpret_cast<sp::dd*>(base + co[c].d_scale);
+    b.fl32 = reinterpret_cast<float*>(base + co[c].l32);
+    b.fiu32 = reinterpret_cast<float*>(base + co[c].iu32);
+    b.fcu32 = reinterpret_cast<float*>(base + co[c].cu32);
+    b.zl = reinterpret_cast<double*>(base + co[c].zl);
+    b.ziu = reinterpret_cast<double*>(base + co[c].ziu);
+    b.zcu = reinterpret_cast<double*>(base + co[c].zcu);
+    {
+      std::vector<char> t;
+      auto put = [&](const void* dst, const std::vector<cpx<double>>& src) {
+        upload_table<sp::dd>(src, t);
+        step(cudaMemcpy((void*)dst, t.data(), t.size(), cudaMemcpyHostToDevice), "copy");
+      };
+      put(b.tw_row_d, h.tw_row);
+      put(b.tw_col_d, h.tw_col);
+      put(b.post_row_d, h.post_row);
+      put(b.post_col_d, h.post_col);
+      put(b.post_col_s_d, h.post_col_s);
+      std::vector<sp::dd> sd(b.nt);
+      for (int i = 0; i < b.nt; ++i) sd[i] = sp::dd(h.row_scale[i]);
+      step(cudaMemcpy((void*)b.row_scale_d, sd.data(), b.nt * sizeof(sp::dd), cudaMemcpyHostToDevice), "copy");
+    }
+    const size_t f32 = (size_t)b.N * b.Kp * sizeof(float), fz = (size_t)b.N * 2 * sizeof(double);
+    for (const float* t : {b.fl32, b.fiu32, b.fcu32}) step(cudaMemset((void*)t, 0, f32), "clear factors");
+    for (const double* t : {b.zl, b.ziu, b.zcu}) step(cudaMemset((void*)t, 0, fz), "clear factors");
     if (rc == SP_OK) {
-      int threads = 128, blocks = (2 * b.K + threads - 1) / threads;
-      sp::launch_factor<double>(sp::Launch{dim3(blocks), threads, 0, 0}, (double*)b.fl, (double*)b.fiu,
-                                (double*)b.fcu, b.N, b.K, b.Kp);
+      sp::launch_factor<float>(sp::Launch{dim3(blocks), threads, 0, 0}, (float*)b.fl32, (float*)b.fiu32,
+                               (float*)b.fcu32, b.N, b.K, b.Kp);
+      sp::launch_factor<double>(sp::Launch{dim3(1), threads, 0, 0}, (double*)b.zl, (double*)b.ziu,
+                                (double*)b.zcu, b.N, 1, 2);
       step(cudaGetLastError(), "k_factor launch");
     }
   }
@@ -940,13 +1027,14 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
   p->bargs.order = d_order;
   p->bargs.count = count;
   p->bargs.slot = (long long)max_slot;
+  p->bargs.sweeps = p->sweeps;
   // persistent grid: every SM filled to the kernel's occupancy
   int sms = 1;
   step(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device), "SM count");
   size_t smem = 0;
   for (auto& b : cls) smem = std::max(smem, class_smem(b));
   int bps = 0;
-  step(sp::batched_fp64_occupancy(big, kBatchThreads, std::max(smem, (size_t)200 * 1024), &bps), "occupancy");
+  step(batched_occupancy(p, std::max(smem, (size_t)200 * 1024), &bps), "occupancy");
   p->bgrid = std::max(1, std::min(count, sms * std::max(bps, 1)));
 
   // autotuning of the transform tiles per size class
@@ -975,7 +1063,7 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
       step(cudaMemcpy(d_cls, cls.data(), nc * sizeof(sp::BatchClass), cudaMemcpyHostToDevice), "copy classes");
     }
     for (int c = 0; c < nc && rc == SP_OK; ++c) {
-      const std::string key = tune_key(prop.name, cls[c].nt, cls[c].nl);
+      const std::string key = tune_key(prop.name, cls[c].nt, cls[c].nl, p->precision);
       auto it = cache.find(key);
       if (it != cache.end()) {
         cls[c].rows = it->second.first;
@@ -1010,7 +1098,7 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
   if (count > 0) {
     step(cudaMemcpy(d_prob, prob.data(), count * sizeof(sp::BatchProblem), cudaMemcpyHostToDevice), "copy problems");
     step(cudaMemcpy(d_order, order.data(), count * sizeof(int), cudaMemcpyHostToDevice), "copy order");
-    step(sp::batched_fp64_occupancy(big, kBatchThreads, smem, &bps), "occupancy");
+    step(batched_occupancy(p, smem, &bps), "occupancy");
     p->bgrid = std::max(1, std::min(count, sms * std::max(bps, 1)));
   }
   p->off_counter = align((size_t)p->bgrid * max_slot * sizeof(cpx<double>));

@@ -81,3 +81,23 @@ def test_calls_reject_null_plan(lib):
     n = ctypes.c_size_t()
     assert lib.sphere_poisson_workspace_size(None, ctypes.byref(n)) == _lib.SP_ERR_BAD_PLAN
     assert lib.sphere_poisson_destroy(None) == _lib.SP_OK
+
+
+def test_batched_plan_argument_checks(lib):
+    from paper_1510_08094_gb300 import _lib
+
+    h = ctypes.c_void_p()
+    nts = (ctypes.c_int * 2)(8, 16)
+    nls = (ctypes.c_int * 2)(16, 32)
+    bad = (ctypes.c_int * 2)(16, 31)
+    plan = lib.sphere_poisson_plan_batched
+    assert plan(None, 2, nts, nls, _lib.SP_FP64, 0, 0, None) == _lib.SP_ERR_NULL
+    assert plan(ctypes.byref(h), -1, nts, nls, _lib.SP_FP64, 0, 0, None) == _lib.SP_ERR_BAD_ARG
+    assert plan(ctypes.byref(h), 2, None, nls, _lib.SP_FP64, 0, 0, None) == _lib.SP_ERR_NULL
+    # the batched form exists in FP64 and FP32 + refinement, not in plain FP32
+    assert plan(ctypes.byref(h), 2, nts, nls, _lib.SP_FP32, 0, 0, None) == _lib.SP_ERR_UNSUPPORTED
+    assert plan(ctypes.byref(h), 2, nts, nls, _lib.SP_FP32_REFINE, 17, 0, None) == _lib.SP_ERR_BAD_ARG
+    assert plan(ctypes.byref(h), 2, nts, nls, _lib.SP_FP32_REFINE, -1, 0, None) == _lib.SP_ERR_BAD_ARG
+    assert plan(ctypes.byref(h), 2, nts, nls, _lib.SP_FP64, 0, 4, None) == _lib.SP_ERR_BAD_ARG
+    assert plan(ctypes.byref(h), 2, nts, bad, _lib.SP_FP32_REFINE, 1, 0, None) == _lib.SP_ERR_BAD_SIZE
+    assert h.value is None
