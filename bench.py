@@ -179,14 +179,19 @@ def run_ours(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import tempfile
+
     import paper_1510_08094_gb300 as sp
     from synth import sh
 
+    if "SPHERE_POISSON_TUNE_CACHE" not in os.environ:
+        os.environ["SPHERE_POISSON_TUNE_CACHE"] = os.path.join(tempfile.gettempdir(), "sphere_poisson_tune.txt")
     w = sh.workload(args.workload)
     N, n = w.n_theta, w.n_lambda
     dev = torch.device("cuda", local)
     f, u_exact = w.make(device=dev)
-    plan = sp.Plan(N, n, args.precision, args.sweeps, device=dev)
+    tune = not args.no_autotune
+    plan = sp.Plan(N, n, args.precision, args.sweeps, device=dev, autotune=tune)
     ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=dev)
     u = torch.empty_like(f)
     stream = torch.cuda.current_stream()
@@ -308,6 +313,7 @@ def run_ours(args):
             "dof_per_solve": dof,
             "dof_convention": "n_theta*n_lambda (= mn/2, the paper's); mn convention = 2x",
             "l2": "inputs (400 MB) larger than L2 (129 MB); no flush",
+            "tiles": "autotuned at plan time" if tune else "default",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
             "max_rel_err_vs_closed_form": err,
         },
@@ -341,7 +347,7 @@ def measure_forms(sp, f, u_exact, u64, N, n, dev, ms_fp64, args):
     res = {}
     steps = max(5, min(args.steps, 50))
     for prec, sweeps in [("fp32", 0), ("fp32_refine", 0), ("fp32_refine", 1), ("fp32_refine", 2)]:
-        plan = sp.Plan(N, n, prec, sweeps, device=dev)
+        plan = sp.Plan(N, n, prec, sweeps, device=dev, autotune=not args.no_autotune)
         ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=dev)
         u = torch.empty_like(f)
         for _ in range(3):
@@ -362,11 +368,11 @@ def measure_forms(sp, f, u_exact, u64, N, n, dev, ms_fp64, args):
                     "gpu_launches_per_step": plan.launches()}
         del plan, ws
     if not args.no_paper_scale:
-        res["paper_scale"] = measure_paper_scale(sp, dev)
+        res["paper_scale"] = measure_paper_scale(sp, dev, args)
     return res
 
 
-def measure_paper_scale(sp, dev):
+def measure_paper_scale(sp, dev, args):
     """The paper's headline size: m = n with mn/2 = 1.03e8 unknowns (7168 x 14336),
     FP64 and FP32+refinement (1 sweep), against the paper's ~1 minute on a laptop."""
     import torch
@@ -378,7 +384,7 @@ def measure_paper_scale(sp, dev):
     out = {"workload": f"{w.name}: n_theta={w.n_theta} x n_lambda={w.n_lambda}, DOF (mn/2) = "
                        f"{w.n_theta * w.n_lambda}", "paper_seconds_context": 60.0}
     for prec, sweeps in [("fp64", 0), ("fp32_refine", 1)]:
-        plan = sp.Plan(w.n_theta, w.n_lambda, prec, sweeps, device=dev)
+        plan = sp.Plan(w.n_theta, w.n_lambda, prec, sweeps, device=dev, autotune=not args.no_autotune)
         ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=dev)
         u = torch.empty_like(f)
         for _ in range(2):
@@ -437,7 +443,7 @@ def measure_batched(sp, dev, args):
         a, c = plan.offsets[b], plan.offsets[b + 1]
         worst = max(worst, float((u[a:c] - ue[a:c]).abs().max() / ue[a:c].abs().max()))
     # plain FP64: one single-problem plan per size, problems solved one by one
-    singles = {sz: sp.Plan(sz[0], sz[1], device=dev) for sz in set(sizes)}
+    singles = {sz: sp.Plan(sz[0], sz[1], device=dev, autotune=not args.no_autotune) for sz in set(sizes)}
     outs = [torch.empty(sz, dtype=torch.float64, device=dev) for sz in sizes]
     views = plan.unpack(f)
     for b, sz in enumerate(sizes[:64]):
@@ -590,6 +596,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp32_refine"])
     ap.add_argument("--sweeps", type=int, default=1)
+    ap.add_argument("--no-autotune", action="store_true", help="plan-time tile tuning off (default tiles)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

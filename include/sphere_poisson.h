@@ -60,6 +60,9 @@ extern "C" {
 
 typedef struct sp_plan_s* sp_plan_t;
 
+/* plan flag: tune the transform tiles at plan time (see the plan calls) */
+#define SP_FLAG_AUTOTUNE 1u
+
 /*
  * Create a plan for grids of n_theta colatitudes x n_lambda longitudes.
  *   n_theta >= 1, n_lambda >= 2 and even (the glide reflection lambda -> lambda+pi
@@ -72,7 +75,12 @@ typedef struct sp_plan_s* sp_plan_t;
  *                 values return SP_ERR_UNSUPPORTED.
  *   refine_sweeps 0..16 residual sweeps for SP_FP32_REFINE (ignored otherwise;
  *                 outside 0..16 SP_ERR_BAD_ARG).
- *   flags         reserved, pass 0.
+ *   flags         0, or SP_FLAG_AUTOTUNE (below): time the transform tiles
+ *                 (rows / columns per CTA and threads per CTA of the longitude
+ *                 and colatitude kernels) as whole solves on zero input at plan
+ *                 time and keep the fastest; cached like the batched tuner's.
+ *                 Tuning allocates an input, an output and a workspace for the
+ *                 duration of the call.
  *   workspace_bytes (out, optional) device workspace the solve calls need.
  * Synchronous: allocates the plan's device tables and fills them on the
  * current device; the plan may only be used with that device.
@@ -100,7 +108,6 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
  * sphere_poisson_solve (and _solve_host); the adjoint returns SP_ERR_UNSUPPORTED.
  * The solve issues one cudaMemsetAsync (the work counter) and one kernel.
  */
-#define SP_FLAG_AUTOTUNE 1u
 int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, const int* n_lambda,
                                 int precision, int refine_sweeps, unsigned flags, size_t* workspace_bytes);
 

@@ -51,10 +51,13 @@ def _check_grid(t: torch.Tensor, shape, name: str):
 
 
 class Plan:
-    """A solver plan for one grid size (n_theta colatitudes x n_lambda longitudes)."""
+    """A solver plan for one grid size (n_theta colatitudes x n_lambda longitudes).
+
+    autotune=True times the transform tiles at plan time and keeps the fastest
+    (cached in $SPHERE_POISSON_TUNE_CACHE if set)."""
 
     def __init__(self, n_theta: int, n_lambda: int, precision: str = "fp64", refine_sweeps: int = 0,
-                 device=None):
+                 device=None, autotune: bool = False):
         lib = _lib.load()
         if precision not in _PRECISIONS:
             raise ValueError(f"precision must be one of {sorted(_PRECISIONS)}")
@@ -65,8 +68,9 @@ class Plan:
         h = ctypes.c_void_p()
         ws = ctypes.c_size_t()
         with torch.cuda.device(self.device):
+            flags = _lib.SP_FLAG_AUTOTUNE if autotune else 0
             _lib.check(lib.sphere_poisson_plan(ctypes.byref(h), self.n_theta, self.n_lambda,
-                                               _PRECISIONS[precision], int(refine_sweeps), 0,
+                                               _PRECISIONS[precision], int(refine_sweeps), flags,
                                                ctypes.byref(ws)), "sphere_poisson_plan")
         self._h = h
         self.workspace_bytes = int(ws.value)

@@ -455,6 +455,10 @@ void destroy_plan(sp_plan_s* p) {
 
 }  // namespace
 
+namespace {
+int tune_single(sp_plan_t p);  // defined with the batched tuner
+}  // namespace
+
 extern "C" {
 
 int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precision,
@@ -464,7 +468,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   if (n_theta < 1 || n_lambda < 2 || (n_lambda & 1)) return SP_ERR_BAD_SIZE;
   if (n_theta > kMaxLen || n_lambda / 2 > kMaxLen) return SP_ERR_BAD_SIZE;
   if (precision != SP_FP64 && precision != SP_FP32 && precision != SP_FP32_REFINE) return SP_ERR_UNSUPPORTED;
-  if (flags != 0 || refine_sweeps < 0 || refine_sweeps > 16) return SP_ERR_BAD_ARG;
+  if ((flags & ~SP_FLAG_AUTOTUNE) != 0 || refine_sweeps < 0 || refine_sweeps > 16) return SP_ERR_BAD_ARG;
 
   FftDesc rd, cd;
   if (!make_fft_desc(n_lambda / 2, &rd) || !make_fft_desc(n_theta, &cd)) return SP_ERR_BAD_SIZE;
@@ -664,6 +668,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
     step(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming), "cudaEventCreate");
   }
   step(allow_all_smem(p->device), "shared memory attribute");
+  if (rc == SP_OK && (flags & SP_FLAG_AUTOTUNE)) rc = tune_single(p);
   if (rc != SP_OK) {
     destroy_plan(p);
     return rc;
@@ -710,15 +715,152 @@ std::string tune_key(const char* gpu, int nt, int nl, int precision) {
   return k;
 }
 
-std::map<std::string, std::pair<int, int>> read_tune_cache(const char* path) {
-  std::map<std::string, std::pair<int, int>> m;
+// tune cache: one entry per line, a key without spaces followed by numbers
+std::map<std::string, std::vector<double>> read_tune_lines(const char* path) {
+  std::map<std::string, std::vector<double>> m;
   if (!path) return m;
   std::ifstream in(path);
-  std::string key;
-  int r, c;
-  double t;
-  while (in >> key >> r >> c >> t) m[key] = {r, c};
+  std::string line;
+  while (std::getline(in, line)) {
+    std::istringstream ls(line);
+    std::string key;
+    if (!(ls >> key)) continue;
+    std::vector<double> v;
+    double x;
+    while (ls >> x) v.push_back(x);
+    m[key] = v;
+  }
   return m;
+}
+
+std::map<std::string, std::pair<int, int>> read_tune_cache(const char* path) {
+  std::map<std::string, std::pair<int, int>> m;
+  for (auto& kv : read_tune_lines(path))
+    if (kv.second.size() >= 2) m[kv.first] = {(int)kv.second[0], (int)kv.second[1]};
+  return m;
+}
+
+std::string spaceless(std::string k) {
+  for (char& ch : k)
+    if (ch == ' ') ch = '_';
+  return k;
+}
+
+const char* precision_tag(int precision) {
+  return precision == SP_FP64 ? "fp64" : precision == SP_FP32 ? "fp32" : "fp32_refine";
+}
+
+// Plan-time tile tuning of a single plan: the candidate (rows per CTA, threads)
+// of the longitude kernels, then (columns per CTA, threads) of the colatitude
+// kernels, each timed as whole solves on zero input (fastest of three after a
+// warm-up); the fastest is kept and cached per GPU, grid and arithmetic in the
+// file named by SPHERE_POISSON_TUNE_CACHE.
+int tune_single(sp_plan_t p) {
+  cudaDeviceProp prop;
+  cudaError_t e = cudaGetDeviceProperties(&prop, p->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  std::ostringstream ko;
+  ko << prop.name << "|" << p->nt << "x" << p->nl << "|single|" << precision_tag(p->precision) << "|"
+     << p->sweeps;
+  const std::string key = spaceless(ko.str());
+  const char* cache_path = std::getenv("SPHERE_POISSON_TUNE_CACHE");
+  const size_t csz = esize(p->precision);
+  auto set_rows = [&](int r, int t) {
+    p->rows_per_cta = r;
+    p->row_threads = t;
+    p->row_smem = (size_t)r * p->L * csz;
+  };
+  auto set_cols = [&](int q, int t) {
+    p->cols_per_cta = q;
+    p->col_threads = t;
+    p->col_smem = (size_t)q * p->N * csz;
+  };
+  {
+    auto cache = read_tune_lines(cache_path);
+    auto it = cache.find(key);
+    if (it != cache.end() && it->second.size() >= 4) {
+      set_rows((int)it->second[0], (int)it->second[1]);
+      set_cols((int)it->second[2], (int)it->second[3]);
+      return SP_OK;
+    }
+  }
+  const size_t grid_vals = (size_t)p->nt * p->nl;
+  double* f = nullptr;
+  double* u = nullptr;
+  void* ws = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = SP_OK;
+  auto step = [&](cudaError_t err, const char* what) {
+    if (rc == SP_OK && err != cudaSuccess) rc = cuda_fail(err, what);
+  };
+  step(cudaMalloc(&f, grid_vals * sizeof(double)), "tune buffers");
+  step(cudaMalloc(&u, grid_vals * sizeof(double)), "tune buffers");
+  step(cudaMalloc(&ws, p->ws_bytes), "tune buffers");
+  step(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "tune stream");
+  step(cudaEventCreate(&e0), "tune events");
+  step(cudaEventCreate(&e1), "tune events");
+  if (rc == SP_OK) step(cudaMemset(f, 0, grid_vals * sizeof(double)), "tune buffers");
+  auto time_solve = [&]() -> double {
+    double best = 1e30;
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(e0, st);
+      int r = launch_solve<false>(p, f, u, ws, st);
+      cudaEventRecord(e1, st);
+      if (r != SP_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+        cudaGetLastError();
+        return 1e30;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) best = std::min(best, (double)ms);
+    }
+    return best;
+  };
+  const int cap_r = p->big_row ? 256 : 512, cap_c = p->big_col ? 256 : 512;
+  double best_ms = 1e30;
+  if (rc == SP_OK) {
+    int br = p->rows_per_cta, bt = p->row_threads;
+    best_ms = time_solve();
+    for (int r = 1; r <= 8 && r <= p->nt; r *= 2)
+      for (int t = 64; t <= cap_r; t *= 2) {
+        if ((size_t)r * p->L * csz > 220 * 1024) continue;
+        set_rows(r, t);
+        const double ms = time_solve();
+        if (ms < best_ms) {
+          best_ms = ms;
+          br = r;
+          bt = t;
+        }
+      }
+    set_rows(br, bt);
+    int bq = p->cols_per_cta, bct = p->col_threads;
+    for (int q = 1; q <= 8 && q <= p->Kp; q *= 2)
+      for (int t = 64; t <= cap_c; t *= 2) {
+        if ((size_t)q * p->N * csz > 220 * 1024) continue;
+        set_cols(q, t);
+        const double ms = time_solve();
+        if (ms < best_ms) {
+          best_ms = ms;
+          bq = q;
+          bct = t;
+        }
+      }
+    set_cols(bq, bct);
+  }
+  if (st) cudaStreamSynchronize(st);
+  cudaFree(f);
+  cudaFree(u);
+  cudaFree(ws);
+  if (st) cudaStreamDestroy(st);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rc == SP_OK && cache_path && best_ms < 1e29) {
+    std::ofstream out(cache_path, std::ios::app);
+    out << key << " " << p->rows_per_cta << " " << p->row_threads << " " << p->cols_per_cta << " "
+        << p->col_threads << " " << best_ms << "\n";
+  }
+  return rc;
 }
 
 // Time candidate tiles of one size class on a batch of `reps_problems` copies
