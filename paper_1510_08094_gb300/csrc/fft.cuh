@@ -4,7 +4,9 @@
 // back to back in shared memory, in place, by decimation in time: the input is
 // loaded in mixed-radix digit-reversed order, pass t combines R_t sub-DFTs of
 // length Ns = R_1 ... R_{t-1}, and the output comes out in natural order.
-// Twiddles come from a table tw[t] = exp(-2 pi i t / L).
+// Twiddles come from a per-pass table laid out so that one butterfly's R
+// twiddles are adjacent (one or a few vector loads, coalesced across the
+// threads of a pass); the odd-prime DFT constants follow the pass tables.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -96,7 +98,33 @@ struct FftDesc {
   FastDiv div_L;               // n / L
   FastDiv div_nb[kMaxStages];  // n / (L / R_s)
   FastDiv div_ns[kMaxStages];  // n / (R_1 ... R_{s-1})
+  // twiddle table: pass s (sub-DFT length Ns = R_1 ... R_{s-1}) holds at
+  // tw_off[s] + k RP + r the value exp(-2 pi i r k / (Ns R_s)), r < R_s, k < Ns,
+  // RP = R_s rounded up to even; for odd R_s >= 7, dft_off[s] + a holds
+  // exp(-2 pi i a / R_s), a < R_s.  tw_len entries in all.
+  int tw_off[kMaxStages];
+  int dft_off[kMaxStages];
+  int tw_len;
 };
+
+// the twiddles w[r], 0 < r < R, of one butterfly from its R-entry slot p
+template <int R, typename T>
+__device__ __forceinline__ void load_stage_tw(const cpx<T>* __restrict__ p, cpx<T>* w) {
+#pragma unroll
+  for (int r = 1; r < R; ++r) w[r] = ldg_c(p + r);
+}
+// FP32: the slot is RP = even entries of 8 bytes starting on a 16-byte boundary,
+// read as RP/2 16-byte loads
+template <int R>
+__device__ __forceinline__ void load_stage_tw(const cpx<float>* __restrict__ p, cpx<float>* w) {
+  constexpr int RP = (R + 1) & ~1;
+#pragma unroll
+  for (int i = 0; i < RP / 2; ++i) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p) + i);
+    if (2 * i < R) w[2 * i] = {q.x, q.y};
+    if (2 * i + 1 < R) w[2 * i + 1] = {q.z, q.w};
+  }
+}
 
 // ---------------------------------------------------------------------------
 // R-point DFTs on registers: y_a = sum_b x_b exp(DIR 2 pi i a b / R)
@@ -187,9 +215,9 @@ __device__ __forceinline__ void dft5(cpx<T>* v) {
 }
 
 // Generic odd R: pair outputs a and R-a, using p_b = x_b + x_{R-b}, q_b = x_b - x_{R-b}.
-// Cos/sin of 2 pi a b / R are read from the length-L table at (a b mod R) L/R.
+// Cos/sin of 2 pi a b / R are read from the R-entry constant table dtw at a b mod R.
 template <int R, int DIR, typename T>
-__device__ __forceinline__ void dft_odd(cpx<T>* v, const cpx<T>* __restrict__ tw, int tstride) {
+__device__ __forceinline__ void dft_odd(cpx<T>* v, const cpx<T>* __restrict__ dtw) {
   constexpr int H = (R - 1) / 2;
   cpx<T> p[H], q[H];
 #pragma unroll
@@ -206,7 +234,7 @@ __device__ __forceinline__ void dft_odd(cpx<T>* v, const cpx<T>* __restrict__ tw
     cpx<T> A = x0, B = {(T)0, (T)0};
 #pragma unroll
     for (int b = 1; b <= H; ++b) {
-      cpx<T> w = ldg_c(tw + ((a * b) % R) * tstride);
+      cpx<T> w = ldg_c(dtw + (a * b) % R);
       T c = w.re, s = -w.im;  // w = exp(-2 pi i ab/R) = c - i s
       A.re = fma(c, p[b - 1].re, A.re);
       A.im = fma(c, p[b - 1].im, A.im);
@@ -222,13 +250,13 @@ __device__ __forceinline__ void dft_odd(cpx<T>* v, const cpx<T>* __restrict__ tw
 }
 
 template <int R, int DIR, typename T>
-__device__ __forceinline__ void dft_any(cpx<T>* v, const cpx<T>* __restrict__ tw, int tstride) {
+__device__ __forceinline__ void dft_any(cpx<T>* v, const cpx<T>* __restrict__ dtw) {
   if constexpr (R == 2) dft2<DIR>(v);
   else if constexpr (R == 3) dft3<DIR>(v);
   else if constexpr (R == 4) dft4<DIR>(v);
   else if constexpr (R == 5) dft5<DIR>(v);
   else if constexpr (R == 8) dft8<DIR>(v);
-  else dft_odd<R, DIR>(v, tw, tstride);  // 7
+  else dft_odd<R, DIR>(v, dtw);  // 7
 }
 
 // ---------------------------------------------------------------------------
@@ -240,12 +268,11 @@ __device__ __forceinline__ void dft_any(cpx<T>* v, const cpx<T>* __restrict__ tw
 // ---------------------------------------------------------------------------
 template <int R, int DIR, typename T>
 __device__ __forceinline__ void fft_pass(cpx<T>* buf, int L, int nbatch, int Ns,
-                                         const cpx<T>* __restrict__ tw, const FastDiv& dnb,
-                                         const FastDiv& dns) {
+                                         const cpx<T>* __restrict__ stw, const cpx<T>* __restrict__ dtw,
+                                         const FastDiv& dnb, const FastDiv& dns) {
+  constexpr int RP = (R + 1) & ~1;
   const int nb = L / R;
   const int total = nb * nbatch;
-  const int tstride_stage = L / (Ns * R);  // table step for w = exp(-2 pi i/(Ns R))
-  const int tstride_R = L / R;
   for (int b = threadIdx.x; b < total; b += blockDim.x) {
     const int batch = (int)fdiv((unsigned)b, dnb);
     const int j = b - batch * nb;
@@ -256,11 +283,19 @@ __device__ __forceinline__ void fft_pass(cpx<T>* buf, int L, int nbatch, int Ns,
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = base[r * Ns];
     if (Ns > 1) {
+      const cpx<T>* tk = stw + k * RP;
+      if constexpr (R <= 8) {
+        cpx<T> w[R];
+        load_stage_tw<R>(tk, w);
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = twmul<DIR>(v[r], ldg_c(tw + r * k * tstride_stage));
+        for (int r = 1; r < R; ++r) v[r] = twmul<DIR>(v[r], w[r]);
+      } else {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = twmul<DIR>(v[r], ldg_c(tk + r));
+      }
     }
     if constexpr (R <= 8) {
-      dft_any<R, DIR>(v, tw, tstride_R);
+      dft_any<R, DIR>(v, dtw);
 #pragma unroll
       for (int r = 0; r < R; ++r) base[r * Ns] = v[r];
     } else {
@@ -288,7 +323,7 @@ __device__ __forceinline__ void fft_pass(cpx<T>* buf, int L, int nbatch, int Ns,
         for (int bb = 1; bb <= H; ++bb) {
           ab += a;
           if (ab >= R) ab -= R;                  // ab = a * bb mod R
-          cpx<T> w = ldg_c(tw + ab * tstride_R);
+          cpx<T> w = ldg_c(dtw + ab);
           T c = w.re, sn = -w.im;                // w = exp(-2 pi i ab/R) = c - i sn
           A.re = fma(c, v[bb].re, A.re);
           A.im = fma(c, v[bb].im, A.im);
@@ -316,24 +351,26 @@ __device__ __forceinline__ void fft_run(cpx<T>* buf, int nbatch, const FftDesc& 
   int Ns = 1;
   for (int s = 0; s < d.nstages; ++s) {
     const int R = d.radix[s];
+    const cpx<T>* stw = tw + d.tw_off[s];
+    const cpx<T>* dtw = tw + d.dft_off[s];
     switch (R) {
-      case 2: fft_pass<2, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
-      case 3: fft_pass<3, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
-      case 4: fft_pass<4, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
-      case 5: fft_pass<5, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
-      case 7: fft_pass<7, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
-      case 8: fft_pass<8, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
+      case 2: fft_pass<2, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 3: fft_pass<3, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 4: fft_pass<4, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 5: fft_pass<5, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 7: fft_pass<7, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 8: fft_pass<8, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
       default: break;
     }
     if constexpr (BIG) {
       switch (R) {
-      case 11: fft_pass<11, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
-      case 13: fft_pass<13, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
-      case 17: fft_pass<17, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
-      case 19: fft_pass<19, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
-      case 23: fft_pass<23, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
-      case 29: fft_pass<29, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
-      case 31: fft_pass<31, DIR>(buf, d.L, nbatch, Ns, tw, d.div_nb[s], d.div_ns[s]); break;
+      case 11: fft_pass<11, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 13: fft_pass<13, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 17: fft_pass<17, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 19: fft_pass<19, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 23: fft_pass<23, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 29: fft_pass<29, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 31: fft_pass<31, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
       default: break;  // the host never builds other radices
       }
     }

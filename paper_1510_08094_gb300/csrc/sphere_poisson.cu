@@ -66,12 +66,22 @@ bool make_fft_desc(int L, FftDesc* d) {
     while (rest % p == 0) if (!push(p)) return false;
   d->nstages = s;
   d->div_L = sp::make_fastdiv((unsigned)L);
-  int ns = 1;
+  int ns = 1, off = 0;
   for (int t = 0; t < s; ++t) {
     d->div_nb[t] = sp::make_fastdiv((unsigned)(L / d->radix[t]));
     d->div_ns[t] = sp::make_fastdiv((unsigned)ns);
+    d->tw_off[t] = off;
+    off += ns * ((d->radix[t] + 1) & ~1);
     ns *= d->radix[t];
   }
+  for (int t = 0; t < s; ++t) {
+    const int R = d->radix[t];
+    if (R >= 7 && (R & 1)) {
+      d->dft_off[t] = off;
+      off += (R + 1) & ~1;
+    }
+  }
+  d->tw_len = off;
   return rest == 1;
 }
 
@@ -128,6 +138,24 @@ void unit_root(long t, long M, double* re, double* im) {
   *im = -sr;
 }
 
+// the twiddle table of an FFT descriptor (layout in FftDesc)
+std::vector<cpx<double>> stage_twiddles(const FftDesc& d) {
+  std::vector<cpx<double>> tab(d.tw_len, cpx<double>{1.0, 0.0});
+  int ns = 1;
+  for (int s = 0; s < d.nstages; ++s) {
+    const int R = d.radix[s], RP = (R + 1) & ~1;
+    for (int k = 0; k < ns; ++k)
+      for (int r = 0; r < R; ++r) {
+        cpx<double>& w = tab[d.tw_off[s] + k * RP + r];
+        unit_root((long)r * k, (long)ns * R, &w.re, &w.im);
+      }
+    if (R >= 7 && (R & 1))
+      for (int a = 0; a < R; ++a) unit_root(a, R, &tab[d.dft_off[s] + a].re, &tab[d.dft_off[s] + a].im);
+    ns *= R;
+  }
+  return tab;
+}
+
 }  // namespace
 
 struct sp_plan_s {
@@ -146,8 +174,8 @@ struct sp_plan_s {
   size_t off_x, off_y, off_z;      // workspace layout (bytes): main array at 0
   void* dev;                       // one allocation holding every table
   // double tables (FP64 path and the FP64 zonal side path)
-  cpx<double>* tw_row;   // exp(-2 pi i t/L), t < L
-  cpx<double>* tw_col;   // exp(-2 pi i t/N), t < N
+  cpx<double>* tw_row;   // FFT twiddles of the rows (length L, layout in FftDesc)
+  cpx<double>* tw_col;   // FFT twiddles of the columns (length N)
   cpx<double>* post_row; // exp(-2 pi i k/n), k <= L
   cpx<double>* post_col; // exp(-i pi j/(2N)), j <= N
   cpx<double>* post_col_s; // the same times 1/(2N) (forward colatitude transform)
@@ -530,9 +558,8 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
 
   // host tables
   const size_t cd_sz = sizeof(cpx<double>);
-  std::vector<cpx<double>> tw_row(p->L), tw_col(p->N), post_row(p->L + 1), post_col(p->N + 1);
-  for (int t = 0; t < p->L; ++t) unit_root(t, p->L, &tw_row[t].re, &tw_row[t].im);
-  for (int t = 0; t < p->N; ++t) unit_root(t, p->N, &tw_col[t].re, &tw_col[t].im);
+  std::vector<cpx<double>> tw_row = stage_twiddles(rd), tw_col = stage_twiddles(cd);
+  std::vector<cpx<double>> post_row(p->L + 1), post_col(p->N + 1);
   for (int k = 0; k <= p->L; ++k) unit_root(k, n_lambda, &post_row[k].re, &post_row[k].im);
   for (int j = 0; j <= p->N; ++j) unit_root(j, 4L * p->N, &post_col[j].re, &post_col[j].im);
   std::vector<cpx<double>> post_col_s(p->N + 1);
@@ -571,7 +598,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
     off = align(off + bytes);
     return o;
   };
-  size_t o_tw_row = take(p->L * cd_sz), o_tw_col = take(p->N * cd_sz);
+  size_t o_tw_row = take(tw_row.size() * cd_sz), o_tw_col = take(tw_col.size() * cd_sz);
   size_t o_post_row = take((p->L + 1) * cd_sz), o_post_col = take((p->N + 1) * cd_sz);
   size_t o_post_col_s = take((p->N + 1) * cd_sz);
   size_t o_scale = take(p->nt * sizeof(double));
@@ -630,8 +657,8 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   auto up = [&](void* dst, const void* src, size_t bytes, const char* what) {
     if (bytes) step(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice), what);
   };
-  up(p->tw_row, tw_row.data(), p->L * cd_sz, "copy tw_row");
-  up(p->tw_col, tw_col.data(), p->N * cd_sz, "copy tw_col");
+  up(p->tw_row, tw_row.data(), tw_row.size() * cd_sz, "copy tw_row");
+  up(p->tw_col, tw_col.data(), tw_col.size() * cd_sz, "copy tw_col");
   up(p->post_row, post_row.data(), (p->L + 1) * cd_sz, "copy post_row");
   up(p->post_col, post_col.data(), (p->N + 1) * cd_sz, "copy post_col");
   up(p->post_col_s, post_col_s.data(), (p->N + 1) * cd_sz, "copy post_col_s");
@@ -1008,12 +1035,10 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
     // FP32 correction (FP32 + refinement: 16 + 16 + 8 bytes per element)
     const size_t nkp = (size_t)b.N * b.Kp;
     max_slot = std::max(max_slot, refine ? (5 * nkp + 1) / 2 : nkp);
-    h.tw_row.resize(b.L);
-    h.tw_col.resize(b.N);
+    h.tw_row = stage_twiddles(h.rd);
+    h.tw_col = stage_twiddles(h.cd);
     h.post_row.resize(b.L + 1);
     h.post_col.resize(b.N + 1);
-    for (int t = 0; t < b.L; ++t) unit_root(t, b.L, &h.tw_row[t].re, &h.tw_row[t].im);
-    for (int t = 0; t < b.N; ++t) unit_root(t, b.N, &h.tw_col[t].re, &h.tw_col[t].im);
     for (int k = 0; k <= b.L; ++k) unit_root(k, b.nl, &h.post_row[k].re, &h.post_row[k].im);
     for (int j = 0; j <= b.N; ++j) unit_root(j, 4L * b.N, &h.post_col[j].re, &h.post_col[j].im);
     h.post_col_s.resize(b.N + 1);
@@ -1030,8 +1055,8 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
     const size_t dsz = refine ? sizeof(cpx<sp::dd>) : 0, f32 = refine ? (size_t)b.N * b.Kp * sizeof(float) : 0;
     const size_t fz = refine ? (size_t)b.N * 2 * sizeof(double) : 0;
     Offs& o = co[c];
-    o.tw_row = take(b.L * csz);
-    o.tw_col = take(b.N * csz);
+    o.tw_row = take(h.tw_row.size() * csz);
+    o.tw_col = take(h.tw_col.size() * csz);
     o.post_row = take((b.L + 1) * csz);
     o.post_col = take((b.N + 1) * csz);
     o.post_col_s = take((b.N + 1) * csz);
@@ -1041,8 +1066,8 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
     o.fl = take(fac);
     o.fiu = take(fac);
     o.fcu = take(fac);
-    o.d_tw_row = take(b.L * dsz);
-    o.d_tw_col = take(b.N * dsz);
+    o.d_tw_row = take(h.tw_row.size() * dsz);
+    o.d_tw_col = take(h.tw_col.size() * dsz);
     o.d_post_row = take((b.L + 1) * dsz);
     o.d_post_col = take((b.N + 1) * dsz);
     o.d_post_col_s = take((b.N + 1) * dsz);
@@ -1088,8 +1113,8 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
     b.fl = reinterpret_cast<double*>(base + co[c].fl);
     b.fiu = reinterpret_cast<double*>(base + co[c].fiu);
     b.fcu = reinterpret_cast<double*>(base + co[c].fcu);
-    step(cudaMemcpy((void*)b.tw_row, h.tw_row.data(), b.L * csz, cudaMemcpyHostToDevice), "copy");
-    step(cudaMemcpy((void*)b.tw_col, h.tw_col.data(), b.N * csz, cudaMemcpyHostToDevice), "copy");
+    step(cudaMemcpy((void*)b.tw_row, h.tw_row.data(), h.tw_row.size() * csz, cudaMemcpyHostToDevice), "copy");
+    step(cudaMemcpy((void*)b.tw_col, h.tw_col.data(), h.tw_col.size() * csz, cudaMemcpyHostToDevice), "copy");
     step(cudaMemcpy((void*)b.post_row, h.post_row.data(), (b.L + 1) * csz, cudaMemcpyHostToDevice), "copy");
     step(cudaMemcpy((void*)b.post_col, h.post_col.data(), (b.N + 1) * csz, cudaMemcpyHostToDevice), "copy");
     step(cudaMemcpy((void*)b.post_col_s, h.post_col_s.data(), (b.N + 1) * csz, cudaMemcpyHostToDevice), "copy");

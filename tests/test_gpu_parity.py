@@ -203,5 +203,20 @@ def test_full_size_single_harmonics(sp, big_case, l, m):
     u = plan.solve(y)
     ref = -y / (l * (l + 1))
     err = float((u - ref).abs().max() / ref.abs().max())
-    # zonal harmonics sit in the k = 0 column, whose system is the worst conditioned
-    assert err < (1e-10 if m == 0 else 1e-12)
+    if m != 0:
+        assert err < 1e-12
+        return
+    # zonal harmonics sit in the k = 0 column, whose system is the worst
+    # conditioned (~4e9 at m = 10^4, so FP64 rounding alone allows ~4e-7): any
+    # FP64 solution of it, the oracle's included, meets the closed form to
+    # ~1e-10 only, and two of them (GPU, oracle) differ by as much.  The GPU's
+    # error must be of the oracle's size.
+    assert err < 3e-10
+    U_ref, _, _ = O.sampled_columns(y.cpu().numpy(), [0])
+    U = O.lambda_spectrum(u.cpu().numpy(), [0])
+    U_ex = O.lambda_spectrum(ref.cpu().numpy(), [0])
+    scale = float(np.abs(U_ex).max())
+    e_gpu = float(np.abs(U - U_ex).max()) / scale
+    e_oracle = float(np.abs(U_ref - U_ex).max()) / scale
+    assert e_oracle < 3e-10 and e_gpu < 3.0 * e_oracle + 1e-12, (e_gpu, e_oracle)
+    assert float(np.abs(U - U_ref).max()) / scale < 3e-10
