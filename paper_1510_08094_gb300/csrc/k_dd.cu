@@ -46,6 +46,7 @@ cudaError_t allow_transform_smem<dd>(int bytes) {
   upd(cudaFuncSetAttribute(k_theta_forward<dd, false, true>, a, bytes));
   upd(cudaFuncSetAttribute(k_theta_inverse<dd, false, false>, a, bytes));
   upd(cudaFuncSetAttribute(k_theta_inverse<dd, false, true>, a, bytes));
+  upd(allow_pipe_smem<dd>(bytes));
   return e;
 }
 
@@ -59,5 +60,7 @@ void launch_zonal_extract(const Launch& l, const cpx<dd>* Wdd, cpx<double>* Z, i
 void launch_zonal_insert(const Launch& l, const cpx<double>* Z, cpx<dd>* X, int N, int Kp) {
   k_zonal_insert<<<l.grid, l.threads, l.smem, l.stream>>>(Z, X, N, Kp);
 }
+
+SP_INSTANTIATE_PIPE(dd);
 
 }  // namespace sp

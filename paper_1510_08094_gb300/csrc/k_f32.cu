@@ -50,6 +50,7 @@ cudaError_t allow_transform_smem<float>(int bytes) {
   upd(cudaFuncSetAttribute(k_theta_inverse<float, false, true>, a, bytes));
   upd(cudaFuncSetAttribute(k_theta_inverse<float, true, false>, a, bytes));
   upd(cudaFuncSetAttribute(k_theta_inverse<float, true, true>, a, bytes));
+  upd(allow_pipe_smem<float>(bytes));
   return e;
 }
 template <>
@@ -62,5 +63,7 @@ template <>
 void launch_factor<float>(const Launch& l, float* fl, float* fiu, float* fcu, int N, int K, int Kp) {
   k_factor<float><<<l.grid, l.threads, l.smem, l.stream>>>(fl, fiu, fcu, N, K, Kp);
 }
+
+SP_INSTANTIATE_PIPE(float);
 
 }  // namespace sp

@@ -52,6 +52,7 @@ cudaError_t allow_transform_smem<double>(int bytes) {
   upd(cudaFuncSetAttribute(k_theta_inverse<double, false, true>, a, bytes));
   upd(cudaFuncSetAttribute(k_theta_inverse<double, true, false>, a, bytes));
   upd(cudaFuncSetAttribute(k_theta_inverse<double, true, true>, a, bytes));
+  upd(allow_pipe_smem<double>(bytes));
   return e;
 }
 template <>
@@ -93,5 +94,7 @@ void launch_batched_fp64(bool big, dim3 grid, int threads, size_t smem, cudaStre
 void launch_sum2_finish(cudaStream_t st, const cpx<double>* C, int N, int Kp, double* out) {
   k_sum2_finish<<<1, 256, 0, st>>>(C, N, Kp, out);
 }
+
+SP_INSTANTIATE_PIPE(double);
 
 }  // namespace sp

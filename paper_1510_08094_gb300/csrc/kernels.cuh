@@ -30,6 +30,20 @@ __device__ __forceinline__ int makhoul_pos(int i, int N) {
   return (i & 1) ? N - 1 - (i >> 1) : (i >> 1);
 }
 
+// cp.async: asynchronous global -> shared copies (16 bytes through L2, 8 through L1)
+__device__ __forceinline__ void cp_async16(void* smem, const void* g) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* g) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Split of a double into two floats hi + lo (|x - hi - lo| <= 2^-48 |x|) with
 // integer operations only: hi keeps the top 24 significand bits (truncated),
 // lo the next 29 bits rounded to 24.  Used where FP64-accurate sums of double
@@ -115,6 +129,63 @@ __device__ __forceinline__ dd block_sum_dd(dd v) {
 }
 
 // ---------------------------------------------------------------------------
+// Tile inputs.  Every transform kernel first gathers its tile into the FFT
+// buffer (permuted, pre-processed); the input is read either straight from
+// global memory or from a copy of the tile that cp.async staged in shared
+// memory while the previous tile was being transformed (the pipelined
+// kernels below).  Element (r, q): row r of the tile, entry q of that row.
+// ---------------------------------------------------------------------------
+template <typename E>
+struct FromGlobal {
+  const E* p;    // element (0, 0)
+  size_t ld;     // row stride in elements
+  __device__ __forceinline__ E operator()(int r, int q) const { return p[(size_t)r * ld + q]; }
+};
+template <typename E>
+struct FromStaged {
+  const E* p;    // shared memory
+  int ld;
+  __device__ __forceinline__ E operator()(int r, int q) const { return p[r * ld + q]; }
+};
+// read-only double pairs of f (rows_forward from global memory)
+struct FromInput {
+  const double2* p;
+  size_t ld;
+  __device__ __forceinline__ double2 operator()(int r, int q) const { return __ldg(p + (size_t)r * ld + q); }
+};
+
+// cp.async copies of `rows` rows of `bytes` bytes each (a multiple of CH = 16
+// or 8) from g (row stride ld_bytes) to consecutive rows of S.
+template <int CH>
+__device__ __forceinline__ void cp_async_chunk(void* s, const void* g) {
+  if constexpr (CH == 16) cp_async16(s, g);
+  else cp_async8(s, g);
+}
+template <int CH>
+__device__ __forceinline__ void stage_rows(void* S, const void* g, size_t ld_bytes, int rows, int bytes) {
+  const int per = bytes / CH;
+  for (int r = 0; r < rows; ++r) {
+    const char* src = static_cast<const char*>(g) + (size_t)r * ld_bytes;
+    char* dst = static_cast<char*>(S) + (size_t)r * bytes;
+    for (int c = threadIdx.x; c < per; c += blockDim.x) cp_async_chunk<CH>(dst + c * CH, src + c * CH);
+  }
+}
+// the same for many short rows (the colatitude tiles: N rows of `cols`
+// elements): `valid` chunks of each row are copied, the thread loop runs over
+// 1 << ps >= valid chunk slots per row
+template <int CH>
+__device__ __forceinline__ void stage_columns(void* S, const void* g, size_t ld_bytes, int nrows, int ps,
+                                              int valid, int row_bytes) {
+  const int total = nrows << ps;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int r = t >> ps, c = t & ((1 << ps) - 1);
+    if (c < valid)
+      cp_async_chunk<CH>(static_cast<char*>(S) + (size_t)r * row_bytes + c * CH,
+                         static_cast<const char*>(g) + (size_t)r * ld_bytes + c * CH);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // rows_forward: real FFT along longitude in arithmetic T.
 //   forward (ADJ = false): W[i][k] = row_scale[i] * G_i(k)
 //   adjoint (ADJ = true):  W[i][k] = c_k * sum_q ubar_iq e^{-2 pi i k q/n},
@@ -123,16 +194,13 @@ __device__ __forceinline__ dd block_sum_dd(dd v) {
 //   (row_scale[i] * sum_q f_iq, or sum_q ubar_iq), summed in double-float from
 //   the double inputs, Z[i][1] = 0; the FP64 side path takes the zonal column
 //   from there.
-// One CTA per `rows` consecutive rows; shared memory rows * L complex.
+// One tile = `rows` consecutive rows; shared memory rows * L complex.
 // ---------------------------------------------------------------------------
-template <typename T, bool ADJ, bool BIG>
-__device__ __forceinline__ void rows_forward_tile(int tile, cpx<T>* __restrict__ sm,
-    const double* __restrict__ f, cpx<T>* __restrict__ W, int nt, int n, int Kp, int rows,
-    const FftDesc& d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
-    const cpx<T>* __restrict__ post, const double* __restrict__ row_scale,
-    const T* __restrict__ row_scale_t, cpx<double>* __restrict__ zonal) {
+template <typename T, bool ADJ, typename Src>
+__device__ __forceinline__ void rows_forward_load(int row0, cpx<T>* __restrict__ sm, const Src& src, int nt,
+    int n, int rows, const int* __restrict__ perm, const double* __restrict__ row_scale,
+    cpx<double>* __restrict__ zonal) {
   const int L = n >> 1;
-  const int row0 = tile * rows;
   for (int r = 0; r < rows; ++r) {
     const int row = row0 + r;
     dd acc(0.f, 0.f);
@@ -140,7 +208,7 @@ __device__ __forceinline__ void rows_forward_tile(int tile, cpx<T>* __restrict__
     for (int q = threadIdx.x; q < L; q += blockDim.x) {
       cpx<T> z = {(T)0, (T)0};
       if (row < nt) {
-        double2 v = __ldg(reinterpret_cast<const double2*>(f + (size_t)row * n) + q);
+        double2 v = src(r, q);
         z = {load_conv<T>(v.x), load_conv<T>(v.y)};
         if (zonal) acc = dd_add(acc, dd_add(split_double(v.x), split_double(v.y)));
       }
@@ -156,7 +224,13 @@ __device__ __forceinline__ void rows_forward_tile(int tile, cpx<T>* __restrict__
       }
     }
   }
-  __syncthreads();
+}
+
+template <typename T, bool ADJ, bool BIG>
+__device__ __forceinline__ void rows_forward_finish(int row0, cpx<T>* __restrict__ sm, cpx<T>* __restrict__ W,
+    int nt, int n, int Kp, int rows, const FftDesc& d, const cpx<T>* __restrict__ tw,
+    const cpx<T>* __restrict__ post, const T* __restrict__ row_scale_t) {
+  const int L = n >> 1;
   fft_run<-1, BIG>(sm, rows, d, tw);
   const int K = L + 1;
   for (int r = 0; r < rows; ++r) {
@@ -181,6 +255,19 @@ __device__ __forceinline__ void rows_forward_tile(int tile, cpx<T>* __restrict__
 }
 
 template <typename T, bool ADJ, bool BIG>
+__device__ __forceinline__ void rows_forward_tile(int tile, cpx<T>* __restrict__ sm,
+    const double* __restrict__ f, cpx<T>* __restrict__ W, int nt, int n, int Kp, int rows,
+    const FftDesc& d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
+    const cpx<T>* __restrict__ post, const double* __restrict__ row_scale,
+    const T* __restrict__ row_scale_t, cpx<double>* __restrict__ zonal) {
+  const int row0 = tile * rows;
+  const FromInput src{reinterpret_cast<const double2*>(f) + (size_t)row0 * (n >> 1), (size_t)(n >> 1)};
+  rows_forward_load<T, ADJ>(row0, sm, src, nt, n, rows, perm, row_scale, zonal);
+  __syncthreads();
+  rows_forward_finish<T, ADJ, BIG>(row0, sm, W, nt, n, Kp, rows, d, tw, post, row_scale_t);
+}
+
+template <typename T, bool ADJ, bool BIG>
 __global__ void __launch_bounds__(BIG ? 256 : 512) k_rows_forward(
     const double* __restrict__ f, cpx<T>* __restrict__ W, int nt, int n, int Kp, int rows,
     FftDesc d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
@@ -189,6 +276,43 @@ __global__ void __launch_bounds__(BIG ? 256 : 512) k_rows_forward(
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
   rows_forward_tile<T, ADJ, BIG>(blockIdx.x, sm, f, W, nt, n, Kp, rows, d, tw, perm, post, row_scale, row_scale_t, zonal);
+}
+
+// Pipelined form: a persistent CTA loops over tiles blockIdx.x, + gridDim.x,
+// ...; while tile t is transformed in the FFT buffer, cp.async stages the
+// input rows of the CTA's next tile in a second shared-memory buffer (rows * n
+// doubles after the rows * L complex FFT buffer), so HBM reads overlap the
+// arithmetic of the same CTA.
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(512) k_rows_forward_pipe(
+    const double* __restrict__ f, cpx<T>* __restrict__ W, int nt, int n, int Kp, int rows,
+    FftDesc d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
+    const cpx<T>* __restrict__ post, const double* __restrict__ row_scale,
+    const T* __restrict__ row_scale_t, cpx<double>* __restrict__ zonal) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = n >> 1;
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  double2* S = reinterpret_cast<double2*>(smem_raw + (((size_t)rows * L * sizeof(cpx<T>) + 15) & ~(size_t)15));
+  const int ntiles = (nt + rows - 1) / rows;
+  auto stage = [&](int t) {
+    const int row0 = t * rows;
+    stage_rows<16>(S, f + (size_t)row0 * n, (size_t)n * sizeof(double), min(rows, nt - row0),
+                   n * (int)sizeof(double));
+  };
+  int tile = blockIdx.x;
+  if (tile < ntiles) stage(tile);
+  cp_commit();
+  for (; tile < ntiles; tile += gridDim.x) {
+    cp_wait_all();
+    __syncthreads();
+    const int row0 = tile * rows;
+    rows_forward_load<T, ADJ>(row0, sm, FromStaged<double2>{S, L}, nt, n, rows, perm, row_scale, zonal);
+    __syncthreads();
+    if (tile + (int)gridDim.x < ntiles) stage(tile + gridDim.x);
+    cp_commit();
+    rows_forward_finish<T, ADJ, false>(row0, sm, W, nt, n, Kp, rows, d, tw, post, row_scale_t);
+  }
+  cp_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -200,23 +324,18 @@ __global__ void __launch_bounds__(BIG ? 256 : 512) k_rows_forward(
 //   zonal (optional): U_0 of row i is taken as Z[i][0].re, added in double
 //            after the transform (the FP64 side path's zonal column).
 // ---------------------------------------------------------------------------
-template <typename T, bool ADJ, bool BIG>
-__device__ __forceinline__ void rows_inverse_tile(int tile, cpx<T>* __restrict__ sm,
-    const cpx<T>* __restrict__ W, double* __restrict__ u, int nt, int n, int Kp, int rows,
-    const FftDesc& d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
-    const cpx<T>* __restrict__ post, const double* __restrict__ row_scale,
-    const T* __restrict__ row_scale_t, const cpx<double>* __restrict__ zonal) {
+template <typename T, bool ADJ, typename Src>
+__device__ __forceinline__ void rows_inverse_load(int row0, cpx<T>* __restrict__ sm, const Src& src, int nt,
+    int n, int rows, const int* __restrict__ perm, const cpx<T>* __restrict__ post, bool zonal) {
   const int L = n >> 1;
-  const int row0 = tile * rows;
   for (int r = 0; r < rows; ++r)
 #pragma unroll 2
   for (int k = threadIdx.x; k < L; k += blockDim.x) {
     const int row = row0 + r;
     cpx<T> z = {(T)0, (T)0};
     if (row < nt) {
-      const cpx<T>* U = W + (size_t)row * Kp;
-      cpx<T> uk = U[k];
-      cpx<T> up = U[L - k];                      // k = 0 pairs with the Nyquist bin
+      cpx<T> uk = src(r, k);
+      cpx<T> up = src(r, L - k);                 // k = 0 pairs with the Nyquist bin
       if (k == 0) {
         uk.im = (T)0;
         up.im = (T)0;
@@ -232,7 +351,14 @@ __device__ __forceinline__ void rows_inverse_tile(int tile, cpx<T>* __restrict__
     }
     sm[r * L + __ldg(perm + k)] = z;
   }
-  __syncthreads();
+}
+
+template <typename T, bool ADJ, bool BIG>
+__device__ __forceinline__ void rows_inverse_finish(int row0, cpx<T>* __restrict__ sm, double* __restrict__ u,
+    int nt, int n, int rows, const FftDesc& d, const cpx<T>* __restrict__ tw,
+    const double* __restrict__ row_scale, const T* __restrict__ row_scale_t,
+    const cpx<double>* __restrict__ zonal) {
+  const int L = n >> 1;
   fft_run<+1, BIG>(sm, rows, d, tw);
   for (int r = 0; r < rows; ++r)
   for (int q = threadIdx.x; q < L; q += blockDim.x) {
@@ -258,6 +384,19 @@ __device__ __forceinline__ void rows_inverse_tile(int tile, cpx<T>* __restrict__
 }
 
 template <typename T, bool ADJ, bool BIG>
+__device__ __forceinline__ void rows_inverse_tile(int tile, cpx<T>* __restrict__ sm,
+    const cpx<T>* __restrict__ W, double* __restrict__ u, int nt, int n, int Kp, int rows,
+    const FftDesc& d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
+    const cpx<T>* __restrict__ post, const double* __restrict__ row_scale,
+    const T* __restrict__ row_scale_t, const cpx<double>* __restrict__ zonal) {
+  const int row0 = tile * rows;
+  rows_inverse_load<T, ADJ>(row0, sm, FromGlobal<cpx<T>>{W + (size_t)row0 * Kp, (size_t)Kp}, nt, n, rows, perm,
+                            post, zonal != nullptr);
+  __syncthreads();
+  rows_inverse_finish<T, ADJ, BIG>(row0, sm, u, nt, n, rows, d, tw, row_scale, row_scale_t, zonal);
+}
+
+template <typename T, bool ADJ, bool BIG>
 __global__ void __launch_bounds__(BIG ? 256 : 512) k_rows_inverse(
     const cpx<T>* __restrict__ W, double* __restrict__ u, int nt, int n, int Kp, int rows,
     FftDesc d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
@@ -266,6 +405,40 @@ __global__ void __launch_bounds__(BIG ? 256 : 512) k_rows_inverse(
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
   rows_inverse_tile<T, ADJ, BIG>(blockIdx.x, sm, W, u, nt, n, Kp, rows, d, tw, perm, post, row_scale, row_scale_t, zonal);
+}
+
+// pipelined form (see k_rows_forward_pipe): the staged copy holds the tile's
+// spectrum rows, rows * Kp complex T, after the rows * L FFT buffer
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(512) k_rows_inverse_pipe(
+    const cpx<T>* __restrict__ W, double* __restrict__ u, int nt, int n, int Kp, int rows,
+    FftDesc d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
+    const cpx<T>* __restrict__ post, const double* __restrict__ row_scale,
+    const T* __restrict__ row_scale_t, const cpx<double>* __restrict__ zonal) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = n >> 1;
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* S = reinterpret_cast<cpx<T>*>(smem_raw + (((size_t)rows * L * sizeof(cpx<T>) + 15) & ~(size_t)15));
+  const int ntiles = (nt + rows - 1) / rows;
+  auto stage = [&](int t) {
+    const int row0 = t * rows;
+    stage_rows<16>(S, W + (size_t)row0 * Kp, (size_t)Kp * sizeof(cpx<T>), min(rows, nt - row0),
+                   Kp * (int)sizeof(cpx<T>));
+  };
+  int tile = blockIdx.x;
+  if (tile < ntiles) stage(tile);
+  cp_commit();
+  for (; tile < ntiles; tile += gridDim.x) {
+    cp_wait_all();
+    __syncthreads();
+    const int row0 = tile * rows;
+    rows_inverse_load<T, ADJ>(row0, sm, FromStaged<cpx<T>>{S, Kp}, nt, n, rows, perm, post, zonal != nullptr);
+    __syncthreads();
+    if (tile + (int)gridDim.x < ntiles) stage(tile + gridDim.x);
+    cp_commit();
+    rows_inverse_finish<T, ADJ, false>(row0, sm, u, nt, n, rows, d, tw, row_scale, row_scale_t, zonal);
+  }
+  cp_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -280,14 +453,11 @@ __global__ void __launch_bounds__(BIG ? 256 : 512) k_rows_inverse(
 //            k = 0 closure.
 //   bit 2 of `zonal` multiplies the result by (-1)^k: the coefficients of the
 //   paper's expansion in e^{i k lambda} with lambda_q = -pi + 2 pi q/n.
-// One CTA per `cols` consecutive columns.  inv_n = 1/N in arithmetic T.
+// One tile = `cols` consecutive columns.  inv_n = 1/N in arithmetic T.
 // ---------------------------------------------------------------------------
-template <typename T, bool ADJ, bool BIG>
-__device__ __forceinline__ void theta_forward_tile(int tile, cpx<T>* __restrict__ sm,
-    cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, const FftDesc& d,
-    const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
-    T inv_n, int zonal) {
-  const int k0 = tile * cols;
+template <typename T, typename Src>
+__device__ __forceinline__ void theta_forward_load(int k0, cpx<T>* __restrict__ sm, const Src& src, int N,
+                                                   int K, int cols, const int* __restrict__ perm) {
   const int cs = __ffs(cols) - 1;            // cols is a power of two
 #pragma unroll 4
   for (int idx = threadIdx.x; idx < N * cols; idx += blockDim.x) {
@@ -295,12 +465,18 @@ __device__ __forceinline__ void theta_forward_tile(int tile, cpx<T>* __restrict_
     int k = k0 + c;
     cpx<T> v = {(T)0, (T)0};
     if (k < K) {
-      v = W[(size_t)i * Kp + k];
+      v = src(i, c);
       if ((k & 1) && (i & 1)) v = {-v.re, -v.im};
     }
     sm[c * N + __ldg(perm + makhoul_pos(i, N))] = v;
   }
-  __syncthreads();
+}
+
+template <typename T, bool ADJ, bool BIG>
+__device__ __forceinline__ void theta_forward_finish(int k0, cpx<T>* __restrict__ sm, cpx<T>* __restrict__ W,
+    int N, int K, int Kp, int cols, const FftDesc& d, const cpx<T>* __restrict__ tw,
+    const cpx<T>* __restrict__ post, int zonal) {
+  const int cs = __ffs(cols) - 1;
   fft_run<-1, BIG>(sm, cols, d, tw);
   for (int idx = threadIdx.x; idx < N * cols; idx += blockDim.x) {
     int j = idx >> cs, c = idx & (cols - 1);
@@ -342,6 +518,18 @@ __device__ __forceinline__ void theta_forward_tile(int tile, cpx<T>* __restrict_
 }
 
 template <typename T, bool ADJ, bool BIG>
+__device__ __forceinline__ void theta_forward_tile(int tile, cpx<T>* __restrict__ sm,
+    cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, const FftDesc& d,
+    const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
+    T inv_n, int zonal) {
+  (void)inv_n;
+  const int k0 = tile * cols;
+  theta_forward_load<T>(k0, sm, FromGlobal<cpx<T>>{W + k0, (size_t)Kp}, N, K, cols, perm);
+  __syncthreads();
+  theta_forward_finish<T, ADJ, BIG>(k0, sm, W, N, K, Kp, cols, d, tw, post, zonal);
+}
+
+template <typename T, bool ADJ, bool BIG>
 __global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_forward(
     cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d,
     const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
@@ -351,48 +539,90 @@ __global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_forward(
   theta_forward_tile<T, ADJ, BIG>(blockIdx.x, sm, W, N, K, Kp, cols, d, tw, perm, post, inv_n, zonal);
 }
 
+// cp.async staging of the columns [k0, k0 + cols) of all N rows of W into S
+// (N rows of `cols` elements; columns at or past Kp are not copied, and the
+// loaders never read them since K <= Kp)
+template <typename T>
+__device__ __forceinline__ void stage_theta(cpx<T>* S, const cpx<T>* W, int k0, int N, int Kp, int cols) {
+  const int ncols = min(cols, Kp - k0);
+  const int row_bytes = cols * (int)sizeof(cpx<T>);
+  const size_t ld = (size_t)Kp * sizeof(cpx<T>);
+  if ((ncols * sizeof(cpx<T>)) % 16 == 0) {
+    const int per = ncols * (int)sizeof(cpx<T>) / 16;
+    const int slots = cols * (int)sizeof(cpx<T>) / 16;      // a power of two >= per
+    stage_columns<16>(S, W + k0, ld, N, __ffs(slots) - 1, per, row_bytes);
+  } else {                                   // one FP32 complex per row
+    stage_columns<8>(S, W + k0, ld, N, 0, 1, row_bytes);
+  }
+}
+
+// pipelined form: persistent CTAs, the next tile's columns staged by cp.async
+// (N * cols complex T after the cols * N FFT buffer) during the transform
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(512) k_theta_forward_pipe(
+    cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d,
+    const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
+    T inv_n, int zonal) {
+  (void)inv_n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* S = reinterpret_cast<cpx<T>*>(smem_raw + (((size_t)cols * N * sizeof(cpx<T>) + 15) & ~(size_t)15));
+  const int ntiles = (K + cols - 1) / cols;
+  int tile = blockIdx.x;
+  if (tile < ntiles) stage_theta(S, W, tile * cols, N, Kp, cols);
+  cp_commit();
+  for (; tile < ntiles; tile += gridDim.x) {
+    cp_wait_all();
+    __syncthreads();
+    const int k0 = tile * cols;
+    theta_forward_load<T>(k0, sm, FromStaged<cpx<T>>{S, cols}, N, K, cols, perm);
+    __syncthreads();
+    if (tile + (int)gridDim.x < ntiles) stage_theta(S, W, (tile + gridDim.x) * cols, N, Kp, cols);
+    cp_commit();
+    theta_forward_finish<T, ADJ, false>(k0, sm, W, N, K, Kp, cols, d, tw, post, zonal);
+  }
+  cp_wait_all();
+}
+
 // ---------------------------------------------------------------------------
 // theta_inverse: per column k, DCT-III (k even) U_i = Y_0 + 2 sum_j Y_j cos(j theta_i)
 // with Y = X, or for k odd i (-1)^i times the DCT-III of Y_j = X_{N-j} (Y_0 = 0),
 // through one inverse FFT of V_j = exp(i pi j/(2N)) (Y_j - i Y_{N-j}) (Y_N = 0)
 // and the inverse Makhoul reordering.
 //   forward: U = DCT-III(X) (k even), i DST-III(X) (k odd); with bit 1 of
-//            `zonal` set (FP64 arithmetic) the first CTA first closes the
+//            `zonal` set (FP64 arithmetic) the first tile first closes the
 //            k = 0 column: X_00 = sum_{j even >= 2} 2 X_j0/(j^2-1) (w^T X_0 = 0);
 //            bit 2 takes the input in the coefficient convention (times (-1)^k).
 //   adjoint: inputs with j >= 1 halved and outputs scaled by inv_n = 1/N: the
 //            transpose of theta_forward
 // ---------------------------------------------------------------------------
-template <typename T, bool ADJ, bool BIG>
-__device__ __forceinline__ void theta_inverse_tile(int tile, cpx<T>* __restrict__ sm,
-    cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, const FftDesc& d,
-    const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
-    T inv_n, int zonal) {
-  const int k0 = tile * cols;
-  if constexpr (std::is_same<T, double>::value) {
-    if (!ADJ && (zonal & 1) && k0 == 0) {
-      cpx<double> acc = {0.0, 0.0};
-      for (int j = 2 + 2 * threadIdx.x; j < N; j += 2 * blockDim.x) {
-        double wj = 2.0 / ((double)j * (double)j - 1.0);
-        acc = acc + wj * W[(size_t)j * Kp];
-      }
-      for (int off = 16; off > 0; off >>= 1) {
-        acc.re = acc.re + __shfl_down_sync(0xffffffffu, acc.re, off);
-        acc.im = acc.im + __shfl_down_sync(0xffffffffu, acc.im, off);
-      }
-      __shared__ cpx<double> red[32];
-      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        cpx<double> tot = {0.0, 0.0};
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot = tot + red[w];
-        W[0] = tot;
-      }
-      __syncthreads();
-    }
+// the k = 0 closure of the FP64 path (whole CTA; W[0] written)
+__device__ __forceinline__ void zonal_closure(cpx<double>* __restrict__ W, int N, int Kp) {
+  cpx<double> acc = {0.0, 0.0};
+  for (int j = 2 + 2 * threadIdx.x; j < N; j += 2 * blockDim.x) {
+    double wj = 2.0 / ((double)j * (double)j - 1.0);
+    acc = acc + wj * W[(size_t)j * Kp];
   }
-  // pre-twiddle straight from global memory, one thread per pair (j, N - j),
-  // j = 0 .. N/2, writing V_j and V_{N-j} to their digit-reversed slots
+  for (int off = 16; off > 0; off >>= 1) {
+    acc.re = acc.re + __shfl_down_sync(0xffffffffu, acc.re, off);
+    acc.im = acc.im + __shfl_down_sync(0xffffffffu, acc.im, off);
+  }
+  __shared__ cpx<double> red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cpx<double> tot = {0.0, 0.0};
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot = tot + red[w];
+    W[0] = tot;
+  }
+  __syncthreads();
+}
+
+template <typename T, bool ADJ, typename Src>
+__device__ __forceinline__ void theta_inverse_load(int k0, cpx<T>* __restrict__ sm, const Src& src, int N,
+    int K, int cols, const int* __restrict__ perm, const cpx<T>* __restrict__ post, int zonal) {
+  // pre-twiddle, one thread per pair (j, N - j), j = 0 .. N/2, writing V_j and
+  // V_{N-j} to their digit-reversed slots
   const int H = N / 2 + 1;
   const int cs = __ffs(cols) - 1;            // cols is a power of two
 #pragma unroll 2
@@ -408,11 +638,11 @@ __device__ __forceinline__ void theta_inverse_tile(int tile, cpx<T>* __restrict_
     }
     if (j == 0) {
       // V_0 = Y_0 - i Y_N = X_0 (k even) or 0 (k odd)
-      V[__ldg(perm + 0)] = odd ? cpx<T>{(T)0, (T)0} : W[k];
+      V[__ldg(perm + 0)] = odd ? cpx<T>{(T)0, (T)0} : src(0, c);
       continue;
     }
     int jj = N - j;
-    cpx<T> xa = W[(size_t)j * Kp + k], xb = W[(size_t)jj * Kp + k];
+    cpx<T> xa = src(j, c), xb = src(jj, c);
     if (ADJ) {
       xa = (T)0.5 * xa;
       xb = (T)0.5 * xb;
@@ -431,7 +661,12 @@ __device__ __forceinline__ void theta_inverse_tile(int tile, cpx<T>* __restrict_
       V[__ldg(perm + jj)] = cmul(wb, cpx<T>{yb.re + ya.im, yb.im - ya.re});
     }
   }
-  __syncthreads();
+}
+
+template <typename T, bool ADJ, bool BIG>
+__device__ __forceinline__ void theta_inverse_finish(int k0, cpx<T>* __restrict__ sm, cpx<T>* __restrict__ W,
+    int N, int K, int Kp, int cols, const FftDesc& d, const cpx<T>* __restrict__ tw, T inv_n) {
+  const int cs = __ffs(cols) - 1;
   fft_run<+1, BIG>(sm, cols, d, tw);
   for (int idx = threadIdx.x; idx < N * cols; idx += blockDim.x) {
     int i = idx >> cs, c = idx & (cols - 1);
@@ -448,6 +683,20 @@ __device__ __forceinline__ void theta_inverse_tile(int tile, cpx<T>* __restrict_
 }
 
 template <typename T, bool ADJ, bool BIG>
+__device__ __forceinline__ void theta_inverse_tile(int tile, cpx<T>* __restrict__ sm,
+    cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, const FftDesc& d,
+    const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
+    T inv_n, int zonal) {
+  const int k0 = tile * cols;
+  if constexpr (std::is_same<T, double>::value) {
+    if (!ADJ && (zonal & 1) && k0 == 0) zonal_closure(W, N, Kp);
+  }
+  theta_inverse_load<T, ADJ>(k0, sm, FromGlobal<cpx<T>>{W + k0, (size_t)Kp}, N, K, cols, perm, post, zonal);
+  __syncthreads();
+  theta_inverse_finish<T, ADJ, BIG>(k0, sm, W, N, K, Kp, cols, d, tw, inv_n);
+}
+
+template <typename T, bool ADJ, bool BIG>
 __global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_inverse(
     cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d,
     const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
@@ -455,6 +704,36 @@ __global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_inverse(
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
   theta_inverse_tile<T, ADJ, BIG>(blockIdx.x, sm, W, N, K, Kp, cols, d, tw, perm, post, inv_n, zonal);
+}
+
+// pipelined form (see k_theta_forward_pipe); the CTA that owns tile 0 closes
+// the k = 0 column before staging it
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(512) k_theta_inverse_pipe(
+    cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d,
+    const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
+    T inv_n, int zonal) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* S = reinterpret_cast<cpx<T>*>(smem_raw + (((size_t)cols * N * sizeof(cpx<T>) + 15) & ~(size_t)15));
+  const int ntiles = (K + cols - 1) / cols;
+  int tile = blockIdx.x;
+  if constexpr (std::is_same<T, double>::value) {
+    if (!ADJ && (zonal & 1) && tile == 0) zonal_closure(W, N, Kp);
+  }
+  if (tile < ntiles) stage_theta(S, W, tile * cols, N, Kp, cols);
+  cp_commit();
+  for (; tile < ntiles; tile += gridDim.x) {
+    cp_wait_all();
+    __syncthreads();
+    const int k0 = tile * cols;
+    theta_inverse_load<T, ADJ>(k0, sm, FromStaged<cpx<T>>{S, cols}, N, K, cols, perm, post, zonal);
+    __syncthreads();
+    if (tile + (int)gridDim.x < ntiles) stage_theta(S, W, (tile + gridDim.x) * cols, N, Kp, cols);
+    cp_commit();
+    theta_inverse_finish<T, ADJ, false>(k0, sm, W, N, K, Kp, cols, d, tw, inv_n);
+  }
+  cp_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -509,18 +788,6 @@ __global__ void k_factor(S* __restrict__ fl, S* __restrict__ fiu, S* __restrict_
 //   then T^T = U^T L^T: z_t = (b_t - c_{t-1} z_{t-1})/u_t, y_t = z_t - l_{t+1} y_{t+1}.
 // ---------------------------------------------------------------------------
 // cp.async helpers (per-thread asynchronous global -> shared copies)
-__device__ __forceinline__ void cp_async16(void* smem, const void* g) {
-  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* g) {
-  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // One warp = 32 chains (consecutive k, one parity).  Each lane streams its own
 // chain's rows through a ring of kRing shared-memory slots filled by its own

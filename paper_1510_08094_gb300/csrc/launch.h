@@ -36,6 +36,31 @@ template <typename T>
 void launch_theta_inverse(bool adj, bool big, const Launch& l, cpx<T>* W, int N, int K, int Kp, int cols,
                           const FftDesc& d, const cpx<T>* tw, const int* perm, const cpx<T>* post, T inv_n,
                           int zonal);
+// Pipelined (persistent) forms of the four transform kernels: grid = a
+// number of resident CTAs, each looping over tiles while cp.async stages its
+// next tile's input; dynamic shared memory = the FFT buffer plus the staged
+// input (16-byte aligned after it).  Non-BIG radices only.
+template <typename T>
+void launch_rows_forward_pipe(bool adj, const Launch& l, const double* f, cpx<T>* W, int nt, int n, int Kp,
+                              int rows, const FftDesc& d, const cpx<T>* tw, const int* perm, const cpx<T>* post,
+                              const double* row_scale, const T* row_scale_t, cpx<double>* zonal);
+template <typename T>
+void launch_rows_inverse_pipe(bool adj, const Launch& l, const cpx<T>* W, double* u, int nt, int n, int Kp,
+                              int rows, const FftDesc& d, const cpx<T>* tw, const int* perm, const cpx<T>* post,
+                              const double* row_scale, const T* row_scale_t, const cpx<double>* zonal);
+template <typename T>
+void launch_theta_forward_pipe(bool adj, const Launch& l, cpx<T>* W, int N, int K, int Kp, int cols,
+                               const FftDesc& d, const cpx<T>* tw, const int* perm, const cpx<T>* post, T inv_n,
+                               int zonal);
+template <typename T>
+void launch_theta_inverse_pipe(bool adj, const Launch& l, cpx<T>* W, int N, int K, int Kp, int cols,
+                               const FftDesc& d, const cpx<T>* tw, const int* perm, const cpx<T>* post, T inv_n,
+                               int zonal);
+// CTAs per SM of pipelined kernel `stage` (0 rows_forward, 1 theta_forward,
+// 2 theta_inverse, 3 rows_inverse); sets its shared-memory cap to `smem`
+template <typename T>
+cudaError_t pipe_occupancy(int stage, bool adj, int threads, size_t smem, int* blocks_per_sm);
+
 // raise the dynamic shared-memory cap of T's transform kernels
 template <typename T>
 cudaError_t allow_transform_smem(int bytes);

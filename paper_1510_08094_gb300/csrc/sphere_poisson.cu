@@ -58,12 +58,16 @@ bool make_fft_desc(int L, FftDesc* d) {
     rest /= r;
     return true;
   };
-  while (rest % 8 == 0) if (!push(8)) return false;
-  if (rest % 4 == 0 && !push(4)) return false;
-  if (rest % 2 == 0 && !push(2)) return false;
+  // odd radices first: the first pass (sub-DFT length 1) reads each
+  // butterfly's R inputs R elements apart, which for R = 8 puts a warp's
+  // accesses on a few shared-memory banks; odd strides spread them (and the
+  // digit-reversed load scatter then steps by L/8 elements, also spread)
   const int primes[] = {5, 3, 7, 11, 13, 17, 19, 23, 29, 31};
   for (int p : primes)
     while (rest % p == 0) if (!push(p)) return false;
+  while (rest % 8 == 0) if (!push(8)) return false;
+  if (rest % 4 == 0 && !push(4)) return false;
+  if (rest % 2 == 0 && !push(2)) return false;
   d->nstages = s;
   d->div_L = sp::make_fastdiv((unsigned)L);
   int ns = 1, off = 0;
@@ -166,6 +170,10 @@ struct sp_plan_s {
   FftDesc row_fft, col_fft;
   bool big_row, big_col;
   int rows_per_cta, cols_per_cta;  // transform tiles in the plan's arithmetic
+  bool pipe_rows, pipe_cols;       // pipelined kernels wanted for the row / column stages
+  bool pipe[4];                    // pipelined kernel per stage (rows fwd, theta fwd, theta inv, rows inv)
+  int pgrid[4];                    // its persistent grid
+  size_t psmem[4];                 // its dynamic shared memory
   int row_threads, col_threads;
   size_t row_smem, col_smem;
   int zcol_threads;                // FP64 zonal side path: one column per CTA
@@ -259,28 +267,117 @@ size_t esize(int precision) {
   return precision == SP_FP32 ? sizeof(cpx<float>) : sizeof(cpx<double>);
 }
 
+template <typename T>
+cudaError_t pipe_occupancy_of(int stage, int threads, size_t smem, int* bps) {
+  return sp::pipe_occupancy<T>(stage, false, threads, smem, bps);
+}
+
+// Decide per stage whether the pipelined kernel runs (wanted, no large-prime
+// radix, FFT buffer + staged input within shared memory, at least one CTA per
+// SM fits) and size its persistent grid: resident CTAs, at most one per tile.
+cudaError_t configure_pipes(sp_plan_t p) {
+  const size_t csz = esize(p->precision);
+  auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  const size_t rbuf = al((size_t)p->rows_per_cta * p->L * csz), cbuf = al((size_t)p->cols_per_cta * p->N * csz);
+  const size_t need[4] = {rbuf + (size_t)p->rows_per_cta * p->nl * sizeof(double),
+                          cbuf + (size_t)p->N * p->cols_per_cta * csz, cbuf + (size_t)p->N * p->cols_per_cta * csz,
+                          rbuf + (size_t)p->rows_per_cta * p->Kp * csz};
+  const bool want[4] = {p->pipe_rows && !p->big_row, p->pipe_cols && !p->big_col, p->pipe_cols && !p->big_col,
+                        p->pipe_rows && !p->big_row};
+  const int threads[4] = {p->row_threads, p->col_threads, p->col_threads, p->row_threads};
+  const int rt = (p->nt + p->rows_per_cta - 1) / p->rows_per_cta, ct = (p->K + p->cols_per_cta - 1) / p->cols_per_cta;
+  const int ntiles[4] = {rt, ct, ct, rt};
+  int sms = 1;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+  if (e != cudaSuccess) return e;
+  for (int s = 0; s < 4; ++s) {
+    p->pipe[s] = false;
+    if (!want[s] || need[s] > 220 * 1024) continue;
+    int bps = 0;
+    if (p->precision == SP_FP64) e = pipe_occupancy_of<double>(s, threads[s], need[s], &bps);
+    else if (p->precision == SP_FP32) e = pipe_occupancy_of<float>(s, threads[s], need[s], &bps);
+    else e = pipe_occupancy_of<sp::dd>(s, threads[s], need[s], &bps);
+    if (e != cudaSuccess) return e;
+    if (bps < 1) continue;
+    p->pipe[s] = true;
+    p->pgrid[s] = std::max(1, std::min(ntiles[s], sms * bps));
+    p->psmem[s] = need[s];
+  }
+  return cudaSuccess;
+}
+
+// The transform launches of a plan: the pipelined persistent kernel where the
+// plan chose it for that stage (pipe[s], grid pgrid[s], shared memory psmem[s]),
+// else one CTA per tile.
+template <typename T>
+void launch_rows_forward_x(sp_plan_t p, bool adj, cudaStream_t st, const double* f, cpx<T>* W, int nt, int n,
+                           int Kp, int rows, const FftDesc& d, const cpx<T>* tw, const int* perm,
+                           const cpx<T>* post, const double* rs, const T* rst, cpx<double>* zonal) {
+  if (p->pipe[0])
+    sp::launch_rows_forward_pipe<T>(adj, sp::Launch{dim3(p->pgrid[0]), p->row_threads, p->psmem[0], st}, f, W, nt,
+                                    n, Kp, rows, d, tw, perm, post, rs, rst, zonal);
+  else
+    sp::launch_rows_forward<T>(adj, p->big_row,
+                               sp::Launch{dim3((nt + rows - 1) / rows), p->row_threads, p->row_smem, st}, f, W, nt,
+                               n, Kp, rows, d, tw, perm, post, rs, rst, zonal);
+}
+template <typename T>
+void launch_theta_forward_x(sp_plan_t p, bool adj, cudaStream_t st, cpx<T>* W, int N, int K, int Kp, int cols,
+                            const FftDesc& d, const cpx<T>* tw, const int* perm, const cpx<T>* post, T inv_n,
+                            int zonal) {
+  if (p->pipe[1])
+    sp::launch_theta_forward_pipe<T>(adj, sp::Launch{dim3(p->pgrid[1]), p->col_threads, p->psmem[1], st}, W, N, K,
+                                     Kp, cols, d, tw, perm, post, inv_n, zonal);
+  else
+    sp::launch_theta_forward<T>(adj, p->big_col,
+                                sp::Launch{dim3((K + cols - 1) / cols), p->col_threads, p->col_smem, st}, W, N, K,
+                                Kp, cols, d, tw, perm, post, inv_n, zonal);
+}
+template <typename T>
+void launch_theta_inverse_x(sp_plan_t p, bool adj, cudaStream_t st, cpx<T>* W, int N, int K, int Kp, int cols,
+                            const FftDesc& d, const cpx<T>* tw, const int* perm, const cpx<T>* post, T inv_n,
+                            int zonal) {
+  if (p->pipe[2])
+    sp::launch_theta_inverse_pipe<T>(adj, sp::Launch{dim3(p->pgrid[2]), p->col_threads, p->psmem[2], st}, W, N, K,
+                                     Kp, cols, d, tw, perm, post, inv_n, zonal);
+  else
+    sp::launch_theta_inverse<T>(adj, p->big_col,
+                                sp::Launch{dim3((K + cols - 1) / cols), p->col_threads, p->col_smem, st}, W, N, K,
+                                Kp, cols, d, tw, perm, post, inv_n, zonal);
+}
+template <typename T>
+void launch_rows_inverse_x(sp_plan_t p, bool adj, cudaStream_t st, const cpx<T>* W, double* u, int nt, int n,
+                           int Kp, int rows, const FftDesc& d, const cpx<T>* tw, const int* perm,
+                           const cpx<T>* post, const double* rs, const T* rst, const cpx<double>* zonal) {
+  if (p->pipe[3])
+    sp::launch_rows_inverse_pipe<T>(adj, sp::Launch{dim3(p->pgrid[3]), p->row_threads, p->psmem[3], st}, W, u, nt,
+                                    n, Kp, rows, d, tw, perm, post, rs, rst, zonal);
+  else
+    sp::launch_rows_inverse<T>(adj, p->big_row,
+                               sp::Launch{dim3((nt + rows - 1) / rows), p->row_threads, p->row_smem, st}, W, u, nt,
+                               n, Kp, rows, d, tw, perm, post, rs, rst, zonal);
+}
+
 void enqueue_fp64(sp_plan_t p, bool adj, const double* in, double* out, void* ws, cudaStream_t st) {
   using sp::Launch;
   cpx<double>* W = static_cast<cpx<double>*>(ws);
   StageMarks m{p, st, !p->prof_events.empty() && p->prof_count < p->prof_max};
-  const Launch rows{dim3((p->nt + p->rows_per_cta - 1) / p->rows_per_cta), p->row_threads, p->row_smem, st};
-  const Launch cols{dim3((p->K + p->cols_per_cta - 1) / p->cols_per_cta), p->col_threads, p->col_smem, st};
   const Launch solve{dim3((p->K + 31) / 32, 2), 32, 0, st};
   const double inv_n = 1.0 / (double)p->N;
   m.mark(0);
-  sp::launch_rows_forward<double>(adj, p->big_row, rows, in, W, p->nt, p->nl, p->Kp, p->rows_per_cta,
+  launch_rows_forward_x<double>(p, adj, st, in, W, p->nt, p->nl, p->Kp, p->rows_per_cta,
                                   p->row_fft, p->tw_row, p->perm_row, p->post_row, p->row_scale, p->row_scale,
                                   nullptr);
   m.mark(1);
-  sp::launch_theta_forward<double>(adj, p->big_col, cols, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
+  launch_theta_forward_x<double>(p, adj, st, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
                                    p->tw_col, p->perm_col, adj ? p->post_col : p->post_col_s, inv_n, 1);
   m.mark(2);
   sp::launch_solve<double>(adj, solve, W, p->fac_l, p->fac_iu, p->fac_cu, p->N, p->K, p->Kp);
   m.mark(3);
-  sp::launch_theta_inverse<double>(adj, p->big_col, cols, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
+  launch_theta_inverse_x<double>(p, adj, st, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
                                    p->tw_col, p->perm_col, p->post_col, inv_n, 1);
   m.mark(4);
-  sp::launch_rows_inverse<double>(adj, p->big_row, rows, W, out, p->nt, p->nl, p->Kp, p->rows_per_cta,
+  launch_rows_inverse_x<double>(p, adj, st, W, out, p->nt, p->nl, p->Kp, p->rows_per_cta,
                                   p->row_fft, p->tw_row, p->perm_row, p->post_row, p->row_scale, p->row_scale,
                                   nullptr);
   m.mark(5);
@@ -303,8 +400,6 @@ void enqueue_fp32(sp_plan_t p, bool adj, const double* in, double* out, void* ws
   cpx<float>* W = static_cast<cpx<float>*>(ws);
   cpx<double>* Z = reinterpret_cast<cpx<double>*>(static_cast<char*>(ws) + p->off_z);
   StageMarks m{p, st, !p->prof_events.empty() && p->prof_count < p->prof_max};
-  const Launch rows{dim3((p->nt + p->rows_per_cta - 1) / p->rows_per_cta), p->row_threads, p->row_smem, st};
-  const Launch cols{dim3((p->K + p->cols_per_cta - 1) / p->cols_per_cta), p->col_threads, p->col_smem, st};
   const Launch solve{dim3((p->K + 31) / 32, 2), 32, 0, st};
   const float inv_n = 1.0f / (float)p->N;
   const cpx<float>* twr = static_cast<const cpx<float>*>(p->tw_row_t);
@@ -312,7 +407,7 @@ void enqueue_fp32(sp_plan_t p, bool adj, const double* in, double* out, void* ws
   const cpx<float>* por = static_cast<const cpx<float>*>(p->post_row_t);
   const cpx<float>* poc = static_cast<const cpx<float>*>(p->post_col_t);
   m.mark(0);
-  sp::launch_rows_forward<float>(adj, p->big_row, rows, in, W, p->nt, p->nl, p->Kp, p->rows_per_cta,
+  launch_rows_forward_x<float>(p, adj, st, in, W, p->nt, p->nl, p->Kp, p->rows_per_cta,
                                  p->row_fft, twr, p->perm_row, por, p->row_scale,
                                  static_cast<const float*>(p->row_scale_t), Z);
   cudaEventRecord(p->ev_fork, st);
@@ -320,17 +415,17 @@ void enqueue_fp32(sp_plan_t p, bool adj, const double* in, double* out, void* ws
   enqueue_zonal_fp64(p, adj, Z, p->side);
   cudaEventRecord(p->ev_join, p->side);
   m.mark(1);
-  sp::launch_theta_forward<float>(adj, p->big_col, cols, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
+  launch_theta_forward_x<float>(p, adj, st, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
                                   twc, p->perm_col, adj ? poc : static_cast<const cpx<float>*>(p->post_col_s_t),
                                   inv_n, 0);
   m.mark(2);
   sp::launch_solve<float>(adj, solve, W, p->f32_l, p->f32_iu, p->f32_cu, p->N, p->K, p->Kp);
   m.mark(3);
-  sp::launch_theta_inverse<float>(adj, p->big_col, cols, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
+  launch_theta_inverse_x<float>(p, adj, st, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
                                   twc, p->perm_col, poc, inv_n, 0);
   cudaStreamWaitEvent(st, p->ev_join, 0);
   m.mark(4);
-  sp::launch_rows_inverse<float>(adj, p->big_row, rows, W, out, p->nt, p->nl, p->Kp, p->rows_per_cta,
+  launch_rows_inverse_x<float>(p, adj, st, W, out, p->nt, p->nl, p->Kp, p->rows_per_cta,
                                  p->row_fft, twr, p->perm_row, por, p->row_scale,
                                  static_cast<const float*>(p->row_scale_t), Z);
   m.mark(5);
@@ -346,8 +441,6 @@ void enqueue_refine(sp_plan_t p, const double* in, double* out, void* ws, cudaSt
   cpx<float>* Y = reinterpret_cast<cpx<float>*>(base + p->off_y);
   cpx<double>* Z = reinterpret_cast<cpx<double>*>(base + p->off_z);
   StageMarks m{p, st, !p->prof_events.empty() && p->prof_count < p->prof_max};
-  const Launch rows{dim3((p->nt + p->rows_per_cta - 1) / p->rows_per_cta), p->row_threads, p->row_smem, st};
-  const Launch cols{dim3((p->K + p->cols_per_cta - 1) / p->cols_per_cta), p->col_threads, p->col_smem, st};
   const Launch solve{dim3((p->K + 31) / 32, 2), 32, 0, st};
   const dd inv_n(1.0 / (double)p->N);
   const cpx<dd>* twr = static_cast<const cpx<dd>*>(p->tw_row_t);
@@ -355,11 +448,11 @@ void enqueue_refine(sp_plan_t p, const double* in, double* out, void* ws, cudaSt
   const cpx<dd>* por = static_cast<const cpx<dd>*>(p->post_row_t);
   const cpx<dd>* poc = static_cast<const cpx<dd>*>(p->post_col_t);
   m.mark(0);
-  sp::launch_rows_forward<dd>(false, p->big_row, rows, in, Fd, p->nt, p->nl, p->Kp, p->rows_per_cta,
+  launch_rows_forward_x<dd>(p, false, st, in, Fd, p->nt, p->nl, p->Kp, p->rows_per_cta,
                               p->row_fft, twr, p->perm_row, por, p->row_scale,
                               static_cast<const dd*>(p->row_scale_t), nullptr);
   m.mark(1);
-  sp::launch_theta_forward<dd>(false, p->big_col, cols, Fd, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
+  launch_theta_forward_x<dd>(p, false, st, Fd, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
                                twc, p->perm_col, static_cast<const cpx<dd>*>(p->post_col_s_t), inv_n, 0);
   cudaEventRecord(p->ev_fork, st);
   cudaStreamWaitEvent(p->side, p->ev_fork, 0);
@@ -375,10 +468,10 @@ void enqueue_refine(sp_plan_t p, const double* in, double* out, void* ws, cudaSt
     sp::launch_refine(solve, Fd, Xd, Y, p->f32_l, p->f32_iu, p->f32_cu, p->N, p->K, p->Kp, s == 0 ? 1 : 0);
   cudaStreamWaitEvent(st, p->ev_join, 0);
   m.mark(3);
-  sp::launch_theta_inverse<dd>(false, p->big_col, cols, Xd, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
+  launch_theta_inverse_x<dd>(p, false, st, Xd, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
                                twc, p->perm_col, poc, inv_n, 0);
   m.mark(4);
-  sp::launch_rows_inverse<dd>(false, p->big_row, rows, Xd, out, p->nt, p->nl, p->Kp, p->rows_per_cta,
+  launch_rows_inverse_x<dd>(p, false, st, Xd, out, p->nt, p->nl, p->Kp, p->rows_per_cta,
                               p->row_fft, twr, p->perm_row, por, p->row_scale,
                               static_cast<const dd*>(p->row_scale_t), nullptr);
   m.mark(5);
@@ -695,6 +788,8 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
     step(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming), "cudaEventCreate");
   }
   step(allow_all_smem(p->device), "shared memory attribute");
+  p->pipe_rows = p->pipe_cols = true;
+  step(configure_pipes(p), "pipelined kernels");
   if (rc == SP_OK && (flags & SP_FLAG_AUTOTUNE)) rc = tune_single(p);
   if (rc != SP_OK) {
     destroy_plan(p);
@@ -792,22 +887,27 @@ int tune_single(sp_plan_t p) {
   const std::string key = spaceless(ko.str());
   const char* cache_path = std::getenv("SPHERE_POISSON_TUNE_CACHE");
   const size_t csz = esize(p->precision);
-  auto set_rows = [&](int r, int t) {
+  auto set_rows = [&](int r, int t, bool pipe) {
     p->rows_per_cta = r;
     p->row_threads = t;
     p->row_smem = (size_t)r * p->L * csz;
+    p->pipe_rows = pipe;
+    configure_pipes(p);
   };
-  auto set_cols = [&](int q, int t) {
+  auto set_cols = [&](int q, int t, bool pipe) {
     p->cols_per_cta = q;
     p->col_threads = t;
     p->col_smem = (size_t)q * p->N * csz;
+    p->pipe_cols = pipe;
+    configure_pipes(p);
   };
   {
     auto cache = read_tune_lines(cache_path);
     auto it = cache.find(key);
-    if (it != cache.end() && it->second.size() >= 4) {
-      set_rows((int)it->second[0], (int)it->second[1]);
-      set_cols((int)it->second[2], (int)it->second[3]);
+    if (it != cache.end() && it->second.size() >= 7) {
+      const std::vector<double>& v = it->second;
+      set_rows((int)v[0], (int)v[1], v[4] != 0.0);
+      set_cols((int)v[2], (int)v[3], v[5] != 0.0);
       return SP_OK;
     }
   }
@@ -848,32 +948,40 @@ int tune_single(sp_plan_t p) {
   double best_ms = 1e30;
   if (rc == SP_OK) {
     int br = p->rows_per_cta, bt = p->row_threads;
+    bool bp = p->pipe_rows;
     best_ms = time_solve();
     for (int r = 1; r <= 8 && r <= p->nt; r *= 2)
-      for (int t = 64; t <= cap_r; t *= 2) {
-        if ((size_t)r * p->L * csz > 220 * 1024) continue;
-        set_rows(r, t);
-        const double ms = time_solve();
-        if (ms < best_ms) {
-          best_ms = ms;
-          br = r;
-          bt = t;
+      for (int t = 64; t <= cap_r; t *= 2)
+        for (int pipe = 0; pipe < 2; ++pipe) {
+          if ((size_t)r * p->L * csz > 220 * 1024) continue;
+          set_rows(r, t, pipe != 0);
+          if (pipe && !p->pipe[0] && !p->pipe[3]) continue;   // the pipelined kernels do not fit
+          const double ms = time_solve();
+          if (ms < best_ms) {
+            best_ms = ms;
+            br = r;
+            bt = t;
+            bp = pipe != 0;
+          }
         }
-      }
-    set_rows(br, bt);
+    set_rows(br, bt, bp);
     int bq = p->cols_per_cta, bct = p->col_threads;
+    bool bcp = p->pipe_cols;
     for (int q = 1; q <= 8 && q <= p->Kp; q *= 2)
-      for (int t = 64; t <= cap_c; t *= 2) {
-        if ((size_t)q * p->N * csz > 220 * 1024) continue;
-        set_cols(q, t);
-        const double ms = time_solve();
-        if (ms < best_ms) {
-          best_ms = ms;
-          bq = q;
-          bct = t;
+      for (int t = 64; t <= cap_c; t *= 2)
+        for (int pipe = 0; pipe < 2; ++pipe) {
+          if ((size_t)q * p->N * csz > 220 * 1024) continue;
+          set_cols(q, t, pipe != 0);
+          if (pipe && !p->pipe[1] && !p->pipe[2]) continue;
+          const double ms = time_solve();
+          if (ms < best_ms) {
+            best_ms = ms;
+            bq = q;
+            bct = t;
+            bcp = pipe != 0;
+          }
         }
-      }
-    set_cols(bq, bct);
+    set_cols(bq, bct, bcp);
   }
   if (st) cudaStreamSynchronize(st);
   cudaFree(f);
@@ -885,7 +993,7 @@ int tune_single(sp_plan_t p) {
   if (rc == SP_OK && cache_path && best_ms < 1e29) {
     std::ofstream out(cache_path, std::ios::app);
     out << key << " " << p->rows_per_cta << " " << p->row_threads << " " << p->cols_per_cta << " "
-        << p->col_threads << " " << best_ms << "\n";
+        << p->col_threads << " " << (int)p->pipe_rows << " " << (int)p->pipe_cols << " " << best_ms << "\n";
   }
   return rc;
 }
@@ -1402,13 +1510,11 @@ static int check_transform_plan(sp_plan_t plan, const void* a, const void* b, co
 // forward transforms of f (no sin^2 weight) into W, coefficient sign convention
 static void enqueue_coeffs2(sp_plan_t p, const double* f, cpx<double>* W, int kcols, cudaStream_t st) {
   using sp::Launch;
-  const Launch rows{dim3((p->nt + p->rows_per_cta - 1) / p->rows_per_cta), p->row_threads, p->row_smem, st};
   const int K = kcols;
-  const Launch cols{dim3((K + p->cols_per_cta - 1) / p->cols_per_cta), p->col_threads, p->col_smem, st};
-  sp::launch_rows_forward<double>(false, p->big_row, rows, f, W, p->nt, p->nl, p->Kp, p->rows_per_cta,
+  launch_rows_forward_x<double>(p, false, st, f, W, p->nt, p->nl, p->Kp, p->rows_per_cta,
                                   p->row_fft, p->tw_row, p->perm_row, p->post_row, p->row_plain, p->row_plain,
                                   nullptr);
-  sp::launch_theta_forward<double>(false, p->big_col, cols, W, p->N, K, p->Kp, p->cols_per_cta, p->col_fft,
+  launch_theta_forward_x<double>(p, false, st, W, p->N, K, p->Kp, p->cols_per_cta, p->col_fft,
                                    p->tw_col, p->perm_col, p->post_col_s, 1.0 / p->N, 2);
 }
 
@@ -1432,11 +1538,9 @@ int sphere_poisson_sample(sp_plan_t plan, const void* coeffs, double* f, void* w
   cpx<double>* W = static_cast<cpx<double>*>(workspace);
   cudaError_t e = cudaMemcpyAsync(W, coeffs, (size_t)p->N * p->Kp * sizeof(cpx<double>), cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "sample copy");
-  const Launch rows{dim3((p->nt + p->rows_per_cta - 1) / p->rows_per_cta), p->row_threads, p->row_smem, st};
-  const Launch cols{dim3((p->K + p->cols_per_cta - 1) / p->cols_per_cta), p->col_threads, p->col_smem, st};
-  sp::launch_theta_inverse<double>(false, p->big_col, cols, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
+  launch_theta_inverse_x<double>(p, false, st, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
                                    p->tw_col, p->perm_col, p->post_col, 1.0 / p->N, 2);
-  sp::launch_rows_inverse<double>(false, p->big_row, rows, W, f, p->nt, p->nl, p->Kp, p->rows_per_cta,
+  launch_rows_inverse_x<double>(p, false, st, W, f, p->nt, p->nl, p->Kp, p->rows_per_cta,
                                   p->row_fft, p->tw_row, p->perm_row, p->post_row, p->row_scale, p->row_scale,
                                   nullptr);
   e = cudaGetLastError();
