@@ -39,17 +39,18 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_GFLOPS_FALLBACK = 1008.0
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each FP64
-# stage kernel, from one ncu capture of the 4096 x 8192 workload (inputs 268 MB, larger
+# stage kernel, from one ncu capture of the 5000 x 5000 workload (the colatitude
+# transforms of the 5000 x 10000 grid on half the longitudes; 200 MB input, larger
 # than L2) on the kernel sources whose hash is `csrc_sha256`; see
-# profiles/traffic_fp64_4096x8192.md.  bench.py scales them to its own grid by the
+# profiles/traffic_fp64_5000x5000.md.  bench.py scales them to its own grid by the
 # spectrum size n_theta * Kp (every stage streams the spectrum once or twice) and
 # reports null when the sources have changed since the capture.
 TRAFFIC_CAPTURE = {
-    "csrc_sha256": "ff69b87e3fdb7438",
-    "n_theta": 4096, "n_lambda": 8192,
-    "bytes": {"rows_forward": 268681472 + 223775488, "theta_forward": 269292032 + 210642688,
-              "solve": 901552384 + 457566720, "theta_inverse": 269249536 + 210393088,
-              "rows_inverse": 269476608 + 219835904},
+    "csrc_sha256": "497a4fab8ccb17ef",
+    "n_theta": 5000, "n_lambda": 5000,
+    "bytes": {"rows_forward": 200933632 + 143427072, "theta_forward": 201038848 + 141302272,
+              "solve": 663076352 + 321691648, "theta_inverse": 200885760 + 142209280,
+              "rows_inverse": 200305920 + 144568832},
 }
 
 
@@ -312,7 +313,7 @@ def run_ours(args):
                         f"random SH series l<={w.lmax}, c~N(0,1)/(1+l)^2, seed {w.seed}",
             "dof_per_solve": dof,
             "dof_convention": "n_theta*n_lambda (= mn/2, the paper's); mn convention = 2x",
-            "l2": "inputs (400 MB) larger than L2 (129 MB); no flush",
+            "l2": f"inputs ({f.numel() * 8 / 1e6:.0f} MB) larger than L2 (129 MB); no flush",
             "tiles": "autotuned at plan time" if tune else "default",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
             "max_rel_err_vs_closed_form": err,

@@ -257,6 +257,9 @@ WORKLOADS = {
     "sh200_512x1024_noisy": Workload("sh200_512x1024_noisy", 512, 1024, 200, 1510080945, "inv_sq", 1e-3),
     # the paper-comparable size: mn/2 = 1.03e8 unknowns (its "100 million in a minute")
     "sh2000_7168x14336": Workload("sh2000_7168x14336", 7168, 14336, 2000, 1510080946, "inv_sq"),
+    # half the longitudes of the 5000 x 10000 grid: the same colatitude transforms
+    # (length 5000) on a 200 MB input, the kernel-profiling case
+    "sh2000_5000x5000": Workload("sh2000_5000x5000", 5000, 5000, 2000, 1510080947, "inv_sq"),
 }
 # the batched workload (4096 uneven spheres) is built by batched_workload()
 
