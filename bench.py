@@ -368,6 +368,35 @@ def measure_forms(sp, f, u_exact, u64, N, n, dev, ms_fp64, args):
                     "max_rel_err_vs_closed_form": float((u - u_exact).abs().max()) / ex,
                     "gpu_launches_per_step": plan.launches()}
         del plan, ws
+    # the adjoint (the transposed solve behind autograd): FP64 and FP32, checked by
+    # the dot-product identity <S f, g> = <f, S^T g> with g = the exact solution
+    g = u_exact
+    sg64 = None
+    for prec in ("fp64", "fp32"):
+        plan = sp.Plan(N, n, prec, 0, device=dev, autotune=not args.no_autotune)
+        ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=dev)
+        out = torch.empty_like(f)
+        for _ in range(3):
+            plan.solve_adjoint(g, out, ws)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            plan.solve_adjoint(g, out, ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        sf = plan.solve(f)
+        lhs, rhs = float((sf * g).sum()), float((f * out).sum())
+        entry = {"value": N * n / (ms * 1e-3), "unit": "DOF/s", "ms_per_step": ms,
+                 "dot_product_identity_rel_err": abs(lhs - rhs) / max(abs(lhs), 1e-300),
+                 "gpu_launches_per_step": plan.launches(adjoint=True)}
+        if prec == "fp64":
+            sg64 = out.clone()
+        else:
+            entry["max_rel_err_vs_fp64_adjoint"] = float((out - sg64).abs().max() / sg64.abs().max())
+        res[f"adjoint_{prec}"] = entry
+        del plan, ws, out, sf
     if not args.no_paper_scale:
         res["paper_scale"] = measure_paper_scale(sp, dev, args)
     return res
