@@ -39,8 +39,10 @@ by LAPACK's banded LU (scipy.linalg.solve_banded) otherwise; neither uses the
 parity split or the BMC fold, which are properties the tests check.
 
 Also here: the surface integral sum2 (Section 4, Integration, eq.
-integrationCoeffs) and the transpose (adjoint) of the whole linear map f -> u,
-both matrix-free and as a dense matrix for tiny grids.
+integrationCoeffs), the tangential derivatives of Section 4 (Differentiation,
+eqs. diff_x..diff_z with the division by sin theta through M_sin^{-1}), and the
+transpose (adjoint) of the whole linear map f -> u, both matrix-free and as a
+dense matrix for tiny grids.
 """
 
 from __future__ import annotations
@@ -317,6 +319,54 @@ def sum2(values_on_grid: np.ndarray) -> float:
     col0 = A[:, n // 2]
     val = 2.0 * math.pi * (integration_weights(m) @ col0)
     return float(val.real)
+
+
+# ----------------------------------------------------------------------------
+# Tangential derivatives (Section 4, Differentiation: eqs. diff_x, diff_y,
+# diff_z, dfdx and Msin)
+# ----------------------------------------------------------------------------
+
+def tangential_gradient(f: np.ndarray):
+    """(d^t f/dx, d^t f/dy, d^t f/dz) on the n_theta x n_lambda grid, the
+    Cartesian components of the surface gradient, computed in coefficient space
+    as the paper does:
+        d^t/dx = -(sin lambda / sin theta) d/dlambda + cos lambda cos theta d/dtheta   (eq. diff_x)
+        d^t/dy =  (cos lambda / sin theta) d/dlambda + sin lambda cos theta d/dtheta   (eq. diff_y)
+        d^t/dz = -sin theta d/dtheta
+    on X = coeffs2(ftilde): d/dtheta = D_m from the left, d/dlambda = D_n from
+    the right, cos / sin theta = M_cos / M_sin from the left, cos / sin lambda
+    the same matrices of size n acting on the k index, 1/sin theta = M_sin^{-1}
+    (eq. Msin; M_sin is invertible for even m).
+    Readings: (1) eq. diff_z prints +sin theta d/dtheta; with the colatitude of
+    eq. sphericalCoordinates the chain rule gives e_z . theta_hat = -sin theta,
+    so the sign here is minus (the tangency x g_x + y g_y + z g_z = 0 holds only
+    with it).  (2) The Nyquist modes j = -m/2 and k = -n/2 of X are dropped
+    before the operators act and of each result after, so the truncation is
+    symmetric (as in the solver's reading B); modes the products push beyond the
+    m x n window are discarded."""
+    ft = dfs_double(f)
+    m, n = ft.shape
+    nt = m // 2
+    X = coeffs2(ft)
+    X[0, :] = 0.0
+    X[:, 0] = 0.0
+    Dm, Dn = op_Dm(m), op_Dm(n)
+    Mcos_t, Msin_t = op_Mcos(m), op_Msin(m)
+    Mcos_l, Msin_l = op_Mcos(n), op_Msin(n)
+    dth = Dm @ X                               # d/dtheta
+    dla = X @ Dn                               # d/dlambda
+    q = np.linalg.solve(Msin_t, dla)           # (1/sin theta) d/dlambda
+    c = Mcos_t @ dth                           # cos theta d/dtheta
+    gx = -(q @ Msin_l.T) + c @ Mcos_l.T        # multiplication by sin / cos lambda acts on k
+    gy = q @ Mcos_l.T + c @ Msin_l.T
+    gz = -(Msin_t @ dth)
+    out = []
+    for G in (gx, gy, gz):
+        G = G.copy()
+        G[0, :] = 0.0
+        G[:, 0] = 0.0
+        out.append(sample(G)[nt:].real.copy())
+    return tuple(out)
 
 
 # ----------------------------------------------------------------------------
