@@ -397,9 +397,49 @@ def measure_forms(sp, f, u_exact, u64, N, n, dev, ms_fp64, args):
             entry["max_rel_err_vs_fp64_adjoint"] = float((out - sg64).abs().max() / sg64.abs().max())
         res[f"adjoint_{prec}"] = entry
         del plan, ws, out, sf
+    res["tangential_gradient"] = measure_tangential(sp, f, N, n, dev, steps, args)
     if not args.no_paper_scale:
         res["paper_scale"] = measure_paper_scale(sp, dev, args)
     return res
+
+
+def measure_tangential(sp, f, N, n, dev, steps, args):
+    """The surface gradient (Section 4, Differentiation) of the bench input, timed;
+    accuracy from a polynomial with a closed-form tangential gradient on the same
+    grid (grad f - (r . grad f) r)."""
+    import torch
+    from synth import sh
+
+    plan = sp.Plan(N, n, device=dev, autotune=not args.no_autotune)
+    ws = torch.empty(plan.gradient_workspace_bytes(), dtype=torch.uint8, device=dev)
+    out = tuple(torch.empty_like(f) for _ in range(3))
+    for _ in range(2):
+        plan.tangential_gradient(f, out, ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(3, min(steps, 10))
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        plan.tangential_gradient(f, out, ws)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    th = torch.tensor(sh.colatitudes(N), device=dev)[:, None]
+    la = torch.tensor(sh.longitudes(n), device=dev)[None, :]
+    x, y, z = torch.cos(la) * torch.sin(th), torch.sin(la) * torch.sin(th), torch.cos(th) + 0 * la
+    p = 1 + x + y ** 2 + x ** 2 * y + x ** 4 + y ** 5 + (x * y * z) ** 2
+    px = 1 + 2 * x * y + 4 * x ** 3 + 2 * x * (y * z) ** 2
+    py = 2 * y + x ** 2 + 5 * y ** 4 + 2 * y * (x * z) ** 2
+    pz = 2 * z * (x * y) ** 2
+    rd = x * px + y * py + z * pz
+    g = plan.tangential_gradient(p.contiguous(), out, ws)
+    errs = [float((gi - (pi - rd * ri)).abs().max() / (pi - rd * ri).abs().max())
+            for gi, pi, ri in zip(g, (px, py, pz), (x, y, z))]
+    return {"value": N * n / (ms * 1e-3), "unit": "DOF/s", "ms_per_call": ms,
+            "outputs": "d^t f/dx, d^t f/dy, d^t f/dz on the grid",
+            "max_rel_err_vs_closed_form_xyz": errs,
+            "closed_form_case": "1 + x + y^2 + x^2 y + x^4 + y^5 + (xyz)^2",
+            "gpu_launches_per_call": 2 + 1 + 3 * 3}
 
 
 def measure_paper_scale(sp, dev, args):

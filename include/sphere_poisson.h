@@ -205,6 +205,33 @@ int sphere_poisson_sample(sp_plan_t plan, const void* coeffs, double* f, void* w
 int sphere_poisson_sum2(sp_plan_t plan, const double* f, double* result, void* workspace,
                         size_t workspace_bytes, void* stream);
 
+/*
+ * Tangential derivatives (Section 4, Differentiation; eqs. diff_x, diff_y,
+ * diff_z, dfdx, Msin): the Cartesian components of the surface gradient of f,
+ *   gx = d^t f/dx = -(sin lambda / sin theta) df/dlambda + cos lambda cos theta df/dtheta,
+ *   gy = d^t f/dy =  (cos lambda / sin theta) df/dlambda + sin lambda cos theta df/dtheta,
+ *   gz = d^t f/dz = -sin theta df/dtheta,
+ * computed on the coefficients of coeffs2 (the maps of Section 4: multiplication
+ * by cos / sin of either angle shifts the index by one, d/dtheta and d/dlambda
+ * multiply by ij and ik) with the division by sin theta done as M_sin^{-1}
+ * (eq. Msin) by the recurrence of M_sin x = a run down from the top of the
+ * coefficient window.  The sign of gz is the chain rule's for the colatitude
+ * theta of eq. sphericalCoordinates (the paper prints +sin theta d/dtheta).
+ * The theta- and lambda-Nyquist modes are dropped from f and from the results.
+ * Exact (to rounding) for f band-limited within the grid's window; for other f
+ * the results carry truncation terms of the window.
+ *   f, gx, gy, gz  device, [n_theta][n_lambda] doubles, 16-byte aligned.
+ *   workspace      device, >= sphere_poisson_gradient_workspace_size bytes
+ *                  (three half spectra: 3 n_theta Kp 16 bytes, Kp = n_lambda/2 + 1
+ *                  rounded up to even).
+ * FP64 single plans only (others: SP_ERR_UNSUPPORTED).  Asynchronous on stream;
+ * 12 kernel launches: the two of coeffs2, one for the division, then per component
+ * one coefficient map and the two inverse transforms.
+ */
+int sphere_poisson_gradient_workspace_size(sp_plan_t plan, size_t* workspace_bytes);
+int sphere_poisson_tangential_gradient(sp_plan_t plan, const double* f, double* gx, double* gy, double* gz,
+                                       void* workspace, size_t workspace_bytes, void* stream);
+
 /* Number of kernel launches one solve (adjoint = 1) issues for this plan. */
 int sphere_poisson_launch_count(sp_plan_t plan, int adjoint, int* launches);
 

@@ -169,6 +169,32 @@ class Plan:
                                                  ws.numel(), _stream_ptr(stream)), "sphere_poisson_sum2")
         return float(res[0])
 
+    def gradient_workspace_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        _lib.check(self._lib.sphere_poisson_gradient_workspace_size(self._h, ctypes.byref(n)),
+                   "sphere_poisson_gradient_workspace_size")
+        return int(n.value)
+
+    def tangential_gradient(self, f: torch.Tensor, out=None, workspace=None, stream=None):
+        """(d^t f/dx, d^t f/dy, d^t f/dz) on the grid: the Cartesian components of
+        the surface gradient (Section 4, Differentiation).  out: optional tuple of
+        three float64 CUDA tensors of the grid's shape."""
+        _check_grid(f, self.shape, "f")
+        if out is None:
+            out = tuple(torch.empty_like(f) for _ in range(3))
+        for o in out:
+            _check_grid(o, self.shape, "out")
+        need = self.gradient_workspace_bytes()
+        if workspace is None:
+            workspace = torch.empty(need, dtype=torch.uint8, device=self.device)
+        elif workspace.numel() * workspace.element_size() < need:
+            raise ValueError("workspace too small")
+        _lib.check(self._lib.sphere_poisson_tangential_gradient(
+            self._h, f.data_ptr(), out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(),
+            workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream_ptr(stream)),
+            "sphere_poisson_tangential_gradient")
+        return out
+
     def host_buffer_bytes(self) -> int:
         n = ctypes.c_size_t()
         _lib.check(self._lib.sphere_poisson_host_buffer_size(self._h, ctypes.byref(n)),

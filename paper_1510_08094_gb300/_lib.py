@@ -43,6 +43,8 @@ EXPORTED = (
     "sphere_poisson_coeffs2",
     "sphere_poisson_sample",
     "sphere_poisson_sum2",
+    "sphere_poisson_gradient_workspace_size",
+    "sphere_poisson_tangential_gradient",
     "sphere_poisson_launch_count",
     "sphere_poisson_profile_begin",
     "sphere_poisson_profile_end",
@@ -89,6 +91,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.sphere_poisson_coeffs2.argtypes = [vp, vp, vp, vp, sz, vp]
     lib.sphere_poisson_sample.argtypes = [vp, vp, vp, vp, sz, vp]
     lib.sphere_poisson_sum2.argtypes = [vp, vp, vp, vp, sz, vp]
+    lib.sphere_poisson_gradient_workspace_size.argtypes = [vp, psz]
+    lib.sphere_poisson_tangential_gradient.argtypes = [vp, vp, vp, vp, vp, vp, sz, vp]
     lib.sphere_poisson_launch_count.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int)]
     lib.sphere_poisson_profile_begin.argtypes = [vp, i32]
     lib.sphere_poisson_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32,

@@ -94,6 +94,16 @@ void launch_batched_fp64(bool big, dim3 grid, int threads, size_t smem, cudaStre
 void launch_sum2_finish(cudaStream_t st, const cpx<double>* C, int N, int Kp, double* out) {
   k_sum2_finish<<<1, 256, 0, st>>>(C, N, Kp, out);
 }
+void launch_msin_div(cudaStream_t st, const cpx<double>* X, cpx<double>* Q, int N, int K, int Kp) {
+  const int threads = 128;
+  k_msin_div<<<(2 * Kp + threads - 1) / threads, threads, 0, st>>>(X, Q, N, K, Kp);
+}
+void launch_tangential(cudaStream_t st, const cpx<double>* X, const cpx<double>* Q, cpx<double>* G, int N, int K,
+                       int Kp, int comp) {
+  const int threads = 256;
+  const size_t total = (size_t)N * Kp;
+  k_tangential<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(X, Q, G, N, K, Kp, comp);
+}
 
 SP_INSTANTIATE_PIPE(double);
 

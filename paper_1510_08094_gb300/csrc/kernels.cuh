@@ -1086,6 +1086,100 @@ __global__ void k_sum2_finish(const cpx<double>* __restrict__ C, int N, int Kp, 
     *out = two_pi * (2.0 * C[0].re + 4.0 * t);
   }
 }
+
+// ---------------------------------------------------------------------------
+// Tangential derivatives (Section 4, Differentiation, eqs. diff_x..diff_z and
+// Msin) on the folded coefficients X[j][k] of coeffs2 (the paper's convention:
+// coefficients of e^{ij theta} e^{ik lambda}, j in [0, N), k in [0, L], with
+// X_{-j,k} = (-1)^k X_{j,k}; the lambda-Nyquist column k = L is dropped).
+//
+// Q = (1/sin theta) d/dlambda f in coefficients: M_sin Q = a with a = ik X
+// (eq. Msin: (i/2)(x_{j+1} - x_{j-1}) = a_j), solved by running the
+// recurrence x_{j-1} = x_{j+1} + 2i a_j down from the top of the window with
+// x_N = x_{N-1} = 0, i.e. x_j = 2i sum_{r = j+1, j+3, ... <= N-1} a_r
+// = -2k sum_{r} X_{r,k}.  This is M_sin^{-1} a whenever the quotient lies in the
+// window (band-limited f).  One thread per (column, parity class of j).
+// ---------------------------------------------------------------------------
+__global__ void k_msin_div(const cpx<double>* __restrict__ X, cpx<double>* __restrict__ Q, int N, int K,
+                           int Kp) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 2 * Kp) return;
+  const int cls = idx >= Kp, k = cls ? idx - Kp : idx;
+  int j = N - 1;
+  if ((j & 1) != cls) --j;
+  const double scale = -2.0 * (double)k;
+  cpx<double> S = {0.0, 0.0};
+  const bool live = k < K - 1;                 // k = L (Nyquist) and padding columns are zero
+  for (; j >= 0; j -= 2) {
+    if (live && j + 1 < N) S = S + X[(size_t)(j + 1) * Kp + k];
+    Q[(size_t)j * Kp + k] = live ? scale * S : cpx<double>{0.0, 0.0};
+  }
+}
+
+// X_{i,k} for i in [-1, N] (the BMC mirror at i = -1, zero at i = N and in the
+// Nyquist column)
+__device__ __forceinline__ cpx<double> x_at(const cpx<double>* __restrict__ X, int i, int k, int N, int K,
+                                            int Kp) {
+  const bool mirror = i < 0;
+  if (mirror) i = 1;
+  if (k >= K - 1 || i >= N) return {0.0, 0.0};
+  const cpx<double> v = X[(size_t)i * Kp + k];
+  return (mirror && (k & 1)) ? cpx<double>{-v.re, -v.im} : v;
+}
+// C = cos theta d/dtheta f: C_j = (D_{j-1} + D_{j+1})/2, D_i = i i X_i; columns
+// k = -1 by the real-function symmetry C_{j,-1} = conj(C_{j,1})
+__device__ __forceinline__ cpx<double> c_at(const cpx<double>* __restrict__ X, int j, int k, int N, int K,
+                                            int Kp) {
+  const int kk = k < 0 ? 1 : k;
+  const cpx<double> a = x_at(X, j - 1, kk, N, K, Kp), b = x_at(X, j + 1, kk, N, K, Kp);
+  const double wa = 0.5 * (double)(j - 1), wb = 0.5 * (double)(j + 1);
+  // i (wa a + wb b), conjugated for k = -1
+  const cpx<double> t = {wa * a.re + wb * b.re, wa * a.im + wb * b.im};
+  return k < 0 ? cpx<double>{-t.im, -t.re} : cpx<double>{-t.im, t.re};
+}
+__device__ __forceinline__ cpx<double> q_at(const cpx<double>* __restrict__ Q, int j, int k, int K, int Kp) {
+  if (k >= K - 1) return {0.0, 0.0};
+  if (k < 0) {
+    cpx<double> v = Q[(size_t)j * Kp + 1];
+    return {v.re, -v.im};
+  }
+  return Q[(size_t)j * Kp + k];
+}
+
+// Coefficients of one Cartesian component of the surface gradient:
+//   comp 0: d^t/dx = -sin(lambda) Q + cos(lambda) C
+//   comp 1: d^t/dy =  cos(lambda) Q + sin(lambda) C
+//   comp 2: d^t/dz = -sin(theta) d/dtheta f, G_j = ((j+1) X_{j+1} - (j-1) X_{j-1})/2
+//           (the chain-rule sign for the colatitude theta)
+// with cos(lambda) g -> (g_{k-1} + g_{k+1})/2, sin(lambda) g -> (i/2)(g_{k+1} - g_{k-1}).
+// One thread per (j, k); the Nyquist and padding columns are written as zero.
+__global__ void k_tangential(const cpx<double>* __restrict__ X, const cpx<double>* __restrict__ Q,
+                             cpx<double>* __restrict__ G, int N, int K, int Kp, int comp) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)N * Kp) return;
+  const int j = (int)(idx / Kp), k = (int)(idx - (size_t)j * Kp);
+  cpx<double> g = {0.0, 0.0};
+  if (k < K - 1) {
+    if (comp == 2) {
+      const cpx<double> a = x_at(X, j + 1, k, N, K, Kp), b = x_at(X, j - 1, k, N, K, Kp);
+      const double wa = 0.5 * (double)(j + 1), wb = 0.5 * (double)(j - 1);
+      g = {wa * a.re - wb * b.re, wa * a.im - wb * b.im};
+    } else {
+      const cpx<double> qp = q_at(Q, j, k + 1, K, Kp), qm = q_at(Q, j, k - 1, K, Kp);
+      const cpx<double> cp = c_at(X, j, k + 1, N, K, Kp), cm = c_at(X, j, k - 1, N, K, Kp);
+      if (comp == 0) {
+        // -(i/2)(qp - qm) + (cp + cm)/2
+        const cpx<double> d = qp - qm;
+        g = {0.5 * (d.im + cp.re + cm.re), 0.5 * (-d.re + cp.im + cm.im)};
+      } else {
+        // (qp + qm)/2 + (i/2)(cp - cm)
+        const cpx<double> d = cp - cm;
+        g = {0.5 * (qp.re + qm.re - d.im), 0.5 * (qp.im + qm.im + d.re)};
+      }
+    }
+  }
+  G[idx] = g;
+}
 #endif  // SP_FP64_KERNELS
 
 // exact product of two floats holding integers, as double-float (TwoProduct)

@@ -85,6 +85,11 @@ void launch_batched_refine(bool big, dim3 grid, int threads, size_t smem, cudaSt
 
 // surface integral from the k = 0 coefficient column (one CTA, result to device memory)
 void launch_sum2_finish(cudaStream_t st, const cpx<double>* C, int N, int Kp, double* out);
+// tangential derivatives: Q = (1/sin theta) d/dlambda in coefficients, then the
+// coefficients of one gradient component (0 x, 1 y, 2 z) into G
+void launch_msin_div(cudaStream_t st, const cpx<double>* X, cpx<double>* Q, int N, int K, int Kp);
+void launch_tangential(cudaStream_t st, const cpx<double>* X, const cpx<double>* Q, cpx<double>* G, int N, int K,
+                       int Kp, int comp);
 
 void launch_refine(const Launch& l, const cpx<dd>* F, cpx<dd>* X, cpx<float>* Y, const float* fl,
                    const float* fiu, const float* fcu, int N, int K, int Kp, int first);

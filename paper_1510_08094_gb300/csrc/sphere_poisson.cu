@@ -1559,6 +1559,45 @@ int sphere_poisson_sum2(sp_plan_t plan, const double* f, double* result, void* w
   return e == cudaSuccess ? SP_OK : cuda_fail(e, "sum2 launch");
 }
 
+int sphere_poisson_gradient_workspace_size(sp_plan_t plan, size_t* workspace_bytes) {
+  if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
+  if (!workspace_bytes) return SP_ERR_NULL;
+  if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
+  const size_t one = ((size_t)plan->N * plan->Kp * sizeof(cpx<double>) + 255) & ~(size_t)255;
+  *workspace_bytes = 3 * one;
+  return SP_OK;
+}
+
+int sphere_poisson_tangential_gradient(sp_plan_t plan, const double* f, double* gx, double* gy, double* gz,
+                                       void* workspace, size_t workspace_bytes, void* stream) {
+  if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
+  if (!f || !gx || !gy || !gz || !workspace) return SP_ERR_NULL;
+  if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
+  if (((uintptr_t)f | (uintptr_t)gx | (uintptr_t)gy | (uintptr_t)gz | (uintptr_t)workspace) & 15)
+    return SP_ERR_MISALIGNED;
+  size_t need = 0;
+  sphere_poisson_gradient_workspace_size(plan, &need);
+  if (workspace_bytes < need) return SP_ERR_WORKSPACE;
+  sp_plan_t p = plan;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t one = need / 3;
+  cpx<double>* X = static_cast<cpx<double>*>(workspace);
+  cpx<double>* Q = reinterpret_cast<cpx<double>*>(static_cast<char*>(workspace) + one);
+  cpx<double>* G = reinterpret_cast<cpx<double>*>(static_cast<char*>(workspace) + 2 * one);
+  enqueue_coeffs2(p, f, X, p->K, st);
+  sp::launch_msin_div(st, X, Q, p->N, p->K, p->Kp);
+  double* out[3] = {gx, gy, gz};
+  for (int c = 0; c < 3; ++c) {
+    sp::launch_tangential(st, X, Q, G, p->N, p->K, p->Kp, c);
+    launch_theta_inverse_x<double>(p, false, st, G, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft, p->tw_col,
+                                   p->perm_col, p->post_col, 1.0 / p->N, 2);
+    launch_rows_inverse_x<double>(p, false, st, G, out[c], p->nt, p->nl, p->Kp, p->rows_per_cta, p->row_fft,
+                                  p->tw_row, p->perm_row, p->post_row, p->row_scale, p->row_scale, nullptr);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SP_OK : cuda_fail(e, "tangential gradient launch");
+}
+
 int sphere_poisson_launch_count(sp_plan_t plan, int adjoint, int* launches) {
   if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
   if (!launches) return SP_ERR_NULL;
