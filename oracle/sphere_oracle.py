@@ -38,7 +38,8 @@ The per-k systems are solved by dense LU (numpy.linalg.solve) at small m and
 by LAPACK's banded LU (scipy.linalg.solve_banded) otherwise; neither uses the
 parity split or the BMC fold, which are properties the tests check.
 
-Also here: the surface integral sum2 (Section 4, Integration, eq.
+Also here: the structure-preserving GE of Section 3 and the low-rank form of
+the coefficients F, the surface integral sum2 (Section 4, Integration, eq.
 integrationCoeffs), the tangential derivatives of Section 4 (Differentiation,
 eqs. diff_x..diff_z with the division by sin theta through M_sin^{-1}), and the
 transpose (adjoint) of the whole linear map f -> u, both matrix-free and as a
@@ -319,6 +320,95 @@ def sum2(values_on_grid: np.ndarray) -> float:
     col0 = A[:, n // 2]
     val = 2.0 * math.pi * (integration_weights(m) @ col0)
     return float(val.real)
+
+
+# ----------------------------------------------------------------------------
+# Structure-preserving Gaussian elimination and low-rank coefficients
+# (Section 3, Figure GaussianElimination; Section 4, eq. 2DFourierExpansion)
+# ----------------------------------------------------------------------------
+
+def pivot_pinv(a: float, b: float, alpha: float = 0.01) -> np.ndarray:
+    """The epsilon-pseudoinverse (Definition pseudoinverse) of the centrosymmetric
+    pivot matrix M = [[a, b], [b, a]] (eq. pivotMatrix) with eps = alpha sigma_1(M):
+    M has the eigenvectors (1, 1)/sqrt2 and (1, -1)/sqrt2 with eigenvalues a + b
+    and a - b, so sigma_{1,2} = max / min(|a + b|, |a - b|) (eq. SingularValues)
+    and the pseudoinverse keeps the eigenpairs with |eigenvalue| > eps."""
+    sig1 = max(abs(a + b), abs(a - b))
+    eps = alpha * sig1
+    P = np.zeros((2, 2))
+    for lam, v in ((a + b, np.array([1.0, 1.0])), (a - b, np.array([1.0, -1.0]))):
+        if abs(lam) > eps:
+            P += np.outer(v, v) / (2.0 * lam)
+    return P
+
+
+def bmc_ge(ft: np.ndarray, alpha: float = 0.01, rtol: float = 1e-13, max_terms: int = 512):
+    """Structure-preserving GE on the samples ft (m x n, the DFS grid) of a BMC
+    function (Section 3, Figure GaussianElimination).  Step k: pick the grid
+    point (lambda*, theta*) in [0, pi) x (0, pi) whose pivot matrix
+    M = [[e(lambda* - pi, theta*), e(lambda*, theta*)], [e(lambda*, theta*),
+    e(lambda* - pi, theta*)]] has the largest sigma_1 (the 2 x 2 analogue of
+    complete pivoting, over the whole grid), then
+        e <- e - [e(lambda* - pi, .)  e(lambda*, .)] M^{dagger_eps} [e(., theta*); e(., -theta*)]
+    (eq. GEstructurePreservingStepPseudoinverse) with eps = alpha sigma_1(M),
+    alpha = 1/100 as the paper chooses.
+    Readings: the pivot search runs over the full sample grid (the paper's
+    coarse-grid search is a speed device); the iteration stops when
+    max |e| <= rtol max |ft| (rtol = 1e-13: "machine precision relative to the
+    maximum" for a residual whose rounding floor is tens of eps), when the
+    residual, already below 1e-9 max |ft|, stops decreasing for three steps
+    (the rounding floor), or after max_terms steps.  The
+    pole zero-out of eq. ZeroOut (for BMC-I structure) is not applied: the
+    sample grid has no pole points.
+    Returns (terms, residual); each term is (cols m x 2, P 2 x 2, rows 2 x n,
+    (p, q)) with ft ~= sum cols @ P @ rows, p, q the pivot's row and column."""
+    ft = np.asarray(ft, dtype=np.float64)
+    m, n = ft.shape
+    N, H = m // 2, n // 2
+    e = ft.copy()
+    scale = float(np.abs(ft).max())
+    terms = []
+    best, stall = np.inf, 0
+    for _ in range(max_terms):
+        r = float(np.abs(e).max())
+        if r <= rtol * scale:
+            break
+        if r < best:
+            best, stall = r, 0
+        elif r < 1e-9 * scale:                        # at the rounding floor
+            stall += 1
+            if stall >= 3:
+                break
+        a = np.roll(e, H, axis=1)                     # a[p, q] = e[p, q - n/2]
+        s1 = np.maximum(np.abs(a + e), np.abs(a - e))[N:, H:]
+        i, j = np.unravel_index(int(np.argmax(s1)), s1.shape)
+        p, q = N + int(i), H + int(j)
+        P = pivot_pinv(float(e[p, q - H]), float(e[p, q]), alpha)
+        cols = e[:, [q - H, q]].copy()
+        rows = e[[p, m - 1 - p], :].copy()
+        e = e - cols @ P @ rows
+        terms.append((cols, P, rows, (p, q)))
+    return terms, e
+
+
+def lowrank_values(terms) -> np.ndarray:
+    """sum of cols @ P @ rows: the low-rank approximant on the DFS grid."""
+    return sum(c @ P @ r for c, P, r, _ in terms)
+
+
+def lowrank_rhs_coefficients(terms, m: int, n: int) -> np.ndarray:
+    """F of the Poisson solve (the 2D Fourier coefficients of sin^2(theta) ftilde)
+    from the low-rank factors by 1D transforms only (Section 4, low-rank form of
+    eq. 2DFourierExpansion): F = sum_t [DFT_theta(sin^2 c_t)] P_t [DFT_lambda(r_t)]^T,
+    with the naive DFTs of coeffs2 in each variable."""
+    s2 = np.sin(dfs_theta(m)) ** 2
+    Et, El = _phase_theta(m), _phase_lambda(n)
+    F = np.zeros((m, n), dtype=complex)
+    for c, P, r, _ in terms:
+        Ch = (Et @ (s2[:, None] * c)) / m            # m x 2
+        Rh = (El @ r.T) / n                          # n x 2
+        F += Ch @ P @ Rh.T
+    return F
 
 
 # ----------------------------------------------------------------------------
