@@ -398,9 +398,49 @@ def measure_forms(sp, f, u_exact, u64, N, n, dev, ms_fp64, args):
         res[f"adjoint_{prec}"] = entry
         del plan, ws, out, sf
     res["tangential_gradient"] = measure_tangential(sp, f, N, n, dev, steps, args)
+    res["lowrank"] = measure_lowrank(sp, N, n, dev, steps, ms_fp64, args)
     if not args.no_paper_scale:
         res["paper_scale"] = measure_paper_scale(sp, dev, args)
     return res
+
+
+def measure_lowrank(sp, N, n, dev, steps, ms_fp64, args):
+    """The low-rank form on the paper's Section 5 right-hand side sin(50 xyz) at
+    the bench grid: the structure-preserving GE (timed once, it synchronises per
+    step) and the solve from the factors, against the dense FP64 solve of the
+    same f."""
+    import torch
+    from synth import sh
+
+    th = torch.tensor(sh.colatitudes(N), device=dev)[:, None]
+    la = torch.tensor(sh.longitudes(n), device=dev)[None, :]
+    f = torch.sin(50 * (torch.cos(la) * torch.sin(th)) * (torch.sin(la) * torch.sin(th)) * torch.cos(th))
+    f = f.contiguous()
+    plan = sp.Plan(N, n, device=dev, autotune=not args.no_autotune)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cols, piv, rows = plan.lowrank_ge(f, max_terms=min(256, N))
+    t_ge = time.perf_counter() - t0
+    rank = sum(int(abs(a + b) > 0) + int(abs(a - b) > 0) for a, b in piv.cpu().tolist())
+    u = torch.empty_like(f)
+    for _ in range(2):
+        plan.solve_lowrank(cols, piv, rows, u)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(3, min(steps, 10))
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        plan.solve_lowrank(cols, piv, rows, u)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ud = plan.solve(f)
+    return {"value": N * n / (ms * 1e-3), "unit": "DOF/s", "ms_per_solve": ms,
+            "case": "f = sin(50 xyz) (the paper's Section 5 example) on the bench grid",
+            "ge_terms": int(cols.shape[0]), "rank": rank, "ge_seconds": t_ge,
+            "speedup_vs_dense_fp64_solve": ms_fp64 / ms,
+            "max_rel_err_vs_dense_fp64_solve": float((u - ud).abs().max() / ud.abs().max()),
+            "gpu_launches_per_solve": 3 + 1 + 3}
 
 
 def measure_tangential(sp, f, N, n, dev, steps, args):

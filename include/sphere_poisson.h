@@ -232,6 +232,43 @@ int sphere_poisson_gradient_workspace_size(sp_plan_t plan, size_t* workspace_byt
 int sphere_poisson_tangential_gradient(sp_plan_t plan, const double* f, double* gx, double* gy, double* gz,
                                        void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * Low-rank form (Section 3, Figure GaussianElimination; Section 4, low-rank
+ * form of eq. 2DFourierExpansion).  A term t is
+ *   [c_t(theta) c_t(-theta)] [[P00, P01], [P01, P00]] [r_t(lambda); r_t(lambda + pi)]
+ * with c_t sampled on the full DFS colatitude grid theta_p = -pi + (p + 1/2) pi / n_theta,
+ * p < m = 2 n_theta (cols[t][p]), r_t on the longitudes (rows[t][q], q < n_lambda) and
+ * the centrosymmetric pivot pseudoinverse in piv[t][0..1]; such terms are BMC
+ * (eq. BMCsphere), so their sum is a function on the sphere.
+ *
+ * sphere_poisson_lowrank_ge: the structure-preserving GE of f (device [n_theta][n_lambda]):
+ *   step k takes the grid point (lambda*, theta*) in [0, pi) x (0, pi) whose pivot
+ *   matrix [[e(lambda* - pi, theta*), e(lambda*, theta*)], [e(lambda*, theta*), e(lambda* - pi, theta*)]]
+ *   has the largest sigma_1 (eq. SingularValues; the smallest grid index among
+ *   ties), its epsilon-pseudoinverse with eps = alpha sigma_1 (Definition
+ *   pseudoinverse; the paper uses alpha = 1/100), and subtracts the term
+ *   (eq. GEstructurePreservingStepPseudoinverse).  Stops when max |e| <= rtol max |f|,
+ *   when the residual, below 1e-9 max |f|, has not decreased for three steps, or
+ *   after max_terms (0..n_theta) steps; *terms receives the count.  cols, rows,
+ *   piv: device arrays of max_terms x m, max_terms x n_lambda, max_terms x 2 doubles.
+ *   Synchronous: the host reads each step's pivot.
+ * sphere_poisson_solve_lowrank: u = S f for f = the sum of `terms` terms, with the
+ *   right-hand side F formed from the factors (one colatitude transform per term
+ *   column, one longitude transform per term row, one outer-product kernel)
+ *   instead of the 2D transform of f; then the eliminations and inverse
+ *   transforms of sphere_poisson_solve.  u device [n_theta][n_lambda].
+ * Workspace of either call: sphere_poisson_lowrank_workspace_size(plan, max_terms).
+ * FP64 single plans only (others SP_ERR_UNSUPPORTED); terms and max_terms
+ * at most n_theta (SP_ERR_BAD_ARG).
+ */
+int sphere_poisson_lowrank_workspace_size(sp_plan_t plan, int max_terms, size_t* workspace_bytes);
+int sphere_poisson_lowrank_ge(sp_plan_t plan, const double* f, int max_terms, double rtol, double alpha,
+                              int* terms, double* cols, double* piv, double* rows, void* workspace,
+                              size_t workspace_bytes, void* stream);
+int sphere_poisson_solve_lowrank(sp_plan_t plan, int terms, const double* cols, const double* piv,
+                                 const double* rows, double* u, void* workspace, size_t workspace_bytes,
+                                 void* stream);
+
 /* Number of kernel launches one solve (adjoint = 1) issues for this plan. */
 int sphere_poisson_launch_count(sp_plan_t plan, int adjoint, int* launches);
 

@@ -195,6 +195,49 @@ class Plan:
             "sphere_poisson_tangential_gradient")
         return out
 
+    def lowrank_workspace_bytes(self, max_terms: int) -> int:
+        n = ctypes.c_size_t()
+        _lib.check(self._lib.sphere_poisson_lowrank_workspace_size(self._h, int(max_terms), ctypes.byref(n)),
+                   "sphere_poisson_lowrank_workspace_size")
+        return int(n.value)
+
+    def lowrank_ge(self, f: torch.Tensor, max_terms: int | None = None, rtol: float = 1e-13,
+                   alpha: float = 0.01, stream=None):
+        """Structure-preserving GE of f (Section 3): (cols [T, 2 n_theta], piv [T, 2],
+        rows [T, n_lambda]) with f ~= sum_t [c_t(theta) c_t(-theta)] P_t [r_t(lambda); r_t(lambda+pi)]."""
+        _check_grid(f, self.shape, "f")
+        T = self.n_theta if max_terms is None else int(max_terms)
+        m, n = 2 * self.n_theta, self.n_lambda
+        cols = torch.empty(max(T, 1), m, dtype=torch.float64, device=self.device)
+        rows = torch.empty(max(T, 1), n, dtype=torch.float64, device=self.device)
+        piv = torch.empty(max(T, 1), 2, dtype=torch.float64, device=self.device)
+        ws = torch.empty(self.lowrank_workspace_bytes(T), dtype=torch.uint8, device=self.device)
+        count = ctypes.c_int()
+        _lib.check(self._lib.sphere_poisson_lowrank_ge(self._h, f.data_ptr(), T, float(rtol), float(alpha),
+                                                       ctypes.byref(count), cols.data_ptr(), piv.data_ptr(),
+                                                       rows.data_ptr(), ws.data_ptr(), ws.numel(),
+                                                       _stream_ptr(stream)), "sphere_poisson_lowrank_ge")
+        k = int(count.value)
+        return cols[:k], piv[:k], rows[:k]
+
+    def solve_lowrank(self, cols: torch.Tensor, piv: torch.Tensor, rows: torch.Tensor, out=None, stream=None):
+        """u = S f for f the sum of the low-rank terms (right-hand side formed from the factors)."""
+        T = int(cols.shape[0])
+        m, n = 2 * self.n_theta, self.n_lambda
+        for t, shape in ((cols, (T, m)), (piv, (T, 2)), (rows, (T, n))):
+            if t.dtype != torch.float64 or not t.is_cuda or tuple(t.shape) != shape:
+                raise ValueError("cols, piv, rows must be float64 CUDA tensors [T, 2 n_theta], [T, 2], [T, n_lambda]")
+        cols, piv, rows = cols.contiguous(), piv.contiguous(), rows.contiguous()
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        _check_grid(out, self.shape, "out")
+        ws = torch.empty(self.lowrank_workspace_bytes(T), dtype=torch.uint8, device=self.device)
+        _lib.check(self._lib.sphere_poisson_solve_lowrank(self._h, T, cols.data_ptr(), piv.data_ptr(),
+                                                          rows.data_ptr(), out.data_ptr(), ws.data_ptr(),
+                                                          ws.numel(), _stream_ptr(stream)),
+                   "sphere_poisson_solve_lowrank")
+        return out
+
     def host_buffer_bytes(self) -> int:
         n = ctypes.c_size_t()
         _lib.check(self._lib.sphere_poisson_host_buffer_size(self._h, ctypes.byref(n)),

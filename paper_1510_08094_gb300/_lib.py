@@ -45,6 +45,9 @@ EXPORTED = (
     "sphere_poisson_sum2",
     "sphere_poisson_gradient_workspace_size",
     "sphere_poisson_tangential_gradient",
+    "sphere_poisson_lowrank_workspace_size",
+    "sphere_poisson_lowrank_ge",
+    "sphere_poisson_solve_lowrank",
     "sphere_poisson_launch_count",
     "sphere_poisson_profile_begin",
     "sphere_poisson_profile_end",
@@ -93,6 +96,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.sphere_poisson_sum2.argtypes = [vp, vp, vp, vp, sz, vp]
     lib.sphere_poisson_gradient_workspace_size.argtypes = [vp, psz]
     lib.sphere_poisson_tangential_gradient.argtypes = [vp, vp, vp, vp, vp, vp, sz, vp]
+    lib.sphere_poisson_lowrank_workspace_size.argtypes = [vp, i32, psz]
+    lib.sphere_poisson_lowrank_ge.argtypes = [vp, vp, i32, ctypes.c_double, ctypes.c_double,
+                                              ctypes.POINTER(ctypes.c_int), vp, vp, vp, vp, sz, vp]
+    lib.sphere_poisson_solve_lowrank.argtypes = [vp, i32, vp, vp, vp, vp, vp, sz, vp]
     lib.sphere_poisson_launch_count.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int)]
     lib.sphere_poisson_profile_begin.argtypes = [vp, i32]
     lib.sphere_poisson_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32,

@@ -56,4 +56,13 @@ struct BatchArgs {
   int sweeps;                          // refinement sweeps (FP32 + refinement plans)
 };
 
+// Pivot record of one step of the structure-preserving GE (written by the
+// pivot-search kernels, read by the host).
+struct GePivot {
+  double best;      // largest sigma_1(M) = max(|a + b|, |a - b|) over the search region
+  double a, b;      // the pivot's a = e(lambda* - pi, theta*), b = e(lambda*, theta*)
+  double maxabs;    // max |e| over the half grid
+  long long index;  // i * (n/2) + (q - n/2) of the pivot (smallest index among ties)
+};
+
 }  // namespace sp

@@ -1,5 +1,6 @@
 // FP64 transform and elimination kernels (and the FP64 zonal side path of the FP32 forms).
 #define SP_FP64_KERNELS
+#include <algorithm>
 #include "launchers.inl"
 #include "batched.cuh"
 
@@ -103,6 +104,28 @@ void launch_tangential(cudaStream_t st, const cpx<double>* X, const cpx<double>*
   const int threads = 256;
   const size_t total = (size_t)N * Kp;
   k_tangential<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(X, Q, G, N, K, Kp, comp);
+}
+
+void launch_ge_pivot(cudaStream_t st, const double* e, int nt, int n, GePivot* part, int nparts, GePivot* out) {
+  k_ge_pivot_partial<<<nparts, 256, 0, st>>>(e, nt, n, part);
+  k_ge_pivot_final<<<1, 1, 0, st>>>(e, n, part, nparts, out);
+}
+void launch_ge_step(cudaStream_t st, double* e, int nt, int n, int istar, int qstar, double* col, double* row,
+                    double p0, double p1, size_t total) {
+  const int threads = 256;
+  const int ext = std::max(2 * nt, n);
+  k_ge_extract<<<(ext + threads - 1) / threads, threads, 0, st>>>(e, nt, n, istar, qstar, col, row);
+  k_ge_update<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(e, nt, n, col, row, p0, p1);
+}
+void launch_lowrank_pack(cudaStream_t st, const double* cols, int terms, int nt, const double* sin2, cpx<double>* Wc) {
+  const int threads = 256, total = nt * terms;
+  k_lowrank_pack<<<(total + threads - 1) / threads, threads, 0, st>>>(cols, terms, nt, sin2, Wc);
+}
+void launch_lowrank_outer(cudaStream_t st, const cpx<double>* Wc, const cpx<double>* R, const double* piv,
+                          int terms, int N, int K, int Kp, cpx<double>* F) {
+  const int threads = 256;
+  const size_t total = (size_t)N * Kp;
+  k_lowrank_outer<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(Wc, R, piv, terms, N, K, Kp, F);
 }
 
 SP_INSTANTIATE_PIPE(double);

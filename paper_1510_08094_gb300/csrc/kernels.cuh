@@ -20,6 +20,7 @@
 
 #include <type_traits>
 
+#include "batch_types.h"
 #include "fft.cuh"
 
 namespace sp {
@@ -1179,6 +1180,151 @@ __global__ void k_tangential(const cpx<double>* __restrict__ X, const cpx<double
     }
   }
   G[idx] = g;
+}
+
+// ---------------------------------------------------------------------------
+// Structure-preserving GE (Section 3, Figure GaussianElimination) on the
+// residual e[i][q] of the theta > 0 half of the DFS grid (the residual stays
+// BMC, so the other half is e(lambda, -theta) = e(lambda + pi, theta)).
+// A term t is a column c_t(theta_p) = e(lambda* - pi, theta_p) on the full DFS
+// grid (m = 2 n_theta samples), a row r_t(lambda_q) = e(lambda_q, theta*) and
+// the entries (P00, P01) of the centrosymmetric epsilon-pseudoinverse of the
+// pivot matrix; the term is [c(theta) c(-theta)] P [r(lambda); r(lambda + pi)].
+// ---------------------------------------------------------------------------
+// (the pivot record GePivot is declared with the batched-plan types)
+// per-block partial maxima over the search region theta_i > 0 (all i),
+// lambda_q in [0, pi) (q >= n/2) and max |e| over all entries
+__global__ void k_ge_pivot_partial(const double* __restrict__ e, int nt, int n, GePivot* __restrict__ part) {
+  const int H = n >> 1;
+  const long long total = (long long)nt * H;
+  double best = -1.0, mx = 0.0;
+  long long bi = 0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / H), qq = (int)(t - (long long)i * H);
+    const double a = e[(size_t)i * n + qq], b = e[(size_t)i * n + qq + H];
+    const double s1 = fmax(fabs(a + b), fabs(a - b));
+    if (s1 > best) {
+      best = s1;
+      bi = t;
+    }
+    mx = fmax(mx, fmax(fabs(a), fabs(b)));
+  }
+  __shared__ double sb[32], sm[32];
+  __shared__ long long si[32];
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ob = __shfl_down_sync(0xffffffffu, best, off);
+    const long long oi = __shfl_down_sync(0xffffffffu, bi, off);
+    if (ob > best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
+    }
+    mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sb[threadIdx.x >> 5] = best;
+    si[threadIdx.x >> 5] = bi;
+    sm[threadIdx.x >> 5] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      if (sb[w] > best || (sb[w] == best && si[w] < bi)) {
+        best = sb[w];
+        bi = si[w];
+      }
+      mx = fmax(mx, sm[w]);
+    }
+    part[blockIdx.x] = GePivot{best, 0.0, 0.0, mx, bi};
+  }
+}
+
+// one thread: reduce the partials, read the pivot's a and b
+__global__ void k_ge_pivot_final(const double* __restrict__ e, int n, const GePivot* __restrict__ part, int nparts,
+                                 GePivot* __restrict__ out) {
+  GePivot r = part[0];
+  for (int w = 1; w < nparts; ++w) {
+    const GePivot& o = part[w];
+    if (o.best > r.best || (o.best == r.best && o.index < r.index)) {
+      r.best = o.best;
+      r.index = o.index;
+    }
+    r.maxabs = fmax(r.maxabs, o.maxabs);
+  }
+  const int H = n >> 1;
+  const int i = (int)(r.index / H), qq = (int)(r.index - (long long)i * H);
+  r.a = e[(size_t)i * n + qq];
+  r.b = e[(size_t)i * n + qq + H];
+  *out = r;
+}
+
+// copy the term's column (full DFS grid, m = 2 nt) and row out of the residual:
+// c(theta_p) = e(lambda* - pi, theta_p): for p >= nt, e[p - nt][q* - n/2]; for
+// p < nt (theta_p = -theta_{nt-1-p}), e(lambda*, theta_{nt-1-p}) = e[nt-1-p][q*]
+__global__ void k_ge_extract(const double* __restrict__ e, int nt, int n, int istar, int qstar,
+                             double* __restrict__ col, double* __restrict__ row) {
+  const int H = n >> 1;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < 2 * nt) {
+    const int p = t;
+    col[p] = p >= nt ? e[(size_t)(p - nt) * n + (qstar - H)] : e[(size_t)(nt - 1 - p) * n + qstar];
+  }
+  if (t < n) row[t] = e[(size_t)istar * n + t];
+}
+
+// e[i][q] -= c(theta_i) (p0 r(lambda_q) + p1 r(lambda_q + pi)) + c(-theta_i) (p1 r(lambda_q) + p0 r(lambda_q + pi))
+__global__ void k_ge_update(double* __restrict__ e, int nt, int n, const double* __restrict__ col,
+                            const double* __restrict__ row, double p0, double p1) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)nt * n) return;
+  const int i = (int)(idx / n), q = (int)(idx - (size_t)i * n);
+  const int H = n >> 1;
+  const double cp = col[nt + i], cm = col[nt - 1 - i];
+  const double r0 = row[q], r1 = row[q < H ? q + H : q - H];
+  e[idx] -= cp * fma(p0, r0, p1 * r1) + cm * fma(p1, r0, p0 * r1);
+}
+
+// ---------------------------------------------------------------------------
+// Low-rank right-hand side: F = coefficients of sin^2(theta) f~ from the terms.
+// With the column's symmetric and antisymmetric parts s_t, a_t (coefficients
+// S_t, A_t from theta_forward) and the row's longitude coefficients R_t, the
+// term [c(theta) c(-theta)] P [r(lambda); r(lambda + pi)] has coefficients
+//   F_jk = 2 (P00 + P01) S_t,j R_t,k (k even),  2 (P00 - P01) A_t,j R_t,k (k odd)
+// since c(-theta) has coefficients S - A and r(lambda + pi) has (-1)^k R.
+// ---------------------------------------------------------------------------
+// packed columns for theta_forward: Wc[i][2t] = sin^2(theta_i) (c(theta_i) + c(-theta_i))/2,
+// Wc[i][2t+1] = sin^2(theta_i) (c(theta_i) - c(-theta_i))/2  (Kc = 2 * terms columns)
+__global__ void k_lowrank_pack(const double* __restrict__ cols, int terms, int nt, const double* __restrict__ sin2,
+                               cpx<double>* __restrict__ Wc) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nt * terms) return;
+  const int i = idx / terms, t = idx - i * terms;
+  const double* c = cols + (size_t)t * 2 * nt;
+  const double cp = c[nt + i], cm = c[nt - 1 - i], w = 0.5 * sin2[i];
+  Wc[(size_t)i * 2 * terms + 2 * t] = {w * (cp + cm), 0.0};
+  Wc[(size_t)i * 2 * terms + 2 * t + 1] = {w * (cp - cm), 0.0};
+}
+
+// F[j][k] = sum_t Z_t,j R[t][k] with Z = 2(P00 + P01) S (k even), 2(P00 - P01) A (k odd);
+// one thread per (j, k), k >= K written as zero
+__global__ void k_lowrank_outer(const cpx<double>* __restrict__ Wc, const cpx<double>* __restrict__ R,
+                                const double* __restrict__ piv, int terms, int N, int K, int Kp,
+                                cpx<double>* __restrict__ F) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)N * Kp) return;
+  const int j = (int)(idx / Kp), k = (int)(idx - (size_t)j * Kp);
+  cpx<double> acc = {0.0, 0.0};
+  if (k < K) {
+    const int odd = k & 1;
+    const cpx<double>* z = Wc + (size_t)j * 2 * terms + odd;
+    for (int t = 0; t < terms; ++t) {
+      const double w = 2.0 * (odd ? __ldg(piv + 2 * t) - __ldg(piv + 2 * t + 1)
+                                  : __ldg(piv + 2 * t) + __ldg(piv + 2 * t + 1));
+      const cpx<double> zt = ldg_c(z + 2 * t), rt = R[(size_t)t * Kp + k];
+      const cpx<double> wz = {w * zt.re, w * zt.im};
+      acc = {fma(wz.re, rt.re, fma(-wz.im, rt.im, acc.re)), fma(wz.re, rt.im, fma(wz.im, rt.re, acc.im))};
+    }
+  }
+  F[idx] = acc;
 }
 #endif  // SP_FP64_KERNELS
 

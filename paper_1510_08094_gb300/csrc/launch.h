@@ -91,6 +91,16 @@ void launch_msin_div(cudaStream_t st, const cpx<double>* X, cpx<double>* Q, int 
 void launch_tangential(cudaStream_t st, const cpx<double>* X, const cpx<double>* Q, cpx<double>* G, int N, int K,
                        int Kp, int comp);
 
+// structure-preserving GE: pivot search (partials + final into *out) and one
+// step (extract the term's column and row, update the residual)
+void launch_ge_pivot(cudaStream_t st, const double* e, int nt, int n, GePivot* part, int nparts, GePivot* out);
+void launch_ge_step(cudaStream_t st, double* e, int nt, int n, int istar, int qstar, double* col, double* row,
+                    double p0, double p1, size_t total);
+// low-rank right-hand side: pack the terms' columns for theta_forward, then F
+void launch_lowrank_pack(cudaStream_t st, const double* cols, int terms, int nt, const double* sin2, cpx<double>* Wc);
+void launch_lowrank_outer(cudaStream_t st, const cpx<double>* Wc, const cpx<double>* R, const double* piv,
+                          int terms, int N, int K, int Kp, cpx<double>* F);
+
 void launch_refine(const Launch& l, const cpx<dd>* F, cpx<dd>* X, cpx<float>* Y, const float* fl,
                    const float* fiu, const float* fcu, int N, int K, int Kp, int first);
 void launch_zonal_extract(const Launch& l, const cpx<dd>* Wdd, cpx<double>* Z, int N, int Kp);

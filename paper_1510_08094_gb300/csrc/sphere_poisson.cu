@@ -191,6 +191,7 @@ struct sp_plan_s {
   int* perm_col;         // digit reversal of the length-N passes
   double* row_scale;     // sin^2(theta_i)/n
   double* row_plain;     // 1/n (transforms without the sin^2 weight)
+  double* sin2;          // sin^2(theta_i) (the low-rank right-hand side)
   void* row_scale_t;     // the same in float (SP_FP32) or double-float (SP_FP32_REFINE)
   // the same tables in float (SP_FP32) or double-float (SP_FP32_REFINE)
   void* tw_row_t;
@@ -696,6 +697,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   size_t o_post_col_s = take((p->N + 1) * cd_sz);
   size_t o_scale = take(p->nt * sizeof(double));
   size_t o_plain = take(p->nt * sizeof(double));
+  size_t o_sin2 = take(p->nt * sizeof(double));
   size_t o_perm_row = take(p->L * sizeof(int)), o_perm_col = take(p->N * sizeof(int));
   size_t o_t_tw_row = take(t_tw_row.size()), o_t_tw_col = take(t_tw_col.size());
   size_t o_t_post_row = take(t_post_row.size()), o_t_post_col = take(t_post_col.size());
@@ -728,6 +730,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   p->post_col_s = reinterpret_cast<cpx<double>*>(base + o_post_col_s);
   p->row_scale = reinterpret_cast<double*>(base + o_scale);
   p->row_plain = reinterpret_cast<double*>(base + o_plain);
+  p->sin2 = reinterpret_cast<double*>(base + o_sin2);
   p->perm_row = reinterpret_cast<int*>(base + o_perm_row);
   p->perm_col = reinterpret_cast<int*>(base + o_perm_col);
   p->tw_row_t = base + o_t_tw_row;
@@ -760,6 +763,13 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   {
     std::vector<double> plain(p->nt, 1.0 / (double)n_lambda);
     up(p->row_plain, plain.data(), p->nt * sizeof(double), "copy row_plain");
+    std::vector<double> s2(p->nt);
+    for (int i = 0; i < p->nt; ++i) {
+      double re, im;
+      unit_root(2 * i + 1, 4L * p->N, &re, &im);  // sin(theta_i) = -im
+      s2[i] = im * im;
+    }
+    up(p->sin2, s2.data(), p->nt * sizeof(double), "copy sin2");
   }
   up(p->perm_row, perm_row.data(), p->L * sizeof(int), "copy perm_row");
   up(p->perm_col, perm_col.data(), p->N * sizeof(int), "copy perm_col");
@@ -1596,6 +1606,123 @@ int sphere_poisson_tangential_gradient(sp_plan_t plan, const double* f, double* 
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SP_OK : cuda_fail(e, "tangential gradient launch");
+}
+
+namespace {
+constexpr int kGeParts = 608;  // partial-maximum blocks of the pivot search (4 per SM)
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+}  // namespace
+
+int sphere_poisson_lowrank_workspace_size(sp_plan_t plan, int max_terms, size_t* workspace_bytes) {
+  if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
+  if (!workspace_bytes) return SP_ERR_NULL;
+  if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
+  if (max_terms < 0 || max_terms > plan->nt) return SP_ERR_BAD_ARG;
+  const size_t ge = al256((size_t)plan->nt * plan->nl * sizeof(double)) + al256(kGeParts * sizeof(sp::GePivot)) +
+                    al256(sizeof(sp::GePivot));
+  const size_t sv = al256((size_t)plan->N * plan->Kp * sizeof(cpx<double>)) +
+                    al256((size_t)plan->N * 2 * std::max(max_terms, 1) * sizeof(cpx<double>)) +
+                    al256((size_t)std::max(max_terms, 1) * plan->Kp * sizeof(cpx<double>));
+  *workspace_bytes = std::max(ge, sv);
+  return SP_OK;
+}
+
+int sphere_poisson_lowrank_ge(sp_plan_t plan, const double* f, int max_terms, double rtol, double alpha,
+                              int* terms, double* cols, double* piv, double* rows, void* workspace,
+                              size_t workspace_bytes, void* stream) {
+  if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
+  if (!f || !terms || !workspace || (max_terms > 0 && (!cols || !piv || !rows))) return SP_ERR_NULL;
+  if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
+  if (max_terms < 0 || max_terms > plan->nt || !(rtol >= 0.0) || !(alpha >= 0.0) || alpha > 1.0)
+    return SP_ERR_BAD_ARG;
+  if (((uintptr_t)f | (uintptr_t)workspace) & 15) return SP_ERR_MISALIGNED;
+  size_t need = 0;
+  sphere_poisson_lowrank_workspace_size(plan, max_terms, &need);
+  if (workspace_bytes < need) return SP_ERR_WORKSPACE;
+  const int nt = plan->nt, n = plan->nl, H = n / 2, m = 2 * nt;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(workspace);
+  double* e = reinterpret_cast<double*>(base);
+  sp::GePivot* part = reinterpret_cast<sp::GePivot*>(base + al256((size_t)nt * n * sizeof(double)));
+  sp::GePivot* pv = reinterpret_cast<sp::GePivot*>(reinterpret_cast<char*>(part) + al256(kGeParts * sizeof(sp::GePivot)));
+  *terms = 0;
+  cudaError_t err = cudaMemcpyAsync(e, f, (size_t)nt * n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (err != cudaSuccess) return cuda_fail(err, "lowrank_ge copy");
+  std::vector<double> hpiv;
+  double scale = 0.0, best = 1e300;
+  int stall = 0, count = 0;
+  const size_t total = (size_t)nt * n;
+  for (int t = 0; t < max_terms; ++t) {
+    sp::launch_ge_pivot(st, e, nt, n, part, kGeParts, pv);
+    sp::GePivot hp;
+    err = cudaMemcpyAsync(&hp, pv, sizeof hp, cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess) return cuda_fail(err, "lowrank_ge pivot");
+    if (t == 0) scale = hp.maxabs;
+    const double r = hp.maxabs;
+    if (r <= rtol * scale) break;
+    if (r < best) {
+      best = r;
+      stall = 0;
+    } else if (r < 1e-9 * scale && ++stall >= 3) {
+      break;  // the residual has reached its rounding floor
+    }
+    const int istar = (int)(hp.index / H), qstar = H + (int)(hp.index % H);
+    // epsilon-pseudoinverse of [[a, b], [b, a]]: eigenvalues a + b ((1,1)/sqrt2), a - b ((1,-1)/sqrt2)
+    const double l1 = hp.a + hp.b, l2 = hp.a - hp.b;
+    const double eps = alpha * std::max(std::fabs(l1), std::fabs(l2));
+    const double h1 = std::fabs(l1) > eps ? 0.5 / l1 : 0.0, h2 = std::fabs(l2) > eps ? 0.5 / l2 : 0.0;
+    const double p0 = h1 + h2, p1 = h1 - h2;
+    double* col = cols + (size_t)t * m;
+    double* row = rows + (size_t)t * n;
+    sp::launch_ge_step(st, e, nt, n, istar, qstar, col, row, p0, p1, total);
+    hpiv.push_back(p0);
+    hpiv.push_back(p1);
+    ++count;
+  }
+  if (count) err = cudaMemcpyAsync(piv, hpiv.data(), hpiv.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+  if (err == cudaSuccess) err = cudaGetLastError();
+  if (err != cudaSuccess) return cuda_fail(err, "lowrank_ge");
+  *terms = count;
+  return SP_OK;
+}
+
+int sphere_poisson_solve_lowrank(sp_plan_t plan, int terms, const double* cols, const double* piv,
+                                 const double* rows, double* u, void* workspace, size_t workspace_bytes,
+                                 void* stream) {
+  if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
+  if (!u || !workspace || (terms > 0 && (!cols || !piv || !rows))) return SP_ERR_NULL;
+  if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
+  if (terms < 0 || terms > plan->nt) return SP_ERR_BAD_ARG;
+  if (((uintptr_t)u | (uintptr_t)workspace | (uintptr_t)cols | (uintptr_t)rows) & 15) return SP_ERR_MISALIGNED;
+  size_t need = 0;
+  sphere_poisson_lowrank_workspace_size(plan, terms, &need);
+  if (workspace_bytes < need) return SP_ERR_WORKSPACE;
+  sp_plan_t p = plan;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(workspace);
+  cpx<double>* W = reinterpret_cast<cpx<double>*>(base);
+  cpx<double>* Wc = reinterpret_cast<cpx<double>*>(base + al256((size_t)p->N * p->Kp * sizeof(cpx<double>)));
+  cpx<double>* R = reinterpret_cast<cpx<double>*>(reinterpret_cast<char*>(Wc) +
+                                                  al256((size_t)p->N * 2 * std::max(terms, 1) * sizeof(cpx<double>)));
+  const double inv_n = 1.0 / (double)p->N;
+  if (terms > 0) {
+    sp::launch_lowrank_pack(st, cols, terms, p->nt, p->sin2, Wc);
+    launch_theta_forward_x<double>(p, false, st, Wc, p->N, 2 * terms, 2 * terms, p->cols_per_cta, p->col_fft,
+                                   p->tw_col, p->perm_col, p->post_col_s, inv_n, 1);
+    launch_rows_forward_x<double>(p, false, st, rows, R, terms, p->nl, p->Kp, p->rows_per_cta, p->row_fft,
+                                  p->tw_row, p->perm_row, p->post_row, p->row_plain, p->row_plain, nullptr);
+  }
+  sp::launch_lowrank_outer(st, Wc, R, piv, terms, p->N, p->K, p->Kp, W);
+  const sp::Launch solve{dim3((p->K + 31) / 32, 2), 32, 0, st};
+  sp::launch_solve<double>(false, solve, W, p->fac_l, p->fac_iu, p->fac_cu, p->N, p->K, p->Kp);
+  launch_theta_inverse_x<double>(p, false, st, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft, p->tw_col,
+                                 p->perm_col, p->post_col, inv_n, 1);
+  launch_rows_inverse_x<double>(p, false, st, W, u, p->nt, p->nl, p->Kp, p->rows_per_cta, p->row_fft,
+                                p->tw_row, p->perm_row, p->post_row, p->row_scale, p->row_scale, nullptr);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SP_OK : cuda_fail(e, "solve_lowrank launch");
 }
 
 int sphere_poisson_launch_count(sp_plan_t plan, int adjoint, int* launches) {
