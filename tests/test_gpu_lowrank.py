@@ -105,7 +105,7 @@ def test_lowrank_solve_at_full_size(sp):
     f = torch.sin(50 * x * y * z).contiguous()            # the paper's Section 5 example
     plan = sp.Plan(nt, nl)
     cols, piv, rows = plan.lowrank_ge(f, max_terms=128)
-    assert cols.shape[0] < 128
+    assert _rank(piv) == 12                                  # the paper: numerical rank 12
     u_low = plan.solve_lowrank(cols, piv, rows)
     u = plan.solve(f)
     assert float((u_low - u).abs().max() / u.abs().max()) < 1e-12

@@ -5,7 +5,8 @@ Pinned against: numpy's SVD-based pseudoinverse with the same cut (the
 epsilon-pseudoinverse of Definition pseudoinverse), the SVD numerical rank of
 the sample matrix (Theorem BMCrankDrop: exact recovery of finite-rank BMC
 functions after as many terms as their rank; spherical harmonics are rank 1),
-the paper's printed rank 23 of eq. sphereTestFunc (tests/golden), the BMC
+the paper's printed ranks 23 of eq. sphereTestFunc and 12 of sin(50 xyz)
+(tests/golden), the BMC
 symmetry of every GE residual, and the dense coefficients of the same function.
 """
 
@@ -18,6 +19,13 @@ from oracle import sphere_oracle as O
 from synth import sh
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "sphere_test_func_rank.txt")
+GOLDEN_SIN50 = os.path.join(os.path.dirname(__file__), "golden", "sin50xyz_rank.txt")
+
+
+def _golden_rank(path):
+    vals = {k.strip(): v.strip() for k, v in (l.split("=", 1) for l in open(path).read().splitlines()
+                                              if "=" in l and not l.startswith("#"))}
+    return int(vals["rank"])
 
 
 def _xyz(nt, nl):
@@ -90,6 +98,19 @@ def test_paper_test_function_rank():
     total = sum(_rank(P) for _, P, _, _ in terms)
     assert rank <= total <= rank + 2                                # GE is near-optimal
     assert float(np.abs(e).max()) < 1e-13
+
+
+@pytest.mark.parametrize("nt,nl", [(75, 150), (128, 256)])
+def test_paper_poisson_example_rank(nt, nl):
+    # the paper's m = n = 150 grid and a finer one
+    rank = _golden_rank(GOLDEN_SIN50)
+    x, y, z = _xyz(nt, nl)
+    ft = O.dfs_double(np.sin(50 * x * y * z))
+    terms, e = O.bmc_ge(ft)
+    assert sum(_rank(P) for _, P, _, _ in terms) == rank
+    assert float(np.abs(e).max()) < 1e-13
+    sv = np.linalg.svd(ft, compute_uv=False)
+    assert int((sv > 1e-14 * sv[0]).sum()) == rank
 
 
 def test_lowrank_coefficients_equal_the_dense_ones():
