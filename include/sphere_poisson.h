@@ -259,7 +259,7 @@ int sphere_poisson_tangential_gradient(sp_plan_t plan, const double* f, double* 
  *   transforms of sphere_poisson_solve.  u device [n_theta][n_lambda].
  * Workspace of either call: sphere_poisson_lowrank_workspace_size(plan, max_terms).
  * FP64 single plans only (others SP_ERR_UNSUPPORTED); terms and max_terms
- * at most n_theta (SP_ERR_BAD_ARG).
+ * at most min(n_theta, 1024) (SP_ERR_BAD_ARG).
  */
 int sphere_poisson_lowrank_workspace_size(sp_plan_t plan, int max_terms, size_t* workspace_bytes);
 int sphere_poisson_lowrank_ge(sp_plan_t plan, const double* f, int max_terms, double rtol, double alpha,

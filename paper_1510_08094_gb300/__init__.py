@@ -206,7 +206,7 @@ class Plan:
         """Structure-preserving GE of f (Section 3): (cols [T, 2 n_theta], piv [T, 2],
         rows [T, n_lambda]) with f ~= sum_t [c_t(theta) c_t(-theta)] P_t [r_t(lambda); r_t(lambda+pi)]."""
         _check_grid(f, self.shape, "f")
-        T = self.n_theta if max_terms is None else int(max_terms)
+        T = min(self.n_theta, 1024) if max_terms is None else int(max_terms)
         m, n = 2 * self.n_theta, self.n_lambda
         cols = torch.empty(max(T, 1), m, dtype=torch.float64, device=self.device)
         rows = torch.empty(max(T, 1), n, dtype=torch.float64, device=self.device)

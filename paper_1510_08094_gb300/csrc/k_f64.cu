@@ -121,11 +121,12 @@ void launch_lowrank_pack(cudaStream_t st, const double* cols, int terms, int nt,
   const int threads = 256, total = nt * terms;
   k_lowrank_pack<<<(total + threads - 1) / threads, threads, 0, st>>>(cols, terms, nt, sin2, Wc);
 }
-void launch_lowrank_outer(cudaStream_t st, const cpx<double>* Wc, const cpx<double>* R, const double* piv,
+void launch_lowrank_outer(cudaStream_t st, cpx<double>* Wc, const cpx<double>* R, const double* piv,
                           int terms, int N, int K, int Kp, cpx<double>* F) {
   const int threads = 256;
-  const size_t total = (size_t)N * Kp;
-  k_lowrank_outer<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(Wc, R, piv, terms, N, K, Kp, F);
+  if (terms > 0) k_lowrank_weights<<<(N * terms + threads - 1) / threads, threads, 0, st>>>(Wc, piv, terms, N);
+  const dim3 grid((Kp + threads - 1) / threads, N);
+  k_lowrank_outer<<<grid, threads, (size_t)2 * terms * sizeof(cpx<double>), st>>>(Wc, R, terms, K, Kp, F);
 }
 
 SP_INSTANTIATE_PIPE(double);

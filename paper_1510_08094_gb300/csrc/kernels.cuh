@@ -1304,27 +1304,39 @@ __global__ void k_lowrank_pack(const double* __restrict__ cols, int terms, int n
   Wc[(size_t)i * 2 * terms + 2 * t + 1] = {w * (cp - cm), 0.0};
 }
 
-// F[j][k] = sum_t Z_t,j R[t][k] with Z = 2(P00 + P01) S (k even), 2(P00 - P01) A (k odd);
-// one thread per (j, k), k >= K written as zero
-__global__ void k_lowrank_outer(const cpx<double>* __restrict__ Wc, const cpx<double>* __restrict__ R,
-                                const double* __restrict__ piv, int terms, int N, int K, int Kp,
-                                cpx<double>* __restrict__ F) {
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (size_t)N * Kp) return;
-  const int j = (int)(idx / Kp), k = (int)(idx - (size_t)j * Kp);
+// fold the pivot weights into the packed coefficients, in place:
+// Wc[j][2t] = 2(P00 + P01) S_t,j, Wc[j][2t+1] = 2(P00 - P01) A_t,j
+__global__ void k_lowrank_weights(cpx<double>* __restrict__ Wc, const double* __restrict__ piv, int terms, int N) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N * terms) return;
+  const int j = idx / terms, t = idx - j * terms;
+  const double p0 = piv[2 * t], p1 = piv[2 * t + 1];
+  const double we = 2.0 * (p0 + p1), wo = 2.0 * (p0 - p1);
+  cpx<double>* z = Wc + (size_t)j * 2 * terms + 2 * t;
+  z[0] = we * z[0];
+  z[1] = wo * z[1];
+}
+
+// F[j][k] = sum_t Wc[j][2t + (k & 1)] R[t][k]: one CTA per row j (its 2 * terms
+// weighted coefficients in shared memory), one thread per k; k >= K written as zero
+__global__ void k_lowrank_outer(const cpx<double>* __restrict__ Wc, const cpx<double>* __restrict__ R, int terms,
+                                int K, int Kp, cpx<double>* __restrict__ F) {
+  extern __shared__ cpx<double> zrow[];
+  const int j = blockIdx.y;
+  for (int s = threadIdx.x; s < 2 * terms; s += blockDim.x) zrow[s] = Wc[(size_t)j * 2 * terms + s];
+  __syncthreads();
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= Kp) return;
   cpx<double> acc = {0.0, 0.0};
   if (k < K) {
-    const int odd = k & 1;
-    const cpx<double>* z = Wc + (size_t)j * 2 * terms + odd;
+    const cpx<double>* z = zrow + (k & 1);
+#pragma unroll 4
     for (int t = 0; t < terms; ++t) {
-      const double w = 2.0 * (odd ? __ldg(piv + 2 * t) - __ldg(piv + 2 * t + 1)
-                                  : __ldg(piv + 2 * t) + __ldg(piv + 2 * t + 1));
-      const cpx<double> zt = ldg_c(z + 2 * t), rt = R[(size_t)t * Kp + k];
-      const cpx<double> wz = {w * zt.re, w * zt.im};
-      acc = {fma(wz.re, rt.re, fma(-wz.im, rt.im, acc.re)), fma(wz.re, rt.im, fma(wz.im, rt.re, acc.im))};
+      const cpx<double> zt = z[2 * t], rt = R[(size_t)t * Kp + k];
+      acc = {fma(zt.re, rt.re, fma(-zt.im, rt.im, acc.re)), fma(zt.re, rt.im, fma(zt.im, rt.re, acc.im))};
     }
   }
-  F[idx] = acc;
+  F[(size_t)j * Kp + k] = acc;
 }
 #endif  // SP_FP64_KERNELS
 

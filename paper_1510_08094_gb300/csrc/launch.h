@@ -98,7 +98,8 @@ void launch_ge_step(cudaStream_t st, double* e, int nt, int n, int istar, int qs
                     double p0, double p1, size_t total);
 // low-rank right-hand side: pack the terms' columns for theta_forward, then F
 void launch_lowrank_pack(cudaStream_t st, const double* cols, int terms, int nt, const double* sin2, cpx<double>* Wc);
-void launch_lowrank_outer(cudaStream_t st, const cpx<double>* Wc, const cpx<double>* R, const double* piv,
+// (scales Wc in place by the pivot weights first)
+void launch_lowrank_outer(cudaStream_t st, cpx<double>* Wc, const cpx<double>* R, const double* piv,
                           int terms, int N, int K, int Kp, cpx<double>* F);
 
 void launch_refine(const Launch& l, const cpx<dd>* F, cpx<dd>* X, cpx<float>* Y, const float* fl,

@@ -1610,6 +1610,7 @@ int sphere_poisson_tangential_gradient(sp_plan_t plan, const double* f, double* 
 
 namespace {
 constexpr int kGeParts = 608;  // partial-maximum blocks of the pivot search (4 per SM)
+constexpr int kMaxTerms = 1024;  // low-rank terms (the outer product keeps 2 x terms coefficients in shared memory)
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 }  // namespace
 
@@ -1617,7 +1618,7 @@ int sphere_poisson_lowrank_workspace_size(sp_plan_t plan, int max_terms, size_t*
   if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
   if (!workspace_bytes) return SP_ERR_NULL;
   if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
-  if (max_terms < 0 || max_terms > plan->nt) return SP_ERR_BAD_ARG;
+  if (max_terms < 0 || max_terms > std::min(plan->nt, kMaxTerms)) return SP_ERR_BAD_ARG;
   const size_t ge = al256((size_t)plan->nt * plan->nl * sizeof(double)) + al256(kGeParts * sizeof(sp::GePivot)) +
                     al256(sizeof(sp::GePivot));
   const size_t sv = al256((size_t)plan->N * plan->Kp * sizeof(cpx<double>)) +
@@ -1633,7 +1634,7 @@ int sphere_poisson_lowrank_ge(sp_plan_t plan, const double* f, int max_terms, do
   if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
   if (!f || !terms || !workspace || (max_terms > 0 && (!cols || !piv || !rows))) return SP_ERR_NULL;
   if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
-  if (max_terms < 0 || max_terms > plan->nt || !(rtol >= 0.0) || !(alpha >= 0.0) || alpha > 1.0)
+  if (max_terms < 0 || max_terms > std::min(plan->nt, kMaxTerms) || !(rtol >= 0.0) || !(alpha >= 0.0) || alpha > 1.0)
     return SP_ERR_BAD_ARG;
   if (((uintptr_t)f | (uintptr_t)workspace) & 15) return SP_ERR_MISALIGNED;
   size_t need = 0;
@@ -1694,7 +1695,7 @@ int sphere_poisson_solve_lowrank(sp_plan_t plan, int terms, const double* cols, 
   if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
   if (!u || !workspace || (terms > 0 && (!cols || !piv || !rows))) return SP_ERR_NULL;
   if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
-  if (terms < 0 || terms > plan->nt) return SP_ERR_BAD_ARG;
+  if (terms < 0 || terms > std::min(plan->nt, kMaxTerms)) return SP_ERR_BAD_ARG;
   if (((uintptr_t)u | (uintptr_t)workspace | (uintptr_t)cols | (uintptr_t)rows) & 15) return SP_ERR_MISALIGNED;
   size_t need = 0;
   sphere_poisson_lowrank_workspace_size(plan, terms, &need);
