@@ -238,20 +238,23 @@ __device__ __forceinline__ void rows_forward_finish(int row0, cpx<T>* __restrict
    const int row = row0 + r;
    if (row >= nt) break;
    const T hrs = ADJ ? (T)1 : (T)0.5 * row_scale_t[row];   // half the row scale
-   for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
-    cpx<T> out = {(T)0, (T)0};
-    if (k < K) {
-      const cpx<T>* Z = sm + r * L;
-      cpx<T> zk = Z[k == L ? 0 : k];
-      cpx<T> zc = conj(Z[k == 0 ? 0 : L - k]);
-      cpx<T> e = ldg_c(post + k);                 // exp(-2 pi i k / n)
-      cpx<T> A = zk + zc, D = zk - zc;
-      // G = scale/2 * (A - i e D)
-      const T hs = ADJ ? ((k == 0 || k == L) ? (T)0.5 : (T)1) : hrs;
-      out = {hs * fma(e.re, D.im, fma(e.im, D.re, A.re)), hs * fma(-e.re, D.re, fma(e.im, D.im, A.im))};
-    }
-    W[(size_t)row * Kp + k] = out;
+   cpx<T>* Wr = W + (size_t)row * Kp;
+   const cpx<T>* Z = sm + r * L;
+   // outputs k and L - k together: with A = Z_k + conj(Z_{L-k}), D = Z_k - conj(Z_{L-k})
+   // and e = exp(-2 pi i k/n), G_k = s (A - i e D) and, since the pair's A, D are
+   // conj(A), -conj(D) and its e is -conj(e), G_{L-k} = s conj(A + i e D)
+   for (int k = threadIdx.x; k <= L / 2; k += blockDim.x) {
+      const cpx<T> zk = Z[k];
+      const cpx<T> zc = conj(Z[k == 0 ? 0 : L - k]);
+      const cpx<T> e = ldg_c(post + k);           // exp(-2 pi i k / n)
+      const cpx<T> A = zk + zc, D = zk - zc;
+      const T x1 = fma(e.re, D.im, e.im * D.re), x2 = fma(e.re, D.re, -(e.im * D.im));   // e D = x2 + i x1
+      const T hs = ADJ ? (k == 0 ? (T)0.5 : (T)1) : hrs;
+      Wr[k] = {hs * (A.re + x1), hs * (A.im - x2)};
+      const int kk = L - k;
+      if (kk != k) Wr[kk] = {hs * (A.re - x1), -(hs * (A.im + x2))};
    }
+   for (int k = K + threadIdx.x; k < Kp; k += blockDim.x) Wr[k] = {(T)0, (T)0};
   }
 }
 
@@ -329,14 +332,19 @@ template <typename T, bool ADJ, typename Src>
 __device__ __forceinline__ void rows_inverse_load(int row0, cpx<T>* __restrict__ sm, const Src& src, int nt,
     int n, int rows, const int* __restrict__ perm, const cpx<T>* __restrict__ post, bool zonal) {
   const int L = n >> 1;
+  // inputs k and L - k together: with A = U_k + conj(U_{L-k}), D = U_k - conj(U_{L-k})
+  // and e = exp(-2 pi i k/n), Z_k = A + i conj(e) D and, since the pair's A, D
+  // are conj(A), -conj(D) and its e is -conj(e), Z_{L-k} = conj(A) + i e conj(D)
+  // (k = 0 pairs with the Nyquist bin U_L and has no partner)
   for (int r = 0; r < rows; ++r)
 #pragma unroll 2
-  for (int k = threadIdx.x; k < L; k += blockDim.x) {
+  for (int k = threadIdx.x; k <= L / 2; k += blockDim.x) {
     const int row = row0 + r;
-    cpx<T> z = {(T)0, (T)0};
+    const int kk = L - k;
+    cpx<T> z = {(T)0, (T)0}, zp = {(T)0, (T)0};
     if (row < nt) {
       cpx<T> uk = src(r, k);
-      cpx<T> up = src(r, L - k);                 // k = 0 pairs with the Nyquist bin
+      cpx<T> up = src(r, kk);
       if (k == 0) {
         uk.im = (T)0;
         up.im = (T)0;
@@ -345,12 +353,15 @@ __device__ __forceinline__ void rows_inverse_load(int row0, cpx<T>* __restrict__
         uk = (T)0.5 * uk;
         up = (T)0.5 * up;
       }
-      cpx<T> uc = conj(up);
-      cpx<T> e = ldg_c(post + k);                // conj(e) = exp(+2 pi i k / n)
-      cpx<T> A = uk + uc, D = uk - uc;           // Z = A + i conj(e) D
-      z = {fma(-e.re, D.im, fma(e.im, D.re, A.re)), fma(e.re, D.re, fma(e.im, D.im, A.im))};
+      const cpx<T> uc = conj(up);
+      const cpx<T> e = ldg_c(post + k);          // conj(e) = exp(+2 pi i k / n)
+      const cpx<T> A = uk + uc, D = uk - uc;
+      const T x1 = fma(e.re, D.im, -(e.im * D.re)), x2 = fma(e.re, D.re, e.im * D.im);
+      z = {A.re - x1, A.im + x2};
+      zp = {A.re + x1, x2 - A.im};
     }
     sm[r * L + __ldg(perm + k)] = z;
+    if (k != 0 && kk != k) sm[r * L + __ldg(perm + kk)] = zp;
   }
 }
 
@@ -479,42 +490,47 @@ __device__ __forceinline__ void theta_forward_finish(int k0, cpx<T>* __restrict_
     const cpx<T>* __restrict__ post, int zonal) {
   const int cs = __ffs(cols) - 1;
   fft_run<-1, BIG>(sm, cols, d, tw);
-  for (int idx = threadIdx.x; idx < N * cols; idx += blockDim.x) {
-    int j = idx >> cs, c = idx & (cols - 1);
-    int k = k0 + c;
+  // P_j = w_j V_j + conj(w_j) V_{N-j} (the forward passes the table w/(2N), the
+  // adjoint w itself) for the pair j, N - j at once: with S = V_j + V_{N-j},
+  // D = V_j - V_{N-j} and w_{N-j} = -i conj(w_j),
+  //   P_j = (w.re S.re - w.im D.im, w.re S.im + w.im D.re),
+  //   P_{N-j} = (-w.im S.re - w.re D.im, -w.im S.im + w.re D.re).
+  // k even: F_j = P_j; k odd: F_j = -i P_{N-j} (F_0 = 0).
+  const int H = N / 2 + 1;
+  for (int idx = threadIdx.x; idx < H * cols; idx += blockDim.x) {
+    const int j = idx >> cs, c = idx & (cols - 1);
+    const int k = k0 + c;
     if (k >= K) continue;
     const cpx<T>* V = sm + c * N;
-    // p = w a + conj(w) b, with a = V_j, b = V_{N-j} (k even) or a = V_{N-j}, b = V_j
-    // (k odd); the forward passes the table w/(2N), the adjoint w itself
-    cpx<T> out;
+    const int jj = N - j;                      // partner output (none for j = 0, or jj = j)
+    const bool pair = j > 0 && jj != j;
+    const cpx<T> w = ldg_c(post + j);
+    const cpx<T> a = V[j], b = V[j == 0 ? 0 : jj];
+    const cpx<T> S = a + b, D = a - b;
+    const cpx<T> pj = {fma(w.re, S.re, -(w.im * D.im)), fma(w.re, S.im, w.im * D.re)};
+    const cpx<T> pjj = {fma(-w.im, S.re, -(w.re * D.im)), fma(-w.im, S.im, w.re * D.re)};
+    cpx<T>* out = W + k;
     if ((k & 1) == 0) {
-      cpx<T> w = ldg_c(post + j);
-      cpx<T> a = V[j], b = V[j == 0 ? 0 : N - j];
-      cpx<T> p = {fma(w.re, a.re + b.re, w.im * (b.im - a.im)), fma(w.re, a.im + b.im, w.im * (a.re - b.re))};
+      cpx<T> oj = pj, ojj = pjj;
       if (ADJ) {
-        out = j == 0 ? (T)0.5 * p : p;
+        if (j == 0) oj = (T)0.5 * oj;
         if constexpr (std::is_same<T, double>::value) {
           // transpose of the k = 0 closure X_0 = sum_{j even >= 2} 2 X_j/(j^2-1):
           // Xbar_j += 2 Xbar_0/(j^2-1), with Xbar_0 = P_0 = V_0
-          if ((zonal & 1) && k == 0 && j >= 2 && !(j & 1)) {
-            double wj = 2.0 / ((double)j * (double)j - 1.0);
-            out = out + wj * V[0];
+          if ((zonal & 1) && k == 0) {
+            if (j >= 2 && !(j & 1)) oj = oj + (2.0 / ((double)j * (double)j - 1.0)) * V[0];
+            if (jj >= 2 && !(jj & 1)) ojj = ojj + (2.0 / ((double)jj * (double)jj - 1.0)) * V[0];
           }
         }
-      } else {
-        out = p;
       }
-    } else if (j == 0) {
-      out = {(T)0, (T)0};
+      out[(size_t)j * Kp] = oj;
+      if (pair) out[(size_t)jj * Kp] = ojj;
     } else {
-      int jj = N - j;
-      cpx<T> w = ldg_c(post + jj);
-      cpx<T> a = V[jj], b = V[j];
-      cpx<T> p = {fma(w.re, a.re + b.re, w.im * (b.im - a.im)), fma(w.re, a.im + b.im, w.im * (a.re - b.re))};
-      out = {p.im, -p.re};                       // -i p
-      if (zonal & 2) out = {-out.re, -out.im};   // coefficient convention: times (-1)^k, k odd
+      // -i p, times -1 in the coefficient convention ((-1)^k for k odd)
+      const T sg = (zonal & 2) ? (T)-1 : (T)1;
+      out[(size_t)j * Kp] = j == 0 ? cpx<T>{(T)0, (T)0} : cpx<T>{sg * pjj.im, -(sg * pjj.re)};
+      if (pair) out[(size_t)jj * Kp] = {sg * pj.im, -(sg * pj.re)};
     }
-    W[(size_t)j * Kp + k] = out;
   }
 }
 
