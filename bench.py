@@ -46,11 +46,11 @@ FP64_PEAK_GFLOPS_FALLBACK = 1008.0
 # spectrum size n_theta * Kp (every stage streams the spectrum once or twice) and
 # reports null when the sources have changed since the capture.
 TRAFFIC_CAPTURE = {
-    "csrc_sha256": "497a4fab8ccb17ef",
+    "csrc_sha256": "fc15ce2e516a1efa",
     "n_theta": 5000, "n_lambda": 5000,
-    "bytes": {"rows_forward": 200933632 + 143427072, "theta_forward": 201038848 + 141302272,
-              "solve": 663076352 + 321691648, "theta_inverse": 200885760 + 142209280,
-              "rows_inverse": 200305920 + 144568832},
+    "bytes": {"rows_forward": 200601856 + 142517504, "theta_forward": 200916736 + 141408768,
+              "solve": 662798336 + 321702144, "theta_inverse": 200890368 + 142440704,
+              "rows_inverse": 200343808 + 142960128},
 }
 
 
