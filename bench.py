@@ -146,6 +146,38 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def init_ranks(backend: str):
+    """(rank, world, local rank) from the launcher's environment; joins the
+    process group (backend "nccl" on GPUs, "gloo" in the CPU tests) when world > 1."""
+    rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        kw = {"device_id": torch.device("cuda", local)} if backend == "nccl" else {}
+        dist.init_process_group(backend, **kw)
+    return rank, world, local
+
+
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time: every rank's timed region ends at the barrier
+    that follows it, so the job's time is the maximum."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(dof_per_rank: int, world: int, ms_per_step: float) -> float:
+    """DOF/s of the whole job: every rank solves its own problem (weak scaling)."""
+    return dof_per_rank * world / (ms_per_step * 1e-3)
+
+
 def algorithmic_flops(n_theta: int, n_lambda: int) -> dict:
     """Conventional FFT flop counts per stage launch: a real FFT of length n costs
     2.5 n log2 n, the folded colatitude transform of one complex column of length
@@ -175,11 +207,8 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
-    local = _env_int("LOCAL_RANK", 0)
+    rank, world, local = init_ranks("nccl")
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import tempfile
 
     import paper_1510_08094_gb300 as sp
@@ -223,13 +252,10 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     stage_ms, recorded = plan.profile_end()
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     ms_step = ms / args.steps
     dof = N * n
-    value = dof * world / (ms_step * 1e-3)
+    value = whole_job_value(dof, world, ms_step)
 
     # end to end through the host-buffer C-ABI call (pinned host memory; the copies
     # of f in and u out are inside the timed region)

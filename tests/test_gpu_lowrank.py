@@ -86,7 +86,7 @@ def test_paper_test_function_rank(sp):
     assert 23 <= _rank(piv) <= 25        # the paper's spherefun reports rank 23
 
 
-@pytest.mark.parametrize("nt,nl", [(24, 48), (64, 128)])
+@pytest.mark.parametrize("nt,nl", [(24, 48), (64, 128), (26, 58), (33, 70)])
 def test_lowrank_solve_matches_dense_and_oracle(sp, nt, nl):
     x, y, z = _xyz(nt, nl, "cuda")
     f = (torch.sin(5 * x * y * z) + torch.cos(2 * x + y)).contiguous()

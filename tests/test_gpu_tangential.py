@@ -42,7 +42,8 @@ def _xyz(nt, nl):
     return [torch.tensor(v, device="cuda") for v in (x, y, z)]
 
 
-@pytest.mark.parametrize("nt,nl,lmax", [(12, 24, 5), (16, 34, 7), (9, 20, 4), (33, 70, 14), (64, 128, 30)])
+@pytest.mark.parametrize("nt,nl,lmax", [(12, 24, 5), (16, 34, 7), (9, 20, 4), (33, 70, 14), (64, 128, 30),
+                                        (22, 58, 9), (31, 62, 12)])
 def test_matches_oracle_on_band_limited_series(sp, nt, nl, lmax):
     f = sh.synthesize(sh.random_sh_coeffs(lmax, 100 + nt), nt, nl).numpy()
     ref = O.tangential_gradient(f)

@@ -28,7 +28,7 @@ def sp():
     return sp
 
 
-@pytest.mark.parametrize("nt,nl", [(24, 48), (33, 70), (64, 128), (5, 10)])
+@pytest.mark.parametrize("nt,nl", [(24, 48), (33, 70), (64, 128), (5, 10), (22, 58), (1, 2)])
 def test_coeffs2_matches_oracle(sp, nt, nl):
     f = np.random.default_rng(nt).standard_normal((nt, nl))
     X = O.coeffs2(O.dfs_double(f))               # [j + m/2, k + n/2]
