@@ -294,7 +294,7 @@ def run_ours(args):
                     f"(sphere_poisson_pipe_rates)")
     except Exception as exc:  # keep the bench line even if the probe fails
         fp64_peak = FP64_PEAK_GFLOPS_FALLBACK
-        peak_src = f"earlier probe on this pool (live probe failed: {exc})"
+        peak_src = f"earlier probe on a GB300 (live probe failed: {exc})"
     hbm_gbs = bytes_[dom] / (dom_ms * 1e-3) / 1e9
     if args.precision == "fp32":
         # FP32 transforms are bounded by HBM traffic, not arithmetic

@@ -152,7 +152,7 @@ int sphere_poisson_solve_host(sp_plan_t plan, const double* f_host, double* u_ho
  * Allocation-free solve.  The paper has no counterpart; this is a service for
  * callers that cannot obtain device memory at the moment they need a solve:
  * code running where a cudaMalloc is not allowed or would stall the device
- * (a real-time loop, a host callback, a section holding a driver-level lock),
+ * (a real-time loop, a host callback, a section holding a runtime lock),
  * programs whose device memory belongs to a framework allocator that forbids
  * raw allocations, or plug-ins that are handed only the input and output
  * buffers by their host application.  It computes exactly what
