@@ -29,6 +29,7 @@ namespace {
 constexpr int kMaxLen = 12288;             // longest transform (n_theta, n_lambda/2)
 constexpr size_t kSmemBudget = 200 * 1024;  // shared memory per CTA for a transform tile
 constexpr int kBatchThreadsPerCta = 256;     // threads of a persistent batched CTA
+constexpr int kHostChunks = 8;               // row chunks of the host-buffer solve's overlapped copies
 constexpr uint32_t kMagic = 0x53504f31u;    // "SPO1"
 constexpr double kHalfPi = 1.57079632679489661923132169163975144;
 
@@ -213,6 +214,9 @@ struct sp_plan_s {
   // the FP32 forms run the zonal column on a second stream
   cudaStream_t side;
   cudaEvent_t ev_fork, ev_join;
+  // host-buffer solve: copy stream and per-chunk events (created on first use)
+  cudaStream_t copy;
+  std::vector<cudaEvent_t> ov_events;
   // stage timing (profile_begin / profile_end)
   std::vector<cudaEvent_t> prof_events;
   int prof_max, prof_count;
@@ -359,16 +363,78 @@ void launch_rows_inverse_x(sp_plan_t p, bool adj, cudaStream_t st, const cpx<T>*
                                n, Kp, rows, d, tw, perm, post, rs, rst, zonal);
 }
 
-void enqueue_fp64(sp_plan_t p, bool adj, const double* in, double* out, void* ws, cudaStream_t st) {
+// Host-buffer solve with the copies overlapped: the grid moves in row chunks on
+// the plan's copy stream; the longitude forward transform of chunk c starts as
+// soon as its rows have arrived, and the rows of u go back chunk by chunk as
+// the longitude inverse transform finishes them.
+struct HostOverlap {
+  const double* f_host;
+  double* u_host;
+  double* d_f;
+  double* d_u;
+  cudaStream_t copy;
+  const cudaEvent_t* ev_in;   // one per chunk
+  const cudaEvent_t* ev_out;  // one per chunk
+  int chunks;
+};
+
+int overlap_chunk_rows(sp_plan_t p, const HostOverlap* ov) { return (p->nt + ov->chunks - 1) / ov->chunks; }
+
+template <typename T>
+void rows_forward_stage(sp_plan_t p, bool adj, cudaStream_t st, const double* in, cpx<T>* W, const cpx<T>* tw,
+                        const cpx<T>* post, const double* rs, const T* rst, cpx<double>* zonal,
+                        const HostOverlap* ov) {
+  if (!ov) {
+    launch_rows_forward_x<T>(p, adj, st, in, W, p->nt, p->nl, p->Kp, p->rows_per_cta, p->row_fft, tw,
+                             p->perm_row, post, rs, rst, zonal);
+    return;
+  }
+  const int chunk = overlap_chunk_rows(p, ov);
+  for (int c = 0, r0 = 0; r0 < p->nt; ++c, r0 += chunk) {
+    const int nr = std::min(chunk, p->nt - r0);
+    const size_t off = (size_t)r0 * p->nl;
+    cudaMemcpyAsync(ov->d_f + off, ov->f_host + off, (size_t)nr * p->nl * sizeof(double), cudaMemcpyHostToDevice,
+                    ov->copy);
+    cudaEventRecord(ov->ev_in[c], ov->copy);
+    cudaStreamWaitEvent(st, ov->ev_in[c], 0);
+    launch_rows_forward_x<T>(p, adj, st, ov->d_f + off, W + (size_t)r0 * p->Kp, nr, p->nl, p->Kp,
+                             p->rows_per_cta, p->row_fft, tw, p->perm_row, post, rs + r0, rst + r0,
+                             zonal ? zonal + 2 * (size_t)r0 : nullptr);
+  }
+}
+
+template <typename T>
+void rows_inverse_stage(sp_plan_t p, bool adj, cudaStream_t st, const cpx<T>* W, double* out, const cpx<T>* tw,
+                        const cpx<T>* post, const double* rs, const T* rst, const cpx<double>* zonal,
+                        const HostOverlap* ov) {
+  if (!ov) {
+    launch_rows_inverse_x<T>(p, adj, st, W, out, p->nt, p->nl, p->Kp, p->rows_per_cta, p->row_fft, tw,
+                             p->perm_row, post, rs, rst, zonal);
+    return;
+  }
+  const int chunk = overlap_chunk_rows(p, ov);
+  for (int c = 0, r0 = 0; r0 < p->nt; ++c, r0 += chunk) {
+    const int nr = std::min(chunk, p->nt - r0);
+    const size_t off = (size_t)r0 * p->nl;
+    launch_rows_inverse_x<T>(p, adj, st, W + (size_t)r0 * p->Kp, ov->d_u + off, nr, p->nl, p->Kp,
+                             p->rows_per_cta, p->row_fft, tw, p->perm_row, post, rs + r0, rst + r0,
+                             zonal ? zonal + 2 * (size_t)r0 : nullptr);
+    cudaEventRecord(ov->ev_out[c], st);
+    cudaStreamWaitEvent(ov->copy, ov->ev_out[c], 0);
+    cudaMemcpyAsync(ov->u_host + off, ov->d_u + off, (size_t)nr * p->nl * sizeof(double), cudaMemcpyDeviceToHost,
+                    ov->copy);
+  }
+}
+
+void enqueue_fp64(sp_plan_t p, bool adj, const double* in, double* out, void* ws, cudaStream_t st,
+                  const HostOverlap* ov = nullptr) {
   using sp::Launch;
   cpx<double>* W = static_cast<cpx<double>*>(ws);
   StageMarks m{p, st, !p->prof_events.empty() && p->prof_count < p->prof_max};
   const Launch solve{dim3((p->K + 31) / 32, 2), 32, 0, st};
   const double inv_n = 1.0 / (double)p->N;
   m.mark(0);
-  launch_rows_forward_x<double>(p, adj, st, in, W, p->nt, p->nl, p->Kp, p->rows_per_cta,
-                                  p->row_fft, p->tw_row, p->perm_row, p->post_row, p->row_scale, p->row_scale,
-                                  nullptr);
+  rows_forward_stage<double>(p, adj, st, in, W, p->tw_row, p->post_row, p->row_scale, p->row_scale, nullptr, ov);
   m.mark(1);
   launch_theta_forward_x<double>(p, adj, st, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
                                    p->tw_col, p->perm_col, adj ? p->post_col : p->post_col_s, inv_n, 1);
@@ -378,9 +444,7 @@ void enqueue_fp64(sp_plan_t p, bool adj, const double* in, double* out, void* ws
   launch_theta_inverse_x<double>(p, adj, st, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
                                    p->tw_col, p->perm_col, p->post_col, inv_n, 1);
   m.mark(4);
-  launch_rows_inverse_x<double>(p, adj, st, W, out, p->nt, p->nl, p->Kp, p->rows_per_cta,
-                                  p->row_fft, p->tw_row, p->perm_row, p->post_row, p->row_scale, p->row_scale,
-                                  nullptr);
+  rows_inverse_stage<double>(p, adj, st, W, out, p->tw_row, p->post_row, p->row_scale, p->row_scale, nullptr, ov);
   m.mark(5);
   m.done();
 }
@@ -396,7 +460,8 @@ void enqueue_zonal_fp64(sp_plan_t p, bool adj, cpx<double>* Z, cudaStream_t st) 
                                    p->post_col, inv_n, 1);
 }
 
-void enqueue_fp32(sp_plan_t p, bool adj, const double* in, double* out, void* ws, cudaStream_t st) {
+void enqueue_fp32(sp_plan_t p, bool adj, const double* in, double* out, void* ws, cudaStream_t st,
+                  const HostOverlap* ov = nullptr) {
   using sp::Launch;
   cpx<float>* W = static_cast<cpx<float>*>(ws);
   cpx<double>* Z = reinterpret_cast<cpx<double>*>(static_cast<char*>(ws) + p->off_z);
@@ -408,9 +473,8 @@ void enqueue_fp32(sp_plan_t p, bool adj, const double* in, double* out, void* ws
   const cpx<float>* por = static_cast<const cpx<float>*>(p->post_row_t);
   const cpx<float>* poc = static_cast<const cpx<float>*>(p->post_col_t);
   m.mark(0);
-  launch_rows_forward_x<float>(p, adj, st, in, W, p->nt, p->nl, p->Kp, p->rows_per_cta,
-                                 p->row_fft, twr, p->perm_row, por, p->row_scale,
-                                 static_cast<const float*>(p->row_scale_t), Z);
+  rows_forward_stage<float>(p, adj, st, in, W, twr, por, p->row_scale, static_cast<const float*>(p->row_scale_t),
+                            Z, ov);
   cudaEventRecord(p->ev_fork, st);
   cudaStreamWaitEvent(p->side, p->ev_fork, 0);
   enqueue_zonal_fp64(p, adj, Z, p->side);
@@ -426,14 +490,14 @@ void enqueue_fp32(sp_plan_t p, bool adj, const double* in, double* out, void* ws
                                   twc, p->perm_col, poc, inv_n, 0);
   cudaStreamWaitEvent(st, p->ev_join, 0);
   m.mark(4);
-  launch_rows_inverse_x<float>(p, adj, st, W, out, p->nt, p->nl, p->Kp, p->rows_per_cta,
-                                 p->row_fft, twr, p->perm_row, por, p->row_scale,
-                                 static_cast<const float*>(p->row_scale_t), Z);
+  rows_inverse_stage<float>(p, adj, st, W, out, twr, por, p->row_scale, static_cast<const float*>(p->row_scale_t),
+                            Z, ov);
   m.mark(5);
   m.done();
 }
 
-void enqueue_refine(sp_plan_t p, const double* in, double* out, void* ws, cudaStream_t st) {
+void enqueue_refine(sp_plan_t p, const double* in, double* out, void* ws, cudaStream_t st,
+                    const HostOverlap* ov = nullptr) {
   using sp::Launch;
   using sp::dd;
   char* base = static_cast<char*>(ws);
@@ -449,9 +513,8 @@ void enqueue_refine(sp_plan_t p, const double* in, double* out, void* ws, cudaSt
   const cpx<dd>* por = static_cast<const cpx<dd>*>(p->post_row_t);
   const cpx<dd>* poc = static_cast<const cpx<dd>*>(p->post_col_t);
   m.mark(0);
-  launch_rows_forward_x<dd>(p, false, st, in, Fd, p->nt, p->nl, p->Kp, p->rows_per_cta,
-                              p->row_fft, twr, p->perm_row, por, p->row_scale,
-                              static_cast<const dd*>(p->row_scale_t), nullptr);
+  rows_forward_stage<dd>(p, false, st, in, Fd, twr, por, p->row_scale, static_cast<const dd*>(p->row_scale_t),
+                         nullptr, ov);
   m.mark(1);
   launch_theta_forward_x<dd>(p, false, st, Fd, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
                                twc, p->perm_col, static_cast<const cpx<dd>*>(p->post_col_s_t), inv_n, 0);
@@ -472,9 +535,8 @@ void enqueue_refine(sp_plan_t p, const double* in, double* out, void* ws, cudaSt
   launch_theta_inverse_x<dd>(p, false, st, Xd, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
                                twc, p->perm_col, poc, inv_n, 0);
   m.mark(4);
-  launch_rows_inverse_x<dd>(p, false, st, Xd, out, p->nt, p->nl, p->Kp, p->rows_per_cta,
-                              p->row_fft, twr, p->perm_row, por, p->row_scale,
-                              static_cast<const dd*>(p->row_scale_t), nullptr);
+  rows_inverse_stage<dd>(p, false, st, Xd, out, twr, por, p->row_scale, static_cast<const dd*>(p->row_scale_t),
+                         nullptr, ov);
   m.mark(5);
   m.done();
 }
@@ -567,6 +629,8 @@ void upload_table<sp::dd>(const std::vector<cpx<double>>& src, std::vector<char>
 
 void destroy_plan(sp_plan_s* p) {
   for (cudaEvent_t e : p->prof_events) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->ov_events) cudaEventDestroy(e);
+  if (p->copy) cudaStreamDestroy(p->copy);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
   if (p->side) cudaStreamDestroy(p->side);
@@ -1455,10 +1519,29 @@ int sphere_poisson_solve_host(sp_plan_t plan, const double* f_host, double* u_ho
   double* d_u = reinterpret_cast<double*>(base + grid);
   void* ws = base + 2 * grid;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  SP_CUDA(cudaMemcpyAsync(d_f, f_host, bytes, cudaMemcpyHostToDevice, st));
-  int rc = launch_solve<false>(plan, d_f, d_u, ws, st);
-  if (rc != SP_OK) return rc;
-  SP_CUDA(cudaMemcpyAsync(u_host, d_u, bytes, cudaMemcpyDeviceToHost, st));
+  if (plan->batched || plan->nt < 2 * kHostChunks) {
+    SP_CUDA(cudaMemcpyAsync(d_f, f_host, bytes, cudaMemcpyHostToDevice, st));
+    int rc = launch_solve<false>(plan, d_f, d_u, ws, st);
+    if (rc != SP_OK) return rc;
+    SP_CUDA(cudaMemcpyAsync(u_host, d_u, bytes, cudaMemcpyDeviceToHost, st));
+    SP_CUDA(cudaStreamSynchronize(st));
+    return SP_OK;
+  }
+  // copies overlapped with the longitude transforms, in kHostChunks row chunks
+  if (!plan->copy) {
+    SP_CUDA(cudaStreamCreateWithFlags(&plan->copy, cudaStreamNonBlocking));
+    plan->ov_events.assign(2 * kHostChunks + 1, nullptr);
+    for (cudaEvent_t& e : plan->ov_events) SP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  const HostOverlap ov{f_host, u_host, d_f, d_u, plan->copy, plan->ov_events.data() + 1,
+                       plan->ov_events.data() + 1 + kHostChunks, kHostChunks};
+  SP_CUDA(cudaEventRecord(plan->ov_events[0], st));     // the copies follow earlier work on the stream
+  SP_CUDA(cudaStreamWaitEvent(plan->copy, plan->ov_events[0], 0));
+  if (plan->precision == SP_FP64) enqueue_fp64(plan, false, d_f, d_u, ws, st, &ov);
+  else if (plan->precision == SP_FP32) enqueue_fp32(plan, false, d_f, d_u, ws, st, &ov);
+  else enqueue_refine(plan, d_f, d_u, ws, st, &ov);
+  SP_CUDA(cudaGetLastError());
+  SP_CUDA(cudaStreamSynchronize(plan->copy));
   SP_CUDA(cudaStreamSynchronize(st));
   return SP_OK;
 }

@@ -107,15 +107,20 @@ def test_autograd_gradient_matches_central_difference(sp):
     assert _rel(grad.cpu().numpy(), ref) < TOL
 
 
-def test_solve_host_matches_device(sp):
-    nt, nl = 100, 200
+@pytest.mark.parametrize("precision,sweeps", [("fp64", 0), ("fp32", 0), ("fp32_refine", 1)])
+@pytest.mark.parametrize("nt,nl", [(100, 200), (13, 26), (62, 124)])
+def test_solve_host_matches_device(sp, precision, sweeps, nt, nl):
+    # the host-buffer solve moves the grid in row chunks overlapped with the
+    # longitude transforms (or in one piece for small grids); the rows are
+    # transformed by the same kernels, so the answer is bit-identical
     f = torch.tensor(_rough(nt, nl, 5))
-    plan = sp.Plan(nt, nl)
+    plan = sp.Plan(nt, nl, precision, sweeps)
     u_dev = plan.solve(f.cuda()).cpu()
     u_host = plan.solve_host(f.pin_memory())
     assert torch.equal(u_dev, u_host)
     u_host2 = plan.solve_host(f)          # pageable memory
     assert torch.equal(u_dev, u_host2)
+    assert torch.equal(plan.solve_host(f.pin_memory()), u_dev)   # a second call reuses the copy stream
 
 
 def test_repeated_and_stream_solves_are_identical(sp):
