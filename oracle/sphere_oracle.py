@@ -41,7 +41,9 @@ parity split or the BMC fold, which are properties the tests check.
 Also here: the structure-preserving GE of Section 3 and the low-rank form of
 the coefficients F, the surface integral sum2 (Section 4, Integration, eq.
 integrationCoeffs), the tangential derivatives of Section 4 (Differentiation,
-eqs. diff_x..diff_z with the division by sin theta through M_sin^{-1}), and the
+eqs. diff_x..diff_z with the division by sin theta through M_sin^{-1}) and the
+vector-calculus operators built from them (divergence, curl, the curl of a
+scalar function of eq. CurlScalarF, vorticity), and the
 transpose (adjoint) of the whole linear map f -> u, both matrix-free and as a
 dense matrix for tiny grids.
 """
@@ -457,6 +459,48 @@ def tangential_gradient(f: np.ndarray):
         G[:, 0] = 0.0
         out.append(sample(G)[nt:].real.copy())
     return tuple(out)
+
+
+# ----------------------------------------------------------------------------
+# Vector calculus (Section 4, vector-valued functions): every operator is a
+# combination of the tangential derivatives above, in the paper's formulas
+# ----------------------------------------------------------------------------
+
+def unit_normal(n_theta: int, n_lambda: int):
+    """(x, y, z) of eq. sphericalCoordinates on the n_theta x n_lambda grid
+    (theta > 0 half of the DFS grid): the outward unit normal n = (x, y, z)."""
+    th = dfs_theta(2 * n_theta)[n_theta:][:, None]
+    la = dfs_lambda(n_lambda)[None, :]
+    return np.cos(la) * np.sin(th), np.sin(la) * np.sin(th), np.cos(th) + 0.0 * la
+
+
+def divergence(f1: np.ndarray, f2: np.ndarray, f3: np.ndarray) -> np.ndarray:
+    """Surface divergence of the field (f1, f2, f3): d^t f1/dx + d^t f2/dy + d^t f3/dz."""
+    return tangential_gradient(f1)[0] + tangential_gradient(f2)[1] + tangential_gradient(f3)[2]
+
+
+def curl(f1: np.ndarray, f2: np.ndarray, f3: np.ndarray):
+    """Surface curl of the field (f1, f2, f3), component by component:
+    (d^t f3/dy - d^t f2/dz, d^t f1/dz - d^t f3/dx, d^t f2/dx - d^t f1/dy).
+    For a tangent field its normal component is the vorticity (see vorticity);
+    the result is tangent only where that vanishes."""
+    g1, g2, g3 = tangential_gradient(f1), tangential_gradient(f2), tangential_gradient(f3)
+    return (g3[1] - g2[2], g1[2] - g3[0], g2[0] - g1[1])
+
+
+def scalar_curl(f: np.ndarray):
+    """Curl of a scalar function (eq. CurlScalarF): n x grad f, with n = (x, y, z),
+    = (y d^t f/dz - z d^t f/dy, z d^t f/dx - x d^t f/dz, x d^t f/dy - y d^t f/dx)."""
+    x, y, z = unit_normal(*f.shape)
+    gx, gy, gz = tangential_gradient(f)
+    return (y * gz - z * gy, z * gx - x * gz, x * gy - y * gx)
+
+
+def vorticity(f1: np.ndarray, f2: np.ndarray, f3: np.ndarray) -> np.ndarray:
+    """Vorticity of the field, the scalar (curl f) . n."""
+    x, y, z = unit_normal(*f1.shape)
+    c1, c2, c3 = curl(f1, f2, f3)
+    return x * c1 + y * c2 + z * c3
 
 
 # ----------------------------------------------------------------------------
