@@ -365,6 +365,9 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
 
 
+FORM_GROUPS = ("precision", "adjoint", "tangential_gradient", "vector_calculus", "lowrank", "paper_scale")
+
+
 def measure_forms(sp, f, u_exact, u64, N, n, dev, ms_fp64, args):
     """The reduced-precision forms on the same input and device, timed the same
     way, with their error against the FP64 solution and the closed form."""
@@ -373,7 +376,10 @@ def measure_forms(sp, f, u_exact, u64, N, n, dev, ms_fp64, args):
     ex = float(u_exact.abs().max())
     res = {}
     steps = max(5, min(args.steps, 50))
+    want = set(args.forms.split(",")) if args.forms else set(FORM_GROUPS)
     for prec, sweeps in [("fp32", 0), ("fp32_refine", 0), ("fp32_refine", 1), ("fp32_refine", 2)]:
+        if "precision" not in want:
+            break
         plan = sp.Plan(N, n, prec, sweeps, device=dev, autotune=not args.no_autotune)
         ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=dev)
         u = torch.empty_like(f)
@@ -399,6 +405,8 @@ def measure_forms(sp, f, u_exact, u64, N, n, dev, ms_fp64, args):
     g = u_exact
     sg64 = None
     for prec in ("fp64", "fp32"):
+        if "adjoint" not in want:
+            break
         plan = sp.Plan(N, n, prec, 0, device=dev, autotune=not args.no_autotune)
         ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=dev)
         out = torch.empty_like(f)
@@ -423,9 +431,13 @@ def measure_forms(sp, f, u_exact, u64, N, n, dev, ms_fp64, args):
             entry["max_rel_err_vs_fp64_adjoint"] = float((out - sg64).abs().max() / sg64.abs().max())
         res[f"adjoint_{prec}"] = entry
         del plan, ws, out, sf
-    res["tangential_gradient"] = measure_tangential(sp, f, N, n, dev, steps, args)
-    res["lowrank"] = measure_lowrank(sp, N, n, dev, steps, ms_fp64, args)
-    if not args.no_paper_scale:
+    if "tangential_gradient" in want:
+        res["tangential_gradient"] = measure_tangential(sp, f, N, n, dev, steps, args)
+    if "vector_calculus" in want:
+        res["vector_calculus"] = measure_vector_calculus(sp, N, n, dev, steps, args)
+    if "lowrank" in want:
+        res["lowrank"] = measure_lowrank(sp, N, n, dev, steps, ms_fp64, args)
+    if "paper_scale" in want and not args.no_paper_scale:
         res["paper_scale"] = measure_paper_scale(sp, dev, args)
     return res
 
@@ -505,7 +517,73 @@ def measure_tangential(sp, f, N, n, dev, steps, args):
             "outputs": "d^t f/dx, d^t f/dy, d^t f/dz on the grid",
             "max_rel_err_vs_closed_form_xyz": errs,
             "closed_form_case": "1 + x + y^2 + x^2 y + x^4 + y^5 + (xyz)^2",
-            "gpu_launches_per_call": 2 + 1 + 3 * 3}
+            "gpu_launches_per_call": 2 + 3 + 1 + 3 * 2}
+
+
+def measure_vector_calculus(sp, N, n, dev, steps, args):
+    """Divergence, curl, curl of a scalar function and vorticity (Section 4) on the
+    paper's Rossby-Haurwitz stream function psi = cos(theta) + sin^4(theta)
+    cos(theta) cos(4 lambda) at the bench size, each timed; accuracy: the
+    vorticity of curl(psi) against the Laplacian of psi, and div curl(psi) = 0."""
+    import torch
+    from synth import sh
+
+    plan = sp.Plan(N, n, device=dev, autotune=not args.no_autotune)
+    ws = torch.empty(plan.curl_workspace_bytes(), dtype=torch.uint8, device=dev)
+    th = torch.tensor(sh.colatitudes(N), device=dev)[:, None]
+    la = torch.tensor(sh.longitudes(n), device=dev)[None, :]
+    x, y, z = torch.cos(la) * torch.sin(th), torch.sin(la) * torch.sin(th), torch.cos(th) + 0 * la
+    q = x ** 4 - 6 * x ** 2 * y ** 2 + y ** 4
+    psi = (z + z * q).contiguous()
+    lap = -2 * z - 30 * z * q
+    del x, y, th, la
+    u = tuple(torch.empty_like(psi) for _ in range(3))
+    c = tuple(torch.empty_like(psi) for _ in range(3))
+    s = torch.empty_like(psi)
+    calls = {
+        "scalar_curl": lambda: plan.scalar_curl(psi, u, ws),
+        "divergence": lambda: plan.divergence(*u, s, ws),
+        "curl": lambda: plan.curl(*u, c, ws),
+        "vorticity": lambda: plan.vorticity(*u, s, ws),
+    }
+    reps = max(3, min(steps, 5))
+    out = {}
+    for name, call in calls.items():
+        for _ in range(2):
+            call()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            call()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = {"ms_per_call": e0.elapsed_time(e1) / reps}
+    chained = {}
+    for rtol in (0.0, 1e-14):
+        plan.set_chop(rtol)
+        plan.scalar_curl(psi, u, ws)
+        zeta = plan.vorticity(*u, s, ws)
+        err_vort = float((zeta - lap).abs().max() / lap.abs().max())
+        div = plan.divergence(*u, c[0], ws)
+        scale = max(float(ui.abs().max()) for ui in u)
+        chained[f"chop_{rtol:g}"] = {"max_rel_err_vort_u_vs_laplacian_psi": err_vort,
+                                     "max_div_u_rel": float(div.abs().max()) / scale}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        plan.vorticity(*u, s, ws)
+    e1.record()
+    torch.cuda.synchronize()
+    out["vorticity_chop_1e-14"] = {"ms_per_call": e0.elapsed_time(e1) / reps}
+    plan.set_chop(0.0)
+    return {"unit": "DOF/s", "calls": out,
+            "value_vorticity": N * n / (out["vorticity"]["ms_per_call"] * 1e-3),
+            "case": "psi = cos(theta) + sin^4(theta) cos(theta) cos(4 lambda); u = n x grad psi",
+            "chained_vort_of_curl": chained,
+            "gpu_launches_per_call": {"scalar_curl": 13, "divergence": 17, "curl": 24, "vorticity": 25,
+                                      "extra_per_input_with_chop": 2}}
 
 
 def measure_paper_scale(sp, dev, args):
@@ -727,6 +805,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--forms", default="",
+                    help="comma-separated subset of the forms to measure: " + ",".join(FORM_GROUPS))
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-paper-scale", action="store_true")
     ap.add_argument("--batch-count", type=int, default=4096)

@@ -226,15 +226,67 @@ int sphere_poisson_sum2(sp_plan_t plan, const double* f, double* result, void* w
  * the results carry truncation terms of the window.
  *   f, gx, gy, gz  device, [n_theta][n_lambda] doubles, 16-byte aligned.
  *   workspace      device, >= sphere_poisson_gradient_workspace_size bytes
- *                  (three half spectra: 3 n_theta Kp 16 bytes, Kp = n_lambda/2 + 1
- *                  rounded up to even).
+ *                  (five half spectra of n_theta Kp 16 bytes, Kp = n_lambda/2 + 1
+ *                  rounded up to even, plus 2 ceil(n_theta/64) Kp 16 bytes of
+ *                  chunk sums for the division and 256 bytes).
  * FP64 single plans only (others: SP_ERR_UNSUPPORTED).  Asynchronous on stream;
- * 12 kernel launches: the two of coeffs2, one for the division, then per component
- * one coefficient map and the two inverse transforms.
+ * 12 kernel launches: the two of coeffs2, three for the division, one forming the
+ * three components' coefficients, then per component the two inverse transforms
+ * (two more with the chop of sphere_poisson_set_chop).
  */
 int sphere_poisson_gradient_workspace_size(sp_plan_t plan, size_t* workspace_bytes);
 int sphere_poisson_tangential_gradient(sp_plan_t plan, const double* f, double* gx, double* gy, double* gz,
                                        void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Vector calculus (Section 4, vector-valued functions), built on the tangential
+ * derivatives above; a vector field is three Cartesian components on the grid.
+ *   sphere_poisson_divergence:  div = d^t f1/dx + d^t f2/dy + d^t f3/dz.
+ *   sphere_poisson_curl:        (c1, c2, c3) = (d^t f3/dy - d^t f2/dz,
+ *                               d^t f1/dz - d^t f3/dx, d^t f2/dx - d^t f1/dy).
+ *                               For a tangent field the normal part n . c is the
+ *                               vorticity, so c is tangent only where that is zero
+ *                               (the solid rotation (-y, x, 0) has c = (xz, yz, 1 + z^2)).
+ *   sphere_poisson_scalar_curl: the curl of a scalar function f (eq. CurlScalarF),
+ *                               n x grad f = (y gz - z gy, z gx - x gz, x gy - y gx)
+ *                               with n = (x, y, z) of eq. sphericalCoordinates.
+ *   sphere_poisson_vorticity:   zeta = (curl f) . n.
+ * The sums of derivative terms are formed in coefficient space (one inverse
+ * transform per output); the products with n are taken pointwise on the grid.
+ * The formulas are applied as printed whether or not the field is tangent.
+ *   f1, f2, f3, f, outputs  device, [n_theta][n_lambda] doubles, 16-byte aligned;
+ *                           outputs must not overlap the inputs.
+ *   workspace  >= sphere_poisson_curl_workspace_size bytes, the same size as the
+ *              gradient's (five half spectra plus the division's scratch); the
+ *              divergence uses the first three spectra and accepts a workspace
+ *              two spectra (2 n_theta Kp 16 bytes) smaller.
+ * FP64 single plans only (others: SP_ERR_UNSUPPORTED); asynchronous on stream.
+ * Accuracy as for the gradient: exact to rounding for band-limited inputs, with
+ * the rounding of the x and y derivative terms amplified up to ~k_max m/pi by
+ * the division by sin theta.
+ */
+int sphere_poisson_curl_workspace_size(sp_plan_t plan, size_t* workspace_bytes);
+/*
+ * Optional truncation of the derivative operators' inputs (tangential_gradient,
+ * divergence, curl, scalar_curl, vorticity): after each input's forward
+ * transform, the coefficients with |X_jk| <= rtol max |X| are set to zero, the
+ * grid counterpart of building a function to machine precision relative to its
+ * maximum (Section 3) and discarding the rest.  Without it the rounding noise in
+ * modes a band-limited input does not have is amplified by the division by
+ * sin theta, which matters when derivatives are chained (the vorticity of the
+ * curl of a degree-5 function at 5000 x 10000: 3e-3 off, 4e-15 with rtol = 1e-14).  rtol in [0, 1); 0 (the
+ * default) is off.  A plain field of the plan: set it before enqueuing calls.
+ * Errors: SP_ERR_BAD_PLAN, SP_ERR_BAD_ARG (rtol negative, >= 1 or NaN).
+ */
+int sphere_poisson_set_chop(sp_plan_t plan, double rtol);
+int sphere_poisson_divergence(sp_plan_t plan, const double* f1, const double* f2, const double* f3, double* div,
+                              void* workspace, size_t workspace_bytes, void* stream);
+int sphere_poisson_curl(sp_plan_t plan, const double* f1, const double* f2, const double* f3, double* c1,
+                        double* c2, double* c3, void* workspace, size_t workspace_bytes, void* stream);
+int sphere_poisson_scalar_curl(sp_plan_t plan, const double* f, double* c1, double* c2, double* c3,
+                               void* workspace, size_t workspace_bytes, void* stream);
+int sphere_poisson_vorticity(sp_plan_t plan, const double* f1, const double* f2, const double* f3, double* zeta,
+                             void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * Low-rank form (Section 3, Figure GaussianElimination; Section 4, low-rank

@@ -418,7 +418,7 @@ def lowrank_rhs_coefficients(terms, m: int, n: int) -> np.ndarray:
 # diff_z, dfdx and Msin)
 # ----------------------------------------------------------------------------
 
-def tangential_gradient(f: np.ndarray):
+def tangential_gradient(f: np.ndarray, chop: float = 0.0):
     """(d^t f/dx, d^t f/dy, d^t f/dz) on the n_theta x n_lambda grid, the
     Cartesian components of the surface gradient, computed in coefficient space
     as the paper does:
@@ -435,13 +435,18 @@ def tangential_gradient(f: np.ndarray):
     with it).  (2) The Nyquist modes j = -m/2 and k = -n/2 of X are dropped
     before the operators act and of each result after, so the truncation is
     symmetric (as in the solver's reading B); modes the products push beyond the
-    m x n window are discarded."""
+    m x n window are discarded.  (3) chop > 0: coefficients with
+    |X_jk| <= chop max |X| are set to zero first, the grid counterpart of the
+    constructor resolving a function to a tolerance relative to its maximum
+    (Section 3)."""
     ft = dfs_double(f)
     m, n = ft.shape
     nt = m // 2
     X = coeffs2(ft)
     X[0, :] = 0.0
     X[:, 0] = 0.0
+    if chop > 0.0:
+        X[np.abs(X) <= chop * np.abs(X).max()] = 0.0
     Dm, Dn = op_Dm(m), op_Dm(n)
     Mcos_t, Msin_t = op_Mcos(m), op_Msin(m)
     Mcos_l, Msin_l = op_Mcos(n), op_Msin(n)
@@ -474,32 +479,33 @@ def unit_normal(n_theta: int, n_lambda: int):
     return np.cos(la) * np.sin(th), np.sin(la) * np.sin(th), np.cos(th) + 0.0 * la
 
 
-def divergence(f1: np.ndarray, f2: np.ndarray, f3: np.ndarray) -> np.ndarray:
+def divergence(f1: np.ndarray, f2: np.ndarray, f3: np.ndarray, chop: float = 0.0) -> np.ndarray:
     """Surface divergence of the field (f1, f2, f3): d^t f1/dx + d^t f2/dy + d^t f3/dz."""
-    return tangential_gradient(f1)[0] + tangential_gradient(f2)[1] + tangential_gradient(f3)[2]
+    return (tangential_gradient(f1, chop)[0] + tangential_gradient(f2, chop)[1]
+            + tangential_gradient(f3, chop)[2])
 
 
-def curl(f1: np.ndarray, f2: np.ndarray, f3: np.ndarray):
+def curl(f1: np.ndarray, f2: np.ndarray, f3: np.ndarray, chop: float = 0.0):
     """Surface curl of the field (f1, f2, f3), component by component:
     (d^t f3/dy - d^t f2/dz, d^t f1/dz - d^t f3/dx, d^t f2/dx - d^t f1/dy).
     For a tangent field its normal component is the vorticity (see vorticity);
     the result is tangent only where that vanishes."""
-    g1, g2, g3 = tangential_gradient(f1), tangential_gradient(f2), tangential_gradient(f3)
+    g1, g2, g3 = (tangential_gradient(fc, chop) for fc in (f1, f2, f3))
     return (g3[1] - g2[2], g1[2] - g3[0], g2[0] - g1[1])
 
 
-def scalar_curl(f: np.ndarray):
+def scalar_curl(f: np.ndarray, chop: float = 0.0):
     """Curl of a scalar function (eq. CurlScalarF): n x grad f, with n = (x, y, z),
     = (y d^t f/dz - z d^t f/dy, z d^t f/dx - x d^t f/dz, x d^t f/dy - y d^t f/dx)."""
     x, y, z = unit_normal(*f.shape)
-    gx, gy, gz = tangential_gradient(f)
+    gx, gy, gz = tangential_gradient(f, chop)
     return (y * gz - z * gy, z * gx - x * gz, x * gy - y * gx)
 
 
-def vorticity(f1: np.ndarray, f2: np.ndarray, f3: np.ndarray) -> np.ndarray:
+def vorticity(f1: np.ndarray, f2: np.ndarray, f3: np.ndarray, chop: float = 0.0) -> np.ndarray:
     """Vorticity of the field, the scalar (curl f) . n."""
     x, y, z = unit_normal(*f1.shape)
-    c1, c2, c3 = curl(f1, f2, f3)
+    c1, c2, c3 = curl(f1, f2, f3, chop)
     return x * c1 + y * c2 + z * c3
 
 

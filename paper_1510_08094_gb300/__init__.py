@@ -175,25 +175,67 @@ class Plan:
                    "sphere_poisson_gradient_workspace_size")
         return int(n.value)
 
-    def tangential_gradient(self, f: torch.Tensor, out=None, workspace=None, stream=None):
-        """(d^t f/dx, d^t f/dy, d^t f/dz) on the grid: the Cartesian components of
-        the surface gradient (Section 4, Differentiation).  out: optional tuple of
-        three float64 CUDA tensors of the grid's shape."""
-        _check_grid(f, self.shape, "f")
+    def curl_workspace_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        _lib.check(self._lib.sphere_poisson_curl_workspace_size(self._h, ctypes.byref(n)),
+                   "sphere_poisson_curl_workspace_size")
+        return int(n.value)
+
+    def set_chop(self, rtol: float):
+        """Zero the coefficients of derivative inputs with |X| <= rtol max |X|
+        before the maps act (0 turns it off)."""
+        _lib.check(self._lib.sphere_poisson_set_chop(self._h, float(rtol)), "sphere_poisson_set_chop")
+        return self
+
+    def _derivative_call(self, name, inputs, n_out, out, workspace, need, stream):
+        for i, f in enumerate(inputs):
+            _check_grid(f, self.shape, f"input {i}")
         if out is None:
-            out = tuple(torch.empty_like(f) for _ in range(3))
+            out = tuple(torch.empty_like(inputs[0]) for _ in range(n_out))
+        nbytes = inputs[0].numel() * 8
         for o in out:
             _check_grid(o, self.shape, "out")
-        need = self.gradient_workspace_bytes()
+            for f in inputs:
+                if abs(o.data_ptr() - f.data_ptr()) < nbytes:
+                    raise ValueError("outputs must not overlap the inputs")
         if workspace is None:
             workspace = torch.empty(need, dtype=torch.uint8, device=self.device)
         elif workspace.numel() * workspace.element_size() < need:
             raise ValueError("workspace too small")
-        _lib.check(self._lib.sphere_poisson_tangential_gradient(
-            self._h, f.data_ptr(), out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(),
-            workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream_ptr(stream)),
-            "sphere_poisson_tangential_gradient")
+        _lib.check(getattr(self._lib, name)(
+            self._h, *[t.data_ptr() for t in inputs], *[o.data_ptr() for o in out],
+            workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream_ptr(stream)), name)
         return out
+
+    def tangential_gradient(self, f: torch.Tensor, out=None, workspace=None, stream=None):
+        """(d^t f/dx, d^t f/dy, d^t f/dz) on the grid: the Cartesian components of
+        the surface gradient (Section 4, Differentiation).  out: optional tuple of
+        three float64 CUDA tensors of the grid's shape."""
+        return self._derivative_call("sphere_poisson_tangential_gradient", (f,), 3, out, workspace,
+                                     self.gradient_workspace_bytes(), stream)
+
+    def divergence(self, f1, f2, f3, out=None, workspace=None, stream=None):
+        """Surface divergence d^t f1/dx + d^t f2/dy + d^t f3/dz (Section 4, vector calculus)."""
+        r = self._derivative_call("sphere_poisson_divergence", (f1, f2, f3), 1,
+                                  None if out is None else (out,), workspace, self.gradient_workspace_bytes(),
+                                  stream)
+        return r[0]
+
+    def curl(self, f1, f2, f3, out=None, workspace=None, stream=None):
+        """Surface curl of the field (f1, f2, f3): three components on the grid."""
+        return self._derivative_call("sphere_poisson_curl", (f1, f2, f3), 3, out, workspace,
+                                     self.curl_workspace_bytes(), stream)
+
+    def scalar_curl(self, f, out=None, workspace=None, stream=None):
+        """Curl of a scalar function, n x grad f (eq. CurlScalarF): three components."""
+        return self._derivative_call("sphere_poisson_scalar_curl", (f,), 3, out, workspace,
+                                     self.gradient_workspace_bytes(), stream)
+
+    def vorticity(self, f1, f2, f3, out=None, workspace=None, stream=None):
+        """Vorticity (curl f) . n of the field (f1, f2, f3)."""
+        r = self._derivative_call("sphere_poisson_vorticity", (f1, f2, f3), 1,
+                                  None if out is None else (out,), workspace, self.curl_workspace_bytes(), stream)
+        return r[0]
 
     def lowrank_workspace_bytes(self, max_terms: int) -> int:
         n = ctypes.c_size_t()

@@ -45,6 +45,12 @@ EXPORTED = (
     "sphere_poisson_sum2",
     "sphere_poisson_gradient_workspace_size",
     "sphere_poisson_tangential_gradient",
+    "sphere_poisson_curl_workspace_size",
+    "sphere_poisson_set_chop",
+    "sphere_poisson_divergence",
+    "sphere_poisson_curl",
+    "sphere_poisson_scalar_curl",
+    "sphere_poisson_vorticity",
     "sphere_poisson_lowrank_workspace_size",
     "sphere_poisson_lowrank_ge",
     "sphere_poisson_solve_lowrank",
@@ -96,6 +102,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.sphere_poisson_sum2.argtypes = [vp, vp, vp, vp, sz, vp]
     lib.sphere_poisson_gradient_workspace_size.argtypes = [vp, psz]
     lib.sphere_poisson_tangential_gradient.argtypes = [vp, vp, vp, vp, vp, vp, sz, vp]
+    lib.sphere_poisson_curl_workspace_size.argtypes = [vp, psz]
+    lib.sphere_poisson_set_chop.argtypes = [vp, ctypes.c_double]
+    lib.sphere_poisson_divergence.argtypes = [vp, vp, vp, vp, vp, vp, sz, vp]
+    lib.sphere_poisson_curl.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    lib.sphere_poisson_scalar_curl.argtypes = [vp, vp, vp, vp, vp, vp, sz, vp]
+    lib.sphere_poisson_vorticity.argtypes = [vp, vp, vp, vp, vp, vp, sz, vp]
     lib.sphere_poisson_lowrank_workspace_size.argtypes = [vp, i32, psz]
     lib.sphere_poisson_lowrank_ge.argtypes = [vp, vp, i32, ctypes.c_double, ctypes.c_double,
                                               ctypes.POINTER(ctypes.c_int), vp, vp, vp, vp, sz, vp]

@@ -65,4 +65,16 @@ struct GePivot {
   long long index;  // i * (n/2) + (q - n/2) of the pivot (smallest index among ties)
 };
 
+// One launch of the tangential coefficient maps: output o receives +-T_c,
+// c = comp[o], of the gradient components of one input (c = 0 x, 1 y, 2 z),
+// added to its contents when bit o of acc is set.
+struct TangentialCombo {
+  cpx<double>* G[3];        // outputs (null: unused)
+  signed char comp[3];      // component of output o
+  unsigned char neg[3];     // output o takes -T_c
+  unsigned char acc;        // bit o: output o is added to
+  unsigned char need_xy;    // some output uses T0 or T1 (reads Q)
+  unsigned char need_z;     // some output uses T2
+};
+
 }  // namespace sp

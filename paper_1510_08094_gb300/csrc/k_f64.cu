@@ -95,15 +95,53 @@ void launch_batched_fp64(bool big, dim3 grid, int threads, size_t smem, cudaStre
 void launch_sum2_finish(cudaStream_t st, const cpx<double>* C, int N, int Kp, double* out) {
   k_sum2_finish<<<1, 256, 0, st>>>(C, N, Kp, out);
 }
-void launch_msin_div(cudaStream_t st, const cpx<double>* X, cpx<double>* Q, int N, int K, int Kp) {
-  const int threads = 128;
-  k_msin_div<<<(2 * Kp + threads - 1) / threads, threads, 0, st>>>(X, Q, N, K, Kp);
+size_t msin_scratch_bytes(int N, int Kp) {
+  const size_t chunks = (size_t)(N + kMsinRows - 1) / kMsinRows;
+  return 2 * chunks * (size_t)Kp * sizeof(cpx<double>);
 }
-void launch_tangential(cudaStream_t st, const cpx<double>* X, const cpx<double>* Q, cpx<double>* G, int N, int K,
-                       int Kp, int comp) {
+void launch_msin_div(cudaStream_t st, const cpx<double>* X, cpx<double>* Q, cpx<double>* P, int N, int K, int Kp) {
+  const int threads = 128, chunks = (N + kMsinRows - 1) / kMsinRows;
+  const dim3 grid((Kp + threads - 1) / threads, chunks);
+  k_msin_partial<<<grid, threads, 0, st>>>(X, P, N, K, Kp);
+  k_msin_scan<<<(2 * Kp + threads - 1) / threads, threads, 0, st>>>(P, chunks, Kp);
+  k_msin_apply<<<grid, threads, 0, st>>>(X, P, Q, N, K, Kp);
+}
+void launch_tangential(cudaStream_t st, const cpx<double>* X, const cpx<double>* Q, const TangentialCombo& tc,
+                       int N, int K, int Kp) {
+  const int threads = 128;
+  const dim3 grid((Kp + threads - 1) / threads, std::min(N, 65535));
+  switch (tc.acc & 7) {
+    case 0: k_tangential<0><<<grid, threads, 0, st>>>(X, Q, tc, N, K, Kp); break;
+    case 1: k_tangential<1><<<grid, threads, 0, st>>>(X, Q, tc, N, K, Kp); break;
+    case 2: k_tangential<2><<<grid, threads, 0, st>>>(X, Q, tc, N, K, Kp); break;
+    case 3: k_tangential<3><<<grid, threads, 0, st>>>(X, Q, tc, N, K, Kp); break;
+    case 4: k_tangential<4><<<grid, threads, 0, st>>>(X, Q, tc, N, K, Kp); break;
+    case 5: k_tangential<5><<<grid, threads, 0, st>>>(X, Q, tc, N, K, Kp); break;
+    case 6: k_tangential<6><<<grid, threads, 0, st>>>(X, Q, tc, N, K, Kp); break;
+    default: k_tangential<7><<<grid, threads, 0, st>>>(X, Q, tc, N, K, Kp); break;
+  }
+}
+void launch_coeff_chop(cudaStream_t st, cpx<double>* X, int N, int K, int Kp, unsigned long long* mx,
+                       double rtol) {
   const int threads = 256;
-  const size_t total = (size_t)N * Kp;
-  k_tangential<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(X, Q, G, N, K, Kp, comp);
+  cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st);
+  const dim3 grid((Kp + threads - 1) / threads, std::min(N, 128));
+  k_coeff_absmax<<<grid, threads, 0, st>>>(X, N, K, Kp, mx);
+  k_coeff_chop<<<grid, threads, 0, st>>>(X, N, K, Kp, mx, rtol);
+}
+namespace {
+dim3 grid_points(int nt, int nl, int threads) {
+  return dim3((nl + threads - 1) / threads, std::min(nt, 4096));
+}
+}  // namespace
+void launch_cross_normal(cudaStream_t st, double* a, double* b, double* c, const double* geo, int nt, int nl) {
+  const int threads = 256;
+  k_cross_normal<<<grid_points(nt, nl, threads), threads, 0, st>>>(a, b, c, geo, nt, nl);
+}
+void launch_normal_dot(cudaStream_t st, const double* a, const double* b, const double* c, double* out,
+                       const double* geo, int nt, int nl) {
+  const int threads = 256;
+  k_normal_dot<<<grid_points(nt, nl, threads), threads, 0, st>>>(a, b, c, out, geo, nt, nl);
 }
 
 void launch_ge_pivot(cudaStream_t st, const double* e, int nt, int n, GePivot* part, int nparts, GePivot* out) {

@@ -1115,24 +1115,117 @@ __global__ void k_sum2_finish(const cpx<double>* __restrict__ C, int N, int Kp, 
 // recurrence x_{j-1} = x_{j+1} + 2i a_j down from the top of the window with
 // x_N = x_{N-1} = 0, i.e. x_j = 2i sum_{r = j+1, j+3, ... <= N-1} a_r
 // = -2k sum_{r} X_{r,k}.  This is M_sin^{-1} a whenever the quotient lies in the
-// window (band-limited f).  One thread per (column, parity class of j).
+// window (band-limited f).
+// The suffix sums are taken over row chunks of kMsinRows rows so that every
+// (chunk, column) has a thread: pass 1 sums each chunk's even and odd rows into
+// P[2c][k], P[2c+1][k]; a scan turns those into the sums over the chunks above
+// (one thread per column and parity); pass 3 walks each chunk downwards writing
+// Q, carrying the sums already scaled by -2k (one FMA per coefficient).
+// Grid of passes 1 and 3: (ceil(Kp / blockDim.x), chunks).
 // ---------------------------------------------------------------------------
-__global__ void k_msin_div(const cpx<double>* __restrict__ X, cpx<double>* __restrict__ Q, int N, int K,
-                           int Kp) {
+constexpr int kMsinRows = 64;
+
+__global__ void k_msin_partial(const cpx<double>* __restrict__ X, cpx<double>* __restrict__ P, int N, int K,
+                               int Kp) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= Kp) return;
+  const int c = blockIdx.y, j0 = c * kMsinRows, j1 = min(N, j0 + kMsinRows);
+  cpx<double> se = {0.0, 0.0}, so = {0.0, 0.0};
+  if (k < K - 1) {                           // k = L (Nyquist) and padding columns are zero
+#pragma unroll 4
+    for (int j = j0; j < j1; j += 2) {       // j0 is even
+      se = se + X[(size_t)j * Kp + k];
+      if (j + 1 < j1) so = so + X[(size_t)(j + 1) * Kp + k];
+    }
+  }
+  P[(size_t)(2 * c) * Kp + k] = se;
+  P[(size_t)(2 * c + 1) * Kp + k] = so;
+}
+
+// P[2c + par][k] <- sum over chunks c' > c of the chunk sums (exclusive suffix)
+__global__ void k_msin_scan(cpx<double>* __restrict__ P, int chunks, int Kp) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= 2 * Kp) return;
-  const int cls = idx >= Kp, k = cls ? idx - Kp : idx;
-  int j = N - 1;
-  if ((j & 1) != cls) --j;
-  const double scale = -2.0 * (double)k;
-  cpx<double> S = {0.0, 0.0};
-  const bool live = k < K - 1;                 // k = L (Nyquist) and padding columns are zero
-  for (; j >= 0; j -= 2) {
-    if (live && j + 1 < N) S = S + X[(size_t)(j + 1) * Kp + k];
-    Q[(size_t)j * Kp + k] = live ? scale * S : cpx<double>{0.0, 0.0};
+  const int par = idx >= Kp, k = par ? idx - Kp : idx;
+  cpx<double> run = {0.0, 0.0};
+  for (int c = chunks - 1; c >= 0; --c) {
+    cpx<double>& slot = P[(size_t)(2 * c + par) * Kp + k];
+    const cpx<double> t = slot;
+    slot = run;
+    run = run + t;
   }
 }
 
+__global__ void k_msin_apply(const cpx<double>* __restrict__ X, const cpx<double>* __restrict__ P,
+                             cpx<double>* __restrict__ Q, int N, int K, int Kp) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= Kp) return;
+  const int c = blockIdx.y, j0 = c * kMsinRows, j1 = min(N, j0 + kMsinRows);
+  const bool live = k < K - 1;
+  const double scale = -2.0 * (double)k;
+  // -2k times the sums of the even / odd rows r >= j1
+  cpx<double> se = {0.0, 0.0}, so = {0.0, 0.0};
+  if (live) {
+    se = scale * P[(size_t)(2 * c) * Kp + k];
+    so = scale * P[(size_t)(2 * c + 1) * Kp + k];
+  }
+#pragma unroll 4
+  for (int j = j1 - 1; j >= j0; --j) {
+    // Q_j takes the rows above j of the other parity
+    Q[(size_t)j * Kp + k] = (j & 1) ? se : so;
+    if (live) {
+      const cpx<double> x = X[(size_t)j * Kp + k];
+      cpx<double>& s = (j & 1) ? so : se;
+      s = {fma(scale, x.re, s.re), fma(scale, x.im, s.im)};
+    }
+  }
+}
+
+// Coefficient chop (the derivative operators' optional truncation): the
+// coefficients with |X_jk| <= rtol max |X| are set to zero before the maps act,
+// so that rounding noise in modes a band-limited input does not have is not
+// amplified by the division by sin theta.  Live columns k < K - 1 only; grid
+// (ceil(Kp / blockDim.x), rows) with the rows striding over j.
+// max |X_jk|^2 into *mx as the bits of a non-negative double (atomicMax on the
+// bit pattern orders non-negative doubles); blockDim.x a multiple of 32
+__global__ void k_coeff_absmax(const cpx<double>* __restrict__ X, int N, int K, int Kp,
+                               unsigned long long* __restrict__ mx) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  double m = 0.0;
+  if (k < K - 1) {
+    for (int j = blockIdx.y; j < N; j += gridDim.y) {
+      const cpx<double> v = X[(size_t)j * Kp + k];
+      m = fmax(m, fma(v.re, v.re, v.im * v.im));
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
+    atomicMax(mx, (unsigned long long)__double_as_longlong(t));
+  }
+}
+// zero |X_jk|^2 <= rtol^2 max |X|^2
+__global__ void k_coeff_chop(cpx<double>* __restrict__ X, int N, int K, int Kp,
+                             const unsigned long long* __restrict__ mx, double rtol) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K - 1) return;
+  const double thr = rtol * rtol * __longlong_as_double((long long)*mx);
+  for (int j = blockIdx.y; j < N; j += gridDim.y) {
+    cpx<double>& v = X[(size_t)j * Kp + k];
+    const cpx<double> x = v;
+    if (fma(x.re, x.re, x.im * x.im) <= thr) v = {0.0, 0.0};
+  }
+}
+
+// x with its sign flipped when c is set: an integer operation on the sign bit,
+// which keeps conditional negations off the FP64 pipe
+__device__ __forceinline__ double flip_if(double x, bool c) {
+  return __longlong_as_double(__double_as_longlong(x) ^ ((long long)c << 63));
+}
 // X_{i,k} for i in [-1, N] (the BMC mirror at i = -1, zero at i = N and in the
 // Nyquist column)
 __device__ __forceinline__ cpx<double> x_at(const cpx<double>* __restrict__ X, int i, int k, int N, int K,
@@ -1141,61 +1234,118 @@ __device__ __forceinline__ cpx<double> x_at(const cpx<double>* __restrict__ X, i
   if (mirror) i = 1;
   if (k >= K - 1 || i >= N) return {0.0, 0.0};
   const cpx<double> v = X[(size_t)i * Kp + k];
-  return (mirror && (k & 1)) ? cpx<double>{-v.re, -v.im} : v;
+  const bool f = mirror && (k & 1);
+  return {flip_if(v.re, f), flip_if(v.im, f)};
 }
-// C = cos theta d/dtheta f: C_j = (D_{j-1} + D_{j+1})/2, D_i = i i X_i; columns
-// k = -1 by the real-function symmetry C_{j,-1} = conj(C_{j,1})
+// s C with C = cos theta d/dtheta f: C_j = (D_{j-1} + D_{j+1})/2, D_i = i i X_i;
+// columns k = -1 by the real-function symmetry C_{j,-1} = conj(C_{j,1}).
+// wm = s (j-1)/2, wp = s (j+1)/2.
 __device__ __forceinline__ cpx<double> c_at(const cpx<double>* __restrict__ X, int j, int k, int N, int K,
-                                            int Kp) {
+                                            int Kp, double wm, double wp) {
   const int kk = k < 0 ? 1 : k;
   const cpx<double> a = x_at(X, j - 1, kk, N, K, Kp), b = x_at(X, j + 1, kk, N, K, Kp);
-  const double wa = 0.5 * (double)(j - 1), wb = 0.5 * (double)(j + 1);
-  // i (wa a + wb b), conjugated for k = -1
-  const cpx<double> t = {wa * a.re + wb * b.re, wa * a.im + wb * b.im};
-  return k < 0 ? cpx<double>{-t.im, -t.re} : cpx<double>{-t.im, t.re};
+  // i (wm a + wp b), conjugated for k = -1
+  const cpx<double> t = {fma(wm, a.re, wp * b.re), fma(wm, a.im, wp * b.im)};
+  return {-t.im, flip_if(t.re, k < 0)};
 }
 __device__ __forceinline__ cpx<double> q_at(const cpx<double>* __restrict__ Q, int j, int k, int K, int Kp) {
   if (k >= K - 1) return {0.0, 0.0};
-  if (k < 0) {
-    cpx<double> v = Q[(size_t)j * Kp + 1];
-    return {v.re, -v.im};
-  }
-  return Q[(size_t)j * Kp + k];
+  const bool c = k < 0;
+  const cpx<double> v = Q[(size_t)j * Kp + (c ? 1 : k)];
+  return {v.re, flip_if(v.im, c)};
 }
 
-// Coefficients of one Cartesian component of the surface gradient:
-//   comp 0: d^t/dx = -sin(lambda) Q + cos(lambda) C
-//   comp 1: d^t/dy =  cos(lambda) Q + sin(lambda) C
-//   comp 2: d^t/dz = -sin(theta) d/dtheta f, G_j = ((j+1) X_{j+1} - (j-1) X_{j-1})/2
-//           (the chain-rule sign for the colatitude theta)
+// Coefficients of the Cartesian components of the surface gradient:
+//   T0: d^t/dx = -sin(lambda) Q + cos(lambda) C
+//   T1: d^t/dy =  cos(lambda) Q + sin(lambda) C
+//   T2: d^t/dz = -sin(theta) d/dtheta f, T2_j = ((j+1) X_{j+1} - (j-1) X_{j-1})/2
+//       (the chain-rule sign for the colatitude theta)
 // with cos(lambda) g -> (g_{k-1} + g_{k+1})/2, sin(lambda) g -> (i/2)(g_{k+1} - g_{k-1}).
-// One thread per (j, k); the Nyquist and padding columns are written as zero.
+// One launch forms up to three outputs from one input, output o receiving
+// +-T_{comp[o]}, added to its contents when bit o of ACC is set: the gradient
+// (three outputs), a divergence term or two curl terms; T0 and T1 share their
+// loads and sums.  Thread per (j, k), grid (ceil(Kp / blockDim.x), rows) with
+// the rows striding over j; the Nyquist and padding columns receive zero terms.
+// ---------------------------------------------------------------------------
+// (the launch descriptor TangentialCombo is declared with the batched-plan types)
+template <int ACC>
 __global__ void k_tangential(const cpx<double>* __restrict__ X, const cpx<double>* __restrict__ Q,
-                             cpx<double>* __restrict__ G, int N, int K, int Kp, int comp) {
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (size_t)N * Kp) return;
-  const int j = (int)(idx / Kp), k = (int)(idx - (size_t)j * Kp);
-  cpx<double> g = {0.0, 0.0};
-  if (k < K - 1) {
-    if (comp == 2) {
-      const cpx<double> a = x_at(X, j + 1, k, N, K, Kp), b = x_at(X, j - 1, k, N, K, Kp);
-      const double wa = 0.5 * (double)(j + 1), wb = 0.5 * (double)(j - 1);
-      g = {wa * a.re - wb * b.re, wa * a.im - wb * b.im};
-    } else {
-      const cpx<double> qp = q_at(Q, j, k + 1, K, Kp), qm = q_at(Q, j, k - 1, K, Kp);
-      const cpx<double> cp = c_at(X, j, k + 1, N, K, Kp), cm = c_at(X, j, k - 1, N, K, Kp);
-      if (comp == 0) {
-        // -(i/2)(qp - qm) + (cp + cm)/2
-        const cpx<double> d = qp - qm;
-        g = {0.5 * (d.im + cp.re + cm.re), 0.5 * (-d.re + cp.im + cm.im)};
-      } else {
-        // (qp + qm)/2 + (i/2)(cp - cm)
-        const cpx<double> d = cp - cm;
-        g = {0.5 * (qp.re + qm.re - d.im), 0.5 * (qp.im + qm.im + d.re)};
+                             const TangentialCombo tc, int N, int K, int Kp) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= Kp) return;
+  const bool live = k < K - 1;
+  for (int j = blockIdx.y; j < N; j += gridDim.y) {
+    cpx<double> T0 = {0.0, 0.0}, T1 = {0.0, 0.0}, T2 = {0.0, 0.0};
+    if (live) {
+      const double wm = fma(0.5, (double)j, -0.5), wp = wm + 1.0;   // (j -+ 1)/2
+      if (tc.need_xy) {
+        const cpx<double> qp = q_at(Q, j, k + 1, K, Kp), qm = q_at(Q, j, k - 1, K, Kp);
+        // C/2 at k +- 1 (half weights), so that T0 and T1 take one FMA per part
+        const double hm = 0.5 * wm, hp = 0.5 * wp;
+        const cpx<double> cp = c_at(X, j, k + 1, N, K, Kp, hm, hp), cm = c_at(X, j, k - 1, N, K, Kp, hm, hp);
+        const cpx<double> dq = qp - qm, sc = cp + cm, sq = qp + qm, dc = cp - cm;
+        T0 = {fma(0.5, dq.im, sc.re), fma(-0.5, dq.re, sc.im)};   // -(i/2) dq + (cp + cm)/2
+        T1 = {fma(0.5, sq.re, -dc.im), fma(0.5, sq.im, dc.re)};   // sq/2 + (i/2)(cp - cm)
+      }
+      if (tc.need_z) {
+        const cpx<double> a = x_at(X, j + 1, k, N, K, Kp), b = x_at(X, j - 1, k, N, K, Kp);
+        T2 = {fma(wp, a.re, -wm * b.re), fma(wp, a.im, -wm * b.im)};
       }
     }
+    const size_t o = (size_t)j * Kp + k;
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+      if (!tc.G[g]) continue;
+      const int c = tc.comp[g];
+      cpx<double> t = c == 0 ? T0 : (c == 1 ? T1 : T2);
+      const bool ng = tc.neg[g] != 0;
+      t = {flip_if(t.re, ng), flip_if(t.im, ng)};
+      if (ACC & (1 << g)) t = tc.G[g][o] + t;
+      tc.G[g][o] = t;
+    }
   }
-  G[idx] = g;
+}
+
+// ---------------------------------------------------------------------------
+// Pointwise products with the unit normal n = (x, y, z) of eq.
+// sphericalCoordinates, x = cos(lambda) sin(theta), y = sin(lambda) sin(theta),
+// z = cos(theta), on the n_theta x n_lambda grid.  geo holds sin(theta_i),
+// cos(theta_i) (n_theta each), then cos(lambda_q), sin(lambda_q) (n_lambda
+// each).  Grid (ceil(n_lambda / blockDim.x), rows), rows striding over i.
+// ---------------------------------------------------------------------------
+struct Normal {
+  double x, y, z;
+};
+__device__ __forceinline__ Normal normal_at(const double* __restrict__ geo, int nt, int nl, int i, int q) {
+  const double st = geo[i], ct = geo[nt + i], cl = geo[2 * nt + q], sl = geo[2 * nt + nl + q];
+  return {cl * st, sl * st, ct};
+}
+// (a, b, c) <- n x (a, b, c): the curl of a scalar function (eq. CurlScalarF)
+// from its gradient
+__global__ void k_cross_normal(double* __restrict__ a, double* __restrict__ b, double* __restrict__ c,
+                               const double* __restrict__ geo, int nt, int nl) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nl) return;
+  for (int i = blockIdx.y; i < nt; i += gridDim.y) {
+    const Normal n = normal_at(geo, nt, nl, i, q);
+    const size_t o = (size_t)i * nl + q;
+    const double va = a[o], vb = b[o], vc = c[o];
+    a[o] = n.y * vc - n.z * vb;
+    b[o] = n.z * va - n.x * vc;
+    c[o] = n.x * vb - n.y * va;
+  }
+}
+// out = x a + y b + z c (the vorticity from the curl); out may be c
+__global__ void k_normal_dot(const double* __restrict__ a, const double* __restrict__ b, const double* c,
+                             double* out, const double* __restrict__ geo, int nt, int nl) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nl) return;
+  for (int i = blockIdx.y; i < nt; i += gridDim.y) {
+    // sin(theta) (cos(lambda) a + sin(lambda) b) + cos(theta) c
+    const double st = geo[i], ct = geo[nt + i], cl = geo[2 * nt + q], sl = geo[2 * nt + nl + q];
+    const size_t o = (size_t)i * nl + q;
+    out[o] = fma(st, fma(cl, a[o], sl * b[o]), ct * c[o]);
+  }
 }
 
 // ---------------------------------------------------------------------------

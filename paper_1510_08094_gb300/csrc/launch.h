@@ -85,11 +85,21 @@ void launch_batched_refine(bool big, dim3 grid, int threads, size_t smem, cudaSt
 
 // surface integral from the k = 0 coefficient column (one CTA, result to device memory)
 void launch_sum2_finish(cudaStream_t st, const cpx<double>* C, int N, int Kp, double* out);
-// tangential derivatives: Q = (1/sin theta) d/dlambda in coefficients, then the
-// coefficients of one gradient component (0 x, 1 y, 2 z) into G
-void launch_msin_div(cudaStream_t st, const cpx<double>* X, cpx<double>* Q, int N, int K, int Kp);
-void launch_tangential(cudaStream_t st, const cpx<double>* X, const cpx<double>* Q, cpx<double>* G, int N, int K,
-                       int Kp, int comp);
+// tangential derivatives: Q = (1/sin theta) d/dlambda in coefficients (the
+// scratch array P of msin_scratch_bytes bytes takes the chunk sums), then the
+// signed sums of gradient components that `tc` describes
+size_t msin_scratch_bytes(int N, int Kp);
+void launch_msin_div(cudaStream_t st, const cpx<double>* X, cpx<double>* Q, cpx<double>* P, int N, int K, int Kp);
+void launch_tangential(cudaStream_t st, const cpx<double>* X, const cpx<double>* Q, const TangentialCombo& tc,
+                       int N, int K, int Kp);
+// X_jk = 0 where |X_jk| <= rtol max |X| (mx: one device word of scratch)
+void launch_coeff_chop(cudaStream_t st, cpx<double>* X, int N, int K, int Kp, unsigned long long* mx,
+                       double rtol);
+// pointwise with the unit normal on the grid (geo: sin, cos theta; cos, sin lambda):
+// (a, b, c) <- n x (a, b, c), and out = n . (a, b, c) (out may be c)
+void launch_cross_normal(cudaStream_t st, double* a, double* b, double* c, const double* geo, int nt, int nl);
+void launch_normal_dot(cudaStream_t st, const double* a, const double* b, const double* c, double* out,
+                       const double* geo, int nt, int nl);
 
 // structure-preserving GE: pivot search (partials + final into *out) and one
 // step (extract the term's column and row, update the residual)

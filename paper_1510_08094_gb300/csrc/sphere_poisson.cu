@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <fstream>
+#include <initializer_list>
 #include <map>
 #include <mutex>
 #include <new>
@@ -193,6 +194,8 @@ struct sp_plan_s {
   double* row_scale;     // sin^2(theta_i)/n
   double* row_plain;     // 1/n (transforms without the sin^2 weight)
   double* sin2;          // sin^2(theta_i) (the low-rank right-hand side)
+  double* geo;           // sin, cos theta_i; cos, sin lambda_q (the unit normal on the grid)
+  double chop;           // relative coefficient threshold of the derivative operators (0: off)
   void* row_scale_t;     // the same in float (SP_FP32) or double-float (SP_FP32_REFINE)
   // the same tables in float (SP_FP32) or double-float (SP_FP32_REFINE)
   void* tw_row_t;
@@ -762,6 +765,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   size_t o_scale = take(p->nt * sizeof(double));
   size_t o_plain = take(p->nt * sizeof(double));
   size_t o_sin2 = take(p->nt * sizeof(double));
+  size_t o_geo = take((size_t)(2 * p->nt + 2 * p->nl) * sizeof(double));
   size_t o_perm_row = take(p->L * sizeof(int)), o_perm_col = take(p->N * sizeof(int));
   size_t o_t_tw_row = take(t_tw_row.size()), o_t_tw_col = take(t_tw_col.size());
   size_t o_t_post_row = take(t_post_row.size()), o_t_post_col = take(t_post_col.size());
@@ -795,6 +799,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   p->row_scale = reinterpret_cast<double*>(base + o_scale);
   p->row_plain = reinterpret_cast<double*>(base + o_plain);
   p->sin2 = reinterpret_cast<double*>(base + o_sin2);
+  p->geo = reinterpret_cast<double*>(base + o_geo);
   p->perm_row = reinterpret_cast<int*>(base + o_perm_row);
   p->perm_col = reinterpret_cast<int*>(base + o_perm_col);
   p->tw_row_t = base + o_t_tw_row;
@@ -834,6 +839,21 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
       s2[i] = im * im;
     }
     up(p->sin2, s2.data(), p->nt * sizeof(double), "copy sin2");
+    // theta_i = 2 pi (2i + 1) / (4N), lambda_q = 2 pi q / n - pi
+    std::vector<double> geo(2 * p->nt + 2 * p->nl);
+    for (int i = 0; i < p->nt; ++i) {
+      double re, im;
+      unit_root(2 * i + 1, 4L * p->N, &re, &im);
+      geo[i] = -im;
+      geo[p->nt + i] = re;
+    }
+    for (int q = 0; q < p->nl; ++q) {
+      double re, im;
+      unit_root(q, p->nl, &re, &im);
+      geo[2 * p->nt + q] = -re;
+      geo[2 * p->nt + p->nl + q] = im;
+    }
+    up(p->geo, geo.data(), geo.size() * sizeof(double), "copy geo");
   }
   up(p->perm_row, perm_row.data(), p->L * sizeof(int), "copy perm_row");
   up(p->perm_col, perm_col.data(), p->N * sizeof(int), "copy perm_col");
@@ -1652,43 +1672,187 @@ int sphere_poisson_sum2(sp_plan_t plan, const double* f, double* result, void* w
   return e == cudaSuccess ? SP_OK : cuda_fail(e, "sum2 launch");
 }
 
+namespace {
+// workspace of the derivative operators: `spectra` half spectra of N x Kp
+// complex doubles, then the chunk sums of the division by sin theta
+size_t spectrum_bytes(sp_plan_t p) { return ((size_t)p->N * p->Kp * sizeof(cpx<double>) + 255) & ~(size_t)255; }
+size_t derivative_workspace(sp_plan_t p, int spectra) {
+  // + 256 bytes for the chop's maximum
+  return spectra * spectrum_bytes(p) + ((sp::msin_scratch_bytes(p->N, p->Kp) + 255) & ~(size_t)255) + 256;
+}
+int check_derivative_call(sp_plan_t plan, int spectra, std::initializer_list<const void*> ptrs, void* workspace,
+                          size_t workspace_bytes) {
+  if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
+  for (const void* q : ptrs)
+    if (!q) return SP_ERR_NULL;
+  if (!workspace) return SP_ERR_NULL;
+  if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
+  uintptr_t bits = (uintptr_t)workspace;
+  for (const void* q : ptrs) bits |= (uintptr_t)q;
+  if (bits & 15) return SP_ERR_MISALIGNED;
+  if (workspace_bytes < derivative_workspace(plan, spectra)) return SP_ERR_WORKSPACE;
+  return SP_OK;
+}
+struct DerivSpace {
+  cpx<double>* X;   // coefficients of the current input
+  cpx<double>* Q;   // (1/sin theta) d/dlambda of it
+  cpx<double>* P;   // chunk sums of the division
+  cpx<double>* G[3];
+  unsigned long long* mx;  // max |X| of the chop
+};
+DerivSpace derivative_space(sp_plan_t p, void* workspace, int spectra) {
+  char* b = static_cast<char*>(workspace);
+  const size_t one = spectrum_bytes(p);
+  DerivSpace d;
+  d.X = reinterpret_cast<cpx<double>*>(b);
+  d.Q = reinterpret_cast<cpx<double>*>(b + one);
+  for (int c = 0; c < 3; ++c) d.G[c] = c + 2 < spectra ? reinterpret_cast<cpx<double>*>(b + (2 + c) * one) : nullptr;
+  d.P = reinterpret_cast<cpx<double>*>(b + spectra * one);
+  d.mx = reinterpret_cast<unsigned long long*>(b + spectra * one +
+                                               ((sp::msin_scratch_bytes(p->N, p->Kp) + 255) & ~(size_t)255));
+  return d;
+}
+// X = coeffs2(f), Q = (1/sin theta) d/dlambda f in coefficients
+void enqueue_derivative_input(sp_plan_t p, const double* f, const DerivSpace& d, bool need_q, cudaStream_t st) {
+  enqueue_coeffs2(p, f, d.X, p->K, st);
+  if (p->chop > 0.0) sp::launch_coeff_chop(st, d.X, p->N, p->K, p->Kp, d.mx, p->chop);
+  if (need_q) sp::launch_msin_div(st, d.X, d.Q, d.P, p->N, p->K, p->Kp);
+}
+// one launch of the coefficient maps on the current input: each output takes
+// one signed component ("+x", "-z": T0, -T2), added to its contents when acc
+struct ComboOut {
+  cpx<double>* G;
+  const char* term;
+  bool acc;
+};
+void enqueue_combo(sp_plan_t p, const DerivSpace& d, std::initializer_list<ComboOut> outs, cudaStream_t st) {
+  sp::TangentialCombo tc = {};
+  int o = 0;
+  for (const ComboOut& c : outs) {
+    const int comp = c.term[1] - 'x';
+    tc.G[o] = c.G;
+    tc.comp[o] = (signed char)comp;
+    tc.neg[o] = c.term[0] == '-';
+    if (c.acc) tc.acc |= (unsigned char)(1u << o);
+    if (comp < 2) tc.need_xy = 1;
+    else tc.need_z = 1;
+    ++o;
+  }
+  sp::launch_tangential(st, d.X, d.Q, tc, p->N, p->K, p->Kp);
+}
+// values on the grid of the coefficients G (destroys G)
+void enqueue_values(sp_plan_t p, cpx<double>* G, double* out, cudaStream_t st) {
+  launch_theta_inverse_x<double>(p, false, st, G, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft, p->tw_col,
+                                 p->perm_col, p->post_col, 1.0 / p->N, 2);
+  launch_rows_inverse_x<double>(p, false, st, G, out, p->nt, p->nl, p->Kp, p->rows_per_cta, p->row_fft,
+                                p->tw_row, p->perm_row, p->post_row, p->row_scale, p->row_scale, nullptr);
+}
+// the coefficients of the three curl components of (f1, f2, f3) into d.G[0..2]:
+// (d/dy f3 - d/dz f2, d/dz f1 - d/dx f3, d/dx f2 - d/dy f1)
+void enqueue_curl_coefficients(sp_plan_t p, const double* f1, const double* f2, const double* f3,
+                               const DerivSpace& d, cudaStream_t st) {
+  enqueue_derivative_input(p, f1, d, true, st);
+  enqueue_combo(p, d, {{d.G[1], "+z", false}, {d.G[2], "-y", false}}, st);
+  enqueue_derivative_input(p, f2, d, true, st);
+  enqueue_combo(p, d, {{d.G[0], "-z", false}, {d.G[2], "+x", true}}, st);
+  enqueue_derivative_input(p, f3, d, true, st);
+  enqueue_combo(p, d, {{d.G[0], "+y", true}, {d.G[1], "-x", true}}, st);
+}
+int launch_status(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SP_OK : cuda_fail(e, what);
+}
+}  // namespace
+
 int sphere_poisson_gradient_workspace_size(sp_plan_t plan, size_t* workspace_bytes) {
   if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
   if (!workspace_bytes) return SP_ERR_NULL;
   if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
-  const size_t one = ((size_t)plan->N * plan->Kp * sizeof(cpx<double>) + 255) & ~(size_t)255;
-  *workspace_bytes = 3 * one;
+  *workspace_bytes = derivative_workspace(plan, 5);
+  return SP_OK;
+}
+
+int sphere_poisson_curl_workspace_size(sp_plan_t plan, size_t* workspace_bytes) {
+  if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
+  if (!workspace_bytes) return SP_ERR_NULL;
+  if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
+  *workspace_bytes = derivative_workspace(plan, 5);
+  return SP_OK;
+}
+
+int sphere_poisson_set_chop(sp_plan_t plan, double rtol) {
+  if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
+  if (!(rtol >= 0.0 && rtol < 1.0)) return SP_ERR_BAD_ARG;  // also rejects NaN
+  plan->chop = rtol;
   return SP_OK;
 }
 
 int sphere_poisson_tangential_gradient(sp_plan_t plan, const double* f, double* gx, double* gy, double* gz,
                                        void* workspace, size_t workspace_bytes, void* stream) {
-  if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
-  if (!f || !gx || !gy || !gz || !workspace) return SP_ERR_NULL;
-  if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
-  if (((uintptr_t)f | (uintptr_t)gx | (uintptr_t)gy | (uintptr_t)gz | (uintptr_t)workspace) & 15)
-    return SP_ERR_MISALIGNED;
-  size_t need = 0;
-  sphere_poisson_gradient_workspace_size(plan, &need);
-  if (workspace_bytes < need) return SP_ERR_WORKSPACE;
+  int rc = check_derivative_call(plan, 5, {f, gx, gy, gz}, workspace, workspace_bytes);
+  if (rc != SP_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const DerivSpace d = derivative_space(plan, workspace, 5);
+  enqueue_derivative_input(plan, f, d, true, st);
+  enqueue_combo(plan, d, {{d.G[0], "+x", false}, {d.G[1], "+y", false}, {d.G[2], "+z", false}}, st);
+  double* out[3] = {gx, gy, gz};
+  for (int c = 0; c < 3; ++c) enqueue_values(plan, d.G[c], out[c], st);
+  return launch_status("tangential gradient launch");
+}
+
+int sphere_poisson_divergence(sp_plan_t plan, const double* f1, const double* f2, const double* f3, double* div,
+                              void* workspace, size_t workspace_bytes, void* stream) {
+  int rc = check_derivative_call(plan, 3, {f1, f2, f3, div}, workspace, workspace_bytes);
+  if (rc != SP_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const DerivSpace d = derivative_space(plan, workspace, 3);
+  const double* f[3] = {f1, f2, f3};
+  const char* terms[3] = {"+x", "+y", "+z"};
+  for (int c = 0; c < 3; ++c) {
+    enqueue_derivative_input(plan, f[c], d, c < 2, st);  // d/dz needs no division
+    enqueue_combo(plan, d, {{d.G[0], terms[c], c > 0}}, st);
+  }
+  enqueue_values(plan, d.G[0], div, st);
+  return launch_status("divergence launch");
+}
+
+int sphere_poisson_curl(sp_plan_t plan, const double* f1, const double* f2, const double* f3, double* c1,
+                        double* c2, double* c3, void* workspace, size_t workspace_bytes, void* stream) {
+  int rc = check_derivative_call(plan, 5, {f1, f2, f3, c1, c2, c3}, workspace, workspace_bytes);
+  if (rc != SP_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const DerivSpace d = derivative_space(plan, workspace, 5);
+  enqueue_curl_coefficients(plan, f1, f2, f3, d, st);
+  double* out[3] = {c1, c2, c3};
+  for (int c = 0; c < 3; ++c) enqueue_values(plan, d.G[c], out[c], st);
+  return launch_status("curl launch");
+}
+
+int sphere_poisson_scalar_curl(sp_plan_t plan, const double* f, double* c1, double* c2, double* c3,
+                               void* workspace, size_t workspace_bytes, void* stream) {
+  int rc = sphere_poisson_tangential_gradient(plan, f, c1, c2, c3, workspace, workspace_bytes, stream);
+  if (rc != SP_OK) return rc;
+  sp::launch_cross_normal(static_cast<cudaStream_t>(stream), c1, c2, c3, plan->geo, plan->nt, plan->nl);
+  return launch_status("scalar curl launch");
+}
+
+int sphere_poisson_vorticity(sp_plan_t plan, const double* f1, const double* f2, const double* f3, double* zeta,
+                             void* workspace, size_t workspace_bytes, void* stream) {
+  int rc = check_derivative_call(plan, 5, {f1, f2, f3, zeta}, workspace, workspace_bytes);
+  if (rc != SP_OK) return rc;
   sp_plan_t p = plan;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t one = need / 3;
-  cpx<double>* X = static_cast<cpx<double>*>(workspace);
-  cpx<double>* Q = reinterpret_cast<cpx<double>*>(static_cast<char*>(workspace) + one);
-  cpx<double>* G = reinterpret_cast<cpx<double>*>(static_cast<char*>(workspace) + 2 * one);
-  enqueue_coeffs2(p, f, X, p->K, st);
-  sp::launch_msin_div(st, X, Q, p->N, p->K, p->Kp);
-  double* out[3] = {gx, gy, gz};
-  for (int c = 0; c < 3; ++c) {
-    sp::launch_tangential(st, X, Q, G, p->N, p->K, p->Kp, c);
-    launch_theta_inverse_x<double>(p, false, st, G, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft, p->tw_col,
-                                   p->perm_col, p->post_col, 1.0 / p->N, 2);
-    launch_rows_inverse_x<double>(p, false, st, G, out[c], p->nt, p->nl, p->Kp, p->rows_per_cta, p->row_fft,
-                                  p->tw_row, p->perm_row, p->post_row, p->row_scale, p->row_scale, nullptr);
-  }
-  cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? SP_OK : cuda_fail(e, "tangential gradient launch");
+  const DerivSpace d = derivative_space(p, workspace, 5);
+  enqueue_curl_coefficients(p, f1, f2, f3, d, st);
+  // the first two curl components land in the (now free) X and Q spectra as
+  // real grids (N Kp 16 >= n_theta n_lambda 8 bytes), the third in zeta
+  double* t1 = reinterpret_cast<double*>(d.X);
+  double* t2 = reinterpret_cast<double*>(d.Q);
+  enqueue_values(p, d.G[0], t1, st);
+  enqueue_values(p, d.G[1], t2, st);
+  enqueue_values(p, d.G[2], zeta, st);
+  sp::launch_normal_dot(st, t1, t2, zeta, zeta, p->geo, p->nt, p->nl);
+  return launch_status("vorticity launch");
 }
 
 namespace {

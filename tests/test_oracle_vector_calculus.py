@@ -88,3 +88,29 @@ def test_curl_of_gradient_is_the_scalar_curl():
     for a, b in zip(c, s):
         assert np.abs(a - b).max() < 1e-11 * scale
     assert np.abs(O.vorticity(*g)).max() < 1e-11 * scale
+
+
+def test_chop_discards_only_the_small_coefficients():
+    # a harmonic plus a 1e-10 copy of a high one: with the chop at 1e-8 the
+    # gradient is that of the harmonic alone; without it the small part stays
+    nt, nl = 24, 48
+    Y = sh.synthesize(sh.single_sh_coeffs(3, 1), nt, nl).numpy()
+    H = sh.synthesize(sh.single_sh_coeffs(20, 7), nt, nl).numpy()
+    g_ref = O.tangential_gradient(Y)
+    g_chop = O.tangential_gradient(Y + 1e-10 * H, chop=1e-8)
+    g_plain = O.tangential_gradient(Y + 1e-10 * H)
+    g_h = O.tangential_gradient(H)
+    for a, b, c in zip(g_chop, O.tangential_gradient(Y, chop=1e-8), g_ref):
+        assert np.abs(a - b).max() < 1e-15
+        # the plain map carries the transforms' noise amplified (~1e-14 here)
+        assert np.abs(a - c).max() < 1e-13
+    for a, b, h in zip(g_plain, g_ref, g_h):
+        assert np.abs((a - b) - 1e-10 * h).max() < 1e-13
+        assert np.abs(1e-10 * h).max() > 1e-10
+
+
+def test_chained_rossby_haurwitz_with_chop():
+    (x, y, z), psi, _, lap = _rossby_haurwitz(16, 34)
+    u = O.scalar_curl(psi, chop=1e-14)
+    assert np.abs(O.vorticity(*u, chop=1e-14) - lap).max() < 1e-11 * np.abs(lap).max()
+    assert np.abs(O.divergence(*u, chop=1e-14)).max() < 1e-11
