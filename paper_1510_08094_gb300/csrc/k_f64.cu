@@ -149,11 +149,12 @@ void launch_ge_pivot(cudaStream_t st, const double* e, int nt, int n, GePivot* p
   k_ge_pivot_final<<<1, 1, 0, st>>>(e, n, part, nparts, out);
 }
 void launch_ge_step(cudaStream_t st, double* e, int nt, int n, int istar, int qstar, double* col, double* row,
-                    double p0, double p1, size_t total) {
+                    double p0, double p1, double* AB) {
   const int threads = 256;
   const int ext = std::max(2 * nt, n);
-  k_ge_extract<<<(ext + threads - 1) / threads, threads, 0, st>>>(e, nt, n, istar, qstar, col, row);
-  k_ge_update<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(e, nt, n, col, row, p0, p1);
+  k_ge_extract<<<(ext + threads - 1) / threads, threads, 0, st>>>(e, nt, n, istar, qstar, col, row, p0, p1, AB);
+  const dim3 grid((n + threads - 1) / threads, std::min(nt, 512));
+  k_ge_update<<<grid, threads, 0, st>>>(e, nt, n, col, AB);
 }
 void launch_lowrank_pack(cudaStream_t st, const double* cols, int terms, int nt, const double* sin2, cpx<double>* Wc) {
   const int threads = 256, total = nt * terms;

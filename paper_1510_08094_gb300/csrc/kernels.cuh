@@ -1365,15 +1365,26 @@ __global__ void k_ge_pivot_partial(const double* __restrict__ e, int nt, int n, 
   const long long total = (long long)nt * H;
   double best = -1.0, mx = 0.0;
   long long bi = 0;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t / H), qq = (int)(t - (long long)i * H);
+  // t = i H + qq, advanced by the grid stride without a division per element
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int di = (int)(stride / H), dq = (int)(stride - (long long)di * H);
+  int i = (int)(t0 / H), qq = (int)(t0 - (long long)i * H);
+  for (long long t = t0; t < total; t += stride) {
     const double a = e[(size_t)i * n + qq], b = e[(size_t)i * n + qq + H];
-    const double s1 = fmax(fabs(a + b), fabs(a - b));
+    // sigma_1 of [[a, b], [b, a]] = max |a +- b| = |a| + |b|
+    const double s1 = fabs(a) + fabs(b);
     if (s1 > best) {
       best = s1;
       bi = t;
     }
     mx = fmax(mx, fmax(fabs(a), fabs(b)));
+    i += di;
+    qq += dq;
+    if (qq >= H) {
+      qq -= H;
+      ++i;
+    }
   }
   __shared__ double sb[32], sm[32];
   __shared__ long long si[32];
@@ -1426,27 +1437,37 @@ __global__ void k_ge_pivot_final(const double* __restrict__ e, int n, const GePi
 // copy the term's column (full DFS grid, m = 2 nt) and row out of the residual:
 // c(theta_p) = e(lambda* - pi, theta_p): for p >= nt, e[p - nt][q* - n/2]; for
 // p < nt (theta_p = -theta_{nt-1-p}), e(lambda*, theta_{nt-1-p}) = e[nt-1-p][q*]
+// the step's column and row of e, and the row's two pivot combinations
+// A_q = p0 r(lambda_q) + p1 r(lambda_q + pi), B_q = p1 r(lambda_q) + p0 r(lambda_q + pi)
 __global__ void k_ge_extract(const double* __restrict__ e, int nt, int n, int istar, int qstar,
-                             double* __restrict__ col, double* __restrict__ row) {
+                             double* __restrict__ col, double* __restrict__ row, double p0, double p1,
+                             double* __restrict__ AB) {
   const int H = n >> 1;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < 2 * nt) {
     const int p = t;
     col[p] = p >= nt ? e[(size_t)(p - nt) * n + (qstar - H)] : e[(size_t)(nt - 1 - p) * n + qstar];
   }
-  if (t < n) row[t] = e[(size_t)istar * n + t];
+  if (t < n) {
+    const double r0 = e[(size_t)istar * n + t], r1 = e[(size_t)istar * n + (t < H ? t + H : t - H)];
+    row[t] = r0;
+    AB[t] = fma(p0, r0, p1 * r1);
+    AB[n + t] = fma(p1, r0, p0 * r1);
+  }
 }
 
-// e[i][q] -= c(theta_i) (p0 r(lambda_q) + p1 r(lambda_q + pi)) + c(-theta_i) (p1 r(lambda_q) + p0 r(lambda_q + pi))
+// e[i][q] -= c(theta_i) A_q + c(-theta_i) B_q; grid (ceil(n / blockDim.x), rows),
+// the rows striding over i so that each thread keeps its A_q, B_q
 __global__ void k_ge_update(double* __restrict__ e, int nt, int n, const double* __restrict__ col,
-                            const double* __restrict__ row, double p0, double p1) {
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (size_t)nt * n) return;
-  const int i = (int)(idx / n), q = (int)(idx - (size_t)i * n);
-  const int H = n >> 1;
-  const double cp = col[nt + i], cm = col[nt - 1 - i];
-  const double r0 = row[q], r1 = row[q < H ? q + H : q - H];
-  e[idx] -= cp * fma(p0, r0, p1 * r1) + cm * fma(p1, r0, p0 * r1);
+                            const double* __restrict__ AB) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const double A = AB[q], B = AB[n + q];
+  for (int i = blockIdx.y; i < nt; i += gridDim.y) {
+    const double cp = col[nt + i], cm = col[nt - 1 - i];
+    double& v = e[(size_t)i * n + q];
+    v = fma(-cp, A, fma(-cm, B, v));
+  }
 }
 
 // ---------------------------------------------------------------------------

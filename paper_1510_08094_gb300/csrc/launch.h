@@ -102,10 +102,11 @@ void launch_normal_dot(cudaStream_t st, const double* a, const double* b, const 
                        const double* geo, int nt, int nl);
 
 // structure-preserving GE: pivot search (partials + final into *out) and one
-// step (extract the term's column and row, update the residual)
+// step (extract the term's column and row, update the residual; AB: 2 n
+// doubles of scratch)
 void launch_ge_pivot(cudaStream_t st, const double* e, int nt, int n, GePivot* part, int nparts, GePivot* out);
 void launch_ge_step(cudaStream_t st, double* e, int nt, int n, int istar, int qstar, double* col, double* row,
-                    double p0, double p1, size_t total);
+                    double p0, double p1, double* AB);
 // low-rank right-hand side: pack the terms' columns for theta_forward, then F
 void launch_lowrank_pack(cudaStream_t st, const double* cols, int terms, int nt, const double* sin2, cpx<double>* Wc);
 // (scales Wc in place by the pivot weights first)

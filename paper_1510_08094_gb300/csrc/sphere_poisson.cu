@@ -1867,7 +1867,7 @@ int sphere_poisson_lowrank_workspace_size(sp_plan_t plan, int max_terms, size_t*
   if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
   if (max_terms < 0 || max_terms > std::min(plan->nt, kMaxTerms)) return SP_ERR_BAD_ARG;
   const size_t ge = al256((size_t)plan->nt * plan->nl * sizeof(double)) + al256(kGeParts * sizeof(sp::GePivot)) +
-                    al256(sizeof(sp::GePivot));
+                    al256(sizeof(sp::GePivot)) + al256(2 * (size_t)plan->nl * sizeof(double));
   const size_t sv = al256((size_t)plan->N * plan->Kp * sizeof(cpx<double>)) +
                     al256((size_t)plan->N * 2 * std::max(max_terms, 1) * sizeof(cpx<double>)) +
                     al256((size_t)std::max(max_terms, 1) * plan->Kp * sizeof(cpx<double>));
@@ -1893,13 +1893,13 @@ int sphere_poisson_lowrank_ge(sp_plan_t plan, const double* f, int max_terms, do
   double* e = reinterpret_cast<double*>(base);
   sp::GePivot* part = reinterpret_cast<sp::GePivot*>(base + al256((size_t)nt * n * sizeof(double)));
   sp::GePivot* pv = reinterpret_cast<sp::GePivot*>(reinterpret_cast<char*>(part) + al256(kGeParts * sizeof(sp::GePivot)));
+  double* AB = reinterpret_cast<double*>(reinterpret_cast<char*>(pv) + al256(sizeof(sp::GePivot)));
   *terms = 0;
   cudaError_t err = cudaMemcpyAsync(e, f, (size_t)nt * n * sizeof(double), cudaMemcpyDeviceToDevice, st);
   if (err != cudaSuccess) return cuda_fail(err, "lowrank_ge copy");
   std::vector<double> hpiv;
   double scale = 0.0, best = 1e300;
   int stall = 0, count = 0;
-  const size_t total = (size_t)nt * n;
   for (int t = 0; t < max_terms; ++t) {
     sp::launch_ge_pivot(st, e, nt, n, part, kGeParts, pv);
     sp::GePivot hp;
@@ -1923,7 +1923,7 @@ int sphere_poisson_lowrank_ge(sp_plan_t plan, const double* f, int max_terms, do
     const double p0 = h1 + h2, p1 = h1 - h2;
     double* col = cols + (size_t)t * m;
     double* row = rows + (size_t)t * n;
-    sp::launch_ge_step(st, e, nt, n, istar, qstar, col, row, p0, p1, total);
+    sp::launch_ge_step(st, e, nt, n, istar, qstar, col, row, p0, p1, AB);
     hpiv.push_back(p0);
     hpiv.push_back(p1);
     ++count;
