@@ -41,31 +41,34 @@ FP64_PEAK_GFLOPS_FALLBACK = 1008.0
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each FP64
 # stage kernel, from one ncu capture of the 5000 x 5000 workload (the colatitude
 # transforms of the 5000 x 10000 grid on half the longitudes; 200 MB input, larger
-# than L2) on the kernel sources whose hash is `csrc_sha256`; see
+# than L2) on the stage-kernel sources whose hash is `csrc_sha256`; see
 # profiles/traffic_fp64_5000x5000.md.  bench.py scales them to its own grid by the
 # spectrum size n_theta * Kp (every stage streams the spectrum once or twice) and
 # reports null when the sources have changed since the capture.
 TRAFFIC_CAPTURE = {
-    "csrc_sha256": "fc15ce2e516a1efa",
+    "csrc_sha256": "cf7ef69c7387c4c3",
     "n_theta": 5000, "n_lambda": 5000,
-    "bytes": {"rows_forward": 200601856 + 142517504, "theta_forward": 200916736 + 141408768,
-              "solve": 662798336 + 321702144, "theta_inverse": 200890368 + 142440704,
-              "rows_inverse": 200343808 + 142960128},
+    "bytes": {"rows_forward": 200194560 + 142166272, "theta_forward": 200850688 + 141419264,
+              "solve": 662737408 + 321661952, "theta_inverse": 201466624 + 142551552,
+              "rows_inverse": 200288768 + 142938368},
 }
 
 
+# the sources the five stage kernels of the solve are compiled from (the
+# operators of calculus.cuh and the plan code do not enter their code)
+TRAFFIC_SOURCES = ("fft.cuh", "kernels.cuh", "launchers.inl")
+
+
 def csrc_hash() -> str:
-    """First 16 hex digits of SHA-256 over the kernel sources (names and bytes, sorted)."""
+    """First 16 hex digits of SHA-256 over the stage kernels' sources (names and bytes)."""
     import hashlib
 
     d = os.path.join(ROOT, "paper_1510_08094_gb300", "csrc")
     h = hashlib.sha256()
-    for n in sorted(os.listdir(d)):
-        q = os.path.join(d, n)
-        if os.path.isfile(q):
-            h.update(n.encode())
-            with open(q, "rb") as fh:
-                h.update(fh.read())
+    for n in TRAFFIC_SOURCES:
+        h.update(n.encode())
+        with open(os.path.join(d, n), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 

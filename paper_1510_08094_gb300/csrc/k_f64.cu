@@ -1,8 +1,9 @@
-// FP64 transform and elimination kernels (and the FP64 zonal side path of the FP32 forms).
-#define SP_FP64_KERNELS
+// FP64 transform and elimination kernels (and the FP64 zonal side path of the
+// FP32 forms), and the FP64 operators of calculus.cuh.
 #include <algorithm>
 #include "launchers.inl"
 #include "batched.cuh"
+#include "calculus.cuh"
 
 namespace sp {
 
@@ -146,7 +147,7 @@ void launch_normal_dot(cudaStream_t st, const double* a, const double* b, const 
 
 void launch_ge_pivot(cudaStream_t st, const double* e, int nt, int n, GePivot* part, int nparts, GePivot* out) {
   k_ge_pivot_partial<<<nparts, 256, 0, st>>>(e, nt, n, part);
-  k_ge_pivot_final<<<1, 1, 0, st>>>(e, n, part, nparts, out);
+  k_ge_pivot_final<<<1, 256, 0, st>>>(e, n, part, nparts, out);
 }
 void launch_ge_step(cudaStream_t st, double* e, int nt, int n, int istar, int qstar, double* col, double* row,
                     double p0, double p1, double* AB) {
