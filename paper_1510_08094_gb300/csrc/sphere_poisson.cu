@@ -30,7 +30,7 @@ namespace {
 constexpr int kMaxLen = 12288;             // longest transform (n_theta, n_lambda/2)
 constexpr size_t kSmemBudget = 200 * 1024;  // shared memory per CTA for a transform tile
 constexpr int kBatchThreadsPerCta = 256;     // threads of a persistent batched CTA
-constexpr int kHostChunks = 8;               // row chunks of the host-buffer solve's overlapped copies
+constexpr int kHostChunks = 16;              // row chunks of the host-buffer solve's overlapped copies
 constexpr uint32_t kMagic = 0x53504f31u;    // "SPO1"
 constexpr double kHalfPi = 1.57079632679489661923132169163975144;
 
@@ -217,8 +217,9 @@ struct sp_plan_s {
   // the FP32 forms run the zonal column on a second stream
   cudaStream_t side;
   cudaEvent_t ev_fork, ev_join;
-  // host-buffer solve: copy stream and per-chunk events (created on first use)
-  cudaStream_t copy;
+  // host-buffer solve: copy stream, a second compute stream for alternate row
+  // chunks, and per-chunk events (created on first use)
+  cudaStream_t copy, alt;
   std::vector<cudaEvent_t> ov_events;
   // stage timing (profile_begin / profile_end)
   std::vector<cudaEvent_t> prof_events;
@@ -369,15 +370,20 @@ void launch_rows_inverse_x(sp_plan_t p, bool adj, cudaStream_t st, const cpx<T>*
 // Host-buffer solve with the copies overlapped: the grid moves in row chunks on
 // the plan's copy stream; the longitude forward transform of chunk c starts as
 // soon as its rows have arrived, and the rows of u go back chunk by chunk as
-// the longitude inverse transform finishes them.
+// the longitude inverse transform finishes them.  Consecutive chunks' transforms
+// alternate between the solve's stream and a second one, so that one chunk's
+// last CTAs run beside the next chunk's first ones instead of leaving the SMs
+// idle at every chunk boundary.
 struct HostOverlap {
   const double* f_host;
   double* u_host;
   double* d_f;
   double* d_u;
   cudaStream_t copy;
+  cudaStream_t alt;
   const cudaEvent_t* ev_in;   // one per chunk
   const cudaEvent_t* ev_out;  // one per chunk
+  const cudaEvent_t* ev_sync; // fork / join of alt for the two stages (4)
   int chunks;
 };
 
@@ -393,17 +399,22 @@ void rows_forward_stage(sp_plan_t p, bool adj, cudaStream_t st, const double* in
     return;
   }
   const int chunk = overlap_chunk_rows(p, ov);
+  cudaEventRecord(ov->ev_sync[0], st);
+  cudaStreamWaitEvent(ov->alt, ov->ev_sync[0], 0);
   for (int c = 0, r0 = 0; r0 < p->nt; ++c, r0 += chunk) {
     const int nr = std::min(chunk, p->nt - r0);
     const size_t off = (size_t)r0 * p->nl;
+    cudaStream_t sc = (c & 1) ? ov->alt : st;
     cudaMemcpyAsync(ov->d_f + off, ov->f_host + off, (size_t)nr * p->nl * sizeof(double), cudaMemcpyHostToDevice,
                     ov->copy);
     cudaEventRecord(ov->ev_in[c], ov->copy);
-    cudaStreamWaitEvent(st, ov->ev_in[c], 0);
-    launch_rows_forward_x<T>(p, adj, st, ov->d_f + off, W + (size_t)r0 * p->Kp, nr, p->nl, p->Kp,
+    cudaStreamWaitEvent(sc, ov->ev_in[c], 0);
+    launch_rows_forward_x<T>(p, adj, sc, ov->d_f + off, W + (size_t)r0 * p->Kp, nr, p->nl, p->Kp,
                              p->rows_per_cta, p->row_fft, tw, p->perm_row, post, rs + r0, rst + r0,
                              zonal ? zonal + 2 * (size_t)r0 : nullptr);
   }
+  cudaEventRecord(ov->ev_sync[1], ov->alt);
+  cudaStreamWaitEvent(st, ov->ev_sync[1], 0);
 }
 
 template <typename T>
@@ -416,17 +427,22 @@ void rows_inverse_stage(sp_plan_t p, bool adj, cudaStream_t st, const cpx<T>* W,
     return;
   }
   const int chunk = overlap_chunk_rows(p, ov);
+  cudaEventRecord(ov->ev_sync[2], st);
+  cudaStreamWaitEvent(ov->alt, ov->ev_sync[2], 0);
   for (int c = 0, r0 = 0; r0 < p->nt; ++c, r0 += chunk) {
     const int nr = std::min(chunk, p->nt - r0);
     const size_t off = (size_t)r0 * p->nl;
-    launch_rows_inverse_x<T>(p, adj, st, W + (size_t)r0 * p->Kp, ov->d_u + off, nr, p->nl, p->Kp,
+    cudaStream_t sc = (c & 1) ? ov->alt : st;
+    launch_rows_inverse_x<T>(p, adj, sc, W + (size_t)r0 * p->Kp, ov->d_u + off, nr, p->nl, p->Kp,
                              p->rows_per_cta, p->row_fft, tw, p->perm_row, post, rs + r0, rst + r0,
                              zonal ? zonal + 2 * (size_t)r0 : nullptr);
-    cudaEventRecord(ov->ev_out[c], st);
+    cudaEventRecord(ov->ev_out[c], sc);
     cudaStreamWaitEvent(ov->copy, ov->ev_out[c], 0);
     cudaMemcpyAsync(ov->u_host + off, ov->d_u + off, (size_t)nr * p->nl * sizeof(double), cudaMemcpyDeviceToHost,
                     ov->copy);
   }
+  cudaEventRecord(ov->ev_sync[3], ov->alt);
+  cudaStreamWaitEvent(st, ov->ev_sync[3], 0);
 }
 
 void enqueue_fp64(sp_plan_t p, bool adj, const double* in, double* out, void* ws, cudaStream_t st,
@@ -634,6 +650,7 @@ void destroy_plan(sp_plan_s* p) {
   for (cudaEvent_t e : p->prof_events) cudaEventDestroy(e);
   for (cudaEvent_t e : p->ov_events) cudaEventDestroy(e);
   if (p->copy) cudaStreamDestroy(p->copy);
+  if (p->alt) cudaStreamDestroy(p->alt);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
   if (p->side) cudaStreamDestroy(p->side);
@@ -1550,11 +1567,13 @@ int sphere_poisson_solve_host(sp_plan_t plan, const double* f_host, double* u_ho
   // copies overlapped with the longitude transforms, in kHostChunks row chunks
   if (!plan->copy) {
     SP_CUDA(cudaStreamCreateWithFlags(&plan->copy, cudaStreamNonBlocking));
-    plan->ov_events.assign(2 * kHostChunks + 1, nullptr);
+    SP_CUDA(cudaStreamCreateWithFlags(&plan->alt, cudaStreamNonBlocking));
+    plan->ov_events.assign(2 * kHostChunks + 5, nullptr);
     for (cudaEvent_t& e : plan->ov_events) SP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
-  const HostOverlap ov{f_host, u_host, d_f, d_u, plan->copy, plan->ov_events.data() + 1,
-                       plan->ov_events.data() + 1 + kHostChunks, kHostChunks};
+  const HostOverlap ov{f_host, u_host, d_f, d_u, plan->copy, plan->alt, plan->ov_events.data() + 1,
+                       plan->ov_events.data() + 1 + kHostChunks, plan->ov_events.data() + 1 + 2 * kHostChunks,
+                       kHostChunks};
   SP_CUDA(cudaEventRecord(plan->ov_events[0], st));     // the copies follow earlier work on the stream
   SP_CUDA(cudaStreamWaitEvent(plan->copy, plan->ov_events[0], 0));
   if (plan->precision == SP_FP64) enqueue_fp64(plan, false, d_f, d_u, ws, st, &ov);
