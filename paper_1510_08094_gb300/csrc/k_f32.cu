@@ -56,12 +56,14 @@ cudaError_t allow_transform_smem<float>(int bytes) {
 template <>
 void launch_solve<float>(bool adj, const Launch& l, cpx<float>* W, const float* fl, const float* fiu,
                          const float* fcu, int N, int K, int Kp) {
-  if (adj) k_solve<true, float><<<l.grid, l.threads, l.smem, l.stream>>>(W, fl, fiu, fcu, N, K, Kp);
-  else k_solve<false, float><<<l.grid, l.threads, l.smem, l.stream>>>(W, fl, fiu, fcu, N, K, Kp);
+  // two warps per CTA (the twisted solve); l.threads is not used
+  if (adj) k_solve<true, float><<<l.grid, kSolveThreads, 0, l.stream>>>(W, fl, fiu, fcu, N, K, Kp);
+  else k_solve<false, float><<<l.grid, kSolveThreads, 0, l.stream>>>(W, fl, fiu, fcu, N, K, Kp);
 }
 template <>
-void launch_factor<float>(const Launch& l, float* fl, float* fiu, float* fcu, int N, int K, int Kp) {
-  k_factor<float><<<l.grid, l.threads, l.smem, l.stream>>>(fl, fiu, fcu, N, K, Kp);
+void launch_factor<float>(const Launch& l, float* fl, float* fiu, float* fcu, int N, int K, int Kp, bool twist) {
+  if (twist) k_factor<float, true><<<l.grid, l.threads, l.smem, l.stream>>>(fl, fiu, fcu, N, K, Kp);
+  else k_factor<float, false><<<l.grid, l.threads, l.smem, l.stream>>>(fl, fiu, fcu, N, K, Kp);
 }
 
 SP_INSTANTIATE_PIPE(float);

@@ -60,12 +60,14 @@ cudaError_t allow_transform_smem<double>(int bytes) {
 template <>
 void launch_solve<double>(bool adj, const Launch& l, cpx<double>* W, const double* fl, const double* fiu,
                           const double* fcu, int N, int K, int Kp) {
-  if (adj) k_solve<true, double><<<l.grid, l.threads, l.smem, l.stream>>>(W, fl, fiu, fcu, N, K, Kp);
-  else k_solve<false, double><<<l.grid, l.threads, l.smem, l.stream>>>(W, fl, fiu, fcu, N, K, Kp);
+  // two warps per CTA (the twisted solve); l.threads is not used
+  if (adj) k_solve<true, double><<<l.grid, kSolveThreads, 0, l.stream>>>(W, fl, fiu, fcu, N, K, Kp);
+  else k_solve<false, double><<<l.grid, kSolveThreads, 0, l.stream>>>(W, fl, fiu, fcu, N, K, Kp);
 }
 template <>
-void launch_factor<double>(const Launch& l, double* fl, double* fiu, double* fcu, int N, int K, int Kp) {
-  k_factor<double><<<l.grid, l.threads, l.smem, l.stream>>>(fl, fiu, fcu, N, K, Kp);
+void launch_factor<double>(const Launch& l, double* fl, double* fiu, double* fcu, int N, int K, int Kp, bool twist) {
+  if (twist) k_factor<double, true><<<l.grid, l.threads, l.smem, l.stream>>>(fl, fiu, fcu, N, K, Kp);
+  else k_factor<double, false><<<l.grid, l.threads, l.smem, l.stream>>>(fl, fiu, fcu, N, K, Kp);
 }
 
 void launch_zonal_scan(bool adj, cudaStream_t st, cpx<double>* Z, const double* zl, const double* ziu,

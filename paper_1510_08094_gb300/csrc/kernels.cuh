@@ -755,13 +755,22 @@ __global__ void __launch_bounds__(512) k_theta_inverse_pipe(
 
 // ---------------------------------------------------------------------------
 // Plan-time factorisation of the parity tridiagonals of every column.
-// Chain rows j = j0, j0+2, ... < N (j0 = 1 odd chain, 2 even chain):
+// Chain rows j = j0, j0+2, ... < N (j0 = 1 odd chain, 2 even chain), t = 0..M-1:
 //   a_j = (j-1)(j-2)/4 (couples j-2), b_j = -(j^2/2 + k^2), c_j = (j+1)(j+2)/4.
-// Thomas without pivoting in increasing j: u_0 = b_j0, l_t = a_t / u_{t-1},
-// u_t = b_t - l_t c_{t-1}.  Stored per (j, k): l, 1/u, c/u.
+// TWIST = false: Thomas without pivoting in increasing j: u_0 = b_j0,
+//   l_t = a_t / u_{t-1}, u_t = b_t - l_t c_{t-1}; stored per (j, k): l, 1/u, c/u.
+// TWIST = true: a twisted factorisation about the middle row m = (M-1)/2, so
+//   that the solve can run the two halves of every chain at once: rows t < m as
+//   above; rows t > m eliminated from the bottom, v_{M-1} = b_{M-1},
+//   g_t = c_t / v_{t+1}, v_t = b_t - g_t a_{t+1}, stored as g, 1/v, a/v; row m
+//   stores l_m = a_m/u_{m-1}, 1/gamma and g_m = c_m/v_{m+1} (in the third table),
+//   gamma = b_m - l_m c_{m-1} - g_m a_{m+1}.
 // Thread layout: idx < K -> odd chain of k = idx; else even chain of k = idx - K.
 // ---------------------------------------------------------------------------
-template <typename S>
+__device__ __forceinline__ double chain_a(double j) { return (j - 1.0) * (j - 2.0) * 0.25; }
+__device__ __forceinline__ double chain_c(double j) { return (j + 1.0) * (j + 2.0) * 0.25; }
+
+template <typename S, bool TWIST>
 __global__ void k_factor(S* __restrict__ fl, S* __restrict__ fiu, S* __restrict__ fcu,
                          int N, int K, int Kp) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -770,25 +779,51 @@ __global__ void k_factor(S* __restrict__ fl, S* __restrict__ fiu, S* __restrict_
   const int k = even ? idx - K : idx;
   const double k2 = (double)k * (double)k;
   const int j0 = even ? 2 : 1;
+  if (j0 >= N) return;
+  const int M = (N - 1 - j0) / 2 + 1;
+  const int m = TWIST ? (M - 1) / 2 : M;
+  auto row = [&](int t) { return (size_t)(j0 + 2 * t) * Kp + k; };
+  auto b_of = [&](int t) { const double j = (double)(j0 + 2 * t); return -(j * j * 0.5 + k2); };
   double u_prev = 0.0, c_prev = 0.0;
-  for (int j = j0; j < N; j += 2) {
-    const double jd = (double)j;
-    const double a = (jd - 1.0) * (jd - 2.0) * 0.25;
-    const double b = -(jd * jd * 0.5 + k2);
-    const double c = (jd + 1.0) * (jd + 2.0) * 0.25;
+  for (int t = 0; t < m; ++t) {
+    const double jd = (double)(j0 + 2 * t);
+    const double a = chain_a(jd), b = b_of(t), c = chain_c(jd);
     double l = 0.0, uu = b;
-    if (j > j0) {
+    if (t > 0) {
       l = a / u_prev;
       uu = b - l * c_prev;
     }
     const double iu = 1.0 / uu;
-    const size_t o = (size_t)j * Kp + k;
-    fl[o] = (S)l;
-    fiu[o] = (S)iu;
-    fcu[o] = (S)(c * iu);
+    fl[row(t)] = (S)l;
+    fiu[row(t)] = (S)iu;
+    fcu[row(t)] = (S)(c * iu);
     u_prev = uu;
     c_prev = c;
   }
+  if (!TWIST) return;
+  double v_next = 0.0, a_next = 0.0;
+  for (int t = M - 1; t > m; --t) {
+    const double jd = (double)(j0 + 2 * t);
+    const double a = chain_a(jd), b = b_of(t), c = chain_c(jd);
+    double g = 0.0, vv = b;
+    if (t < M - 1) {
+      g = c / v_next;
+      vv = b - g * a_next;
+    }
+    const double iv = 1.0 / vv;
+    fl[row(t)] = (S)g;
+    fiu[row(t)] = (S)iv;
+    fcu[row(t)] = (S)(a * iv);
+    v_next = vv;
+    a_next = a;
+  }
+  const double jm = (double)(j0 + 2 * m);
+  const double lm = m > 0 ? chain_a(jm) / u_prev : 0.0;
+  const double gm = m < M - 1 ? chain_c(jm) / v_next : 0.0;
+  const double gam = b_of(m) - (m > 0 ? lm * c_prev : 0.0) - (m < M - 1 ? gm * a_next : 0.0);
+  fl[row(m)] = (S)lm;
+  fiu[row(m)] = (S)(1.0 / gam);
+  fcu[row(m)] = (S)gm;
 }
 
 // ---------------------------------------------------------------------------
@@ -802,16 +837,15 @@ __global__ void k_factor(S* __restrict__ fl, S* __restrict__ fiu, S* __restrict_
 //   k even != 0: Fbar_0 = -Xbar_0/k^2 and Xbar_2 += Xbar_0/k^2; k = 0:
 //   Xbar_j += 2 Xbar_0/(j^2-1) for even j (added by theta_forward's adjoint),
 //   Fbar_0 = 0; k odd: Fbar_0 = 0;
-//   then T^T = U^T L^T: z_t = (b_t - c_{t-1} z_{t-1})/u_t, y_t = z_t - l_{t+1} y_{t+1}.
+//   then the transposed chain solve (below).
 // ---------------------------------------------------------------------------
 // cp.async helpers (per-thread asynchronous global -> shared copies)
 
-// One warp = 32 chains (consecutive k, one parity).  Each lane streams its own
-// chain's rows through a ring of kRing shared-memory slots filled by its own
-// cp.async copies, kRing rows ahead of the elimination, so every lane keeps
-// kRing rows of loads in flight without any cross-lane synchronisation.
+// Each lane streams its own chain's rows through a ring of shared-memory slots
+// filled by its own cp.async copies, a ring's depth of rows ahead of the
+// elimination, so every lane keeps that many rows of loads in flight without
+// any cross-lane synchronisation.
 // S is the storage and arithmetic type (double, or float for the FP32 form).
-constexpr int kRing = 32;
 template <typename S>
 struct RingSlot {
   cpx<S> d[32];
@@ -834,133 +868,180 @@ __device__ __forceinline__ void cp_async_s(S* smem, const S* g) {
   }
 }
 
-template <bool ADJ, typename S>
-__global__ void __launch_bounds__(32) k_solve(cpx<S>* __restrict__ W, const S* __restrict__ fl,
-                                              const S* __restrict__ fiu, const S* __restrict__ fcu,
-                                              int N, int K, int Kp) {
-  __shared__ RingSlot<S> ring[kRing];
-  const int lane = threadIdx.x;
-  const bool even = blockIdx.y == 1;
-  const int k = blockIdx.x * 32 + lane;
-  if (k >= K) return;
-  const int j0 = even ? 2 : 1;
-  const S ik2 = k ? (S)(1.0 / ((double)k * (double)k)) : (S)0;
-  if (j0 >= N) {
-    // no chain rows; only the closure of row 0 remains (forward: X_0 = -F_0/k^2,
-    // adjoint: Fbar_0 = -Xbar_0/k^2, both zero for k = 0 and odd k)
-    if (even) {
-      cpx<S> x0 = W[k];
-      W[k] = (k == 0 || (k & 1)) ? cpx<S>{(S)0, (S)0} : (-ik2) * x0;
-    }
-    return;
-  }
-  const int M = (N - 1 - j0) / 2 + 1;            // chain length
-  const size_t stride = (size_t)2 * Kp;          // one chain step
-  cpx<S>* Wc = W + (size_t)j0 * Kp + k;
-  const S* Lc = fl + (size_t)j0 * Kp + k;
-  const S* IUc = fiu + (size_t)j0 * Kp + k;
-  const S* CUc = fcu + (size_t)j0 * Kp + k;
-
-  // ascending sweep issue: row t -> slot t % kRing (data + one table)
-  auto issue_up = [&](int t, const S* tab) {
-    if (t < M) {
-      RingSlot<S>& sl = ring[t & (kRing - 1)];
-      cp_async_c(&sl.d[lane], Wc + t * stride);
-      cp_async_s(&sl.a[lane], tab + t * stride);
-    }
-    cp_commit();
-  };
-  // descending sweep issue: r-th row from the end -> slot r % kRing (data + two tables)
-  auto issue_down = [&](int r, const S* ta, const S* tb) {
-    int t = M - 1 - r;
-    if (t >= 0) {
-      RingSlot<S>& sl = ring[r & (kRing - 1)];
+// Rows t = t0 + dir s, s = 0..len-1, of one chain streamed through this warp's
+// ring: the copies of row s + kSolveRing are issued after row s has been consumed by
+// body(t, d, a, b) (d from Wc, a and b from the tables ta, tb; tb may be null).
+// The ring holds kSolveRing rows (two rings of 16 KB each for FP64).
+constexpr int kSolveRing = 16;
+template <typename S, typename Body>
+__device__ __forceinline__ void ring_sweep(RingSlot<S>* ring, int lane, bool active, cpx<S>* Wc, const S* ta,
+                                           const S* tb, size_t stride, int t0, int dir, int len, Body body) {
+  auto issue = [&](int q) {
+    if (active && q < len) {
+      const int t = t0 + dir * q;
+      RingSlot<S>& sl = ring[q & (kSolveRing - 1)];
       cp_async_c(&sl.d[lane], Wc + t * stride);
       cp_async_s(&sl.a[lane], ta + t * stride);
       if (tb) cp_async_s(&sl.b[lane], tb + t * stride);
     }
     cp_commit();
   };
+  for (int q = 0; q < kSolveRing; ++q) issue(q);
+  for (int q = 0; q < len; ++q) {
+    cp_wait<kSolveRing - 1>();
+    const RingSlot<S>& sl = ring[q & (kSolveRing - 1)];
+    if (active) body(t0 + dir * q, sl.d[lane], sl.a[lane], tb ? sl.b[lane] : (S)0);
+    issue(q + kSolveRing);
+  }
+  cp_wait_all();
+}
+
+// Twisted solve: CTA = 2 warps over the same 32 chains (consecutive k, one
+// parity, blockIdx.y = 1 the even chains); warp 0 runs rows t < m from the top,
+// warp 1 rows t > m from the bottom, each through its own ring, and they meet
+// at the middle row m through shared memory (tables of k_factor<S, true>).
+//   forward: y_t = d_t - l_t y_{t-1} (t < m), z_t = d_t - g_t z_{t+1} (t > m),
+//     x_m = (d_m - l_m y_{m-1} - g_m z_{m+1}) / gamma, then
+//     x_t = y_t/u_t - (c_t/u_t) x_{t+1} (t < m), x_t = z_t/v_t - (a_t/v_t) x_{t-1} (t > m).
+//   adjoint (the transpose of those steps in reverse order):
+//     p_t = (b_t - c_{t-1} p_{t-1})/u_t (t < m), q_t = (b_t - a_{t+1} q_{t+1})/v_t (t > m),
+//     s = (b_m - c_{m-1} p_{m-1} - a_{m+1} q_{m+1}) / gamma, then
+//     r_t = p_t - l_{t+1} r_{t+1} (t < m, r_m = s), w_t = q_t - g_{t-1} w_{t-1} (t > m, w_m = s).
+constexpr int kSolveThreads = 64;
+template <bool ADJ, typename S>
+__global__ void __launch_bounds__(kSolveThreads) k_solve(cpx<S>* __restrict__ W, const S* __restrict__ fl,
+                                                         const S* __restrict__ fiu, const S* __restrict__ fcu,
+                                                         int N, int K, int Kp) {
+  __shared__ RingSlot<S> ring[2][kSolveRing];
+  __shared__ cpx<S> meet[3][32];
+  const int lane = threadIdx.x & 31, half = threadIdx.x >> 5;   // half 0: top, 1: bottom
+  const bool even = blockIdx.y == 1;
+  const int k = blockIdx.x * 32 + lane;
+  const bool active = k < K;
+  const int j0 = even ? 2 : 1;
+  const S ik2 = k ? (S)(1.0 / ((double)k * (double)k)) : (S)0;
+  if (j0 >= N) {
+    // no chain rows; only the closure of row 0 remains (forward: X_0 = -F_0/k^2,
+    // adjoint: Fbar_0 = -Xbar_0/k^2, both zero for k = 0 and odd k)
+    if (even && half == 0 && active) {
+      cpx<S> x0 = W[k];
+      W[k] = (k == 0 || (k & 1)) ? cpx<S>{(S)0, (S)0} : (-ik2) * x0;
+    }
+    return;
+  }
+  const int M = (N - 1 - j0) / 2 + 1;            // chain length
+  const int m = (M - 1) / 2;                     // the rows meet at t = m
+  const size_t stride = (size_t)2 * Kp;          // one chain step
+  cpx<S>* Wc = W + (size_t)j0 * Kp + (active ? k : 0);
+  const S* Lc = fl + (size_t)j0 * Kp + (active ? k : 0);
+  const S* IUc = fiu + (size_t)j0 * Kp + (active ? k : 0);
+  const S* CUc = fcu + (size_t)j0 * Kp + (active ? k : 0);
+  RingSlot<S>* rg = ring[half];
+  const int jm = j0 + 2 * m;
 
   if (!ADJ) {
-    // forward sweep y_t = d_t - l_t y_{t-1}
-    for (int t = 0; t < kRing; ++t) issue_up(t, Lc);
-    cpx<S> y = {(S)0, (S)0};
-    for (int t = 0; t < M; ++t) {
-      cp_wait<kRing - 1>();
-      const RingSlot<S>& sl = ring[t & (kRing - 1)];
-      cpx<S> d = sl.d[lane];
-      S l = sl.a[lane];
-      y = {fma(-l, y.re, d.re), fma(-l, y.im, d.im)};
-      Wc[t * stride] = y;
-      issue_up(t + kRing, Lc);
+    // first sweeps: y (top, rows 0..m-1) and z (bottom, rows M-1..m+1)
+    cpx<S> e = {(S)0, (S)0};
+    if (half == 0) {
+      ring_sweep(rg, lane, active, Wc, Lc, (const S*)nullptr, stride, 0, 1, m, [&](int t, cpx<S> d, S l, S) {
+        e = {fma(-l, e.re, d.re), fma(-l, e.im, d.im)};
+        Wc[t * stride] = e;
+      });
+    } else {
+      ring_sweep(rg, lane, active, Wc, Lc, (const S*)nullptr, stride, M - 1, -1, M - 1 - m,
+                 [&](int t, cpx<S> d, S g, S) {
+                   e = {fma(-g, e.re, d.re), fma(-g, e.im, d.im)};
+                   Wc[t * stride] = e;
+                 });
     }
-    cp_wait_all();
-    __threadfence();  // the descending copies read rows this thread just stored
-    // backward sweep x_t = y_t / u_t - (c_t / u_t) x_{t+1}
-    for (int r = 0; r < kRing; ++r) issue_down(r, IUc, CUc);
-    cpx<S> x = {(S)0, (S)0};
-    for (int r = 0; r < M; ++r) {
-      cp_wait<kRing - 1>();
-      const RingSlot<S>& sl = ring[r & (kRing - 1)];
-      cpx<S> yv = sl.d[lane];
-      S iu = sl.a[lane], cu = sl.b[lane];
-      const int t = M - 1 - r;
-      x = {fma(yv.re, iu, -cu * x.re), fma(yv.im, iu, -cu * x.im)};
-      Wc[t * stride] = x;
-      issue_down(r + kRing, IUc, CUc);
+    meet[half][lane] = e;
+    __syncthreads();
+    if (half == 0 && active) {
+      const cpx<S> ym1 = meet[0][lane], zp1 = meet[1][lane], dm = Wc[m * stride];
+      const S lm = Lc[m * stride], gm = CUc[m * stride], ig = IUc[m * stride];
+      const cpx<S> xm = {ig * (dm.re - lm * ym1.re - gm * zp1.re), ig * (dm.im - lm * ym1.im - gm * zp1.im)};
+      Wc[m * stride] = xm;
+      meet[2][lane] = xm;
     }
-    cp_wait_all();
-    if (even && k != 0) {
-      // x holds X_2: row 0 closure X_0 = (X_2 - F_0)/k^2 (k even), X_0 = 0 (k odd).
-      // The k = 0 closure (w^T X_0 = 0) is summed by theta_inverse's first CTA.
-      cpx<S> f0 = W[k];
-      if (k & 1) W[k] = {(S)0, (S)0};
-      else W[k] = {(x.re - f0.re) * ik2, (x.im - f0.im) * ik2};
+    __syncthreads();
+    __threadfence();  // the copies below read rows this thread stored
+    cpx<S> x = meet[2][lane];
+    if (half == 0) {
+      ring_sweep(rg, lane, active, Wc, IUc, CUc, stride, m - 1, -1, m, [&](int t, cpx<S> yv, S iu, S cu) {
+        x = {fma(yv.re, iu, -cu * x.re), fma(yv.im, iu, -cu * x.im)};
+        Wc[t * stride] = x;
+      });
+      if (even && k != 0 && active) {
+        // x holds X_2: row 0 closure X_0 = (X_2 - F_0)/k^2 (k even), X_0 = 0 (k odd).
+        // The k = 0 closure (w^T X_0 = 0) is summed by theta_inverse's first CTA.
+        cpx<S> f0 = W[k];
+        if (k & 1) W[k] = {(S)0, (S)0};
+        else W[k] = {(x.re - f0.re) * ik2, (x.im - f0.im) * ik2};
+      }
+    } else {
+      ring_sweep(rg, lane, active, Wc, IUc, CUc, stride, m + 1, 1, M - 1 - m, [&](int t, cpx<S> zv, S iv, S av) {
+        x = {fma(zv.re, iv, -av * x.re), fma(zv.im, iv, -av * x.im)};
+        Wc[t * stride] = x;
+      });
     }
   } else {
     cpx<S> xb0 = {(S)0, (S)0};
-    if (even) {
+    if (even && half == 0 && active) {
       xb0 = W[k];
       W[k] = (k == 0 || (k & 1)) ? cpx<S>{(S)0, (S)0} : (-ik2) * xb0;
     }
-    const bool bump2 = even && k != 0 && !(k & 1);   // Xbar_2 += Xbar_0 / k^2
-    // forward sweep with U^T: z_t = (b_t - c_{t-1} z_{t-1}) / u_t
-    for (int t = 0; t < kRing; ++t) issue_up(t, IUc);
-    cpx<S> z = {(S)0, (S)0};
-    for (int t = 0; t < M; ++t) {
-      cp_wait<kRing - 1>();
-      const RingSlot<S>& sl = ring[t & (kRing - 1)];
-      cpx<S> bv = sl.d[lane];
-      S iu = sl.a[lane];
-      const int j = j0 + 2 * t;
-      // (k = 0: the terms 2 Xbar_0/(j^2-1) were added by theta_forward's adjoint)
-      if (bump2 && t == 0) {
-        bv = {fma(ik2, xb0.re, bv.re), fma(ik2, xb0.im, bv.im)};
-      }
-      S cprev = t ? (S)((double)((j - 1) * j) * 0.25) : (S)0;   // c_{j-2} = (j-1) j / 4
-      z = {(bv.re - cprev * z.re) * iu, (bv.im - cprev * z.im) * iu};
-      Wc[t * stride] = z;
-      issue_up(t + kRing, IUc);
+    const bool bump2 = even && k != 0 && !(k & 1);   // Xbar_2 += Xbar_0 / k^2 (row t = 0)
+    // (k = 0: the terms 2 Xbar_0/(j^2-1) were added by theta_forward's adjoint)
+    cpx<S> e = {(S)0, (S)0};
+    if (half == 0) {
+      ring_sweep(rg, lane, active, Wc, IUc, (const S*)nullptr, stride, 0, 1, m, [&](int t, cpx<S> b, S iu, S) {
+        if (bump2 && t == 0) b = {fma(ik2, xb0.re, b.re), fma(ik2, xb0.im, b.im)};
+        const int j = j0 + 2 * t;
+        const S cprev = t ? (S)((double)((j - 1) * j) * 0.25) : (S)0;   // c_{j-2} = (j-1) j / 4
+        e = {(b.re - cprev * e.re) * iu, (b.im - cprev * e.im) * iu};
+        Wc[t * stride] = e;
+      });
+    } else {
+      ring_sweep(rg, lane, active, Wc, IUc, (const S*)nullptr, stride, M - 1, -1, M - 1 - m,
+                 [&](int t, cpx<S> b, S iv, S) {
+                   const int j = j0 + 2 * t;
+                   const S anext = t < M - 1 ? (S)((double)((j + 1) * j) * 0.25) : (S)0;   // a_{j+2}
+                   e = {(b.re - anext * e.re) * iv, (b.im - anext * e.im) * iv};
+                   Wc[t * stride] = e;
+                 });
     }
-    cp_wait_all();
+    meet[half][lane] = e;
+    __syncthreads();
+    if (half == 0 && active) {
+      const cpx<S> pm1 = meet[0][lane], qp1 = meet[1][lane];
+      cpx<S> bm = Wc[m * stride];
+      if (bump2 && m == 0) bm = {fma(ik2, xb0.re, bm.re), fma(ik2, xb0.im, bm.im)};
+      const S cm1 = m > 0 ? (S)((double)((jm - 1) * jm) * 0.25) : (S)0;       // c_{jm-2}
+      const S ap1 = m < M - 1 ? (S)((double)((jm + 1) * jm) * 0.25) : (S)0;   // a_{jm+2}
+      const S ig = IUc[m * stride];
+      const cpx<S> sm = {ig * (bm.re - cm1 * pm1.re - ap1 * qp1.re), ig * (bm.im - cm1 * pm1.im - ap1 * qp1.im)};
+      Wc[m * stride] = sm;
+      meet[2][lane] = sm;
+    }
+    __syncthreads();
     __threadfence();
-    // backward sweep with L^T: y_t = z_t - l_{t+1} y_{t+1}
-    for (int r = 0; r < kRing; ++r) issue_down(r, Lc, nullptr);
-    cpx<S> y = {(S)0, (S)0};
-    S lnext = (S)0;
-    for (int r = 0; r < M; ++r) {
-      cp_wait<kRing - 1>();
-      const RingSlot<S>& sl = ring[r & (kRing - 1)];
-      cpx<S> zv = sl.d[lane];
-      S l = sl.a[lane];
-      const int t = M - 1 - r;
-      y = {fma(-lnext, y.re, zv.re), fma(-lnext, y.im, zv.im)};
-      Wc[t * stride] = y;
-      lnext = l;
-      issue_down(r + kRing, Lc, nullptr);
+    cpx<S> r = meet[2][lane];
+    if (half == 0) {
+      S lnext = active ? Lc[m * stride] : (S)0;
+      ring_sweep(rg, lane, active, Wc, Lc, (const S*)nullptr, stride, m - 1, -1, m, [&](int t, cpx<S> pv, S l, S) {
+        r = {fma(-lnext, r.re, pv.re), fma(-lnext, r.im, pv.im)};
+        Wc[t * stride] = r;
+        lnext = l;
+      });
+    } else {
+      S gprev = active ? CUc[m * stride] : (S)0;
+      ring_sweep(rg, lane, active, Wc, Lc, (const S*)nullptr, stride, m + 1, 1, M - 1 - m,
+                 [&](int t, cpx<S> qv, S g, S) {
+                   r = {fma(-gprev, r.re, qv.re), fma(-gprev, r.im, qv.im)};
+                   Wc[t * stride] = r;
+                   gprev = g;
+                 });
     }
-    cp_wait_all();
   }
 }
 

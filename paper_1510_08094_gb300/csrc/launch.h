@@ -68,8 +68,10 @@ cudaError_t allow_transform_smem(int bytes);
 template <typename S>
 void launch_solve(bool adj, const Launch& l, cpx<S>* W, const S* fl, const S* fiu, const S* fcu, int N, int K,
                   int Kp);
+// twist: the twisted factorisation k_solve needs; false: the top-down one of the
+// zonal scan, the batched kernels and the refinement
 template <typename S>
-void launch_factor(const Launch& l, S* fl, S* fiu, S* fcu, int N, int K, int Kp);
+void launch_factor(const Launch& l, S* fl, S* fiu, S* fcu, int N, int K, int Kp, bool twist);
 
 // FP64 zonal-column eliminations by parallel scan (one CTA)
 void launch_zonal_scan(bool adj, cudaStream_t st, cpx<double>* Z, const double* zl, const double* ziu,

@@ -884,11 +884,12 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
     int threads = 128, blocks = (2 * p->K + threads - 1) / threads;
     if (precision == SP_FP64) {
       sp::launch_factor<double>(sp::Launch{dim3(blocks), threads, 0, 0}, p->fac_l, p->fac_iu, p->fac_cu, p->N,
-                                p->K, p->Kp);
+                                p->K, p->Kp, true);
     } else {
+      // the FP32 form solves with k_solve (twisted); the refinement with k_refine (top-down)
       sp::launch_factor<float>(sp::Launch{dim3(blocks), threads, 0, 0}, p->f32_l, p->f32_iu, p->f32_cu, p->N,
-                               p->K, p->Kp);
-      sp::launch_factor<double>(sp::Launch{dim3(1), threads, 0, 0}, p->z_l, p->z_iu, p->z_cu, p->N, 1, 2);
+                               p->K, p->Kp, precision == SP_FP32);
+      sp::launch_factor<double>(sp::Launch{dim3(1), threads, 0, 0}, p->z_l, p->z_iu, p->z_cu, p->N, 1, 2, false);
     }
     step(cudaGetLastError(), "k_factor launch");
     step(cudaDeviceSynchronize(), "k_factor");
@@ -1346,7 +1347,7 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
       for (const double* t : {b.fl, b.fiu, b.fcu}) step(cudaMemset((void*)t, 0, fac), "clear factors");
       if (rc == SP_OK) {
         sp::launch_factor<double>(sp::Launch{dim3(blocks), threads, 0, 0}, (double*)b.fl, (double*)b.fiu,
-                                  (double*)b.fcu, b.N, b.K, b.Kp);
+                                  (double*)b.fcu, b.N, b.K, b.Kp, false);
         step(cudaGetLastError(), "k_factor launch");
       }
       b.tw_row_d = b.tw_col_d = b.post_row_d = b.post_col_d = b.post_col_s_d = nullptr;
@@ -1388,9 +1389,9 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
     for (const double* t : {b.zl, b.ziu, b.zcu}) step(cudaMemset((void*)t, 0, fz), "clear factors");
     if (rc == SP_OK) {
       sp::launch_factor<float>(sp::Launch{dim3(blocks), threads, 0, 0}, (float*)b.fl32, (float*)b.fiu32,
-                               (float*)b.fcu32, b.N, b.K, b.Kp);
+                               (float*)b.fcu32, b.N, b.K, b.Kp, false);
       sp::launch_factor<double>(sp::Launch{dim3(1), threads, 0, 0}, (double*)b.zl, (double*)b.ziu,
-                                (double*)b.zcu, b.N, 1, 2);
+                                (double*)b.zcu, b.N, 1, 2, false);
       step(cudaGetLastError(), "k_factor launch");
     }
   }
