@@ -42,8 +42,10 @@ def _rough(nt, nl, seed):
     return np.random.default_rng(seed).standard_normal((nt, nl))
 
 
+# small n_theta give chains of 0..4 rows, where the twisted solve's halves are
+# empty or one row long
 SIZES = [(64, 128), (75, 150), (48, 96), (100, 200), (33, 70), (17, 34), (5, 10), (2, 4),
-         (1, 2), (3, 2), (128, 64), (256, 512), (31, 62), (7, 14)]
+         (1, 2), (3, 2), (128, 64), (256, 512), (31, 62), (7, 14), (4, 8), (6, 12), (9, 18), (10, 20)]
 
 
 @pytest.mark.parametrize("nt,nl", SIZES)
@@ -65,7 +67,8 @@ def test_solve_matches_oracle_and_closed_form_sh(sp, nt, nl, lmax):
     assert _rel(u, u_exact) < 1e-12
 
 
-@pytest.mark.parametrize("nt,nl", [(8, 16), (16, 32), (33, 70), (64, 128), (5, 10), (1, 2), (2, 4)])
+@pytest.mark.parametrize("nt,nl", [(8, 16), (16, 32), (33, 70), (64, 128), (5, 10), (1, 2), (2, 4), (3, 6),
+                                   (4, 8), (6, 12), (7, 14), (9, 18)])
 def test_adjoint_matches_oracle(sp, nt, nl):
     g = _rough(nt, nl, 7 + nt)
     ref = O.poisson_adjoint(g)
