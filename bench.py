@@ -46,11 +46,11 @@ FP64_PEAK_GFLOPS_FALLBACK = 1008.0
 # spectrum size n_theta * Kp (every stage streams the spectrum once or twice) and
 # reports null when the sources have changed since the capture.
 TRAFFIC_CAPTURE = {
-    "csrc_sha256": "cf7ef69c7387c4c3",
+    "csrc_sha256": "c95637f28df84252",
     "n_theta": 5000, "n_lambda": 5000,
-    "bytes": {"rows_forward": 200194560 + 142166272, "theta_forward": 200850688 + 141419264,
-              "solve": 662737408 + 321661952, "theta_inverse": 201466624 + 142551552,
-              "rows_inverse": 200288768 + 142938368},
+    "bytes": {"rows_forward": 200262144 + 142538240, "theta_forward": 200977152 + 141618944,
+              "solve": 662283520 + 321690624, "theta_inverse": 201590016 + 142290432,
+              "rows_inverse": 200357888 + 142897408},
 }
 
 

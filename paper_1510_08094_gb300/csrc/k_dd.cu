@@ -52,7 +52,8 @@ cudaError_t allow_transform_smem<dd>(int bytes) {
 
 void launch_refine(const Launch& l, const cpx<dd>* F, cpx<dd>* X, cpx<float>* Y, const float* fl,
                    const float* fiu, const float* fcu, int N, int K, int Kp, int first) {
-  k_refine<<<l.grid, l.threads, l.smem, l.stream>>>(F, X, Y, fl, fiu, fcu, N, K, Kp, first);
+  // two warps per CTA (the twisted form); l.threads is not used
+  k_refine<<<l.grid, kRefineThreads, 0, l.stream>>>(F, X, Y, fl, fiu, fcu, N, K, Kp, first);
 }
 void launch_zonal_extract(const Launch& l, const cpx<dd>* Wdd, cpx<double>* Z, int N, int Kp) {
   k_zonal_extract<<<l.grid, l.threads, l.smem, l.stream>>>(Wdd, Z, N, Kp);

@@ -1198,77 +1198,126 @@ union RefRing {
   RefSlotDown down[16];
 };
 constexpr int kRefRing = 16;
+constexpr int kRefineThreads = 64;
 
-__global__ void __launch_bounds__(32) k_refine(const cpx<dd>* __restrict__ F, cpx<dd>* __restrict__ X,
-                                               cpx<float>* __restrict__ Y, const float* __restrict__ fl,
-                                               const float* __restrict__ fiu, const float* __restrict__ fcu,
-                                               int N, int K, int Kp, int first) {
-  __shared__ RefRing ring;
-  const int lane = threadIdx.x;
+// R_t = F_t - (a_t X_{t-1} + b_t X_t + c_t X_{t+1}) in double-float, the
+// coefficients exact: a = (j-1)(j-2)/4, b = -(j^2 + 2k^2)/2, c = (j+1)(j+2)/4
+__device__ __forceinline__ cpx<dd> refine_residual(cpx<dd> f, float jf, dd two_k2, cpx<dd> xm1, cpx<dd> x0,
+                                                   cpx<dd> xp1) {
+  dd a = dd_prod(jf - 1.f, jf - 2.f);
+  a = dd(a.hi * 0.25f, a.lo * 0.25f);
+  dd b = dd_add(dd_prod(jf, jf), two_k2);
+  b = dd(b.hi * -0.5f, b.lo * -0.5f);
+  dd c = dd_prod(jf + 1.f, jf + 2.f);
+  c = dd(c.hi * 0.25f, c.lo * 0.25f);
+  cpx<dd> lx = cdd_scale(b, x0);
+  lx = {dd_fma(a, xm1.re, lx.re), dd_fma(a, xm1.im, lx.im)};
+  lx = {dd_fma(c, xp1.re, lx.re), dd_fma(c, xp1.im, lx.im)};
+  return {dd_sub(f.re, lx.re), dd_sub(f.im, lx.im)};
+}
+
+// Twisted form (tables of k_factor<float, true>): CTA = 2 warps over the same
+// 32 chains; warp 0 takes rows t < m upwards, warp 1 rows t > m downwards, both
+// forming residuals and the FP32 elimination of their half into Y; at the middle
+// row m (one barrier) warp 0 forms the row's residual and correction
+// d_m = (R_m - l_m y_{m-1} - g_m z_{m+1}) / gamma; both then substitute outwards
+// (d_t = y_t/u_t - (c_t/u_t) d_{t+1} above, d_t = z_t/v_t - (a_t/v_t) d_{t-1}
+// below) and add d to X.  Every read of X precedes the barrier, every write
+// follows it.
+__global__ void __launch_bounds__(kRefineThreads) k_refine(const cpx<dd>* __restrict__ F, cpx<dd>* __restrict__ X,
+                                                           cpx<float>* __restrict__ Y, const float* __restrict__ fl,
+                                                           const float* __restrict__ fiu,
+                                                           const float* __restrict__ fcu, int N, int K, int Kp,
+                                                           int first) {
+  __shared__ RefRing rings[2];
+  __shared__ cpx<float> meet[3][32];
+  const int lane = threadIdx.x & 31, half = threadIdx.x >> 5;
   const bool even = blockIdx.y == 1;
   const int k = blockIdx.x * 32 + lane;
-  if (k >= K || k == 0) return;
+  const bool active = k < K && k != 0;          // column k = 0 is the FP64 zonal path's
   const int j0 = even ? 2 : 1;
   const float kf = (float)k;
   const dd two_k2 = dd_mul(dd_prod(kf, kf), dd(2.f, 0.f));   // 2 k^2, exact
+  RefRing& ring = rings[half];
+  const cpx<dd> zero = {dd(0.f, 0.f), dd(0.f, 0.f)};
   if (j0 < N) {
     const int M = (N - 1 - j0) / 2 + 1;
+    const int m = (M - 1) / 2;
     const size_t stride = (size_t)2 * Kp;
-    const size_t base = (size_t)j0 * Kp + k;
-    // ascending: residual and FP32 forward elimination.  X_{t+1} is prefetched
-    // with row t's F; X_t and X_{t-1} stay in registers.
-    auto issue_up = [&](int t) {
-      if (t < M) {
-        RefSlot& sl = ring.up[t & (kRefRing - 1)];
+    const size_t base = (size_t)j0 * Kp + (active ? k : 0);
+    // first sweep of this half: rows t = t0 + dir q, q < len; the neighbour
+    // X_{t+dir} is prefetched with row t's F, X_t and X_{t-dir} stay in registers
+    const int t0 = half ? M - 1 : 0, dir = half ? -1 : 1, len = half ? M - 1 - m : m;
+    auto issue_up = [&](int q) {
+      if (active && q < len) {
+        const int t = t0 + dir * q;
+        RefSlot& sl = ring.up[q & (kRefRing - 1)];
         cp_async16(&sl.f[lane], F + base + t * stride);
-        if (!first) {
-          if (t + 1 < M) cp_async16(&sl.x[lane], X + base + (t + 1) * stride);
-        }
+        const int tn = t + dir;
+        if (!first && tn >= 0 && tn < M) cp_async16(&sl.x[lane], X + base + tn * stride);
         unsigned sa = (unsigned)__cvta_generic_to_shared(&sl.a[lane]);
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(fl + base + t * stride) : "memory");
       }
       cp_commit();
     };
-    for (int t = 0; t < kRefRing; ++t) issue_up(t);
-    cpx<dd> xm1 = {dd(0.f, 0.f), dd(0.f, 0.f)};
-    cpx<dd> x0 = {dd(0.f, 0.f), dd(0.f, 0.f)};
-    if (!first) x0 = X[base];
-    cpx<float> y = {0.f, 0.f};
-    float jf = (float)j0;                       // j of row t, exact in float
-    for (int t = 0; t < M; ++t, jf += 2.f) {
+    for (int q = 0; q < kRefRing; ++q) issue_up(q);
+    cpx<dd> xprev = zero, xcur = zero;          // X_{t - dir}, X_t
+    if (!first && active && len > 0) xcur = X[base + t0 * stride];
+    cpx<float> e = {0.f, 0.f};
+    float jf = (float)(j0 + 2 * t0);            // j of row t, exact in float
+    const float djf = 2.f * (float)dir;
+    for (int q = 0; q < len; ++q, jf += djf) {
       cp_wait<kRefRing - 1>();
-      const RefSlot& sl = ring.up[t & (kRefRing - 1)];
-      cpx<dd> r = sl.f[lane];
-      float l = sl.a[lane];
-      cpx<dd> xp1 = {dd(0.f, 0.f), dd(0.f, 0.f)};
-      if (!first) {
-        if (t + 1 < M) xp1 = sl.x[lane];
-        // exact coefficients: a = (j-1)(j-2)/4, b = -(j^2 + 2k^2)/2, c = (j+1)(j+2)/4
-        dd a = dd_prod(jf - 1.f, jf - 2.f);
-        a = dd(a.hi * 0.25f, a.lo * 0.25f);
-        dd b = dd_add(dd_prod(jf, jf), two_k2);
-        b = dd(b.hi * -0.5f, b.lo * -0.5f);
-        dd c = dd_prod(jf + 1.f, jf + 2.f);
-        c = dd(c.hi * 0.25f, c.lo * 0.25f);
-        cpx<dd> lx = cdd_scale(b, x0);
-        lx = {dd_fma(a, xm1.re, lx.re), dd_fma(a, xm1.im, lx.im)};
-        lx = {dd_fma(c, xp1.re, lx.re), dd_fma(c, xp1.im, lx.im)};
-        r = {dd_sub(r.re, lx.re), dd_sub(r.im, lx.im)};
+      const RefSlot& sl = ring.up[q & (kRefRing - 1)];
+      if (active) {
+        const int t = t0 + dir * q;
+        cpx<dd> r = sl.f[lane];
+        const float l = sl.a[lane];
+        cpx<dd> xnext = zero;
+        if (!first) {
+          const int tn = t + dir;
+          if (tn >= 0 && tn < M) xnext = sl.x[lane];
+          // ascending: X_{t-1} = xprev, X_{t+1} = xnext; descending the reverse
+          r = half ? refine_residual(r, jf, two_k2, xnext, xcur, xprev)
+                   : refine_residual(r, jf, two_k2, xprev, xcur, xnext);
+        }
+        const cpx<float> rf = {r.re.hi + r.re.lo, r.im.hi + r.im.lo};
+        e = {fmaf(-l, e.re, rf.re), fmaf(-l, e.im, rf.im)};
+        Y[base + t * stride] = e;
+        xprev = xcur;
+        xcur = xnext;
       }
-      cpx<float> rf = {r.re.hi + r.re.lo, r.im.hi + r.im.lo};
-      y = {fmaf(-l, y.re, rf.re), fmaf(-l, y.im, rf.im)};
-      Y[base + t * stride] = y;
-      xm1 = x0;
-      x0 = xp1;
-      issue_up(t + kRefRing);
+      issue_up(q + kRefRing);
     }
     cp_wait_all();
+    meet[half][lane] = e;
+    __syncthreads();
+    if (half == 0 && active) {
+      // the middle row: residual from X_{m-1}, X_m, X_{m+1} and the correction
+      cpx<dd> r = F[base + m * stride];
+      if (!first) {
+        const cpx<dd> xa = m > 0 ? X[base + (m - 1) * stride] : zero;
+        const cpx<dd> xb = X[base + m * stride];
+        const cpx<dd> xc = m + 1 < M ? X[base + (m + 1) * stride] : zero;
+        r = refine_residual(r, (float)(j0 + 2 * m), two_k2, xa, xb, xc);
+      }
+      const cpx<float> rf = {r.re.hi + r.re.lo, r.im.hi + r.im.lo};
+      const cpx<float> ym1 = meet[0][lane], zp1 = meet[1][lane];
+      const float lm = fl[base + m * stride], ig = fiu[base + m * stride], gm = fcu[base + m * stride];
+      const cpx<float> dm = {ig * (rf.re - lm * ym1.re - gm * zp1.re), ig * (rf.im - lm * ym1.im - gm * zp1.im)};
+      cpx<dd> xv = first ? zero : X[base + m * stride];
+      xv = {dd_add(xv.re, dd(dm.re, 0.f)), dd_add(xv.im, dd(dm.im, 0.f))};
+      X[base + m * stride] = xv;
+      meet[2][lane] = dm;
+    }
+    __syncthreads();
     __threadfence();
-    // descending: FP32 back substitution and the double-float update of X
-    auto issue_down = [&](int r) {
-      int t = M - 1 - r;
-      if (t >= 0) {
-        RefSlotDown& sl = ring.down[r & (kRefRing - 1)];
+    // second sweep of this half: rows t1 + dir2 q (outwards from the middle row)
+    const int t1 = half ? m + 1 : m - 1, dir2 = half ? 1 : -1;
+    auto issue_down = [&](int q) {
+      if (active && q < len) {
+        const int t = t1 + dir2 * q;
+        RefSlotDown& sl = ring.down[q & (kRefRing - 1)];
         cp_async8(&sl.y[lane], Y + base + t * stride);
         if (!first) cp_async16(&sl.x[lane], X + base + t * stride);
         unsigned sa = (unsigned)__cvta_generic_to_shared(&sl.a[lane]);
@@ -1278,29 +1327,31 @@ __global__ void __launch_bounds__(32) k_refine(const cpx<dd>* __restrict__ F, cp
       }
       cp_commit();
     };
-    for (int r = 0; r < kRefRing; ++r) issue_down(r);
-    cpx<float> dlt = {0.f, 0.f};
-    for (int r = 0; r < M; ++r) {
+    for (int q = 0; q < kRefRing; ++q) issue_down(q);
+    cpx<float> dlt = meet[2][lane];
+    for (int q = 0; q < len; ++q) {
       cp_wait<kRefRing - 1>();
-      const RefSlotDown& sl = ring.down[r & (kRefRing - 1)];
-      cpx<float> yv = sl.y[lane];
-      float iu = sl.a[lane], cu = sl.b[lane];
-      const int t = M - 1 - r;
-      dlt = {fmaf(yv.re, iu, -cu * dlt.re), fmaf(yv.im, iu, -cu * dlt.im)};
-      cpx<dd> xv = {dd(0.f, 0.f), dd(0.f, 0.f)};
-      if (!first) xv = sl.x[lane];
-      xv = {dd_add(xv.re, dd(dlt.re, 0.f)), dd_add(xv.im, dd(dlt.im, 0.f))};
-      X[base + t * stride] = xv;
-      issue_down(r + kRefRing);
+      const RefSlotDown& sl = ring.down[q & (kRefRing - 1)];
+      if (active) {
+        const int t = t1 + dir2 * q;
+        const cpx<float> yv = sl.y[lane];
+        const float iu = sl.a[lane], cu = sl.b[lane];
+        dlt = {fmaf(yv.re, iu, -cu * dlt.re), fmaf(yv.im, iu, -cu * dlt.im)};
+        cpx<dd> xv = zero;
+        if (!first) xv = sl.x[lane];
+        xv = {dd_add(xv.re, dd(dlt.re, 0.f)), dd_add(xv.im, dd(dlt.im, 0.f))};
+        X[base + t * stride] = xv;
+      }
+      issue_down(q + kRefRing);
     }
     cp_wait_all();
   }
-  if (even) {
+  if (even && half == 0 && active) {
     // row 0 closure in double-float: X_0 = (X_2 - F_0)/k^2 (k even), 0 (k odd)
-    cpx<dd> x0v = {dd(0.f, 0.f), dd(0.f, 0.f)};
+    cpx<dd> x0v = zero;
     if (!(k & 1)) {
       __threadfence();
-      cpx<dd> x2 = (2 < N) ? X[(size_t)2 * Kp + k] : cpx<dd>{dd(0.f, 0.f), dd(0.f, 0.f)};
+      cpx<dd> x2 = (2 < N) ? X[(size_t)2 * Kp + k] : zero;
       cpx<dd> f0 = F[k];
       dd ik2 = dd_from_double(1.0 / ((double)k * (double)k));
       x0v = {dd_mul(dd_sub(x2.re, f0.re), ik2), dd_mul(dd_sub(x2.im, f0.im), ik2)};

@@ -68,8 +68,8 @@ cudaError_t allow_transform_smem(int bytes);
 template <typename S>
 void launch_solve(bool adj, const Launch& l, cpx<S>* W, const S* fl, const S* fiu, const S* fcu, int N, int K,
                   int Kp);
-// twist: the twisted factorisation k_solve needs; false: the top-down one of the
-// zonal scan, the batched kernels and the refinement
+// twist: the twisted factorisation k_solve and k_refine need; false: the
+// top-down one of the zonal scan and the batched kernels
 template <typename S>
 void launch_factor(const Launch& l, S* fl, S* fiu, S* fcu, int N, int K, int Kp, bool twist);
 

@@ -886,9 +886,9 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
       sp::launch_factor<double>(sp::Launch{dim3(blocks), threads, 0, 0}, p->fac_l, p->fac_iu, p->fac_cu, p->N,
                                 p->K, p->Kp, true);
     } else {
-      // the FP32 form solves with k_solve (twisted); the refinement with k_refine (top-down)
+      // twisted, for k_solve (FP32) and k_refine (FP32 + refinement)
       sp::launch_factor<float>(sp::Launch{dim3(blocks), threads, 0, 0}, p->f32_l, p->f32_iu, p->f32_cu, p->N,
-                               p->K, p->Kp, precision == SP_FP32);
+                               p->K, p->Kp, true);
       sp::launch_factor<double>(sp::Launch{dim3(1), threads, 0, 0}, p->z_l, p->z_iu, p->z_cu, p->N, 1, 2, false);
     }
     step(cudaGetLastError(), "k_factor launch");
