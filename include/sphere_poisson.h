@@ -141,12 +141,14 @@ int sphere_poisson_solve_adjoint(sp_plan_t plan, const double* ubar, double* fba
  * Host-buffer convenience form of sphere_poisson_solve: copies f_host to the
  * device, solves, copies u back to u_host and synchronises before returning.
  * device_buffer must hold host_buffer_bytes (from sphere_poisson_host_buffer_size):
- * room for f, u and the workspace.  For single plans with n_theta >= 16 the grid
- * moves in 8 row chunks on a plan-owned copy stream, overlapped with the
+ * room for f, u and the workspace.  For single plans with n_theta >= 32 the grid
+ * moves in 16 row chunks on a plan-owned copy stream, overlapped with the
  * longitude transforms (the forward transform of a chunk starts when its rows
- * have arrived; the rows of u return as the inverse transform finishes them);
- * calls on one plan from several host threads must be serialised.  Pinned
- * host memory gives the fastest copies; pageable memory also works.
+ * have arrived; the rows of u return as the inverse transform finishes them),
+ * and consecutive chunks' transforms alternate between `stream` and a second
+ * plan-owned stream; calls on one plan from several host threads must be
+ * serialised.  Pinned host memory gives the fastest copies; pageable memory
+ * also works.
  */
 int sphere_poisson_host_buffer_size(sp_plan_t plan, size_t* device_buffer_bytes);
 int sphere_poisson_solve_host(sp_plan_t plan, const double* f_host, double* u_host,
