@@ -46,11 +46,11 @@ FP64_PEAK_GFLOPS_FALLBACK = 1008.0
 # spectrum size n_theta * Kp (every stage streams the spectrum once or twice) and
 # reports null when the sources have changed since the capture.
 TRAFFIC_CAPTURE = {
-    "csrc_sha256": "c95637f28df84252",
+    "csrc_sha256": "22adb68835dcf59e",
     "n_theta": 5000, "n_lambda": 5000,
-    "bytes": {"rows_forward": 200262144 + 142538240, "theta_forward": 200977152 + 141618944,
-              "solve": 662283520 + 321690624, "theta_inverse": 201590016 + 142290432,
-              "rows_inverse": 200357888 + 142897408},
+    "bytes": {"rows_forward": 200238080 + 142479104, "theta_forward": 201291776 + 141524736,
+              "solve": 662390272 + 321816320, "theta_inverse": 200931072 + 142281216,
+              "rows_inverse": 200330240 + 142811136},
 }
 
 

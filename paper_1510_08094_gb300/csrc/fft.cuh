@@ -117,13 +117,22 @@ __device__ __forceinline__ void load_stage_tw(const cpx<T>* __restrict__ p, cpx<
 // read as RP/2 16-byte loads
 template <int R>
 __device__ __forceinline__ void load_stage_tw(const cpx<float>* __restrict__ p, cpx<float>* w) {
-  constexpr int RP = (R + 1) & ~1;
-#pragma unroll
-  for (int i = 0; i < RP / 2; ++i) {
-    const float4 q = __ldg(reinterpret_cast<const float4*>(p) + i);
-    if (2 * i < R) w[2 * i] = {q.x, q.y};
-    if (2 * i + 1 < R) w[2 * i + 1] = {q.z, q.w};
+  // w^1 and w^2 from the table (one 16-byte load), higher powers by products of
+  // depth <= 2 (w^3 = w^2 w, w^4 = w^2 w^2, w^5 = w^4 w, w^6 = w^4 w^2, w^7 = w^4 w^3)
+  const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+  w[1] = {q.z, q.w};
+  if constexpr (R > 2) {
+    const float4 q2 = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    w[2] = {q2.x, q2.y};
   }
+  auto mul = [](cpx<float> a, cpx<float> b) {
+    return cpx<float>{fmaf(a.re, b.re, -a.im * b.im), fmaf(a.re, b.im, a.im * b.re)};
+  };
+  if constexpr (R > 3) w[3] = mul(w[2], w[1]);
+  if constexpr (R > 4) w[4] = mul(w[2], w[2]);
+  if constexpr (R > 5) w[5] = mul(w[4], w[1]);
+  if constexpr (R > 6) w[6] = mul(w[4], w[2]);
+  if constexpr (R > 7) w[7] = mul(w[4], w[3]);
 }
 
 // ---------------------------------------------------------------------------

@@ -205,7 +205,7 @@ __device__ __forceinline__ void rows_forward_load(int row0, cpx<T>* __restrict__
   for (int r = 0; r < rows; ++r) {
     const int row = row0 + r;
     dd acc(0.f, 0.f);
-#pragma unroll 4
+#pragma unroll (sizeof(T) == 4 ? 8 : 4)
     for (int q = threadIdx.x; q < L; q += blockDim.x) {
       cpx<T> z = {(T)0, (T)0};
       if (row < nt) {
