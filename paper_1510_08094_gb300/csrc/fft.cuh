@@ -156,6 +156,10 @@ __device__ __forceinline__ void dft4(cpx<T>* v) {
   v[3] = d0 - d1;
 }
 
+// In the butterflies below a constant factor of a term that is only added to
+// or subtracted from another is folded into the final additions as FMAs
+// (y = t +- i s w with s real: y.re = fma(-+s, w.im, t.re), ...), which saves
+// the separate multiplications on the FP64 pipe.
 template <int DIR, typename T>
 __device__ __forceinline__ void dft8(cpx<T>* v) {
   const T h = (T)0.70710678118654752440084436210484903928;
@@ -170,20 +174,29 @@ __device__ __forceinline__ void dft8(cpx<T>* v) {
     cpx<T> s0 = o[0] + o[2], d0 = o[0] - o[2], s1 = o[1] + o[3], d1 = rot<DIR>(o[1] - o[3]);
     o[0] = s0 + s1; o[2] = s0 - s1; o[1] = d0 + d1; o[3] = d0 - d1;
   }
-  // twiddles W8^k (DIR sense): W8^1 = (1 + DIR i)/sqrt2, W8^2 = DIR i, W8^3 = (-1 + DIR i)/sqrt2
-  cpx<T> t1, t3;
-  if (DIR < 0) {
-    t1 = {h * (o[1].re + o[1].im), h * (o[1].im - o[1].re)};
-    t3 = {h * (o[3].im - o[3].re), -h * (o[3].re + o[3].im)};
-  } else {
-    t1 = {h * (o[1].re - o[1].im), h * (o[1].im + o[1].re)};
-    t3 = {-h * (o[3].re + o[3].im), h * (o[3].re - o[3].im)};
-  }
+  // twiddles W8^k (DIR sense): W8^1 = (1 + DIR i)/sqrt2, W8^2 = DIR i, W8^3 = (-1 + DIR i)/sqrt2:
+  //   W8^1 o1 = h (p1, q1),  W8^3 o3 = h (ha p3, hb q3) with the signs ha, hb
+  //   (DIR < 0: ( o3.im - o3.re, -(o3.re + o3.im)); DIR > 0: (-(o3.re + o3.im), o3.re - o3.im))
+  const T p1 = DIR < 0 ? o[1].re + o[1].im : o[1].re - o[1].im;
+  const T q1 = DIR < 0 ? o[1].im - o[1].re : o[1].im + o[1].re;
+  const T p3 = DIR < 0 ? o[3].im - o[3].re : o[3].re + o[3].im;
+  const T q3 = DIR < 0 ? o[3].re + o[3].im : o[3].re - o[3].im;
+  const T ha = DIR < 0 ? h : -h, hb = DIR < 0 ? -h : h;
   cpx<T> t2 = rot<DIR>(o[2]);
   v[0] = e[0] + o[0]; v[4] = e[0] - o[0];
-  v[1] = e[1] + t1;   v[5] = e[1] - t1;
+  v[1] = {fma(h, p1, e[1].re), fma(h, q1, e[1].im)};
+  v[5] = {fma(-h, p1, e[1].re), fma(-h, q1, e[1].im)};
   v[2] = e[2] + t2;   v[6] = e[2] - t2;
-  v[3] = e[3] + t3;   v[7] = e[3] - t3;
+  v[3] = {fma(ha, p3, e[3].re), fma(hb, q3, e[3].im)};
+  v[7] = {fma(-ha, p3, e[3].re), fma(-hb, q3, e[3].im)};
+}
+
+// y = t + DIR i s w and y' = t - DIR i s w for real s
+template <int DIR, typename T>
+__device__ __forceinline__ void plus_minus_i(cpx<T> t, T s, cpx<T> w, cpx<T>& y, cpx<T>& yc) {
+  const T g = DIR < 0 ? s : -s;              // DIR i s w = (-DIR s w.im, DIR s w.re)
+  y = {fma(g, w.im, t.re), fma(-g, w.re, t.im)};
+  yc = {fma(-g, w.im, t.re), fma(g, w.re, t.im)};
 }
 
 template <int DIR, typename T>
@@ -192,35 +205,34 @@ __device__ __forceinline__ void dft3(cpx<T>* v) {
   const T s = (T)0.86602540378443864676372317075293618347;  // sin(2 pi / 3)
   cpx<T> a = v[1] + v[2], b = v[1] - v[2];
   cpx<T> t = {fma(c, a.re, v[0].re), fma(c, a.im, v[0].im)};
-  cpx<T> sb = s * b;
   v[0] = v[0] + a;
   // y1 = t + DIR i s b, y2 = t - DIR i s b
-  cpx<T> isb = DIR < 0 ? cpx<T>{sb.im, -sb.re} : cpx<T>{-sb.im, sb.re};
-  v[1] = t + isb;
-  v[2] = t - isb;
+  plus_minus_i<DIR>(t, s, b, v[1], v[2]);
 }
 
+// 5 points with cos(2 pi/5) = (sqrt5 - 1)/4, cos(4 pi/5) = -(sqrt5 + 1)/4:
+//   y0 = x0 + S, t1,2 = x0 - S/4 +- (sqrt5/4) D  (S = a1 + a2, D = a1 - a2),
+//   y1,4 = t1 +- DIR i s1 (b1 + r b2), y2,3 = t2 +- DIR i s2 (b1 - b2 / r),
+// s1 = sin(2 pi/5), s2 = sin(4 pi/5), r = s2/s1 = (sqrt5 - 1)/2.
 template <int DIR, typename T>
 __device__ __forceinline__ void dft5(cpx<T>* v) {
-  const T c1 = (T)0.30901699437494742410229341718281905886;   // cos(2 pi/5)
-  const T c2 = (T)-0.80901699437494742410229341718281905886;  // cos(4 pi/5)
+  const T q5 = (T)0.55901699437494742410229341718281905886;   // sqrt5 / 4
   const T s1 = (T)0.95105651629515357211643933337938214340;   // sin(2 pi/5)
   const T s2 = (T)0.58778525229247312916870595463907276860;   // sin(4 pi/5)
+  const T r = (T)0.61803398874989484820458683436563811772;    // s2 / s1
+  const T ri = (T)1.61803398874989484820458683436563811772;   // s1 / s2
   cpx<T> a1 = v[1] + v[4], b1 = v[1] - v[4];
   cpx<T> a2 = v[2] + v[3], b2 = v[2] - v[3];
   cpx<T> x0 = v[0];
-  cpx<T> t1 = {fma(c2, a2.re, fma(c1, a1.re, x0.re)), fma(c2, a2.im, fma(c1, a1.im, x0.im))};
-  cpx<T> t2 = {fma(c1, a2.re, fma(c2, a1.re, x0.re)), fma(c1, a2.im, fma(c2, a1.im, x0.im))};
-  cpx<T> u1 = {fma(s2, b2.re, s1 * b1.re), fma(s2, b2.im, s1 * b1.im)};
-  cpx<T> u2 = {fma(-s1, b2.re, s2 * b1.re), fma(-s1, b2.im, s2 * b1.im)};
-  v[0] = x0 + a1 + a2;
-  // y1 = t1 + DIR i u1, y4 = t1 - DIR i u1, y2 = t2 + DIR i u2, y3 = t2 - DIR i u2
-  cpx<T> iu1 = DIR < 0 ? cpx<T>{u1.im, -u1.re} : cpx<T>{-u1.im, u1.re};
-  cpx<T> iu2 = DIR < 0 ? cpx<T>{u2.im, -u2.re} : cpx<T>{-u2.im, u2.re};
-  v[1] = t1 + iu1;
-  v[4] = t1 - iu1;
-  v[2] = t2 + iu2;
-  v[3] = t2 - iu2;
+  cpx<T> S = a1 + a2, D = a1 - a2;
+  cpx<T> m = {fma((T)-0.25, S.re, x0.re), fma((T)-0.25, S.im, x0.im)};
+  cpx<T> t1 = {fma(q5, D.re, m.re), fma(q5, D.im, m.im)};
+  cpx<T> t2 = {fma(-q5, D.re, m.re), fma(-q5, D.im, m.im)};
+  cpx<T> w1 = {fma(r, b2.re, b1.re), fma(r, b2.im, b1.im)};
+  cpx<T> w2 = {fma(-ri, b2.re, b1.re), fma(-ri, b2.im, b1.im)};
+  v[0] = x0 + S;
+  plus_minus_i<DIR>(t1, s1, w1, v[1], v[4]);
+  plus_minus_i<DIR>(t2, s2, w2, v[2], v[3]);
 }
 
 // Generic odd R: pair outputs a and R-a, using p_b = x_b + x_{R-b}, q_b = x_b - x_{R-b}.
