@@ -25,6 +25,19 @@ template <typename T> __device__ __forceinline__ cpx<T> operator+(cpx<T> a, cpx<
 template <typename T> __device__ __forceinline__ cpx<T> operator-(cpx<T> a, cpx<T> b) { return {a.re - b.re, a.im - b.im}; }
 template <typename T> __device__ __forceinline__ cpx<T> operator*(T s, cpx<T> a) { return {s * a.re, s * a.im}; }
 template <typename T> __device__ __forceinline__ cpx<T> conj(cpx<T> a) { return {a.re, -a.im}; }
+// x, negated when c is set, by flipping the sign bit(s) with integer operations:
+// a runtime-conditional negation written as a select between x and -x costs an
+// FP64 (or FP32) add per element, on GB300's narrow FP64 pipe a real cost
+__device__ __forceinline__ double neg_if(double x, bool c) {
+  return __longlong_as_double(__double_as_longlong(x) ^ ((long long)c << 63));
+}
+__device__ __forceinline__ float neg_if(float x, bool c) {
+  return __int_as_float(__float_as_int(x) ^ ((int)c << 31));
+}
+__device__ __forceinline__ dd neg_if(dd x, bool c) { return dd(neg_if(x.hi, c), neg_if(x.lo, c)); }
+template <typename T> __device__ __forceinline__ cpx<T> neg_if(cpx<T> a, bool c) {
+  return {neg_if(a.re, c), neg_if(a.im, c)};
+}
 // a * b
 template <typename T> __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
   return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};

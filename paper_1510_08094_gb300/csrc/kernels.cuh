@@ -250,9 +250,11 @@ __device__ __forceinline__ void rows_forward_finish(int row0, cpx<T>* __restrict
       const cpx<T> A = zk + zc, D = zk - zc;
       const T x1 = fma(e.re, D.im, e.im * D.re), x2 = fma(e.re, D.re, -(e.im * D.im));   // e D = x2 + i x1
       const T hs = ADJ ? (k == 0 ? (T)0.5 : (T)1) : hrs;
-      Wr[k] = {hs * (A.re + x1), hs * (A.im - x2)};
+      // the scale taken into the final FMAs: s (A.re + x1) = fma(s, x1, s A.re), ...
+      const cpx<T> hA = {hs * A.re, hs * A.im};
+      Wr[k] = {fma(hs, x1, hA.re), fma(-hs, x2, hA.im)};
       const int kk = L - k;
-      if (kk != k) Wr[kk] = {hs * (A.re - x1), -(hs * (A.im + x2))};
+      if (kk != k) Wr[kk] = {fma(-hs, x1, hA.re), fma(-hs, x2, -hA.im)};
    }
    for (int k = K + threadIdx.x; k < Kp; k += blockDim.x) Wr[k] = {(T)0, (T)0};
   }
@@ -477,8 +479,7 @@ __device__ __forceinline__ void theta_forward_load(int k0, cpx<T>* __restrict__ 
     int k = k0 + c;
     cpx<T> v = {(T)0, (T)0};
     if (k < K) {
-      v = src(i, c);
-      if ((k & 1) && (i & 1)) v = {-v.re, -v.im};
+      v = neg_if(src(i, c), (k & 1) && (i & 1));
     }
     sm[c * N + __ldg(perm + makhoul_pos(i, N))] = v;
   }
@@ -527,9 +528,9 @@ __device__ __forceinline__ void theta_forward_finish(int k0, cpx<T>* __restrict_
       if (pair) out[(size_t)jj * Kp] = ojj;
     } else {
       // -i p, times -1 in the coefficient convention ((-1)^k for k odd)
-      const T sg = (zonal & 2) ? (T)-1 : (T)1;
-      out[(size_t)j * Kp] = j == 0 ? cpx<T>{(T)0, (T)0} : cpx<T>{sg * pjj.im, -(sg * pjj.re)};
-      if (pair) out[(size_t)jj * Kp] = {sg * pj.im, -(sg * pj.re)};
+      const bool ng = (zonal & 2) != 0;
+      out[(size_t)j * Kp] = j == 0 ? cpx<T>{(T)0, (T)0} : cpx<T>{neg_if(pjj.im, ng), neg_if(pjj.re, !ng)};
+      if (pair) out[(size_t)jj * Kp] = {neg_if(pj.im, ng), neg_if(pj.re, !ng)};
     }
   }
 }
@@ -664,10 +665,9 @@ __device__ __forceinline__ void theta_inverse_load(int k0, cpx<T>* __restrict__ 
       xa = (T)0.5 * xa;
       xb = (T)0.5 * xb;
     }
-    if ((zonal & 2) && odd) {                  // input in the coefficient convention
-      xa = {-xa.re, -xa.im};
-      xb = {-xb.re, -xb.im};
-    }
+    const bool ng = (zonal & 2) && odd;        // input in the coefficient convention
+    xa = neg_if(xa, ng);
+    xb = neg_if(xb, ng);
     // Y_j, Y_{N-j}
     cpx<T> ya = odd ? xb : xa;
     cpx<T> yb = odd ? xa : xb;
@@ -693,7 +693,7 @@ __device__ __forceinline__ void theta_inverse_finish(int k0, cpx<T>* __restrict_
     if (ADJ) v = inv_n * v;
     if (k & 1) {
       // times i (-1)^i
-      v = (i & 1) ? cpx<T>{v.im, -v.re} : cpx<T>{-v.im, v.re};
+      v = {neg_if(v.im, !(i & 1)), neg_if(v.re, (i & 1) != 0)};
     }
     W[(size_t)i * Kp + k] = v;
   }
