@@ -46,11 +46,11 @@ FP64_PEAK_GFLOPS_FALLBACK = 1008.0
 # spectrum size n_theta * Kp (every stage streams the spectrum once or twice) and
 # reports null when the sources have changed since the capture.
 TRAFFIC_CAPTURE = {
-    "csrc_sha256": "22adb68835dcf59e",
+    "csrc_sha256": "5f72f958fe50273b",
     "n_theta": 5000, "n_lambda": 5000,
-    "bytes": {"rows_forward": 200238080 + 142479104, "theta_forward": 201291776 + 141524736,
-              "solve": 662390272 + 321816320, "theta_inverse": 200931072 + 142281216,
-              "rows_inverse": 200330240 + 142811136},
+    "bytes": {"rows_forward": 200347648 + 142671872, "theta_forward": 200848128 + 141853184,
+              "solve": 662456064 + 322026240, "theta_inverse": 200890368 + 142690048,
+              "rows_inverse": 200326912 + 142841856},
 }
 
 
