@@ -368,7 +368,8 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
 
 
-FORM_GROUPS = ("precision", "adjoint", "tangential_gradient", "vector_calculus", "lowrank", "paper_scale")
+FORM_GROUPS = ("precision", "adjoint", "transforms", "tangential_gradient", "vector_calculus", "lowrank",
+               "paper_scale")
 
 
 def measure_forms(sp, f, u_exact, u64, N, n, dev, ms_fp64, args):
@@ -434,6 +435,8 @@ def measure_forms(sp, f, u_exact, u64, N, n, dev, ms_fp64, args):
             entry["max_rel_err_vs_fp64_adjoint"] = float((out - sg64).abs().max() / sg64.abs().max())
         res[f"adjoint_{prec}"] = entry
         del plan, ws, out, sf
+    if "transforms" in want:
+        res["transforms"] = measure_transforms(sp, f, N, n, dev, steps, args)
     if "tangential_gradient" in want:
         res["tangential_gradient"] = measure_tangential(sp, f, N, n, dev, steps, args)
     if "vector_calculus" in want:
@@ -521,6 +524,42 @@ def measure_tangential(sp, f, N, n, dev, steps, args):
             "max_rel_err_vs_closed_form_xyz": errs,
             "closed_form_case": "1 + x + y^2 + x^2 y + x^4 + y^5 + (xyz)^2",
             "gpu_launches_per_call": 2 + 3 + 1 + 3 * 2}
+
+
+def measure_transforms(sp, f, N, n, dev, steps, args):
+    """The transforms alone (Section 4): coeffs2, sample and sum2 of the bench
+    input, each timed; accuracy from the round trip sample(coeffs2(f)) = f (the
+    input is band-limited inside the grid) and from sum2 of the paper's worked
+    example 1 + x + y^2 + x^2 y + x^4 + y^5 + (xyz)^2, whose integral is 216 pi/35."""
+    import torch
+    from synth import sh
+
+    plan = sp.Plan(N, n, device=dev, autotune=not args.no_autotune)
+    X = plan.coeffs2(f)
+    calls = {"coeffs2": lambda: plan.coeffs2(f), "sample": lambda: plan.sample(X), "sum2": lambda: plan.sum2(f)}
+    reps = max(3, min(steps, 10))
+    out = {}
+    for name, call in calls.items():
+        for _ in range(2):
+            call()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            call()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms_per_call": ms, "value": N * n / (ms * 1e-3)}
+    rt = float((plan.sample(X) - f).abs().max() / f.abs().max())
+    th = torch.tensor(sh.colatitudes(N), device=dev)[:, None]
+    la = torch.tensor(sh.longitudes(n), device=dev)[None, :]
+    x, y, z = torch.cos(la) * torch.sin(th), torch.sin(la) * torch.sin(th), torch.cos(th) + 0 * la
+    p = (1 + x + y ** 2 + x ** 2 * y + x ** 4 + y ** 5 + (x * y * z) ** 2).contiguous()
+    exact = 216 * math.pi / 35
+    return {"unit": "DOF/s", "calls": out, "max_rel_err_sample_coeffs2_roundtrip": rt,
+            "sum2_worked_example_abs_err": abs(plan.sum2(p) - exact),
+            "gpu_launches_per_call": {"coeffs2": 2, "sample": 2, "sum2": 3}}
 
 
 def measure_vector_calculus(sp, N, n, dev, steps, args):
