@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "dd.cuh"
+#include <type_traits>
 
 namespace sp {
 
@@ -117,7 +118,29 @@ struct FftDesc {
   // exp(-2 pi i a / R_s), a < R_s.  tw_len entries in all.
   int tw_off[kMaxStages];
   int dft_off[kMaxStages];
+  // radix-5 passes with Ns > 1: g_off[s] + 8 k holds butterfly k's scaled
+  // twiddle record for the FP64 kernels (see fft_pass), else -1
+  int g_off[kMaxStages];
   int tw_len;
+};
+
+// Scaled twiddle record of one radix-5 butterfly (16 doubles as 8 complex
+// entries).  Each twiddle is written w_r = sigma_r (1 + i tau_r), or, where
+// |Im w_r| > |Re w_r|, w_r = i sigma_r (1 + i tau_r), so |tau_r| <= 1 and
+// |sigma_r| >= 1/sqrt2; the butterfly then forms x_r (1 + i tau_r) (two FMAs),
+// rotates by i where flagged (sign-bit and register moves only), and carries the
+// real scales sigma_r through the 5-point DFT as the ratios and products below,
+// taken into its FMAs.
+struct Radix5Record {
+  double tau[4];        // tau_1 .. tau_4
+  double q4, q3, rho;   // sigma_4/sigma_1, sigma_3/sigma_2, sigma_2/sigma_1
+  double s1;            // sigma_1
+  double s1q;           // sigma_1 / 4
+  double q5s1;          // (sqrt5/4) sigma_1
+  double rrho, rirho;   // r rho, rho / r  (r = sin(4 pi/5) / sin(2 pi/5))
+  double ss1, ss2;      // sin(2 pi/5) sigma_1, sin(4 pi/5) sigma_1
+  long long rot;        // bit r-1: w_r carries the factor i
+  long long pad;
 };
 
 // the twiddles w[r], 0 < r < R, of one butterfly from its R-entry slot p
@@ -300,10 +323,51 @@ __device__ __forceinline__ void dft_any(cpx<T>* v, const cpx<T>* __restrict__ dt
 // Butterflies of a pass touch disjoint elements, so threads stream through
 // them holding only R values.
 // ---------------------------------------------------------------------------
+// the radix-5 butterfly on the scaled record (FP64; see Radix5Record): the same
+// outputs as twiddle multiplication followed by dft5, with 40 FP64 operations
+// instead of 48
+template <int DIR>
+__device__ __forceinline__ void radix5_scaled(cpx<double>* v, const Radix5Record* __restrict__ rec) {
+  const double2* q = reinterpret_cast<const double2*>(rec);
+  const double2 t01 = __ldg(q), t23 = __ldg(q + 1), qq = __ldg(q + 2), rs = __ldg(q + 3);
+  const double2 sq = __ldg(q + 4), rr = __ldg(q + 5), ss = __ldg(q + 6);
+  const long long rot = __ldg(&rec->rot);
+  const double tau[4] = {t01.x, t01.y, t23.x, t23.y};
+  cpx<double> h[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    // the inverse transform uses conj(w): tau -> -tau and the factor i -> -i
+    const double t = DIR < 0 ? tau[r] : -tau[r];
+    const cpx<double> x = v[r + 1];
+    const cpx<double> xt = {fma(-t, x.im, x.re), fma(t, x.re, x.im)};
+    const bool rt = (rot >> r) & 1;
+    // times i (forward) or -i (inverse) where flagged
+    h[r] = {rt ? neg_if(xt.im, DIR < 0) : xt.re, rt ? neg_if(xt.re, DIR > 0) : xt.im};
+  }
+  const double q4 = qq.x, q3 = qq.y, rho = rs.x, s1 = rs.y, s1q = sq.x, q5s1 = sq.y;
+  const double rrho = rr.x, rirho = rr.y, ss1 = ss.x, ss2 = ss.y;
+  const cpx<double> a1 = {fma(q4, h[3].re, h[0].re), fma(q4, h[3].im, h[0].im)};
+  const cpx<double> b1 = {fma(-q4, h[3].re, h[0].re), fma(-q4, h[3].im, h[0].im)};
+  const cpx<double> a2 = {fma(q3, h[2].re, h[1].re), fma(q3, h[2].im, h[1].im)};
+  const cpx<double> b2 = {fma(-q3, h[2].re, h[1].re), fma(-q3, h[2].im, h[1].im)};
+  const cpx<double> S = {fma(rho, a2.re, a1.re), fma(rho, a2.im, a1.im)};
+  const cpx<double> D = {fma(-rho, a2.re, a1.re), fma(-rho, a2.im, a1.im)};
+  const cpx<double> x0 = v[0];
+  v[0] = {fma(s1, S.re, x0.re), fma(s1, S.im, x0.im)};
+  const cpx<double> m = {fma(-s1q, S.re, x0.re), fma(-s1q, S.im, x0.im)};
+  const cpx<double> t1 = {fma(q5s1, D.re, m.re), fma(q5s1, D.im, m.im)};
+  const cpx<double> t2 = {fma(-q5s1, D.re, m.re), fma(-q5s1, D.im, m.im)};
+  const cpx<double> w1 = {fma(rrho, b2.re, b1.re), fma(rrho, b2.im, b1.im)};
+  const cpx<double> w2 = {fma(-rirho, b2.re, b1.re), fma(-rirho, b2.im, b1.im)};
+  plus_minus_i<DIR>(t1, ss1, w1, v[1], v[4]);
+  plus_minus_i<DIR>(t2, ss2, w2, v[2], v[3]);
+}
+
 template <int R, int DIR, typename T>
 __device__ __forceinline__ void fft_pass(cpx<T>* buf, int L, int nbatch, int Ns,
                                          const cpx<T>* __restrict__ stw, const cpx<T>* __restrict__ dtw,
-                                         const FastDiv& dnb, const FastDiv& dns) {
+                                         const FastDiv& dnb, const FastDiv& dns,
+                                         const cpx<T>* __restrict__ gtw = nullptr) {
   constexpr int RP = (R + 1) & ~1;
   const int nb = L / R;
   const int total = nb * nbatch;
@@ -316,6 +380,14 @@ __device__ __forceinline__ void fft_pass(cpx<T>* buf, int L, int nbatch, int Ns,
     cpx<T> v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = base[r * Ns];
+    if constexpr (R == 5 && std::is_same<T, double>::value) {
+      if (gtw) {
+        radix5_scaled<DIR>(v, reinterpret_cast<const Radix5Record*>(gtw) + k);
+#pragma unroll
+        for (int r = 0; r < R; ++r) base[r * Ns] = v[r];
+        continue;
+      }
+    }
     if (Ns > 1) {
       const cpx<T>* tk = stw + k * RP;
       if constexpr (R <= 8) {
@@ -387,11 +459,13 @@ __device__ __forceinline__ void fft_run(cpx<T>* buf, int nbatch, const FftDesc& 
     const int R = d.radix[s];
     const cpx<T>* stw = tw + d.tw_off[s];
     const cpx<T>* dtw = tw + d.dft_off[s];
+    // the scaled radix-5 records serve the FP64 kernels only
+    const cpx<T>* gtw = (std::is_same<T, double>::value && d.g_off[s] >= 0) ? tw + d.g_off[s] : nullptr;
     switch (R) {
       case 2: fft_pass<2, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
       case 3: fft_pass<3, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
       case 4: fft_pass<4, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
-      case 5: fft_pass<5, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 5: fft_pass<5, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s], gtw); break;
       case 7: fft_pass<7, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
       case 8: fft_pass<8, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
       default: break;

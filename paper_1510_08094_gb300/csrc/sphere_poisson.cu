@@ -87,6 +87,15 @@ bool make_fft_desc(int L, FftDesc* d) {
       off += (R + 1) & ~1;
     }
   }
+  ns = 1;
+  for (int t = 0; t < s; ++t) {
+    d->g_off[t] = -1;
+    if (d->radix[t] == 5 && ns > 1) {
+      d->g_off[t] = off;
+      off += ns * (int)(sizeof(sp::Radix5Record) / sizeof(cpx<double>));
+    }
+    ns *= d->radix[t];
+  }
   d->tw_len = off;
   return rest == 1;
 }
@@ -157,6 +166,42 @@ std::vector<cpx<double>> stage_twiddles(const FftDesc& d) {
       }
     if (R >= 7 && (R & 1))
       for (int a = 0; a < R; ++a) unit_root(a, R, &tab[d.dft_off[s] + a].re, &tab[d.dft_off[s] + a].im);
+    if (d.g_off[s] >= 0) {
+      // the FP64 radix-5 records: w_r = sigma_r (1 + i tau_r), or i sigma_r (1 + i tau_r)
+      // where |Im w_r| > |Re w_r|
+      const double q5 = 0.55901699437494742410229341718281905886;   // sqrt5 / 4
+      const double sn1 = 0.95105651629515357211643933337938214340;  // sin(2 pi/5)
+      const double sn2 = 0.58778525229247312916870595463907276860;  // sin(4 pi/5)
+      const double r5 = 0.61803398874989484820458683436563811772;   // sn2 / sn1
+      const double ri5 = 1.61803398874989484820458683436563811772;  // sn1 / sn2
+      for (int k = 0; k < ns; ++k) {
+        sp::Radix5Record rec = {};
+        double sg[4];
+        for (int r = 1; r <= 4; ++r) {
+          double re, im;
+          unit_root((long)r * k, (long)ns * R, &re, &im);
+          if (std::fabs(re) >= std::fabs(im)) {
+            sg[r - 1] = re;
+            rec.tau[r - 1] = im / re;
+          } else {
+            sg[r - 1] = im;
+            rec.tau[r - 1] = -re / im;
+            rec.rot |= 1LL << (r - 1);
+          }
+        }
+        rec.q4 = sg[3] / sg[0];
+        rec.q3 = sg[2] / sg[1];
+        rec.rho = sg[1] / sg[0];
+        rec.s1 = sg[0];
+        rec.s1q = 0.25 * sg[0];
+        rec.q5s1 = q5 * sg[0];
+        rec.rrho = r5 * rec.rho;
+        rec.rirho = ri5 * rec.rho;
+        rec.ss1 = sn1 * sg[0];
+        rec.ss2 = sn2 * sg[0];
+        std::memcpy(&tab[d.g_off[s] + k * (sizeof(rec) / sizeof(cpx<double>))], &rec, sizeof rec);
+      }
+    }
     ns *= R;
   }
   return tab;
