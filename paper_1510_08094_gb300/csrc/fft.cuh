@@ -118,8 +118,8 @@ struct FftDesc {
   // exp(-2 pi i a / R_s), a < R_s.  tw_len entries in all.
   int tw_off[kMaxStages];
   int dft_off[kMaxStages];
-  // radix-5 passes with Ns > 1: g_off[s] + 8 k holds butterfly k's scaled
-  // twiddle record for the FP64 kernels (see fft_pass), else -1
+  // radix-5 and radix-8 passes with Ns > 1: g_off[s] + 8 k holds butterfly k's
+  // scaled twiddle record for the FP64 kernels (see fft_pass), else -1
   int g_off[kMaxStages];
   int tw_len;
 };
@@ -141,6 +141,17 @@ struct Radix5Record {
   double ss1, ss2;      // sin(2 pi/5) sigma_1, sin(4 pi/5) sigma_1
   long long rot;        // bit r-1: w_r carries the factor i
   long long pad;
+};
+// The same for a radix-8 butterfly: the even inputs 0, 2, 4, 6 and the odd
+// inputs 1, 3, 5, 7 form their 4-point DFTs with the scales as ratios, the odd
+// half ending on the common scale sigma_1.
+struct Radix8Record {
+  double tau[7];        // tau_1 .. tau_7
+  double s4;            // sigma_4
+  double q62, s2;       // sigma_6/sigma_2, sigma_2
+  double q51, q73, q31; // sigma_5/sigma_1, sigma_7/sigma_3, sigma_3/sigma_1
+  double s1, s1h;       // sigma_1, sigma_1/sqrt2
+  long long rot;        // bit r-1: w_r carries the factor i
 };
 
 // the twiddles w[r], 0 < r < R, of one butterfly from its R-entry slot p
@@ -363,6 +374,66 @@ __device__ __forceinline__ void radix5_scaled(cpx<double>* v, const Radix5Record
   plus_minus_i<DIR>(t2, ss2, w2, v[2], v[3]);
 }
 
+// x w for the scaled twiddle w = sigma (1 + i tau) (or i sigma (1 + i tau) when
+// flagged), without the factor sigma: x (1 + i tau), then times i (forward) or
+// -i (inverse, which uses conj(w)) where flagged
+template <int DIR>
+__device__ __forceinline__ cpx<double> scaled_input(cpx<double> x, double tau, bool rt) {
+  const double t = DIR < 0 ? tau : -tau;
+  const cpx<double> xt = {fma(-t, x.im, x.re), fma(t, x.re, x.im)};
+  return {rt ? neg_if(xt.im, DIR < 0) : xt.re, rt ? neg_if(xt.re, DIR > 0) : xt.im};
+}
+
+// the radix-8 butterfly on the scaled record: the outputs of twiddle
+// multiplication followed by dft8, with 66 FP64 operations instead of 80
+template <int DIR>
+__device__ __forceinline__ void radix8_scaled(cpx<double>* v, const Radix8Record* __restrict__ rec) {
+  const double2* q = reinterpret_cast<const double2*>(rec);
+  const double2 a0 = __ldg(q), a1 = __ldg(q + 1), a2 = __ldg(q + 2), a3 = __ldg(q + 3);
+  const double2 a4 = __ldg(q + 4), a5 = __ldg(q + 5), a6 = __ldg(q + 6);
+  const double s1h = __ldg(&rec->s1h);
+  const long long rbits = __ldg(&rec->rot);
+  const double tau[7] = {a0.x, a0.y, a1.x, a1.y, a2.x, a2.y, a3.x};
+  const double s4 = a3.y, q62 = a4.x, s2 = a4.y, q51 = a5.x, q73 = a5.y, q31 = a6.x, s1 = a6.y;
+  cpx<double> h[8];
+  h[0] = v[0];
+#pragma unroll
+  for (int r = 1; r < 8; ++r) h[r] = scaled_input<DIR>(v[r], tau[r - 1], (rbits >> (r - 1)) & 1);
+  // even inputs: x0 + sigma_4 h4, sigma_2 (h2 +- q62 h6)
+  const cpx<double> s0 = {fma(s4, h[4].re, h[0].re), fma(s4, h[4].im, h[0].im)};
+  const cpx<double> d0 = {fma(-s4, h[4].re, h[0].re), fma(-s4, h[4].im, h[0].im)};
+  const cpx<double> u1 = {fma(q62, h[6].re, h[2].re), fma(q62, h[6].im, h[2].im)};
+  const cpx<double> w1 = rot<DIR>(cpx<double>{fma(-q62, h[6].re, h[2].re), fma(-q62, h[6].im, h[2].im)});
+  const cpx<double> e0 = {fma(s2, u1.re, s0.re), fma(s2, u1.im, s0.im)};
+  const cpx<double> e2 = {fma(-s2, u1.re, s0.re), fma(-s2, u1.im, s0.im)};
+  const cpx<double> e1 = {fma(s2, w1.re, d0.re), fma(s2, w1.im, d0.im)};
+  const cpx<double> e3 = {fma(-s2, w1.re, d0.re), fma(-s2, w1.im, d0.im)};
+  // odd inputs, on the common scale sigma_1
+  const cpx<double> y0 = {fma(q51, h[5].re, h[1].re), fma(q51, h[5].im, h[1].im)};
+  const cpx<double> z0 = {fma(-q51, h[5].re, h[1].re), fma(-q51, h[5].im, h[1].im)};
+  const cpx<double> y1 = {fma(q73, h[7].re, h[3].re), fma(q73, h[7].im, h[3].im)};
+  const cpx<double> z1 = rot<DIR>(cpx<double>{fma(-q73, h[7].re, h[3].re), fma(-q73, h[7].im, h[3].im)});
+  const cpx<double> o0 = {fma(q31, y1.re, y0.re), fma(q31, y1.im, y0.im)};
+  const cpx<double> o2 = {fma(-q31, y1.re, y0.re), fma(-q31, y1.im, y0.im)};
+  const cpx<double> o1 = {fma(q31, z1.re, z0.re), fma(q31, z1.im, z0.im)};
+  const cpx<double> o3 = {fma(-q31, z1.re, z0.re), fma(-q31, z1.im, z0.im)};
+  // combine with W8^a (as in dft8), the scale sigma_1 inside the FMAs
+  const double p1 = DIR < 0 ? o1.re + o1.im : o1.re - o1.im;
+  const double r1 = DIR < 0 ? o1.im - o1.re : o1.im + o1.re;
+  const double p3 = DIR < 0 ? o3.im - o3.re : o3.re + o3.im;
+  const double r3 = DIR < 0 ? o3.re + o3.im : o3.re - o3.im;
+  const double ha = DIR < 0 ? s1h : -s1h, hb = DIR < 0 ? -s1h : s1h;
+  const cpx<double> t2 = rot<DIR>(o2);
+  v[0] = {fma(s1, o0.re, e0.re), fma(s1, o0.im, e0.im)};
+  v[4] = {fma(-s1, o0.re, e0.re), fma(-s1, o0.im, e0.im)};
+  v[2] = {fma(s1, t2.re, e2.re), fma(s1, t2.im, e2.im)};
+  v[6] = {fma(-s1, t2.re, e2.re), fma(-s1, t2.im, e2.im)};
+  v[1] = {fma(s1h, p1, e1.re), fma(s1h, r1, e1.im)};
+  v[5] = {fma(-s1h, p1, e1.re), fma(-s1h, r1, e1.im)};
+  v[3] = {fma(ha, p3, e3.re), fma(hb, r3, e3.im)};
+  v[7] = {fma(-ha, p3, e3.re), fma(-hb, r3, e3.im)};
+}
+
 template <int R, int DIR, typename T>
 __device__ __forceinline__ void fft_pass(cpx<T>* buf, int L, int nbatch, int Ns,
                                          const cpx<T>* __restrict__ stw, const cpx<T>* __restrict__ dtw,
@@ -380,9 +451,10 @@ __device__ __forceinline__ void fft_pass(cpx<T>* buf, int L, int nbatch, int Ns,
     cpx<T> v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = base[r * Ns];
-    if constexpr (R == 5 && std::is_same<T, double>::value) {
+    if constexpr ((R == 5 || R == 8) && std::is_same<T, double>::value) {
       if (gtw) {
-        radix5_scaled<DIR>(v, reinterpret_cast<const Radix5Record*>(gtw) + k);
+        if constexpr (R == 5) radix5_scaled<DIR>(v, reinterpret_cast<const Radix5Record*>(gtw) + k);
+        else radix8_scaled<DIR>(v, reinterpret_cast<const Radix8Record*>(gtw) + k);
 #pragma unroll
         for (int r = 0; r < R; ++r) base[r * Ns] = v[r];
         continue;
@@ -467,7 +539,7 @@ __device__ __forceinline__ void fft_run(cpx<T>* buf, int nbatch, const FftDesc& 
       case 4: fft_pass<4, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
       case 5: fft_pass<5, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s], gtw); break;
       case 7: fft_pass<7, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
-      case 8: fft_pass<8, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 8: fft_pass<8, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s], gtw); break;
       default: break;
     }
     if constexpr (BIG) {

@@ -90,7 +90,8 @@ bool make_fft_desc(int L, FftDesc* d) {
   ns = 1;
   for (int t = 0; t < s; ++t) {
     d->g_off[t] = -1;
-    if (d->radix[t] == 5 && ns > 1) {
+    if ((d->radix[t] == 5 || d->radix[t] == 8) && ns > 1) {
+      static_assert(sizeof(sp::Radix5Record) == sizeof(sp::Radix8Record), "one record size");
       d->g_off[t] = off;
       off += ns * (int)(sizeof(sp::Radix5Record) / sizeof(cpx<double>));
     }
@@ -166,9 +167,38 @@ std::vector<cpx<double>> stage_twiddles(const FftDesc& d) {
       }
     if (R >= 7 && (R & 1))
       for (int a = 0; a < R; ++a) unit_root(a, R, &tab[d.dft_off[s] + a].re, &tab[d.dft_off[s] + a].im);
-    if (d.g_off[s] >= 0) {
-      // the FP64 radix-5 records: w_r = sigma_r (1 + i tau_r), or i sigma_r (1 + i tau_r)
-      // where |Im w_r| > |Re w_r|
+    // w_r = sigma_r (1 + i tau_r), or i sigma_r (1 + i tau_r) where |Im w_r| > |Re w_r|
+    auto scaled_root = [&](int r, int k, double* sigma, double* tau, long long* rot) {
+      double re, im;
+      unit_root((long)r * k, (long)ns * R, &re, &im);
+      if (std::fabs(re) >= std::fabs(im)) {
+        *sigma = re;
+        *tau = im / re;
+      } else {
+        *sigma = im;
+        *tau = -re / im;
+        *rot |= 1LL << (r - 1);
+      }
+    };
+    if (d.g_off[s] >= 0 && R == 8) {
+      const size_t per = sizeof(sp::Radix8Record) / sizeof(cpx<double>);
+      for (int k = 0; k < ns; ++k) {
+        sp::Radix8Record rec = {};
+        double sg[8] = {1.0};
+        for (int r = 1; r < 8; ++r) scaled_root(r, k, &sg[r], &rec.tau[r - 1], &rec.rot);
+        rec.s4 = sg[4];
+        rec.q62 = sg[6] / sg[2];
+        rec.s2 = sg[2];
+        rec.q51 = sg[5] / sg[1];
+        rec.q73 = sg[7] / sg[3];
+        rec.q31 = sg[3] / sg[1];
+        rec.s1 = sg[1];
+        rec.s1h = 0.70710678118654752440084436210484903928 * sg[1];
+        std::memcpy(&tab[d.g_off[s] + k * per], &rec, sizeof rec);
+      }
+    }
+    if (d.g_off[s] >= 0 && R == 5) {
+      // the FP64 radix-5 records
       const double q5 = 0.55901699437494742410229341718281905886;   // sqrt5 / 4
       const double sn1 = 0.95105651629515357211643933337938214340;  // sin(2 pi/5)
       const double sn2 = 0.58778525229247312916870595463907276860;  // sin(4 pi/5)
@@ -177,18 +207,7 @@ std::vector<cpx<double>> stage_twiddles(const FftDesc& d) {
       for (int k = 0; k < ns; ++k) {
         sp::Radix5Record rec = {};
         double sg[4];
-        for (int r = 1; r <= 4; ++r) {
-          double re, im;
-          unit_root((long)r * k, (long)ns * R, &re, &im);
-          if (std::fabs(re) >= std::fabs(im)) {
-            sg[r - 1] = re;
-            rec.tau[r - 1] = im / re;
-          } else {
-            sg[r - 1] = im;
-            rec.tau[r - 1] = -re / im;
-            rec.rot |= 1LL << (r - 1);
-          }
-        }
+        for (int r = 1; r <= 4; ++r) scaled_root(r, k, &sg[r - 1], &rec.tau[r - 1], &rec.rot);
         rec.q4 = sg[3] / sg[0];
         rec.q3 = sg[2] / sg[1];
         rec.rho = sg[1] / sg[0];
