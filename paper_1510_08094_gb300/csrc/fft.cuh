@@ -118,8 +118,8 @@ struct FftDesc {
   // exp(-2 pi i a / R_s), a < R_s.  tw_len entries in all.
   int tw_off[kMaxStages];
   int dft_off[kMaxStages];
-  // radix-5 and radix-8 passes with Ns > 1: g_off[s] + 8 k holds butterfly k's
-  // scaled twiddle record for the FP64 kernels (see fft_pass), else -1
+  // radix-2, 3, 4, 5 and 8 passes with Ns > 1: g_off[s] + 8 k holds butterfly
+  // k's scaled twiddle record for the FP64 kernels (see fft_pass), else -1
   int g_off[kMaxStages];
   int tw_len;
 };
@@ -152,6 +152,26 @@ struct Radix8Record {
   double q51, q73, q31; // sigma_5/sigma_1, sigma_7/sigma_3, sigma_3/sigma_1
   double s1, s1h;       // sigma_1, sigma_1/sqrt2
   long long rot;        // bit r-1: w_r carries the factor i
+};
+// radix 4: x0 +- sigma_2 h2 and sigma_1 (h1 +- q31 h3)
+struct Radix4Record {
+  double tau[3];
+  double s2, q31, s1;
+  long long rot;
+  double pad[9];
+};
+// radix 3: sigma_1 (h1 +- q21 h2), then the constants -1/2 and sin(2 pi/3) times sigma_1
+struct Radix3Record {
+  double tau[2];
+  double q21, s1, s1half, ss1;
+  long long rot;
+  double pad[9];
+};
+// radix 2: x0 +- sigma_1 h1
+struct Radix2Record {
+  double tau, s1;
+  long long rot;
+  double pad[13];
 };
 
 // the twiddles w[r], 0 < r < R, of one butterfly from its R-entry slot p
@@ -434,6 +454,54 @@ __device__ __forceinline__ void radix8_scaled(cpx<double>* v, const Radix8Record
   v[7] = {fma(-ha, p3, e3.re), fma(-hb, r3, e3.im)};
 }
 
+template <int DIR>
+__device__ __forceinline__ void radix4_scaled(cpx<double>* v, const Radix4Record* __restrict__ rec) {
+  const double2* q = reinterpret_cast<const double2*>(rec);
+  const double2 a0 = __ldg(q), a1 = __ldg(q + 1), a2 = __ldg(q + 2);
+  const long long rbits = __ldg(&rec->rot);
+  const double tau[3] = {a0.x, a0.y, a1.x};
+  const double s2 = a1.y, q31 = a2.x, s1 = a2.y;
+  cpx<double> h[4];
+  h[0] = v[0];
+#pragma unroll
+  for (int r = 1; r < 4; ++r) h[r] = scaled_input<DIR>(v[r], tau[r - 1], (rbits >> (r - 1)) & 1);
+  const cpx<double> s0 = {fma(s2, h[2].re, h[0].re), fma(s2, h[2].im, h[0].im)};
+  const cpx<double> d0 = {fma(-s2, h[2].re, h[0].re), fma(-s2, h[2].im, h[0].im)};
+  const cpx<double> u = {fma(q31, h[3].re, h[1].re), fma(q31, h[3].im, h[1].im)};
+  const cpx<double> w = rot<DIR>(cpx<double>{fma(-q31, h[3].re, h[1].re), fma(-q31, h[3].im, h[1].im)});
+  v[0] = {fma(s1, u.re, s0.re), fma(s1, u.im, s0.im)};
+  v[2] = {fma(-s1, u.re, s0.re), fma(-s1, u.im, s0.im)};
+  v[1] = {fma(s1, w.re, d0.re), fma(s1, w.im, d0.im)};
+  v[3] = {fma(-s1, w.re, d0.re), fma(-s1, w.im, d0.im)};
+}
+
+template <int DIR>
+__device__ __forceinline__ void radix3_scaled(cpx<double>* v, const Radix3Record* __restrict__ rec) {
+  const double2* q = reinterpret_cast<const double2*>(rec);
+  const double2 a0 = __ldg(q), a1 = __ldg(q + 1), a2 = __ldg(q + 2);
+  const long long rbits = __ldg(&rec->rot);
+  const double q21 = a1.x, s1 = a1.y, s1half = a2.x, ss1 = a2.y;
+  const cpx<double> h1 = scaled_input<DIR>(v[1], a0.x, rbits & 1);
+  const cpx<double> h2 = scaled_input<DIR>(v[2], a0.y, (rbits >> 1) & 1);
+  const cpx<double> a = {fma(q21, h2.re, h1.re), fma(q21, h2.im, h1.im)};
+  const cpx<double> b = {fma(-q21, h2.re, h1.re), fma(-q21, h2.im, h1.im)};
+  const cpx<double> x0 = v[0];
+  const cpx<double> t = {fma(-s1half, a.re, x0.re), fma(-s1half, a.im, x0.im)};
+  v[0] = {fma(s1, a.re, x0.re), fma(s1, a.im, x0.im)};
+  plus_minus_i<DIR>(t, ss1, b, v[1], v[2]);
+}
+
+template <int DIR>
+__device__ __forceinline__ void radix2_scaled(cpx<double>* v, const Radix2Record* __restrict__ rec) {
+  const double2 a0 = __ldg(reinterpret_cast<const double2*>(rec));
+  const long long rbits = __ldg(&rec->rot);
+  const cpx<double> h1 = scaled_input<DIR>(v[1], a0.x, rbits & 1);
+  const double s1 = a0.y;
+  const cpx<double> x0 = v[0];
+  v[0] = {fma(s1, h1.re, x0.re), fma(s1, h1.im, x0.im)};
+  v[1] = {fma(-s1, h1.re, x0.re), fma(-s1, h1.im, x0.im)};
+}
+
 template <int R, int DIR, typename T>
 __device__ __forceinline__ void fft_pass(cpx<T>* buf, int L, int nbatch, int Ns,
                                          const cpx<T>* __restrict__ stw, const cpx<T>* __restrict__ dtw,
@@ -451,10 +519,13 @@ __device__ __forceinline__ void fft_pass(cpx<T>* buf, int L, int nbatch, int Ns,
     cpx<T> v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = base[r * Ns];
-    if constexpr ((R == 5 || R == 8) && std::is_same<T, double>::value) {
+    if constexpr (R <= 8 && R != 7 && std::is_same<T, double>::value) {
       if (gtw) {
         if constexpr (R == 5) radix5_scaled<DIR>(v, reinterpret_cast<const Radix5Record*>(gtw) + k);
-        else radix8_scaled<DIR>(v, reinterpret_cast<const Radix8Record*>(gtw) + k);
+        else if constexpr (R == 8) radix8_scaled<DIR>(v, reinterpret_cast<const Radix8Record*>(gtw) + k);
+        else if constexpr (R == 4) radix4_scaled<DIR>(v, reinterpret_cast<const Radix4Record*>(gtw) + k);
+        else if constexpr (R == 3) radix3_scaled<DIR>(v, reinterpret_cast<const Radix3Record*>(gtw) + k);
+        else radix2_scaled<DIR>(v, reinterpret_cast<const Radix2Record*>(gtw) + k);
 #pragma unroll
         for (int r = 0; r < R; ++r) base[r * Ns] = v[r];
         continue;
@@ -534,9 +605,9 @@ __device__ __forceinline__ void fft_run(cpx<T>* buf, int nbatch, const FftDesc& 
     // the scaled radix-5 records serve the FP64 kernels only
     const cpx<T>* gtw = (std::is_same<T, double>::value && d.g_off[s] >= 0) ? tw + d.g_off[s] : nullptr;
     switch (R) {
-      case 2: fft_pass<2, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
-      case 3: fft_pass<3, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
-      case 4: fft_pass<4, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 2: fft_pass<2, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s], gtw); break;
+      case 3: fft_pass<3, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s], gtw); break;
+      case 4: fft_pass<4, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s], gtw); break;
       case 5: fft_pass<5, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s], gtw); break;
       case 7: fft_pass<7, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
       case 8: fft_pass<8, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s], gtw); break;

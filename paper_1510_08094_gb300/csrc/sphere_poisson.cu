@@ -90,8 +90,12 @@ bool make_fft_desc(int L, FftDesc* d) {
   ns = 1;
   for (int t = 0; t < s; ++t) {
     d->g_off[t] = -1;
-    if ((d->radix[t] == 5 || d->radix[t] == 8) && ns > 1) {
-      static_assert(sizeof(sp::Radix5Record) == sizeof(sp::Radix8Record), "one record size");
+    const int rt = d->radix[t];
+    if ((rt == 2 || rt == 3 || rt == 4 || rt == 5 || rt == 8) && ns > 1) {
+      static_assert(sizeof(sp::Radix5Record) == sizeof(sp::Radix8Record) &&
+                    sizeof(sp::Radix5Record) == sizeof(sp::Radix4Record) &&
+                    sizeof(sp::Radix5Record) == sizeof(sp::Radix3Record) &&
+                    sizeof(sp::Radix5Record) == sizeof(sp::Radix2Record), "one record size");
       d->g_off[t] = off;
       off += ns * (int)(sizeof(sp::Radix5Record) / sizeof(cpx<double>));
     }
@@ -195,6 +199,38 @@ std::vector<cpx<double>> stage_twiddles(const FftDesc& d) {
         rec.s1 = sg[1];
         rec.s1h = 0.70710678118654752440084436210484903928 * sg[1];
         std::memcpy(&tab[d.g_off[s] + k * per], &rec, sizeof rec);
+      }
+    }
+    if (d.g_off[s] >= 0 && R == 4) {
+      for (int k = 0; k < ns; ++k) {
+        sp::Radix4Record rec = {};
+        double sg[4] = {1.0};
+        for (int r = 1; r < 4; ++r) scaled_root(r, k, &sg[r], &rec.tau[r - 1], &rec.rot);
+        rec.s2 = sg[2];
+        rec.q31 = sg[3] / sg[1];
+        rec.s1 = sg[1];
+        std::memcpy(&tab[d.g_off[s] + k * (sizeof(rec) / sizeof(cpx<double>))], &rec, sizeof rec);
+      }
+    }
+    if (d.g_off[s] >= 0 && R == 3) {
+      for (int k = 0; k < ns; ++k) {
+        sp::Radix3Record rec = {};
+        double sg[3] = {1.0};
+        for (int r = 1; r < 3; ++r) scaled_root(r, k, &sg[r], &rec.tau[r - 1], &rec.rot);
+        rec.q21 = sg[2] / sg[1];
+        rec.s1 = sg[1];
+        rec.s1half = 0.5 * sg[1];
+        rec.ss1 = 0.86602540378443864676372317075293618347 * sg[1];   // sin(2 pi/3)
+        std::memcpy(&tab[d.g_off[s] + k * (sizeof(rec) / sizeof(cpx<double>))], &rec, sizeof rec);
+      }
+    }
+    if (d.g_off[s] >= 0 && R == 2) {
+      for (int k = 0; k < ns; ++k) {
+        sp::Radix2Record rec = {};
+        double sg1 = 1.0;
+        scaled_root(1, k, &sg1, &rec.tau, &rec.rot);
+        rec.s1 = sg1;
+        std::memcpy(&tab[d.g_off[s] + k * (sizeof(rec) / sizeof(cpx<double>))], &rec, sizeof rec);
       }
     }
     if (d.g_off[s] >= 0 && R == 5) {
