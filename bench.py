@@ -368,8 +368,8 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
 
 
-FORM_GROUPS = ("precision", "adjoint", "transforms", "tangential_gradient", "vector_calculus", "lowrank",
-               "paper_scale")
+FORM_GROUPS = ("precision", "adjoint", "inverse_fit", "transforms", "tangential_gradient", "vector_calculus",
+               "lowrank", "paper_scale")
 
 
 def measure_forms(sp, f, u_exact, u64, N, n, dev, ms_fp64, args):
@@ -435,6 +435,8 @@ def measure_forms(sp, f, u_exact, u64, N, n, dev, ms_fp64, args):
             entry["max_rel_err_vs_fp64_adjoint"] = float((out - sg64).abs().max() / sg64.abs().max())
         res[f"adjoint_{prec}"] = entry
         del plan, ws, out, sf
+    if "inverse_fit" in want:
+        res["inverse_fit"] = measure_inverse_fit(sp, dev, steps, args)
     if "transforms" in want:
         res["transforms"] = measure_transforms(sp, f, N, n, dev, steps, args)
     if "tangential_gradient" in want:
@@ -562,6 +564,51 @@ def measure_transforms(sp, f, N, n, dev, steps, args):
     return {"unit": "DOF/s", "calls": out, "max_rel_err_sample_coeffs2_roundtrip": rt,
             "sum2_worked_example_abs_err": abs(plan.sum2(p) - exact),
             "gpu_launches_per_call": {"coeffs2": 2, "sample": 2, "sum2": 3}}
+
+
+def measure_inverse_fit(sp, dev, steps, args):
+    """The differentiation form on its workload (512 x 1024, u_obs a seeded l <= 200
+    series plus N(0, 1e-3) noise): one gradient of ||u(f) - u_obs||^2 through the
+    autograd function (forward solve, loss, adjoint solve), timed in FP64 and FP32;
+    the FP64 gradient checked against a central difference (h = 1e-6) along a
+    random direction and the FP32 one against it."""
+    import numpy as np
+    import torch
+    from synth import sh
+
+    w = sh.workload("sh200_512x1024_noisy")
+    u_obs = w.observation(device=dev)
+    f0 = torch.tensor(np.random.default_rng(55).standard_normal((w.n_theta, w.n_lambda)) * 0.1, device=dev)
+    reps = max(5, min(steps, 50))
+    res = {"workload": w.name, "unit": "DOF/s"}
+    grads = {}
+    for prec in ("fp64", "fp32"):
+        def gradient():
+            f = f0.clone().requires_grad_(True)
+            loss = ((sp.poisson(f, prec) - u_obs) ** 2).sum()
+            loss.backward()
+            return f.grad
+        for _ in range(3):
+            gradient()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            gradient()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        grads[prec] = gradient()
+        res[prec] = {"ms_per_gradient": ms, "value": w.n_theta * w.n_lambda / (ms * 1e-3)}
+    plan = sp.get_plan(w.n_theta, w.n_lambda, device=dev)
+    d = torch.tensor(np.random.default_rng(7).standard_normal(tuple(f0.shape)), device=dev)
+    loss = lambda x: float(((plan.solve(x) - u_obs) ** 2).sum())
+    h = 1e-6
+    fd = (loss(f0 + h * d) - loss(f0 - h * d)) / (2 * h)
+    res["fp64"]["central_difference_rel_err"] = abs(fd - float((grads["fp64"] * d).sum())) / max(1.0, abs(fd))
+    res["fp32"]["max_rel_err_vs_fp64_gradient"] = float((grads["fp32"] - grads["fp64"]).abs().max()
+                                                        / grads["fp64"].abs().max())
+    return res
 
 
 def measure_vector_calculus(sp, N, n, dev, steps, args):
