@@ -369,7 +369,7 @@ def run_ours(args):
 
 
 FORM_GROUPS = ("precision", "adjoint", "inverse_fit", "transforms", "tangential_gradient", "vector_calculus",
-               "lowrank", "paper_scale")
+               "lowrank", "mixed_sizes", "paper_scale")
 
 
 def measure_forms(sp, f, u_exact, u64, N, n, dev, ms_fp64, args):
@@ -445,6 +445,8 @@ def measure_forms(sp, f, u_exact, u64, N, n, dev, ms_fp64, args):
         res["vector_calculus"] = measure_vector_calculus(sp, N, n, dev, steps, args)
     if "lowrank" in want:
         res["lowrank"] = measure_lowrank(sp, N, n, dev, steps, ms_fp64, args)
+    if "mixed_sizes" in want:
+        res["mixed_sizes"] = measure_mixed_sizes(sp, dev, args)
     if "paper_scale" in want and not args.no_paper_scale:
         res["paper_scale"] = measure_paper_scale(sp, dev, args)
     return res
@@ -705,6 +707,49 @@ def measure_paper_scale(sp, dev, args):
         out[prec] = {"ms_per_solve": ms, "value": w.n_theta * w.n_lambda / (ms * 1e-3), "unit": "DOF/s",
                      "max_rel_err_vs_closed_form": float((u - ue).abs().max()) / ex}
         del plan, ws, u
+    return out
+
+
+def measure_mixed_sizes(sp, dev, args):
+    """The mixed-precision workloads at 2048 x 4096 and 4096 x 8192: FP64, FP32 and
+    FP32 + refinement with 1, 2 and 3 sweeps, each timed, with the error of each
+    against the FP64 solution (itself within 1e-12 of the oracle) and against
+    the closed form of the series, per sweep."""
+    import torch
+    from synth import sh
+
+    out = {}
+    for name in ("sh1024_2048x4096", "sh2048_4096x8192"):
+        w = sh.workload(name)
+        f, ue = w.make(device=dev)
+        ex = float(ue.abs().max())
+        entry = {"n_theta": w.n_theta, "n_lambda": w.n_lambda, "unit": "DOF/s"}
+        u64 = None
+        for prec, sweeps in [("fp64", 0), ("fp32", 0), ("fp32_refine", 1), ("fp32_refine", 2), ("fp32_refine", 3)]:
+            plan = sp.Plan(w.n_theta, w.n_lambda, prec, sweeps, device=dev, autotune=not args.no_autotune)
+            ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=dev)
+            u = torch.empty_like(f)
+            for _ in range(3):
+                plan.solve(f, u, ws)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(10):
+                plan.solve(f, u, ws)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 10
+            key = prec if prec != "fp32_refine" else f"fp32_refine_sweeps{sweeps}"
+            r = {"ms_per_solve": ms, "value": w.n_theta * w.n_lambda / (ms * 1e-3),
+                 "max_rel_err_vs_closed_form": float((u - ue).abs().max()) / ex}
+            if u64 is None:
+                u64 = u.clone()
+            else:
+                r["max_rel_err_vs_fp64"] = float((u - u64).abs().max()) / ex
+            entry[key] = r
+            del plan, ws, u
+        out[name] = entry
+        del f, ue, u64
     return out
 
 
