@@ -5,8 +5,12 @@ the target sets for this solver.  Sizes span several transform tiles, ragged
 tails (odd lengths, large prime factors, the smallest legal grids) and the
 full-size workload (5000 x 10000), where the oracle is evaluated on sampled
 longitudinal wavenumbers and the whole field is checked against the closed
-form of spherical-harmonic inputs.
+form of spherical-harmonic inputs, and the largest legal grid (12288 x 24576,
+both transforms at their longest length), checked against closed forms and
+the adjoint identity.
 """
+
+import math
 
 import numpy as np
 import pytest
@@ -228,3 +232,84 @@ def test_full_size_single_harmonics(sp, big_case, l, m):
     e_oracle = float(np.abs(U_ref - U_ex).max()) / scale
     assert e_oracle < 3e-10 and e_gpu < 3.0 * e_oracle + 1e-12, (e_gpu, e_oracle)
     assert float(np.abs(U - U_ref).max()) / scale < 3e-10
+
+
+# --------------------------------------------------------------------------
+# Largest legal grid: 12288 colatitudes x 24576 longitudes, both transforms at
+# their longest length (12288 = 2^12 * 3); 2.4 GB per field
+# --------------------------------------------------------------------------
+
+MAX_NT, MAX_NL = 12288, 24576
+
+
+def _sectoral(m, nt, nl):
+    """Re (x + iy)^m = sin^m(theta) cos(m lambda) on the grid.  (x + iy)^m is a
+    homogeneous harmonic polynomial of degree m, so on the sphere it is a
+    spherical harmonic of degree m (Delta = -m(m+1)); it reaches the high
+    wavenumbers the recurrence of the synthesiser would take long to."""
+    th = torch.tensor(sh.colatitudes(nt), dtype=torch.float64, device="cuda")
+    q = torch.arange(nl, dtype=torch.int64, device="cuda")
+    r = torch.remainder(m * (2 * q - nl), 2 * nl).to(torch.float64)
+    return torch.exp(m * torch.log(torch.sin(th)))[:, None] * torch.cos(r * (math.pi / nl))[None, :]
+
+
+@pytest.fixture(scope="module")
+def largest_grid_inputs(sp):
+    # (name, degree l, samples Y): the solution of Delta u = Y is -Y / (l(l+1))
+    return [("sectoral 12000", 12000, _sectoral(12000, MAX_NT, MAX_NL)),
+            ("x", 1, _sectoral(1, MAX_NT, MAX_NL)),
+            ("Y_700^-333", 700, sh.synthesize(sh.single_sh_coeffs(700, -333), MAX_NT, MAX_NL, device="cuda")),
+            ("Y_12^5", 12, sh.synthesize(sh.single_sh_coeffs(12, 5), MAX_NT, MAX_NL, device="cuda"))]
+
+
+def _column(v, k):
+    """(1/n) sum_q v[:, q] exp(-i k lambda_q): the longitudinal wavenumber-k
+    column of the samples v, as (real, imaginary) parts."""
+    nl = v.shape[1]
+    q = torch.arange(nl, dtype=torch.int64, device=v.device)
+    ang = torch.remainder(k * (2 * q - nl), 2 * nl).to(torch.float64) * (math.pi / nl)
+    return v @ torch.cos(ang) / nl, -(v @ torch.sin(ang)) / nl
+
+
+@pytest.mark.parametrize("precision,sweeps,tol", [("fp64", 0, 1e-12), ("fp32_refine", 2, 1e-12),
+                                                  ("fp32", 0, 1e-5)])
+def test_largest_grid_closed_forms(sp, largest_grid_inputs, precision, sweeps, tol):
+    # For Y of degree l the solution -Y/(l(l+1)) is l(l+1)/2 times smaller than
+    # the largest one a unit input can have (the l = 1 gain 1/2), and rounding
+    # noise that lands in low-degree modes is amplified by up to that factor
+    # relative to it.  So the error is measured against max|u| for the low and
+    # moderate degrees, and for the degree-12000 harmonic against max|Y|/2 over
+    # the whole field and against max|u| on its own wavenumber column.
+    plan = sp.Plan(MAX_NT, MAX_NL, precision, sweeps)
+    errs = {}
+    for name, l, y in largest_grid_inputs:
+        u = plan.solve(y)
+        ref = y / -(l * (l + 1.0))
+        d = (u - ref).abs().max()
+        if l < 1000:
+            errs[name] = float(d / ref.abs().max())
+        else:
+            errs[name + " field / (max|Y|/2)"] = float(d / (0.5 * y.abs().max()))
+            (ur, ui), (rr, ri) = _column(u, l), _column(ref, l)
+            den = float(torch.sqrt(rr * rr + ri * ri).max())
+            errs[name + " column"] = float(torch.sqrt((ur - rr) ** 2 + (ui - ri) ** 2).max()) / den
+            errs[name + " field (rel, not asserted)"] = float(d / ref.abs().max())
+        del u, ref
+    del plan
+    torch.cuda.empty_cache()
+    print(precision, errs)
+    asserted = {k: v for k, v in errs.items() if "not asserted" not in k}
+    assert max(asserted.values()) < tol, errs
+
+
+def test_largest_grid_adjoint_dot_product(sp):
+    plan = sp.Plan(MAX_NT, MAX_NL)
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    f = torch.randn(MAX_NT, MAX_NL, device="cuda", dtype=torch.float64, generator=gen)
+    g = torch.randn(MAX_NT, MAX_NL, device="cuda", dtype=torch.float64, generator=gen)
+    a = float((plan.solve(f) * g).sum())
+    b = float((f * plan.solve_adjoint(g)).sum())
+    del f, g, plan
+    torch.cuda.empty_cache()
+    print("dot product", a, b, abs(a - b) / abs(a))
+    assert abs(a - b) < 1e-11 * abs(a)

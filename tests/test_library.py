@@ -49,8 +49,11 @@ def test_status_strings(lib):
     assert "unknown" in _lib.status_string(-999)
 
 
+# the last four: just past the longest transform (12288 = 2^12 * 3 is the last
+# legal length; 12800 = 2^9 * 5^2 factors but is too long; 12289 is prime)
 @pytest.mark.parametrize("nt,nl", [(0, 8), (8, 0), (8, 7), (8, 1), (-1, 8), (37, 64), (8, 74),
-                                   (20000, 64), (64, 40000)])
+                                   (20000, 64), (64, 40000), (12800, 64), (12289, 8), (8, 25600),
+                                   (8, 24578)])
 def test_plan_rejects_bad_sizes(lib, nt, nl):
     from paper_1510_08094_gb300 import _lib
 
