@@ -6,12 +6,14 @@ a transposed operand, a wrong index or normalisation, in the DFS doubling
 (eq. BMCsphere), the 2D Fourier coefficients (eq. 2DFourierExpansion), the
 banded operator (eq. SylvesterSphericalPoisson, eq. linearSystems), the
 zero-mean row (eq. integrationCoeffs, eq. pentdiagonalPlusRankOne), the
-transposed map and the vector calculus (Section 4).  It then re-runs a compact
-copy of the pins (closed forms, the printed 216 pi / 35, a trigonometric
-polynomial's coefficients, the zero mean, the dense transpose, div grad =
-Delta, the gradient of x, solid rotation) at their own tolerances, and asserts
-that the named pins fail.  The unmodified oracle passes every pin (the control
-case)."""
+transposed map, the vector calculus (Section 4), the pivot pseudoinverse and
+the structure-preserving GE (Section 3) and the low-rank coefficients.  It
+then re-runs a compact copy of the pins (closed forms, the printed 216 pi / 35,
+a trigonometric polynomial's coefficients, the zero mean, the dense transpose,
+div grad = Delta, the gradient of x, solid rotation, the SVD pseudoinverse,
+exact recovery at the SVD rank, the dense F of the approximant) at their own
+tolerances, and asserts that the named pins fail.  The unmodified oracle
+passes every pin (the control case)."""
 
 import math
 
@@ -112,6 +114,37 @@ def pin_solid_rotation():
     return ok and np.abs(O.vorticity(-y, x, 0 * z) - 2 * z).max() < 1e-12
 
 
+def pin_pivot_pseudoinverse():
+    # the epsilon-pseudoinverse of [[a, b], [b, a]] against numpy's SVD cut
+    for a, b in [(1.0, 0.3), (2.0, -1.99), (-0.5, 0.5000001), (0.7, -0.7)]:
+        P = O.pivot_pinv(a, b, 0.01)
+        R = np.linalg.pinv(np.array([[a, b], [b, a]]), rcond=0.01)
+        if not np.all(np.isfinite(P)) or np.abs(P - R).max() > 1e-12 * max(1.0, np.abs(R).max()):
+            return False
+    return True
+
+
+def pin_ge_recovery():
+    # a band-limited series is recovered after as many terms as its SVD rank
+    ft = O.dfs_double(sh.synthesize(sh.random_sh_coeffs(6, 5), 24, 48).numpy())
+    terms, e = O.bmc_ge(ft, max_terms=64)
+    sv = np.linalg.svd(ft, compute_uv=False)
+    rank = sum(int(np.linalg.matrix_rank(P)) for _, P, _, _ in terms)
+    return rank == int((sv > 1e-11 * sv[0]).sum()) and float(np.abs(e).max()) < 1e-12 * float(np.abs(ft).max())
+
+
+def pin_lowrank_coefficients():
+    # F from the low-rank factors equals the dense F of the approximant
+    nt, nl = 24, 50
+    th = sh.colatitudes(nt)[:, None]
+    la = sh.longitudes(nl)[None, :]
+    x, y, z = np.cos(la) * np.sin(th), np.sin(la) * np.sin(th), np.cos(th) + 0 * la
+    ft = O.dfs_double(np.cos(1 + 2 * x + np.sin(2 * z)) * (1 + 0.5 * y))
+    terms, _ = O.bmc_ge(ft)
+    F_dense = O.rhs_coefficients(O.lowrank_values(terms)[nt:])
+    return np.abs(O.lowrank_rhs_coefficients(terms, *ft.shape) - F_dense).max() < 1e-13 * np.abs(F_dense).max()
+
+
 PINS = {
     "closed forms (dense)": lambda: pin_closed_forms("dense"),
     "closed forms (banded)": lambda: pin_closed_forms("banded"),
@@ -123,6 +156,9 @@ PINS = {
     "div grad": pin_div_grad,
     "gradient of x": pin_gradient_of_x,
     "solid rotation": pin_solid_rotation,
+    "pivot pseudoinverse": pin_pivot_pseudoinverse,
+    "GE recovery": pin_ge_recovery,
+    "low-rank coefficients": pin_lowrank_coefficients,
 }
 
 
@@ -146,7 +182,7 @@ def _failing_pins():
 _orig = {name: getattr(O, name) for name in
          ("theta_bands_B", "system_matrix", "_bands_of", "integration_weights", "dfs_double",
           "_phase_theta", "coeffs2", "rhs_coefficients", "poisson_adjoint", "tangential_gradient",
-          "curl")}
+          "curl", "pivot_pinv", "bmc_ge", "lowrank_rhs_coefficients")}
 
 
 def _bands_swapped(m):
@@ -227,6 +263,40 @@ def _curl_sign_flipped(f1, f2, f3, chop=0.0):
     return c1, c2, -c3
 
 
+def _pinv_without_cut(a, b, alpha=0.01):
+    return np.linalg.inv(np.array([[a, b], [b, a]]))  # the epsilon cut of the pseudoinverse dropped
+
+
+def _ge_with_unreflected_row(ft, alpha=0.01, rtol=1e-13, max_terms=512):
+    # the pivot's second row taken at theta* again instead of at -theta*
+    ft = np.asarray(ft, dtype=np.float64)
+    m, n = ft.shape
+    N, H = m // 2, n // 2
+    e = ft.copy()
+    terms = []
+    for _ in range(max_terms):
+        if float(np.abs(e).max()) <= rtol * float(np.abs(ft).max()):
+            break
+        a = np.roll(e, H, axis=1)
+        s1 = np.maximum(np.abs(a + e), np.abs(a - e))[N:, H:]
+        i, j = np.unravel_index(int(np.argmax(s1)), s1.shape)
+        p, q = N + int(i), H + int(j)
+        P = O.pivot_pinv(float(e[p, q - H]), float(e[p, q]), alpha)
+        cols = e[:, [q - H, q]].copy()
+        rows = e[[p, p], :].copy()
+        e = e - cols @ P @ rows
+        terms.append((cols, P, rows, (p, q)))
+    return terms, e
+
+
+def _lowrank_without_weight(terms, m, n):
+    Et, El = O._phase_theta(m), O._phase_lambda(n)
+    F = np.zeros((m, n), dtype=complex)
+    for c, P, r, _ in terms:
+        F += ((Et @ c) / m) @ P @ ((El @ r.T) / n).T   # sin^2(theta) factor dropped
+    return F
+
+
 MISTAKES = [
     ("theta_bands_B", _bands_swapped, {"closed forms (dense)", "closed forms (banded)"}),
     ("theta_bands_B", _bands_without_first_order, {"closed forms (dense)", "closed forms (banded)"}),
@@ -243,6 +313,9 @@ MISTAKES = [
     # x and the rotation are not
     ("tangential_gradient", _gradient_xy_swapped, {"gradient of x", "solid rotation"}),
     ("curl", _curl_sign_flipped, {"solid rotation"}),
+    ("pivot_pinv", _pinv_without_cut, {"pivot pseudoinverse"}),
+    ("bmc_ge", _ge_with_unreflected_row, {"GE recovery"}),
+    ("lowrank_rhs_coefficients", _lowrank_without_weight, {"low-rank coefficients"}),
 ]
 
 
