@@ -850,6 +850,23 @@ def measure_batched(sp, dev, args):
     return out
 
 
+def _host_threads() -> int:
+    """Threads the oracle's numpy / LAPACK calls run on: the BLAS pool's size
+    where threadpoolctl can read it, else the CPUs this process may run on."""
+    try:
+        from threadpoolctl import threadpool_info
+
+        n = [i["num_threads"] for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def _oracle_sample(f_np, ks):
     """Time the oracle's sampled-column solve on wavenumbers ks of the full input."""
     from oracle import sphere_oracle as O
@@ -878,7 +895,7 @@ def cpu_baseline(f_np, budget_s: float = 20.0, ks=None) -> dict:
             break
     per_k = t / len(used)
     full = per_k * nl
-    return {"value": nt * nl / full, "unit": "DOF/s", "cores": os.cpu_count(), "kind": "oracle",
+    return {"value": nt * nl / full, "unit": "DOF/s", "cores": _host_threads(), "kind": "oracle",
             "sample": f"oracle.sampled_columns on {len(used)} of the {nl} wavenumbers of the "
                       f"{nt}x{nl} input, one call each ({t:.1f} s; a first call building the cached "
                       f"colatitude phase matrix took {t_warm:.1f} s and is not counted), "
@@ -921,7 +938,7 @@ def run_reference(args):
         "data": "synthetic: seeded spherical-harmonic series (no dataset)",
         "config": {"workload": f"{w.name}: CPU FP64 oracle on the same input",
                    "dof_per_solve": w.n_theta * w.n_lambda},
-        "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": os.cpu_count(), "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": _host_threads(), "kind": "oracle",
                          "sample": f"each step: oracle.sampled_columns on 1 of the {w.n_lambda} "
                                    f"wavenumbers, scaled by {w.n_lambda}"},
         "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
