@@ -225,7 +225,9 @@ int sphere_poisson_sum2(sp_plan_t plan, const double* f, double* result, void* w
  * theta of eq. sphericalCoordinates (the paper prints +sin theta d/dtheta).
  * The theta- and lambda-Nyquist modes are dropped from f and from the results.
  * Exact (to rounding) for f band-limited within the grid's window; for other f
- * the results carry truncation terms of the window.
+ * the results carry truncation terms of the window, and the recurrence's are not
+ * those of the dense inverse of the truncated M_sin (the window's boundary rows
+ * differ; on the degenerate grids 1 x n, 2 x 4 and n x 2 the two agree).
  *   f, gx, gy, gz  device, [n_theta][n_lambda] doubles, 16-byte aligned.
  *   workspace      device, >= sphere_poisson_gradient_workspace_size bytes
  *                  (five half spectra of n_theta Kp 16 bytes, Kp = n_lambda/2 + 1
