@@ -182,7 +182,7 @@ def _failing_pins():
 _orig = {name: getattr(O, name) for name in
          ("theta_bands_B", "system_matrix", "_bands_of", "integration_weights", "dfs_double",
           "_phase_theta", "coeffs2", "rhs_coefficients", "poisson_adjoint", "tangential_gradient",
-          "curl", "pivot_pinv", "bmc_ge", "lowrank_rhs_coefficients")}
+          "curl", "pivot_pinv", "bmc_ge", "lowrank_rhs_coefficients", "_solve_columns_T")}
 
 
 def _bands_swapped(m):
@@ -253,6 +253,15 @@ def _adjoint_is_forward(g, reading="B"):
     return O.poisson(g, reading)                    # the map taken as its own transpose
 
 
+def _adjoint_solves_untransposed(B, reading="B"):
+    m, n = B.shape
+    Y = np.zeros_like(B, dtype=np.complex128)
+    for kk in range(n):
+        # M_k instead of M_k^T in the transposed solves
+        Y[:, kk] = np.linalg.solve(O.system_matrix(m, kk - n // 2, reading), B[:, kk])
+    return Y
+
+
 def _gradient_xy_swapped(f, chop=0.0):
     gx, gy, gz = _orig["tangential_gradient"](f, chop)
     return gy, gx, gz
@@ -309,6 +318,7 @@ MISTAKES = [
     ("coeffs2", _coeffs2_half_normalised, {"coeffs2/sample round trip"}),
     ("rhs_coefficients", _rhs_without_weight, {"closed forms (dense)"}),
     ("poisson_adjoint", _adjoint_is_forward, {"dense transpose"}),
+    ("_solve_columns_T", _adjoint_solves_untransposed, {"dense transpose"}),
     # div grad is blind to a consistent relabelling of x and y; the gradient of
     # x and the rotation are not
     ("tangential_gradient", _gradient_xy_swapped, {"gradient of x", "solid rotation"}),
