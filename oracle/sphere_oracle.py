@@ -43,9 +43,10 @@ the coefficients F, the surface integral sum2 (Section 4, Integration, eq.
 integrationCoeffs), the tangential derivatives of Section 4 (Differentiation,
 eqs. diff_x..diff_z with the division by sin theta through M_sin^{-1}) and the
 vector-calculus operators built from them (divergence, curl, the curl of a
-scalar function of eq. CurlScalarF, vorticity), and the
+scalar function of eq. CurlScalarF, vorticity), the
 transpose (adjoint) of the whole linear map f -> u, both matrix-free and as a
-dense matrix for tiny grids.
+dense matrix for tiny grids, and the single-precision per-k solves refined by
+FP64 residuals (refine_reference).
 """
 
 from __future__ import annotations
@@ -583,6 +584,80 @@ def poisson_adjoint(g: np.ndarray, reading: str = "B") -> np.ndarray:
     out = vbar[nt:].copy()
     back = vbar[:nt][::-1]                         # row n_theta-1-p -> f row i
     out += np.roll(back, n // 2, axis=1)           # undo the q + n/2 shift
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Residual refinement of the per-k solves (the single-precision form)
+# ----------------------------------------------------------------------------
+
+def _solve_one_fp32(Fk: np.ndarray, m: int, k: int, reading: str = "B") -> np.ndarray:
+    """X_k of one column system with k != 0 (eq. linearSystems) by LU in IEEE
+    single precision: the bands and the right-hand side rounded to float32 /
+    complex64, LAPACK's single-precision banded solve, the result widened."""
+    rhs = Fk.astype(np.complex128).copy()
+    if reading == "B":
+        rhs[0] = 0.0
+    sub, d, sup = _bands_of(m, k, reading)
+    ab = np.zeros((5, m), dtype=np.float32)
+    ab[0, 2:] = sup[:-2]
+    ab[2, :] = d
+    ab[4, :-2] = sub[2:]
+    return _sla.solve_banded((2, 2), ab, rhs.astype(np.complex64)).astype(np.complex128)
+
+
+def _replaced_system_apply(X: np.ndarray, reading: str = "B") -> np.ndarray:
+    """M_k X_k for every k, M_k the system actually solved: the bands of
+    eq. linearSystems with the Nyquist row j = -m/2 the identity (reading B) and,
+    for k = 0, row j = 0 replaced by w^T (eq. pentdiagonalPlusRankOne)."""
+    m, n = X.shape
+    out = np.zeros_like(X, dtype=np.complex128)
+    for kk in range(n):
+        k = kk - n // 2
+        sub, d, sup = _bands_of(m, k, reading)
+        x = X[:, kk]
+        y = d * x
+        y[2:] += sub[2:] * x[:-2]
+        y[:-2] += sup[:-2] * x[2:]
+        if k == 0:
+            w = integration_weights(m)
+            if reading == "B":
+                w[0] = 0.0
+            y[m // 2] = w @ x
+        out[:, kk] = y
+    return out
+
+
+def refine_reference(f: np.ndarray, sweeps: int, reading: str = "B"):
+    """The single-precision form with residual refinement, in coefficient space:
+    X_0 = S32 F and X_{s+1} = X_s + S32 (F~ - M X_s), where F~ is F of
+    eq. SylvesterSphericalPoisson with the replaced rows zeroed, M the systems
+    actually solved (see _replaced_system_apply), the residual formed in FP64,
+    and S32 solves every k != 0 column in single precision and the
+    ill-conditioned k = 0 column (eq. pentdiagonalPlusRankOne) in FP64.  F and
+    the final synthesis are FP64.  Returns [u_0, u_1, ..., u_sweeps], the grid
+    values after each number of sweeps."""
+    f = np.asarray(f, dtype=np.float64)
+    nt, n = f.shape
+    m = 2 * nt
+    F = rhs_coefficients(f)
+    Ft = F.copy()
+    Ft[m // 2, n // 2] = 0.0
+    if reading == "B":
+        Ft[0, :] = 0.0
+
+    def s32(R):
+        X = np.zeros_like(R, dtype=np.complex128)
+        for kk in range(n):
+            k = kk - n // 2
+            X[:, kk] = _solve_one(R[:, kk], m, 0, reading) if k == 0 else _solve_one_fp32(R[:, kk], m, k, reading)
+        return X
+
+    X = s32(F)
+    out = [sample(X)[nt:].real.copy()]
+    for _ in range(sweeps):
+        X = X + s32(Ft - _replaced_system_apply(X, reading))
+        out.append(sample(X)[nt:].real.copy())
     return out
 
 

@@ -7,13 +7,14 @@ a transposed operand, a wrong index or normalisation, in the DFS doubling
 banded operator (eq. SylvesterSphericalPoisson, eq. linearSystems), the
 zero-mean row (eq. integrationCoeffs, eq. pentdiagonalPlusRankOne), the
 transposed map, the vector calculus (Section 4), the pivot pseudoinverse and
-the structure-preserving GE (Section 3) and the low-rank coefficients.  It
-then re-runs a compact copy of the pins (closed forms, the printed 216 pi / 35,
-a trigonometric polynomial's coefficients, the zero mean, the dense transpose,
-div grad = Delta, the gradient of x, solid rotation, the SVD pseudoinverse,
-exact recovery at the SVD rank, the dense F of the approximant) at their own
-tolerances, and asserts that the named pins fail.  The unmodified oracle
-passes every pin (the control case)."""
+the structure-preserving GE (Section 3), the low-rank coefficients and the
+refinement reference.  It then re-runs a compact copy of the pins (closed
+forms, the printed 216 pi / 35, a trigonometric polynomial's coefficients, the
+zero mean, the dense transpose, div grad = Delta, the gradient of x, solid
+rotation, the SVD pseudoinverse, exact recovery at the SVD rank, the dense F of
+the approximant, the refinement's single-precision start and FP64 limit) at
+their own tolerances, and asserts that the named pins fail.  The unmodified
+oracle passes every pin (the control case)."""
 
 import math
 
@@ -145,6 +146,15 @@ def pin_lowrank_coefficients():
     return np.abs(O.lowrank_rhs_coefficients(terms, *ft.shape) - F_dense).max() < 1e-13 * np.abs(F_dense).max()
 
 
+def pin_refinement_converges():
+    nt, nl = 32, 64
+    f = sh.synthesize(sh.random_sh_coeffs(14, 3), nt, nl).numpy()
+    u0, u1, u2 = O.refine_reference(f, 2)
+    u64 = O.poisson(f)
+    e0, e2 = _rel(u0, u64), _rel(u2, u64)
+    return 1e-10 < e0 < 1e-5 and e2 < 1e-13
+
+
 PINS = {
     "closed forms (dense)": lambda: pin_closed_forms("dense"),
     "closed forms (banded)": lambda: pin_closed_forms("banded"),
@@ -159,6 +169,7 @@ PINS = {
     "pivot pseudoinverse": pin_pivot_pseudoinverse,
     "GE recovery": pin_ge_recovery,
     "low-rank coefficients": pin_lowrank_coefficients,
+    "refinement converges": pin_refinement_converges,
 }
 
 
@@ -182,7 +193,8 @@ def _failing_pins():
 _orig = {name: getattr(O, name) for name in
          ("theta_bands_B", "system_matrix", "_bands_of", "integration_weights", "dfs_double",
           "_phase_theta", "coeffs2", "rhs_coefficients", "poisson_adjoint", "tangential_gradient",
-          "curl", "pivot_pinv", "bmc_ge", "lowrank_rhs_coefficients", "_solve_columns_T")}
+          "curl", "pivot_pinv", "bmc_ge", "lowrank_rhs_coefficients", "_solve_columns_T",
+          "_replaced_system_apply", "_solve_one_fp32")}
 
 
 def _bands_swapped(m):
@@ -306,6 +318,14 @@ def _lowrank_without_weight(terms, m, n):
     return F
 
 
+def _residual_sign_flipped(X, reading="B"):
+    return -_orig["_replaced_system_apply"](X, reading)   # F + M X instead of F - M X
+
+
+def _fp32_solve_in_fp64(Fk, m, k, reading="B"):
+    return O._solve_one(Fk, m, k, reading)                  # the single-precision solve done in FP64
+
+
 MISTAKES = [
     ("theta_bands_B", _bands_swapped, {"closed forms (dense)", "closed forms (banded)"}),
     ("theta_bands_B", _bands_without_first_order, {"closed forms (dense)", "closed forms (banded)"}),
@@ -326,6 +346,8 @@ MISTAKES = [
     ("pivot_pinv", _pinv_without_cut, {"pivot pseudoinverse"}),
     ("bmc_ge", _ge_with_unreflected_row, {"GE recovery"}),
     ("lowrank_rhs_coefficients", _lowrank_without_weight, {"low-rank coefficients"}),
+    ("_replaced_system_apply", _residual_sign_flipped, {"refinement converges"}),
+    ("_solve_one_fp32", _fp32_solve_in_fp64, {"refinement converges"}),
 ]
 
 
