@@ -17,8 +17,15 @@ forward-column recurrence of Holmes & Featherstone (J. Geodesy 76, 2002):
   Pbar_{m+1}^m = sqrt(2m+3) cos(theta) Pbar_m^m
   Pbar_l^m = a_lm (cos(theta) Pbar_{l-1}^m - Pbar_{l-2}^m / a_{l-1,m}),
   a_lm = sqrt((4 l^2 - 1) / (l^2 - m^2)).
-Values below the double range near the poles underflow to zero; the true
-values there are smaller than 1e-300 of the field's scale.
+The recurrences run on scaled values: each column m carries an integer power
+of two per colatitude (the scaling of Holmes & Featherstone's Section 2.7),
+renormalised by exact powers of two whenever a value leaves [2^-600, 2^600].
+Without it the sectoral seeds Pbar_m^m ~ sin^m(theta) go subnormal for m near
+1000 while, at degrees near 2048, Pbar_l^m at the same colatitude (its turning
+point, sin(theta) ~ m/l) is of order one: the seeds' lost digits came out as
+relative errors of 1e-9 there.  Values that stay below the double range (deep
+in the evanescent zone near the poles) are zero; the true ones are smaller
+than 1e-300 of the field's scale.
 
 Coefficients are held as a dense array C of shape (L+1, 2L+1), C[l, L+m]
 being the weight of Y_l^m (entries with |m| > l are ignored).  Random draws
@@ -85,6 +92,62 @@ def _angle_table(mmax: int, n_lambda: int, device) -> tuple[torch.Tensor, torch.
     return torch.cos(ang), torch.sin(ang)
 
 
+_RENORM = 600                      # exponent step of the renormalisation
+_BIG = 2.0 ** _RENORM
+_SMALL = 2.0 ** -_RENORM
+
+
+def _ldexp(p: torch.Tensor, e: torch.Tensor) -> torch.Tensor:
+    """p * 2**e for integer-valued float64 e, in two exact halves so that no
+    power of two underflows while the product is still representable."""
+    h = torch.floor(e * 0.5)
+    return p * torch.exp2(h) * torch.exp2(e - h)
+
+
+def _legendre_columns(lmax: int, theta: torch.Tensor):
+    """Yield (l, P) for l = 0..lmax, P[m, i] = Pbar_l^m(cos theta_i) for m <= l
+    (the forward-column recurrence of the module docstring, on scaled values)."""
+    dev = theta.device
+    nt = theta.shape[0]
+    x = torch.cos(theta)
+    s = torch.sin(theta)
+    # sectoral seeds Pbar_m^m = pm[m] * 2**pe[m]
+    pm = torch.empty((lmax + 1, nt), dtype=torch.float64, device=dev)
+    pe = torch.zeros((lmax + 1, nt), dtype=torch.float64, device=dev)
+    cur = torch.full((nt,), 1.0 / math.sqrt(4.0 * math.pi), dtype=torch.float64, device=dev)
+    ce = torch.zeros(nt, dtype=torch.float64, device=dev)
+    pm[0] = cur
+    for m in range(1, lmax + 1):
+        cur = cur * s * math.sqrt((2.0 * m + 1.0) / (2.0 * m))
+        small = cur.abs() < _SMALL
+        cur = torch.where(small, cur * _BIG, cur)
+        ce = torch.where(small, ce - _RENORM, ce)
+        pm[m] = cur
+        pe[m] = ce
+    # columns m of the recurrence in l, each with its own exponent ecol[m]
+    ecol = pe.clone()
+    p_prev2 = torch.zeros((lmax + 1, nt), dtype=torch.float64, device=dev)
+    p_prev = torch.zeros((lmax + 1, nt), dtype=torch.float64, device=dev)
+    mvec = torch.arange(lmax + 1, dtype=torch.float64, device=dev)
+    for l in range(0, lmax + 1):
+        p_l = torch.zeros((lmax + 1, nt), dtype=torch.float64, device=dev)
+        if l >= 2:
+            mm = mvec[: l - 1]
+            a_l = torch.sqrt((4.0 * l * l - 1.0) / (l * l - mm * mm))
+            a_lm1 = torch.sqrt((4.0 * (l - 1) ** 2 - 1.0) / ((l - 1) ** 2 - mm * mm))
+            p_l[: l - 1] = a_l[:, None] * (x[None, :] * p_prev[: l - 1] - p_prev2[: l - 1] / a_lm1[:, None])
+        if l >= 1:
+            p_l[l - 1] = math.sqrt(2.0 * l + 1.0) * x * pm[l - 1]
+        p_l[l] = pm[l]
+        big = p_l.abs() > _BIG
+        if bool(big.any()):
+            p_l = torch.where(big, p_l * _SMALL, p_l)
+            p_prev = torch.where(big, p_prev * _SMALL, p_prev)
+            ecol = torch.where(big, ecol + _RENORM, ecol)
+        yield l, _ldexp(p_l[: l + 1], ecol[: l + 1])
+        p_prev2, p_prev = p_prev, p_l
+
+
 def synthesize(coeffs: np.ndarray, n_theta: int, n_lambda: int, device="cpu") -> torch.Tensor:
     """Sample sum_lm C[l, L+m] Y_l^m on the grid; returns float64 [n_theta, n_lambda]."""
     coeffs = np.asarray(coeffs, dtype=np.float64)
@@ -93,8 +156,6 @@ def synthesize(coeffs: np.ndarray, n_theta: int, n_lambda: int, device="cpu") ->
         raise ValueError("coefficient array must have shape (L+1, 2L+1)")
     dev = torch.device(device)
     theta = torch.tensor(colatitudes(n_theta), dtype=torch.float64, device=dev)
-    x = torch.cos(theta)
-    s = torch.sin(theta)
     cc = torch.tensor(coeffs, dtype=torch.float64, device=dev)
     # column weights: cos part (m >= 0) and sin part (m > 0)
     ccos = cc[:, lmax:]                                   # [L+1, L+1]  m = 0..L
@@ -102,30 +163,11 @@ def synthesize(coeffs: np.ndarray, n_theta: int, n_lambda: int, device="cpu") ->
     csin = csin.clone()
     csin[:, 0] = 0.0
 
-    # sectoral start values Pbar_m^m for all m
-    pmm = torch.empty((lmax + 1, n_theta), dtype=torch.float64, device=dev)
-    pmm[0] = 1.0 / math.sqrt(4.0 * math.pi)
-    for m in range(1, lmax + 1):
-        pmm[m] = pmm[m - 1] * s * math.sqrt((2.0 * m + 1.0) / (2.0 * m))
-
     acc_c = torch.zeros((lmax + 1, n_theta), dtype=torch.float64, device=dev)
     acc_s = torch.zeros((lmax + 1, n_theta), dtype=torch.float64, device=dev)
-    p_prev2 = torch.zeros((lmax + 1, n_theta), dtype=torch.float64, device=dev)
-    p_prev = torch.zeros((lmax + 1, n_theta), dtype=torch.float64, device=dev)
-    mvec = torch.arange(lmax + 1, dtype=torch.float64, device=dev)
-    for l in range(0, lmax + 1):
-        p_l = torch.zeros((lmax + 1, n_theta), dtype=torch.float64, device=dev)
-        if l >= 2:
-            mm = mvec[: l - 1]
-            a_l = torch.sqrt((4.0 * l * l - 1.0) / (l * l - mm * mm))
-            a_lm1 = torch.sqrt((4.0 * (l - 1) ** 2 - 1.0) / ((l - 1) ** 2 - mm * mm))
-            p_l[: l - 1] = a_l[:, None] * (x[None, :] * p_prev[: l - 1] - p_prev2[: l - 1] / a_lm1[:, None])
-        if l >= 1:
-            p_l[l - 1] = math.sqrt(2.0 * l + 1.0) * x * pmm[l - 1]
-        p_l[l] = pmm[l]
-        acc_c[: l + 1] += ccos[l, : l + 1, None] * p_l[: l + 1]
-        acc_s[: l + 1] += csin[l, : l + 1, None] * p_l[: l + 1]
-        p_prev2, p_prev = p_prev, p_l
+    for l, p_l in _legendre_columns(lmax, theta):
+        acc_c[: l + 1] += ccos[l, : l + 1, None] * p_l
+        acc_s[: l + 1] += csin[l, : l + 1, None] * p_l
 
     scale = torch.full((lmax + 1,), math.sqrt(2.0), dtype=torch.float64, device=dev)
     scale[0] = 1.0
@@ -145,33 +187,14 @@ def synthesize_many(coeff_list, n_theta: int, n_lambda: int, device="cpu") -> to
     cc = torch.tensor(np.stack([np.asarray(c, dtype=np.float64) for c in coeff_list]), dtype=torch.float64,
                       device=dev)                                    # [P, L+1, 2L+1]
     theta = torch.tensor(colatitudes(n_theta), dtype=torch.float64, device=dev)
-    x = torch.cos(theta)
-    s = torch.sin(theta)
     ccos = cc[:, :, lmax:]                                           # [P, L+1, L+1] (m = 0..L)
     csin = torch.flip(cc[:, :, : lmax + 1], dims=[2]).clone()
     csin[:, :, 0] = 0.0
-    pmm = torch.empty((lmax + 1, n_theta), dtype=torch.float64, device=dev)
-    pmm[0] = 1.0 / math.sqrt(4.0 * math.pi)
-    for m in range(1, lmax + 1):
-        pmm[m] = pmm[m - 1] * s * math.sqrt((2.0 * m + 1.0) / (2.0 * m))
     acc_c = torch.zeros((P, lmax + 1, n_theta), dtype=torch.float64, device=dev)
     acc_s = torch.zeros((P, lmax + 1, n_theta), dtype=torch.float64, device=dev)
-    p_prev2 = torch.zeros((lmax + 1, n_theta), dtype=torch.float64, device=dev)
-    p_prev = torch.zeros((lmax + 1, n_theta), dtype=torch.float64, device=dev)
-    mvec = torch.arange(lmax + 1, dtype=torch.float64, device=dev)
-    for l in range(0, lmax + 1):
-        p_l = torch.zeros((lmax + 1, n_theta), dtype=torch.float64, device=dev)
-        if l >= 2:
-            mm = mvec[: l - 1]
-            a_l = torch.sqrt((4.0 * l * l - 1.0) / (l * l - mm * mm))
-            a_lm1 = torch.sqrt((4.0 * (l - 1) ** 2 - 1.0) / ((l - 1) ** 2 - mm * mm))
-            p_l[: l - 1] = a_l[:, None] * (x[None, :] * p_prev[: l - 1] - p_prev2[: l - 1] / a_lm1[:, None])
-        if l >= 1:
-            p_l[l - 1] = math.sqrt(2.0 * l + 1.0) * x * pmm[l - 1]
-        p_l[l] = pmm[l]
-        acc_c[:, : l + 1] += ccos[:, l, : l + 1, None] * p_l[None, : l + 1]
-        acc_s[:, : l + 1] += csin[:, l, : l + 1, None] * p_l[None, : l + 1]
-        p_prev2, p_prev = p_prev, p_l
+    for l, p_l in _legendre_columns(lmax, theta):
+        acc_c[:, : l + 1] += ccos[:, l, : l + 1, None] * p_l[None]
+        acc_s[:, : l + 1] += csin[:, l, : l + 1, None] * p_l[None]
     scale = torch.full((lmax + 1,), math.sqrt(2.0), dtype=torch.float64, device=dev)
     scale[0] = 1.0
     acc_c = acc_c * scale[None, :, None]

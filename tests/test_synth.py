@@ -66,3 +66,22 @@ def test_seeded_coefficients_are_reproducible():
     ls = np.arange(31)[:, None]
     ms = np.arange(-30, 31)[None, :]
     assert np.all(a[np.abs(ms) > ls] == 0)
+
+
+def test_turning_point_values_at_degree_2048():
+    # Pbar_l^m near its turning point sin(theta) ~ m/l, where the sectoral seed
+    # sin^m(theta) is below the normal double range (m ~ 1000): the scaled
+    # recurrence must keep full accuracy there.  Reference: mpmath's
+    # hypergeometric associated Legendre function at 40 digits, normalised as
+    # Pbar_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!) P_l^m, without the
+    # Condon-Shortley phase.
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    l, m, nt, nl = 2048, 1024, 64, 4100
+    f = sh.synthesize(sh.single_sh_coeffs(l, m), nt, nl).numpy()
+    th = sh.colatitudes(nt)
+    norm = mp.sqrt((2 * l + 1) / (4 * mp.pi) * mp.factorial(l - m) / mp.factorial(l + m)) * mp.sqrt(2)
+    for i in range(9, 14):                    # theta from 26.7 to 37.9 degrees; turning point at 30.0
+        p = mp.legenp(l, m, mp.cos(mp.mpf(th[i])), type=2)
+        ref = float(abs(p) * norm) * (1.0 if p * (-1) ** m >= 0 else -1.0)
+        assert abs(f[i, nl // 2] - ref) < 1e-12, (i, f[i, nl // 2], ref)   # lambda = 0: cos(m lambda) = 1
