@@ -34,15 +34,17 @@ if ROOT not in sys.path:
 METRIC = "Poisson DOF/s on 1 GB300 at stated error vs FP64 oracle"
 WORKLOAD = "sh2000_5000x10000"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 pipe peak if the live probe fails: 504 G DFMA/s measured on a GB300
-# (profiles/fp64_fp32_peak_probe.md) = 1008 GFLOP/s counting an FMA as 2 flops.
+# FP64 pipe peak if the live probe fails: 504 G DFMA/s, measured on a GB300 by
+# the library's register-only FMA loop filling every SM (sphere_poisson_pipe_rates),
+# = 1008 GFLOP/s counting an FMA as 2 flops.
 FP64_PEAK_GFLOPS_FALLBACK = 1008.0
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each FP64
 # stage kernel, from one ncu capture of the 5000 x 5000 workload (the colatitude
 # transforms of the 5000 x 10000 grid on half the longitudes; 200 MB input, larger
-# than L2) on the stage-kernel sources whose hash is `csrc_sha256`; see
-# profiles/traffic_fp64_5000x5000.md.  bench.py scales them to its own grid by the
+# than L2) on the stage-kernel sources whose hash is `csrc_sha256`, with
+# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` on one solve after
+# warm-up (read + write bytes below).  bench.py scales them to its own grid by the
 # spectrum size n_theta * Kp (every stage streams the spectrum once or twice) and
 # reports null when the sources have changed since the capture.
 TRAFFIC_CAPTURE = {

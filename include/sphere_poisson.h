@@ -43,6 +43,7 @@ extern "C" {
 
 /* status codes */
 #define SP_OK                0
+#define SP_WARN_NONZERO_MEAN 1   /* success; |mean of f| > 1e3 eps max|f| (sphere_poisson_solve_host) */
 #define SP_ERR_BAD_SIZE     -1   /* n_theta < 1, n_lambda < 2 or odd, too large, or a prime factor > 31 */
 #define SP_ERR_NULL         -2   /* a required pointer is NULL */
 #define SP_ERR_MISALIGNED   -3   /* a device pointer is not 16-byte aligned */
@@ -120,14 +121,27 @@ int sphere_poisson_workspace_size(sp_plan_t plan, size_t* workspace_bytes);
 /*
  * u = S f: the zero-mean solution of Delta u = f on the plan's grid.
  *   f          device, [n_theta][n_lambda] doubles, read only.  The paper assumes
- *              int_S f = 0; for other f the k = 0, j = 0 equation is dropped as in
- *              eq. pentdiagonalPlusRankOne and u solves the remaining equations.
+ *              int_S f = 0 (Section 5, the problem statement of eq.
+ *              SphericalLaplacian and eq. integralConstraint2); for other f the
+ *              k = 0, j = 0 equation is dropped as in eq. pentdiagonalPlusRankOne
+ *              and u solves the remaining equations.
  *   u          device, [n_theta][n_lambda] doubles, written.
  *   workspace  device, >= workspace_bytes; contents are scratch.
  *   stream     cudaStream_t (as void*) or NULL.
+ *   f_mean_out optional DEVICE pointer (8-byte aligned) or NULL: receives the
+ *              mean of f over the sphere, (1/4 pi) int_S f, by the quadrature of
+ *              eq. integrationCoeffs on the grid (the w-weights applied to the
+ *              colatitude coefficients of the lambda mean of f, theta-Nyquist
+ *              mode dropped; the value sphere_poisson_sum2 gives, divided by 4 pi).
+ *              Written asynchronously on `stream` by two extra kernels that read
+ *              f once before the solve; nothing is synchronised, so the call stays
+ *              capturable in a CUDA graph.  A caller compares it with its own
+ *              scale of f (sphere_poisson_solve_host does that check itself).
+ *              Single plans only (batched plans: SP_ERR_UNSUPPORTED).
+ * Errors: SP_ERR_BAD_ARG when the current device is not the plan's device.
  */
 int sphere_poisson_solve(sp_plan_t plan, const double* f, double* u, void* workspace,
-                         size_t workspace_bytes, void* stream);
+                         size_t workspace_bytes, void* stream, double* f_mean_out);
 
 /*
  * fbar = S^T ubar: the transpose of the linear map f -> u of sphere_poisson_solve
@@ -149,10 +163,18 @@ int sphere_poisson_solve_adjoint(sp_plan_t plan, const double* ubar, double* fba
  * plan-owned stream; calls on one plan from several host threads must be
  * serialised.  Pinned host memory gives the fastest copies; pageable memory
  * also works.
+ *   f_mean_out optional HOST pointer or NULL: receives the mean of f over the
+ *              sphere as in sphere_poisson_solve (computed on the device after
+ *              the solve, with max |f| in the same pass), and the call then
+ *              returns SP_WARN_NONZERO_MEAN (> 0: u is still written) when
+ *              |mean| > 1e3 eps max |f|, eps = 2^-52: f is not mean-zero to
+ *              rounding, so the dropped k = 0, j = 0 equation was not redundant.
+ *              Single plans only (batched plans: SP_ERR_UNSUPPORTED).
  */
 int sphere_poisson_host_buffer_size(sp_plan_t plan, size_t* device_buffer_bytes);
 int sphere_poisson_solve_host(sp_plan_t plan, const double* f_host, double* u_host,
-                              void* device_buffer, size_t device_buffer_bytes, void* stream);
+                              void* device_buffer, size_t device_buffer_bytes, void* stream,
+                              double* f_mean_out);
 
 /*
  * Allocation-free solve.  The paper has no counterpart; this is a service for
@@ -167,10 +189,13 @@ int sphere_poisson_solve_host(sp_plan_t plan, const double* f_host, double* u_ho
  * SP_NOALLOC_SCRATCH_BYTES (32 MiB), which every GPU that loads the library
  * holds until the process exits.
  *   plan    an existing plan (creating the plan allocates its tables; do it at
- *           start-up).  Its workspace size must not exceed SP_NOALLOC_SCRATCH_BYTES
- *           (n_theta * Kp * 16 bytes, Kp = n_lambda/2 + 1 rounded up to even,
- *           e.g. 1024 x 2048 fits, 2048 x 4096 does not); larger plans get
- *           SP_ERR_SCRATCH_LIMIT and nothing runs.
+ *           start-up), single or batched, of any precision.  Its workspace size
+ *           (sphere_poisson_workspace_size) must not exceed SP_NOALLOC_SCRATCH_BYTES;
+ *           larger plans get SP_ERR_SCRATCH_LIMIT and nothing runs.  For example
+ *           an SP_FP64 plan needs n_theta * Kp * 16 bytes (Kp = n_lambda/2 + 1
+ *           rounded up to even), so 1024 x 2048 fits and 2048 x 4096 does not; an
+ *           SP_FP32_REFINE plan needs about 2.5 times that (two double-float
+ *           spectra and an FP32 one), so 512 x 1024 fits and 1024 x 2048 does not.
  *   f, u    device arrays as for sphere_poisson_solve.
  *   stream  cudaStream_t (as void*) or NULL.
  * The current device must be the plan's device (else SP_ERR_BAD_ARG).  The first
@@ -220,14 +245,17 @@ int sphere_poisson_sum2(sp_plan_t plan, const double* f, double* result, void* w
  * computed on the coefficients of coeffs2 (the maps of Section 4: multiplication
  * by cos / sin of either angle shifts the index by one, d/dtheta and d/dlambda
  * multiply by ij and ik) with the division by sin theta done as M_sin^{-1}
- * (eq. Msin) by the recurrence of M_sin x = a run down from the top of the
- * coefficient window.  The sign of gz is the chain rule's for the colatitude
- * theta of eq. sphericalCoordinates (the paper prints +sin theta d/dtheta).
- * The theta- and lambda-Nyquist modes are dropped from f and from the results.
- * Exact (to rounding) for f band-limited within the grid's window; for other f
- * the results carry truncation terms of the window, and the recurrence's are not
- * those of the dense inverse of the truncated M_sin (the window's boundary rows
- * differ; on the degenerate grids 1 x n, 2 x 4 and n x 2 the two agree).
+ * (eq. Msin) on the m-point coefficient window j in [-m/2, m/2-1].  Only the
+ * folded half j >= 0 of the quotient is formed, whose symmetry a quotient by
+ * sin theta of a function on the sphere has: odd-k columns by the recurrence of
+ * M_sin x = a run down from the top of the window, even-k columns (x_0 = 0) run
+ * up from row 0.  That is the part of the window solve with this symmetry, and
+ * the rest of the window solve does not reach the samples on theta > 0, so the
+ * results are those of the dense solve for every f.  The sign of gz is the
+ * chain rule's for the colatitude theta of eq. sphericalCoordinates (the paper
+ * prints +sin theta d/dtheta).  The theta- and lambda-Nyquist modes are dropped
+ * from f and from the results.  Exact (to rounding) for f band-limited within
+ * the grid's window; for other f the results carry the window's truncation.
  *   f, gx, gy, gz  device, [n_theta][n_lambda] doubles, 16-byte aligned.
  *   workspace      device, >= sphere_poisson_gradient_workspace_size bytes
  *                  (five half spectra of n_theta Kp 16 bytes, Kp = n_lambda/2 + 1

@@ -439,7 +439,13 @@ def tangential_gradient(f: np.ndarray, chop: float = 0.0):
     m x n window are discarded.  (3) chop > 0: coefficients with
     |X_jk| <= chop max |X| are set to zero first, the grid counterpart of the
     constructor resolving a function to a tolerance relative to its maximum
-    (Section 3)."""
+    (Section 3).  (4) The window j in [-m/2, m/2-1] of eq. Msin is not symmetric
+    about j = 0: when the quotient is not band-limited inside it, the solve
+    also returns a part without the symmetry q_{-j,k} = -(-1)^k q_{j,k} that a
+    quotient by sin theta of a function on the sphere has (Section 2, BMC
+    functions).  That part never reaches the results on theta > 0: dropping the
+    theta-Nyquist row of each result and taking the real part removes it, so
+    the results are those of the symmetric part alone."""
     ft = dfs_double(f)
     m, n = ft.shape
     nt = m // 2

@@ -37,11 +37,15 @@ def _stream_ptr(stream) -> int:
     return int(stream.cuda_stream)
 
 
-def _check_grid(t: torch.Tensor, shape, name: str):
+def _check_grid(t: torch.Tensor, shape, name: str, device=None):
+    """Shape, dtype, contiguity and device of a grid argument; `device` is the
+    plan's device (the library's tables live there and its kernels run there)."""
     if not isinstance(t, torch.Tensor):
         raise TypeError(f"{name} must be a torch.Tensor")
     if t.dtype != torch.float64:
         raise TypeError(f"{name} must be float64, got {t.dtype}")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, the plan is on {device}")
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
     if tuple(t.shape) != tuple(shape):
@@ -96,29 +100,40 @@ class Plan:
                    "sphere_poisson_launch_count")
         return int(n.value)
 
-    def solve(self, f: torch.Tensor, out: torch.Tensor | None = None, workspace=None, stream=None):
-        """u with Delta u = f and zero sphere mean (f: float64 CUDA [n_theta, n_lambda])."""
-        _check_grid(f, self.shape, "f")
+    def solve(self, f: torch.Tensor, out: torch.Tensor | None = None, workspace=None, stream=None,
+              mean_out: torch.Tensor | None = None):
+        """u with Delta u = f and zero sphere mean (f: float64 CUDA [n_theta, n_lambda]).
+
+        mean_out: optional float64 tensor on the plan's device; its first element
+        receives the mean of f over the sphere (written on the stream, no sync)."""
+        _check_grid(f, self.shape, "f", self.device)
         if out is None:
             out = torch.empty_like(f)
-        _check_grid(out, self.shape, "out")
+        _check_grid(out, self.shape, "out", self.device)
+        mean_ptr = None
+        if mean_out is not None:
+            if mean_out.dtype != torch.float64 or mean_out.device != self.device or mean_out.numel() < 1:
+                raise ValueError("mean_out must be a float64 tensor on the plan's device")
+            mean_ptr = mean_out.data_ptr()
         ws = self._workspace(workspace)
-        _lib.check(self._lib.sphere_poisson_solve(self._h, f.data_ptr(), out.data_ptr(), ws.data_ptr(),
-                                                  ws.numel() * ws.element_size(), _stream_ptr(stream)),
-                   "sphere_poisson_solve")
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sphere_poisson_solve(self._h, f.data_ptr(), out.data_ptr(), ws.data_ptr(),
+                                                      ws.numel() * ws.element_size(), _stream_ptr(stream),
+                                                      mean_ptr), "sphere_poisson_solve")
         return out
 
     def solve_adjoint(self, ubar: torch.Tensor, out: torch.Tensor | None = None, workspace=None, stream=None):
         """S^T ubar, the transpose of f -> u (the vector-Jacobian product)."""
-        _check_grid(ubar, self.shape, "ubar")
+        _check_grid(ubar, self.shape, "ubar", self.device)
         if out is None:
             out = torch.empty_like(ubar)
-        _check_grid(out, self.shape, "out")
+        _check_grid(out, self.shape, "out", self.device)
         ws = self._workspace(workspace)
-        _lib.check(self._lib.sphere_poisson_solve_adjoint(self._h, ubar.data_ptr(), out.data_ptr(),
-                                                          ws.data_ptr(), ws.numel() * ws.element_size(),
-                                                          _stream_ptr(stream)),
-                   "sphere_poisson_solve_adjoint")
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sphere_poisson_solve_adjoint(self._h, ubar.data_ptr(), out.data_ptr(),
+                                                              ws.data_ptr(), ws.numel() * ws.element_size(),
+                                                              _stream_ptr(stream)),
+                       "sphere_poisson_solve_adjoint")
         return out
 
     def solve_noalloc(self, f: torch.Tensor, out: torch.Tensor, stream=None):
@@ -126,11 +141,12 @@ class Plan:
         they solve: no workspace, the library's fixed 32 MiB scratch array is used
         instead (grids up to that size).  Calls that overlap on the GPU race on
         that shared array; `out` must be given because this call allocates nothing."""
-        _check_grid(f, self.shape, "f")
-        _check_grid(out, self.shape, "out")
-        _lib.check(self._lib.sphere_poisson_solve_noalloc(self._h, f.data_ptr(), out.data_ptr(),
-                                                          _stream_ptr(stream)),
-                   "sphere_poisson_solve_noalloc")
+        _check_grid(f, self.shape, "f", self.device)
+        _check_grid(out, self.shape, "out", self.device)
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sphere_poisson_solve_noalloc(self._h, f.data_ptr(), out.data_ptr(),
+                                                              _stream_ptr(stream)),
+                       "sphere_poisson_solve_noalloc")
         return out
 
     @property
@@ -142,11 +158,12 @@ class Plan:
     def coeffs2(self, f: torch.Tensor, stream=None) -> torch.Tensor:
         """2D Fourier coefficients X[j, k] of f~, j = 0..n_theta-1, k = 0..n_lambda/2
         (the last column is k = -n_lambda/2), as a complex128 tensor [n_theta, Kp]."""
-        _check_grid(f, self.shape, "f")
+        _check_grid(f, self.shape, "f", self.device)
         out = torch.empty(self.spectrum_shape, dtype=torch.complex128, device=self.device)
         ws = self._workspace(None)
-        _lib.check(self._lib.sphere_poisson_coeffs2(self._h, f.data_ptr(), out.data_ptr(), ws.data_ptr(),
-                                                    ws.numel(), _stream_ptr(stream)), "sphere_poisson_coeffs2")
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sphere_poisson_coeffs2(self._h, f.data_ptr(), out.data_ptr(), ws.data_ptr(),
+                                                        ws.numel(), _stream_ptr(stream)), "sphere_poisson_coeffs2")
         return out
 
     def sample(self, coeffs: torch.Tensor, stream=None) -> torch.Tensor:
@@ -156,17 +173,19 @@ class Plan:
         coeffs = coeffs.contiguous()
         out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
         ws = self._workspace(None)
-        _lib.check(self._lib.sphere_poisson_sample(self._h, coeffs.data_ptr(), out.data_ptr(), ws.data_ptr(),
-                                                   ws.numel(), _stream_ptr(stream)), "sphere_poisson_sample")
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sphere_poisson_sample(self._h, coeffs.data_ptr(), out.data_ptr(), ws.data_ptr(),
+                                                       ws.numel(), _stream_ptr(stream)), "sphere_poisson_sample")
         return out
 
     def sum2(self, f: torch.Tensor, stream=None) -> float:
         """Surface integral of f over the unit sphere (synchronises)."""
-        _check_grid(f, self.shape, "f")
+        _check_grid(f, self.shape, "f", self.device)
         res = torch.empty(2, dtype=torch.float64, device=self.device)
         ws = self._workspace(None)
-        _lib.check(self._lib.sphere_poisson_sum2(self._h, f.data_ptr(), res.data_ptr(), ws.data_ptr(),
-                                                 ws.numel(), _stream_ptr(stream)), "sphere_poisson_sum2")
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sphere_poisson_sum2(self._h, f.data_ptr(), res.data_ptr(), ws.data_ptr(),
+                                                     ws.numel(), _stream_ptr(stream)), "sphere_poisson_sum2")
         return float(res[0])
 
     def gradient_workspace_bytes(self) -> int:
@@ -189,12 +208,12 @@ class Plan:
 
     def _derivative_call(self, name, inputs, n_out, out, workspace, need, stream):
         for i, f in enumerate(inputs):
-            _check_grid(f, self.shape, f"input {i}")
+            _check_grid(f, self.shape, f"input {i}", self.device)
         if out is None:
             out = tuple(torch.empty_like(inputs[0]) for _ in range(n_out))
         nbytes = inputs[0].numel() * 8
         for o in out:
-            _check_grid(o, self.shape, "out")
+            _check_grid(o, self.shape, "out", self.device)
             for f in inputs:
                 if abs(o.data_ptr() - f.data_ptr()) < nbytes:
                     raise ValueError("outputs must not overlap the inputs")
@@ -202,9 +221,10 @@ class Plan:
             workspace = torch.empty(need, dtype=torch.uint8, device=self.device)
         elif workspace.numel() * workspace.element_size() < need:
             raise ValueError("workspace too small")
-        _lib.check(getattr(self._lib, name)(
-            self._h, *[t.data_ptr() for t in inputs], *[o.data_ptr() for o in out],
-            workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream_ptr(stream)), name)
+        with torch.cuda.device(self.device):
+            _lib.check(getattr(self._lib, name)(
+                self._h, *[t.data_ptr() for t in inputs], *[o.data_ptr() for o in out],
+                workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream_ptr(stream)), name)
         return out
 
     def tangential_gradient(self, f: torch.Tensor, out=None, workspace=None, stream=None):
@@ -247,7 +267,7 @@ class Plan:
                    alpha: float = 0.01, stream=None):
         """Structure-preserving GE of f (Section 3): (cols [T, 2 n_theta], piv [T, 2],
         rows [T, n_lambda]) with f ~= sum_t [c_t(theta) c_t(-theta)] P_t [r_t(lambda); r_t(lambda+pi)]."""
-        _check_grid(f, self.shape, "f")
+        _check_grid(f, self.shape, "f", self.device)
         T = min(self.n_theta, 1024) if max_terms is None else int(max_terms)
         m, n = 2 * self.n_theta, self.n_lambda
         cols = torch.empty(max(T, 1), m, dtype=torch.float64, device=self.device)
@@ -255,10 +275,11 @@ class Plan:
         piv = torch.empty(max(T, 1), 2, dtype=torch.float64, device=self.device)
         ws = torch.empty(self.lowrank_workspace_bytes(T), dtype=torch.uint8, device=self.device)
         count = ctypes.c_int()
-        _lib.check(self._lib.sphere_poisson_lowrank_ge(self._h, f.data_ptr(), T, float(rtol), float(alpha),
-                                                       ctypes.byref(count), cols.data_ptr(), piv.data_ptr(),
-                                                       rows.data_ptr(), ws.data_ptr(), ws.numel(),
-                                                       _stream_ptr(stream)), "sphere_poisson_lowrank_ge")
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sphere_poisson_lowrank_ge(self._h, f.data_ptr(), T, float(rtol), float(alpha),
+                                                           ctypes.byref(count), cols.data_ptr(), piv.data_ptr(),
+                                                           rows.data_ptr(), ws.data_ptr(), ws.numel(),
+                                                           _stream_ptr(stream)), "sphere_poisson_lowrank_ge")
         k = int(count.value)
         return cols[:k], piv[:k], rows[:k]
 
@@ -272,12 +293,13 @@ class Plan:
         cols, piv, rows = cols.contiguous(), piv.contiguous(), rows.contiguous()
         if out is None:
             out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
-        _check_grid(out, self.shape, "out")
+        _check_grid(out, self.shape, "out", self.device)
         ws = torch.empty(self.lowrank_workspace_bytes(T), dtype=torch.uint8, device=self.device)
-        _lib.check(self._lib.sphere_poisson_solve_lowrank(self._h, T, cols.data_ptr(), piv.data_ptr(),
-                                                          rows.data_ptr(), out.data_ptr(), ws.data_ptr(),
-                                                          ws.numel(), _stream_ptr(stream)),
-                   "sphere_poisson_solve_lowrank")
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sphere_poisson_solve_lowrank(self._h, T, cols.data_ptr(), piv.data_ptr(),
+                                                              rows.data_ptr(), out.data_ptr(), ws.data_ptr(),
+                                                              ws.numel(), _stream_ptr(stream)),
+                       "sphere_poisson_solve_lowrank")
         return out
 
     def host_buffer_bytes(self) -> int:
@@ -287,8 +309,11 @@ class Plan:
         return int(n.value)
 
     def solve_host(self, f_host: torch.Tensor, out: torch.Tensor | None = None, device_buffer=None,
-                   stream=None):
-        """Host-memory form: copies f in, solves, copies u out, then synchronises."""
+                   stream=None, with_mean: bool = False):
+        """Host-memory form: copies f in, solves, copies u out, then synchronises.
+
+        with_mean=True returns (u, mean of f, status): status is
+        SP_WARN_NONZERO_MEAN when f is not mean-zero to rounding, else SP_OK."""
         if f_host.dtype != torch.float64 or f_host.is_cuda or tuple(f_host.shape) != self.shape:
             raise ValueError("f_host must be a float64 CPU tensor of the plan's shape")
         f_host = f_host.contiguous()
@@ -297,10 +322,17 @@ class Plan:
         need = self.host_buffer_bytes()
         if device_buffer is None:
             device_buffer = torch.empty(need, dtype=torch.uint8, device=self.device)
-        _lib.check(self._lib.sphere_poisson_solve_host(self._h, f_host.data_ptr(), out.data_ptr(),
-                                                       device_buffer.data_ptr(),
-                                                       device_buffer.numel(), _stream_ptr(stream)),
-                   "sphere_poisson_solve_host")
+        elif device_buffer.device != self.device:
+            raise ValueError("device_buffer is not on the plan's device")
+        mean = ctypes.c_double()
+        with torch.cuda.device(self.device):
+            rc = _lib.check(self._lib.sphere_poisson_solve_host(self._h, f_host.data_ptr(), out.data_ptr(),
+                                                                device_buffer.data_ptr(), device_buffer.numel(),
+                                                                _stream_ptr(stream),
+                                                                ctypes.byref(mean) if with_mean else None),
+                            "sphere_poisson_solve_host")
+        if with_mean:
+            return out, float(mean.value), int(rc)
         return out
 
     def profile_begin(self, max_solves: int):
@@ -383,10 +415,10 @@ class BatchedPlan(Plan):
     def unpack(self, packed):
         return [packed[self.offsets[b]:self.offsets[b + 1]].view(*self.sizes[b]) for b in range(len(self.sizes))]
 
-    def solve(self, f, out=None, workspace=None, stream=None):
+    def solve(self, f, out=None, workspace=None, stream=None, mean_out=None):
         if f.dim() != 1:
             raise ValueError("batched solve takes the packed 1-D array")
-        return super().solve(f, out, workspace, stream)
+        return super().solve(f, out, workspace, stream, mean_out)
 
 
 _plans: dict = {}
@@ -414,17 +446,24 @@ def solve_adjoint(ubar: torch.Tensor, precision: str = "fp64", refine_sweeps: in
 
 
 class SpherePoisson(torch.autograd.Function):
-    """Differentiable solve: forward u = S f, backward grad_f = S^T grad_u."""
+    """Differentiable solve: forward u = S f, backward grad_f = S^T grad_u.
+
+    The fp64 and fp32 forms have their own transposes.  The fp32_refine form
+    computes the FP64 solution map to ~1e-13 (refined), so its backward is the
+    FP64 adjoint, the transpose of the map it approximates; the refinement
+    itself is not differentiated (its iterates depend on f through rounding only)."""
 
     @staticmethod
     def forward(ctx, f, precision="fp64", refine_sweeps=0):
+        if precision not in _PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(_PRECISIONS)}")
         ctx.precision = precision
-        ctx.refine_sweeps = refine_sweeps
         return solve(f.contiguous(), precision, refine_sweeps)
 
     @staticmethod
     def backward(ctx, grad_u):
-        g = solve_adjoint(grad_u.contiguous(), ctx.precision, ctx.refine_sweeps)
+        adj = "fp64" if ctx.precision == "fp32_refine" else ctx.precision
+        g = solve_adjoint(grad_u.contiguous(), adj)
         return g, None, None
 
 

@@ -14,6 +14,7 @@ from . import build as _build
 _lib = None
 
 SP_OK = 0
+SP_WARN_NONZERO_MEAN = 1
 SP_ERR_BAD_SIZE = -1
 SP_ERR_NULL = -2
 SP_ERR_MISALIGNED = -3
@@ -92,10 +93,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                                 ctypes.POINTER(ctypes.c_int), i32, i32, u32, psz]
     lib.sphere_poisson_batch_offsets.argtypes = [vp, psz]
     lib.sphere_poisson_workspace_size.argtypes = [vp, psz]
-    lib.sphere_poisson_solve.argtypes = [vp, vp, vp, vp, sz, vp]
+    lib.sphere_poisson_solve.argtypes = [vp, vp, vp, vp, sz, vp, vp]
     lib.sphere_poisson_solve_adjoint.argtypes = [vp, vp, vp, vp, sz, vp]
     lib.sphere_poisson_host_buffer_size.argtypes = [vp, psz]
-    lib.sphere_poisson_solve_host.argtypes = [vp, vp, vp, vp, sz, vp]
+    lib.sphere_poisson_solve_host.argtypes = [vp, vp, vp, vp, sz, vp, ctypes.POINTER(ctypes.c_double)]
     lib.sphere_poisson_solve_noalloc.argtypes = [vp, vp, vp, vp]
     lib.sphere_poisson_coeffs2.argtypes = [vp, vp, vp, vp, sz, vp]
     lib.sphere_poisson_sample.argtypes = [vp, vp, vp, vp, sz, vp]

@@ -31,6 +31,80 @@ __global__ void k_sum2_finish(const cpx<double>* __restrict__ C, int N, int Kp, 
   }
 }
 
+// Mean of f over the sphere, (1/4 pi) int_S f, by the same quadrature as the
+// surface integral above (eq. integrationCoeffs on the DFS interpolant, the
+// theta-Nyquist mode dropped), written on the grid values: the lambda mean of
+// row i is (1/n) sum_q f_iq, and the colatitude quadrature is the plan's row
+// weight w_i, so mean = sum_i sum_q (w_i / n) f_iq with wrow[i] = w_i / n.
+// Pass 1: each CTA takes rows blockIdx.x, blockIdx.x + gridDim.x, ... and
+// writes (its weighted sum, the largest |f_iq| as the bits of a non-negative
+// double) to part[blockIdx.x]; pass 2 (one CTA) adds the parts in a fixed
+// order, so the result does not depend on scheduling.  Rows are read as
+// 16-byte pairs (n even, f 16-byte aligned).  blockDim.x: a multiple of 32, <= 1024.
+__device__ __forceinline__ void block_sum_max(double& s, unsigned long long& mx) {
+  __shared__ double rs[32];
+  __shared__ unsigned long long rm[32];
+  for (int off = 16; off > 0; off >>= 1) {
+    s += __shfl_down_sync(0xffffffffu, s, off);
+    const unsigned long long o = __shfl_down_sync(0xffffffffu, mx, off);
+    mx = o > mx ? o : mx;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    rs[threadIdx.x >> 5] = s;
+    rm[threadIdx.x >> 5] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    unsigned long long m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      t += rs[w];
+      m = rm[w] > m ? rm[w] : m;
+    }
+    s = t;
+    mx = m;
+  }
+}
+
+__global__ void k_mean_partial(const double* __restrict__ f, int nt, int n, const double* __restrict__ wrow,
+                               double2* __restrict__ part) {
+  double acc = 0.0;
+  unsigned long long mx = 0;
+  const int half = n >> 1;
+  for (int i = blockIdx.x; i < nt; i += gridDim.x) {
+    const double2* row = reinterpret_cast<const double2*>(f + (size_t)i * n);
+    double s = 0.0;
+    for (int q = threadIdx.x; q < half; q += blockDim.x) {
+      const double2 v = row[q];
+      s += v.x + v.y;
+      const unsigned long long a = (unsigned long long)__double_as_longlong(v.x) & 0x7fffffffffffffffull;
+      const unsigned long long b = (unsigned long long)__double_as_longlong(v.y) & 0x7fffffffffffffffull;
+      const unsigned long long ab = a > b ? a : b;
+      mx = ab > mx ? ab : mx;
+    }
+    acc = fma(wrow[i], s, acc);
+  }
+  block_sum_max(acc, mx);
+  if (threadIdx.x == 0) part[blockIdx.x] = make_double2(acc, __longlong_as_double((long long)mx));
+}
+
+__global__ void k_mean_final(const double2* __restrict__ part, int nparts, double* __restrict__ mean,
+                             double* __restrict__ absmax) {
+  double s = 0.0;
+  unsigned long long mx = 0;
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+    const double2 v = part[b];
+    s += v.x;
+    const unsigned long long m = (unsigned long long)__double_as_longlong(v.y);
+    mx = m > mx ? m : mx;
+  }
+  block_sum_max(s, mx);
+  if (threadIdx.x == 0) {
+    if (mean) *mean = s;
+    if (absmax) *absmax = __longlong_as_double((long long)mx);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Tangential derivatives (Section 4, Differentiation, eqs. diff_x..diff_z and
 // Msin) on the folded coefficients X[j][k] of coeffs2 (the paper's convention:
@@ -38,16 +112,29 @@ __global__ void k_sum2_finish(const cpx<double>* __restrict__ C, int N, int Kp, 
 // X_{-j,k} = (-1)^k X_{j,k}; the lambda-Nyquist column k = L is dropped).
 //
 // Q = (1/sin theta) d/dlambda f in coefficients: M_sin Q = a with a = ik X
-// (eq. Msin: (i/2)(x_{j+1} - x_{j-1}) = a_j), solved by running the
-// recurrence x_{j-1} = x_{j+1} + 2i a_j down from the top of the window with
-// x_N = x_{N-1} = 0, i.e. x_j = 2i sum_{r = j+1, j+3, ... <= N-1} a_r
-// = -2k sum_{r} X_{r,k}.  This is M_sin^{-1} a whenever the quotient lies in the
-// window (band-limited f).
-// The suffix sums are taken over row chunks of kMsinRows rows so that every
+// (eq. Msin: (i/2)(x_{j+1} - x_{j-1}) = a_j).  A quotient by sin theta of a
+// function on the sphere has the symmetry Q_{-j,k} = -(-1)^k Q_{j,k} (the
+// numerator is BMC, sin theta is odd in theta), so only j >= 0 is formed, and
+// the rows of M_sin that the folded unknowns can satisfy fix it:
+//   k odd  (Q_{-j} = Q_j):  rows j = 1..N-1 with x_N = x_{N-1} = 0, run down
+//          from the top: x_{j-1} = x_{j+1} + 2i a_j, i.e.
+//          x_j = 2i sum_{r = j+1, j+3, ... <= N-1} a_r = -2k sum_r X_{r,k};
+//   k even (Q_{-j} = -Q_j, so x_0 = 0):  rows j = 0..N-2 run up from the
+//          bottom, row 0 reading -2 x_1 = 2i a_0: x_{j+1} = x_{j-1} - 2i a_j, i.e.
+//          x_j = -2i sum_{r = j-1, j-3, ... >= 0} w_r a_r = 2k sum_r w_r X_{r,k}
+//          with w_0 = 1/2, w_r = 1 otherwise.
+// This is the part with that symmetry of the dense solve of M_sin on the
+// m-point window j in [-m/2, m/2-1] (for odd k the solve has the symmetry
+// already; for even k the window's asymmetric bottom row leaves a part
+// without it, which the samples on theta > 0 do not see), and M_sin^{-1} a
+// itself whenever the quotient lies in the window (band-limited f).
+// The sums are taken over row chunks of kMsinRows rows so that every
 // (chunk, column) has a thread: pass 1 sums each chunk's even and odd rows into
-// P[2c][k], P[2c+1][k]; a scan turns those into the sums over the chunks above
-// (one thread per column and parity); pass 3 walks each chunk downwards writing
-// Q, carrying the sums already scaled by -2k (one FMA per coefficient).
+// P[2c][k], P[2c+1][k] (row 0 weighted 1/2 in even columns); a scan turns those
+// into the sums over the chunks above (odd k) or below (even k), one thread per
+// column and parity; pass 3 walks each chunk, downwards for odd k and upwards for
+// even k, writing Q and carrying the sums already scaled by -/+2k (one FMA per
+// coefficient).
 // Grid of passes 1 and 3: (ceil(Kp / blockDim.x), chunks).
 // ---------------------------------------------------------------------------
 constexpr int kMsinRows = 64;
@@ -64,22 +151,26 @@ __global__ void k_msin_partial(const cpx<double>* __restrict__ X, cpx<double>* _
       se = se + X[(size_t)j * Kp + k];
       if (j + 1 < j1) so = so + X[(size_t)(j + 1) * Kp + k];
     }
+    if (c == 0 && (k & 1) == 0) se = se - 0.5 * X[k];   // w_0 = 1/2 in even columns
   }
   P[(size_t)(2 * c) * Kp + k] = se;
   P[(size_t)(2 * c + 1) * Kp + k] = so;
 }
 
-// P[2c + par][k] <- sum over chunks c' > c of the chunk sums (exclusive suffix)
+// P[2c + par][k] <- the sum of the chunk sums over the chunks c' > c (odd k) or
+// c' < c (even k): an exclusive scan in the direction that column's walk takes
 __global__ void k_msin_scan(cpx<double>* __restrict__ P, int chunks, int Kp) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= 2 * Kp) return;
   const int par = idx >= Kp, k = par ? idx - Kp : idx;
+  const bool up = (k & 1) == 0;
   cpx<double> run = {0.0, 0.0};
-  for (int c = chunks - 1; c >= 0; --c) {
+  for (int t = 0; t < chunks; ++t) {
+    const int c = up ? t : chunks - 1 - t;
     cpx<double>& slot = P[(size_t)(2 * c + par) * Kp + k];
-    const cpx<double> t = slot;
+    const cpx<double> v = slot;
     slot = run;
-    run = run + t;
+    run = run + v;
   }
 }
 
@@ -89,21 +180,25 @@ __global__ void k_msin_apply(const cpx<double>* __restrict__ X, const cpx<double
   if (k >= Kp) return;
   const int c = blockIdx.y, j0 = c * kMsinRows, j1 = min(N, j0 + kMsinRows);
   const bool live = k < K - 1;
-  const double scale = -2.0 * (double)k;
-  // -2k times the sums of the even / odd rows r >= j1
+  const bool up = (k & 1) == 0;
+  const double scale = up ? 2.0 * (double)k : -2.0 * (double)k;
+  // the scaled sums of the even / odd rows beyond this chunk in the walk's direction
   cpx<double> se = {0.0, 0.0}, so = {0.0, 0.0};
   if (live) {
     se = scale * P[(size_t)(2 * c) * Kp + k];
     so = scale * P[(size_t)(2 * c + 1) * Kp + k];
   }
+  const int len = j1 - j0;
 #pragma unroll 4
-  for (int j = j1 - 1; j >= j0; --j) {
-    // Q_j takes the rows above j of the other parity
+  for (int t = 0; t < len; ++t) {
+    const int j = up ? j0 + t : j1 - 1 - t;
+    // Q_j takes the rows of the other parity already walked past
     Q[(size_t)j * Kp + k] = (j & 1) ? se : so;
     if (live) {
       const cpx<double> x = X[(size_t)j * Kp + k];
+      const double sc = (up && j == 0) ? 0.5 * scale : scale;
       cpx<double>& s = (j & 1) ? so : se;
-      s = {fma(scale, x.re, s.re), fma(scale, x.im, s.im)};
+      s = {fma(sc, x.re, s.re), fma(sc, x.im, s.im)};
     }
   }
 }

@@ -98,6 +98,11 @@ void launch_batched_fp64(bool big, dim3 grid, int threads, size_t smem, cudaStre
 void launch_sum2_finish(cudaStream_t st, const cpx<double>* C, int N, int Kp, double* out) {
   k_sum2_finish<<<1, 256, 0, st>>>(C, N, Kp, out);
 }
+void launch_mean(cudaStream_t st, const double* f, int nt, int n, const double* wrow, double2* part, int nparts,
+                 double* mean, double* absmax) {
+  k_mean_partial<<<nparts, 256, 0, st>>>(f, nt, n, wrow, part);
+  k_mean_final<<<1, 256, 0, st>>>(part, nparts, mean, absmax);
+}
 size_t msin_scratch_bytes(int N, int Kp) {
   const size_t chunks = (size_t)(N + kMsinRows - 1) / kMsinRows;
   return 2 * chunks * (size_t)Kp * sizeof(cpx<double>);

@@ -87,6 +87,10 @@ void launch_batched_refine(bool big, dim3 grid, int threads, size_t smem, cudaSt
 
 // surface integral from the k = 0 coefficient column (one CTA, result to device memory)
 void launch_sum2_finish(cudaStream_t st, const cpx<double>* C, int N, int Kp, double* out);
+// mean of f over the sphere and max |f| (either output may be NULL): `nparts`
+// partial sums in part[0..nparts) (device scratch), then one CTA adds them
+void launch_mean(cudaStream_t st, const double* f, int nt, int n, const double* wrow, double2* part, int nparts,
+                 double* mean, double* absmax);
 // tangential derivatives: Q = (1/sin theta) d/dlambda in coefficients (the
 // scratch array P of msin_scratch_bytes bytes takes the chunk sums), then the
 // signed sums of gradient components that `tc` describes

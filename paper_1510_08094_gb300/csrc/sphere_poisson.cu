@@ -31,6 +31,7 @@ constexpr int kMaxLen = 12288;             // longest transform (n_theta, n_lamb
 constexpr size_t kSmemBudget = 200 * 1024;  // shared memory per CTA for a transform tile
 constexpr int kBatchThreadsPerCta = 256;     // threads of a persistent batched CTA
 constexpr int kHostChunks = 16;              // row chunks of the host-buffer solve's overlapped copies
+constexpr double kMeanWarnFactor = 1e3 * 2.220446049250313080847263336181640625e-16;  // 1e3 eps
 constexpr uint32_t kMagic = 0x53504f31u;    // "SPO1"
 constexpr double kHalfPi = 1.57079632679489661923132169163975144;
 
@@ -295,6 +296,8 @@ struct sp_plan_s {
   double* row_plain;     // 1/n (transforms without the sin^2 weight)
   double* sin2;          // sin^2(theta_i) (the low-rank right-hand side)
   double* geo;           // sin, cos theta_i; cos, sin lambda_q (the unit normal on the grid)
+  double* mean_w;        // w_i / n: the quadrature weight of row i in the mean of f (single plans)
+  int sms;               // multiprocessors of the plan's device
   double chop;           // relative coefficient threshold of the derivative operators (0: off)
   void* row_scale_t;     // the same in float (SP_FP32) or double-float (SP_FP32_REFINE)
   // the same tables in float (SP_FP32) or double-float (SP_FP32_REFINE)
@@ -340,12 +343,38 @@ namespace {
 
 bool plan_ok(sp_plan_t p) { return p != nullptr && p->magic == kMagic; }
 
+// SP_OK if the current device is the plan's (its tables live there), else SP_ERR_BAD_ARG
+int on_plan_device(sp_plan_t p) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  return dev == p->device ? SP_OK : SP_ERR_BAD_ARG;
+}
+
 int check_arrays(sp_plan_t p, const void* a, const void* b, const void* ws, size_t ws_bytes) {
   if (!plan_ok(p)) return SP_ERR_BAD_PLAN;
   if (!a || !b || !ws) return SP_ERR_NULL;
   if (((uintptr_t)a | (uintptr_t)b | (uintptr_t)ws) & 15) return SP_ERR_MISALIGNED;
   if (ws_bytes < p->ws_bytes) return SP_ERR_WORKSPACE;
-  return SP_OK;
+  return on_plan_device(p);
+}
+
+// the mean of f and max |f| by the row-weight quadrature: partial sums in the
+// first nparts 16-byte slots of the workspace (nparts + 1 slots fit in any
+// plan's workspace), the result to `mean` / `absmax` (device; either may be NULL)
+int mean_parts(sp_plan_t p) {
+  size_t slots = p->ws_bytes / sizeof(double2);
+  int n = std::min(p->nt, 2 * std::max(p->sms, 1));
+  if (slots < 2) return 0;
+  if ((size_t)n > slots - 1) n = (int)(slots - 1);
+  return n;
+}
+int enqueue_mean(sp_plan_t p, const double* f, void* ws, double* mean, double* absmax, cudaStream_t st) {
+  const int nparts = mean_parts(p);
+  if (nparts < 1) return SP_ERR_WORKSPACE;
+  sp::launch_mean(st, f, p->nt, p->nl, p->mean_w, static_cast<double2*>(ws), nparts, mean, absmax);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SP_OK : cuda_fail(e, "mean launch");
 }
 
 // true if the radix plan needs the general (large odd prime) pass set
@@ -833,6 +862,10 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
     delete p;
     return cuda_fail(cudaGetLastError(), "cudaGetDevice");
   }
+  if (cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+    delete p;
+    return cuda_fail(cudaGetLastError(), "cudaDeviceGetAttribute");
+  }
 
   // host tables
   const size_t cd_sz = sizeof(cpx<double>);
@@ -883,6 +916,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   size_t o_plain = take(p->nt * sizeof(double));
   size_t o_sin2 = take(p->nt * sizeof(double));
   size_t o_geo = take((size_t)(2 * p->nt + 2 * p->nl) * sizeof(double));
+  size_t o_mean_w = take(p->nt * sizeof(double));
   size_t o_perm_row = take(p->L * sizeof(int)), o_perm_col = take(p->N * sizeof(int));
   size_t o_t_tw_row = take(t_tw_row.size()), o_t_tw_col = take(t_tw_col.size());
   size_t o_t_post_row = take(t_post_row.size()), o_t_post_col = take(t_post_col.size());
@@ -917,6 +951,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   p->row_plain = reinterpret_cast<double*>(base + o_plain);
   p->sin2 = reinterpret_cast<double*>(base + o_sin2);
   p->geo = reinterpret_cast<double*>(base + o_geo);
+  p->mean_w = reinterpret_cast<double*>(base + o_mean_w);
   p->perm_row = reinterpret_cast<int*>(base + o_perm_row);
   p->perm_col = reinterpret_cast<int*>(base + o_perm_col);
   p->tw_row_t = base + o_t_tw_row;
@@ -971,6 +1006,31 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
       geo[2 * p->nt + p->nl + q] = im;
     }
     up(p->geo, geo.data(), geo.size() * sizeof(double), "copy geo");
+    // row weights of the mean of f: the w-quadrature of eq. integrationCoeffs on
+    // the colatitude coefficients of the lambda mean (the theta-Nyquist mode
+    // dropped), divided by 4 pi and written on the samples:
+    //   mean = sum_i w_i fbar_i,  w_i = (2/m) (1 + 2 sum_{j even, 2 <= j <= N-1} cos(j theta_i) / (1 - j^2)),
+    // with j theta_i = 2 pi j (2i + 1) / (4N) reduced exactly through a table of cos(2 pi r / 4N)
+    const long M4 = 4L * p->N;
+    std::vector<double> c4(M4);
+    for (long r = 0; r < M4; ++r) {
+      double re, im;
+      unit_root(r, M4, &re, &im);
+      c4[r] = re;
+    }
+    std::vector<double> mw(p->nt);
+    for (int i = 0; i < p->nt; ++i) {
+      const long step = (2L * (2 * i + 1)) % M4;
+      long r = 0;
+      double sum = 0.0;
+      for (int j = 2; j <= p->N - 1; j += 2) {
+        r += step;
+        if (r >= M4) r -= M4;
+        sum += c4[r] / (1.0 - (double)j * (double)j);
+      }
+      mw[i] = (1.0 + 2.0 * sum) / (double)p->N / (double)n_lambda;
+    }
+    up(p->mean_w, mw.data(), p->nt * sizeof(double), "copy mean_w");
   }
   up(p->perm_row, perm_row.data(), p->L * sizeof(int), "copy perm_row");
   up(p->perm_col, perm_col.data(), p->N * sizeof(int), "copy perm_col");
@@ -1620,10 +1680,17 @@ int sphere_poisson_workspace_size(sp_plan_t plan, size_t* workspace_bytes) {
 }
 
 int sphere_poisson_solve(sp_plan_t plan, const double* f, double* u, void* workspace,
-                         size_t workspace_bytes, void* stream) {
+                         size_t workspace_bytes, void* stream, double* f_mean_out) {
   int rc = check_arrays(plan, f, u, workspace, workspace_bytes);
   if (rc != SP_OK) return rc;
-  return launch_solve<false>(plan, f, u, workspace, static_cast<cudaStream_t>(stream));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (f_mean_out) {
+    if (plan->batched) return SP_ERR_UNSUPPORTED;
+    if ((uintptr_t)f_mean_out & 7) return SP_ERR_MISALIGNED;
+    rc = enqueue_mean(plan, f, workspace, f_mean_out, nullptr, st);  // before the solve reuses the workspace
+    if (rc != SP_OK) return rc;
+  }
+  return launch_solve<false>(plan, f, u, workspace, st);
 }
 
 int sphere_poisson_solve_adjoint(sp_plan_t plan, const double* ubar, double* fbar, void* workspace,
@@ -1643,13 +1710,16 @@ int sphere_poisson_host_buffer_size(sp_plan_t plan, size_t* device_buffer_bytes)
 }
 
 int sphere_poisson_solve_host(sp_plan_t plan, const double* f_host, double* u_host, void* device_buffer,
-                              size_t device_buffer_bytes, void* stream) {
+                              size_t device_buffer_bytes, void* stream, double* f_mean_out) {
   if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
   if (!f_host || !u_host || !device_buffer) return SP_ERR_NULL;
   if ((uintptr_t)device_buffer & 15) return SP_ERR_MISALIGNED;
+  if (f_mean_out && plan->batched) return SP_ERR_UNSUPPORTED;
   size_t need = 0;
   sphere_poisson_host_buffer_size(plan, &need);
   if (device_buffer_bytes < need) return SP_ERR_WORKSPACE;
+  int drc = on_plan_device(plan);
+  if (drc != SP_OK) return drc;
   const size_t bytes = (plan->batched ? plan->total : (size_t)plan->nt * plan->nl) * sizeof(double);
   const size_t grid = (bytes + 255) & ~(size_t)255;
   char* base = static_cast<char*>(device_buffer);
@@ -1657,13 +1727,30 @@ int sphere_poisson_solve_host(sp_plan_t plan, const double* f_host, double* u_ho
   double* d_u = reinterpret_cast<double*>(base + grid);
   void* ws = base + 2 * grid;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // after the solve, the workspace is free: the mean of f and max |f| go to its
+  // slot mean_parts(plan), and the call returns the warning when the mean is not
+  // zero to rounding
+  double mm[2] = {0.0, 0.0};
+  auto mean_check = [&]() -> int {
+    const int nparts = mean_parts(plan);
+    double2* res = static_cast<double2*>(ws) + nparts;
+    int rc = enqueue_mean(plan, d_f, ws, &res->x, &res->y, st);
+    if (rc != SP_OK) return rc;
+    SP_CUDA(cudaMemcpyAsync(mm, res, sizeof mm, cudaMemcpyDeviceToHost, st));
+    return SP_OK;
+  };
+  auto mean_status = [&]() -> int {
+    *f_mean_out = mm[0];
+    return std::fabs(mm[0]) > kMeanWarnFactor * mm[1] ? SP_WARN_NONZERO_MEAN : SP_OK;
+  };
   if (plan->batched || plan->nt < 2 * kHostChunks) {
     SP_CUDA(cudaMemcpyAsync(d_f, f_host, bytes, cudaMemcpyHostToDevice, st));
     int rc = launch_solve<false>(plan, d_f, d_u, ws, st);
     if (rc != SP_OK) return rc;
     SP_CUDA(cudaMemcpyAsync(u_host, d_u, bytes, cudaMemcpyDeviceToHost, st));
+    if (f_mean_out && (rc = mean_check()) != SP_OK) return rc;
     SP_CUDA(cudaStreamSynchronize(st));
-    return SP_OK;
+    return f_mean_out ? mean_status() : SP_OK;
   }
   // copies overlapped with the longitude transforms, in kHostChunks row chunks
   if (!plan->copy) {
@@ -1681,9 +1768,13 @@ int sphere_poisson_solve_host(sp_plan_t plan, const double* f_host, double* u_ho
   else if (plan->precision == SP_FP32) enqueue_fp32(plan, false, d_f, d_u, ws, st, &ov);
   else enqueue_refine(plan, d_f, d_u, ws, st, &ov);
   SP_CUDA(cudaGetLastError());
+  if (f_mean_out) {
+    int rc = mean_check();
+    if (rc != SP_OK) return rc;
+  }
   SP_CUDA(cudaStreamSynchronize(plan->copy));
   SP_CUDA(cudaStreamSynchronize(st));
-  return SP_OK;
+  return f_mean_out ? mean_status() : SP_OK;
 }
 
 }  // extern "C"
@@ -1811,7 +1902,7 @@ int check_derivative_call(sp_plan_t plan, int spectra, std::initializer_list<con
   for (const void* q : ptrs) bits |= (uintptr_t)q;
   if (bits & 15) return SP_ERR_MISALIGNED;
   if (workspace_bytes < derivative_workspace(plan, spectra)) return SP_ERR_WORKSPACE;
-  return SP_OK;
+  return on_plan_device(plan);
 }
 struct DerivSpace {
   cpx<double>* X;   // coefficients of the current input
@@ -2007,6 +2098,7 @@ int sphere_poisson_lowrank_ge(sp_plan_t plan, const double* f, int max_terms, do
   size_t need = 0;
   sphere_poisson_lowrank_workspace_size(plan, max_terms, &need);
   if (workspace_bytes < need) return SP_ERR_WORKSPACE;
+  if (int drc = on_plan_device(plan)) return drc;
   const int nt = plan->nt, n = plan->nl, H = n / 2, m = 2 * nt;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char* base = static_cast<char*>(workspace);
@@ -2067,6 +2159,7 @@ int sphere_poisson_solve_lowrank(sp_plan_t plan, int terms, const double* cols, 
   size_t need = 0;
   sphere_poisson_lowrank_workspace_size(plan, terms, &need);
   if (workspace_bytes < need) return SP_ERR_WORKSPACE;
+  if (int drc = on_plan_device(plan)) return drc;
   sp_plan_t p = plan;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char* base = static_cast<char*>(workspace);
@@ -2167,6 +2260,8 @@ int sphere_poisson_destroy(sp_plan_t plan) {
 const char* sphere_poisson_status_string(int status) {
   switch (status) {
     case SP_OK: return "success";
+    case SP_WARN_NONZERO_MEAN: return "warning: f does not have zero mean over the sphere (the paper's assumption); "
+                                      "the solve dropped the k = 0, j = 0 equation";
     case SP_ERR_BAD_SIZE: return "bad grid size: need n_theta >= 1, even n_lambda >= 2, lengths <= 12288 "
                                  "with prime factors <= 31";
     case SP_ERR_NULL: return "a required pointer is NULL";

@@ -27,8 +27,8 @@ int main(void) {
   if (plan != (sp_plan_t)0) bad |= 8;
   if (sphere_poisson_plan(&plan, 8, 16, 99, 0, 0u, &ws) != SP_ERR_UNSUPPORTED) bad |= 16;
   if (sphere_poisson_plan((sp_plan_t*)0, 8, 16, SP_FP64, 0, 0u, &ws) != SP_ERR_NULL) bad |= 32;
-  if (sphere_poisson_solve((sp_plan_t)0, (const double*)0, (double*)0, (void*)0, 0, (void*)0)
-      != SP_ERR_BAD_PLAN) bad |= 64;
+  if (sphere_poisson_solve((sp_plan_t)0, (const double*)0, (double*)0, (void*)0, 0, (void*)0,
+                           (double*)0) != SP_ERR_BAD_PLAN) bad |= 64;
   if (strlen(sphere_poisson_status_string(SP_ERR_BAD_SIZE)) < 5) bad |= 128;
   printf("%s\n", sphere_poisson_status_string(SP_ERR_BAD_SIZE));
   return bad;

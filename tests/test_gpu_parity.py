@@ -157,11 +157,11 @@ def test_error_paths(sp):
     # misaligned output pointer and a short workspace are refused without launching
     big = torch.zeros(16 * 32 + 1, dtype=torch.float64, device="cuda")
     assert lib.sphere_poisson_solve(plan._h, f.data_ptr(), big.data_ptr() + 8, ws.data_ptr(),
-                                    plan.workspace_bytes, None) == _lib.SP_ERR_MISALIGNED
+                                    plan.workspace_bytes, None, None) == _lib.SP_ERR_MISALIGNED
     assert lib.sphere_poisson_solve(plan._h, f.data_ptr(), u.data_ptr(), ws.data_ptr(),
-                                    plan.workspace_bytes - 1, None) == _lib.SP_ERR_WORKSPACE
+                                    plan.workspace_bytes - 1, None, None) == _lib.SP_ERR_WORKSPACE
     assert lib.sphere_poisson_solve(plan._h, 0, u.data_ptr(), ws.data_ptr(),
-                                    plan.workspace_bytes, None) == _lib.SP_ERR_NULL
+                                    plan.workspace_bytes, None, None) == _lib.SP_ERR_NULL
     with pytest.raises(TypeError):
         plan.solve(f.float())
 

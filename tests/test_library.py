@@ -78,9 +78,9 @@ def test_calls_reject_null_plan(lib):
 
     buf = ctypes.create_string_buffer(64)
     p = ctypes.addressof(buf)
-    assert lib.sphere_poisson_solve(None, p, p, p, 64, None) == _lib.SP_ERR_BAD_PLAN
+    assert lib.sphere_poisson_solve(None, p, p, p, 64, None, None) == _lib.SP_ERR_BAD_PLAN
     assert lib.sphere_poisson_solve_adjoint(None, p, p, p, 64, None) == _lib.SP_ERR_BAD_PLAN
-    assert lib.sphere_poisson_solve_host(None, p, p, p, 64, None) == _lib.SP_ERR_BAD_PLAN
+    assert lib.sphere_poisson_solve_host(None, p, p, p, 64, None, None) == _lib.SP_ERR_BAD_PLAN
     n = ctypes.c_size_t()
     assert lib.sphere_poisson_workspace_size(None, ctypes.byref(n)) == _lib.SP_ERR_BAD_PLAN
     assert lib.sphere_poisson_destroy(None) == _lib.SP_OK
@@ -104,3 +104,18 @@ def test_batched_plan_argument_checks(lib):
     assert plan(ctypes.byref(h), 2, nts, nls, _lib.SP_FP64, 0, 4, None) == _lib.SP_ERR_BAD_ARG
     assert plan(ctypes.byref(h), 2, nts, bad, _lib.SP_FP32_REFINE, 1, 0, None) == _lib.SP_ERR_BAD_SIZE
     assert h.value is None
+
+
+def test_grid_on_another_device_is_refused():
+    # the binding refuses a tensor that is not on the plan's device before any
+    # library call (the plan's tables and kernels live on that device); the
+    # library itself returns SP_ERR_BAD_ARG when the current device differs
+    import torch
+
+    from paper_1510_08094_gb300 import _check_grid
+
+    t = torch.zeros(2, 4, dtype=torch.float64)
+    with pytest.raises(ValueError, match="the plan is on cuda:0"):
+        _check_grid(t, (2, 4), "f", torch.device("cuda", 0))
+    with pytest.raises(ValueError, match="must be a CUDA tensor"):
+        _check_grid(t, (2, 4), "f")
