@@ -183,6 +183,23 @@ def whole_job_value(dof_per_rank: int, world: int, ms_per_step: float) -> float:
     return dof_per_rank * world / (ms_per_step * 1e-3)
 
 
+def shard_lpt(sizes, world: int):
+    """Split independent problems of the given (n_theta, n_lambda) sizes over
+    `world` ranks by the longest-processing-time rule: largest problem first
+    (ties by index), each to the rank with the least work so far (ties to the
+    lowest rank), work = n_theta * n_lambda.  Returns one sorted index list per
+    rank.  Deterministic, so every rank computes the same split without any
+    exchange."""
+    order = sorted(range(len(sizes)), key=lambda b: (-sizes[b][0] * sizes[b][1], b))
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for b in order:
+        r = min(range(world), key=lambda i: (load[i], i))
+        parts[r].append(b)
+        load[r] += sizes[b][0] * sizes[b][1]
+    return [sorted(p) for p in parts]
+
+
 def algorithmic_flops(n_theta: int, n_lambda: int) -> dict:
     """Conventional FFT flop counts per stage launch: a real FFT of length n costs
     2.5 n log2 n, the folded colatitude transform of one complex column of length
@@ -367,9 +384,11 @@ def run_ours(args):
         out["forms"] = measure_forms(sp, f, u_exact, u, N, n, dev, ms_step, args)
     if not args.no_batched and args.precision == "fp64":
         del f_host, u_host, dbuf
-        out["batched"] = measure_batched(sp, dev, args)
+        out["batched"] = measure_batched(sp, dev, args, rank, world)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(f.cpu().numpy(), budget_s=args.cpu_budget)
+    if rank == 0 and not args.no_cpu_fast:
+        out["cpu_fft_thomas"] = cpu_fft_thomas(f.cpu().numpy(), u.cpu().numpy())
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -762,11 +781,14 @@ def measure_mixed_sizes(sp, dev, args):
     return out
 
 
-def measure_batched(sp, dev, args):
+def measure_batched(sp, dev, args, rank: int = 0, world: int = 1):
     """4096 spheres of uneven resolution (n_theta = 16 s, s uniform in 2..32,
     n_lambda = 2 n_theta, SH series l <= n_theta/2) in one persistent launch
     with autotuned tiles, against the same problems solved one by one with
-    single-problem FP64 plans; then the same batch in FP32 + refinement."""
+    single-problem FP64 plans; then the same batch in FP32 + refinement.
+    With several ranks the problems are split by shard_lpt (no collective on the
+    data path: each rank solves its shard in its own launch); the batch's time
+    is the slowest rank's and the value counts every rank's problems."""
     import tempfile
 
     import torch
@@ -777,6 +799,13 @@ def measure_batched(sp, dev, args):
     t0 = time.perf_counter()
     sizes, fs, us = sh.batched_workload(args.batch_count, device=dev)
     t_gen = time.perf_counter() - t0
+    total_dof = sum(a * b for a, b in sizes)
+    total_problems = len(sizes)
+    if world > 1:
+        mine = shard_lpt(sizes, world)[rank]
+        sizes = [sizes[b] for b in mine]
+        fs = [fs[b] for b in mine]
+        us = [us[b] for b in mine]
     t0 = time.perf_counter()
     plan = sp.BatchedPlan(sizes, autotune=True, device=dev)
     t_plan = time.perf_counter() - t0
@@ -790,17 +819,22 @@ def measure_batched(sp, dev, args):
     reps = max(3, min(args.steps, 10))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
     e0.record()
     for _ in range(reps):
         plan.solve(f, u, ws)
     e1.record()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
+    ms = max_over_ranks(e0.elapsed_time(e1) / reps, world, dev)
     # error per problem against the closed form, worst case
     worst = 0.0
     for b in range(len(sizes)):
         a, c = plan.offsets[b], plan.offsets[b + 1]
         worst = max(worst, float((u[a:c] - ue[a:c]).abs().max() / ue[a:c].abs().max()))
+    worst = max_over_ranks(worst, world, dev)
     # plain FP64: one single-problem plan per size, problems solved one by one
     singles = {sz: sp.Plan(sz[0], sz[1], device=dev, autotune=not args.no_autotune) for sz in set(sizes)}
     outs = [torch.empty(sz, dtype=torch.float64, device=dev) for sz in sizes]
@@ -814,13 +848,17 @@ def measure_batched(sp, dev, args):
     e1.record()
     torch.cuda.synchronize()
     ms_plain = e0.elapsed_time(e1)
-    dof = plan.offsets[-1]
+    dof = total_dof
+    ms_plain = max_over_ranks(ms_plain, world, dev)
     del outs, views, singles
-    out = {"value": dof / (ms * 1e-3), "unit": "DOF/s", "ms_per_batch": ms, "problems": len(sizes),
+    out = {"value": dof / (ms * 1e-3), "unit": "DOF/s", "ms_per_batch": ms, "problems": total_problems,
            "dof_per_batch": dof, "distinct_sizes": len(set(sizes)), "gpu_launches_per_batch": plan.launches(),
            "plain_fp64_loop_ms": ms_plain, "speedup_vs_plain_fp64_loop": ms_plain / ms,
            "max_rel_err_vs_closed_form": worst, "autotuned": True, "plan_seconds": t_plan,
-           "input_generation_seconds": t_gen}
+           "input_generation_seconds": t_gen,
+           "sharding": (f"{world} ranks, longest-processing-time split by n_theta*n_lambda, no collective "
+                        f"on the data path; this rank {len(sizes)} problems, {plan.offsets[-1]} DOF"
+                        if world > 1 else "single GPU")}
 
     # the same batch in FP32 + refinement (one sweep), one persistent launch
     sweeps = 1
@@ -833,17 +871,21 @@ def measure_batched(sp, dev, args):
     for _ in range(2):
         rplan.solve(f, ur, rws)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     e0.record()
     for _ in range(reps):
         rplan.solve(f, ur, rws)
     e1.record()
     torch.cuda.synchronize()
-    ms_r = e0.elapsed_time(e1) / reps
+    ms_r = max_over_ranks(e0.elapsed_time(e1) / reps, world, dev)
     worst_r = worst_r64 = 0.0
     for b in range(len(sizes)):
         a, c = plan.offsets[b], plan.offsets[b + 1]
         worst_r = max(worst_r, float((ur[a:c] - ue[a:c]).abs().max() / ue[a:c].abs().max()))
         worst_r64 = max(worst_r64, float((ur[a:c] - u[a:c]).abs().max() / u[a:c].abs().max()))
+    worst_r = max_over_ranks(worst_r, world, dev)
+    worst_r64 = max_over_ranks(worst_r64, world, dev)
     out["fp32_refine"] = {"value": dof / (ms_r * 1e-3), "unit": "DOF/s", "ms_per_batch": ms_r,
                           "refine_sweeps": sweeps, "speedup_vs_batched_fp64": ms / ms_r,
                           "max_rel_err_vs_batched_fp64": worst_r64, "max_rel_err_vs_closed_form": worst_r,
@@ -902,6 +944,33 @@ def cpu_baseline(f_np, budget_s: float = 20.0, ks=None) -> dict:
                       f"{nt}x{nl} input, one call each ({t:.1f} s; a first call building the cached "
                       f"colatitude phase matrix took {t_warm:.1f} s and is not counted), "
                       f"scaled by {nl}/{len(used)}"}
+
+
+def cpu_fft_thomas(f_np, u_gpu) -> dict:
+    """A full CPU solve of the same input by the paper's algorithm as a plain
+    CPU program (baseline/fft_thomas.py: scipy.fft transforms, numpy Thomas
+    eliminations), timed once on one core and once with the FFTs on every host
+    core: measured whole solves, not extrapolated."""
+    from baseline import fft_thomas
+
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    nt, nl = f_np.shape
+    times = {}
+    u = None
+    for workers in (1, cores):
+        t0 = time.perf_counter()
+        u = fft_thomas.solve(f_np, workers=workers)
+        times[workers] = time.perf_counter() - t0
+    diff = float(abs(u - u_gpu).max() / abs(u_gpu).max())
+    return {"kind": "fft+thomas", "unit": "DOF/s", "dof_per_solve": nt * nl,
+            "value_1_core": nt * nl / times[1], "seconds_1_core": times[1],
+            "value_all_cores": nt * nl / times[cores], "seconds_all_cores": times[cores], "cores": cores,
+            "sample": f"one full {nt}x{nl} solve per core count (scipy.fft with workers=1 and "
+                      f"workers={cores}; the eliminations run on one thread in both)",
+            "max_rel_diff_vs_gpu_solution": diff}
 
 
 def run_reference(args):
@@ -966,6 +1035,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-fast", action="store_true", help="skip the full CPU FFT + Thomas solves")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--forms", default="",
                     help="comma-separated subset of the forms to measure: " + ",".join(FORM_GROUPS))

@@ -204,15 +204,21 @@ def synthesize_many(coeff_list, n_theta: int, n_lambda: int, device="cpu") -> to
     return f.contiguous()
 
 
+def batched_sizes(count: int = 4096, seed: int = 1510080944):
+    """The uneven-resolution batch's sizes (n_theta = 16 s, s uniform in 2..32,
+    n_lambda = 2 n_theta) and per-problem seeds, from one PCG64 stream."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    svals = rng.integers(2, 33, size=count)
+    seeds = rng.integers(0, 2**62, size=count)
+    return [(16 * int(v), 32 * int(v)) for v in svals], seeds
+
+
 def batched_workload(count: int = 4096, seed: int = 1510080944, device="cpu"):
     """The uneven-resolution batch: n_theta = 16 s with s uniform in 2..32,
     n_lambda = 2 n_theta, a random series l <= n_theta/2 with N(0,1)/(1+l)^2
     coefficients per problem (seeds drawn from one PCG64 stream).  Returns
     (sizes, f list, exact-solution list)."""
-    rng = np.random.Generator(np.random.PCG64(seed))
-    svals = rng.integers(2, 33, size=count)
-    seeds = rng.integers(0, 2**62, size=count)
-    sizes = [(16 * int(v), 32 * int(v)) for v in svals]
+    sizes, seeds = batched_sizes(count, seed)
     fs = [None] * count
     us = [None] * count
     by_size = {}
