@@ -69,6 +69,37 @@ def test_ge_matches_oracle(sp, nt, nl):
     assert np.abs(approx - O.lowrank_values(terms)).max() < 1e-12 * np.abs(ft).max()
 
 
+@pytest.mark.parametrize("nt,nl", [(24, 48), (75, 150)])
+def test_every_ge_term_matches_oracle_on_rough_input(sp, nt, nl):
+    # rough N(0,1) samples: the largest sigma_1 of each step is separated from
+    # the next by far more than rounding, so the pivot sequence is unique and
+    # every term (column pair, pseudoinverse, row pair, hence pivot position)
+    # must be the oracle's for the first steps
+    K = 8
+    f = np.random.default_rng(nt).standard_normal((nt, nl))
+    ft = O.dfs_double(f)
+    terms, _ = O.bmc_ge(ft, max_terms=K)
+    cols, piv, rows = sp.Plan(nt, nl).lowrank_ge(torch.tensor(f, device="cuda"), max_terms=K)
+    assert len(terms) == K and cols.shape[0] == K
+    cols, piv, rows = cols.cpu().numpy(), piv.cpu().numpy(), rows.cpu().numpy()
+    scale = np.abs(ft).max()
+    H = nl // 2
+    resid = ft.copy()
+    for t, (c, P, r, (p, q)) in enumerate(terms):
+        # the GPU's term [c(theta) c(-theta)] P [r(lambda); r(lambda + pi)] against the
+        # oracle's cols @ P @ rows: c = e(., lambda* - pi), c(-theta) = e(., lambda*),
+        # r = e(theta*, .), r(. + pi) = e(-theta*, .)
+        assert np.abs(cols[t] - c[:, 0]).max() < 1e-12 * scale, t
+        assert np.abs(cols[t][::-1] - c[:, 1]).max() < 1e-12 * scale, t
+        assert np.abs(rows[t] - r[0]).max() < 1e-12 * scale, t
+        assert np.abs(np.roll(rows[t], -H) - r[1]).max() < 1e-12 * scale, t
+        assert np.abs(piv[t] - P[0]).max() < 1e-12 * np.abs(P).max(), t
+        # the pivot position (p, q): the residual's column at lambda* - pi and row at theta*
+        assert np.abs(cols[t] - resid[:, q - H]).max() < 1e-12 * scale, t
+        assert np.abs(rows[t] - resid[p]).max() < 1e-12 * scale, t
+        resid = resid - c @ P @ r
+
+
 def test_exact_recovery_at_svd_rank(sp):
     nt, nl = 32, 64
     f = sh.synthesize(sh.random_sh_coeffs(10, 11), nt, nl).numpy()

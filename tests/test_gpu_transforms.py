@@ -50,6 +50,53 @@ def test_sample_inverts_coeffs2_on_band_limited_input(sp):
     assert float((back - f).abs().max() / f.abs().max()) < 1e-13
 
 
+def _random_sphere_coefficients(nt, nl, rng):
+    """Random coefficients in the coeffs2 layout [n_theta, Kp] of a real BMC
+    function: complex N(0,1) entries, except X_{0,k} = 0 for odd k (the BMC
+    symmetry X_{-j,k} = (-1)^k X_{j,k} at j = 0), a real k = 0 column and a
+    k = -n/2 column that is real for even n/2 and imaginary for odd n/2 (the
+    aliased longitude Nyquist mode of a real function)."""
+    L = nl // 2
+    kp = (L + 2) // 2 * 2
+    X = np.zeros((nt, kp), dtype=complex)
+    X[:, : L + 1] = rng.standard_normal((nt, L + 1)) + 1j * rng.standard_normal((nt, L + 1))
+    X[0, 1: L + 1: 2] = 0.0
+    X[:, 0] = X[:, 0].real
+    X[:, L] = X[:, L].real if L % 2 == 0 else 1j * X[:, L].imag
+    if L % 2:
+        X[0, L] = 0.0
+    return X
+
+
+def _full_window(X, nt, nl):
+    """The same coefficients on the oracle's full m x n window [j + m/2, k + n/2]:
+    negative j by X_{-j,k} = (-1)^k X_{j,k}, negative k by X_{j,-k} = (-1)^k conj X_{j,k},
+    the theta-Nyquist row zero."""
+    m, n, N, L = 2 * nt, nl, nt, nl // 2
+    F = np.zeros((m, n), dtype=complex)
+    for k in range(L):
+        sgn = (-1.0) ** k
+        F[N:, L + k] = X[:, k]
+        F[N - np.arange(1, N), L + k] = sgn * X[1:, k]
+        if k:
+            F[:, L - k] = sgn * np.conj(F[:, L + k])
+    F[N:, 0] = X[:, L]                                  # k = -n/2
+    F[N - np.arange(1, N), 0] = (-1.0) ** L * X[1:, L]
+    return F
+
+
+@pytest.mark.parametrize("nt,nl", [(1, 2), (2, 4), (5, 10), (24, 48), (33, 70), (22, 58), (64, 130)])
+def test_sample_matches_oracle_on_arbitrary_coefficients(sp, nt, nl):
+    # not only the inverse of coeffs2: any coefficient array of a real function
+    # on the sphere, against the oracle's inverse 2D expansion
+    X = _random_sphere_coefficients(nt, nl, np.random.default_rng(nt * nl))
+    F = _full_window(X, nt, nl)
+    ref = O.sample(F)[nt:]
+    assert np.abs(ref.imag).max() < 1e-12 * np.abs(ref.real).max()
+    got = sp.Plan(nt, nl).sample(torch.tensor(X, device="cuda")).cpu().numpy()
+    assert np.abs(got - ref.real).max() < 1e-13 * np.abs(ref.real).max() * max(1.0, math.log2(nt * nl))
+
+
 def test_sum2_worked_example(sp):
     vals = {}
     for line in open(GOLDEN).read().splitlines():
