@@ -210,7 +210,7 @@ def algorithmic_flops(n_theta: int, n_lambda: int) -> dict:
     cols = K * 5.0 * N * math.log2(max(N, 2))
     solve = 10.0 * N * K
     return {"rows_forward": rows, "theta_forward": cols, "solve": solve,
-            "theta_inverse": cols, "rows_inverse": rows}
+            "theta_inverse": cols, "rows_inverse": rows, "theta_fused": 2 * cols + solve}
 
 
 def algorithmic_bytes(n_theta: int, n_lambda: int, spec_elem: int = 16, table_elem: int = 8) -> dict:
@@ -221,8 +221,12 @@ def algorithmic_bytes(n_theta: int, n_lambda: int, spec_elem: int = 16, table_el
     Kp = (n // 2 + 2) // 2 * 2
     grid = 8.0 * N * n
     spec = float(spec_elem) * N * Kp
+    K = n // 2 + 1
     return {"rows_forward": grid + spec, "theta_forward": 2 * spec, "solve": 2 * spec + 3.0 * table_elem * N * Kp,
-            "theta_inverse": 2 * spec, "rows_inverse": spec + grid}
+            "theta_inverse": 2 * spec, "rows_inverse": spec + grid,
+            # the fused colatitude stage of the FP32 form: the spectrum in and out once,
+            # its per-column pivot table (K columns) once
+            "theta_fused": 2 * spec + 1.0 * table_elem * N * K}
 
 
 def run_ours(args):

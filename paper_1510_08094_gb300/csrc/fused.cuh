@@ -1,0 +1,338 @@
+// Fused colatitude stage of the single-precision form (SP_FP32, forward solve).
+//
+// Per tile of `cols` consecutive wavenumber columns k, one CTA runs
+//   1. the forward colatitude transform of theta_forward (the BMC fold's
+//      DCT-II / DST-II, Section 4, eq. 2DFourierExpansion),
+//   2. the per-k systems of eq. linearSystems on their two parity chains and
+//      the j = 0 closure (as k_solve; the k = 0 column of this form is carried
+//      in FP64 on the side path and replaces column 0 in rows_inverse),
+//   3. the inverse colatitude transform of theta_inverse,
+// with the tile's coefficients kept in shared memory between the steps: the
+// spectrum crosses HBM once each way instead of three times, and the
+// eliminations' factor tables are read once, column by column.
+//
+// The eliminations run as parallel chunked scans.  With the top-down
+// factorisation of a chain (rows t = 0..M-1, j = j0 + 2t, pivots u_t; 1/u from
+// k_factor_cols, stored per column so that one column's entries are
+// contiguous; l_t = a_j/u_{t-1} and c_j/u_t formed from it and the closed-form
+// bands a_j = (j-1)(j-2)/4, c_j = (j+1)(j+2)/4), the solve is two affine
+// first-order recurrences,
+//   y_t = d_t - l_t y_{t-1}           (t increasing, y_{-1} = 0),
+//   x_t = (1/u_t) y_t - (c_t/u_t) x_{t+1}   (t decreasing, x_M = 0),
+// each of the form z = alpha z_prev + beta.  P threads per chain take
+// contiguous chunks of C rows: (1) each folds its chunk from a zero incoming
+// value into (product of alpha, value at the chunk's end), (2) one warp per
+// chain combines the P chunk results by a shuffle scan of the composed affine
+// maps into every chunk's incoming value, (3) each thread re-runs its chunk
+// from its incoming value and writes the result.  The products of alpha stay bounded (|l_t|, |c_t/u_t| < 1 on
+// these diagonally dominant bands), so the scan is as accurate as the
+// sequential sweep up to rounding order.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "kernels.cuh"
+
+namespace sp {
+
+// Plan-time top-down factorisation of every parity chain, stored per column:
+// entry (k, j) at k N + j of fiu holds 1/u_t for the chain row j = j0 + 2t
+// (u_0 = b_j0, u_t = b_j - a_j c_{j-2} / u_{t-1}), in FP64 then rounded.
+// One thread per (k, parity); idx < K the odd chain of k = idx, else the even
+// chain of k = idx - K.  Rows j = 0 are not written.
+template <typename S>
+__global__ void k_factor_cols(S* __restrict__ fiu, int N, int K) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 2 * K) return;
+  const bool even = idx >= K;
+  const int k = even ? idx - K : idx;
+  const double k2 = (double)k * (double)k;
+  const size_t col = (size_t)k * N;
+  double u_prev = 0.0, c_prev = 0.0;
+  for (int j = even ? 2 : 1, t = 0; j < N; j += 2, ++t) {
+    const double jd = (double)j;
+    const double a = chain_a(jd), b = -(jd * jd * 0.5 + k2), c = chain_c(jd);
+    double l = 0.0, uu = b;
+    if (t > 0) {
+      l = a / u_prev;
+      uu = b - l * c_prev;
+    }
+    fiu[col + j] = (S)(1.0 / uu);
+    u_prev = uu;
+    c_prev = c;
+  }
+}
+
+// the bands of a chain row j in the arithmetic T (exact integers before the scaling)
+template <typename T>
+__device__ __forceinline__ T band_a(int j) { return (T)((j - 1) * (j - 2)) * (T)0.25; }
+template <typename T>
+__device__ __forceinline__ T band_c(int j) { return (T)((j + 1) * (j + 2)) * (T)0.25; }
+
+// Scratch of the scans: one (product, value) pair per thread.
+template <typename T>
+struct ScanSlot {
+  T a;
+  cpx<T> z;
+};
+
+// Shared-memory bytes of the fused kernel for a tile of `cols` columns of
+// length N with `threads` threads: FFT buffer, coefficient buffer, scan slots.
+template <typename T>
+__host__ __device__ inline size_t fused_smem_bytes(int N, int cols, int threads) {
+  const size_t buf = ((size_t)cols * N * sizeof(cpx<T>) + 15) & ~(size_t)15;
+  return 2 * buf + (size_t)threads * sizeof(ScanSlot<T>);
+}
+
+// Phase 2 of one chain's scan, run by one warp: slots slot[q * stride] for the
+// chunks q = 0..P-1 hold (product of alpha, value at the chunk's end from a zero
+// incoming value); on return each holds the chunk's incoming value instead
+// (chunks taken in increasing q, or in decreasing q when `down`).  Each lane
+// folds a run of consecutive chunks, the lanes' runs are combined by a
+// shuffle scan of the composed affine maps, and each lane writes its chunks'
+// incoming values.
+template <typename T>
+__device__ __forceinline__ void chain_carry_scan(ScanSlot<T>* slot, int stride, int P, bool down) {
+  const int lane = threadIdx.x & 31;
+  const int Q = (P + 31) / 32;
+  auto at = [&](int i) -> ScanSlot<T>& { return slot[(down ? P - 1 - i : i) * stride]; };
+  // the lane's run i = lane Q .. lane Q + Q - 1 as one map z -> A z + Z
+  T A = (T)1;
+  cpx<T> Z = {(T)0, (T)0};
+  for (int i = lane * Q; i < min(P, lane * Q + Q); ++i) {
+    const ScanSlot<T> v = at(i);
+    Z = {fma(v.a, Z.re, v.z.re), fma(v.a, Z.im, v.z.im)};
+    A = A * v.a;
+  }
+  // inclusive scan over lanes: the maps of lanes 0..lane composed
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const T Ao = __shfl_up_sync(0xffffffffu, A, off);
+    const T Zr = __shfl_up_sync(0xffffffffu, Z.re, off);
+    const T Zi = __shfl_up_sync(0xffffffffu, Z.im, off);
+    if (lane >= off) {
+      Z = {fma(A, Zr, Z.re), fma(A, Zi, Z.im)};
+      A = A * Ao;
+    }
+  }
+  // incoming value of the lane's run: the composed map of the lanes before it, applied to 0
+  cpx<T> carry = {__shfl_up_sync(0xffffffffu, Z.re, 1), __shfl_up_sync(0xffffffffu, Z.im, 1)};
+  if (lane == 0) carry = {(T)0, (T)0};
+  for (int i = lane * Q; i < min(P, lane * Q + Q); ++i) {
+    ScanSlot<T>& v = at(i);
+    const cpx<T> out = {fma(v.a, carry.re, v.z.re), fma(v.a, carry.im, v.z.im)};
+    v.z = carry;
+    carry = out;
+  }
+}
+
+// The eliminations of a tile and its row-0 closure, in place in X ([j][cols],
+// the forward transform's output), by the chunked scans described above.
+// Whole CTA; ends with a barrier.
+template <typename T>
+__device__ __forceinline__ void fused_solve(cpx<T>* __restrict__ X, ScanSlot<T>* __restrict__ slot, int k0,
+                                            int cols, int N, int K, const T* __restrict__ fiu) {
+  // thread -> (chain ch, chunk p); chain ch = column ch >> 1,
+  //    parity ch & 1 (0: odd rows j = 1, 3, ..; 1: even rows j = 2, 4, ..)
+  const int chains = 2 * cols;
+  const int ch = threadIdx.x % chains, p = threadIdx.x / chains;
+  const int P = blockDim.x / chains;
+  const int c = ch >> 1, j0 = (ch & 1) ? 2 : 1;
+  const int k = k0 + c;
+  const int M = (j0 < N) ? (N - 1 - j0) / 2 + 1 : 0;
+  const int C = ((M + P - 1) / P) | 1;        // odd, so that the chunks' rows spread over the banks
+  const int s = min(M, p * C), e = min(M, s + C);
+  const bool live = k < K && p < P;
+  const size_t tcol = (size_t)(live ? k : 0) * N;
+  ScanSlot<T>* mine = slot + threadIdx.x;
+  // forward sweep y_t = d_t - l_t y_{t-1}, phase 1
+  {
+    T A = (T)1;
+    cpx<T> y = {(T)0, (T)0};
+    if (live) {
+#pragma unroll 4
+      for (int t = s; t < e; ++t) {
+        const int j = j0 + 2 * t;
+        const T l = t > 0 ? band_a<T>(j) * __ldg(fiu + tcol + j - 2) : (T)0;
+        const cpx<T> dv = X[j * cols + c];
+        y = {fma(-l, y.re, dv.re), fma(-l, y.im, dv.im)};
+        A = A * (-l);
+      }
+    }
+    mine->a = A;
+    mine->z = y;
+  }
+  __syncthreads();
+  // phase 2: chunk p's incoming value, in its slot (warp w scans chain w)
+  {
+    const int w = threadIdx.x >> 5;
+    if (w < chains && k0 + (w >> 1) < K) chain_carry_scan(slot + w, chains, P, false);
+  }
+  __syncthreads();
+  // phase 3
+  if (live) {
+    cpx<T> y = mine->z;
+    for (int t = s; t < e; ++t) {
+      const int j = j0 + 2 * t;
+      const T l = t > 0 ? band_a<T>(j) * __ldg(fiu + tcol + j - 2) : (T)0;
+      cpx<T>& dv = X[j * cols + c];
+      y = {fma(-l, y.re, dv.re), fma(-l, y.im, dv.im)};
+      dv = y;
+    }
+  }
+  __syncthreads();
+  // backward sweep x_t = iu_t y_t - cu_t x_{t+1} (t decreasing), phase 1
+  {
+    T A = (T)1;
+    cpx<T> x = {(T)0, (T)0};
+    if (live) {
+#pragma unroll 4
+      for (int t = e - 1; t >= s; --t) {
+        const int j = j0 + 2 * t;
+        const T iu = __ldg(fiu + tcol + j), cu = band_c<T>(j) * iu;
+        const cpx<T> yv = X[j * cols + c];
+        x = {fma(iu, yv.re, -cu * x.re), fma(iu, yv.im, -cu * x.im)};
+        A = A * (-cu);
+      }
+    }
+    mine->a = A;
+    mine->z = x;
+  }
+  __syncthreads();
+  {
+    const int w = threadIdx.x >> 5;
+    if (w < chains && k0 + (w >> 1) < K) chain_carry_scan(slot + w, chains, P, true);
+  }
+  __syncthreads();
+  if (live) {
+    cpx<T> x = mine->z;
+    for (int t = e - 1; t >= s; --t) {
+      const int j = j0 + 2 * t;
+      const T iu = __ldg(fiu + tcol + j), cu = band_c<T>(j) * iu;
+      cpx<T>& yv = X[j * cols + c];
+      x = {fma(iu, yv.re, -cu * x.re), fma(iu, yv.im, -cu * x.im)};
+      yv = x;
+    }
+  }
+  __syncthreads();
+  // row 0: k even != 0: X_0 = (X_2 - F_0)/k^2 (row 0 with X_{-2,k} = X_{2,k});
+  // k odd: X_0 = 0; k = 0: left to the FP64 zonal column
+  if (threadIdx.x < cols) {
+    const int kc = k0 + threadIdx.x;
+    if (kc < K && kc != 0) {
+      cpx<T>& x0 = X[threadIdx.x];
+      if (kc & 1) {
+        x0 = {(T)0, (T)0};
+      } else {
+        const T ik2 = (T)(1.0 / ((double)kc * (double)kc));
+        const cpx<T> x2 = N > 2 ? X[2 * cols + threadIdx.x] : cpx<T>{(T)0, (T)0};
+        x0 = {(x2.re - x0.re) * ik2, (x2.im - x0.im) * ik2};
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, bool BIG>
+__global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_fused(
+    cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d, const cpx<T>* __restrict__ tw,
+    const int* __restrict__ perm, const cpx<T>* __restrict__ post_s, const cpx<T>* __restrict__ post,
+    const T* __restrict__ fiu, T inv_n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const size_t buf = ((size_t)cols * N * sizeof(cpx<T>) + 15) & ~(size_t)15;
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);                 // FFT buffer, [c][N] permuted
+  cpx<T>* X = reinterpret_cast<cpx<T>*>(smem_raw + buf);            // coefficients, [j][cols]
+  ScanSlot<T>* slot = reinterpret_cast<ScanSlot<T>*>(smem_raw + 2 * buf);
+  const int k0 = blockIdx.x * cols;
+
+  // 1. forward colatitude transform into X (theta_forward with the tile's
+  //    coefficient buffer as its output array: row stride cols, column k - k0)
+  theta_forward_load<T>(k0, sm, FromGlobal<cpx<T>>{W + k0, (size_t)Kp}, N, K, cols, perm);
+  __syncthreads();
+  theta_forward_finish<T, false, BIG>(k0, sm, X - k0, N, K, cols, cols, d, tw, post_s, 0);
+  __syncthreads();
+
+  // 2. eliminations and the row-0 closure, in X
+  fused_solve<T>(X, slot, k0, cols, N, K, fiu);
+
+  // 3. inverse colatitude transform from X back to W
+  theta_inverse_load<T, false>(k0, sm, FromStaged<cpx<T>>{X, cols}, N, K, cols, perm, post, 0);
+  __syncthreads();
+  theta_inverse_finish<T, false, BIG>(k0, sm, W, N, K, Kp, cols, d, tw, inv_n);
+}
+
+// Cluster form: a cluster of kFuseCluster = 4 CTAs takes four consecutive
+// columns, one per CTA, and the CTAs share the tile's global traffic through
+// distributed shared memory: CTA r loads (and at the end stores) every fourth
+// row of all four columns, 32 contiguous bytes per row, and scatters the
+// values into (gathers them from) the four CTAs' transform buffers.  A column
+// of this layout alone is 8 scattered bytes per row, a quarter of a 32-byte
+// sector; four neighbouring columns fill the sector.  FP32 arithmetic only
+// (one complex value = 8 bytes, four = two 16-byte vectors).
+constexpr int kFuseCluster = 4;
+
+template <bool BIG>
+__global__ void __cluster_dims__(kFuseCluster, 1, 1) __launch_bounds__(BIG ? 256 : 512) k_theta_fused_cl(
+    cpx<float>* __restrict__ W, int N, int K, int Kp, FftDesc d, const cpx<float>* __restrict__ tw,
+    const int* __restrict__ perm, const cpx<float>* __restrict__ post_s, const cpx<float>* __restrict__ post,
+    const float* __restrict__ fiu) {
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int r = (int)cluster.block_rank();
+  const int kc0 = (int)(blockIdx.x / kFuseCluster) * kFuseCluster;   // the cluster's first column
+  const int k = kc0 + r;                                              // this CTA's column
+  const size_t buf = ((size_t)N * sizeof(cpx<float>) + 15) & ~(size_t)15;
+  cpx<float>* sm = reinterpret_cast<cpx<float>*>(smem_raw);          // this column's transform buffer
+  cpx<float>* X = reinterpret_cast<cpx<float>*>(smem_raw + buf);     // its coefficients
+  ScanSlot<float>* slot = reinterpret_cast<ScanSlot<float>*>(smem_raw + 2 * buf);
+  cpx<float>* peer[kFuseCluster];
+#pragma unroll
+  for (int q = 0; q < kFuseCluster; ++q) peer[q] = cluster.map_shared_rank(sm, q);
+  // the two 16-byte halves of a row's four columns exist when their first column is
+  // below Kp (Kp is even and kc0 a multiple of 4, so the second column is too)
+  const bool half1 = kc0 + 2 < Kp;
+
+  // 1. load: rows i = r, r + 4, ..; the Makhoul reordering with (-1)^i on odd k and
+  //    the digit-reversed position as in theta_forward_load
+  for (int i = r + kFuseCluster * (int)threadIdx.x; i < N; i += kFuseCluster * (int)blockDim.x) {
+    const float4* src = reinterpret_cast<const float4*>(W + (size_t)i * Kp + kc0);
+    const float4 a = src[0];
+    const float4 b = half1 ? src[1] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const cpx<float> v[kFuseCluster] = {{a.x, a.y}, {a.z, a.w}, {b.x, b.y}, {b.z, b.w}};
+    const int pos = __ldg(perm + makhoul_pos(i, N));
+#pragma unroll
+    for (int q = 0; q < kFuseCluster; ++q) {
+      const int kq = kc0 + q;
+      peer[q][pos] = kq < K ? neg_if(v[q], (kq & 1) && (i & 1)) : cpx<float>{0.f, 0.f};
+    }
+  }
+  cluster.sync();
+
+  // 2. this column: forward transform into X, eliminations, inverse transform in sm
+  theta_forward_finish<float, false, BIG>(k, sm, X - k, N, K, 1, 1, d, tw, post_s, 0);
+  __syncthreads();
+  fused_solve<float>(X, slot, k, 1, N, K, fiu);
+  theta_inverse_load<float, false>(k, sm, FromStaged<cpx<float>>{X, 1}, N, K, 1, perm, post, 0);
+  __syncthreads();
+  fft_run<+1, BIG>(sm, 1, d, tw);
+  cluster.sync();
+
+  // 3. store: rows i = r, r + 4, ..; the inverse Makhoul reordering and, on odd
+  //    k, the factor i (-1)^i as in theta_inverse_finish
+  for (int i = r + kFuseCluster * (int)threadIdx.x; i < N; i += kFuseCluster * (int)blockDim.x) {
+    const int pos = makhoul_pos(i, N);
+    cpx<float> v[kFuseCluster];
+#pragma unroll
+    for (int q = 0; q < kFuseCluster; ++q) {
+      const cpx<float> x = peer[q][pos];
+      v[q] = ((kc0 + q) & 1) ? cpx<float>{neg_if(x.im, !(i & 1)), neg_if(x.re, (i & 1) != 0)} : x;
+    }
+    float4* dst = reinterpret_cast<float4*>(W + (size_t)i * Kp + kc0);
+    dst[0] = make_float4(v[0].re, v[0].im, v[1].re, v[1].im);
+    if (half1) dst[1] = make_float4(v[2].re, v[2].im, v[3].re, v[3].im);
+  }
+  cluster.sync();   // no CTA leaves while a peer still reads its buffer
+}
+
+}  // namespace sp

@@ -1,5 +1,6 @@
 // FP32 transform and elimination kernels (the SP_FP32 form).
 #include "launchers.inl"
+#include "fused.cuh"
 
 namespace sp {
 
@@ -51,7 +52,35 @@ cudaError_t allow_transform_smem<float>(int bytes) {
   upd(cudaFuncSetAttribute(k_theta_inverse<float, true, false>, a, bytes));
   upd(cudaFuncSetAttribute(k_theta_inverse<float, true, true>, a, bytes));
   upd(allow_pipe_smem<float>(bytes));
+  upd(cudaFuncSetAttribute(k_theta_fused<float, false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_fused<float, true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_fused_cl<false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_fused_cl<true>, a, bytes));
   return e;
+}
+void launch_theta_fused(bool big, const Launch& l, cpx<float>* W, int N, int K, int Kp, int cols, const FftDesc& d,
+                        const cpx<float>* tw, const int* perm, const cpx<float>* post_s, const cpx<float>* post,
+                        const float* fiu, float inv_n) {
+  if (cols == 0) {   // the cluster form: one column per CTA, clusters of kFuseCluster
+    const dim3 grid(((K + kFuseCluster - 1) / kFuseCluster) * kFuseCluster);
+    if (big)
+      k_theta_fused_cl<true><<<grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, d, tw, perm, post_s, post, fiu);
+    else
+      k_theta_fused_cl<false><<<grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, d, tw, perm, post_s, post, fiu);
+    return;
+  }
+  if (big)
+    k_theta_fused<float, true><<<l.grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, cols, d, tw, perm, post_s,
+                                                                        post, fiu, inv_n);
+  else
+    k_theta_fused<float, false><<<l.grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, cols, d, tw, perm, post_s,
+                                                                         post, fiu, inv_n);
+}
+size_t theta_fused_smem(int N, int cols, int threads) {
+  return fused_smem_bytes<float>(N, cols > 0 ? cols : 1, threads);
+}
+void launch_factor_cols(const Launch& l, float* fiu, int N, int K) {
+  k_factor_cols<float><<<l.grid, l.threads, l.smem, l.stream>>>(fiu, N, K);
 }
 template <>
 void launch_solve<float>(bool adj, const Launch& l, cpx<float>* W, const float* fl, const float* fiu,

@@ -73,6 +73,19 @@ void launch_solve(bool adj, const Launch& l, cpx<S>* W, const S* fl, const S* fi
 template <typename S>
 void launch_factor(const Launch& l, S* fl, S* fiu, S* fcu, int N, int K, int Kp, bool twist);
 
+// the FP32 form's fused colatitude stage (forward transform, parity
+// eliminations, inverse transform per column tile; fused.cuh): tables of
+// launch_factor_cols, one CTA per tile of `cols` columns, or with cols = 0 one
+// column per CTA in clusters of four that share their loads and stores
+// (l.grid is then ignored); theta_fused_smem dynamic bytes
+void launch_theta_fused(bool big, const Launch& l, cpx<float>* W, int N, int K, int Kp, int cols, const FftDesc& d,
+                        const cpx<float>* tw, const int* perm, const cpx<float>* post_s, const cpx<float>* post,
+                        const float* fiu, float inv_n);
+size_t theta_fused_smem(int N, int cols, int threads);
+// pivots 1/u of the top-down factorisation of every parity chain, stored per
+// column ([k][j]), 2K threads
+void launch_factor_cols(const Launch& l, float* fiu, int N, int K);
+
 // FP64 zonal-column eliminations by parallel scan (one CTA)
 void launch_zonal_scan(bool adj, cudaStream_t st, cpx<double>* Z, const double* zl, const double* ziu,
                        const double* zcu, int N);

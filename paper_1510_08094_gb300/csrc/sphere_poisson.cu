@@ -317,6 +317,12 @@ struct sp_plan_s {
   double* z_l;
   double* z_iu;
   double* z_cu;
+  // SP_FP32 forward solve: the fused colatitude stage (fused.cuh) and the
+  // pivots 1/u of its top-down factorisation, per column [k][j]
+  bool fused;
+  int fuse_cols, fuse_threads;
+  size_t fuse_smem;
+  float* fc_iu;
   // the FP32 forms run the zonal column on a second stream
   cudaStream_t side;
   cudaEvent_t ev_fork, ev_join;
@@ -387,6 +393,14 @@ bool needs_big(const FftDesc& d) {
 constexpr int kStages = 5;
 const char* const kStageNames[kStages] = {"rows_forward", "theta_forward", "solve", "theta_inverse",
                                           "rows_inverse"};
+// plans whose forward solve runs the fused colatitude stage: stage 1 times the
+// fused kernel, stages 2 and 3 are empty
+const char* const kFusedStageNames[kStages] = {"rows_forward", "theta_fused", "solve (in theta_fused)",
+                                               "theta_inverse (in theta_fused)", "rows_inverse"};
+
+// the fused stage's tile: `cols` columns per CTA and `threads` threads (false
+// if its shared memory does not fit)
+bool set_fused_tile(sp_plan_t p, int cols, int threads);
 
 // records the boundary event s of the current profiled call, if any
 struct StageMarks {
@@ -628,14 +642,24 @@ void enqueue_fp32(sp_plan_t p, bool adj, const double* in, double* out, void* ws
   enqueue_zonal_fp64(p, adj, Z, p->side);
   cudaEventRecord(p->ev_join, p->side);
   m.mark(1);
-  launch_theta_forward_x<float>(p, adj, st, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
-                                  twc, p->perm_col, adj ? poc : static_cast<const cpx<float>*>(p->post_col_s_t),
-                                  inv_n, 0);
-  m.mark(2);
-  sp::launch_solve<float>(adj, solve, W, p->f32_l, p->f32_iu, p->f32_cu, p->N, p->K, p->Kp);
-  m.mark(3);
-  launch_theta_inverse_x<float>(p, adj, st, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
-                                  twc, p->perm_col, poc, inv_n, 0);
+  if (!adj && p->fused) {
+    sp::launch_theta_fused(p->big_col,
+                           Launch{dim3((p->K + std::max(p->fuse_cols, 1) - 1) / std::max(p->fuse_cols, 1)),
+                                  p->fuse_threads, p->fuse_smem, st},
+                           W, p->N, p->K, p->Kp, p->fuse_cols, p->col_fft, twc, p->perm_col,
+                           static_cast<const cpx<float>*>(p->post_col_s_t), poc, p->fc_iu, inv_n);
+    m.mark(2);
+    m.mark(3);
+  } else {
+    launch_theta_forward_x<float>(p, adj, st, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
+                                    twc, p->perm_col, adj ? poc : static_cast<const cpx<float>*>(p->post_col_s_t),
+                                    inv_n, 0);
+    m.mark(2);
+    sp::launch_solve<float>(adj, solve, W, p->f32_l, p->f32_iu, p->f32_cu, p->N, p->K, p->Kp);
+    m.mark(3);
+    launch_theta_inverse_x<float>(p, adj, st, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
+                                    twc, p->perm_col, poc, inv_n, 0);
+  }
   cudaStreamWaitEvent(st, p->ev_join, 0);
   m.mark(4);
   rows_inverse_stage<float>(p, adj, st, W, out, twr, por, p->row_scale, static_cast<const float*>(p->row_scale_t),
@@ -756,6 +780,17 @@ cudaError_t allow_all_smem(int device) {
   upd(sp::allow_transform_smem<sp::dd>(optin));
   if (r == cudaSuccess && device >= 0 && device < 64) g_attr_done[device] = true;
   return r;
+}
+
+bool set_fused_tile(sp_plan_t p, int cols, int threads) {
+  // cols = 0: the cluster form (one column per CTA, four CTAs per cluster)
+  if (p->precision != SP_FP32 || cols < 0 || threads < 64) return false;
+  const size_t smem = sp::theta_fused_smem(p->N, cols, threads);
+  if (smem > 220 * 1024 || 2 * std::max(cols, 1) * 32 > threads) return false;
+  p->fuse_cols = cols;
+  p->fuse_threads = threads;
+  p->fuse_smem = smem;
+  return true;
 }
 
 template <typename S>
@@ -925,10 +960,12 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   const size_t fac64 = precision == SP_FP64 ? grid * sizeof(double) : 0;
   const size_t fac32 = precision == SP_FP64 ? 0 : grid * sizeof(float);
   const size_t facz = precision == SP_FP64 ? 0 : (size_t)p->N * 2 * sizeof(double);
+  const size_t faccol = precision == SP_FP32 ? (size_t)p->K * p->N * sizeof(float) : 0;
   const size_t o_fac_begin = off;
   size_t o_l = take(fac64), o_iu = take(fac64), o_cu = take(fac64);
   size_t o_l32 = take(fac32), o_iu32 = take(fac32), o_cu32 = take(fac32);
   size_t o_zl = take(facz), o_ziu = take(facz), o_zcu = take(facz);
+  size_t o_fciu = take(faccol);
   const size_t total = off;
 
   int rc = SP_OK;
@@ -969,6 +1006,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   p->z_l = reinterpret_cast<double*>(base + o_zl);
   p->z_iu = reinterpret_cast<double*>(base + o_ziu);
   p->z_cu = reinterpret_cast<double*>(base + o_zcu);
+  p->fc_iu = reinterpret_cast<float*>(base + o_fciu);
   p->magic = kMagic;
 
   auto up = [&](void* dst, const void* src, size_t bytes, const char* what) {
@@ -1050,18 +1088,28 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
       sp::launch_factor<float>(sp::Launch{dim3(blocks), threads, 0, 0}, p->f32_l, p->f32_iu, p->f32_cu, p->N,
                                p->K, p->Kp, true);
       sp::launch_factor<double>(sp::Launch{dim3(1), threads, 0, 0}, p->z_l, p->z_iu, p->z_cu, p->N, 1, 2, false);
+      if (precision == SP_FP32)   // per-column top-down tables of the fused colatitude stage
+        sp::launch_factor_cols(sp::Launch{dim3(blocks), threads, 0, 0}, p->fc_iu, p->N, p->K);
     }
     step(cudaGetLastError(), "k_factor launch");
     step(cudaDeviceSynchronize(), "k_factor");
   }
   if (precision != SP_FP64 && rc == SP_OK) {
-    step(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking), "cudaStreamCreate(side)");
+    // the zonal side path is a chain of one-CTA kernels: at the highest priority
+    // they are dispatched ahead of the main stream's queued CTAs instead of
+    // waiting for shared memory to free up at the end of a full-grid kernel
+    int lo_prio = 0, hi_prio = 0;
+    step(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio), "cudaDeviceGetStreamPriorityRange");
+    step(cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, hi_prio), "cudaStreamCreate(side)");
     step(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
     step(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming), "cudaEventCreate");
   }
   step(allow_all_smem(p->device), "shared memory attribute");
   p->pipe_rows = p->pipe_cols = true;
   step(configure_pipes(p), "pipelined kernels");
+  // the FP32 form fuses its colatitude stages: one column per CTA, the widest
+  // thread count the kernel allows (the tuner may choose otherwise)
+  p->fused = precision == SP_FP32 && set_fused_tile(p, 0, p->big_col ? 256 : 512);
   if (rc == SP_OK && (flags & SP_FLAG_AUTOTUNE)) rc = tune_single(p);
   if (rc != SP_OK) {
     destroy_plan(p);
@@ -1180,6 +1228,8 @@ int tune_single(sp_plan_t p) {
       const std::vector<double>& v = it->second;
       set_rows((int)v[0], (int)v[1], v[4] != 0.0);
       set_cols((int)v[2], (int)v[3], v[5] != 0.0);
+      if (v.size() >= 10 && p->precision == SP_FP32)
+        p->fused = v[7] != 0.0 && set_fused_tile(p, (int)v[8], (int)v[9]);
       return SP_OK;
     }
   }
@@ -1218,6 +1268,10 @@ int tune_single(sp_plan_t p) {
   };
   const int cap_r = p->big_row ? 256 : 512, cap_c = p->big_col ? 256 : 512;
   double best_ms = 1e30;
+  // the transform tiles are tuned on the unfused path, then the fused stage's tiles
+  const bool fused0 = p->fused;
+  const int fc0 = p->fuse_cols, ft0 = p->fuse_threads;
+  p->fused = false;
   if (rc == SP_OK) {
     int br = p->rows_per_cta, bt = p->row_threads;
     bool bp = p->pipe_rows;
@@ -1254,6 +1308,27 @@ int tune_single(sp_plan_t p) {
           }
         }
     set_cols(bq, bct, bcp);
+    if (fused0) {
+      bool bf = false;
+      int bfc = fc0, bft = ft0;
+      for (int q = 0; q <= 4 && q <= p->Kp; q = q ? 2 * q : 1)
+        for (int t = 128; t <= cap_c; t *= 2) {
+          if (!set_fused_tile(p, q, t)) continue;
+          p->fused = true;
+          const double ms = time_solve();
+          p->fused = false;
+          if (ms < best_ms) {
+            best_ms = ms;
+            bf = true;
+            bfc = q;
+            bft = t;
+          }
+        }
+      p->fused = bf && set_fused_tile(p, bfc, bft);
+      if (!p->fused) set_fused_tile(p, fc0, ft0);
+    }
+  } else {
+    p->fused = fused0;
   }
   if (st) cudaStreamSynchronize(st);
   cudaFree(f);
@@ -1265,7 +1340,8 @@ int tune_single(sp_plan_t p) {
   if (rc == SP_OK && cache_path && best_ms < 1e29) {
     std::ofstream out(cache_path, std::ios::app);
     out << key << " " << p->rows_per_cta << " " << p->row_threads << " " << p->cols_per_cta << " "
-        << p->col_threads << " " << (int)p->pipe_rows << " " << (int)p->pipe_cols << " " << best_ms << "\n";
+        << p->col_threads << " " << (int)p->pipe_rows << " " << (int)p->pipe_cols << " " << best_ms << " "
+        << (int)p->fused << " " << p->fuse_cols << " " << p->fuse_threads << "\n";
   }
   return rc;
 }
@@ -2191,7 +2267,7 @@ int sphere_poisson_launch_count(sp_plan_t plan, int adjoint, int* launches) {
   if (!launches) return SP_ERR_NULL;
   if (plan->batched) *launches = plan->count ? 1 : 0;
   else if (plan->precision == SP_FP64) *launches = kStages;
-  else if (plan->precision == SP_FP32) *launches = kStages + 3;
+  else if (plan->precision == SP_FP32) *launches = (plan->fused && !adjoint ? kStages - 2 : kStages) + 3;
   else *launches = adjoint ? 0 : kStages - 1 + 3 + (plan->sweeps + 1);
   return SP_OK;
 }
@@ -2244,7 +2320,7 @@ int sphere_poisson_profile_end(sp_plan_t plan, double* stage_ms, int max_stages,
 
 const char* sphere_poisson_stage_name(sp_plan_t plan, int stage) {
   if (!plan_ok(plan) || stage < 0 || stage >= kStages) return "";
-  return kStageNames[stage];
+  return plan->fused ? kFusedStageNames[stage] : kStageNames[stage];
 }
 
 int sphere_poisson_destroy(sp_plan_t plan) {
