@@ -25,6 +25,8 @@ def test_algorithmic_bytes_at_5000x10000():
     # FP32 spectrum and tables
     b32 = bench.algorithmic_bytes(5000, 10000, spec_elem=8, table_elem=4)
     assert b32["theta_forward"] == 2 * 8 * 5000 * 5002
+    # fused: the spectrum in and out once, one FP32 pivot per (j, k) of the 5001 columns
+    assert b32["theta_fused"] == 2 * 8 * 5000 * 5002 + 4 * 5000 * 5001
 
 
 def test_algorithmic_flops_are_the_conventional_counts():
@@ -32,8 +34,11 @@ def test_algorithmic_flops_are_the_conventional_counts():
     assert f["rows_forward"] == pytest.approx(5000 * 2.5 * 10000 * math.log2(10000))
     assert f["theta_forward"] == pytest.approx(5001 * 5.0 * 5000 * math.log2(5000))
     assert f["solve"] == 10.0 * 5000 * 5001
-    per_dof = sum(f.values()) / (5000 * 10000)
+    stages = ("rows_forward", "theta_forward", "solve", "theta_inverse", "rows_inverse")
+    per_dof = sum(f[s] for s in stages) / (5000 * 10000)
     assert 130 < per_dof < 145                  # ~5 log2(n N) + 10
+    # the fused colatitude stage of the FP32 form does both transforms and the solve
+    assert f["theta_fused"] == pytest.approx(f["theta_forward"] + f["solve"] + f["theta_inverse"])
 
 
 def test_whole_job_value_counts_every_rank():
