@@ -589,6 +589,119 @@ __device__ __forceinline__ void fft_pass(cpx<T>* buf, int L, int nbatch, int Ns,
   __syncthreads();
 }
 
+// Decimation in frequency: the transpose of the pass above.  Pass (R, Ns) as
+// a matrix is (I (x) DFT_R (x) I_Ns) D with D the twiddles w^(r k); its transpose
+// D (I (x) DFT_R (x) I_Ns) applies the R-point DFT first and the same twiddles
+// after, on the same elements.  Since the DFT matrix is symmetric, running the
+// transposed passes in reverse order on a sequence in natural order leaves
+// the transform in digit-reversed order: output q at position perm[q], the
+// position the DIT load gives input q.  Plain twiddle tables only (the FP32 and
+// double-float kernels).
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void fft_pass_dif(cpx<T>* buf, int L, int nbatch, int Ns,
+                                             const cpx<T>* __restrict__ stw, const cpx<T>* __restrict__ dtw,
+                                             const FastDiv& dnb, const FastDiv& dns) {
+  constexpr int RP = (R + 1) & ~1;
+  const int nb = L / R;
+  const int total = nb * nbatch;
+  for (int b = threadIdx.x; b < total; b += blockDim.x) {
+    const int batch = (int)fdiv((unsigned)b, dnb);
+    const int j = b - batch * nb;
+    const int g = (int)fdiv((unsigned)j, dns);
+    const int k = j - g * Ns;
+    cpx<T>* base = buf + batch * L + g * Ns * R + k;
+    const cpx<T>* tk = stw + k * RP;
+    cpx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = base[r * Ns];
+    if constexpr (R <= 8) {
+      dft_any<R, DIR>(v, dtw);
+      if (Ns > 1) {
+        cpx<T> w[R];
+        load_stage_tw<R>(tk, w);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = twmul<DIR>(v[r], w[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) base[r * Ns] = v[r];
+    } else {
+      // large odd prime: as in fft_pass, each output pair (a, R - a) formed in a
+      // rolled loop, then multiplied by its twiddle and stored
+      constexpr int H = (R - 1) / 2;
+      cpx<T> y0 = v[0];
+#pragma unroll
+      for (int bb = 1; bb <= H; ++bb) {
+        cpx<T> pb = v[bb] + v[R - bb];
+        cpx<T> qb = v[bb] - v[R - bb];
+        v[bb] = pb;
+        v[R - bb] = qb;
+        y0 = y0 + pb;
+      }
+      const cpx<T> x0 = v[0];
+      base[0] = y0;
+#pragma unroll 1
+      for (int a = 1; a <= H; ++a) {
+        cpx<T> A = x0, B = {(T)0, (T)0};
+        int ab = 0;
+#pragma unroll
+        for (int bb = 1; bb <= H; ++bb) {
+          ab += a;
+          if (ab >= R) ab -= R;
+          cpx<T> w = ldg_c(dtw + ab);
+          T c = w.re, sn = -w.im;
+          A.re = fma(c, v[bb].re, A.re);
+          A.im = fma(c, v[bb].im, A.im);
+          B.re = fma(sn, v[R - bb].re, B.re);
+          B.im = fma(sn, v[R - bb].im, B.im);
+        }
+        cpx<T> iB = DIR < 0 ? cpx<T>{B.im, -B.re} : cpx<T>{-B.im, B.re};
+        cpx<T> ya = A + iB, yb = A - iB;
+        if (Ns > 1) {
+          ya = twmul<DIR>(ya, ldg_c(tk + a));
+          yb = twmul<DIR>(yb, ldg_c(tk + (R - a)));
+        }
+        base[a * Ns] = ya;
+        base[(R - a) * Ns] = yb;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Full decimation-in-frequency transform: natural order in, output q at
+// position perm[q] (perm as for fft_run's input).  Expects a barrier before entry.
+template <int DIR, bool BIG, typename T>
+__device__ __forceinline__ void fft_run_dif(cpx<T>* buf, int nbatch, const FftDesc& d, const cpx<T>* __restrict__ tw) {
+  int Ns = d.L;
+  for (int s = d.nstages - 1; s >= 0; --s) {
+    const int R = d.radix[s];
+    Ns /= R;                                   // R_1 ... R_{s-1}
+    const cpx<T>* stw = tw + d.tw_off[s];
+    const cpx<T>* dtw = tw + d.dft_off[s];
+    switch (R) {
+      case 2: fft_pass_dif<2, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 3: fft_pass_dif<3, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 4: fft_pass_dif<4, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 5: fft_pass_dif<5, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 7: fft_pass_dif<7, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 8: fft_pass_dif<8, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      default: break;
+    }
+    if constexpr (BIG) {
+      switch (R) {
+      case 11: fft_pass_dif<11, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 13: fft_pass_dif<13, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 17: fft_pass_dif<17, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 19: fft_pass_dif<19, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 23: fft_pass_dif<23, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 29: fft_pass_dif<29, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      case 31: fft_pass_dif<31, DIR>(buf, d.L, nbatch, Ns, stw, dtw, d.div_nb[s], d.div_ns[s]); break;
+      default: break;
+      }
+    }
+  }
+}
+
 // Full transform of sequences stored in digit-reversed order (position
 // perm[q] holds input q; see the host's digit_reversal): DIR = -1 computes
 // sum_q a_q exp(-2 pi i q k / L) (unnormalised), DIR = +1 the same with exp(+...),

@@ -77,11 +77,12 @@ struct ScanSlot {
 };
 
 // Shared-memory bytes of the fused kernel for a tile of `cols` columns of
-// length N with `threads` threads: FFT buffer, coefficient buffer, scan slots.
+// length N with `threads` threads: transform buffer, coefficient buffer
+// (`buffers` = 2; the single-buffer form has none), scan slots.
 template <typename T>
-__host__ __device__ inline size_t fused_smem_bytes(int N, int cols, int threads) {
+__host__ __device__ inline size_t fused_smem_bytes(int N, int cols, int threads, int buffers = 2) {
   const size_t buf = ((size_t)cols * N * sizeof(cpx<T>) + 15) & ~(size_t)15;
-  return 2 * buf + (size_t)threads * sizeof(ScanSlot<T>);
+  return buffers * buf + (size_t)threads * sizeof(ScanSlot<T>);
 }
 
 // Phase 2 of one chain's scan, run by one warp: slots slot[q * stride] for the
@@ -126,12 +127,13 @@ __device__ __forceinline__ void chain_carry_scan(ScanSlot<T>* slot, int stride, 
   }
 }
 
-// The eliminations of a tile and its row-0 closure, in place in X ([j][cols],
-// the forward transform's output), by the chunked scans described above.
-// Whole CTA; ends with a barrier.
+// The eliminations of a tile and its row-0 closure, in place in X (the
+// forward transform's output; coefficient (j, column c) at X[j js + c cs]), by
+// the chunked scans described above.  Whole CTA; ends with a barrier.
 template <typename T>
-__device__ __forceinline__ void fused_solve(cpx<T>* __restrict__ X, ScanSlot<T>* __restrict__ slot, int k0,
-                                            int cols, int N, int K, const T* __restrict__ fiu) {
+__device__ __forceinline__ void fused_solve(cpx<T>* __restrict__ X, int js, int cs,
+                                            ScanSlot<T>* __restrict__ slot, int k0, int cols, int N, int K,
+                                            const T* __restrict__ fiu) {
   // thread -> (chain ch, chunk p); chain ch = column ch >> 1,
   //    parity ch & 1 (0: odd rows j = 1, 3, ..; 1: even rows j = 2, 4, ..)
   const int chains = 2 * cols;
@@ -154,7 +156,7 @@ __device__ __forceinline__ void fused_solve(cpx<T>* __restrict__ X, ScanSlot<T>*
       for (int t = s; t < e; ++t) {
         const int j = j0 + 2 * t;
         const T l = t > 0 ? band_a<T>(j) * __ldg(fiu + tcol + j - 2) : (T)0;
-        const cpx<T> dv = X[j * cols + c];
+        const cpx<T> dv = X[j * js + c * cs];
         y = {fma(-l, y.re, dv.re), fma(-l, y.im, dv.im)};
         A = A * (-l);
       }
@@ -175,7 +177,7 @@ __device__ __forceinline__ void fused_solve(cpx<T>* __restrict__ X, ScanSlot<T>*
     for (int t = s; t < e; ++t) {
       const int j = j0 + 2 * t;
       const T l = t > 0 ? band_a<T>(j) * __ldg(fiu + tcol + j - 2) : (T)0;
-      cpx<T>& dv = X[j * cols + c];
+      cpx<T>& dv = X[j * js + c * cs];
       y = {fma(-l, y.re, dv.re), fma(-l, y.im, dv.im)};
       dv = y;
     }
@@ -190,7 +192,7 @@ __device__ __forceinline__ void fused_solve(cpx<T>* __restrict__ X, ScanSlot<T>*
       for (int t = e - 1; t >= s; --t) {
         const int j = j0 + 2 * t;
         const T iu = __ldg(fiu + tcol + j), cu = band_c<T>(j) * iu;
-        const cpx<T> yv = X[j * cols + c];
+        const cpx<T> yv = X[j * js + c * cs];
         x = {fma(iu, yv.re, -cu * x.re), fma(iu, yv.im, -cu * x.im)};
         A = A * (-cu);
       }
@@ -209,7 +211,7 @@ __device__ __forceinline__ void fused_solve(cpx<T>* __restrict__ X, ScanSlot<T>*
     for (int t = e - 1; t >= s; --t) {
       const int j = j0 + 2 * t;
       const T iu = __ldg(fiu + tcol + j), cu = band_c<T>(j) * iu;
-      cpx<T>& yv = X[j * cols + c];
+      cpx<T>& yv = X[j * js + c * cs];
       x = {fma(iu, yv.re, -cu * x.re), fma(iu, yv.im, -cu * x.im)};
       yv = x;
     }
@@ -220,12 +222,12 @@ __device__ __forceinline__ void fused_solve(cpx<T>* __restrict__ X, ScanSlot<T>*
   if (threadIdx.x < cols) {
     const int kc = k0 + threadIdx.x;
     if (kc < K && kc != 0) {
-      cpx<T>& x0 = X[threadIdx.x];
+      cpx<T>& x0 = X[threadIdx.x * cs];
       if (kc & 1) {
         x0 = {(T)0, (T)0};
       } else {
         const T ik2 = (T)(1.0 / ((double)kc * (double)kc));
-        const cpx<T> x2 = N > 2 ? X[2 * cols + threadIdx.x] : cpx<T>{(T)0, (T)0};
+        const cpx<T> x2 = N > 2 ? X[2 * js + threadIdx.x * cs] : cpx<T>{(T)0, (T)0};
         x0 = {(x2.re - x0.re) * ik2, (x2.im - x0.im) * ik2};
       }
     }
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_fused(
   __syncthreads();
 
   // 2. eliminations and the row-0 closure, in X
-  fused_solve<T>(X, slot, k0, cols, N, K, fiu);
+  fused_solve<T>(X, cols, 1, slot, k0, cols, N, K, fiu);
 
   // 3. inverse colatitude transform from X back to W
   theta_inverse_load<T, false>(k0, sm, FromStaged<cpx<T>>{X, cols}, N, K, cols, perm, post, 0);
@@ -312,7 +314,7 @@ __global__ void __cluster_dims__(kFuseCluster, 1, 1) __launch_bounds__(BIG ? 256
   // 2. this column: forward transform into X, eliminations, inverse transform in sm
   theta_forward_finish<float, false, BIG>(k, sm, X - k, N, K, 1, 1, d, tw, post_s, 0);
   __syncthreads();
-  fused_solve<float>(X, slot, k, 1, N, K, fiu);
+  fused_solve<float>(X, 1, 1, slot, k, 1, N, K, fiu);
   theta_inverse_load<float, false>(k, sm, FromStaged<cpx<float>>{X, 1}, N, K, 1, perm, post, 0);
   __syncthreads();
   fft_run<+1, BIG>(sm, 1, d, tw);
@@ -333,6 +335,91 @@ __global__ void __cluster_dims__(kFuseCluster, 1, 1) __launch_bounds__(BIG ? 256
     if (half1) dst[1] = make_float4(v[2].re, v[2].im, v[3].re, v[3].im);
   }
   cluster.sync();   // no CTA leaves while a peer still reads its buffer
+}
+
+// Single-buffer form: the tile lives in one shared-memory buffer ([c][N]) from
+// load to store.  The forward transform runs by decimation in time (digit-
+// reversed input, natural output), the DCT/DST post-twiddle, the eliminations
+// and the inverse pre-twiddle work in place on natural-order pairs (j, N - j),
+// and the inverse transform runs by decimation in frequency (natural input,
+// digit-reversed output), read back through the same permutation at the store.
+// Half the shared memory of the two-buffer form, so two columns per CTA keep
+// two CTAs per SM.
+template <bool BIG>
+__global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_fused1(
+    cpx<float>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d, const cpx<float>* __restrict__ tw,
+    const int* __restrict__ perm, const cpx<float>* __restrict__ post_s, const cpx<float>* __restrict__ post,
+    const float* __restrict__ fiu) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const size_t buf = ((size_t)cols * N * sizeof(cpx<float>) + 15) & ~(size_t)15;
+  cpx<float>* sm = reinterpret_cast<cpx<float>*>(smem_raw);
+  ScanSlot<float>* slot = reinterpret_cast<ScanSlot<float>*>(smem_raw + buf);
+  const int k0 = blockIdx.x * cols;
+  const int cs = __ffs(cols) - 1;              // cols is a power of two
+  const int H = N / 2 + 1;
+
+  // 1. load (Makhoul reordering, digit-reversed positions) and forward DIT transform
+  theta_forward_load<float>(k0, sm, FromGlobal<cpx<float>>{W + k0, (size_t)Kp}, N, K, cols, perm);
+  __syncthreads();
+  fft_run<-1, BIG>(sm, cols, d, tw);
+  // 2. post-twiddle in place on the pairs (j, N - j) (theta_forward_finish, forward form)
+  for (int idx = threadIdx.x; idx < H * cols; idx += blockDim.x) {
+    const int j = idx >> cs, c = idx & (cols - 1);
+    const int k = k0 + c;
+    if (k >= K) continue;
+    cpx<float>* V = sm + c * N;
+    const int jj = N - j;
+    const bool pair = j > 0 && jj != j;
+    const cpx<float> w = ldg_c(post_s + j);
+    const cpx<float> a = V[j], b = V[j == 0 ? 0 : jj];
+    const cpx<float> S = a + b, D = a - b;
+    const cpx<float> pj = {fmaf(w.re, S.re, -(w.im * D.im)), fmaf(w.re, S.im, w.im * D.re)};
+    const cpx<float> pjj = {fmaf(-w.im, S.re, -(w.re * D.im)), fmaf(-w.im, S.im, w.re * D.re)};
+    if ((k & 1) == 0) {
+      V[j] = pj;
+      if (pair) V[jj] = pjj;
+    } else {
+      V[j] = j == 0 ? cpx<float>{0.f, 0.f} : cpx<float>{pjj.im, -pjj.re};
+      if (pair) V[jj] = {pj.im, -pj.re};
+    }
+  }
+  __syncthreads();
+  // 3. eliminations in place
+  fused_solve<float>(sm, 1, N, slot, k0, cols, N, K, fiu);
+  // 4. pre-twiddle of the inverse in place (theta_inverse_load, forward form),
+  //    in natural order
+  for (int idx = threadIdx.x; idx < H * cols; idx += blockDim.x) {
+    const int j = idx >> cs, c = idx & (cols - 1);
+    const int k = k0 + c;
+    cpx<float>* V = sm + c * N;
+    const int jj = N - j;
+    const bool odd = (k & 1);
+    if (k >= K) {
+      V[j] = {0.f, 0.f};
+      if (j > 0 && jj != j) V[jj] = {0.f, 0.f};
+      continue;
+    }
+    if (j == 0) {
+      if (odd) V[0] = {0.f, 0.f};
+      continue;
+    }
+    const cpx<float> xa = V[j], xb = V[jj];
+    const cpx<float> ya = odd ? xb : xa, yb = odd ? xa : xb;
+    V[j] = cmul(conj(ldg_c(post + j)), cpx<float>{ya.re + yb.im, ya.im - yb.re});
+    if (jj != j) V[jj] = cmul(conj(ldg_c(post + jj)), cpx<float>{yb.re + ya.im, yb.im - ya.re});
+  }
+  __syncthreads();
+  // 5. inverse DIF transform (output q at position perm[q]) and store with the
+  //    inverse Makhoul reordering and, on odd k, the factor i (-1)^i
+  fft_run_dif<+1, BIG>(sm, cols, d, tw);
+  for (int idx = threadIdx.x; idx < N * cols; idx += blockDim.x) {
+    const int i = idx >> cs, c = idx & (cols - 1);
+    const int k = k0 + c;
+    if (k >= K) continue;
+    cpx<float> v = sm[c * N + __ldg(perm + makhoul_pos(i, N))];
+    if (k & 1) v = {neg_if(v.im, !(i & 1)), neg_if(v.re, (i & 1) != 0)};
+    W[(size_t)i * Kp + k] = v;
+  }
 }
 
 }  // namespace sp

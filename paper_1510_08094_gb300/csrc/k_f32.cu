@@ -56,11 +56,22 @@ cudaError_t allow_transform_smem<float>(int bytes) {
   upd(cudaFuncSetAttribute(k_theta_fused<float, true>, a, bytes));
   upd(cudaFuncSetAttribute(k_theta_fused_cl<false>, a, bytes));
   upd(cudaFuncSetAttribute(k_theta_fused_cl<true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_fused1<false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_fused1<true>, a, bytes));
   return e;
 }
 void launch_theta_fused(bool big, const Launch& l, cpx<float>* W, int N, int K, int Kp, int cols, const FftDesc& d,
                         const cpx<float>* tw, const int* perm, const cpx<float>* post_s, const cpx<float>* post,
                         const float* fiu, float inv_n) {
+  if (cols < 0) {    // the single-buffer form, -cols columns per CTA
+    const int q = -cols;
+    const dim3 grid((K + q - 1) / q);
+    if (big)
+      k_theta_fused1<true><<<grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, q, d, tw, perm, post_s, post, fiu);
+    else
+      k_theta_fused1<false><<<grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, q, d, tw, perm, post_s, post, fiu);
+    return;
+  }
   if (cols == 0) {   // the cluster form: one column per CTA, clusters of kFuseCluster
     const dim3 grid(((K + kFuseCluster - 1) / kFuseCluster) * kFuseCluster);
     if (big)
@@ -77,6 +88,7 @@ void launch_theta_fused(bool big, const Launch& l, cpx<float>* W, int N, int K, 
                                                                          post, fiu, inv_n);
 }
 size_t theta_fused_smem(int N, int cols, int threads) {
+  if (cols < 0) return fused_smem_bytes<float>(N, -cols, threads, 1);
   return fused_smem_bytes<float>(N, cols > 0 ? cols : 1, threads);
 }
 void launch_factor_cols(const Launch& l, float* fiu, int N, int K) {

@@ -75,9 +75,11 @@ void launch_factor(const Launch& l, S* fl, S* fiu, S* fcu, int N, int K, int Kp,
 
 // the FP32 form's fused colatitude stage (forward transform, parity
 // eliminations, inverse transform per column tile; fused.cuh): tables of
-// launch_factor_cols, one CTA per tile of `cols` columns, or with cols = 0 one
-// column per CTA in clusters of four that share their loads and stores
-// (l.grid is then ignored); theta_fused_smem dynamic bytes
+// launch_factor_cols, one CTA per tile of `cols` columns with a transform
+// buffer and a coefficient buffer; cols < 0: -cols columns per CTA in one
+// buffer (decimation-in-frequency inverse); cols = 0: one column per CTA in
+// clusters of four that share their loads and stores (l.grid is ignored);
+// theta_fused_smem dynamic bytes
 void launch_theta_fused(bool big, const Launch& l, cpx<float>* W, int N, int K, int Kp, int cols, const FftDesc& d,
                         const cpx<float>* tw, const int* perm, const cpx<float>* post_s, const cpx<float>* post,
                         const float* fiu, float inv_n);

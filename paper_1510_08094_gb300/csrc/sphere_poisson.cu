@@ -645,7 +645,7 @@ void enqueue_fp32(sp_plan_t p, bool adj, const double* in, double* out, void* ws
   if (!adj && p->fused) {
     sp::launch_theta_fused(p->big_col,
                            Launch{dim3((p->K + std::max(p->fuse_cols, 1) - 1) / std::max(p->fuse_cols, 1)),
-                                  p->fuse_threads, p->fuse_smem, st},
+                                  p->fuse_threads, p->fuse_smem, st},  // grid recomputed for cols <= 0
                            W, p->N, p->K, p->Kp, p->fuse_cols, p->col_fft, twc, p->perm_col,
                            static_cast<const cpx<float>*>(p->post_col_s_t), poc, p->fc_iu, inv_n);
     m.mark(2);
@@ -783,10 +783,12 @@ cudaError_t allow_all_smem(int device) {
 }
 
 bool set_fused_tile(sp_plan_t p, int cols, int threads) {
-  // cols = 0: the cluster form (one column per CTA, four CTAs per cluster)
-  if (p->precision != SP_FP32 || cols < 0 || threads < 64) return false;
+  // cols > 0: two buffers, cols columns per CTA; cols < 0: one buffer, -cols
+  // columns per CTA; cols = 0: the cluster form (one column per CTA, four CTAs
+  // per cluster)
+  if (p->precision != SP_FP32 || threads < 64) return false;
   const size_t smem = sp::theta_fused_smem(p->N, cols, threads);
-  if (smem > 220 * 1024 || 2 * std::max(cols, 1) * 32 > threads) return false;
+  if (smem > 220 * 1024 || 2 * std::max(std::abs(cols), 1) * 32 > threads) return false;
   p->fuse_cols = cols;
   p->fuse_threads = threads;
   p->fuse_smem = smem;
@@ -1109,7 +1111,8 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   step(configure_pipes(p), "pipelined kernels");
   // the FP32 form fuses its colatitude stages: one column per CTA, the widest
   // thread count the kernel allows (the tuner may choose otherwise)
-  p->fused = precision == SP_FP32 && set_fused_tile(p, 0, p->big_col ? 256 : 512);
+  p->fused = precision == SP_FP32 && (set_fused_tile(p, p->Kp >= 2 ? -2 : -1, p->big_col ? 256 : 512) ||
+                                      set_fused_tile(p, -1, p->big_col ? 256 : 512));
   if (rc == SP_OK && (flags & SP_FLAG_AUTOTUNE)) rc = tune_single(p);
   if (rc != SP_OK) {
     destroy_plan(p);
@@ -1311,8 +1314,9 @@ int tune_single(sp_plan_t p) {
     if (fused0) {
       bool bf = false;
       int bfc = fc0, bft = ft0;
-      for (int q = 0; q <= 4 && q <= p->Kp; q = q ? 2 * q : 1)
+      for (int q : {-1, -2, -4, 0, 1, 2, 4})
         for (int t = 128; t <= cap_c; t *= 2) {
+          if (std::abs(q) > p->Kp) continue;
           if (!set_fused_tile(p, q, t)) continue;
           p->fused = true;
           const double ms = time_solve();
