@@ -337,6 +337,82 @@ __global__ void __cluster_dims__(kFuseCluster, 1, 1) __launch_bounds__(BIG ? 256
   cluster.sync();   // no CTA leaves while a peer still reads its buffer
 }
 
+// In-place DCT/DST post-twiddle of the forward colatitude transform on
+// natural-order pairs (j, N - j) of each column c of sm ([c][N]), the forward
+// form of theta_forward_finish: each thread reads a pair and writes the same
+// pair.  Columns k >= K are left alone.
+template <typename T>
+__device__ __forceinline__ void post_twiddle_inplace(cpx<T>* __restrict__ sm, int k0, int cols, int N, int K,
+                                                     const cpx<T>* __restrict__ post_s) {
+  const int cs = __ffs(cols) - 1;
+  const int H = N / 2 + 1;
+  for (int idx = threadIdx.x; idx < H * cols; idx += blockDim.x) {
+    const int j = idx >> cs, c = idx & (cols - 1);
+    const int k = k0 + c;
+    if (k >= K) continue;
+    cpx<T>* V = sm + c * N;
+    const int jj = N - j;
+    const bool pair = j > 0 && jj != j;
+    const cpx<T> w = ldg_c(post_s + j);
+    const cpx<T> a = V[j], b = V[j == 0 ? 0 : jj];
+    const cpx<T> S = a + b, D = a - b;
+    const cpx<T> pj = {fma(w.re, S.re, -(w.im * D.im)), fma(w.re, S.im, w.im * D.re)};
+    const cpx<T> pjj = {fma(-w.im, S.re, -(w.re * D.im)), fma(-w.im, S.im, w.re * D.re)};
+    if ((k & 1) == 0) {
+      V[j] = pj;
+      if (pair) V[jj] = pjj;
+    } else {
+      V[j] = j == 0 ? cpx<T>{(T)0, (T)0} : cpx<T>{pjj.im, -pjj.re};
+      if (pair) V[jj] = {pj.im, -pj.re};
+    }
+  }
+}
+
+// In-place pre-twiddle of the inverse colatitude transform (the forward form
+// of theta_inverse_load) in natural order; columns k >= K are zeroed.
+template <typename T>
+__device__ __forceinline__ void pre_twiddle_inplace(cpx<T>* __restrict__ sm, int k0, int cols, int N, int K,
+                                                    const cpx<T>* __restrict__ post) {
+  const int cs = __ffs(cols) - 1;
+  const int H = N / 2 + 1;
+  for (int idx = threadIdx.x; idx < H * cols; idx += blockDim.x) {
+    const int j = idx >> cs, c = idx & (cols - 1);
+    const int k = k0 + c;
+    cpx<T>* V = sm + c * N;
+    const int jj = N - j;
+    const bool odd = (k & 1);
+    if (k >= K) {
+      V[j] = {(T)0, (T)0};
+      if (j > 0 && jj != j) V[jj] = {(T)0, (T)0};
+      continue;
+    }
+    if (j == 0) {
+      if (odd) V[0] = {(T)0, (T)0};
+      continue;
+    }
+    const cpx<T> xa = V[j], xb = V[jj];
+    const cpx<T> ya = odd ? xb : xa, yb = odd ? xa : xb;
+    V[j] = cmul(conj(ldg_c(post + j)), cpx<T>{ya.re + yb.im, ya.im - yb.re});
+    if (jj != j) V[jj] = cmul(conj(ldg_c(post + jj)), cpx<T>{yb.re + ya.im, yb.im - ya.re});
+  }
+}
+
+// The store after a decimation-in-frequency inverse: output i of column c is
+// at sm[c N + perm[makhoul_pos(i, N)]]; on odd k the factor i (-1)^i.
+template <typename T>
+__device__ __forceinline__ void store_dif_columns(const cpx<T>* __restrict__ sm, cpx<T>* __restrict__ W, int k0,
+                                                  int cols, int N, int K, int Kp, const int* __restrict__ perm) {
+  const int cs = __ffs(cols) - 1;
+  for (int idx = threadIdx.x; idx < N * cols; idx += blockDim.x) {
+    const int i = idx >> cs, c = idx & (cols - 1);
+    const int k = k0 + c;
+    if (k >= K) continue;
+    cpx<T> v = sm[c * N + __ldg(perm + makhoul_pos(i, N))];
+    if (k & 1) v = {neg_if(v.im, !(i & 1)), neg_if(v.re, (i & 1) != 0)};
+    W[(size_t)i * Kp + k] = v;
+  }
+}
+
 // Single-buffer form: the tile lives in one shared-memory buffer ([c][N]) from
 // load to store.  The forward transform runs by decimation in time (digit-
 // reversed input, natural output), the DCT/DST post-twiddle, the eliminations
@@ -355,71 +431,24 @@ __global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_fused1(
   cpx<float>* sm = reinterpret_cast<cpx<float>*>(smem_raw);
   ScanSlot<float>* slot = reinterpret_cast<ScanSlot<float>*>(smem_raw + buf);
   const int k0 = blockIdx.x * cols;
-  const int cs = __ffs(cols) - 1;              // cols is a power of two
-  const int H = N / 2 + 1;
 
   // 1. load (Makhoul reordering, digit-reversed positions) and forward DIT transform
   theta_forward_load<float>(k0, sm, FromGlobal<cpx<float>>{W + k0, (size_t)Kp}, N, K, cols, perm);
   __syncthreads();
   fft_run<-1, BIG>(sm, cols, d, tw);
   // 2. post-twiddle in place on the pairs (j, N - j) (theta_forward_finish, forward form)
-  for (int idx = threadIdx.x; idx < H * cols; idx += blockDim.x) {
-    const int j = idx >> cs, c = idx & (cols - 1);
-    const int k = k0 + c;
-    if (k >= K) continue;
-    cpx<float>* V = sm + c * N;
-    const int jj = N - j;
-    const bool pair = j > 0 && jj != j;
-    const cpx<float> w = ldg_c(post_s + j);
-    const cpx<float> a = V[j], b = V[j == 0 ? 0 : jj];
-    const cpx<float> S = a + b, D = a - b;
-    const cpx<float> pj = {fmaf(w.re, S.re, -(w.im * D.im)), fmaf(w.re, S.im, w.im * D.re)};
-    const cpx<float> pjj = {fmaf(-w.im, S.re, -(w.re * D.im)), fmaf(-w.im, S.im, w.re * D.re)};
-    if ((k & 1) == 0) {
-      V[j] = pj;
-      if (pair) V[jj] = pjj;
-    } else {
-      V[j] = j == 0 ? cpx<float>{0.f, 0.f} : cpx<float>{pjj.im, -pjj.re};
-      if (pair) V[jj] = {pj.im, -pj.re};
-    }
-  }
+  post_twiddle_inplace<float>(sm, k0, cols, N, K, post_s);
   __syncthreads();
   // 3. eliminations in place
   fused_solve<float>(sm, 1, N, slot, k0, cols, N, K, fiu);
   // 4. pre-twiddle of the inverse in place (theta_inverse_load, forward form),
   //    in natural order
-  for (int idx = threadIdx.x; idx < H * cols; idx += blockDim.x) {
-    const int j = idx >> cs, c = idx & (cols - 1);
-    const int k = k0 + c;
-    cpx<float>* V = sm + c * N;
-    const int jj = N - j;
-    const bool odd = (k & 1);
-    if (k >= K) {
-      V[j] = {0.f, 0.f};
-      if (j > 0 && jj != j) V[jj] = {0.f, 0.f};
-      continue;
-    }
-    if (j == 0) {
-      if (odd) V[0] = {0.f, 0.f};
-      continue;
-    }
-    const cpx<float> xa = V[j], xb = V[jj];
-    const cpx<float> ya = odd ? xb : xa, yb = odd ? xa : xb;
-    V[j] = cmul(conj(ldg_c(post + j)), cpx<float>{ya.re + yb.im, ya.im - yb.re});
-    if (jj != j) V[jj] = cmul(conj(ldg_c(post + jj)), cpx<float>{yb.re + ya.im, yb.im - ya.re});
-  }
+  pre_twiddle_inplace<float>(sm, k0, cols, N, K, post);
   __syncthreads();
   // 5. inverse DIF transform (output q at position perm[q]) and store with the
   //    inverse Makhoul reordering and, on odd k, the factor i (-1)^i
   fft_run_dif<+1, BIG>(sm, cols, d, tw);
-  for (int idx = threadIdx.x; idx < N * cols; idx += blockDim.x) {
-    const int i = idx >> cs, c = idx & (cols - 1);
-    const int k = k0 + c;
-    if (k >= K) continue;
-    cpx<float> v = sm[c * N + __ldg(perm + makhoul_pos(i, N))];
-    if (k & 1) v = {neg_if(v.im, !(i & 1)), neg_if(v.re, (i & 1) != 0)};
-    W[(size_t)i * Kp + k] = v;
-  }
+  store_dif_columns<float>(sm, W, k0, cols, N, K, Kp, perm);
 }
 
 }  // namespace sp

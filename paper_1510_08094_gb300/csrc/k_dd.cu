@@ -2,6 +2,7 @@
 // That form has no adjoint, so only the forward instantiations exist.
 #define SP_REFINE_KERNELS
 #include "launchers.inl"
+#include "fused_refine.cuh"
 
 namespace sp {
 
@@ -47,8 +48,21 @@ cudaError_t allow_transform_smem<dd>(int bytes) {
   upd(cudaFuncSetAttribute(k_theta_inverse<dd, false, false>, a, bytes));
   upd(cudaFuncSetAttribute(k_theta_inverse<dd, false, true>, a, bytes));
   upd(allow_pipe_smem<dd>(bytes));
+  upd(cudaFuncSetAttribute(k_refine_fused<false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_refine_fused<true>, a, bytes));
   return e;
 }
+void launch_refine_fused(bool big, const Launch& l, cpx<dd>* W, int N, int K, int Kp, const FftDesc& d,
+                         const cpx<dd>* tw, const int* perm, const cpx<dd>* post_s, const cpx<dd>* post,
+                         const float* fiu, int sweeps) {
+  if (K < 2) return;   // column 0 only: nothing for this kernel
+  const dim3 grid(K - 1);
+  if (big)
+    k_refine_fused<true><<<grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, d, tw, perm, post_s, post, fiu, sweeps);
+  else
+    k_refine_fused<false><<<grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, d, tw, perm, post_s, post, fiu, sweeps);
+}
+size_t refine_fused_smem(int N, int threads) { return refine_fused_smem_bytes(N, threads); }
 
 void launch_refine(const Launch& l, const cpx<dd>* F, cpx<dd>* X, cpx<float>* Y, const float* fl,
                    const float* fiu, const float* fcu, int N, int K, int Kp, int first) {

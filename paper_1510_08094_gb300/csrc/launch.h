@@ -84,6 +84,13 @@ void launch_theta_fused(bool big, const Launch& l, cpx<float>* W, int N, int K, 
                         const cpx<float>* tw, const int* perm, const cpx<float>* post_s, const cpx<float>* post,
                         const float* fiu, float inv_n);
 size_t theta_fused_smem(int N, int cols, int threads);
+// the FP32 + refinement form's fused colatitude stage (fused_refine.cuh): one
+// CTA per column k >= 1 (column 0 is the FP64 zonal path's), in place in W
+// (double-float spectrum); refine_fused_smem dynamic bytes
+void launch_refine_fused(bool big, const Launch& l, cpx<dd>* W, int N, int K, int Kp, const FftDesc& d,
+                         const cpx<dd>* tw, const int* perm, const cpx<dd>* post_s, const cpx<dd>* post,
+                         const float* fiu, int sweeps);
+size_t refine_fused_smem(int N, int threads);
 // pivots 1/u of the top-down factorisation of every parity chain, stored per
 // column ([k][j]), 2K threads
 void launch_factor_cols(const Launch& l, float* fiu, int N, int K);

@@ -317,8 +317,9 @@ struct sp_plan_s {
   double* z_l;
   double* z_iu;
   double* z_cu;
-  // SP_FP32 forward solve: the fused colatitude stage (fused.cuh) and the
-  // pivots 1/u of its top-down factorisation, per column [k][j]
+  // SP_FP32 forward solve and SP_FP32_REFINE solve: the fused colatitude
+  // stage (fused.cuh, fused_refine.cuh) and the pivots 1/u of its top-down
+  // factorisation, per column [k][j]
   bool fused;
   int fuse_cols, fuse_threads;
   size_t fuse_smem;
@@ -687,6 +688,35 @@ void enqueue_refine(sp_plan_t p, const double* in, double* out, void* ws, cudaSt
   m.mark(0);
   rows_forward_stage<dd>(p, false, st, in, Fd, twr, por, p->row_scale, static_cast<const dd*>(p->row_scale_t),
                          nullptr, ov);
+  if (p->fused) {
+    // column 0 on the side stream: its double-float colatitude transforms
+    // bracket the FP64 zonal eliminations; every other column in the fused
+    // stage on the main stream, in place in Fd
+    m.mark(1);
+    const cpx<dd>* pcs = static_cast<const cpx<dd>*>(p->post_col_s_t);
+    cudaEventRecord(p->ev_fork, st);
+    cudaStreamWaitEvent(p->side, p->ev_fork, 0);
+    launch_theta_forward_x<dd>(p, false, p->side, Fd, p->N, 1, p->Kp, p->cols_per_cta, p->col_fft, twc,
+                               p->perm_col, pcs, inv_n, 0);
+    const int zt = 256;
+    sp::launch_zonal_extract(Launch{dim3((p->N + zt - 1) / zt), zt, 0, p->side}, Fd, Z, p->N, p->Kp);
+    sp::launch_zonal_scan(false, p->side, Z, p->z_l, p->z_iu, p->z_cu, p->N);
+    sp::launch_zonal_insert(Launch{dim3(1), 512, 0, p->side}, Z, Fd, p->N, p->Kp);
+    launch_theta_inverse_x<dd>(p, false, p->side, Fd, p->N, 1, p->Kp, p->cols_per_cta, p->col_fft, twc,
+                               p->perm_col, poc, inv_n, 0);
+    cudaEventRecord(p->ev_join, p->side);
+    sp::launch_refine_fused(p->big_col, Launch{dim3(1), p->fuse_threads, p->fuse_smem, st}, Fd, p->N, p->K, p->Kp,
+                            p->col_fft, twc, p->perm_col, pcs, poc, p->fc_iu, p->sweeps);
+    m.mark(2);
+    m.mark(3);
+    cudaStreamWaitEvent(st, p->ev_join, 0);
+    m.mark(4);
+    rows_inverse_stage<dd>(p, false, st, Fd, out, twr, por, p->row_scale, static_cast<const dd*>(p->row_scale_t),
+                           nullptr, ov);
+    m.mark(5);
+    m.done();
+    return;
+  }
   m.mark(1);
   launch_theta_forward_x<dd>(p, false, st, Fd, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
                                twc, p->perm_col, static_cast<const cpx<dd>*>(p->post_col_s_t), inv_n, 0);
@@ -783,10 +813,18 @@ cudaError_t allow_all_smem(int device) {
 }
 
 bool set_fused_tile(sp_plan_t p, int cols, int threads) {
-  // cols > 0: two buffers, cols columns per CTA; cols < 0: one buffer, -cols
-  // columns per CTA; cols = 0: the cluster form (one column per CTA, four CTAs
-  // per cluster)
-  if (p->precision != SP_FP32 || threads < 64) return false;
+  // FP32: cols > 0: two buffers, cols columns per CTA; cols < 0: one buffer,
+  // -cols columns per CTA; cols = 0: the cluster form (one column per CTA, four
+  // CTAs per cluster).  FP32 + refinement: one column per CTA (cols ignored).
+  if (p->batched || p->precision == SP_FP64 || threads < 64) return false;
+  if (p->precision == SP_FP32_REFINE) {
+    const size_t smem = sp::refine_fused_smem(p->N, threads);
+    if (smem > 220 * 1024) return false;
+    p->fuse_cols = 1;
+    p->fuse_threads = threads;
+    p->fuse_smem = smem;
+    return true;
+  }
   const size_t smem = sp::theta_fused_smem(p->N, cols, threads);
   if (smem > 220 * 1024 || 2 * std::max(std::abs(cols), 1) * 32 > threads) return false;
   p->fuse_cols = cols;
@@ -962,7 +1000,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   const size_t fac64 = precision == SP_FP64 ? grid * sizeof(double) : 0;
   const size_t fac32 = precision == SP_FP64 ? 0 : grid * sizeof(float);
   const size_t facz = precision == SP_FP64 ? 0 : (size_t)p->N * 2 * sizeof(double);
-  const size_t faccol = precision == SP_FP32 ? (size_t)p->K * p->N * sizeof(float) : 0;
+  const size_t faccol = precision != SP_FP64 ? (size_t)p->K * p->N * sizeof(float) : 0;
   const size_t o_fac_begin = off;
   size_t o_l = take(fac64), o_iu = take(fac64), o_cu = take(fac64);
   size_t o_l32 = take(fac32), o_iu32 = take(fac32), o_cu32 = take(fac32);
@@ -1090,8 +1128,8 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
       sp::launch_factor<float>(sp::Launch{dim3(blocks), threads, 0, 0}, p->f32_l, p->f32_iu, p->f32_cu, p->N,
                                p->K, p->Kp, true);
       sp::launch_factor<double>(sp::Launch{dim3(1), threads, 0, 0}, p->z_l, p->z_iu, p->z_cu, p->N, 1, 2, false);
-      if (precision == SP_FP32)   // per-column top-down tables of the fused colatitude stage
-        sp::launch_factor_cols(sp::Launch{dim3(blocks), threads, 0, 0}, p->fc_iu, p->N, p->K);
+      // per-column pivots of the fused colatitude stages
+      sp::launch_factor_cols(sp::Launch{dim3(blocks), threads, 0, 0}, p->fc_iu, p->N, p->K);
     }
     step(cudaGetLastError(), "k_factor launch");
     step(cudaDeviceSynchronize(), "k_factor");
@@ -1111,8 +1149,11 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   step(configure_pipes(p), "pipelined kernels");
   // the FP32 form fuses its colatitude stages: one column per CTA, the widest
   // thread count the kernel allows (the tuner may choose otherwise)
-  p->fused = precision == SP_FP32 && (set_fused_tile(p, p->Kp >= 2 ? -2 : -1, p->big_col ? 256 : 512) ||
-                                      set_fused_tile(p, -1, p->big_col ? 256 : 512));
+  if (precision == SP_FP32)
+    p->fused = set_fused_tile(p, p->Kp >= 2 ? -2 : -1, p->big_col ? 256 : 512) ||
+               set_fused_tile(p, -1, p->big_col ? 256 : 512);
+  else if (precision == SP_FP32_REFINE)
+    p->fused = set_fused_tile(p, 1, p->big_col ? 256 : 512) || set_fused_tile(p, 1, 256);
   if (rc == SP_OK && (flags & SP_FLAG_AUTOTUNE)) rc = tune_single(p);
   if (rc != SP_OK) {
     destroy_plan(p);
@@ -1231,7 +1272,7 @@ int tune_single(sp_plan_t p) {
       const std::vector<double>& v = it->second;
       set_rows((int)v[0], (int)v[1], v[4] != 0.0);
       set_cols((int)v[2], (int)v[3], v[5] != 0.0);
-      if (v.size() >= 10 && p->precision == SP_FP32)
+      if (v.size() >= 10 && p->precision != SP_FP64)
         p->fused = v[7] != 0.0 && set_fused_tile(p, (int)v[8], (int)v[9]);
       return SP_OK;
     }
@@ -1314,7 +1355,9 @@ int tune_single(sp_plan_t p) {
     if (fused0) {
       bool bf = false;
       int bfc = fc0, bft = ft0;
-      for (int q : {-1, -2, -4, 0, 1, 2, 4})
+      const std::vector<int> tiles = p->precision == SP_FP32 ? std::vector<int>{-1, -2, -4, 0, 1, 2, 4}
+                                                             : std::vector<int>{1};
+      for (int q : tiles)
         for (int t = 128; t <= cap_c; t *= 2) {
           if (std::abs(q) > p->Kp) continue;
           if (!set_fused_tile(p, q, t)) continue;
@@ -2272,7 +2315,8 @@ int sphere_poisson_launch_count(sp_plan_t plan, int adjoint, int* launches) {
   if (plan->batched) *launches = plan->count ? 1 : 0;
   else if (plan->precision == SP_FP64) *launches = kStages;
   else if (plan->precision == SP_FP32) *launches = (plan->fused && !adjoint ? kStages - 2 : kStages) + 3;
-  else *launches = adjoint ? 0 : kStages - 1 + 3 + (plan->sweeps + 1);
+  else if (adjoint) *launches = 0;
+  else *launches = plan->fused ? 3 + 5 : kStages - 1 + 3 + (plan->sweeps + 1);
   return SP_OK;
 }
 
