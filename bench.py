@@ -48,26 +48,36 @@ FP64_PEAK_GFLOPS_FALLBACK = 1008.0
 # spectrum size n_theta * Kp (every stage streams the spectrum once or twice) and
 # reports null when the sources have changed since the capture.
 TRAFFIC_CAPTURE = {
-    "csrc_sha256": "07d91de96aafe39d",
+    "csrc_sha256": "71476f62e5e892ce",
     "n_theta": 5000, "n_lambda": 5000,
-    "bytes": {"rows_forward": 200275200 + 142569472, "theta_forward": 200852224 + 142159616,
-              "solve": 662269952 + 321523200, "theta_inverse": 200989952 + 142168832,
-              "rows_inverse": 200773376 + 143161344},
+    "bytes": {"rows_forward": 200250624 + 143131904, "theta_forward": 200877312 + 141872384,
+              "solve": 662319616 + 321766400, "theta_inverse": 200901376 + 142283008,
+              "rows_inverse": 200384512 + 143336960},
+}
+# the same for the FP32 form's dominant kernel, the fused colatitude stage
+# (k_theta_fused1, one column per CTA at 5000 x 5000; `ncu --section ...
+# --metrics dram__bytes_read.sum,dram__bytes_write.sum` on two launches after
+# warm-up), over the sources it is compiled from
+TRAFFIC_CAPTURE_FP32 = {
+    "csrc_sha256": "1a2315eaa565f784",
+    "n_theta": 5000, "n_lambda": 5000,
+    "bytes": {"theta_fused": 150854144 + 47709696},
 }
 
 
 # the sources the five stage kernels of the solve are compiled from (the
 # operators of calculus.cuh and the plan code do not enter their code)
 TRAFFIC_SOURCES = ("fft.cuh", "kernels.cuh", "launchers.inl")
+TRAFFIC_SOURCES_FP32 = ("fft.cuh", "kernels.cuh", "launchers.inl", "fused.cuh")
 
 
-def csrc_hash() -> str:
+def csrc_hash(sources=TRAFFIC_SOURCES) -> str:
     """First 16 hex digits of SHA-256 over the stage kernels' sources (names and bytes)."""
     import hashlib
 
     d = os.path.join(ROOT, "paper_1510_08094_gb300", "csrc")
     h = hashlib.sha256()
-    for n in TRAFFIC_SOURCES:
+    for n in sources:
         h.update(n.encode())
         with open(os.path.join(d, n), "rb") as fh:
             h.update(fh.read())
@@ -77,10 +87,15 @@ def csrc_hash() -> str:
 def traffic_for(stage: str, n_theta: int, n_lambda: int, precision: str):
     """(bytes per launch, note) of an FP64 stage kernel scaled from the ncu capture,
     or (None, why) when no capture of the current sources exists."""
-    cap = TRAFFIC_CAPTURE
-    if precision != "fp64":
-        return None, "no ncu traffic capture of the reduced-precision kernels on these sources"
-    if csrc_hash() != cap["csrc_sha256"]:
+    if precision == "fp64":
+        cap, sources = TRAFFIC_CAPTURE, TRAFFIC_SOURCES
+    elif precision == "fp32":
+        cap, sources = TRAFFIC_CAPTURE_FP32, TRAFFIC_SOURCES_FP32
+    else:
+        return None, "no ncu traffic capture of the double-float kernels on these sources"
+    if stage not in cap["bytes"]:
+        return None, f"no ncu traffic capture of the {stage} kernel"
+    if csrc_hash(sources) != cap["csrc_sha256"]:
         return None, "kernel sources changed since the ncu traffic capture"
     kp = lambda nl: (nl // 2 + 2) // 2 * 2
     ratio = (n_theta * kp(n_lambda)) / (cap["n_theta"] * kp(cap["n_lambda"]))

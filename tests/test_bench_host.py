@@ -48,13 +48,20 @@ def test_whole_job_value_counts_every_rank():
 
 def test_traffic_is_scaled_from_the_capture_and_withheld_on_changed_sources(monkeypatch):
     cap = bench.TRAFFIC_CAPTURE
-    monkeypatch.setattr(bench, "csrc_hash", lambda: cap["csrc_sha256"])
+    cap32 = bench.TRAFFIC_CAPTURE_FP32
+    monkeypatch.setattr(bench, "csrc_hash",
+                        lambda sources=bench.TRAFFIC_SOURCES: cap32["csrc_sha256"] if "fused.cuh" in sources
+                        else cap["csrc_sha256"])
     t, note = bench.traffic_for("theta_inverse", cap["n_theta"], cap["n_lambda"], "fp64")
     assert t == cap["bytes"]["theta_inverse"]
     t2, _ = bench.traffic_for("theta_inverse", 5000, 10000, "fp64")
     assert t2 == int(cap["bytes"]["theta_inverse"] * (5000 * 5002) / (5000 * 2502))
+    # the FP32 form has a capture of its fused colatitude stage only
     assert bench.traffic_for("theta_inverse", 5000, 10000, "fp32")[0] is None
-    monkeypatch.setattr(bench, "csrc_hash", lambda: "0" * 16)
+    t32, _ = bench.traffic_for("theta_fused", 5000, 10000, "fp32")
+    assert t32 == int(cap32["bytes"]["theta_fused"] * (5000 * 5002) / (5000 * 2502))
+    assert bench.traffic_for("theta_fused", 5000, 10000, "fp32_refine")[0] is None
+    monkeypatch.setattr(bench, "csrc_hash", lambda sources=bench.TRAFFIC_SOURCES: "0" * 16)
     t3, why = bench.traffic_for("theta_inverse", 5000, 10000, "fp64")
     assert t3 is None and "changed" in why
 
@@ -62,5 +69,5 @@ def test_traffic_is_scaled_from_the_capture_and_withheld_on_changed_sources(monk
 def test_source_hash_covers_the_stage_kernel_sources():
     h = bench.csrc_hash()
     assert len(h) == 16 and all(c in "0123456789abcdef" for c in h)
-    for name in bench.TRAFFIC_SOURCES:
+    for name in bench.TRAFFIC_SOURCES + bench.TRAFFIC_SOURCES_FP32:
         assert os.path.exists(os.path.join(ROOT, "paper_1510_08094_gb300", "csrc", name))
