@@ -69,6 +69,43 @@ __device__ __forceinline__ dd dd_fma(dd a, dd b, dd c) {
   return {hi, lo};
 }
 
+// Unnormalised forms for values that feed further double-float operations
+// inside one butterfly: the same operations without the final renormalisation
+// (FastTwoSum, three operations), returning (hi, lo) with hi + lo the same
+// value and |lo| a few ulp(hi) instead of at most half of one.  TwoSum and the
+// FMA TwoProduct are exact for any float inputs, so the next operation loses
+// nothing but the last bit or two of the lo parts' FP32 sum; stored results go
+// through dd_norm.
+__device__ __forceinline__ dd dd_norm(dd a) {
+  float hi = __fadd_rn(a.hi, a.lo);
+  float lo = __fsub_rn(a.lo, __fsub_rn(hi, a.hi));
+  return {hi, lo};
+}
+__device__ __forceinline__ dd dd_add_u(dd a, dd b) {
+  float s = __fadd_rn(a.hi, b.hi);
+  float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return {s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
+}
+__device__ __forceinline__ dd dd_sub_u(dd a, dd b) { return dd_add_u(a, dd(-b.hi, -b.lo)); }
+__device__ __forceinline__ dd dd_mul_u(dd a, dd b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return {p, e};
+}
+__device__ __forceinline__ dd dd_fma_u(dd a, dd b, dd c) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  float s = __fadd_rn(p, c.hi);
+  float bb = __fsub_rn(s, p);
+  float t = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(c.hi, bb));
+  return {s, __fadd_rn(t, __fadd_rn(e, c.lo))};
+}
+
 __device__ __forceinline__ dd operator+(dd a, dd b) { return dd_add(a, b); }
 __device__ __forceinline__ dd operator-(dd a, dd b) { return dd_sub(a, b); }
 __device__ __forceinline__ dd operator-(dd a) { return dd_neg(a); }

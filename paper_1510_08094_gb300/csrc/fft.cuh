@@ -337,6 +337,108 @@ __device__ __forceinline__ void dft_odd(cpx<T>* v, const cpx<T>* __restrict__ dt
   v[0] = y0;
 }
 
+// ---------------------------------------------------------------------------
+// Double-float butterflies: the same formulas, with every value that only
+// feeds further operations of the butterfly kept unnormalised (dd.cuh) and
+// every output normalised before it is stored.  The twiddle products are left
+// unnormalised too: they feed the DFT (decimation in time), or are normalised
+// by the decimation-in-frequency pass that stores them.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ cpx<dd> cdd_add(cpx<dd> a, cpx<dd> b) { return {dd_add_u(a.re, b.re), dd_add_u(a.im, b.im)}; }
+__device__ __forceinline__ cpx<dd> cdd_sub(cpx<dd> a, cpx<dd> b) { return {dd_sub_u(a.re, b.re), dd_sub_u(a.im, b.im)}; }
+__device__ __forceinline__ cpx<dd> cdd_norm(cpx<dd> a) { return {dd_norm(a.re), dd_norm(a.im)}; }
+// s x + t for a real double-float s
+__device__ __forceinline__ cpx<dd> cdd_fmas(dd s, cpx<dd> x, cpx<dd> t) {
+  return {dd_fma_u(s, x.re, t.re), dd_fma_u(s, x.im, t.im)};
+}
+__device__ __forceinline__ dd dd_flip(dd a) { return {-a.hi, -a.lo}; }
+template <typename T> __device__ __forceinline__ cpx<T> out_norm(cpx<T> a) { return a; }
+template <> __device__ __forceinline__ cpx<dd> out_norm<dd>(cpx<dd> a) { return cdd_norm(a); }
+
+template <int DIR> __device__ __forceinline__ cpx<dd> twmul(cpx<dd> a, cpx<dd> w) {
+  if (DIR < 0)   // a w
+    return {dd_fma_u(a.re, w.re, dd_flip(dd_mul_u(a.im, w.im))), dd_fma_u(a.re, w.im, dd_mul_u(a.im, w.re))};
+  // a conj(w)
+  return {dd_fma_u(a.re, w.re, dd_mul_u(a.im, w.im)), dd_fma_u(a.im, w.re, dd_flip(dd_mul_u(a.re, w.im)))};
+}
+
+template <int DIR> __device__ __forceinline__ void dft2(cpx<dd>* v) {
+  const cpx<dd> a = v[0], b = v[1];
+  v[0] = cdd_norm(cdd_add(a, b));
+  v[1] = cdd_norm(cdd_sub(a, b));
+}
+
+template <int DIR> __device__ __forceinline__ void dft4(cpx<dd>* v) {
+  const cpx<dd> s0 = cdd_add(v[0], v[2]), d0 = cdd_sub(v[0], v[2]);
+  const cpx<dd> s1 = cdd_add(v[1], v[3]), d1 = rot<DIR>(cdd_sub(v[1], v[3]));
+  v[0] = cdd_norm(cdd_add(s0, s1));
+  v[2] = cdd_norm(cdd_sub(s0, s1));
+  v[1] = cdd_norm(cdd_add(d0, d1));
+  v[3] = cdd_norm(cdd_sub(d0, d1));
+}
+
+// y = t + DIR i s w and y' = t - DIR i s w for real s, normalised
+template <int DIR>
+__device__ __forceinline__ void plus_minus_i(cpx<dd> t, dd s, cpx<dd> w, cpx<dd>& y, cpx<dd>& yc) {
+  const dd g = DIR < 0 ? s : dd_flip(s);
+  y = {dd_norm(dd_fma_u(g, w.im, t.re)), dd_norm(dd_fma_u(dd_flip(g), w.re, t.im))};
+  yc = {dd_norm(dd_fma_u(dd_flip(g), w.im, t.re)), dd_norm(dd_fma_u(g, w.re, t.im))};
+}
+
+template <int DIR> __device__ __forceinline__ void dft3(cpx<dd>* v) {
+  const dd c(-0.5), s(0.86602540378443864676372317075293618347);
+  const cpx<dd> a = cdd_add(v[1], v[2]), b = cdd_sub(v[1], v[2]);
+  const cpx<dd> t = cdd_fmas(c, a, v[0]);
+  const cpx<dd> x0 = v[0];
+  v[0] = cdd_norm(cdd_add(x0, a));
+  plus_minus_i<DIR>(t, s, b, v[1], v[2]);
+}
+
+template <int DIR> __device__ __forceinline__ void dft5(cpx<dd>* v) {
+  const dd q5(0.55901699437494742410229341718281905886), s1(0.95105651629515357211643933337938214340),
+      s2(0.58778525229247312916870595463907276860), r(0.61803398874989484820458683436563811772),
+      ri(1.61803398874989484820458683436563811772), quarter(-0.25);
+  const cpx<dd> a1 = cdd_add(v[1], v[4]), b1 = cdd_sub(v[1], v[4]);
+  const cpx<dd> a2 = cdd_add(v[2], v[3]), b2 = cdd_sub(v[2], v[3]);
+  const cpx<dd> x0 = v[0];
+  const cpx<dd> S = cdd_add(a1, a2), D = cdd_sub(a1, a2);
+  const cpx<dd> m = cdd_fmas(quarter, S, x0);
+  const cpx<dd> t1 = cdd_fmas(q5, D, m), t2 = cdd_fmas(dd_flip(q5), D, m);
+  const cpx<dd> w1 = cdd_fmas(r, b2, b1), w2 = cdd_fmas(dd_flip(ri), b2, b1);
+  v[0] = cdd_norm(cdd_add(x0, S));
+  plus_minus_i<DIR>(t1, s1, w1, v[1], v[4]);
+  plus_minus_i<DIR>(t2, s2, w2, v[2], v[3]);
+}
+
+template <int DIR> __device__ __forceinline__ void dft8(cpx<dd>* v) {
+  const dd h(0.70710678118654752440084436210484903928);
+  cpx<dd> e[4] = {v[0], v[2], v[4], v[6]};
+  cpx<dd> o[4] = {v[1], v[3], v[5], v[7]};
+  {
+    const cpx<dd> s0 = cdd_add(e[0], e[2]), d0 = cdd_sub(e[0], e[2]), s1 = cdd_add(e[1], e[3]),
+                  d1 = rot<DIR>(cdd_sub(e[1], e[3]));
+    e[0] = cdd_add(s0, s1); e[2] = cdd_sub(s0, s1); e[1] = cdd_add(d0, d1); e[3] = cdd_sub(d0, d1);
+  }
+  {
+    const cpx<dd> s0 = cdd_add(o[0], o[2]), d0 = cdd_sub(o[0], o[2]), s1 = cdd_add(o[1], o[3]),
+                  d1 = rot<DIR>(cdd_sub(o[1], o[3]));
+    o[0] = cdd_add(s0, s1); o[2] = cdd_sub(s0, s1); o[1] = cdd_add(d0, d1); o[3] = cdd_sub(d0, d1);
+  }
+  // as in the generic dft8: W8 o1 = h (p1, q1), W8^3 o3 = h (ha p3, hb q3)
+  const dd p1 = DIR < 0 ? dd_add_u(o[1].re, o[1].im) : dd_sub_u(o[1].re, o[1].im);
+  const dd q1 = DIR < 0 ? dd_sub_u(o[1].im, o[1].re) : dd_add_u(o[1].im, o[1].re);
+  const dd p3 = DIR < 0 ? dd_sub_u(o[3].im, o[3].re) : dd_add_u(o[3].re, o[3].im);
+  const dd q3 = DIR < 0 ? dd_add_u(o[3].re, o[3].im) : dd_sub_u(o[3].re, o[3].im);
+  const dd ha = DIR < 0 ? h : dd_flip(h), hb = DIR < 0 ? dd_flip(h) : h;
+  const cpx<dd> t2 = rot<DIR>(o[2]);
+  v[0] = cdd_norm(cdd_add(e[0], o[0])); v[4] = cdd_norm(cdd_sub(e[0], o[0]));
+  v[1] = {dd_norm(dd_fma_u(h, p1, e[1].re)), dd_norm(dd_fma_u(h, q1, e[1].im))};
+  v[5] = {dd_norm(dd_fma_u(dd_flip(h), p1, e[1].re)), dd_norm(dd_fma_u(dd_flip(h), q1, e[1].im))};
+  v[2] = cdd_norm(cdd_add(e[2], t2)); v[6] = cdd_norm(cdd_sub(e[2], t2));
+  v[3] = {dd_norm(dd_fma_u(ha, p3, e[3].re)), dd_norm(dd_fma_u(hb, q3, e[3].im))};
+  v[7] = {dd_norm(dd_fma_u(dd_flip(ha), p3, e[3].re)), dd_norm(dd_fma_u(dd_flip(hb), q3, e[3].im))};
+}
+
 template <int R, int DIR, typename T>
 __device__ __forceinline__ void dft_any(cpx<T>* v, const cpx<T>* __restrict__ dtw) {
   if constexpr (R == 2) dft2<DIR>(v);
@@ -620,7 +722,7 @@ __device__ __forceinline__ void fft_pass_dif(cpx<T>* buf, int L, int nbatch, int
         cpx<T> w[R];
         load_stage_tw<R>(tk, w);
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[r] = twmul<DIR>(v[r], w[r]);
+        for (int r = 1; r < R; ++r) v[r] = out_norm<T>(twmul<DIR>(v[r], w[r]));
       }
 #pragma unroll
       for (int r = 0; r < R; ++r) base[r * Ns] = v[r];
@@ -657,8 +759,8 @@ __device__ __forceinline__ void fft_pass_dif(cpx<T>* buf, int L, int nbatch, int
         cpx<T> iB = DIR < 0 ? cpx<T>{B.im, -B.re} : cpx<T>{-B.im, B.re};
         cpx<T> ya = A + iB, yb = A - iB;
         if (Ns > 1) {
-          ya = twmul<DIR>(ya, ldg_c(tk + a));
-          yb = twmul<DIR>(yb, ldg_c(tk + (R - a)));
+          ya = out_norm<T>(twmul<DIR>(ya, ldg_c(tk + a)));
+          yb = out_norm<T>(twmul<DIR>(yb, ldg_c(tk + (R - a))));
         }
         base[a * Ns] = ya;
         base[(R - a) * Ns] = yb;
