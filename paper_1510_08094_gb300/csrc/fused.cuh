@@ -130,6 +130,17 @@ __device__ __forceinline__ void chain_carry_scan(ScanSlot<T>* slot, int stride, 
 // The eliminations of a tile and its row-0 closure, in place in X (the
 // forward transform's output; coefficient (j, column c) at X[j js + c cs]), by
 // the chunked scans described above.  Whole CTA; ends with a barrier.
+// A thread's chunk of C rows needs the pivots 1/u_{s-1} .. 1/u_{e-1}: l_t on
+// the way down, 1/u_t on the way up.  When C + 1 <= 24 they are read from the
+// table once, into R registers (R = 12, 18 or 24, the smallest that holds
+// them: the passes are unrolled R - 1 times), before the first scan; the four
+// scan passes would otherwise each read them again.  Longer chunks read the
+// table in every pass.
+template <typename T, int R>
+__device__ __forceinline__ void fused_solve_reg(cpx<T>* __restrict__ X, int js, int cs,
+                                                ScanSlot<T>* __restrict__ slot, int k0, int cols, int N, int K,
+                                                const T* __restrict__ fiu);
+
 template <typename T>
 __device__ __forceinline__ void fused_solve(cpx<T>* __restrict__ X, int js, int cs,
                                             ScanSlot<T>* __restrict__ slot, int k0, int cols, int N, int K,
@@ -143,6 +154,14 @@ __device__ __forceinline__ void fused_solve(cpx<T>* __restrict__ X, int js, int 
   const int k = k0 + c;
   const int M = (j0 < N) ? (N - 1 - j0) / 2 + 1 : 0;
   const int C = ((M + P - 1) / P) | 1;        // odd, so that the chunks' rows spread over the banks
+  // (C is the same for both parities: M differs by at most one row, and the rounding to odd absorbs it)
+  {
+    const int M1 = (1 < N) ? (N - 2) / 2 + 1 : 0;
+    const int C1 = ((M1 + P - 1) / P) | 1;
+    if (C1 + 1 <= 12) return fused_solve_reg<T, 12>(X, js, cs, slot, k0, cols, N, K, fiu);
+    if (C1 + 1 <= 18) return fused_solve_reg<T, 18>(X, js, cs, slot, k0, cols, N, K, fiu);
+    if (C1 + 1 <= 24) return fused_solve_reg<T, 24>(X, js, cs, slot, k0, cols, N, K, fiu);
+  }
   const int s = min(M, p * C), e = min(M, s + C);
   const bool live = k < K && p < P;
   const size_t tcol = (size_t)(live ? k : 0) * N;
@@ -219,6 +238,126 @@ __device__ __forceinline__ void fused_solve(cpx<T>* __restrict__ X, int js, int 
   __syncthreads();
   // row 0: k even != 0: X_0 = (X_2 - F_0)/k^2 (row 0 with X_{-2,k} = X_{2,k});
   // k odd: X_0 = 0; k = 0: left to the FP64 zonal column
+  if (threadIdx.x < cols) {
+    const int kc = k0 + threadIdx.x;
+    if (kc < K && kc != 0) {
+      cpx<T>& x0 = X[threadIdx.x * cs];
+      if (kc & 1) {
+        x0 = {(T)0, (T)0};
+      } else {
+        const T ik2 = (T)(1.0 / ((double)kc * (double)kc));
+        const cpx<T> x2 = N > 2 ? X[2 * js + threadIdx.x * cs] : cpx<T>{(T)0, (T)0};
+        x0 = {(x2.re - x0.re) * ik2, (x2.im - x0.im) * ik2};
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// fused_solve with the chunk's pivots in registers (C + 1 <= R): the same
+// scans, passes and row-0 closure.  Whole CTA; ends with a barrier.
+template <typename T, int R>
+__device__ __forceinline__ void fused_solve_reg(cpx<T>* __restrict__ X, int js, int cs,
+                                                ScanSlot<T>* __restrict__ slot, int k0, int cols, int N, int K,
+                                                const T* __restrict__ fiu) {
+  const int chains = 2 * cols;
+  const int ch = threadIdx.x % chains, p = threadIdx.x / chains;
+  const int P = blockDim.x / chains;
+  const int c = ch >> 1, j0 = (ch & 1) ? 2 : 1;
+  const int k = k0 + c;
+  const int M = (j0 < N) ? (N - 1 - j0) / 2 + 1 : 0;
+  const int C = ((M + P - 1) / P) | 1;
+  const int s = min(M, p * C), e = min(M, s + C);
+  const bool live = k < K && p < P;
+  const size_t tcol = (size_t)(live ? k : 0) * N;
+  ScanSlot<T>* mine = slot + threadIdx.x;
+  cpx<T>* Xc = X + c * cs;
+  // iu[q] = 1/u_{s-1+q} for q = 0 .. e - s (zero where t < 0 or past the chunk)
+  T iu[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int t = s - 1 + q;
+    iu[q] = (live && t >= 0 && t < e) ? __ldg(fiu + tcol + j0 + 2 * t) : (T)0;
+  }
+  // forward sweep y_t = d_t - l_t y_{t-1}, l_t = a_j / u_{t-1} (l_0 = 0 since iu[0] = 0 at s = 0)
+  {
+    T A = (T)1;
+    cpx<T> y = {(T)0, (T)0};
+#pragma unroll
+    for (int q = 0; q < R - 1; ++q) {
+      const int t = s + q;
+      if (live && t < e) {
+        const int j = j0 + 2 * t;
+        const T l = band_a<T>(j) * iu[q];
+        const cpx<T> dv = Xc[j * js];
+        y = {fma(-l, y.re, dv.re), fma(-l, y.im, dv.im)};
+        A = A * (-l);
+      }
+    }
+    mine->a = A;
+    mine->z = y;
+  }
+  __syncthreads();
+  {
+    const int w = threadIdx.x >> 5;
+    if (w < chains && k0 + (w >> 1) < K) chain_carry_scan(slot + w, chains, P, false);
+  }
+  __syncthreads();
+  {
+    cpx<T> y = mine->z;
+#pragma unroll
+    for (int q = 0; q < R - 1; ++q) {
+      const int t = s + q;
+      if (live && t < e) {
+        const int j = j0 + 2 * t;
+        const T l = band_a<T>(j) * iu[q];
+        cpx<T>& dv = Xc[j * js];
+        y = {fma(-l, y.re, dv.re), fma(-l, y.im, dv.im)};
+        dv = y;
+      }
+    }
+  }
+  __syncthreads();
+  // backward sweep x_t = iu_t y_t - cu_t x_{t+1} (t decreasing), iu_t = iu[t - s + 1]
+  {
+    T A = (T)1;
+    cpx<T> x = {(T)0, (T)0};
+#pragma unroll
+    for (int q = R - 2; q >= 0; --q) {
+      const int t = s + q;
+      if (live && t < e) {
+        const int j = j0 + 2 * t;
+        const T u = iu[q + 1], cu = band_c<T>(j) * u;
+        const cpx<T> yv = Xc[j * js];
+        x = {fma(u, yv.re, -cu * x.re), fma(u, yv.im, -cu * x.im)};
+        A = A * (-cu);
+      }
+    }
+    mine->a = A;
+    mine->z = x;
+  }
+  __syncthreads();
+  {
+    const int w = threadIdx.x >> 5;
+    if (w < chains && k0 + (w >> 1) < K) chain_carry_scan(slot + w, chains, P, true);
+  }
+  __syncthreads();
+  {
+    cpx<T> x = mine->z;
+#pragma unroll
+    for (int q = R - 2; q >= 0; --q) {
+      const int t = s + q;
+      if (live && t < e) {
+        const int j = j0 + 2 * t;
+        const T u = iu[q + 1], cu = band_c<T>(j) * u;
+        cpx<T>& yv = Xc[j * js];
+        x = {fma(u, yv.re, -cu * x.re), fma(u, yv.im, -cu * x.im)};
+        yv = x;
+      }
+    }
+  }
+  __syncthreads();
+  // row 0 as in fused_solve
   if (threadIdx.x < cols) {
     const int kc = k0 + threadIdx.x;
     if (kc < K && kc != 0) {
