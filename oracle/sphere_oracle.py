@@ -38,7 +38,9 @@ The per-k systems are solved by dense LU (numpy.linalg.solve) at small m and
 by LAPACK's banded LU (scipy.linalg.solve_banded) otherwise; neither uses the
 parity split or the BMC fold, which are properties the tests check.
 
-Also here: the structure-preserving GE of Section 3 and the low-rank form of
+Also here: the same solve on the grid with both poles (theta_i = i pi /
+n_theta, i = 0..n_theta; the DFS grid theta_p = -pi + 2 pi p / m, the same
+per-k systems), the structure-preserving GE of Section 3 and the low-rank form of
 the coefficients F, the surface integral sum2 (Section 4, Integration, eq.
 integrationCoeffs), the tangential derivatives of Section 4 (Differentiation,
 eqs. diff_x..diff_z with the division by sin theta through M_sin^{-1}) and the
@@ -308,6 +310,95 @@ def poisson(f: np.ndarray, reading: str = "B", method: str = "auto", return_all:
     F = rhs_coefficients(f)
     X = solve_columns(F, reading, method)
     U = sample(X)[nt:]
+    u = U.real.copy()
+    if return_all:
+        return u, F, X, float(np.abs(U.imag).max())
+    return u
+
+
+# ----------------------------------------------------------------------------
+# The grid with both poles (Section 2: the DFS grid of a function sampled on
+# theta in [0, pi], the poles included)
+#
+# theta_i = i pi / n_theta, i = 0..n_theta (n_theta + 1 rows, both poles);
+# doubled, theta_p = -pi + 2 pi p / m, p = 0..m-1, m = 2 n_theta: row p =
+# n_theta + i holds theta_i (i = 0..n_theta-1) and row p = n_theta - i holds
+# -theta_i (i = 1..n_theta; p = 0 is theta = -pi, the south pole seen from the
+# other side).  The per-k systems are those of the pole-free grid (they act on
+# coefficients, not samples; reading B, theta-Nyquist mode dropped), only the
+# samples change.
+# ----------------------------------------------------------------------------
+
+def pole_colatitudes(n_theta: int) -> np.ndarray:
+    """theta_i = i pi / n_theta, i = 0..n_theta."""
+    return np.arange(n_theta + 1, dtype=np.float64) * math.pi / n_theta
+
+
+def dfs_theta_poles(m: int) -> np.ndarray:
+    """theta_p = -pi + 2 pi p / m, p = 0..m-1."""
+    return -math.pi + 2.0 * math.pi * np.arange(m, dtype=np.float64) / m
+
+
+def dfs_double_poles(f: np.ndarray) -> np.ndarray:
+    """eq. BMCsphere on the grid with poles: f has n_theta + 1 rows
+    (theta_0 = 0 .. theta_{n_theta} = pi); ftilde has m = 2 n_theta rows.
+    Rows p >= n_theta: ftilde = f row p - n_theta.  Rows p < n_theta hold
+    theta_p = -theta_{n_theta - p}: ftilde(lambda, theta_p) = f(lambda + pi,
+    theta_{n_theta - p}) (the shift q -> q + n/2)."""
+    f = np.asarray(f, dtype=np.float64)
+    rows, n = f.shape
+    nt = rows - 1
+    if n % 2 or nt < 1:
+        raise ValueError("n_lambda must be even and n_theta >= 1")
+    ft = np.empty((2 * nt, n), dtype=np.float64)
+    ft[nt:] = f[:nt]
+    shifted = np.roll(f, -(n // 2), axis=1)
+    ft[:nt] = shifted[nt:0:-1]                     # row p <- f row n_theta - p, p = 0..n_theta-1
+    return ft
+
+
+def _phase_theta_poles(m: int) -> np.ndarray:
+    """E[j + m/2, p] = exp(-i j theta_p), j theta_p = pi j (2p - m) / m reduced exactly."""
+    j = np.arange(-m // 2, m // 2, dtype=np.int64)[:, None]
+    p = np.arange(m, dtype=np.int64)[None, :]
+    r = np.mod(j * (2 * p - m), 2 * m).astype(np.float64)
+    ang = math.pi * r / m
+    return np.cos(ang) - 1j * np.sin(ang)
+
+
+def coeffs2_poles(values: np.ndarray) -> np.ndarray:
+    """Naive 2D DFT of values on the m x n DFS grid with poles, normalised by 1/(mn)."""
+    m, n = values.shape
+    return (_phase_theta_poles(m) @ values @ _phase_lambda(n).T) / (m * n)
+
+
+def sample_poles(X: np.ndarray) -> np.ndarray:
+    """Inverse of coeffs2_poles: sum_jk X_jk exp(i j theta_p) exp(i k lambda_q) (complex)."""
+    m, n = X.shape
+    return _phase_theta_poles(m).conj().T @ X @ _phase_lambda(n).conj()
+
+
+def rhs_coefficients_poles(f: np.ndarray) -> np.ndarray:
+    """F of eq. SylvesterSphericalPoisson from samples on the grid with poles."""
+    ft = dfs_double_poles(f)
+    m, _ = ft.shape
+    s2 = np.sin(dfs_theta_poles(m)) ** 2
+    return coeffs2_poles(s2[:, None] * ft)
+
+
+def poisson_poles(f: np.ndarray, reading: str = "B", method: str = "auto", return_all: bool = False):
+    """u on the (n_theta + 1) x n_lambda grid with poles, Delta u = f, zero mean.
+
+    The samples of f on the pole rows do not enter (sin^2 theta vanishes
+    there).  u on rows i = 0..n_theta-1 is the interpolant at theta_i = theta_p,
+    p = n_theta + i; on the south pole row i = n_theta it is the interpolant at
+    theta = -pi, the same point as theta = pi by periodicity (no shift)."""
+    f = np.asarray(f, dtype=np.float64)
+    nt = f.shape[0] - 1
+    F = rhs_coefficients_poles(f)
+    X = solve_columns(F, reading, method)
+    U = sample_poles(X)
+    U = np.concatenate([U[nt:], U[:1]], axis=0)
     u = U.real.copy()
     if return_all:
         return u, F, X, float(np.abs(U.imag).max())

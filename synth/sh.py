@@ -47,6 +47,22 @@ def colatitudes(n_theta: int) -> np.ndarray:
     return (i + 0.5) * math.pi / n_theta
 
 
+def pole_colatitudes(n_theta: int) -> np.ndarray:
+    """theta_i = i pi / n_theta, i = 0 .. n_theta (the grid with both poles:
+    n_theta + 1 rows)."""
+    return np.arange(n_theta + 1, dtype=np.float64) * math.pi / n_theta
+
+
+def grid_colatitudes(n_theta: int, grid: str = "shifted") -> np.ndarray:
+    """The colatitudes of a grid: "shifted" (pole-free, n_theta rows) or
+    "poles" (n_theta + 1 rows, both poles)."""
+    if grid == "shifted":
+        return colatitudes(n_theta)
+    if grid == "poles":
+        return pole_colatitudes(n_theta)
+    raise ValueError(f"unknown grid {grid!r}")
+
+
 def longitudes(n_lambda: int) -> np.ndarray:
     """lambda_q = -pi + 2 pi q / n_lambda."""
     q = np.arange(n_lambda, dtype=np.float64)
@@ -148,14 +164,16 @@ def _legendre_columns(lmax: int, theta: torch.Tensor):
         p_prev2, p_prev = p_prev, p_l
 
 
-def synthesize(coeffs: np.ndarray, n_theta: int, n_lambda: int, device="cpu") -> torch.Tensor:
-    """Sample sum_lm C[l, L+m] Y_l^m on the grid; returns float64 [n_theta, n_lambda]."""
+def synthesize(coeffs: np.ndarray, n_theta: int, n_lambda: int, device="cpu", grid: str = "shifted") -> torch.Tensor:
+    """Sample sum_lm C[l, L+m] Y_l^m on the grid; returns float64 [rows, n_lambda]
+    (rows = n_theta, or n_theta + 1 on the grid with poles)."""
     coeffs = np.asarray(coeffs, dtype=np.float64)
     lmax = coeffs.shape[0] - 1
     if coeffs.shape != (lmax + 1, 2 * lmax + 1):
         raise ValueError("coefficient array must have shape (L+1, 2L+1)")
     dev = torch.device(device)
-    theta = torch.tensor(colatitudes(n_theta), dtype=torch.float64, device=dev)
+    theta = torch.tensor(grid_colatitudes(n_theta, grid), dtype=torch.float64, device=dev)
+    rows = theta.shape[0]
     cc = torch.tensor(coeffs, dtype=torch.float64, device=dev)
     # column weights: cos part (m >= 0) and sin part (m > 0)
     ccos = cc[:, lmax:]                                   # [L+1, L+1]  m = 0..L
@@ -163,8 +181,8 @@ def synthesize(coeffs: np.ndarray, n_theta: int, n_lambda: int, device="cpu") ->
     csin = csin.clone()
     csin[:, 0] = 0.0
 
-    acc_c = torch.zeros((lmax + 1, n_theta), dtype=torch.float64, device=dev)
-    acc_s = torch.zeros((lmax + 1, n_theta), dtype=torch.float64, device=dev)
+    acc_c = torch.zeros((lmax + 1, rows), dtype=torch.float64, device=dev)
+    acc_s = torch.zeros((lmax + 1, rows), dtype=torch.float64, device=dev)
     for l, p_l in _legendre_columns(lmax, theta):
         acc_c[: l + 1] += ccos[l, : l + 1, None] * p_l
         acc_s[: l + 1] += csin[l, : l + 1, None] * p_l
