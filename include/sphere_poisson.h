@@ -63,6 +63,23 @@ typedef struct sp_plan_s* sp_plan_t;
 
 /* plan flag: tune the transform tiles at plan time (see the plan calls) */
 #define SP_FLAG_AUTOTUNE 1u
+/*
+ * plan flag: the grid with both poles.  f and u are [n_theta + 1][n_lambda],
+ * row i = colatitude theta_i = i pi / n_theta, i = 0..n_theta (row 0 the north
+ * pole, row n_theta the south pole; the DFS grid of Section 2 sampled on
+ * theta in [0, pi]).  Doubled, the colatitudes are theta_p = -pi + 2 pi p / m,
+ * m = 2 n_theta; the coefficients, their truncation and the per-k systems are
+ * those of the pole-free grid.  The samples of f on the pole rows are
+ * multiplied by sin^2 theta = 0 and do not enter; u is written on every row,
+ * the poles included.  SP_FP64 single plans only (other precisions return
+ * SP_ERR_UNSUPPORTED), 2 n_theta <= 12288 with 2 n_theta factoring into primes
+ * <= 31 (else SP_ERR_BAD_SIZE).  Such a plan supports sphere_poisson_solve
+ * (f_mean_out included: the same quadrature on this grid, each pole row
+ * weighted once), _solve_host, _solve_noalloc, the profiling and size queries;
+ * every other call on it returns SP_ERR_UNSUPPORTED (the adjoint, the
+ * transforms alone, sum2, the derivatives and the low-rank calls).
+ */
+#define SP_FLAG_POLES 2u
 
 /*
  * Create a plan for grids of n_theta colatitudes x n_lambda longitudes.
@@ -76,7 +93,8 @@ typedef struct sp_plan_s* sp_plan_t;
  *                 values return SP_ERR_UNSUPPORTED.
  *   refine_sweeps 0..16 residual sweeps for SP_FP32_REFINE (ignored otherwise;
  *                 outside 0..16 SP_ERR_BAD_ARG).
- *   flags         0, or SP_FLAG_AUTOTUNE (below): time the transform tiles
+ *   flags         0, SP_FLAG_POLES (above: the grid with both poles), and/or
+ *                 SP_FLAG_AUTOTUNE (below): time the transform tiles
  *                 (rows / columns per CTA and threads per CTA of the longitude
  *                 and colatitude kernels) as whole solves on zero input at plan
  *                 time and keep the fastest; cached like the batched tuner's.

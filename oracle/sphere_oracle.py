@@ -405,6 +405,20 @@ def poisson_poles(f: np.ndarray, reading: str = "B", method: str = "auto", retur
     return u
 
 
+def sum2_poles(values_on_grid: np.ndarray) -> float:
+    """sum2 on the grid with poles: 2 pi sum_j w_j A_{j,0}, A = coeffs2_poles(ftilde),
+    over the symmetric window |j| <= m/2 - 1 of the solve (reading B).  On this
+    grid the theta-Nyquist coefficient of a theta-even column is not zero (the
+    doubled samples pair p with m - p, of the same parity), unlike the
+    pole-free grid's, so the window is stated: the Nyquist term is left out."""
+    ft = dfs_double_poles(values_on_grid)
+    m, n = ft.shape
+    A = coeffs2_poles(ft)
+    w = integration_weights(m)
+    w[0] = 0.0                                  # j = -m/2
+    return float((2.0 * math.pi * (w @ A[:, n // 2])).real)
+
+
 def sum2(values_on_grid: np.ndarray) -> float:
     """Surface integral over the unit sphere (Section 4, Integration):
     2 pi sum_j w_j A_{j,0} with A = coeffs2(ftilde)."""

@@ -58,13 +58,18 @@ class Plan:
     """A solver plan for one grid size (n_theta colatitudes x n_lambda longitudes).
 
     autotune=True times the transform tiles at plan time and keeps the fastest
-    (cached in $SPHERE_POISSON_TUNE_CACHE if set)."""
+    (cached in $SPHERE_POISSON_TUNE_CACHE if set).  grid="poles" is the grid
+    with both poles (SP_FLAG_POLES): n_theta + 1 rows theta_i = i pi / n_theta,
+    FP64 solves only."""
 
     def __init__(self, n_theta: int, n_lambda: int, precision: str = "fp64", refine_sweeps: int = 0,
-                 device=None, autotune: bool = False):
+                 device=None, autotune: bool = False, grid: str = "shifted"):
         lib = _lib.load()
         if precision not in _PRECISIONS:
             raise ValueError(f"precision must be one of {sorted(_PRECISIONS)}")
+        if grid not in ("shifted", "poles"):
+            raise ValueError('grid must be "shifted" or "poles"')
+        self.grid = grid
         self.n_theta, self.n_lambda = int(n_theta), int(n_lambda)
         self.precision = precision
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
@@ -72,7 +77,7 @@ class Plan:
         h = ctypes.c_void_p()
         ws = ctypes.c_size_t()
         with torch.cuda.device(self.device):
-            flags = _lib.SP_FLAG_AUTOTUNE if autotune else 0
+            flags = (_lib.SP_FLAG_AUTOTUNE if autotune else 0) | (_lib.SP_FLAG_POLES if grid == "poles" else 0)
             _lib.check(lib.sphere_poisson_plan(ctypes.byref(h), self.n_theta, self.n_lambda,
                                                _PRECISIONS[precision], int(refine_sweeps), flags,
                                                ctypes.byref(ws)), "sphere_poisson_plan")
@@ -83,7 +88,7 @@ class Plan:
 
     @property
     def shape(self):
-        return (self.n_theta, self.n_lambda)
+        return (self.n_theta + (1 if self.grid == "poles" else 0), self.n_lambda)
 
     def _workspace(self, workspace):
         if workspace is not None:
@@ -396,6 +401,7 @@ class BatchedPlan(Plan):
         _lib.check(lib.sphere_poisson_batch_offsets(h, offs), "sphere_poisson_batch_offsets")
         self.offsets = [int(offs[i]) for i in range(cnt + 1)]
         self.n_theta, self.n_lambda = 1, self.offsets[-1]
+        self.grid = "shifted"
 
     @property
     def shape(self):

@@ -30,6 +30,7 @@ SP_FP64 = 0
 SP_FP32 = 1
 SP_FP32_REFINE = 2
 SP_FLAG_AUTOTUNE = 1
+SP_FLAG_POLES = 2
 
 EXPORTED = (
     "sphere_poisson_plan",

@@ -4,6 +4,7 @@
 #include "launchers.inl"
 #include "batched.cuh"
 #include "calculus.cuh"
+#include "poles.cuh"
 
 namespace sp {
 
@@ -33,6 +34,16 @@ void launch_theta_inverse<double>(bool adj, bool big, const Launch& l, cpx<doubl
                                   const cpx<double>* post, double inv_n, int zonal) {
   SP_PICK(k_theta_inverse, double, adj, big, W, N, K, Kp, cols, d, tw, perm, post, inv_n, zonal);
 }
+void launch_theta_poles(bool inverse, bool big, const Launch& l, cpx<double>* W, int N, int K, int Kp,
+                        const FftDesc& d, const cpx<double>* tw, const int* perm) {
+  if (inverse) {
+    if (big) k_theta_inverse_poles<true><<<l.grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, d, tw, perm);
+    else k_theta_inverse_poles<false><<<l.grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, d, tw, perm);
+  } else {
+    if (big) k_theta_forward_poles<true><<<l.grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, d, tw, perm);
+    else k_theta_forward_poles<false><<<l.grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, d, tw, perm);
+  }
+}
 template <>
 cudaError_t allow_transform_smem<double>(int bytes) {
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
@@ -54,6 +65,10 @@ cudaError_t allow_transform_smem<double>(int bytes) {
   upd(cudaFuncSetAttribute(k_theta_inverse<double, false, true>, a, bytes));
   upd(cudaFuncSetAttribute(k_theta_inverse<double, true, false>, a, bytes));
   upd(cudaFuncSetAttribute(k_theta_inverse<double, true, true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_forward_poles<false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_forward_poles<true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_inverse_poles<false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_inverse_poles<true>, a, bytes));
   upd(allow_pipe_smem<double>(bytes));
   return e;
 }

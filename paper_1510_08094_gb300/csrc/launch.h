@@ -84,6 +84,11 @@ void launch_theta_fused(bool big, const Launch& l, cpx<float>* W, int N, int K, 
                         const cpx<float>* tw, const int* perm, const cpx<float>* post_s, const cpx<float>* post,
                         const float* fiu, float inv_n);
 size_t theta_fused_smem(int N, int cols, int threads);
+// the colatitude transforms of the grid with both poles (poles.cuh): one CTA
+// per column k < K (grid K), 2N complex doubles of dynamic shared memory;
+// d, tw and perm describe the length-2N FFT
+void launch_theta_poles(bool inverse, bool big, const Launch& l, cpx<double>* W, int N, int K, int Kp,
+                        const FftDesc& d, const cpx<double>* tw, const int* perm);
 // the FP32 + refinement form's fused colatitude stage (fused_refine.cuh): one
 // CTA per column k >= 1 (column 0 is the FP64 zonal path's), in place in W
 // (double-float spectrum); refine_fused_smem dynamic bytes

@@ -272,6 +272,15 @@ struct sp_plan_s {
   int device;
   FftDesc row_fft, col_fft;
   bool big_row, big_col;
+  // the grid with both poles (SP_FLAG_POLES): nt = N + 1 sample rows, the
+  // colatitude transforms of length 2N (poles.cuh)
+  bool poles;
+  FftDesc pole_fft;
+  bool big_pole;
+  int pole_threads;
+  size_t pole_smem;
+  cpx<double>* tw_pole;  // twiddles of the length-2N passes
+  int* perm_pole;        // their digit reversal
   int rows_per_cta, cols_per_cta;  // transform tiles in the plan's arithmetic
   bool pipe_rows, pipe_cols;       // pipelined kernels wanted for the row / column stages
   bool pipe[4];                    // pipelined kernel per stage (rows fwd, theta fwd, theta inv, rows inv)
@@ -599,13 +608,20 @@ void enqueue_fp64(sp_plan_t p, bool adj, const double* in, double* out, void* ws
   m.mark(0);
   rows_forward_stage<double>(p, adj, st, in, W, p->tw_row, p->post_row, p->row_scale, p->row_scale, nullptr, ov);
   m.mark(1);
-  launch_theta_forward_x<double>(p, adj, st, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
-                                   p->tw_col, p->perm_col, adj ? p->post_col : p->post_col_s, inv_n, 1);
+  const Launch pole{dim3(p->K), p->pole_threads, p->pole_smem, st};
+  if (p->poles)   // forward only (the adjoint of this grid is not built)
+    sp::launch_theta_poles(false, p->big_pole, pole, W, p->N, p->K, p->Kp, p->pole_fft, p->tw_pole, p->perm_pole);
+  else
+    launch_theta_forward_x<double>(p, adj, st, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
+                                     p->tw_col, p->perm_col, adj ? p->post_col : p->post_col_s, inv_n, 1);
   m.mark(2);
   sp::launch_solve<double>(adj, solve, W, p->fac_l, p->fac_iu, p->fac_cu, p->N, p->K, p->Kp);
   m.mark(3);
-  launch_theta_inverse_x<double>(p, adj, st, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
-                                   p->tw_col, p->perm_col, p->post_col, inv_n, 1);
+  if (p->poles)
+    sp::launch_theta_poles(true, p->big_pole, pole, W, p->N, p->K, p->Kp, p->pole_fft, p->tw_pole, p->perm_pole);
+  else
+    launch_theta_inverse_x<double>(p, adj, st, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
+                                     p->tw_col, p->perm_col, p->post_col, inv_n, 1);
   m.mark(4);
   rows_inverse_stage<double>(p, adj, st, W, out, p->tw_row, p->post_row, p->row_scale, p->row_scale, nullptr, ov);
   m.mark(5);
@@ -779,6 +795,7 @@ int launch_solve(sp_plan_t p, const double* in, double* out, void* workspace, cu
     return launch_batched(p, in, out, workspace, st);
   }
   if (p->precision == SP_FP64) {
+    if (ADJ && p->poles) return SP_ERR_UNSUPPORTED;
     enqueue_fp64(p, ADJ, in, out, workspace, st);
   } else if (p->precision == SP_FP32) {
     enqueue_fp32(p, ADJ, in, out, workspace, st);
@@ -878,14 +895,20 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   if (n_theta < 1 || n_lambda < 2 || (n_lambda & 1)) return SP_ERR_BAD_SIZE;
   if (n_theta > kMaxLen || n_lambda / 2 > kMaxLen) return SP_ERR_BAD_SIZE;
   if (precision != SP_FP64 && precision != SP_FP32 && precision != SP_FP32_REFINE) return SP_ERR_UNSUPPORTED;
-  if ((flags & ~SP_FLAG_AUTOTUNE) != 0 || refine_sweeps < 0 || refine_sweeps > 16) return SP_ERR_BAD_ARG;
+  if ((flags & ~(SP_FLAG_AUTOTUNE | SP_FLAG_POLES)) != 0 || refine_sweeps < 0 || refine_sweeps > 16)
+    return SP_ERR_BAD_ARG;
+  const bool poles = (flags & SP_FLAG_POLES) != 0;
+  if (poles && precision != SP_FP64) return SP_ERR_UNSUPPORTED;
+  if (poles && 2 * n_theta > kMaxLen) return SP_ERR_BAD_SIZE;
 
-  FftDesc rd, cd;
+  FftDesc rd, cd, pd{};
   if (!make_fft_desc(n_lambda / 2, &rd) || !make_fft_desc(n_theta, &cd)) return SP_ERR_BAD_SIZE;
+  if (poles && !make_fft_desc(2 * n_theta, &pd)) return SP_ERR_BAD_SIZE;
 
   sp_plan_s* p = new (std::nothrow) sp_plan_s();
   if (!p) return SP_ERR_CUDA;
-  p->nt = n_theta;
+  p->poles = poles;
+  p->nt = poles ? n_theta + 1 : n_theta;
   p->nl = n_lambda;
   p->L = n_lambda / 2;
   p->N = n_theta;
@@ -913,8 +936,14 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   p->col_threads = fft_threads(cd, p->cols_per_cta);
   p->zcol_threads = fft_threads(cd, 1);
   p->zcol_smem = (size_t)p->N * sizeof(cpx<double>);
+  if (poles) {
+    p->pole_fft = pd;
+    p->big_pole = needs_big(pd);
+    p->pole_threads = fft_threads(pd, 1);
+    p->pole_smem = (size_t)pd.L * sizeof(cpx<double>);
+  }
   if (p->row_threads < 0 || p->col_threads < 0 || p->row_smem > 220 * 1024 || p->col_smem > 220 * 1024 ||
-      p->zcol_smem > 220 * 1024) {
+      p->zcol_smem > 220 * 1024 || p->pole_threads < 0 || p->pole_smem > 220 * 1024) {
     delete p;
     return SP_ERR_BAD_SIZE;
   }
@@ -922,7 +951,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   const size_t grid = (size_t)p->N * p->Kp;
   const size_t zbytes = (size_t)p->N * 2 * sizeof(cpx<double>);
   if (precision == SP_FP64) {
-    p->ws_bytes = grid * sizeof(cpx<double>);
+    p->ws_bytes = (size_t)std::max(p->nt, p->N) * p->Kp * sizeof(cpx<double>);   // poles: N + 1 sample rows
   } else if (precision == SP_FP32) {
     p->off_z = align(grid * sizeof(cpx<float>));
     p->ws_bytes = p->off_z + zbytes;
@@ -953,11 +982,19 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   std::vector<int> perm_row, perm_col;
   digit_reversal(rd, perm_row);
   digit_reversal(cd, perm_col);
+  // exp(-i theta_i) with theta_i = 2 pi (2i + 1) / (4N) (pole-free) or 2 pi (2i) / (4N) (poles), exactly reduced
+  auto theta_root = [&](int i, double* re, double* im) { unit_root(poles ? 2L * i : 2L * i + 1, 4L * p->N, re, im); };
   std::vector<double> row_scale(p->nt);
   for (int i = 0; i < p->nt; ++i) {
     double re, im;
-    unit_root(2 * i + 1, 4L * p->N, &re, &im);  // sin(theta_i) = -im
+    theta_root(i, &re, &im);  // sin(theta_i) = -im (exactly 0 at the poles)
     row_scale[i] = (im * im) / (double)n_lambda;
+  }
+  std::vector<cpx<double>> tw_pole;
+  std::vector<int> perm_pole;
+  if (poles) {
+    tw_pole = stage_twiddles(pd);
+    digit_reversal(pd, perm_pole);
   }
   std::vector<char> t_tw_row, t_tw_col, t_post_row, t_post_col, t_post_col_s, t_scale;
   if (precision == SP_FP32) {
@@ -993,6 +1030,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   size_t o_geo = take((size_t)(2 * p->nt + 2 * p->nl) * sizeof(double));
   size_t o_mean_w = take(p->nt * sizeof(double));
   size_t o_perm_row = take(p->L * sizeof(int)), o_perm_col = take(p->N * sizeof(int));
+  size_t o_tw_pole = take(tw_pole.size() * cd_sz), o_perm_pole = take(perm_pole.size() * sizeof(int));
   size_t o_t_tw_row = take(t_tw_row.size()), o_t_tw_col = take(t_tw_col.size());
   size_t o_t_post_row = take(t_post_row.size()), o_t_post_col = take(t_post_col.size());
   size_t o_t_scale = take(t_scale.size());
@@ -1031,6 +1069,8 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   p->mean_w = reinterpret_cast<double*>(base + o_mean_w);
   p->perm_row = reinterpret_cast<int*>(base + o_perm_row);
   p->perm_col = reinterpret_cast<int*>(base + o_perm_col);
+  p->tw_pole = poles ? reinterpret_cast<cpx<double>*>(base + o_tw_pole) : nullptr;
+  p->perm_pole = poles ? reinterpret_cast<int*>(base + o_perm_pole) : nullptr;
   p->tw_row_t = base + o_t_tw_row;
   p->tw_col_t = base + o_t_tw_col;
   p->post_row_t = base + o_t_post_row;
@@ -1065,7 +1105,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
     std::vector<double> s2(p->nt);
     for (int i = 0; i < p->nt; ++i) {
       double re, im;
-      unit_root(2 * i + 1, 4L * p->N, &re, &im);  // sin(theta_i) = -im
+      theta_root(i, &re, &im);  // sin(theta_i) = -im
       s2[i] = im * im;
     }
     up(p->sin2, s2.data(), p->nt * sizeof(double), "copy sin2");
@@ -1073,7 +1113,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
     std::vector<double> geo(2 * p->nt + 2 * p->nl);
     for (int i = 0; i < p->nt; ++i) {
       double re, im;
-      unit_root(2 * i + 1, 4L * p->N, &re, &im);
+      theta_root(i, &re, &im);
       geo[i] = -im;
       geo[p->nt + i] = re;
     }
@@ -1096,9 +1136,12 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
       unit_root(r, M4, &re, &im);
       c4[r] = re;
     }
+    // On the grid with poles j theta_i = 2 pi j (2i) / (4N), and the doubled
+    // grid holds the interior rows twice but each pole once: the pole rows'
+    // weights are halved.
     std::vector<double> mw(p->nt);
     for (int i = 0; i < p->nt; ++i) {
-      const long step = (2L * (2 * i + 1)) % M4;
+      const long step = (2L * (poles ? 2L * i : 2L * i + 1)) % M4;
       long r = 0;
       double sum = 0.0;
       for (int j = 2; j <= p->N - 1; j += 2) {
@@ -1106,12 +1149,17 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
         if (r >= M4) r -= M4;
         sum += c4[r] / (1.0 - (double)j * (double)j);
       }
-      mw[i] = (1.0 + 2.0 * sum) / (double)p->N / (double)n_lambda;
+      const double half = (poles && (i == 0 || i == p->N)) ? 0.5 : 1.0;
+      mw[i] = half * (1.0 + 2.0 * sum) / (double)p->N / (double)n_lambda;
     }
     up(p->mean_w, mw.data(), p->nt * sizeof(double), "copy mean_w");
   }
   up(p->perm_row, perm_row.data(), p->L * sizeof(int), "copy perm_row");
   up(p->perm_col, perm_col.data(), p->N * sizeof(int), "copy perm_col");
+  if (poles) {
+    up(p->tw_pole, tw_pole.data(), tw_pole.size() * cd_sz, "copy tw_pole");
+    up(p->perm_pole, perm_pole.data(), perm_pole.size() * sizeof(int), "copy perm_pole");
+  }
   up(p->tw_row_t, t_tw_row.data(), t_tw_row.size(), "copy tw_row_t");
   up(p->tw_col_t, t_tw_col.data(), t_tw_col.size(), "copy tw_col_t");
   up(p->post_row_t, t_post_row.data(), t_post_row.size(), "copy post_row_t");
@@ -1247,7 +1295,7 @@ int tune_single(sp_plan_t p) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
   std::ostringstream ko;
   ko << prop.name << "|" << p->nt << "x" << p->nl << "|single|" << precision_tag(p->precision) << "|"
-     << p->sweeps;
+     << p->sweeps << (p->poles ? "|poles" : "");
   const std::string key = spaceless(ko.str());
   const char* cache_path = std::getenv("SPHERE_POISSON_TUNE_CACHE");
   const size_t csz = esize(p->precision);
@@ -1950,7 +1998,7 @@ int sphere_poisson_solve_noalloc(sp_plan_t plan, const double* f, double* u, voi
 static int check_transform_plan(sp_plan_t plan, const void* a, const void* b, const void* ws, size_t ws_bytes) {
   int rc = check_arrays(plan, a, b, ws, ws_bytes);
   if (rc != SP_OK) return rc;
-  if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
+  if (plan->batched || plan->precision != SP_FP64 || plan->poles) return SP_ERR_UNSUPPORTED;
   return SP_OK;
 }
 
@@ -2020,7 +2068,7 @@ int check_derivative_call(sp_plan_t plan, int spectra, std::initializer_list<con
   for (const void* q : ptrs)
     if (!q) return SP_ERR_NULL;
   if (!workspace) return SP_ERR_NULL;
-  if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
+  if (plan->batched || plan->precision != SP_FP64 || plan->poles) return SP_ERR_UNSUPPORTED;
   uintptr_t bits = (uintptr_t)workspace;
   for (const void* q : ptrs) bits |= (uintptr_t)q;
   if (bits & 15) return SP_ERR_MISALIGNED;
@@ -2101,7 +2149,7 @@ int launch_status(const char* what) {
 int sphere_poisson_gradient_workspace_size(sp_plan_t plan, size_t* workspace_bytes) {
   if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
   if (!workspace_bytes) return SP_ERR_NULL;
-  if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
+  if (plan->batched || plan->precision != SP_FP64 || plan->poles) return SP_ERR_UNSUPPORTED;
   *workspace_bytes = derivative_workspace(plan, 5);
   return SP_OK;
 }
@@ -2109,7 +2157,7 @@ int sphere_poisson_gradient_workspace_size(sp_plan_t plan, size_t* workspace_byt
 int sphere_poisson_curl_workspace_size(sp_plan_t plan, size_t* workspace_bytes) {
   if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
   if (!workspace_bytes) return SP_ERR_NULL;
-  if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
+  if (plan->batched || plan->precision != SP_FP64 || plan->poles) return SP_ERR_UNSUPPORTED;
   *workspace_bytes = derivative_workspace(plan, 5);
   return SP_OK;
 }
@@ -2198,7 +2246,7 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 int sphere_poisson_lowrank_workspace_size(sp_plan_t plan, int max_terms, size_t* workspace_bytes) {
   if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
   if (!workspace_bytes) return SP_ERR_NULL;
-  if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
+  if (plan->batched || plan->precision != SP_FP64 || plan->poles) return SP_ERR_UNSUPPORTED;
   if (max_terms < 0 || max_terms > std::min(plan->nt, kMaxTerms)) return SP_ERR_BAD_ARG;
   const size_t ge = al256((size_t)plan->nt * plan->nl * sizeof(double)) + al256(kGeParts * sizeof(sp::GePivot)) +
                     al256(sizeof(sp::GePivot)) + al256(2 * (size_t)plan->nl * sizeof(double));
@@ -2214,7 +2262,7 @@ int sphere_poisson_lowrank_ge(sp_plan_t plan, const double* f, int max_terms, do
                               size_t workspace_bytes, void* stream) {
   if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
   if (!f || !terms || !workspace || (max_terms > 0 && (!cols || !piv || !rows))) return SP_ERR_NULL;
-  if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
+  if (plan->batched || plan->precision != SP_FP64 || plan->poles) return SP_ERR_UNSUPPORTED;
   if (max_terms < 0 || max_terms > std::min(plan->nt, kMaxTerms) || !(rtol >= 0.0) || !(alpha >= 0.0) || alpha > 1.0)
     return SP_ERR_BAD_ARG;
   if (((uintptr_t)f | (uintptr_t)workspace) & 15) return SP_ERR_MISALIGNED;
@@ -2276,7 +2324,7 @@ int sphere_poisson_solve_lowrank(sp_plan_t plan, int terms, const double* cols, 
                                  void* stream) {
   if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
   if (!u || !workspace || (terms > 0 && (!cols || !piv || !rows))) return SP_ERR_NULL;
-  if (plan->batched || plan->precision != SP_FP64) return SP_ERR_UNSUPPORTED;
+  if (plan->batched || plan->precision != SP_FP64 || plan->poles) return SP_ERR_UNSUPPORTED;
   if (terms < 0 || terms > std::min(plan->nt, kMaxTerms)) return SP_ERR_BAD_ARG;
   if (((uintptr_t)u | (uintptr_t)workspace | (uintptr_t)cols | (uintptr_t)rows) & 15) return SP_ERR_MISALIGNED;
   size_t need = 0;

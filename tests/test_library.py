@@ -71,6 +71,13 @@ def test_plan_argument_checks(lib):
     h = ctypes.c_void_p()
     assert lib.sphere_poisson_plan(ctypes.byref(h), 8, 16, 7, 0, 0, None) == _lib.SP_ERR_UNSUPPORTED
     assert lib.sphere_poisson_plan(ctypes.byref(h), 8, 16, 0, 0, 5, None) == _lib.SP_ERR_BAD_ARG
+    # the grid with both poles: FP64 only, 2 n_theta <= 12288
+    poles = _lib.SP_FLAG_POLES
+    assert lib.sphere_poisson_plan(ctypes.byref(h), 8, 16, _lib.SP_FP32, 0, poles, None) == _lib.SP_ERR_UNSUPPORTED
+    assert lib.sphere_poisson_plan(ctypes.byref(h), 8, 16, _lib.SP_FP32_REFINE, 1, poles, None) == \
+        _lib.SP_ERR_UNSUPPORTED
+    assert lib.sphere_poisson_plan(ctypes.byref(h), 6145, 16, 0, 0, poles, None) == _lib.SP_ERR_BAD_SIZE
+    assert h.value is None
 
 
 def test_calls_reject_null_plan(lib):

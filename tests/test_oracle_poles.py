@@ -9,6 +9,7 @@ theta in [0, pi]), pinned by what does not depend on the oracle itself.
     rows included.
   * The samples of f on the pole rows are multiplied by sin^2 theta = 0: they
     do not change u.
+  * Its surface integral of the printed polynomial is 216 pi / 35.
   * u is the same function whichever grid samples f: on the rows both grids
     share no point, so the check is the interpolant, evaluated from the
     pole-grid coefficients at the pole-free colatitudes, against the
@@ -77,7 +78,19 @@ def pin_same_function_on_both_grids():
     return _rel(up, us) < 1e-12
 
 
-PINS = [pin_dft_of_trig_polynomial, pin_closed_forms, pin_series, pin_same_function_on_both_grids]
+def pin_sum2_worked_example():
+    # the printed polynomial integrates to 216 pi / 35 (Section 4, Integration);
+    # exact on a grid that resolves its degree, poles included
+    nt, nl = 12, 24
+    th = sh.pole_colatitudes(nt)[:, None]
+    la = sh.longitudes(nl)[None, :]
+    x, y, z = np.cos(la) * np.sin(th), np.sin(la) * np.sin(th), np.cos(th) + 0 * la
+    f = 1 + x + y ** 2 + x ** 2 * y + x ** 4 + y ** 5 + (x * y * z) ** 2
+    return abs(O.sum2_poles(f) - 216 * math.pi / 35) < 2e-14
+
+
+PINS = [pin_dft_of_trig_polynomial, pin_closed_forms, pin_series, pin_same_function_on_both_grids,
+        pin_sum2_worked_example]
 
 
 def test_pole_grid_oracle_passes_its_pins():
