@@ -416,7 +416,7 @@ def run_ours(args):
 
 
 FORM_GROUPS = ("precision", "adjoint", "inverse_fit", "transforms", "tangential_gradient", "vector_calculus",
-               "lowrank", "mixed_sizes", "paper_scale")
+               "lowrank", "mixed_sizes", "paper_scale", "poles")
 
 
 def measure_forms(sp, f, u_exact, u64, N, n, dev, ms_fp64, args):
@@ -496,7 +496,42 @@ def measure_forms(sp, f, u_exact, u64, N, n, dev, ms_fp64, args):
         res["mixed_sizes"] = measure_mixed_sizes(sp, dev, args)
     if "paper_scale" in want and not args.no_paper_scale:
         res["paper_scale"] = measure_paper_scale(sp, dev, args)
+    if "poles" in want:
+        res["poles"] = measure_poles(sp, N, n, dev, steps, ms_fp64, args)
     return res
+
+
+def measure_poles(sp, N, n, dev, steps, ms_fp64, args):
+    """The FP64 solve on the grid with both poles (n_theta + 1 rows theta_i =
+    i pi / n_theta) for the same series and grid size, against the closed form
+    on every row; its colatitude transforms have length 2 n_theta."""
+    import torch
+    from synth import sh
+
+    w = sh.workload(args.workload)
+    c = w.coeffs()
+    f = sh.synthesize(c, N, n, device=dev, grid="poles")
+    ue = sh.synthesize(sh.poisson_exact(c), N, n, device=dev, grid="poles")
+    plan = sp.Plan(N, n, "fp64", device=dev, autotune=not args.no_autotune, grid="poles")
+    ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=dev)
+    u = torch.empty_like(f)
+    for _ in range(3):
+        plan.solve(f, u, ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        plan.solve(f, u, ws)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    rows = N + 1
+    out = {"grid": f"{rows} x {n} (theta_i = i pi / {N}, both poles)", "value": rows * n / (ms * 1e-3),
+           "unit": "DOF/s", "ms_per_step": ms, "ms_vs_pole_free_fp64": ms / ms_fp64,
+           "max_rel_err_vs_closed_form": float((u - ue).abs().max() / ue.abs().max()),
+           "gpu_launches_per_step": plan.launches()}
+    del plan, ws, u, f, ue
+    return out
 
 
 def measure_lowrank(sp, N, n, dev, steps, ms_fp64, args):
