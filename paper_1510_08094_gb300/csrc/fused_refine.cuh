@@ -12,7 +12,9 @@
 //      frequency), storing the column over its input.
 // F, X and the FP32 residual live in shared memory for the whole column, so
 // the spectrum crosses HBM once each way instead of the unfused path's four
-// times plus three per sweep.
+// times plus three per sweep.  One CTA per SM (about 200 KB of shared memory),
+// persistent over the columns, with the next column's load in flight during
+// the current column's inverse transform.
 #pragma once
 
 #include "fused.cuh"
@@ -27,6 +29,14 @@ __host__ __device__ inline size_t refine_fused_smem_bytes(int N, int threads) {
 
 __device__ __forceinline__ cpx<float> round_dd(cpx<dd> v) { return {v.re.hi + v.re.lo, v.im.hi + v.im.lo}; }
 
+// Persistent: CTA b takes the columns k = 1 + b, 1 + b + gridDim.x, ...  The
+// two double-float buffers swap roles from column to column: once the row-0
+// closure has read F for the last time, cp.async copies the next column's raw
+// samples (one 16-byte element per row, in natural order) into F's buffer
+// while the current solution is transformed back and stored from the other;
+// the next column then scatters them (Makhoul order, digit reversal) into the
+// buffer just freed by the store.  The load of every column but the CTA's
+// first overlaps the arithmetic of the previous one.
 template <bool BIG>
 __global__ void __launch_bounds__(BIG ? 256 : 512) k_refine_fused(
     cpx<dd>* __restrict__ W, int N, int K, int Kp, FftDesc d, const cpx<dd>* __restrict__ tw,
@@ -36,59 +46,73 @@ __global__ void __launch_bounds__(BIG ? 256 : 512) k_refine_fused(
   const size_t a16 = ((size_t)N * sizeof(cpx<dd>) + 15) & ~(size_t)15;
   const size_t a8 = ((size_t)N * sizeof(cpx<float>) + 15) & ~(size_t)15;
   cpx<dd>* A = reinterpret_cast<cpx<dd>*>(smem_raw);                    // the transform, then F
-  cpx<dd>* X = reinterpret_cast<cpx<dd>*>(smem_raw + a16);              // the solution, then its transform
+  cpx<dd>* X = reinterpret_cast<cpx<dd>*>(smem_raw + a16);              // raw samples, then the solution
   cpx<float>* C = reinterpret_cast<cpx<float>*>(smem_raw + 2 * a16);    // FP32 right-hand sides / corrections
   ScanSlot<float>* slot = reinterpret_cast<ScanSlot<float>*>(smem_raw + 2 * a16 + a8);
-  const int k = 1 + (int)blockIdx.x;
   const cpx<dd> zero = {dd(0.f, 0.f), dd(0.f, 0.f)};
+  int k = 1 + (int)blockIdx.x;
+  if (k >= K) return;                                  // uniform over the block
+  stage_theta<dd>(X, W, k, N, Kp, 1);                  // the CTA's first column
+  cp_commit();
 
-  // 1. forward colatitude transform in double-float, F in A
-  theta_forward_load<dd>(k, A, FromGlobal<cpx<dd>>{W + k, (size_t)Kp}, N, K, 1, perm);
-  __syncthreads();
-  fft_run<-1, BIG>(A, 1, d, tw);
-  post_twiddle_inplace<dd>(A, k, 1, N, K, post_s);
-  __syncthreads();
-  // 2. X = S32 F (rows j >= 1; row 0 is closed at the end)
-  for (int j = threadIdx.x; j < N; j += blockDim.x) C[j] = round_dd(A[j]);
-  __syncthreads();
-  fused_solve<float>(C, 1, N, slot, k, 1, N, K, fiu);
-  for (int j = threadIdx.x; j < N; j += blockDim.x)
-    X[j] = j == 0 ? zero : cpx<dd>{dd(C[j].re, 0.f), dd(C[j].im, 0.f)};
-  __syncthreads();
-  // 3. sweeps: R = F - M X (double-float), X += S32 R
-  const float kf = (float)k;
-  const dd two_k2 = dd_mul(dd_prod(kf, kf), dd(2.f, 0.f));   // 2 k^2, exact
-  for (int s = 0; s < sweeps; ++s) {
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
-      if (j == 0) {
-        C[0] = {0.f, 0.f};
-        continue;
-      }
-      const cpx<dd> xm = j >= 3 ? X[j - 2] : zero;     // rows 1 and 2 have no X_{j-2} term (a_j = 0)
-      const cpx<dd> xp = j + 2 < N ? X[j + 2] : zero;
-      C[j] = round_dd(refine_residual(A[j], (float)j, two_k2, xm, X[j], xp));
-    }
+  for (; k < K; k += (int)gridDim.x) {
+    cp_wait_all();
+    __syncthreads();
+    // 1. forward colatitude transform in double-float, F in A
+    theta_forward_load<dd>(k, A, FromStaged<cpx<dd>>{X, 1}, N, K, 1, perm);
+    __syncthreads();
+    fft_run<-1, BIG>(A, 1, d, tw);
+    post_twiddle_inplace<dd>(A, k, 1, N, K, post_s);
+    __syncthreads();
+    // 2. X = S32 F (rows j >= 1; row 0 is closed at the end)
+    for (int j = threadIdx.x; j < N; j += blockDim.x) C[j] = round_dd(A[j]);
     __syncthreads();
     fused_solve<float>(C, 1, N, slot, k, 1, N, K, fiu);
-    for (int j = 1 + threadIdx.x; j < N; j += blockDim.x)
-      X[j] = {dd_add(X[j].re, dd(C[j].re, 0.f)), dd_add(X[j].im, dd(C[j].im, 0.f))};
+    for (int j = threadIdx.x; j < N; j += blockDim.x)
+      X[j] = j == 0 ? zero : cpx<dd>{dd(C[j].re, 0.f), dd(C[j].im, 0.f)};
     __syncthreads();
-  }
-  // 4. row 0 in double-float, then the inverse transform of X and the store
-  if (threadIdx.x == 0) {
-    cpx<dd> x0 = zero;
-    if (!(k & 1)) {
-      const cpx<dd> x2 = N > 2 ? X[2] : zero;
-      const dd ik2 = dd_from_double(1.0 / ((double)k * (double)k));
-      x0 = {dd_mul(dd_sub(x2.re, A[0].re), ik2), dd_mul(dd_sub(x2.im, A[0].im), ik2)};
+    // 3. sweeps: R = F - M X (double-float), X += S32 R
+    const float kf = (float)k;
+    const dd two_k2 = dd_mul(dd_prod(kf, kf), dd(2.f, 0.f));   // 2 k^2, exact
+    for (int s = 0; s < sweeps; ++s) {
+      for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        if (j == 0) {
+          C[0] = {0.f, 0.f};
+          continue;
+        }
+        const cpx<dd> xm = j >= 3 ? X[j - 2] : zero;     // rows 1 and 2 have no X_{j-2} term (a_j = 0)
+        const cpx<dd> xp = j + 2 < N ? X[j + 2] : zero;
+        C[j] = round_dd(refine_residual(A[j], (float)j, two_k2, xm, X[j], xp));
+      }
+      __syncthreads();
+      fused_solve<float>(C, 1, N, slot, k, 1, N, K, fiu);
+      for (int j = 1 + threadIdx.x; j < N; j += blockDim.x)
+        X[j] = {dd_add(X[j].re, dd(C[j].re, 0.f)), dd_add(X[j].im, dd(C[j].im, 0.f))};
+      __syncthreads();
     }
-    X[0] = x0;
+    // 4. row 0 in double-float; after it F is not read again, and A takes the
+    //    next column's raw samples while X is transformed back and stored
+    if (threadIdx.x == 0) {
+      cpx<dd> x0 = zero;
+      if (!(k & 1)) {
+        const cpx<dd> x2 = N > 2 ? X[2] : zero;
+        const dd ik2 = dd_from_double(1.0 / ((double)k * (double)k));
+        x0 = {dd_mul(dd_sub(x2.re, A[0].re), ik2), dd_mul(dd_sub(x2.im, A[0].im), ik2)};
+      }
+      X[0] = x0;
+    }
+    __syncthreads();
+    if (k + (int)gridDim.x < K) stage_theta<dd>(A, W, k + (int)gridDim.x, N, Kp, 1);
+    cp_commit();
+    pre_twiddle_inplace<dd>(X, k, 1, N, K, post);
+    __syncthreads();
+    fft_run_dif<+1, BIG>(X, 1, d, tw);
+    store_dif_columns<dd>(X, W, k, 1, N, K, Kp, perm);
+    cpx<dd>* t = A;     // the raw samples are in A: the next column scatters them into X's buffer
+    A = X;
+    X = t;
   }
-  __syncthreads();
-  pre_twiddle_inplace<dd>(X, k, 1, N, K, post);
-  __syncthreads();
-  fft_run_dif<+1, BIG>(X, 1, d, tw);
-  store_dif_columns<dd>(X, W, k, 1, N, K, Kp, perm);
+  cp_wait_all();
 }
 
 }  // namespace sp

@@ -1,6 +1,7 @@
 // Double-float transform kernels and the refinement kernels (the SP_FP32_REFINE form).
 // That form has no adjoint, so only the forward instantiations exist.
 #define SP_REFINE_KERNELS
+#include <algorithm>
 #include "launchers.inl"
 #include "fused_refine.cuh"
 
@@ -56,7 +57,17 @@ void launch_refine_fused(bool big, const Launch& l, cpx<dd>* W, int N, int K, in
                          const cpx<dd>* tw, const int* perm, const cpx<dd>* post_s, const cpx<dd>* post,
                          const float* fiu, int sweeps) {
   if (K < 2) return;   // column 0 only: nothing for this kernel
-  const dim3 grid(K - 1);
+  // persistent: as many CTAs as fit on the device at once, less one, at most one
+  // per column.  A resident CTA fills its SM's registers and shared memory, so
+  // the one SM left free is where the zonal column's one-CTA kernels (the
+  // plan's high-priority side stream) run meanwhile instead of after the stage.
+  int dev = 0, sms = 1, bps = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (big) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_refine_fused<true>, l.threads, l.smem);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_refine_fused<false>, l.threads, l.smem);
+  const int resident = bps > 0 ? std::max(1, bps * sms - 1) : K - 1;
+  const dim3 grid(std::min(K - 1, resident));
   if (big)
     k_refine_fused<true><<<grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, d, tw, perm, post_s, post, fiu, sweeps);
   else
