@@ -48,20 +48,20 @@ FP64_PEAK_GFLOPS_FALLBACK = 1008.0
 # spectrum size n_theta * Kp (every stage streams the spectrum once or twice) and
 # reports null when the sources have changed since the capture.
 TRAFFIC_CAPTURE = {
-    "csrc_sha256": "71476f62e5e892ce",
+    "csrc_sha256": "7d63a2d00141864d",
     "n_theta": 5000, "n_lambda": 5000,
-    "bytes": {"rows_forward": 200250624 + 143131904, "theta_forward": 200877312 + 141872384,
-              "solve": 662319616 + 321766400, "theta_inverse": 200901376 + 142283008,
-              "rows_inverse": 200384512 + 143336960},
+    "bytes": {"rows_forward": 200336640 + 142869504, "theta_forward": 200851456 + 141943040,
+              "solve": 662401536 + 321671680, "theta_inverse": 200906752 + 142315008,
+              "rows_inverse": 200361728 + 143462656},
 }
 # the same for the FP32 form's dominant kernel, the fused colatitude stage
 # (k_theta_fused1, one column per CTA at 5000 x 5000; `ncu --section ...
 # --metrics dram__bytes_read.sum,dram__bytes_write.sum` on two launches after
 # warm-up), over the sources it is compiled from
 TRAFFIC_CAPTURE_FP32 = {
-    "csrc_sha256": "1a2315eaa565f784",
+    "csrc_sha256": "f64026d50d0baadb",
     "n_theta": 5000, "n_lambda": 5000,
-    "bytes": {"theta_fused": 150854144 + 47709696},
+    "bytes": {"theta_fused": 150865920 + 49989376},
 }
 
 
