@@ -53,6 +53,8 @@ extern "C" {
 #define SP_ERR_BAD_PLAN     -7   /* NULL or destroyed plan handle */
 #define SP_ERR_BAD_ARG      -8   /* other invalid argument */
 #define SP_ERR_SCRATCH_LIMIT -9  /* grid too large for the fixed scratch of sphere_poisson_solve_noalloc */
+#define SP_ERR_TIMEOUT      -10  /* a kernel's bounded wait for its asynchronous copies gave up (see
+                                    sphere_poisson_device_status) */
 
 /* precision of the arithmetic inside the solve (inputs and outputs are always double) */
 #define SP_FP64         0   /* IEEE double throughout */
@@ -402,6 +404,29 @@ int sphere_poisson_pipe_rates(double* fp64_fma_gops, double* fp32_fma_gops);
 
 /* Release the plan and its device tables.  Synchronous; NULL is accepted. */
 int sphere_poisson_destroy(sp_plan_t plan);
+
+/*
+ * Status of a plan's kernels that wait on asynchronous copies.  The SP_FP32_REFINE
+ * form's fused colatitude stage has the tensor memory accelerator (TMA) copy
+ * the next column into shared memory and waits for the copy on an mbarrier;
+ * that wait polls a bounded number of times, and if the copy never lands the
+ * kernel stops and sets the plan's device status word instead of hanging (the
+ * results of that solve are then not valid).  Synchronises `stream` (the
+ * stream the solves ran on, as void*, or NULL), reads the status word and
+ * clears it: SP_OK, or SP_ERR_TIMEOUT if a wait gave up since the last check.
+ * sphere_poisson_solve_host makes the same check before it returns.  Not part
+ * of the paper's method: the bookkeeping of this implementation's copies.
+ */
+int sphere_poisson_device_status(sp_plan_t plan, void* stream);
+
+/*
+ * Diagnostic of that mechanism: launches, on `stream`, one thread that waits
+ * `polls` polls on an mbarrier nothing completes and then sets the plan's
+ * status word as a timed-out copy wait would.  The next
+ * sphere_poisson_device_status returns SP_ERR_TIMEOUT.  SP_ERR_UNSUPPORTED on a
+ * batched plan.
+ */
+int sphere_poisson_wait_selftest(sp_plan_t plan, unsigned polls, void* stream);
 
 /* Static message for a status code (the last CUDA error text for SP_ERR_CUDA). */
 const char* sphere_poisson_status_string(int status);

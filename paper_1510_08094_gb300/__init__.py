@@ -141,6 +141,12 @@ class Plan:
                        "sphere_poisson_solve_adjoint")
         return out
 
+    def device_status(self, stream=None) -> int:
+        """SP_OK, or SP_ERR_TIMEOUT if a kernel's bounded wait for its asynchronous
+        copies gave up since the last check (synchronises `stream`; clears the status)."""
+        with torch.cuda.device(self.device):
+            return int(self._lib.sphere_poisson_device_status(self._h, _stream_ptr(stream)))
+
     def solve_noalloc(self, f: torch.Tensor, out: torch.Tensor, stream=None):
         """Allocation-free solve for callers that cannot allocate device memory when
         they solve: no workspace, the library's fixed 32 MiB scratch array is used

@@ -24,6 +24,7 @@ SP_ERR_UNSUPPORTED = -6
 SP_ERR_BAD_PLAN = -7
 SP_ERR_BAD_ARG = -8
 SP_ERR_SCRATCH_LIMIT = -9
+SP_ERR_TIMEOUT = -10
 SP_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 SP_FP64 = 0
@@ -42,6 +43,8 @@ EXPORTED = (
     "sphere_poisson_host_buffer_size",
     "sphere_poisson_solve_host",
     "sphere_poisson_solve_noalloc",
+    "sphere_poisson_device_status",
+    "sphere_poisson_wait_selftest",
     "sphere_poisson_coeffs2",
     "sphere_poisson_sample",
     "sphere_poisson_sum2",
@@ -99,6 +102,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.sphere_poisson_host_buffer_size.argtypes = [vp, psz]
     lib.sphere_poisson_solve_host.argtypes = [vp, vp, vp, vp, sz, vp, ctypes.POINTER(ctypes.c_double)]
     lib.sphere_poisson_solve_noalloc.argtypes = [vp, vp, vp, vp]
+    lib.sphere_poisson_device_status.argtypes = [vp, vp]
+    lib.sphere_poisson_wait_selftest.argtypes = [vp, u32, vp]
     lib.sphere_poisson_coeffs2.argtypes = [vp, vp, vp, vp, sz, vp]
     lib.sphere_poisson_sample.argtypes = [vp, vp, vp, vp, sz, vp]
     lib.sphere_poisson_sum2.argtypes = [vp, vp, vp, vp, sz, vp]

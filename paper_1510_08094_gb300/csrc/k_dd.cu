@@ -1,7 +1,10 @@
 // Double-float transform kernels and the refinement kernels (the SP_FP32_REFINE form).
 // That form has no adjoint, so only the forward instantiations exist.
 #define SP_REFINE_KERNELS
+#include <cudaTypedefs.h>
+
 #include <algorithm>
+#include <cstring>
 #include "launchers.inl"
 #include "fused_refine.cuh"
 
@@ -53,10 +56,41 @@ cudaError_t allow_transform_smem<dd>(int bytes) {
   upd(cudaFuncSetAttribute(k_refine_fused<true>, a, bytes));
   return e;
 }
+namespace {
+// the driver's tensor-map encoder, through the runtime (no link-time libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+// the [N][Kp] double-float spectrum as a 2D array of 32-bit words (4 per
+// element), box = one element (16 bytes) x kRefineBoxRows rows
+bool encode_column_map(CUtensorMap* m, const cpx<dd>* W, int N, int Kp) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || !W || N < 1 || (reinterpret_cast<uintptr_t>(W) & 15)) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)4 * Kp, (cuuint64_t)N};
+  const cuuint64_t strides[1] = {(cuuint64_t)Kp * sizeof(cpx<dd>)};
+  const cuuint32_t box[2] = {4, (cuuint32_t)kRefineBoxRows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<cpx<dd>*>(W), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
 void launch_refine_fused(bool big, const Launch& l, cpx<dd>* W, int N, int K, int Kp, const FftDesc& d,
                          const cpx<dd>* tw, const int* perm, const cpx<dd>* post_s, const cpx<dd>* post,
-                         const float* fiu, int sweeps) {
+                         const float* fiu, int sweeps, int* status) {
   if (K < 2) return;   // column 0 only: nothing for this kernel
+  CUtensorMap tm;
+  std::memset(&tm, 0, sizeof(tm));
+  const int use_tma = status && encode_column_map(&tm, W, N, Kp) ? 1 : 0;
   // persistent: as many CTAs as fit on the device at once, less one, at most one
   // per column.  A resident CTA fills its SM's registers and shared memory, so
   // the one SM left free is where the zonal column's one-CTA kernels (the
@@ -69,11 +103,26 @@ void launch_refine_fused(bool big, const Launch& l, cpx<dd>* W, int N, int K, in
   const int resident = bps > 0 ? std::max(1, bps * sms - 1) : K - 1;
   const dim3 grid(std::min(K - 1, resident));
   if (big)
-    k_refine_fused<true><<<grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, d, tw, perm, post_s, post, fiu, sweeps);
+    k_refine_fused<true><<<grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, d, tw, perm, post_s, post, fiu, sweeps,
+                                                                  tm, use_tma, status);
   else
-    k_refine_fused<false><<<grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, d, tw, perm, post_s, post, fiu, sweeps);
+    k_refine_fused<false><<<grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, d, tw, perm, post_s, post, fiu, sweeps,
+                                                                   tm, use_tma, status);
 }
 size_t refine_fused_smem(int N, int threads) { return refine_fused_smem_bytes(N, threads); }
+
+// one thread polls `polls` times for an mbarrier phase that nothing completes
+// (no arrival, no copy in flight), then records kStatusTmaTimeout: the path a
+// TMA wait takes when its copies never land
+__global__ void k_wait_selftest(int* status, unsigned polls) {
+  __shared__ uint64_t bar;
+  mbar_init(&bar, 1);
+  mbar_init_fence();
+  if (!mbar_wait_bounded(&bar, 0, polls)) atomicExch(status, kStatusTmaTimeout);
+}
+void launch_wait_selftest(int* status, unsigned polls, cudaStream_t st) {
+  k_wait_selftest<<<1, 1, 0, st>>>(status, polls);
+}
 
 void launch_refine(const Launch& l, const cpx<dd>* F, cpx<dd>* X, cpx<float>* Y, const float* fl,
                    const float* fiu, const float* fcu, int N, int K, int Kp, int first) {

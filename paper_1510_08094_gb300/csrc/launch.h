@@ -92,10 +92,15 @@ void launch_theta_poles(bool inverse, bool big, const Launch& l, cpx<double>* W,
 // the FP32 + refinement form's fused colatitude stage (fused_refine.cuh): one
 // CTA per column k >= 1 (column 0 is the FP64 zonal path's), in place in W
 // (double-float spectrum); refine_fused_smem dynamic bytes
+// The next columns' samples are copied by the tensor memory accelerator when
+// a tensor map of W can be encoded and `status` (a device int) is given, else
+// by cp.async; status receives kStatusTmaTimeout if a TMA wait gives up.
 void launch_refine_fused(bool big, const Launch& l, cpx<dd>* W, int N, int K, int Kp, const FftDesc& d,
                          const cpx<dd>* tw, const int* perm, const cpx<dd>* post_s, const cpx<dd>* post,
-                         const float* fiu, int sweeps);
+                         const float* fiu, int sweeps, int* status);
 size_t refine_fused_smem(int N, int threads);
+// a bounded wait that runs out: sets *status (device) to kStatusTmaTimeout
+void launch_wait_selftest(int* status, unsigned polls, cudaStream_t st);
 // pivots 1/u of the top-down factorisation of every parity chain, stored per
 // column ([k][j]), 2K threads
 void launch_factor_cols(const Launch& l, float* fiu, int N, int K);

@@ -307,6 +307,7 @@ struct sp_plan_s {
   double* geo;           // sin, cos theta_i; cos, sin lambda_q (the unit normal on the grid)
   double* mean_w;        // w_i / n: the quadrature weight of row i in the mean of f (single plans)
   int sms;               // multiprocessors of the plan's device
+  int* dev_status;       // device status word: nonzero when a kernel's bounded wait gave up (read by the host)
   double chop;           // relative coefficient threshold of the derivative operators (0: off)
   void* row_scale_t;     // the same in float (SP_FP32) or double-float (SP_FP32_REFINE)
   // the same tables in float (SP_FP32) or double-float (SP_FP32_REFINE)
@@ -365,6 +366,21 @@ int on_plan_device(sp_plan_t p) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   return dev == p->device ? SP_OK : SP_ERR_BAD_ARG;
+}
+
+// Reads and clears the plan's device status word after `st` has been
+// synchronised by the caller: SP_ERR_TIMEOUT if a kernel's bounded wait gave up.
+int take_device_status(sp_plan_t p, cudaStream_t st) {
+  if (!p->dev_status) return SP_OK;
+  int v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, p->dev_status, sizeof v, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "device status read");
+  if (v == 0) return SP_OK;
+  e = cudaMemsetAsync(p->dev_status, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "device status clear");
+  return SP_ERR_TIMEOUT;
 }
 
 int check_arrays(sp_plan_t p, const void* a, const void* b, const void* ws, size_t ws_bytes) {
@@ -722,7 +738,7 @@ void enqueue_refine(sp_plan_t p, const double* in, double* out, void* ws, cudaSt
                                p->perm_col, poc, inv_n, 0);
     cudaEventRecord(p->ev_join, p->side);
     sp::launch_refine_fused(p->big_col, Launch{dim3(1), p->fuse_threads, p->fuse_smem, st}, Fd, p->N, p->K, p->Kp,
-                            p->col_fft, twc, p->perm_col, pcs, poc, p->fc_iu, p->sweeps);
+                            p->col_fft, twc, p->perm_col, pcs, poc, p->fc_iu, p->sweeps, p->dev_status);
     m.mark(2);
     m.mark(3);
     cudaStreamWaitEvent(st, p->ev_join, 0);
@@ -1031,6 +1047,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   size_t o_mean_w = take(p->nt * sizeof(double));
   size_t o_perm_row = take(p->L * sizeof(int)), o_perm_col = take(p->N * sizeof(int));
   size_t o_tw_pole = take(tw_pole.size() * cd_sz), o_perm_pole = take(perm_pole.size() * sizeof(int));
+  size_t o_status = take(sizeof(int));
   size_t o_t_tw_row = take(t_tw_row.size()), o_t_tw_col = take(t_tw_col.size());
   size_t o_t_post_row = take(t_post_row.size()), o_t_post_col = take(t_post_col.size());
   size_t o_t_scale = take(t_scale.size());
@@ -1071,6 +1088,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   p->perm_col = reinterpret_cast<int*>(base + o_perm_col);
   p->tw_pole = poles ? reinterpret_cast<cpx<double>*>(base + o_tw_pole) : nullptr;
   p->perm_pole = poles ? reinterpret_cast<int*>(base + o_perm_pole) : nullptr;
+  p->dev_status = reinterpret_cast<int*>(base + o_status);
   p->tw_row_t = base + o_t_tw_row;
   p->tw_col_t = base + o_t_tw_col;
   p->post_row_t = base + o_t_post_row;
@@ -1166,6 +1184,7 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
   up(p->post_col_t, t_post_col.data(), t_post_col.size(), "copy post_col_t");
   up(p->row_scale_t, t_scale.data(), t_scale.size(), "copy row_scale_t");
   step(cudaMemset(base + o_fac_begin, 0, total - o_fac_begin), "clear factors");
+  step(cudaMemset(p->dev_status, 0, sizeof(int)), "clear status");
   if (rc == SP_OK) {
     int threads = 128, blocks = (2 * p->K + threads - 1) / threads;
     if (precision == SP_FP64) {
@@ -1921,6 +1940,7 @@ int sphere_poisson_solve_host(sp_plan_t plan, const double* f_host, double* u_ho
     SP_CUDA(cudaMemcpyAsync(u_host, d_u, bytes, cudaMemcpyDeviceToHost, st));
     if (f_mean_out && (rc = mean_check()) != SP_OK) return rc;
     SP_CUDA(cudaStreamSynchronize(st));
+    if ((rc = take_device_status(plan, st)) != SP_OK) return rc;
     return f_mean_out ? mean_status() : SP_OK;
   }
   // copies overlapped with the longitude transforms, in kHostChunks row chunks
@@ -1945,7 +1965,28 @@ int sphere_poisson_solve_host(sp_plan_t plan, const double* f_host, double* u_ho
   }
   SP_CUDA(cudaStreamSynchronize(plan->copy));
   SP_CUDA(cudaStreamSynchronize(st));
+  const int drc2 = take_device_status(plan, st);
+  if (drc2 != SP_OK) return drc2;
   return f_mean_out ? mean_status() : SP_OK;
+}
+
+int sphere_poisson_device_status(sp_plan_t plan, void* stream) {
+  if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
+  const int drc = on_plan_device(plan);
+  if (drc != SP_OK) return drc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SP_CUDA(cudaStreamSynchronize(st));
+  return take_device_status(plan, st);
+}
+
+int sphere_poisson_wait_selftest(sp_plan_t plan, unsigned polls, void* stream) {
+  if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
+  if (!plan->dev_status) return SP_ERR_UNSUPPORTED;
+  const int drc = on_plan_device(plan);
+  if (drc != SP_OK) return drc;
+  sp::launch_wait_selftest(plan->dev_status, polls, static_cast<cudaStream_t>(stream));
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SP_OK : cuda_fail(e, "wait self-test launch");
 }
 
 }  // extern "C"
@@ -2445,6 +2486,8 @@ const char* sphere_poisson_status_string(int status) {
     case SP_ERR_BAD_ARG: return "invalid argument";
     case SP_ERR_SCRATCH_LIMIT: return "grid too large for the 32 MiB fixed scratch of sphere_poisson_solve_noalloc; "
                                       "use sphere_poisson_solve with a workspace";
+    case SP_ERR_TIMEOUT: return "a kernel's bounded wait for its asynchronous copies gave up; the results of the "
+                                "solves since the last status check are not valid";
     default: return "unknown status";
   }
 }
