@@ -32,6 +32,7 @@
 #include <cooperative_groups.h>
 
 #include "kernels.cuh"
+#include "tma.cuh"
 
 namespace sp {
 
@@ -83,6 +84,24 @@ template <typename T>
 __host__ __device__ inline size_t fused_smem_bytes(int N, int cols, int threads, int buffers = 2) {
   const size_t buf = ((size_t)cols * N * sizeof(cpx<T>) + 15) & ~(size_t)15;
   return buffers * buf + (size_t)threads * sizeof(ScanSlot<T>);
+}
+
+// The single-buffer FP32 form with two columns per CTA can take its tile by
+// TMA: boxes of 16 bytes (the two columns' elements of a row) x kFusedBoxRows
+// rows land in row order in the buffer (padded to whole boxes), and each thread
+// then moves its kFusedTmaRegs or fewer elements through registers to their
+// digit-reversed positions.
+constexpr int kFusedBoxRows = 256;
+constexpr int kFusedTmaRegs = 24;
+__host__ __device__ inline bool fused1_tma_fits(int N, int cols, int threads) {
+  return cols == 2 && threads > 0 && (2 * N + threads - 1) / threads <= kFusedTmaRegs;
+}
+// dynamic shared memory of the single-buffer form: the buffer (or the padded
+// landing area of the TMA boxes, if larger) from a 128-byte boundary, the slots
+__host__ __device__ inline size_t fused1_smem_bytes(int N, int cols, int threads) {
+  const size_t buf = ((size_t)cols * N * sizeof(cpx<float>) + 15) & ~(size_t)15;
+  const size_t land = (size_t)((N + kFusedBoxRows - 1) / kFusedBoxRows) * kFusedBoxRows * cols * sizeof(cpx<float>);
+  return 128 + (buf > land ? buf : land) + (size_t)threads * sizeof(ScanSlot<float>);
 }
 
 // Phase 2 of one chain's scan, run by one warp: slots slot[q * stride] for the
@@ -560,19 +579,68 @@ __device__ __forceinline__ void store_dif_columns(const cpx<T>* __restrict__ sm,
 // digit-reversed output), read back through the same permutation at the store.
 // Half the shared memory of the two-buffer form, so two columns per CTA keep
 // two CTAs per SM.
+//
+// With use_tma (two columns per CTA, fused1_tma_fits) the tile arrives by TMA
+// (tensor map tmW: the [N][Kp] spectrum as 32-bit words) on an mbarrier with a
+// bounded wait; a wait that gives up sets *status = kStatusTmaTimeout and the
+// CTA stops.
 template <bool BIG>
-__global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_fused1(
+__global__ void __launch_bounds__(BIG ? 256 : 512, BIG ? 1 : 2) k_theta_fused1(
     cpx<float>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d, const cpx<float>* __restrict__ tw,
     const int* __restrict__ perm, const cpx<float>* __restrict__ post_s, const cpx<float>* __restrict__ post,
-    const float* __restrict__ fiu) {
+    const float* __restrict__ fiu, const __grid_constant__ CUtensorMap tmW, int use_tma,
+    int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t bar;
+  // the first 128-byte boundary of the dynamic region (128 spare bytes are allocated)
+  unsigned char* smem_al = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   const size_t buf = ((size_t)cols * N * sizeof(cpx<float>) + 15) & ~(size_t)15;
-  cpx<float>* sm = reinterpret_cast<cpx<float>*>(smem_raw);
-  ScanSlot<float>* slot = reinterpret_cast<ScanSlot<float>*>(smem_raw + buf);
+  const int nbox = (N + kFusedBoxRows - 1) / kFusedBoxRows;
+  const size_t land = (size_t)nbox * kFusedBoxRows * cols * sizeof(cpx<float>);
+  cpx<float>* sm = reinterpret_cast<cpx<float>*>(smem_al);
+  ScanSlot<float>* slot = reinterpret_cast<ScanSlot<float>*>(smem_al + (buf > land ? buf : land));
   const int k0 = blockIdx.x * cols;
 
   // 1. load (Makhoul reordering, digit-reversed positions) and forward DIT transform
-  theta_forward_load<float>(k0, sm, FromGlobal<cpx<float>>{W + k0, (size_t)Kp}, N, K, cols, perm);
+  if (use_tma) {
+    if (threadIdx.x == 0) {
+      mbar_init(&bar, 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
+    // (sm is 128-byte aligned by construction and each box is 4096 bytes; a
+    // misaligned destination is not issued, and the wait below reports it)
+    if (threadIdx.x == 0 && (smem_u32(sm) & 127u) == 0) {
+      mbar_expect_tx(&bar, (unsigned)land);
+      for (int b = 0; b < nbox; ++b) tma_load_2d(sm + b * kFusedBoxRows * 2, &tmW, 2 * k0, b * kFusedBoxRows, &bar);
+    }
+    const bool ok = mbar_wait_bounded(&bar, 0, kTmaPolls);
+    if (__syncthreads_or(!ok)) {
+      mbar_wait_bounded(&bar, 0, kTmaPolls);            // the copies still in flight
+      __syncthreads();
+      if (threadIdx.x == 0) atomicExch(status, kStatusTmaTimeout);
+      return;
+    }
+    // row-ordered elements e = 2 i + c to their digit-reversed positions, through registers
+    cpx<float> v[kFusedTmaRegs];
+#pragma unroll
+    for (int t = 0; t < kFusedTmaRegs; ++t) {
+      const int e = (int)threadIdx.x + t * (int)blockDim.x;
+      if (e < 2 * N) v[t] = sm[e];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < kFusedTmaRegs; ++t) {
+      const int e = (int)threadIdx.x + t * (int)blockDim.x;
+      if (e < 2 * N) {
+        const int i = e >> 1, c = e & 1, k = k0 + c;
+        const cpx<float> z = k < K ? neg_if(v[t], (k & 1) && (i & 1)) : cpx<float>{0.f, 0.f};
+        sm[c * N + __ldg(perm + makhoul_pos(i, N))] = z;
+      }
+    }
+  } else {
+    theta_forward_load<float>(k0, sm, FromGlobal<cpx<float>>{W + k0, (size_t)Kp}, N, K, cols, perm);
+  }
   __syncthreads();
   fft_run<-1, BIG>(sm, cols, d, tw);
   // 2. post-twiddle in place on the pairs (j, N - j) (theta_forward_finish, forward form)

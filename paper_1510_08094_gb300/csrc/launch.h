@@ -80,9 +80,12 @@ void launch_factor(const Launch& l, S* fl, S* fiu, S* fcu, int N, int K, int Kp,
 // buffer (decimation-in-frequency inverse); cols = 0: one column per CTA in
 // clusters of four that share their loads and stores (l.grid is ignored);
 // theta_fused_smem dynamic bytes
+// The single-buffer form with two columns per CTA takes its tile by TMA when a
+// tensor map of W can be encoded and `status` (a device int) is given; status
+// receives kStatusTmaTimeout if the bounded wait gives up.
 void launch_theta_fused(bool big, const Launch& l, cpx<float>* W, int N, int K, int Kp, int cols, const FftDesc& d,
                         const cpx<float>* tw, const int* perm, const cpx<float>* post_s, const cpx<float>* post,
-                        const float* fiu, float inv_n);
+                        const float* fiu, float inv_n, int* status);
 size_t theta_fused_smem(int N, int cols, int threads);
 // the colatitude transforms of the grid with both poles (poles.cuh): one CTA
 // per column k < K (grid K), 2N complex doubles of dynamic shared memory;

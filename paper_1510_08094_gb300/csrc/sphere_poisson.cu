@@ -680,7 +680,7 @@ void enqueue_fp32(sp_plan_t p, bool adj, const double* in, double* out, void* ws
                            Launch{dim3((p->K + std::max(p->fuse_cols, 1) - 1) / std::max(p->fuse_cols, 1)),
                                   p->fuse_threads, p->fuse_smem, st},  // grid recomputed for cols <= 0
                            W, p->N, p->K, p->Kp, p->fuse_cols, p->col_fft, twc, p->perm_col,
-                           static_cast<const cpx<float>*>(p->post_col_s_t), poc, p->fc_iu, inv_n);
+                           static_cast<const cpx<float>*>(p->post_col_s_t), poc, p->fc_iu, inv_n, p->dev_status);
     m.mark(2);
     m.mark(3);
   } else {
