@@ -55,13 +55,13 @@ TRAFFIC_CAPTURE = {
               "rows_inverse": 200361728 + 143462656},
 }
 # the same for the FP32 form's dominant kernel, the fused colatitude stage
-# (k_theta_fused1, one column per CTA at 5000 x 5000; `ncu --section ...
-# --metrics dram__bytes_read.sum,dram__bytes_write.sum` on two launches after
-# warm-up), over the sources it is compiled from
+# (k_theta_fused1 with two columns per CTA, its tile by TMA, at 5000 x 5000;
+# `ncu --section ... --metrics dram__bytes_read.sum,dram__bytes_write.sum` on
+# two launches after warm-up), over the sources it is compiled from
 TRAFFIC_CAPTURE_FP32 = {
-    "csrc_sha256": "f64026d50d0baadb",
+    "csrc_sha256": "d8ea4bef5b5cc6f0",
     "n_theta": 5000, "n_lambda": 5000,
-    "bytes": {"theta_fused": 150865920 + 49989376},
+    "bytes": {"theta_fused": 150894848 + 50328832},
 }
 
 
