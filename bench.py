@@ -837,7 +837,7 @@ def measure_mixed_sizes(sp, dev, args):
 
 def measure_batched(sp, dev, args, rank: int = 0, world: int = 1):
     """4096 spheres of uneven resolution (n_theta = 16 s, s uniform in 2..32,
-    n_lambda = 2 n_theta, SH series l <= n_theta/2) in one persistent launch
+    n_lambda = 2 n_theta, SH series l <= n_theta/2) in persistent launches (one per radix group)
     with autotuned tiles, against the same problems solved one by one with
     single-problem FP64 plans; then the same batch in FP32 + refinement.
     With several ranks the problems are split by shard_lpt (no collective on the
@@ -914,7 +914,7 @@ def measure_batched(sp, dev, args, rank: int = 0, world: int = 1):
                         f"on the data path; this rank {len(sizes)} problems, {plan.offsets[-1]} DOF"
                         if world > 1 else "single GPU")}
 
-    # the same batch in FP32 + refinement (one sweep), one persistent launch
+    # the same batch in FP32 + refinement (one sweep), the same launches
     sweeps = 1
     t0 = time.perf_counter()
     rplan = sp.BatchedPlan(sizes, precision="fp32_refine", refine_sweeps=sweeps, autotune=True, device=dev)

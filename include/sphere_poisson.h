@@ -112,10 +112,12 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
 /*
  * Batched plan: `count` independent spheres of uneven resolution, problem b on
  * an n_theta[b] x n_lambda[b] grid (each size obeying the rules above), solved
- * together in ONE persistent kernel launch: every CTA repeatedly claims the
- * next problem (largest first) from an atomic counter and runs all stages of
- * that problem itself, with the spectrum in its own scratch slot.  Problem
- * sizes share tables.  f and u of the solve calls are then the problems'
+ * together by persistent kernels: every CTA repeatedly claims the next problem
+ * (largest first) from an atomic counter and runs all stages of that problem
+ * itself, with the spectrum in its own scratch slot.  Sizes whose transforms
+ * use radices <= 8 only and sizes that need the large-prime passes go to two
+ * launches (one per group, each with its own counter): the first kernel needs
+ * half the registers and runs two CTAs per SM.  Problem sizes share tables.  f and u of the solve calls are then the problems'
  * [n_theta][n_lambda] arrays packed back to back in problem order, problem b
  * starting at offsets[b] doubles (sphere_poisson_batch_offsets).
  *   precision   SP_FP64, or SP_FP32_REFINE (the arithmetic of the single-plan
@@ -127,7 +129,9 @@ int sphere_poisson_plan(sp_plan_t* plan, int n_theta, int n_lambda, int precisio
  *               environment variable SPHERE_POISSON_TUNE_CACHE if it is set.
  * count = 0 gives a plan whose solve does nothing.  The batched plan supports
  * sphere_poisson_solve (and _solve_host); the adjoint returns SP_ERR_UNSUPPORTED.
- * The solve issues one cudaMemsetAsync (the work counter) and one kernel.
+ * The solve issues one cudaMemsetAsync (the two work counters) and one kernel
+ * per non-empty group (sphere_poisson_launch_count), and can be captured in a
+ * CUDA graph as a whole.
  */
 int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, const int* n_lambda,
                                 int precision, int refine_sweeps, unsigned flags, size_t* workspace_bytes);

@@ -372,7 +372,7 @@ class Plan:
 
 
 class BatchedPlan(Plan):
-    """Many independent spheres of uneven resolution solved in one persistent launch.
+    """Many independent spheres of uneven resolution solved by persistent launches (one per radix group).
 
     sizes: sequence of (n_theta, n_lambda).  The solve takes and returns the
     problems' grids packed back to back in one float64 CUDA tensor (see

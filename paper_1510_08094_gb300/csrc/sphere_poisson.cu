@@ -350,10 +350,17 @@ struct sp_plan_s {
   size_t total;                      // doubles in the packed f / u arrays
   std::vector<size_t> offsets;       // count + 1
   sp::BatchArgs bargs;               // device pointers (f, u, scratch, counter filled per call)
-  bool bbig;
-  int bgrid, bthreads;
+  bool bbig;                         // some class needs the large-prime passes
+  // The problems are launched in two groups, each a persistent kernel with its
+  // own work counter: the classes whose transforms use radices <= 8 only
+  // (order[0 .. bsplit), a kernel fitting two CTAs per SM) and those that need
+  // the large-prime passes (order[bsplit .. count), one CTA per SM).
+  int bsplit;
+  int bgrid_g[2];
+  size_t bsmem_g[2];
+  int bgrid, bthreads;               // bgrid: the larger group grid (scratch slots)
   size_t bsmem;
-  size_t off_counter;                // counter position in the workspace
+  size_t off_counter;                // two counters in the workspace
 };
 
 namespace {
@@ -775,14 +782,15 @@ void enqueue_refine(sp_plan_t p, const double* in, double* out, void* ws, cudaSt
   m.done();
 }
 
-// the persistent kernel of the plan's arithmetic
-cudaError_t batched_occupancy(const sp_plan_s* p, size_t smem, int* bps) {
-  if (p->precision == SP_FP64) return sp::batched_fp64_occupancy(p->bbig, kBatchThreadsPerCta, smem, bps);
-  return sp::batched_refine_occupancy(p->bbig, kBatchThreadsPerCta, smem, bps);
+// the persistent kernel of the plan's arithmetic; big: with the large-prime passes
+cudaError_t batched_occupancy(const sp_plan_s* p, bool big, size_t smem, int* bps) {
+  if (p->precision == SP_FP64) return sp::batched_fp64_occupancy(big, kBatchThreadsPerCta, smem, bps);
+  return sp::batched_refine_occupancy(big, kBatchThreadsPerCta, smem, bps);
 }
-void launch_batched_kernel(const sp_plan_s* p, dim3 grid, size_t smem, cudaStream_t st, const sp::BatchArgs& a) {
-  if (p->precision == SP_FP64) sp::launch_batched_fp64(p->bbig, grid, kBatchThreadsPerCta, smem, st, a);
-  else sp::launch_batched_refine(p->bbig, grid, kBatchThreadsPerCta, smem, st, a);
+void launch_batched_kernel(const sp_plan_s* p, bool big, dim3 grid, size_t smem, cudaStream_t st,
+                           const sp::BatchArgs& a) {
+  if (p->precision == SP_FP64) sp::launch_batched_fp64(big, grid, kBatchThreadsPerCta, smem, st, a);
+  else sp::launch_batched_refine(big, grid, kBatchThreadsPerCta, smem, st, a);
 }
 
 int launch_batched(sp_plan_t p, const double* in, double* out, void* workspace, cudaStream_t st) {
@@ -791,12 +799,20 @@ int launch_batched(sp_plan_t p, const double* in, double* out, void* workspace, 
   a.f = in;
   a.u = out;
   a.scratch = static_cast<cpx<double>*>(workspace);
-  a.counter = reinterpret_cast<int*>(static_cast<char*>(workspace) + p->off_counter);
-  cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(batch counter)");
+  int* counters = reinterpret_cast<int*>(static_cast<char*>(workspace) + p->off_counter);
+  cudaError_t e = cudaMemsetAsync(counters, 0, 2 * sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(batch counters)");
   StageMarks m{p, st, !p->prof_events.empty() && p->prof_count < p->prof_max};
   m.mark(0);
-  launch_batched_kernel(p, dim3(p->bgrid), p->bsmem, st, a);
+  const int first[2] = {0, p->bsplit}, n[2] = {p->bsplit, p->count - p->bsplit};
+  for (int g = 0; g < 2; ++g) {
+    if (n[g] == 0) continue;
+    sp::BatchArgs ag = a;
+    ag.order = a.order + first[g];
+    ag.count = n[g];
+    ag.counter = counters + g;
+    launch_batched_kernel(p, g == 1, dim3(p->bgrid_g[g]), p->bsmem_g[g], st, ag);
+  }
   for (int s = 1; s <= kStages; ++s) m.mark(s);
   m.done();
   e = cudaGetLastError();
@@ -1489,8 +1505,9 @@ int tune_class(sp_plan_t p, int ci, std::vector<sp::BatchClass>& cls, sp::BatchC
       c.cols = q;
       cudaMemcpy(d_cls + ci, &c, sizeof(sp::BatchClass), cudaMemcpyHostToDevice);
       const size_t smem = class_smem(c);
+      const bool big = needs_big(c.row_fft) || needs_big(c.col_fft);
       int bps = 0;
-      if (batched_occupancy(p, smem, &bps) != cudaSuccess || bps < 1) continue;
+      if (batched_occupancy(p, big, smem, &bps) != cudaSuccess || bps < 1) continue;
       sp::BatchArgs a = p->bargs;
       a.problems = d_prob;
       a.order = d_order;
@@ -1504,7 +1521,7 @@ int tune_class(sp_plan_t p, int ci, std::vector<sp::BatchClass>& cls, sp::BatchC
       for (int rep = 0; rep < 3; ++rep) {
         cudaMemsetAsync(d_counter, 0, sizeof(int), 0);
         cudaEventRecord(e0, 0);
-        launch_batched_kernel(p, dim3(grid), smem, 0, a);
+        launch_batched_kernel(p, big, dim3(grid), smem, 0, a);
         cudaEventRecord(e1, 0);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -1753,9 +1770,15 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
     prob[b] = {prob_cls[b], 0, (long long)p->offsets[b]};
     order[b] = b;
   }
+  // the small-radix group first, then the large-prime group; largest first in each
+  auto cls_big = [&](int c) { return needs_big(cls[c].row_fft) || needs_big(cls[c].col_fft); };
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const bool bx = cls_big(prob_cls[x]), by = cls_big(prob_cls[y]);
+    if (bx != by) return !bx;
     return (size_t)n_theta[x] * n_lambda[x] > (size_t)n_theta[y] * n_lambda[y];
   });
+  p->bsplit = 0;
+  for (int b = 0; b < count; ++b) p->bsplit += cls_big(prob_cls[b]) ? 0 : 1;
   sp::BatchClass* d_cls = reinterpret_cast<sp::BatchClass*>(base + o_cls);
   sp::BatchProblem* d_prob = reinterpret_cast<sp::BatchProblem*>(base + o_prob);
   int* d_order = reinterpret_cast<int*>(base + o_order);
@@ -1771,8 +1794,8 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
   size_t smem = 0;
   for (auto& b : cls) smem = std::max(smem, class_smem(b));
   int bps = 0;
-  step(batched_occupancy(p, std::max(smem, (size_t)200 * 1024), &bps), "occupancy");
-  p->bgrid = std::max(1, std::min(count, sms * std::max(bps, 1)));
+  step(batched_occupancy(p, p->bbig, std::max(smem, (size_t)200 * 1024), &bps), "occupancy");
+  p->bgrid = std::max(1, std::min(count, sms * std::max(bps, 1)));   // the tuner's timing grid
 
   // autotuning of the transform tiles per size class
   if (rc == SP_OK && count > 0 && (flags & SP_FLAG_AUTOTUNE)) {
@@ -1828,6 +1851,8 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
       for (auto& l : new_lines) out << l << "\n";
     }
   }
+  // per group: shared memory of its largest class, a persistent grid at the
+  // kernel's occupancy, at most one CTA per problem
   smem = 0;
   for (auto& b : cls) smem = std::max(smem, class_smem(b));
   p->bsmem = smem;
@@ -1835,8 +1860,20 @@ int sphere_poisson_plan_batched(sp_plan_t* plan, int count, const int* n_theta, 
   if (count > 0) {
     step(cudaMemcpy(d_prob, prob.data(), count * sizeof(sp::BatchProblem), cudaMemcpyHostToDevice), "copy problems");
     step(cudaMemcpy(d_order, order.data(), count * sizeof(int), cudaMemcpyHostToDevice), "copy order");
-    step(batched_occupancy(p, smem, &bps), "occupancy");
-    p->bgrid = std::max(1, std::min(count, sms * std::max(bps, 1)));
+    p->bgrid = 1;
+    for (int g = 0; g < 2; ++g) {
+      const int n = g == 0 ? p->bsplit : count - p->bsplit;
+      size_t gs = 0;
+      for (int c = 0; c < nc; ++c)
+        if (cls_big(c) == (g == 1)) gs = std::max(gs, class_smem(cls[c]));
+      p->bsmem_g[g] = gs;
+      p->bgrid_g[g] = 0;
+      if (n == 0) continue;
+      int gbps = 0;
+      step(batched_occupancy(p, g == 1, gs, &gbps), "occupancy");
+      p->bgrid_g[g] = std::max(1, std::min(n, sms * std::max(gbps, 1)));
+      p->bgrid = std::max(p->bgrid, p->bgrid_g[g]);
+    }
   }
   p->off_counter = align((size_t)p->bgrid * max_slot * sizeof(cpx<double>));
   p->ws_bytes = p->off_counter + 256;
@@ -2401,7 +2438,7 @@ int sphere_poisson_solve_lowrank(sp_plan_t plan, int terms, const double* cols, 
 int sphere_poisson_launch_count(sp_plan_t plan, int adjoint, int* launches) {
   if (!plan_ok(plan)) return SP_ERR_BAD_PLAN;
   if (!launches) return SP_ERR_NULL;
-  if (plan->batched) *launches = plan->count ? 1 : 0;
+  if (plan->batched) *launches = (plan->bsplit > 0 ? 1 : 0) + (plan->count > plan->bsplit ? 1 : 0);
   else if (plan->precision == SP_FP64) *launches = kStages;
   else if (plan->precision == SP_FP32) *launches = (plan->fused && !adjoint ? kStages - 2 : kStages) + 3;
   else if (adjoint) *launches = 0;

@@ -116,6 +116,35 @@ def test_batched_launch_captured_in_cuda_graph(sp):
     assert _rel(u, plan.solve(f2)) < 1e-15
 
 
+@pytest.mark.parametrize("precision,sweeps", [("fp64", 0), ("fp32_refine", 1)])
+def test_mixed_radix_groups_two_launches_in_one_graph(sp, precision, sweeps):
+    # 44 = 4 * 11 and 33 = 3 * 11 need the large-prime passes, 32 and 64 do not:
+    # the solve is one launch per group, and the pair captures into one graph
+    sizes = [(32, 64), (44, 88), (64, 128), (33, 66), (32, 64)]
+    plan = sp.BatchedPlan(sizes, precision, sweeps)
+    assert plan.launches() == 2
+    fs = _inputs(sizes, 12)
+    f = plan.pack(fs)
+    u = torch.empty_like(f)
+    ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+    plan.solve(f, u, ws)
+    torch.cuda.synchronize()
+    for b, (nt, nl) in enumerate(sizes):
+        single = sp.Plan(nt, nl, precision, sweeps).solve(fs[b])
+        got = u[plan.offsets[b]:plan.offsets[b + 1]].view(nt, nl)
+        assert _rel(got, single) < (1e-12 if precision == "fp64" else 1e-11)
+    ref = u.clone()
+    u.zero_()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.solve(f, u, ws)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(u, ref)
+
+
 def test_empty_batch(sp):
     plan = sp.BatchedPlan([])
     assert plan.offsets == [0]
