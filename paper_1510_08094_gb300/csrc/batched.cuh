@@ -83,7 +83,7 @@ __device__ __forceinline__ void solve_chains_cta(cpx<double>* __restrict__ W, co
 }
 
 template <bool BIG>
-__global__ void __launch_bounds__(256, BIG ? 1 : 3) k_batched_fp64(BatchArgs a) {
+__global__ void __launch_bounds__(256, BIG ? 2 : 3) k_batched_fp64(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<double>* sm = reinterpret_cast<cpx<double>*>(smem_raw);
   __shared__ int s_item;

@@ -205,7 +205,7 @@ __device__ __forceinline__ void zonal_finish(cpx<dd>* __restrict__ X, int N, int
 // N x Kp each, 16 bytes an element) then Y (complex FP32, N x Kp): 40 bytes per
 // spectral element.
 template <bool BIG>
-__global__ void __launch_bounds__(256, BIG ? 1 : 2) k_batched_refine(BatchArgs a) {
+__global__ void __launch_bounds__(256, 2) k_batched_refine(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<dd>* sm = reinterpret_cast<cpx<dd>*>(smem_raw);
   __shared__ int s_item;
