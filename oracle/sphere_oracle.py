@@ -38,9 +38,9 @@ The per-k systems are solved by dense LU (numpy.linalg.solve) at small m and
 by LAPACK's banded LU (scipy.linalg.solve_banded) otherwise; neither uses the
 parity split or the BMC fold, which are properties the tests check.
 
-Also here: the same solve on the grid with both poles (theta_i = i pi /
-n_theta, i = 0..n_theta; the DFS grid theta_p = -pi + 2 pi p / m, the same
-per-k systems), the structure-preserving GE of Section 3 and the low-rank form of
+Also here: the same solve and its transpose on the grid with both poles
+(theta_i = i pi / n_theta, i = 0..n_theta; the DFS grid theta_p = -pi + 2 pi p
+/ m, the same per-k systems), the structure-preserving GE of Section 3 and the low-rank form of
 the coefficients F, the surface integral sum2 (Section 4, Integration, eq.
 integrationCoeffs), the tangential derivatives of Section 4 (Differentiation,
 eqs. diff_x..diff_z with the division by sin theta through M_sin^{-1}) and the
@@ -695,6 +695,34 @@ def poisson_adjoint(g: np.ndarray, reading: str = "B") -> np.ndarray:
     out = vbar[nt:].copy()
     back = vbar[:nt][::-1]                         # row n_theta-1-p -> f row i
     out += np.roll(back, n // 2, axis=1)           # undo the q + n/2 shift
+    return out
+
+
+def poisson_poles_adjoint(g: np.ndarray, reading: str = "B") -> np.ndarray:
+    """S^T g for the real-linear map S: f -> u of poisson_poles(), step by step
+    as poisson_adjoint: the restriction to the rows p = n_theta..m-1 and p = 0
+    becomes a zero-extension, the complex-linear maps their conjugate
+    transposes, and the doubling with poles (rows p = n_theta + i from f row i,
+    rows p = n_theta - i from f row i at lambda + pi) a fold."""
+    g = np.asarray(g, dtype=np.float64)
+    rows, n = g.shape
+    nt = rows - 1
+    m = 2 * nt
+    Gfull = np.zeros((m, n), dtype=np.complex128)
+    Gfull[nt:] = g[:nt]
+    Gfull[0] += g[nt]
+    Et = _phase_theta_poles(m)
+    El = _phase_lambda(n)
+    Xbar = Et @ Gfull @ El.T
+    Fbar = _solve_columns_T(Xbar, reading)
+    Fbar[m // 2, n // 2] = 0.0
+    if reading == "B":
+        Fbar[0, :] = 0.0
+    Vbar = (Et.conj().T @ Fbar @ El.conj()) / (m * n)
+    vbar = np.sin(dfs_theta_poles(m))[:, None] ** 2 * Vbar.real
+    out = np.zeros((rows, n), dtype=np.float64)
+    out[:nt] += vbar[nt:]
+    out[nt:0:-1] += np.roll(vbar[:nt], n // 2, axis=1)   # row p < n_theta from f row n_theta - p
     return out
 
 

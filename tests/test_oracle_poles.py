@@ -10,13 +10,16 @@ theta in [0, pi]), pinned by what does not depend on the oracle itself.
   * The samples of f on the pole rows are multiplied by sin^2 theta = 0: they
     do not change u.
   * Its surface integral of the printed polynomial is 216 pi / 35.
+  * Its transpose of f -> u equals the dense matrix of the solve, built
+    column by column from unit inputs, transposed.
   * u is the same function whichever grid samples f: on the rows both grids
     share no point, so the check is the interpolant, evaluated from the
     pole-grid coefficients at the pole-free colatitudes, against the
     pole-free solve of the same band-limited f.
-Three plausible mistakes in the pole-grid code (the pole-free grid's phase,
+Four plausible mistakes in the pole-grid code (the pole-free grid's phase,
 the glide reflection without its half-turn in longitude, the south pole row
-taken from the wrong end of the doubled grid) are planted and caught."""
+taken from the wrong end of the doubled grid, the transpose's fold without the
+half-turn) are planted and caught."""
 
 import math
 
@@ -89,8 +92,24 @@ def pin_sum2_worked_example():
     return abs(O.sum2_poles(f) - 216 * math.pi / 35) < 2e-14
 
 
+def pin_dense_transpose():
+    # the transpose of f -> u built column by column from the solve itself
+    rng = np.random.default_rng(11)
+    for nt, nl in [(3, 6), (4, 8), (8, 16)]:
+        size = (nt + 1) * nl
+        S = np.zeros((size, size))
+        for c in range(size):
+            e = np.zeros(size)
+            e[c] = 1.0
+            S[:, c] = O.poisson_poles(e.reshape(nt + 1, nl)).ravel()
+        g = rng.standard_normal((nt + 1, nl))
+        if np.abs(O.poisson_poles_adjoint(g).ravel() - S.T @ g.ravel()).max() > 1e-13 * np.abs(S).max() * size:
+            return False
+    return True
+
+
 PINS = [pin_dft_of_trig_polynomial, pin_closed_forms, pin_series, pin_same_function_on_both_grids,
-        pin_sum2_worked_example]
+        pin_sum2_worked_example, pin_dense_transpose]
 
 
 def test_pole_grid_oracle_passes_its_pins():
@@ -147,10 +166,31 @@ def _poisson_poles_south_row_from_p_last(f, reading="B", method="auto", return_a
     return np.concatenate([U[nt:], U[-1:]], axis=0).real
 
 
+def _adjoint_fold_without_half_turn(g, reading="B"):
+    g = np.asarray(g, dtype=np.float64)
+    rows, n = g.shape
+    nt = rows - 1
+    m = 2 * nt
+    Gfull = np.zeros((m, n), dtype=np.complex128)
+    Gfull[nt:] = g[:nt]
+    Gfull[0] += g[nt]
+    Et = O._phase_theta_poles(m)
+    El = O._phase_lambda(n)
+    Fbar = O._solve_columns_T(Et @ Gfull @ El.T, reading)
+    Fbar[m // 2, n // 2] = 0.0
+    Fbar[0, :] = 0.0
+    vbar = np.sin(O.dfs_theta_poles(m))[:, None] ** 2 * ((Et.conj().T @ Fbar @ El.conj()) / (m * n)).real
+    out = np.zeros((rows, n))
+    out[:nt] += vbar[nt:]
+    out[nt:0:-1] += vbar[:nt]
+    return out
+
+
 MISTAKES = [
     ("_phase_theta_poles", _phase_of_pole_free_grid, {"pin_dft_of_trig_polynomial", "pin_closed_forms"}),
     ("dfs_double_poles", _double_without_half_turn, {"pin_closed_forms", "pin_series"}),
     ("poisson_poles", _poisson_poles_south_row_from_p_last, {"pin_closed_forms", "pin_series"}),
+    ("poisson_poles_adjoint", _adjoint_fold_without_half_turn, {"pin_dense_transpose"}),
 ]
 
 
