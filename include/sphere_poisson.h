@@ -77,8 +77,9 @@ typedef struct sp_plan_s* sp_plan_t;
  * SP_ERR_UNSUPPORTED), 2 n_theta <= 12288 with 2 n_theta factoring into primes
  * <= 31 (else SP_ERR_BAD_SIZE).  Such a plan supports sphere_poisson_solve
  * (f_mean_out included: the same quadrature on this grid, each pole row
- * weighted once), _solve_host, _solve_noalloc, the profiling and size queries;
- * every other call on it returns SP_ERR_UNSUPPORTED (the adjoint, the
+ * weighted once), _solve_adjoint (the transpose of that solve, on the same
+ * [n_theta + 1][n_lambda] arrays), _solve_host, _solve_noalloc, the profiling
+ * and size queries; every other call on it returns SP_ERR_UNSUPPORTED (the
  * transforms alone, sum2, the derivatives and the low-rank calls).
  */
 #define SP_FLAG_POLES 2u

@@ -437,24 +437,33 @@ _plans: dict = {}
 _plans_lock = threading.Lock()
 
 
-def get_plan(n_theta: int, n_lambda: int, precision: str = "fp64", refine_sweeps: int = 0, device=None) -> Plan:
+def get_plan(n_theta: int, n_lambda: int, precision: str = "fp64", refine_sweeps: int = 0, device=None,
+             grid: str = "shifted") -> Plan:
     dev = torch.cuda.current_device() if device is None else torch.device(device).index or 0
-    key = (int(n_theta), int(n_lambda), precision, int(refine_sweeps), dev)
+    key = (int(n_theta), int(n_lambda), precision, int(refine_sweeps), dev, grid)
     with _plans_lock:
         p = _plans.get(key)
         if p is None:
-            p = Plan(n_theta, n_lambda, precision, refine_sweeps, device=torch.device("cuda", dev))
+            p = Plan(n_theta, n_lambda, precision, refine_sweeps, device=torch.device("cuda", dev), grid=grid)
             _plans[key] = p
         return p
 
 
-def solve(f: torch.Tensor, precision: str = "fp64", refine_sweeps: int = 0) -> torch.Tensor:
-    """u = S f on f's device (cached plan per shape)."""
-    return get_plan(f.shape[0], f.shape[1], precision, refine_sweeps, f.device).solve(f)
+def _grid_n_theta(rows: int, grid: str) -> int:
+    return rows - 1 if grid == "poles" else rows
 
 
-def solve_adjoint(ubar: torch.Tensor, precision: str = "fp64", refine_sweeps: int = 0) -> torch.Tensor:
-    return get_plan(ubar.shape[0], ubar.shape[1], precision, refine_sweeps, ubar.device).solve_adjoint(ubar)
+def solve(f: torch.Tensor, precision: str = "fp64", refine_sweeps: int = 0, grid: str = "shifted") -> torch.Tensor:
+    """u = S f on f's device (cached plan per shape); grid="poles" takes f with
+    n_theta + 1 rows on the grid with both poles."""
+    return get_plan(_grid_n_theta(f.shape[0], grid), f.shape[1], precision, refine_sweeps, f.device,
+                    grid).solve(f)
+
+
+def solve_adjoint(ubar: torch.Tensor, precision: str = "fp64", refine_sweeps: int = 0,
+                  grid: str = "shifted") -> torch.Tensor:
+    return get_plan(_grid_n_theta(ubar.shape[0], grid), ubar.shape[1], precision, refine_sweeps, ubar.device,
+                    grid).solve_adjoint(ubar)
 
 
 class SpherePoisson(torch.autograd.Function):
@@ -466,17 +475,18 @@ class SpherePoisson(torch.autograd.Function):
     itself is not differentiated (its iterates depend on f through rounding only)."""
 
     @staticmethod
-    def forward(ctx, f, precision="fp64", refine_sweeps=0):
+    def forward(ctx, f, precision="fp64", refine_sweeps=0, grid="shifted"):
         if precision not in _PRECISIONS:
             raise ValueError(f"precision must be one of {sorted(_PRECISIONS)}")
         ctx.precision = precision
-        return solve(f.contiguous(), precision, refine_sweeps)
+        ctx.grid = grid
+        return solve(f.contiguous(), precision, refine_sweeps, grid)
 
     @staticmethod
     def backward(ctx, grad_u):
         adj = "fp64" if ctx.precision == "fp32_refine" else ctx.precision
-        g = solve_adjoint(grad_u.contiguous(), adj)
-        return g, None, None
+        g = solve_adjoint(grad_u.contiguous(), adj, 0, ctx.grid)
+        return g, None, None, None
 
 
 def pipe_rates() -> dict:
@@ -487,5 +497,5 @@ def pipe_rates() -> dict:
     return {"fp64_fma_gops": a.value, "fp32_fma_gops": b.value}
 
 
-def poisson(f: torch.Tensor, precision: str = "fp64", refine_sweeps: int = 0) -> torch.Tensor:
-    return SpherePoisson.apply(f, precision, refine_sweeps)
+def poisson(f: torch.Tensor, precision: str = "fp64", refine_sweeps: int = 0, grid: str = "shifted") -> torch.Tensor:
+    return SpherePoisson.apply(f, precision, refine_sweeps, grid)

@@ -34,6 +34,16 @@ void launch_theta_inverse<double>(bool adj, bool big, const Launch& l, cpx<doubl
                                   const cpx<double>* post, double inv_n, int zonal) {
   SP_PICK(k_theta_inverse, double, adj, big, W, N, K, Kp, cols, d, tw, perm, post, inv_n, zonal);
 }
+void launch_theta_poles_adj(bool last, bool big, const Launch& l, cpx<double>* W, int N, int K, int Kp,
+                            const FftDesc& d, const cpx<double>* tw, const int* perm) {
+  if (last) {
+    if (big) k_theta_poles_adj_last<true><<<l.grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, d, tw, perm);
+    else k_theta_poles_adj_last<false><<<l.grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, d, tw, perm);
+  } else {
+    if (big) k_theta_poles_adj_first<true><<<l.grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, d, tw, perm);
+    else k_theta_poles_adj_first<false><<<l.grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, d, tw, perm);
+  }
+}
 void launch_theta_poles(bool inverse, bool big, const Launch& l, cpx<double>* W, int N, int K, int Kp,
                         const FftDesc& d, const cpx<double>* tw, const int* perm) {
   if (inverse) {
@@ -69,6 +79,10 @@ cudaError_t allow_transform_smem<double>(int bytes) {
   upd(cudaFuncSetAttribute(k_theta_forward_poles<true>, a, bytes));
   upd(cudaFuncSetAttribute(k_theta_inverse_poles<false>, a, bytes));
   upd(cudaFuncSetAttribute(k_theta_inverse_poles<true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_poles_adj_first<false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_poles_adj_first<true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_poles_adj_last<false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_poles_adj_last<true>, a, bytes));
   upd(allow_pipe_smem<double>(bytes));
   return e;
 }

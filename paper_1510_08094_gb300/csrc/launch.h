@@ -92,6 +92,11 @@ size_t theta_fused_smem(int N, int cols, int threads);
 // d, tw and perm describe the length-2N FFT
 void launch_theta_poles(bool inverse, bool big, const Launch& l, cpx<double>* W, int N, int K, int Kp,
                         const FftDesc& d, const cpx<double>* tw, const int* perm);
+// their conjugate transposes for the adjoint: last = false the transpose of the
+// inverse (the adjoint's first colatitude stage, with the zero-mean closure's
+// transpose), last = true the transpose of the forward
+void launch_theta_poles_adj(bool last, bool big, const Launch& l, cpx<double>* W, int N, int K, int Kp,
+                            const FftDesc& d, const cpx<double>* tw, const int* perm);
 // the FP32 + refinement form's fused colatitude stage (fused_refine.cuh): one
 // CTA per column k >= 1 (column 0 is the FP64 zonal path's), in place in W
 // (double-float spectrum); refine_fused_smem dynamic bytes

@@ -88,4 +88,89 @@ __global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_inverse_poles(
   for (int i = threadIdx.x; i <= N; i += blockDim.x) W[(size_t)i * Kp + k] = sm[i < N ? N + i : 0];
 }
 
+// ---------------------------------------------------------------------------
+// The adjoint (ubar -> fbar) runs the conjugate transposes of the two maps
+// above, per column, with the same FFT:
+//   of the inverse (first colatitude stage of the adjoint): with G_p = Ubar at
+//     the rows' positions (p = N + i for row i < N, p = 0 for row N, zero at
+//     p = 1..N-1) and Y its length-m DFT (exp(-2 pi i q p / m)),
+//       Xbar_0 = Y_0,  Xbar_j = (-1)^j (Y_j + (-1)^k Y_{m-j}),  j = 1..N-1,
+//     and for k = 0 the transpose of the zero-mean closure:
+//       Xbar_j += 2 Xbar_0 / (j^2 - 1) for even j >= 2;
+//   of the forward (last colatitude stage of the adjoint): with v the inverse
+//     DFT of z_q = (-1)^q Fbar_q (q < N, zero above),
+//       gbar_i = (v_{N+i} [i < N] + (-1)^k v_{N-i} [i >= 1]) / m,  i = 0..N.
+// ---------------------------------------------------------------------------
+template <bool BIG>
+__global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_poles_adj_first(
+    cpx<double>* __restrict__ W, int N, int K, int Kp, FftDesc d, const cpx<double>* __restrict__ tw,
+    const int* __restrict__ perm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<double>* sm = reinterpret_cast<cpx<double>*>(smem_raw);
+  const int k = blockIdx.x;
+  if (k >= K) return;
+  const int m = 2 * N;
+  const bool odd = (k & 1) != 0;
+  for (int p = threadIdx.x; p < m; p += blockDim.x) {
+    cpx<double> v = {0.0, 0.0};
+    if (p >= N) v = W[(size_t)(p - N) * Kp + k];
+    else if (p == 0) v = W[(size_t)N * Kp + k];
+    sm[__ldg(perm + p)] = v;
+  }
+  __syncthreads();
+  fft_run<-1, BIG>(sm, 1, d, tw);
+  __syncthreads();
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    cpx<double> y = sm[j];
+    if (j > 0) {
+      const cpx<double> yc = sm[m - j];
+      y = odd ? cpx<double>{y.re - yc.re, y.im - yc.im} : cpx<double>{y.re + yc.re, y.im + yc.im};
+    }
+    if (j & 1) y = {-y.re, -y.im};
+    W[(size_t)j * Kp + k] = y;
+  }
+  if (k == 0) {     // uniform over the block
+    __syncthreads();
+    const cpx<double> x0 = W[0];
+    for (int j = 2 + 2 * (int)threadIdx.x; j < N; j += 2 * (int)blockDim.x) {
+      const double w = 2.0 / ((double)j * (double)j - 1.0);
+      cpx<double>& x = W[(size_t)j * Kp];
+      x = {fma(w, x0.re, x.re), fma(w, x0.im, x.im)};
+    }
+  }
+}
+
+template <bool BIG>
+__global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_poles_adj_last(
+    cpx<double>* __restrict__ W, int N, int K, int Kp, FftDesc d, const cpx<double>* __restrict__ tw,
+    const int* __restrict__ perm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<double>* sm = reinterpret_cast<cpx<double>*>(smem_raw);
+  const int k = blockIdx.x;
+  if (k >= K) return;
+  const int m = 2 * N;
+  const bool odd = (k & 1) != 0;
+  for (int q = threadIdx.x; q < m; q += blockDim.x) {
+    cpx<double> v = {0.0, 0.0};
+    if (q < N) {
+      v = W[(size_t)q * Kp + k];
+      if (q & 1) v = {-v.re, -v.im};
+    }
+    sm[__ldg(perm + q)] = v;
+  }
+  __syncthreads();
+  fft_run<+1, BIG>(sm, 1, d, tw);
+  __syncthreads();
+  const double inv_m = 1.0 / (double)m;
+  for (int i = threadIdx.x; i <= N; i += blockDim.x) {
+    cpx<double> g = {0.0, 0.0};
+    if (i < N) g = sm[N + i];
+    if (i >= 1) {
+      const cpx<double> t = sm[N - i];
+      g = odd ? cpx<double>{g.re - t.re, g.im - t.im} : cpx<double>{g.re + t.re, g.im + t.im};
+    }
+    W[(size_t)i * Kp + k] = {g.re * inv_m, g.im * inv_m};
+  }
+}
+
 }  // namespace sp

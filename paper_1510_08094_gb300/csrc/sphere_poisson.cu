@@ -632,7 +632,10 @@ void enqueue_fp64(sp_plan_t p, bool adj, const double* in, double* out, void* ws
   rows_forward_stage<double>(p, adj, st, in, W, p->tw_row, p->post_row, p->row_scale, p->row_scale, nullptr, ov);
   m.mark(1);
   const Launch pole{dim3(p->K), p->pole_threads, p->pole_smem, st};
-  if (p->poles)   // forward only (the adjoint of this grid is not built)
+  if (p->poles && adj)
+    sp::launch_theta_poles_adj(false, p->big_pole, pole, W, p->N, p->K, p->Kp, p->pole_fft, p->tw_pole,
+                               p->perm_pole);
+  else if (p->poles)
     sp::launch_theta_poles(false, p->big_pole, pole, W, p->N, p->K, p->Kp, p->pole_fft, p->tw_pole, p->perm_pole);
   else
     launch_theta_forward_x<double>(p, adj, st, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
@@ -640,7 +643,10 @@ void enqueue_fp64(sp_plan_t p, bool adj, const double* in, double* out, void* ws
   m.mark(2);
   sp::launch_solve<double>(adj, solve, W, p->fac_l, p->fac_iu, p->fac_cu, p->N, p->K, p->Kp);
   m.mark(3);
-  if (p->poles)
+  if (p->poles && adj)
+    sp::launch_theta_poles_adj(true, p->big_pole, pole, W, p->N, p->K, p->Kp, p->pole_fft, p->tw_pole,
+                               p->perm_pole);
+  else if (p->poles)
     sp::launch_theta_poles(true, p->big_pole, pole, W, p->N, p->K, p->Kp, p->pole_fft, p->tw_pole, p->perm_pole);
   else
     launch_theta_inverse_x<double>(p, adj, st, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
@@ -827,7 +833,6 @@ int launch_solve(sp_plan_t p, const double* in, double* out, void* workspace, cu
     return launch_batched(p, in, out, workspace, st);
   }
   if (p->precision == SP_FP64) {
-    if (ADJ && p->poles) return SP_ERR_UNSUPPORTED;
     enqueue_fp64(p, ADJ, in, out, workspace, st);
   } else if (p->precision == SP_FP32) {
     enqueue_fp32(p, ADJ, in, out, workspace, st);

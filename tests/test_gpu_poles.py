@@ -10,8 +10,10 @@ element by element on rough N(0,1) input (pole rows included) from 1 x 2 to
 band-limited series on every row up to the bench's 5000 x 10000 grid and the
 largest pole grid (2 n_theta = 12288); the mean of f against the oracle's
 surface integral and the paper's worked example; the host-buffer and
-allocation-free calls against the device solve; and the calls a pole plan
-refuses."""
+allocation-free calls against the device solve; the transpose (adjoint)
+against the oracle's element by element, by the dot-product identity up to the
+bench's grid, and through autograd against a central difference; and the
+calls a pole plan refuses."""
 
 import math
 
@@ -147,12 +149,49 @@ def test_pole_host_and_noalloc_solves_match_device(sp, nt, nl):
     assert plan.launches() == sp.Plan(nt, nl).launches()
 
 
+@pytest.mark.parametrize("nt,nl", [(1, 2), (2, 4), (3, 6), (5, 10), (8, 16), (13, 26), (33, 70), (64, 128),
+                                   (75, 150)])
+def test_pole_adjoint_matches_oracle(sp, nt, nl):
+    g = np.random.default_rng(31 * nt + nl).standard_normal((nt + 1, nl))
+    ref = O.poisson_poles_adjoint(g)
+    out = sp.Plan(nt, nl, grid="poles").solve_adjoint(torch.tensor(g, device="cuda")).cpu().numpy()
+    scale = max(float(np.abs(ref).max()), 1e-300)
+    assert float(np.abs(out - ref).max()) / scale < TOL or float(np.abs(out - ref).max()) < 1e-15 * np.abs(g).max()
+
+
+@pytest.mark.parametrize("nt,nl", [(512, 1024), (5000, 10000)])
+def test_pole_adjoint_dot_product(sp, nt, nl):
+    gen = torch.Generator(device="cuda").manual_seed(nt)
+    f = torch.randn(nt + 1, nl, dtype=torch.float64, device="cuda", generator=gen)
+    g = torch.randn(nt + 1, nl, dtype=torch.float64, device="cuda", generator=gen)
+    plan = sp.Plan(nt, nl, grid="poles")
+    lhs = float((plan.solve(f) * g).sum())
+    rhs = float((f * plan.solve_adjoint(g)).sum())
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs), (lhs, rhs)
+
+
+def test_pole_autograd_matches_central_difference(sp):
+    # loss = <u(f), w>: its gradient is S^T w; check one directional derivative
+    nt, nl = 40, 80
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    f = torch.randn(nt + 1, nl, dtype=torch.float64, device="cuda", generator=gen).requires_grad_(True)
+    w = torch.randn(nt + 1, nl, dtype=torch.float64, device="cuda", generator=gen)
+    d = torch.randn(nt + 1, nl, dtype=torch.float64, device="cuda", generator=gen)
+    loss = (sp.poisson(f, grid="poles") * w).sum()
+    loss.backward()
+    h = 1e-6
+    with torch.no_grad():
+        lp = float((sp.poisson(f + h * d, grid="poles") * w).sum())
+        lm = float((sp.poisson(f - h * d, grid="poles") * w).sum())
+    fd = (lp - lm) / (2 * h)
+    an = float((f.grad * d).sum())
+    assert abs(fd - an) < 1e-7 * max(abs(an), 1.0), (fd, an)
+
+
 def test_pole_plan_refusals(sp):
     nt, nl = 16, 32
     plan = sp.Plan(nt, nl, grid="poles")
     f = torch.zeros(nt + 1, nl, dtype=torch.float64, device="cuda")
-    with pytest.raises(RuntimeError):
-        plan.solve_adjoint(f)
     with pytest.raises(RuntimeError):
         plan.coeffs2(f)
     with pytest.raises(ValueError):
