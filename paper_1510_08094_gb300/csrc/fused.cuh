@@ -393,6 +393,161 @@ __device__ __forceinline__ void fused_solve_reg(cpx<T>* __restrict__ X, int js, 
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// The transposed eliminations of the adjoint (the transpose of fused_solve):
+// with the same top-down factorisation M = L U of each chain,
+//   U^T p = b:  p_t = (1/u_t) (b_t - c_{j-2} p_{t-1})          (t increasing),
+//   L^T r = p:  r_t = p_t - (a_{j+2}/u_t) r_{t+1}               (t decreasing),
+// both affine first-order recurrences run as the same chunked scans, and before
+// them the transposed row-0 closure: for even k != 0, Fbar_0 = -Xbar_0/k^2 and
+// Xbar_2 += Xbar_0/k^2; for odd k and k = 0, Fbar_0 = 0 (the k = 0 column is the
+// FP64 zonal path's).  Pivots from the per-column table, in registers when the chunk is
+// short enough (R of them), else read in each pass.  Whole CTA; ends with a
+// barrier.
+template <typename T, int R>
+__device__ __forceinline__ void fused_solve_adj_impl(cpx<T>* __restrict__ X, int js, int cs,
+                                                     ScanSlot<T>* __restrict__ slot, int k0, int cols, int N,
+                                                     int K, const T* __restrict__ fiu) {
+  // transposed closure of row 0, then the chains on rows j >= 1
+  if (threadIdx.x < cols) {
+    const int kc = k0 + threadIdx.x;
+    if (kc < K) {
+      cpx<T>& x0 = X[threadIdx.x * cs];
+      const cpx<T> xb0 = x0;
+      if (kc == 0 || (kc & 1)) {
+        x0 = {(T)0, (T)0};
+      } else {
+        const T ik2 = (T)(1.0 / ((double)kc * (double)kc));
+        x0 = {-xb0.re * ik2, -xb0.im * ik2};
+        if (N > 2) {
+          cpx<T>& x2 = X[2 * js + threadIdx.x * cs];
+          x2 = {fma(ik2, xb0.re, x2.re), fma(ik2, xb0.im, x2.im)};
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const int chains = 2 * cols;
+  const int ch = threadIdx.x % chains, p = threadIdx.x / chains;
+  const int P = blockDim.x / chains;
+  const int c = ch >> 1, j0 = (ch & 1) ? 2 : 1;
+  const int k = k0 + c;
+  const int M = (j0 < N) ? (N - 1 - j0) / 2 + 1 : 0;
+  const int C = ((M + P - 1) / P) | 1;
+  const int s = min(M, p * C), e = min(M, s + C);
+  const bool live = k < K && p < P;
+  const size_t tcol = (size_t)(live ? k : 0) * N;
+  ScanSlot<T>* mine = slot + threadIdx.x;
+  cpx<T>* Xc = X + c * cs;
+  // pivot of chain row t (t in the chunk)
+  T iu[R > 0 ? R : 1];
+  if constexpr (R > 0) {
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int t = s + q;
+      iu[q] = (live && t < e) ? __ldg(fiu + tcol + j0 + 2 * t) : (T)0;
+    }
+  }
+  auto piv = [&](int q, int t) -> T {
+    if constexpr (R > 0) return iu[q];
+    else return __ldg(fiu + tcol + j0 + 2 * t);
+  };
+  const int span = R > 0 ? R : C;     // loop bound (rows past e are skipped)
+  // U^T p = b: p_t = iu_t b_t - (c_{j-2} iu_t) p_{t-1}
+  {
+    T A = (T)1;
+    cpx<T> z = {(T)0, (T)0};
+#pragma unroll
+    for (int q = 0; q < span; ++q) {
+      const int t = s + q;
+      if (live && t < e) {
+        const int j = j0 + 2 * t;
+        const T u = piv(q, t);
+        const T al = t > 0 ? -band_c<T>(j - 2) * u : (T)0;
+        const cpx<T> b = Xc[j * js];
+        z = {fma(al, z.re, u * b.re), fma(al, z.im, u * b.im)};
+        A = A * al;
+      }
+    }
+    mine->a = A;
+    mine->z = z;
+  }
+  __syncthreads();
+  {
+    const int w = threadIdx.x >> 5;
+    if (w < chains && k0 + (w >> 1) < K) chain_carry_scan(slot + w, chains, P, false);
+  }
+  __syncthreads();
+  {
+    cpx<T> z = mine->z;
+#pragma unroll
+    for (int q = 0; q < span; ++q) {
+      const int t = s + q;
+      if (live && t < e) {
+        const int j = j0 + 2 * t;
+        const T u = piv(q, t);
+        const T al = t > 0 ? -band_c<T>(j - 2) * u : (T)0;
+        cpx<T>& b = Xc[j * js];
+        z = {fma(al, z.re, u * b.re), fma(al, z.im, u * b.im)};
+        b = z;
+      }
+    }
+  }
+  __syncthreads();
+  // L^T r = p: r_t = p_t - (a_{j+2} iu_t) r_{t+1}
+  {
+    T A = (T)1;
+    cpx<T> z = {(T)0, (T)0};
+#pragma unroll
+    for (int q = span - 1; q >= 0; --q) {
+      const int t = s + q;
+      if (live && t < e) {
+        const int j = j0 + 2 * t;
+        const T al = t < M - 1 ? -band_a<T>(j + 2) * piv(q, t) : (T)0;
+        const cpx<T> pv = Xc[j * js];
+        z = {fma(al, z.re, pv.re), fma(al, z.im, pv.im)};
+        A = A * al;
+      }
+    }
+    mine->a = A;
+    mine->z = z;
+  }
+  __syncthreads();
+  {
+    const int w = threadIdx.x >> 5;
+    if (w < chains && k0 + (w >> 1) < K) chain_carry_scan(slot + w, chains, P, true);
+  }
+  __syncthreads();
+  {
+    cpx<T> z = mine->z;
+#pragma unroll
+    for (int q = span - 1; q >= 0; --q) {
+      const int t = s + q;
+      if (live && t < e) {
+        const int j = j0 + 2 * t;
+        const T al = t < M - 1 ? -band_a<T>(j + 2) * piv(q, t) : (T)0;
+        cpx<T>& pv = Xc[j * js];
+        z = {fma(al, z.re, pv.re), fma(al, z.im, pv.im)};
+        pv = z;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void fused_solve_adj(cpx<T>* __restrict__ X, int js, int cs,
+                                                ScanSlot<T>* __restrict__ slot, int k0, int cols, int N, int K,
+                                                const T* __restrict__ fiu) {
+  const int P = blockDim.x / (2 * cols);
+  const int M1 = (1 < N) ? (N - 2) / 2 + 1 : 0;
+  const int C1 = ((M1 + P - 1) / P) | 1;
+  if (C1 <= 12) return fused_solve_adj_impl<T, 12>(X, js, cs, slot, k0, cols, N, K, fiu);
+  if (C1 <= 18) return fused_solve_adj_impl<T, 18>(X, js, cs, slot, k0, cols, N, K, fiu);
+  if (C1 <= 24) return fused_solve_adj_impl<T, 24>(X, js, cs, slot, k0, cols, N, K, fiu);
+  fused_solve_adj_impl<T, 0>(X, js, cs, slot, k0, cols, N, K, fiu);
+}
+
 template <typename T, bool BIG>
 __global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_fused(
     cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d, const cpx<T>* __restrict__ tw,
@@ -499,7 +654,9 @@ __global__ void __cluster_dims__(kFuseCluster, 1, 1) __launch_bounds__(BIG ? 256
 // natural-order pairs (j, N - j) of each column c of sm ([c][N]), the forward
 // form of theta_forward_finish: each thread reads a pair and writes the same
 // pair.  Columns k >= K are left alone.
-template <typename T>
+// ADJ: the adjoint's form (the transpose of theta_inverse, as theta_forward's
+// adjoint): called with the unscaled table, the j = 0 output of even k halved.
+template <typename T, bool ADJ = false>
 __device__ __forceinline__ void post_twiddle_inplace(cpx<T>* __restrict__ sm, int k0, int cols, int N, int K,
                                                      const cpx<T>* __restrict__ post_s) {
   const int cs = __ffs(cols) - 1;
@@ -517,7 +674,7 @@ __device__ __forceinline__ void post_twiddle_inplace(cpx<T>* __restrict__ sm, in
     const cpx<T> pj = {fma(w.re, S.re, -(w.im * D.im)), fma(w.re, S.im, w.im * D.re)};
     const cpx<T> pjj = {fma(-w.im, S.re, -(w.re * D.im)), fma(-w.im, S.im, w.re * D.re)};
     if ((k & 1) == 0) {
-      V[j] = pj;
+      V[j] = (ADJ && j == 0) ? cpx<T>{(T)0.5 * pj.re, (T)0.5 * pj.im} : pj;
       if (pair) V[jj] = pjj;
     } else {
       V[j] = j == 0 ? cpx<T>{(T)0, (T)0} : cpx<T>{pjj.im, -pjj.re};
@@ -528,7 +685,8 @@ __device__ __forceinline__ void post_twiddle_inplace(cpx<T>* __restrict__ sm, in
 
 // In-place pre-twiddle of the inverse colatitude transform (the forward form
 // of theta_inverse_load) in natural order; columns k >= K are zeroed.
-template <typename T>
+// ADJ: the adjoint's form (the transpose of theta_forward): inputs j >= 1 halved.
+template <typename T, bool ADJ = false>
 __device__ __forceinline__ void pre_twiddle_inplace(cpx<T>* __restrict__ sm, int k0, int cols, int N, int K,
                                                     const cpx<T>* __restrict__ post) {
   const int cs = __ffs(cols) - 1;
@@ -548,7 +706,11 @@ __device__ __forceinline__ void pre_twiddle_inplace(cpx<T>* __restrict__ sm, int
       if (odd) V[0] = {(T)0, (T)0};
       continue;
     }
-    const cpx<T> xa = V[j], xb = V[jj];
+    cpx<T> xa = V[j], xb = V[jj];
+    if (ADJ) {
+      xa = {(T)0.5 * xa.re, (T)0.5 * xa.im};
+      xb = {(T)0.5 * xb.re, (T)0.5 * xb.im};
+    }
     const cpx<T> ya = odd ? xb : xa, yb = odd ? xa : xb;
     V[j] = cmul(conj(ldg_c(post + j)), cpx<T>{ya.re + yb.im, ya.im - yb.re});
     if (jj != j) V[jj] = cmul(conj(ldg_c(post + jj)), cpx<T>{yb.re + ya.im, yb.im - ya.re});
@@ -556,10 +718,12 @@ __device__ __forceinline__ void pre_twiddle_inplace(cpx<T>* __restrict__ sm, int
 }
 
 // The store after a decimation-in-frequency inverse: output i of column c is
-// at sm[c N + perm[makhoul_pos(i, N)]]; on odd k the factor i (-1)^i.
-template <typename T>
+// at sm[c N + perm[makhoul_pos(i, N)]]; on odd k the factor i (-1)^i; SCALED:
+// times `scale` (the adjoint's 1/N).
+template <typename T, bool SCALED = false>
 __device__ __forceinline__ void store_dif_columns(const cpx<T>* __restrict__ sm, cpx<T>* __restrict__ W, int k0,
-                                                  int cols, int N, int K, int Kp, const int* __restrict__ perm) {
+                                                  int cols, int N, int K, int Kp, const int* __restrict__ perm,
+                                                  T scale = (T)1) {
   const int cs = __ffs(cols) - 1;
   for (int idx = threadIdx.x; idx < N * cols; idx += blockDim.x) {
     const int i = idx >> cs, c = idx & (cols - 1);
@@ -567,8 +731,61 @@ __device__ __forceinline__ void store_dif_columns(const cpx<T>* __restrict__ sm,
     if (k >= K) continue;
     cpx<T> v = sm[c * N + __ldg(perm + makhoul_pos(i, N))];
     if (k & 1) v = {neg_if(v.im, !(i & 1)), neg_if(v.re, (i & 1) != 0)};
+    if (SCALED) v = {scale * v.re, scale * v.im};
     W[(size_t)i * Kp + k] = v;
   }
+}
+
+// The tile load of the single-buffer kernels: columns [k0, k0 + cols) of W
+// (Makhoul reordering, digit-reversed positions; the factor (-1)^i on odd k)
+// into sm, by TMA with use_tma (two columns per CTA) or by per-thread loads.
+// false (uniformly over the block) if the TMA wait gave up; ends with a barrier.
+__device__ __forceinline__ bool fused1_load(cpx<float>* sm, uint64_t& bar, const cpx<float>* __restrict__ W, int N,
+                                            int K, int Kp, int cols, int k0, const int* __restrict__ perm,
+                                            const CUtensorMap* tmW, int use_tma, int* __restrict__ status) {
+  const int nbox = (N + kFusedBoxRows - 1) / kFusedBoxRows;
+  const size_t land = (size_t)nbox * kFusedBoxRows * cols * sizeof(cpx<float>);
+  if (use_tma) {
+    if (threadIdx.x == 0) {
+      mbar_init(&bar, 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
+    // (sm is 128-byte aligned by construction and each box is 4096 bytes; a
+    // misaligned destination is not issued, and the wait below reports it)
+    if (threadIdx.x == 0 && (smem_u32(sm) & 127u) == 0) {
+      mbar_expect_tx(&bar, (unsigned)land);
+      for (int b = 0; b < nbox; ++b) tma_load_2d(sm + b * kFusedBoxRows * 2, tmW, 2 * k0, b * kFusedBoxRows, &bar);
+    }
+    const bool ok = mbar_wait_bounded(&bar, 0, kTmaPolls);
+    if (__syncthreads_or(!ok)) {
+      mbar_wait_bounded(&bar, 0, kTmaPolls);            // the copies still in flight
+      __syncthreads();
+      if (threadIdx.x == 0) atomicExch(status, kStatusTmaTimeout);
+      return false;
+    }
+    // row-ordered elements e = 2 i + c to their digit-reversed positions, through registers
+    cpx<float> v[kFusedTmaRegs];
+#pragma unroll
+    for (int t = 0; t < kFusedTmaRegs; ++t) {
+      const int e = (int)threadIdx.x + t * (int)blockDim.x;
+      if (e < 2 * N) v[t] = sm[e];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < kFusedTmaRegs; ++t) {
+      const int e = (int)threadIdx.x + t * (int)blockDim.x;
+      if (e < 2 * N) {
+        const int i = e >> 1, c = e & 1, k = k0 + c;
+        const cpx<float> z = k < K ? neg_if(v[t], (k & 1) && (i & 1)) : cpx<float>{0.f, 0.f};
+        sm[c * N + __ldg(perm + makhoul_pos(i, N))] = z;
+      }
+    }
+  } else {
+    theta_forward_load<float>(k0, sm, FromGlobal<cpx<float>>{W + k0, (size_t)Kp}, N, K, cols, perm);
+  }
+  __syncthreads();
+  return true;
 }
 
 // Single-buffer form: the tile lives in one shared-memory buffer ([c][N]) from
@@ -602,46 +819,7 @@ __global__ void __launch_bounds__(BIG ? 256 : 512, BIG ? 1 : 2) k_theta_fused1(
   const int k0 = blockIdx.x * cols;
 
   // 1. load (Makhoul reordering, digit-reversed positions) and forward DIT transform
-  if (use_tma) {
-    if (threadIdx.x == 0) {
-      mbar_init(&bar, 1);
-      mbar_init_fence();
-    }
-    __syncthreads();
-    // (sm is 128-byte aligned by construction and each box is 4096 bytes; a
-    // misaligned destination is not issued, and the wait below reports it)
-    if (threadIdx.x == 0 && (smem_u32(sm) & 127u) == 0) {
-      mbar_expect_tx(&bar, (unsigned)land);
-      for (int b = 0; b < nbox; ++b) tma_load_2d(sm + b * kFusedBoxRows * 2, &tmW, 2 * k0, b * kFusedBoxRows, &bar);
-    }
-    const bool ok = mbar_wait_bounded(&bar, 0, kTmaPolls);
-    if (__syncthreads_or(!ok)) {
-      mbar_wait_bounded(&bar, 0, kTmaPolls);            // the copies still in flight
-      __syncthreads();
-      if (threadIdx.x == 0) atomicExch(status, kStatusTmaTimeout);
-      return;
-    }
-    // row-ordered elements e = 2 i + c to their digit-reversed positions, through registers
-    cpx<float> v[kFusedTmaRegs];
-#pragma unroll
-    for (int t = 0; t < kFusedTmaRegs; ++t) {
-      const int e = (int)threadIdx.x + t * (int)blockDim.x;
-      if (e < 2 * N) v[t] = sm[e];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < kFusedTmaRegs; ++t) {
-      const int e = (int)threadIdx.x + t * (int)blockDim.x;
-      if (e < 2 * N) {
-        const int i = e >> 1, c = e & 1, k = k0 + c;
-        const cpx<float> z = k < K ? neg_if(v[t], (k & 1) && (i & 1)) : cpx<float>{0.f, 0.f};
-        sm[c * N + __ldg(perm + makhoul_pos(i, N))] = z;
-      }
-    }
-  } else {
-    theta_forward_load<float>(k0, sm, FromGlobal<cpx<float>>{W + k0, (size_t)Kp}, N, K, cols, perm);
-  }
-  __syncthreads();
+  if (!fused1_load(sm, bar, W, N, K, Kp, cols, k0, perm, &tmW, use_tma, status)) return;
   fft_run<-1, BIG>(sm, cols, d, tw);
   // 2. post-twiddle in place on the pairs (j, N - j) (theta_forward_finish, forward form)
   post_twiddle_inplace<float>(sm, k0, cols, N, K, post_s);
@@ -656,6 +834,39 @@ __global__ void __launch_bounds__(BIG ? 256 : 512, BIG ? 1 : 2) k_theta_fused1(
   //    inverse Makhoul reordering and, on odd k, the factor i (-1)^i
   fft_run_dif<+1, BIG>(sm, cols, d, tw);
   store_dif_columns<float>(sm, W, k0, cols, N, K, Kp, perm);
+}
+
+// The adjoint's colatitude stage in the same single buffer: the transposes of
+// theta_inverse (the forward DIT transform, the post-twiddle with the unscaled
+// table and the j = 0 output of even k halved), of the eliminations
+// (fused_solve_adj) and of theta_forward (the pre-twiddle with inputs j >= 1
+// halved, the DIF inverse, the store scaled by inv_n = 1/N): what
+// theta_forward<ADJ>, k_solve<ADJ> and theta_inverse<ADJ> compute in three
+// launches.
+template <bool BIG>
+__global__ void __launch_bounds__(BIG ? 256 : 512, BIG ? 1 : 2) k_theta_fused1_adj(
+    cpx<float>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d, const cpx<float>* __restrict__ tw,
+    const int* __restrict__ perm, const cpx<float>* __restrict__ post, const float* __restrict__ fiu, float inv_n,
+    const __grid_constant__ CUtensorMap tmW, int use_tma, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t bar;
+  unsigned char* smem_al = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  const size_t buf = ((size_t)cols * N * sizeof(cpx<float>) + 15) & ~(size_t)15;
+  const int nbox = (N + kFusedBoxRows - 1) / kFusedBoxRows;
+  const size_t land = (size_t)nbox * kFusedBoxRows * cols * sizeof(cpx<float>);
+  cpx<float>* sm = reinterpret_cast<cpx<float>*>(smem_al);
+  ScanSlot<float>* slot = reinterpret_cast<ScanSlot<float>*>(smem_al + (buf > land ? buf : land));
+  const int k0 = blockIdx.x * cols;
+
+  if (!fused1_load(sm, bar, W, N, K, Kp, cols, k0, perm, &tmW, use_tma, status)) return;
+  fft_run<-1, BIG>(sm, cols, d, tw);
+  post_twiddle_inplace<float, true>(sm, k0, cols, N, K, post);
+  __syncthreads();
+  fused_solve_adj<float>(sm, 1, N, slot, k0, cols, N, K, fiu);
+  pre_twiddle_inplace<float, true>(sm, k0, cols, N, K, post);
+  __syncthreads();
+  fft_run_dif<+1, BIG>(sm, cols, d, tw);
+  store_dif_columns<float, true>(sm, W, k0, cols, N, K, Kp, perm, inv_n);
 }
 
 }  // namespace sp

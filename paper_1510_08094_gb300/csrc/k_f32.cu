@@ -62,6 +62,8 @@ cudaError_t allow_transform_smem<float>(int bytes) {
   upd(cudaFuncSetAttribute(k_theta_fused_cl<true>, a, bytes));
   upd(cudaFuncSetAttribute(k_theta_fused1<false>, a, bytes));
   upd(cudaFuncSetAttribute(k_theta_fused1<true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_fused1_adj<false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_fused1_adj<true>, a, bytes));
   return e;
 }
 namespace {
@@ -123,6 +125,21 @@ void launch_theta_fused(bool big, const Launch& l, cpx<float>* W, int N, int K, 
   else
     k_theta_fused<float, false><<<l.grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, cols, d, tw, perm, post_s,
                                                                          post, fiu, inv_n);
+}
+void launch_theta_fused_adj(bool big, const Launch& l, cpx<float>* W, int N, int K, int Kp, int cols,
+                            const FftDesc& d, const cpx<float>* tw, const int* perm, const cpx<float>* post,
+                            const float* fiu, float inv_n, int* status) {
+  const int q = cols < 0 ? -cols : 1;
+  const dim3 grid((K + q - 1) / q);
+  CUtensorMap tm;
+  std::memset(&tm, 0, sizeof(tm));
+  const int use_tma = status && !big && fused1_tma_fits(N, q, l.threads) && encode_pair_map(&tm, W, N, Kp) ? 1 : 0;
+  if (big)
+    k_theta_fused1_adj<true><<<grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, q, d, tw, perm, post, fiu, inv_n,
+                                                                     tm, use_tma, status);
+  else
+    k_theta_fused1_adj<false><<<grid, l.threads, l.smem, l.stream>>>(W, N, K, Kp, q, d, tw, perm, post, fiu, inv_n,
+                                                                      tm, use_tma, status);
 }
 size_t theta_fused_smem(int N, int cols, int threads) {
   if (cols < 0) return fused1_smem_bytes(N, -cols, threads);

@@ -87,6 +87,12 @@ void launch_theta_fused(bool big, const Launch& l, cpx<float>* W, int N, int K, 
                         const cpx<float>* tw, const int* perm, const cpx<float>* post_s, const cpx<float>* post,
                         const float* fiu, float inv_n, int* status);
 size_t theta_fused_smem(int N, int cols, int threads);
+// the adjoint's colatitude stage (transposed transforms and eliminations) in
+// one launch: the single-buffer form, -cols columns per CTA (cols < 0; 1 else),
+// theta_fused_smem(N, cols, threads) bytes, post the unscaled DCT table
+void launch_theta_fused_adj(bool big, const Launch& l, cpx<float>* W, int N, int K, int Kp, int cols,
+                            const FftDesc& d, const cpx<float>* tw, const int* perm, const cpx<float>* post,
+                            const float* fiu, float inv_n, int* status);
 // the colatitude transforms of the grid with both poles (poles.cuh): one CTA
 // per column k < K (grid K), 2N complex doubles of dynamic shared memory;
 // d, tw and perm describe the length-2N FFT

@@ -696,6 +696,13 @@ void enqueue_fp32(sp_plan_t p, bool adj, const double* in, double* out, void* ws
                            static_cast<const cpx<float>*>(p->post_col_s_t), poc, p->fc_iu, inv_n, p->dev_status);
     m.mark(2);
     m.mark(3);
+  } else if (adj && p->fused && p->fuse_cols < 0) {
+    // the adjoint's colatitude stage in one launch, on the forward's single-buffer tile
+    sp::launch_theta_fused_adj(p->big_col, Launch{dim3(1), p->fuse_threads, p->fuse_smem, st}, W, p->N, p->K,
+                               p->Kp, p->fuse_cols, p->col_fft, twc, p->perm_col, poc, p->fc_iu, inv_n,
+                               p->dev_status);
+    m.mark(2);
+    m.mark(3);
   } else {
     launch_theta_forward_x<float>(p, adj, st, W, p->N, p->K, p->Kp, p->cols_per_cta, p->col_fft,
                                     twc, p->perm_col, adj ? poc : static_cast<const cpx<float>*>(p->post_col_s_t),
@@ -2445,7 +2452,8 @@ int sphere_poisson_launch_count(sp_plan_t plan, int adjoint, int* launches) {
   if (!launches) return SP_ERR_NULL;
   if (plan->batched) *launches = (plan->bsplit > 0 ? 1 : 0) + (plan->count > plan->bsplit ? 1 : 0);
   else if (plan->precision == SP_FP64) *launches = kStages;
-  else if (plan->precision == SP_FP32) *launches = (plan->fused && !adjoint ? kStages - 2 : kStages) + 3;
+  else if (plan->precision == SP_FP32)
+    *launches = (plan->fused && (!adjoint || plan->fuse_cols < 0) ? kStages - 2 : kStages) + 3;
   else if (adjoint) *launches = 0;
   else *launches = plan->fused ? 3 + 5 : kStages - 1 + 3 + (plan->sweeps + 1);
   return SP_OK;

@@ -49,12 +49,32 @@ def test_fp32_matches_oracle(sp, nt, nl):
     assert _rel(u, u_ref) < FP32_TOL
 
 
-@pytest.mark.parametrize("nt,nl", [(16, 32), (64, 128), (33, 70)])
+@pytest.mark.parametrize("nt,nl", [(16, 32), (64, 128), (33, 70), (5, 10), (2, 4), (100, 200), (75, 150)])
 def test_fp32_adjoint_matches_oracle(sp, nt, nl):
     g = np.random.default_rng(nt).standard_normal((nt, nl))
     ref = O.poisson_adjoint(g)
     out = sp.Plan(nt, nl, "fp32").solve_adjoint(torch.tensor(g, device="cuda")).cpu().numpy()
     assert _rel(out, ref) < FP32_TOL
+
+
+@pytest.mark.parametrize("nt,nl", [(256, 512), (1000, 2000), (5000, 10000), (6144, 12288)])
+def test_fp32_adjoint_dot_product(sp, nt, nl):
+    # the FP32 adjoint (its colatitude stage fused in one launch, the tile by TMA
+    # where two columns fit) against the FP32 forward by <S f, g> = <f, S^T g>,
+    # and against the FP64 adjoint
+    gen = torch.Generator(device="cuda").manual_seed(nt)
+    f = torch.randn(nt, nl, dtype=torch.float64, device="cuda", generator=gen)
+    g = torch.randn(nt, nl, dtype=torch.float64, device="cuda", generator=gen)
+    plan = sp.Plan(nt, nl, "fp32")
+    sg = plan.solve_adjoint(g)
+    sf = plan.solve(f)
+    lhs = float((sf * g).sum())
+    rhs = float((f * sg).sum())
+    # the sums cancel heavily for random f and g: bound by the norms instead
+    scale = float(sf.norm() * g.norm() + f.norm() * sg.norm())
+    assert abs(lhs - rhs) < 1e-6 * scale, (lhs, rhs, scale)
+    sg64 = sp.Plan(nt, nl, "fp64").solve_adjoint(g)
+    assert float((sg - sg64).abs().max() / sg64.abs().max()) < FP32_TOL
 
 
 @pytest.mark.parametrize("nt,nl", SIZES)
