@@ -48,20 +48,20 @@ FP64_PEAK_GFLOPS_FALLBACK = 1008.0
 # spectrum size n_theta * Kp (every stage streams the spectrum once or twice) and
 # reports null when the sources have changed since the capture.
 TRAFFIC_CAPTURE = {
-    "csrc_sha256": "7d63a2d00141864d",
+    "csrc_sha256": "4a9c478bb523e9f7",
     "n_theta": 5000, "n_lambda": 5000,
-    "bytes": {"rows_forward": 200336640 + 142869504, "theta_forward": 200851456 + 141943040,
-              "solve": 662401536 + 321671680, "theta_inverse": 200906752 + 142315008,
-              "rows_inverse": 200361728 + 143462656},
+    "bytes": {"rows_forward": 200250624 + 146526208, "theta_forward": 200994816 + 142276608,
+              "solve": 662278144 + 321565696, "theta_inverse": 200930560 + 142064384,
+              "rows_inverse": 200482560 + 145078528},
 }
 # the same for the FP32 form's dominant kernel, the fused colatitude stage
 # (k_theta_fused1 with two columns per CTA, its tile by TMA, at 5000 x 5000;
 # `ncu --section ... --metrics dram__bytes_read.sum,dram__bytes_write.sum` on
 # two launches after warm-up), over the sources it is compiled from
 TRAFFIC_CAPTURE_FP32 = {
-    "csrc_sha256": "d8ea4bef5b5cc6f0",
+    "csrc_sha256": "be0277e740998f8f",
     "n_theta": 5000, "n_lambda": 5000,
-    "bytes": {"theta_fused": 150894848 + 50328832},
+    "bytes": {"theta_fused": 150896896 + 50039296},
 }
 
 
