@@ -276,9 +276,14 @@ __device__ __forceinline__ void rows_forward_tile(int tile, cpx<T>* __restrict__
 // FP32 longitude kernels are bounded to 40 registers (small spills): five
 // 256-thread CTAs then fit per SM (their 40 KB of shared memory allows five)
 // instead of four, which took the forward kernel 0.306 -> 0.281 ms at
-// 5000 x 10000.
+// 5000 x 10000.  FP64 transform kernels (longitude and colatitude) are bounded
+// to 64 registers (about 100 bytes of spills per thread): two 512-thread CTAs
+// then fit per SM beside their 80 KB tiles, 32 warps instead of the 16 that
+// 84-106 registers allowed, and the FP64 pipe hides more of its dependent
+// latency (the FP64 solve 9.42 -> 9.27 ms at 5000 x 10000, every transform
+// 1.5-2 % faster).
 template <typename T, bool ADJ, bool BIG>
-__global__ void __launch_bounds__(BIG ? 256 : 512, (sizeof(T) == 4 && !BIG) ? 3 : 1) k_rows_forward(
+__global__ void __launch_bounds__(BIG ? 256 : 512, BIG ? 1 : (sizeof(T) == 4 ? 3 : (std::is_same<T, double>::value ? 2 : 1))) k_rows_forward(
     const double* __restrict__ f, cpx<T>* __restrict__ W, int nt, int n, int Kp, int rows,
     FftDesc d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
     const cpx<T>* __restrict__ post, const double* __restrict__ row_scale,
@@ -415,7 +420,7 @@ __device__ __forceinline__ void rows_inverse_tile(int tile, cpx<T>* __restrict__
 }
 
 template <typename T, bool ADJ, bool BIG>
-__global__ void __launch_bounds__(BIG ? 256 : 512, (sizeof(T) == 4 && !BIG) ? 3 : 1) k_rows_inverse(
+__global__ void __launch_bounds__(BIG ? 256 : 512, BIG ? 1 : (sizeof(T) == 4 ? 3 : (std::is_same<T, double>::value ? 2 : 1))) k_rows_inverse(
     const cpx<T>* __restrict__ W, double* __restrict__ u, int nt, int n, int Kp, int rows,
     FftDesc d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
     const cpx<T>* __restrict__ post, const double* __restrict__ row_scale,
@@ -552,7 +557,7 @@ __device__ __forceinline__ void theta_forward_tile(int tile, cpx<T>* __restrict_
 }
 
 template <typename T, bool ADJ, bool BIG>
-__global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_forward(
+__global__ void __launch_bounds__(BIG ? 256 : 512, (std::is_same<T, double>::value && !BIG) ? 2 : 1) k_theta_forward(
     cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d,
     const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
     T inv_n, int zonal) {
@@ -718,7 +723,7 @@ __device__ __forceinline__ void theta_inverse_tile(int tile, cpx<T>* __restrict_
 }
 
 template <typename T, bool ADJ, bool BIG>
-__global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_inverse(
+__global__ void __launch_bounds__(BIG ? 256 : 512, (std::is_same<T, double>::value && !BIG) ? 2 : 1) k_theta_inverse(
     cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d,
     const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
     T inv_n, int zonal) {
