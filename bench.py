@@ -48,20 +48,20 @@ FP64_PEAK_GFLOPS_FALLBACK = 1008.0
 # spectrum size n_theta * Kp (every stage streams the spectrum once or twice) and
 # reports null when the sources have changed since the capture.
 TRAFFIC_CAPTURE = {
-    "csrc_sha256": "4a9c478bb523e9f7",
+    "csrc_sha256": "0b9b4e97ebbf3a8d",
     "n_theta": 5000, "n_lambda": 5000,
-    "bytes": {"rows_forward": 200250624 + 146526208, "theta_forward": 200994816 + 142276608,
-              "solve": 662278144 + 321565696, "theta_inverse": 200930560 + 142064384,
-              "rows_inverse": 200482560 + 145078528},
+    "bytes": {"rows_forward": 200262144 + 146544640, "theta_forward": 200859392 + 159024640,
+              "solve": 662331136 + 321661440, "theta_inverse": 200991232 + 164858368,
+              "rows_inverse": 200418560 + 146610176},
 }
 # the same for the FP32 form's dominant kernel, the fused colatitude stage
 # (k_theta_fused1 with two columns per CTA, its tile by TMA, at 5000 x 5000;
 # `ncu --section ... --metrics dram__bytes_read.sum,dram__bytes_write.sum` on
 # two launches after warm-up), over the sources it is compiled from
 TRAFFIC_CAPTURE_FP32 = {
-    "csrc_sha256": "be0277e740998f8f",
+    "csrc_sha256": "ce527bed57b1eb4d",
     "n_theta": 5000, "n_lambda": 5000,
-    "bytes": {"theta_fused": 150896896 + 50039296},
+    "bytes": {"theta_fused": 150887936 + 49901824},
 }
 
 
