@@ -8,31 +8,51 @@
 
 namespace sp {
 
+// FP64 transforms whose passes all have scaled twiddle records run in the
+// kernels bounded to two 512-thread CTAs per SM (the *_two kernels)
+static bool two_ctas(const FftDesc& d) {
+  for (int s = 0; s < d.nstages; ++s) {
+    const int r = d.radix[s];
+    if (r != 2 && r != 3 && r != 4 && r != 5 && r != 8) return false;
+  }
+  return true;
+}
+
+#define SP_PICK64(FN, ADJV, BIGV, DESC, ...)                                                   \
+  do {                                                                                         \
+    if (!(BIGV) && two_ctas(DESC)) {                                                           \
+      if (ADJV) FN##_two<double, true><<<l.grid, l.threads, l.smem, l.stream>>>(__VA_ARGS__);  \
+      else FN##_two<double, false><<<l.grid, l.threads, l.smem, l.stream>>>(__VA_ARGS__);      \
+    } else {                                                                                   \
+      SP_PICK(FN, double, ADJV, BIGV, __VA_ARGS__);                                            \
+    }                                                                                          \
+  } while (0)
+
 template <>
 void launch_rows_forward<double>(bool adj, bool big, const Launch& l, const double* f, cpx<double>* W, int nt,
                                  int n, int Kp, int rows, const FftDesc& d, const cpx<double>* tw,
                                  const int* perm, const cpx<double>* post, const double* row_scale,
                                  const double* row_scale_t, cpx<double>* zonal) {
-  SP_PICK(k_rows_forward, double, adj, big, f, W, nt, n, Kp, rows, d, tw, perm, post, row_scale, row_scale_t, zonal);
+  SP_PICK64(k_rows_forward, adj, big, d, f, W, nt, n, Kp, rows, d, tw, perm, post, row_scale, row_scale_t, zonal);
 }
 template <>
 void launch_rows_inverse<double>(bool adj, bool big, const Launch& l, const cpx<double>* W, double* u, int nt,
                                  int n, int Kp, int rows, const FftDesc& d, const cpx<double>* tw,
                                  const int* perm, const cpx<double>* post, const double* row_scale,
                                  const double* row_scale_t, const cpx<double>* zonal) {
-  SP_PICK(k_rows_inverse, double, adj, big, W, u, nt, n, Kp, rows, d, tw, perm, post, row_scale, row_scale_t, zonal);
+  SP_PICK64(k_rows_inverse, adj, big, d, W, u, nt, n, Kp, rows, d, tw, perm, post, row_scale, row_scale_t, zonal);
 }
 template <>
 void launch_theta_forward<double>(bool adj, bool big, const Launch& l, cpx<double>* W, int N, int K, int Kp,
                                   int cols, const FftDesc& d, const cpx<double>* tw, const int* perm,
                                   const cpx<double>* post, double inv_n, int zonal) {
-  SP_PICK(k_theta_forward, double, adj, big, W, N, K, Kp, cols, d, tw, perm, post, inv_n, zonal);
+  SP_PICK64(k_theta_forward, adj, big, d, W, N, K, Kp, cols, d, tw, perm, post, inv_n, zonal);
 }
 template <>
 void launch_theta_inverse<double>(bool adj, bool big, const Launch& l, cpx<double>* W, int N, int K, int Kp,
                                   int cols, const FftDesc& d, const cpx<double>* tw, const int* perm,
                                   const cpx<double>* post, double inv_n, int zonal) {
-  SP_PICK(k_theta_inverse, double, adj, big, W, N, K, Kp, cols, d, tw, perm, post, inv_n, zonal);
+  SP_PICK64(k_theta_inverse, adj, big, d, W, N, K, Kp, cols, d, tw, perm, post, inv_n, zonal);
 }
 void launch_theta_poles_adj(bool last, bool big, const Launch& l, cpx<double>* W, int N, int K, int Kp,
                             const FftDesc& d, const cpx<double>* tw, const int* perm) {
@@ -83,6 +103,14 @@ cudaError_t allow_transform_smem<double>(int bytes) {
   upd(cudaFuncSetAttribute(k_theta_poles_adj_first<true>, a, bytes));
   upd(cudaFuncSetAttribute(k_theta_poles_adj_last<false>, a, bytes));
   upd(cudaFuncSetAttribute(k_theta_poles_adj_last<true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_rows_forward_two<double, false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_rows_forward_two<double, true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_rows_inverse_two<double, false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_rows_inverse_two<double, true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_forward_two<double, false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_forward_two<double, true>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_inverse_two<double, false>, a, bytes));
+  upd(cudaFuncSetAttribute(k_theta_inverse_two<double, true>, a, bytes));
   upd(allow_pipe_smem<double>(bytes));
   return e;
 }

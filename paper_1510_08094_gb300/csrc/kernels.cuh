@@ -276,14 +276,10 @@ __device__ __forceinline__ void rows_forward_tile(int tile, cpx<T>* __restrict__
 // FP32 longitude kernels are bounded to 40 registers (small spills): five
 // 256-thread CTAs then fit per SM (their 40 KB of shared memory allows five)
 // instead of four, which took the forward kernel 0.306 -> 0.281 ms at
-// 5000 x 10000.  FP64 transform kernels (longitude and colatitude) are bounded
-// to 64 registers (about 100 bytes of spills per thread): two 512-thread CTAs
-// then fit per SM beside their 80 KB tiles, 32 warps instead of the 16 that
-// 84-106 registers allowed, and the FP64 pipe hides more of its dependent
-// latency (the FP64 solve 9.42 -> 9.27 ms at 5000 x 10000, every transform
-// 1.5-2 % faster).
+// 5000 x 10000.  The FP64 transforms also come as the *_two kernels at the
+// end of this file, bounded to two 512-thread CTAs per SM.
 template <typename T, bool ADJ, bool BIG>
-__global__ void __launch_bounds__(BIG ? 256 : 512, BIG ? 1 : (sizeof(T) == 4 ? 3 : (std::is_same<T, double>::value ? 2 : 1))) k_rows_forward(
+__global__ void __launch_bounds__(BIG ? 256 : 512, (sizeof(T) == 4 && !BIG) ? 3 : 1) k_rows_forward(
     const double* __restrict__ f, cpx<T>* __restrict__ W, int nt, int n, int Kp, int rows,
     FftDesc d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
     const cpx<T>* __restrict__ post, const double* __restrict__ row_scale,
@@ -420,7 +416,7 @@ __device__ __forceinline__ void rows_inverse_tile(int tile, cpx<T>* __restrict__
 }
 
 template <typename T, bool ADJ, bool BIG>
-__global__ void __launch_bounds__(BIG ? 256 : 512, BIG ? 1 : (sizeof(T) == 4 ? 3 : (std::is_same<T, double>::value ? 2 : 1))) k_rows_inverse(
+__global__ void __launch_bounds__(BIG ? 256 : 512, (sizeof(T) == 4 && !BIG) ? 3 : 1) k_rows_inverse(
     const cpx<T>* __restrict__ W, double* __restrict__ u, int nt, int n, int Kp, int rows,
     FftDesc d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
     const cpx<T>* __restrict__ post, const double* __restrict__ row_scale,
@@ -557,7 +553,7 @@ __device__ __forceinline__ void theta_forward_tile(int tile, cpx<T>* __restrict_
 }
 
 template <typename T, bool ADJ, bool BIG>
-__global__ void __launch_bounds__(BIG ? 256 : 512, (std::is_same<T, double>::value && !BIG) ? 2 : 1) k_theta_forward(
+__global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_forward(
     cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d,
     const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
     T inv_n, int zonal) {
@@ -723,7 +719,7 @@ __device__ __forceinline__ void theta_inverse_tile(int tile, cpx<T>* __restrict_
 }
 
 template <typename T, bool ADJ, bool BIG>
-__global__ void __launch_bounds__(BIG ? 256 : 512, (std::is_same<T, double>::value && !BIG) ? 2 : 1) k_theta_inverse(
+__global__ void __launch_bounds__(BIG ? 256 : 512) k_theta_inverse(
     cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d,
     const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
     T inv_n, int zonal) {
@@ -1406,5 +1402,59 @@ __global__ void k_zonal_insert(const cpx<double>* __restrict__ Z, cpx<dd>* __res
 }
 
 #endif  // SP_REFINE_KERNELS
+
+// ---------------------------------------------------------------------------
+// The transform kernels bounded to 64 registers (about 100 bytes of spills per
+// thread, to L1): two 512-thread CTAs then fit per SM beside their 80 KB FP64
+// tiles, 32 warps instead of the 16 that 84-106 registers allow, and the FP64
+// pipe hides more of its dependent latency (the FP64 solve 9.42 -> 9.27 ms at
+// 5000 x 10000, every transform 1.5-2 % faster).  The FP64 launchers take them
+// for transforms whose passes all have scaled twiddle records (radices 2, 3,
+// 4, 5, 8); a radix-7 pass (plain twiddles) spills more under the bound and
+// runs faster in the kernels above.
+// ---------------------------------------------------------------------------
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(512, 2) k_rows_forward_two(
+    const double* __restrict__ f, cpx<T>* __restrict__ W, int nt, int n, int Kp, int rows,
+    FftDesc d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
+    const cpx<T>* __restrict__ post, const double* __restrict__ row_scale,
+    const T* __restrict__ row_scale_t, cpx<double>* __restrict__ zonal) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  rows_forward_tile<T, ADJ, false>(blockIdx.x, sm, f, W, nt, n, Kp, rows, d, tw, perm, post, row_scale, row_scale_t,
+                                   zonal);
+}
+
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(512, 2) k_rows_inverse_two(
+    const cpx<T>* __restrict__ W, double* __restrict__ u, int nt, int n, int Kp, int rows,
+    FftDesc d, const cpx<T>* __restrict__ tw, const int* __restrict__ perm,
+    const cpx<T>* __restrict__ post, const double* __restrict__ row_scale,
+    const T* __restrict__ row_scale_t, const cpx<double>* __restrict__ zonal) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  rows_inverse_tile<T, ADJ, false>(blockIdx.x, sm, W, u, nt, n, Kp, rows, d, tw, perm, post, row_scale, row_scale_t,
+                                   zonal);
+}
+
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(512, 2) k_theta_forward_two(
+    cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d,
+    const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
+    T inv_n, int zonal) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  theta_forward_tile<T, ADJ, false>(blockIdx.x, sm, W, N, K, Kp, cols, d, tw, perm, post, inv_n, zonal);
+}
+
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(512, 2) k_theta_inverse_two(
+    cpx<T>* __restrict__ W, int N, int K, int Kp, int cols, FftDesc d,
+    const cpx<T>* __restrict__ tw, const int* __restrict__ perm, const cpx<T>* __restrict__ post,
+    T inv_n, int zonal) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  theta_inverse_tile<T, ADJ, false>(blockIdx.x, sm, W, N, K, Kp, cols, d, tw, perm, post, inv_n, zonal);
+}
 
 }  // namespace sp
