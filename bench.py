@@ -48,20 +48,20 @@ FP64_PEAK_GFLOPS_FALLBACK = 1008.0
 # spectrum size n_theta * Kp (every stage streams the spectrum once or twice) and
 # reports null when the sources have changed since the capture.
 TRAFFIC_CAPTURE = {
-    "csrc_sha256": "0b9b4e97ebbf3a8d",
+    "csrc_sha256": "02e997e5d6337967",
     "n_theta": 5000, "n_lambda": 5000,
-    "bytes": {"rows_forward": 200262144 + 146544640, "theta_forward": 200859392 + 159024640,
-              "solve": 662331136 + 321661440, "theta_inverse": 200991232 + 164858368,
-              "rows_inverse": 200418560 + 146610176},
+    "bytes": {"rows_forward": 200256000 + 146959616, "theta_forward": 200861184 + 159193088,
+              "solve": 662352640 + 321982976, "theta_inverse": 201085696 + 164486400,
+              "rows_inverse": 200748032 + 146642688},
 }
 # the same for the FP32 form's dominant kernel, the fused colatitude stage
 # (k_theta_fused1 with two columns per CTA, its tile by TMA, at 5000 x 5000;
 # `ncu --section ... --metrics dram__bytes_read.sum,dram__bytes_write.sum` on
 # two launches after warm-up), over the sources it is compiled from
 TRAFFIC_CAPTURE_FP32 = {
-    "csrc_sha256": "ce527bed57b1eb4d",
+    "csrc_sha256": "825b545093ed33d5",
     "n_theta": 5000, "n_lambda": 5000,
-    "bytes": {"theta_fused": 150887936 + 49901824},
+    "bytes": {"theta_fused": 150896640 + 50061568},
 }
 
 
